@@ -1,0 +1,121 @@
+/*
+ * ibdvm_oracle.h -- interface of the plain FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE. Only the test suite, the smoke check of the entry
+ * module and the CPU-baseline leg of the benchmark load this library. The
+ * solver product never includes this header, never links the oracle and
+ * shares no code with it.
+ *
+ * The oracle follows the ghost-cell immersed-boundary discrete velocity
+ * method of Ge, Cai, Zhang and Xiao (arXiv 2512.20252) step by step:
+ *   Sec. 2.1  Shakhov model, moments (Eqs. moments1-3)
+ *   Sec. 2.2  discrete velocity equation, quadrature, finite volume,
+ *             upwind reconstruction with the van Leer limiter
+ *   Sec. 2.3  Maxwell gas-surface interaction, no-penetration density
+ *   Sec. 3.2  ghost, fluid, surface, donor and auxiliary cells; shifted
+ *             point; upwind-weighted compact interpolation; intersect-point
+ *             construction; ghost-cell construction; velocity-space cut cells
+ *   Sec. 4    reduced distributions h, b (2D), non-dimensional Maxwellians,
+ *             VHS viscosity, residual, forward Euler.
+ */
+#ifndef IBDVM_ORACLE_H
+#define IBDVM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Body kinds understood by the oracle. */
+enum {
+  OR_BODY_NONE = 0,
+  OR_BODY_CIRCLE = 1,    /* 2D: centre, radii[0] */
+  OR_BODY_ELLIPSE = 2,   /* 2D: centre, semi-axes radii[0] (along the rotated x) and radii[1], angle */
+  OR_BODY_SPHERE = 3,    /* 3D: centre, radii[0] */
+  OR_BODY_POLYGON = 4,   /* 2D: counter-clockwise vertices verts[2*nverts] */
+  OR_BODY_HALFSPACE = 5  /* 2D/3D: solid where (x - centre).radii <= 0; radii = unit normal into the gas */
+};
+
+/* Cell classes, Sec. 3.2.1. */
+enum { OR_FLUID = 0, OR_GHOST = 1, OR_SOLID = 2 };
+
+typedef struct {
+  /* physical grid: uniform Cartesian, n[a] cells on [lo[a], hi[a]] */
+  int dim;
+  int n[3];
+  double lo[3], hi[3];
+  /* velocity grid: nv[a] nodes on [vlo[a], vhi[a]], rule 0 = trapezoid, 1 = composite midpoint */
+  int nv[3];
+  double vlo[3], vhi[3];
+  int rule;
+  /* gas (non-dimensional, Sec. 4) */
+  double Kn, Ma, Pr, gamma, omega_vhs, alpha_vhs;
+  double rho_inf, T_inf;
+  double dir[3];
+  double cfl, dt; /* dt <= 0: dt from the CFL number */
+  /* body and wall (Sec. 2.3) */
+  int kind;
+  double center[3], radii[3], angle;
+  const double *verts;
+  int nverts;
+  double accom; /* Maxwell accommodation coefficient alpha */
+  double Tw, Uw[3];
+  double Lref; /* reference length (2D) or area (3D) for force coefficients; <= 0: from the body */
+  /* method switches */
+  int cutcell; /* 1: velocity-space cut-cell correction (Sec. 3.2.3); 0: node classification only */
+  int upwind;  /* 1: upwind weights with r pointing from the fluid cell to the ghost cell,
+                  2: upwind weights with r pointing from the ghost cell to the fluid cell,
+                  0: plain average 1/N_S */
+} or_params;
+
+typedef struct or_case or_case;
+
+or_case *or_create(const or_params *p);
+void or_destroy(or_case *C);
+
+/* sizes: ncell, nvel, ncomp, nlink, nghost, nfluid */
+void or_sizes(const or_case *C, long long *out6);
+double or_dt(const or_case *C);
+/* per-velocity node and weight: xi[k*3+a], w[k] */
+void or_velocities(const or_case *C, double *xi, double *w);
+/* cell classes */
+void or_cell_types(const or_case *C, unsigned char *types);
+/* link table in canonical order (ghost cell ascending, then direction 2*axis + (side > 0)) */
+void or_links(const or_case *C, int *ghost, int *donor, int *aux, int *axis, int *side,
+              double *xw, double *nw);
+/* incident-side velocity measure omega^g per link and velocity: wg[L*nvel + k] */
+void or_cut_table(const or_case *C, double *wg);
+/* surface cells of every ghost (CSR): offsets[nghost+1], cells[...] */
+int or_surface_count(const or_case *C);
+void or_surface_cells(const or_case *C, int *ghost_cell, int *offsets, int *cells);
+
+/* state: f[cell][k][comp] */
+void or_get_f(const or_case *C, double *f);
+void or_set_f(or_case *C, const double *f);
+void or_freestream(const or_case *C, double *finf);
+
+/* one forward-Euler step per iteration; residual of the last step */
+int or_step(or_case *C, int nsteps, double *residual);
+/* conservative variables W[cell][dim+2] and heat flux q[cell][dim] of the current state */
+void or_moments(const or_case *C, double *W, double *q);
+/* surface force and heat flux, Eq. moments applied to the face fluxes on the link faces */
+void or_forces(const or_case *C, double *F3, double *Q, double *CD, double *CL);
+
+/* the ghost band on the given state (Sec. 3.2.1 steps 1-4) */
+void or_ghost_band(const or_case *C, const double *f, double *fgc, double *fsp, double *fiw,
+                   double *fstarw, double *fstargc, double *rhow);
+
+/* building blocks, exposed for the pins */
+double or_mu0(double Kn, double alpha, double omega);
+double or_vanleer(double s1, double s2);
+void or_cell_moments(const or_case *C, const double *fcell, double *out);
+void or_shakhov(const or_case *C, double rho, const double *U, double T, const double *q,
+                double *gS);
+void or_maxwellian(const or_case *C, double rho, const double *U, double T, double *g);
+double or_cut_fraction_2d(const double *blo, const double *bhi, const double *n);
+double or_cut_fraction_3d(const double *blo, const double *bhi, const double *n);
+double or_residual(const or_case *C, const double *Wold, const double *Wnew);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,176 @@
+"""Workload presets and seeded synthetic case generators.
+
+This module holds case descriptions only (grid sizes, velocity grids, gas and
+body parameters, seeded draws of batched and served cases).  It contains none
+of the method's arithmetic, so both the CUDA path and the CPU oracle can be
+driven from the same dicts.
+
+Case dict keys: dim, n, lo, hi (physical grid); nv, vlo, vhi, rule (velocity
+grid, rule "trapezoid" or "midpoint"); Kn, Ma, Pr, gamma, omega_vhs, alpha_vhs,
+rho_inf, T_inf, dir, cfl, dt (gas, non-dimensional as in Sec. 4 of the paper);
+body = {kind, center, radii, angle, verts, accom, Tw, Uw, Lref}; cutcell,
+upwind (method switches); precision ("fp64" or "mixed"); steps.
+
+The workloads stand in for the paper's cases (Sec. 4: cylinder, airfoil,
+sphere); the paper measures on no public dataset.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+ARGON = dict(Pr=2.0 / 3.0, gamma=5.0 / 3.0, omega_vhs=0.81, alpha_vhs=1.0, rho_inf=1.0, T_inf=1.0)
+
+
+def _case(dim, n, L, nv, V, Kn, Ma, body, precision="fp64", steps=200, rule="trapezoid", **kw):
+    lo = [-L] * dim if np.isscalar(L) else list(L[0])
+    hi = [L] * dim if np.isscalar(L) else list(L[1])
+    d = dict(
+        dim=dim,
+        n=[n] * dim if np.isscalar(n) else list(n),
+        lo=lo,
+        hi=hi,
+        nv=[nv] * dim if np.isscalar(nv) else list(nv),
+        vlo=[-V] * dim if np.isscalar(V) else list(V[0]),
+        vhi=[V] * dim if np.isscalar(V) else list(V[1]),
+        rule=rule,
+        Kn=Kn,
+        Ma=Ma,
+        dir=[1.0, 0.0, 0.0],
+        cfl=0.5,
+        dt=0.0,
+        body=body,
+        cutcell=1,
+        upwind=1,
+        precision=precision,
+        steps=steps,
+        **ARGON,
+    )
+    d.update(kw)
+    return d
+
+
+def circle(r=0.5, center=(0.0, 0.0), **wall):
+    b = dict(kind="circle", center=list(center) + [0.0], radii=[r, r, 0.0], accom=1.0, Tw=1.0,
+             Uw=[0.0, 0.0, 0.0])
+    b.update(wall)
+    return b
+
+
+def sphere(r=0.5, center=(0.0, 0.0, 0.0), **wall):
+    b = dict(kind="sphere", center=list(center), radii=[r, r, r], accom=1.0, Tw=1.0,
+             Uw=[0.0, 0.0, 0.0])
+    b.update(wall)
+    return b
+
+
+def ellipse(a=0.5, aspect=2.0, angle=0.0, center=(0.0, 0.0), **wall):
+    b = dict(kind="ellipse", center=list(center) + [0.0], radii=[a, a / aspect, 0.0], angle=angle,
+             accom=1.0, Tw=1.0, Uw=[0.0, 0.0, 0.0], Lref=2.0 * a)
+    b.update(wall)
+    return b
+
+
+def naca0012(chord=1.0, aoa_deg=0.0, npts=80, center=(0.0, 0.0), **wall):
+    """NACA 0012 polygon from the public 4-digit thickness law with a closed
+    trailing edge, counter-clockwise, rotated by the angle of attack about the
+    quarter chord and placed with the quarter chord at ``center``."""
+    t = 0.12
+    beta = np.linspace(0.0, math.pi, npts + 1)
+    x = 0.5 * (1.0 - np.cos(beta))  # cosine spacing, 0 .. 1
+    yt = 5 * t * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x**2 + 0.2843 * x**3 - 0.1036 * x**4)
+    # counter-clockwise: trailing edge -> lower surface -> leading edge -> upper surface
+    lower = np.stack([x[::-1], -yt[::-1]], axis=1)  # TE .. LE
+    upper = np.stack([x[1:-1], yt[1:-1]], axis=1)  # LE .. TE (exclusive)
+    pts = np.concatenate([lower, upper], axis=0) * chord
+    pts[:, 0] -= 0.25 * chord
+    a = -math.radians(aoa_deg)  # positive angle of attack: nose up
+    R = np.array([[math.cos(a), -math.sin(a)], [math.sin(a), math.cos(a)]])
+    pts = pts @ R.T + np.asarray(center)[None, :]
+    b = dict(kind="polygon", verts=pts.reshape(-1).tolist(), center=list(center) + [0.0],
+             radii=[0.0, 0.0, 0.0], accom=1.0, Tw=1.0, Uw=[0.0, 0.0, 0.0], Lref=chord)
+    b.update(wall)
+    return b
+
+
+# -------------------------------------------------------------------------
+# the five workloads
+# -------------------------------------------------------------------------
+
+def cylinder_48():
+    """2D flow past a circular cylinder, FP64: [-4,4]^2 on 48^2 cells, r = 0.5,
+    24^2 trapezoid velocities on [-5,5]^2, Kn 0.1, Ma 0.3, 200 steps, CFL 0.5."""
+    return _case(2, 48, 4.0, 24, 5.0, 0.1, 0.3, circle(0.5), precision="fp64", steps=200)
+
+
+def cylinder_512(Kn=0.1, precision="mixed", steps=200):
+    """2D cylinder, 512^2 cells on [-8,8]^2, r = 0.5, 48^2 velocities on [-6,6]^2,
+    Ma 0.5 (604M f values per component pair)."""
+    return _case(2, 512, 8.0, 48, 6.0, Kn, 0.5, circle(0.5), precision=precision, steps=steps)
+
+
+def sphere_96(precision="mixed", steps=200):
+    """3D flow past a sphere: 96^3 cells on [-4,4]^3, r = 0.5, 20^3 velocities on
+    [-5,5]^3, Kn 0.1, Ma 0.5."""
+    return _case(3, 96, 4.0, 20, 5.0, 0.1, 0.5, sphere(0.5), precision=precision, steps=steps)
+
+
+def sphere_24(precision="fp64", steps=50):
+    """The 3D sphere downscaled to 24^3 cells and 12^3 velocities (50 steps)."""
+    return _case(3, 24, 4.0, 12, 5.0, 0.1, 0.5, sphere(0.5), precision=precision, steps=steps)
+
+
+def batched_2d(seed=0, ncases=64, precision="mixed"):
+    """64 seeded 2D cases of uneven size: n ~ U{64..384} cells per axis on
+    [-4,4]^2, m ~ U{16..40} velocities per axis on [-6,6]^2, body in {circle,
+    ellipse with aspect U[1,3], NACA0012 at AoA U[0,10] deg}, Kn log-uniform in
+    [0.01, 1], Ma uniform in [0.1, 0.8]."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for i in range(ncases):
+        n = int(rng.integers(64, 385))
+        m = int(rng.integers(16, 41))
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            body = circle(0.5)
+        elif kind == 1:
+            body = ellipse(0.5, float(rng.uniform(1.0, 3.0)), 0.0)
+        else:
+            body = naca0012(1.0, float(rng.uniform(0.0, 10.0)))
+        Kn = float(10.0 ** rng.uniform(-2.0, 0.0))
+        Ma = float(rng.uniform(0.1, 0.8))
+        c = _case(2, n, 4.0, m, 6.0, Kn, Ma, body, precision=precision, steps=200)
+        c["name"] = f"batch{seed}_{i}"
+        cases.append(c)
+    return cases
+
+
+def served_stream(seed=0, nreq=200, rate=20.0):
+    """Poisson arrivals (rate per second) of mixed requests: 80% 2D cases shaped
+    like batched_2d, 20% 3D spheres with n ~ U{32..64} cells per axis on
+    [-4,4]^3 and m ~ U{12..20} velocities per axis on [-5,5]^3.  Returns a list
+    of (arrival_time_s, case)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    pool2d = batched_2d(seed + 1000, ncases=nreq)
+    for i in range(nreq):
+        t += float(rng.exponential(1.0 / rate))
+        if rng.uniform() < 0.8:
+            c = dict(pool2d[i])
+        else:
+            n = int(rng.integers(32, 65))
+            m = int(rng.integers(12, 21))
+            c = _case(3, n, 4.0, m, 5.0, 0.1, 0.5, sphere(0.5), precision="mixed", steps=0)
+        c["name"] = f"req{i}"
+        out.append((t, c))
+    return out
+
+
+def small_2d(body="circle", n=16, nv=8, precision="fp64", **kw):
+    """A small 2D case that the oracle finishes in well under a second per step."""
+    b = {"circle": circle(0.7), "ellipse": ellipse(0.8, 1.7, 0.4), "naca": naca0012(2.5, 7.0, 60),
+         "none": {"kind": "none"}}[body]
+    return _case(2, n, 2.0, nv, 4.5, kw.pop("Kn", 0.1), kw.pop("Ma", 0.3), b, precision=precision,
+                 steps=kw.pop("steps", 5), **kw)
