@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the immersed-boundary DVM step on GB300.
+
+Metric: DVM cell x velocity updates per second (fluid cells x discrete
+velocities advanced per step, summed over ranks), with the achieved fraction
+of the HBM roofline of the dominant kernel (the transport/relaxation sweep).
+
+Default workload: the 2D cylinder, 512^2 cells on [-8,8]^2, 48^2 velocities on
+[-6,6]^2, Kn 0.1, Ma 0.5, mixed precision (FP32 f, FP64 wall balance, forces
+and residual).  A step is the whole hot path: ghost band (upwind-weighted
+interpolation, wall density, cut-cell blend, ghost values), surface forces,
+transport and relaxation of every fluid cell, moments and residual.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 the script runs under torch.distributed.run: every rank advances
+its own replica of the case (the method has no exchange between independent
+cases), timing is the max over ranks, and the value is the sum over ranks.
+"--impl reference" times the CPU oracle on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "cylinder_512": lambda p: __import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).cylinder_512(0.1, p),
+    "sphere_96": lambda p: __import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).sphere_96(p),
+    "cylinder_48": lambda p: dict(__import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).cylinder_48(),
+                                  precision=p),
+}
+DESCRIPTIONS = {
+    "cylinder_512": "2D cylinder r=0.5, 512x512 cells on [-8,8]^2, 48x48 trapezoid velocities on [-6,6]^2, Kn=0.1, Ma=0.5",
+    "sphere_96": "3D sphere r=0.5, 96^3 cells on [-4,4]^3, 20^3 trapezoid velocities on [-5,5]^3, Kn=0.1, Ma=0.5",
+    "cylinder_48": "2D cylinder r=0.5, 48x48 cells on [-4,4]^2, 24x24 trapezoid velocities on [-5,5]^2, Kn=0.1, Ma=0.3",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cylinder_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) >= 9:
+                        rows.append(p)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(nprocs: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_sample_case(case: dict) -> dict:
+    """A bounded sample of the workload for the CPU oracle: the same gas,
+    body, velocity grid and domain on a coarser cell grid (48 cells per axis in
+    2D, 12 in 3D) so that one oracle step takes about a second."""
+    c = dict(case)
+    c["n"] = [48] * 2 if case["dim"] == 2 else [12] * 3
+    c["precision"] = "fp64"
+    return c
+
+
+def time_oracle(case: dict, budget_s: float, max_steps: int | None = None):
+    import oracle
+
+    oc = oracle.OracleCase(case)
+    oc.step(1)  # warm
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        oc.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps and steps >= max_steps) or (not max_steps and el > budget_s):
+            break
+    pairs = oc.nfluid * oc.nvel
+    return pairs * steps / el, steps, el, oc
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    case = WORKLOADS[args.workload](args.precision)
+    sample = cpu_sample_case(case)
+    import oracle
+
+    oc = oracle.OracleCase(sample)
+    for _ in range(max(args.warmup, 0)):
+        oc.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oc.step(1)
+    el = time.perf_counter() - t0
+    pairs = oc.nfluid * oc.nvel
+    value = pairs * args.steps / el
+    desc = f"oracle (plain FP64 C, 1 thread) on the workload's gas, body and velocity grid with {sample['n'][0]} cells per axis"
+    line = {
+        "impl": "reference", "metric": "DVM cell x velocity updates/s", "value": value,
+        "unit": "cell-velocity updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": DESCRIPTIONS[args.workload], "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "cell-velocity updates/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+        if rank != 0:
+            __graft_entry__.build()
+        dist.barrier()
+    torch.cuda.set_device(local)
+    from paper_2512_20252_gb300 import ibdvm
+
+    case = WORKLOADS[args.workload](args.precision)
+    stream = torch.cuda.Stream()
+    solver = ibdvm.Solver(case, stream=stream.cuda_stream)
+    info = solver.info
+    pairs = int(info.nfluid) * int(info.nvel)
+    esize = 8 if args.precision == "fp64" else 4
+    ncomp = int(info.ncomp)
+
+    # warm-up (untimed)
+    solver.step(max(args.warmup, 3))
+    solver.set_profiling(True)
+    solver.reset_kernel_times()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    res = solver.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    kt = solver.kernel_times()
+    solver.set_profiling(False)
+    if pg:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_pairs = pairs * args.steps * world
+    value = total_pairs / (elapsed_ms / 1e3)
+    sweep_ms, sweep_n = kt["sweep"]
+    alg_bytes = pairs * ncomp * esize * 2  # read f^n, write f^{n+1}
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (sweep_ms / sweep_n / 1e3) / 1e9 if sweep_n else None
+    launches = sum(n for _, n in kt.values())
+    F, Q, CD, CL = solver.step_forces()
+
+    # end to end through the C-ABI with host buffers: every step uploads f^n
+    # from pinned host memory, advances one step and reads W^{n+1} back
+    shp = solver.native_shape()
+    hbuf = torch.empty(shp, dtype=torch.float32 if esize == 4 else torch.float64, pin_memory=True)
+    nbytes = hbuf.numel() * esize
+    solver.get_f_native(hbuf.data_ptr(), nbytes)
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_f_native(hbuf.data_ptr(), nbytes)
+        solver.step(1)
+        W, q, _ = solver.moments()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    d2h = W.nbytes + q.nbytes + 8
+    e2e_value = pairs * e2e_steps * world / e2e_s
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sample = cpu_sample_case(case)
+        v, n, el, oc = time_oracle(sample, args.cpu_sample_seconds)
+        cpu = {"value": v, "unit": "cell-velocity updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} oracle steps ({el:.1f} s) of the workload's gas, body and velocity grid "
+                         f"on {sample['n'][0]} cells per axis ({oc.nfluid} fluid cells x {oc.nvel} velocities)"}
+    if rank == 0:
+        line = {
+            "metric": "DVM cell x velocity updates/s",
+            "value": value,
+            "unit": "cell-velocity updates/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32" if esize == 4 else "f64",
+            "data": "synthetic",
+            "config": {"workload": DESCRIPTIONS[args.workload], "precision": args.precision,
+                       "cells": int(info.ncell), "fluid_cells": int(info.nfluid), "velocities": int(info.nvel),
+                       "l2": f"inputs larger than L2 (f^n is {alg_bytes / 2 / 1e9:.2f} GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "sweep_kernel", "peak_kind": peak_kind,
+                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms / max(sweep_n, 1)},
+            "kernel_ms": {k: v[0] for k, v in kt.items()},
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "residual": res,
+            "CD": CD,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

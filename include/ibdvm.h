@@ -1,0 +1,235 @@
+/*
+ * ibdvm.h -- C-ABI of the GB300-native immersed-boundary discrete velocity
+ * solver (libibdvm.so).
+ *
+ * The library advances the discrete velocity model of the Shakhov-Boltzmann
+ * equation on a uniform Cartesian grid with an immersed rigid body, following
+ * the ghost-cell immersed boundary method of Ge, Cai, Zhang and Xiao,
+ * "An immersed boundary method for the discrete velocity model of the
+ * Boltzmann equation" (arXiv 2512.20252):
+ *   - Sec. 2.2: finite-volume upwind fluxes with van Leer-limited linear
+ *     reconstruction (Eqs. half-discrete, reconstruction, limiter), velocity
+ *     quadrature (Eq. quadrature), Shakhov relaxation (Eq. shakhov);
+ *   - Sec. 2.3: Maxwell gas-surface interaction (Eqs. general bc, Maxwell BC,
+ *     boundary maxwell) with the wall density from zero normal mass flux
+ *     (Eqs. npc, dnpc);
+ *   - Sec. 3.2: ghost, fluid, surface, donor and auxiliary cells, shifted
+ *     point (Eqs. sp, fsp), upwind-weighted compact interpolation
+ *     (Eqs. extrapolation 1, upwind), intersect point (Eq. fw), ghost-cell
+ *     construction (Eq. extrapolation 2) and the velocity-space cut-cell
+ *     correction (Eqs. fwc, cc_np, rhowc);
+ *   - Sec. 4: reduced distributions h, b in 2D, non-dimensional equilibria,
+ *     VHS viscosity (Eq. viscosity), residual and forward Euler time marching.
+ *
+ * Conventions for every call:
+ *   - Status codes: every call returns an ibdvm_status and never aborts or
+ *     traps.  On an error the context state is unchanged unless the call says
+ *     otherwise, and ibdvm_last_error() returns a one-line reason.
+ *   - Host arrays are caller-owned, row-major, FP64 unless stated; the library
+ *     copies inputs and never keeps caller pointers.
+ *   - Cell index c = i + n0*(j + n1*k) (x fastest); velocity index
+ *     k = kx + nv0*(ky + nv1*kz) (xi_x fastest); distribution arrays are
+ *     f[cell][k][comp] with comp = {h, b} in 2D (Sec. 4 reduced distributions)
+ *     and comp = {f} in 3D.
+ *   - A context owns all its device memory and is bound to one CUDA stream;
+ *     it is not thread-safe; distinct contexts are independent.
+ *   - Quantities are non-dimensional as in Sec. 4 (xi / sqrt(2 R T0), ...).
+ */
+#ifndef IBDVM_H
+#define IBDVM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibdvm_ctx ibdvm_ctx;
+typedef struct ibdvm_geom ibdvm_geom;
+
+typedef enum {
+  IBDVM_OK = 0,
+  IBDVM_E_INVAL = 1,        /* an argument is out of range or inconsistent */
+  IBDVM_E_NOMEM = 2,        /* host or device allocation failed */
+  IBDVM_E_CUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+  IBDVM_E_UNSTABLE = 4,     /* dt / tau > 1 somewhere: forward Euler relaxation would overshoot */
+  IBDVM_E_NONFINITE = 5,    /* a non-finite moment or residual appeared */
+  IBDVM_E_NOTCONVERGED = 6, /* reserved for callers that iterate to a residual */
+  IBDVM_E_TIMEOUT = 7,      /* a bounded device wait gave up */
+  IBDVM_E_STATE = 8         /* the call is not valid in the current state */
+} ibdvm_status;
+
+enum { IBDVM_RULE_TRAPEZOID = 0, IBDVM_RULE_MIDPOINT = 1 };
+enum { IBDVM_FP64 = 0, IBDVM_MIXED = 1 };
+enum {
+  IBDVM_BODY_NONE = 0,
+  IBDVM_BODY_CIRCLE = 1,   /* 2D: center, radii[0] */
+  IBDVM_BODY_ELLIPSE = 2,  /* 2D: center, semi-axes radii[0] (rotated x) and radii[1], angle (rad) */
+  IBDVM_BODY_SPHERE = 3,   /* 3D: center, radii[0] */
+  IBDVM_BODY_POLYGON = 4,  /* 2D: counter-clockwise verts[2*nverts] */
+  IBDVM_BODY_HALFSPACE = 5 /* 2D/3D: solid where (x - center).radii <= 0, radii = unit normal into the gas */
+};
+enum { IBDVM_CELL_FLUID = 0, IBDVM_CELL_GHOST = 1, IBDVM_CELL_SOLID = 2 };
+/* method switches (ibdvm_gas_desc.flags) */
+enum {
+  IBDVM_NO_CUTCELL = 1,        /* incident/reflected by the node sign of xi.n only (no Sec. 3.2.3) */
+  IBDVM_PLAIN_AVERAGE = 2,     /* weights 1/N_S instead of Eq. upwind (ablation) */
+  IBDVM_RHAT_GHOST_TO_FLUID = 4 /* Eq. upwind with r pointing from the ghost to the fluid cell */
+};
+
+/* Uniform Cartesian grid: dim = 2 or 3, n[a] cells on [lo[a], hi[a]]. */
+typedef struct {
+  int dim;
+  int n[3];
+  double lo[3], hi[3];
+} ibdvm_grid_desc;
+
+/* Velocity grid (Eq. quadrature): n[a] nodes per axis on [lo[a], hi[a]],
+   rule = IBDVM_RULE_TRAPEZOID (nodes at both ends) or IBDVM_RULE_MIDPOINT
+   (composite midpoint, Sec. 3.2.3).  Each node owns the dual box
+   [xi - dxi/2, xi + dxi/2] clipped to the interval; its measure is the weight. */
+typedef struct {
+  int n[3];
+  double lo[3], hi[3];
+  int rule;
+} ibdvm_vgrid_desc;
+
+/* Gas and run parameters (Sec. 4): Knudsen and Mach numbers, Prandtl number,
+   specific-heat ratio, VHS omega and alpha (Eq. viscosity: mu0 from Kn),
+   freestream density, temperature and flow direction (U = Ma sqrt(gamma T/2)),
+   CFL number or a fixed dt (> 0 overrides the CFL), precision (IBDVM_FP64 or
+   IBDVM_MIXED: FP32 storage of f and FP32 transport/relaxation, FP64 wall
+   balance, forces and residual), method flags. */
+typedef struct {
+  double Kn, Ma, Pr, gamma, omega_vhs, alpha_vhs;
+  double rho_inf, T_inf;
+  double dir[3];
+  double cfl, dt;
+  int precision;
+  int flags;
+} ibdvm_gas_desc;
+
+/* Immersed body and its wall (Sec. 2.3): Maxwell accommodation coefficient
+   accom_alpha in [0,1] (1 = fully diffuse), wall temperature T_w and velocity
+   U_w; L_ref is the reference length (2D, per unit span) or area (3D) of the
+   force coefficients (<= 0: diameter, major axis, chord or pi r^2). */
+typedef struct {
+  int kind;
+  double center[3], radii[3], angle;
+  const double *verts;
+  int nverts;
+  double accom_alpha, T_w, U_w[3], L_ref;
+} ibdvm_body_desc;
+
+typedef struct {
+  int dim, ncomp;
+  long long ncell, nfluid;
+  int nvel, nvel_padded;
+  int nlink, nghost;
+  double dt;
+  int precision;
+  long long steps_done;
+  size_t device_bytes;
+} ibdvm_info;
+
+/* Creates a context: velocity grid, freestream Maxwellian in every cell, no
+   body.  cuda_stream is a cudaStream_t (NULL = the legacy default stream).
+   Errors: IBDVM_E_INVAL (bad descriptor), IBDVM_E_NOMEM, IBDVM_E_CUDA. */
+ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *vgrid,
+                               const ibdvm_gas_desc *gas, void *cuda_stream, ibdvm_ctx **out);
+
+/* Places the body (Sec. 3.2.1): classifies the cells, builds one link per
+   (ghost cell, fluid face neighbour) with its intersect point, normal, donor,
+   auxiliary cell and shifted point, the surface-cell lists, and the
+   incident-side velocity measures of the cut cells (Sec. 3.2.3).  Resets
+   nothing else: f is kept.  Errors: IBDVM_E_INVAL, IBDVM_E_NOMEM, IBDVM_E_CUDA. */
+ibdvm_status ibdvm_set_body(ibdvm_ctx *ctx, const ibdvm_body_desc *body);
+
+/* Advances nsteps forward-Euler steps (Sec. 4): ghost band, then transport
+   and relaxation of every fluid cell, then the moments.  residual_out
+   (nullable) receives the residual of the last step (Sec. 4 convergence
+   criterion).  Errors: IBDVM_E_INVAL (nsteps < 0), IBDVM_E_UNSTABLE,
+   IBDVM_E_NONFINITE (the state is then the one after the failing step),
+   IBDVM_E_CUDA. */
+ibdvm_status ibdvm_step(ibdvm_ctx *ctx, int nsteps, double *residual_out);
+
+/* Conservative variables W[cell][dim+2] = (rho, rho U, rho E) and heat flux
+   q[cell][dim] of the current state (Eqs. moments1-3; plain quadrature), and
+   the cell classes (nullable outputs).  Values of non-fluid cells are not
+   meaningful. */
+ibdvm_status ibdvm_moments(ibdvm_ctx *ctx, double *W, double *q, unsigned char *celltype);
+
+/* Surface force F[3] (per unit span in 2D) and heat flux Q into the body:
+   momentum and energy carried into the solid through the donor-ghost faces by
+   the face fluxes of the update, on the current state; CD, CL normalised by
+   rho_inf U^2 L_ref / 2 along and normal to the flow (normalisation of the
+   pressure coefficient, Sec. 4.3).  Any output may be NULL. */
+ibdvm_status ibdvm_forces(ibdvm_ctx *ctx, double F[3], double *Q, double *CD, double *CL);
+
+/* The surface force and heat flux of the face fluxes that the last
+   ibdvm_step applied (computed on the device every step, FP64), normalised as
+   in ibdvm_forces.  Any output may be NULL.  Before the first step: zeros. */
+ibdvm_status ibdvm_step_forces(ibdvm_ctx *ctx, double F[3], double *Q, double *CD, double *CL);
+
+/* State transfer in FP64: f[cell][k][comp] with k < nvel (padding excluded). */
+ibdvm_status ibdvm_get_f(ibdvm_ctx *ctx, double *f);
+ibdvm_status ibdvm_set_f(ibdvm_ctx *ctx, const double *f);
+
+/* State transfer in the storage precision and layout: f[cell][k_padded][comp]
+   of double (FP64) or float (mixed); bytes must equal
+   ncell * nvel_padded * ncomp * sizeof(element).  Pinned host memory makes
+   these copies asynchronous-capable; they complete before returning. */
+ibdvm_status ibdvm_get_f_native(ibdvm_ctx *ctx, void *host, size_t bytes);
+ibdvm_status ibdvm_set_f_native(ibdvm_ctx *ctx, const void *host, size_t bytes);
+
+/* The ghost band of the current state (Sec. 3.2.1 steps 1-4) for every link:
+   incident distribution at the intersect point fiw, wall distribution fstarw,
+   ghost value fstargc ([link][k][comp], nullable) and wall density rhow[link]. */
+ibdvm_status ibdvm_ghost_band(ibdvm_ctx *ctx, double *fiw, double *fstarw, double *fstargc,
+                              double *rhow);
+
+/* Kernel timing.  With profiling on, every kernel launch class is bracketed
+   by CUDA events on the context's stream; ms[8] receives the accumulated
+   device time and launches[8] the number of kernel launches per class
+   (0 ghost band, 1 transport/relaxation sweep, 2 moments and residual,
+   3 forces, 4-7 reserved).  Launch counts are kept with profiling off too. */
+ibdvm_status ibdvm_set_profiling(ibdvm_ctx *ctx, int on);
+ibdvm_status ibdvm_get_kernel_times(ibdvm_ctx *ctx, double *ms, long long *launches);
+ibdvm_status ibdvm_reset_kernel_times(ibdvm_ctx *ctx);
+
+ibdvm_status ibdvm_get_info(const ibdvm_ctx *ctx, ibdvm_info *info);
+ibdvm_status ibdvm_set_stream(ibdvm_ctx *ctx, void *cuda_stream);
+/* Geometry of the context (host copy); see ibdvm_geom_* for the layouts. */
+const ibdvm_geom *ibdvm_get_geom(const ibdvm_ctx *ctx);
+void ibdvm_destroy(ibdvm_ctx *ctx);
+const char *ibdvm_last_error(const ibdvm_ctx *ctx);
+const char *ibdvm_status_string(ibdvm_status s);
+
+/* ------------------------------------------------------------------------
+ * Host-only geometry (no GPU needed): the classification, links, surface
+ * cells and cut-cell table that ibdvm_set_body builds.
+ * ------------------------------------------------------------------------ */
+ibdvm_status ibdvm_geom_build(const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *vgrid,
+                              const ibdvm_gas_desc *gas, const ibdvm_body_desc *body,
+                              ibdvm_geom **out);
+/* sizes[8] = ncell, nvel, ncomp, nlink, nghost, nfluid, nsurf, nvel_padded */
+ibdvm_status ibdvm_geom_sizes(const ibdvm_geom *g, long long *sizes);
+ibdvm_status ibdvm_geom_cells(const ibdvm_geom *g, unsigned char *types);
+/* links in canonical order: ghost cell ascending, then direction 2*axis + (side > 0);
+   side = sign of (x_donor - x_ghost) along axis; aux = -1 when unusable;
+   xw[link][3] intersect point, nw[link][3] unit normal into the gas */
+ibdvm_status ibdvm_geom_links(const ibdvm_geom *g, int *ghost, int *donor, int *aux, int *axis,
+                              int *side, double *xw, double *nw);
+/* incident-side measure omega^g[link][k] of every velocity box */
+ibdvm_status ibdvm_geom_cut_table(const ibdvm_geom *g, double *wg);
+ibdvm_status ibdvm_geom_velocities(const ibdvm_geom *g, double *xi, double *w);
+/* surface cells: ghost_cell[nghost], offsets[nghost+1], cells[nsurf] */
+ibdvm_status ibdvm_geom_surface(const ibdvm_geom *g, int *ghost_cell, int *offsets, int *cells);
+double ibdvm_geom_dt(const ibdvm_geom *g);
+void ibdvm_geom_destroy(ibdvm_geom *g);
+const char *ibdvm_geom_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,100 @@
+// ctx.h -- the solver context behind the C-ABI handle and the kernel launch
+// interface shared by capi.cpp and the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "geom.h"
+
+namespace ibdvm {
+
+// Per-cell macroscopic slots (array of [kMac][ncell] in the storage type):
+// the Shakhov equilibrium parameters of the current state (Sec. 2.1, Sec. 4).
+enum MacSlot {
+  kPre = 0,    // rho / (pi T)      (2D reduced)  or rho / (pi T)^{3/2}  (3D)
+  kU0 = 1,     // U_x, U_y, U_z
+  kInvT = 4,   // 1 / T
+  kHalfT = 5,  // T / 2              (B = T/2 H, Sec. 4)
+  kShA = 6,    // 4 (1 - Pr) / (5 rho T^2)
+  kQ0 = 7,     // q_x, q_y, q_z
+  kDtTau = 10, // dt / tau, tau = mu / p, mu = mu0 T^omega
+  kMac = 12
+};
+
+// kernel classes of the timing counters
+enum KernelClass { kKGhost = 0, kKSweep = 1, kKMoments = 2, kKForces = 3, kKOther = 4 };
+
+// flags written by the moment kernel
+enum : int { kFlagNonFinite = 1, kFlagUnstable = 2 };
+
+} // namespace ibdvm
+
+struct ibdvm_ctx {
+  ibdvm::Geom geom;
+  cudaStream_t stream = nullptr;
+  int precision = 0, dim = 2, ncomp = 2, nv = 0, nvp = 0;
+  long long ncell = 0;
+  size_t esize = 8;
+  // state and per-cell data
+  void *f[2] = {nullptr, nullptr};
+  int cur = 0;
+  void *mac = nullptr;       // [kMac][ncell]
+  double *W[2] = {nullptr, nullptr}; // [dim+2][ncell]
+  int wcur = 0;
+  double *part = nullptr;    // moment partial sums [nchunk][NM][ncell]
+  int nchunk = 1, kloop = 1;
+  double *resblk = nullptr;  // residual partial sums per block
+  int nresblk = 0;
+  double *d_res = nullptr;   // residual scalar
+  int *d_flags = nullptr;
+  // velocity tables
+  void *xiT = nullptr, *wT = nullptr, *finf = nullptr;
+  double *xiD = nullptr, *wD = nullptr;
+  // cell tables
+  uint8_t *ctype = nullptr;
+  int *dslot = nullptr, *dlinks = nullptr;
+  // ghost band
+  int nlink = 0, nghost = 0, nsurf = 0;
+  int *l_int = nullptr;      // [nlink][8]
+  double *l_dbl = nullptr;   // [nlink][8]
+  double *l_wg = nullptr;    // [nlink][nvp]
+  int *g_int = nullptr;      // [nghost][4]
+  int *s_int = nullptr;      // [nsurf][8]
+  double *s_dbl = nullptr;   // [nsurf][8]
+  void *lval = nullptr;      // [nlink][nvp][ncomp] ghost values f*_gc
+  void *fi_scr = nullptr;    // [nlink][nvp][ncomp] incident distribution at the wall
+  void *fsp_scr = nullptr;   // [nlink][nvp][ncomp] shifted-point value
+  double *rhow = nullptr;    // [nlink]
+  double *fpart = nullptr;   // [nlink][4] force partial sums
+  double *d_forces = nullptr; // [4]
+  double *d_step_forces = nullptr; // [4] forces of the fluxes the last step applied
+  // kernel timing (CUDA events around each launch class, when enabled)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_marks; // (kernel class, index of the start event)
+  double kernel_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long kernel_launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // bookkeeping
+  long long steps = 0;
+  size_t dev_bytes = 0;
+  std::string err;
+};
+
+namespace ibdvm {
+
+// Kernel launchers (kernels.cu).  All enqueue on ctx->stream and return the
+// launch status.
+cudaError_t launch_init_state(ibdvm_ctx *ctx);
+cudaError_t launch_moments(ibdvm_ctx *ctx, bool shift, bool residual);
+cudaError_t launch_ghost_band(ibdvm_ctx *ctx, double *dbg_fstarw);
+cudaError_t launch_sweep(ibdvm_ctx *ctx);
+cudaError_t launch_forces(ibdvm_ctx *ctx, double *dst);
+// dense FP64 [ncells][nv][ncomp] (device) <-> cells [c0, c0 + ncells) of the current state
+cudaError_t launch_convert(ibdvm_ctx *ctx, double *dense, long long c0, long long ncells, bool to_state);
+
+} // namespace ibdvm

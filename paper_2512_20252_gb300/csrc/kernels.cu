@@ -1,0 +1,1053 @@
+// kernels.cu -- CUDA kernels (sm_103a) of one forward-Euler step of the
+// ghost-cell immersed-boundary discrete velocity method (arXiv 2512.20252).
+//
+//   ghost_band_kernel   Sec. 3.2.1-3.2.3: per link, the upwind-weighted compact
+//                       interpolation f_gc (Eqs. extrapolation 1, upwind), the
+//                       shifted point (Eqs. sp, fsp), the incident distribution
+//                       at the intersect point (Eq. fw), the wall density from
+//                       zero normal mass flux with the cut-cell split (Eq. rhowc,
+//                       FP64 block reduction), the cut-cell blend (Eq. fwc) and
+//                       the ghost value (Eq. extrapolation 2).
+//   sweep_kernel        Sec. 2.2 and Sec. 4: per (cell, velocity), van Leer
+//                       limited upwind face values (Eqs. reconstruction,
+//                       limiter), flux divergence, Shakhov relaxation with the
+//                       reduced equilibria, forward Euler, and the velocity
+//                       moments of the new state reduced per cell.
+//   finalize_kernel     moments -> W, T, q, tau per cell; residual partial sums
+//                       (Sec. 4, FP64).
+//   forces kernels      momentum and energy through the donor-ghost faces (FP64).
+//
+// Storage type T is double (FP64 path) or float (mixed path: FP32 f, FP32
+// transport and relaxation with compensated FP32 moment sums; FP64 wall
+// balance, forces and residual).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <type_traits>
+
+#include "ctx.h"
+
+namespace ibdvm {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kThreadsPerCell = 64; // threads over velocities for one cell
+constexpr int kCellsPerBlock = 4;   // cells of one sweep block
+constexpr int kBlock = kThreadsPerCell * kCellsPerBlock;
+
+template <int D> struct Dims {
+  static constexpr int NC = (D == 2) ? 2 : 1;   // components: (h, b) or f
+  static constexpr int NM = (D == 2) ? 9 : 14;  // moment sums per cell
+  static constexpr int NW = D + 2;              // conservative variables
+};
+
+// ---------------------------------------------------------------------------
+// small numerics
+// ---------------------------------------------------------------------------
+
+// van Leer limited difference, Eq. limiter: (sgn a + sgn b)|a||b|/(|a|+|b|)
+// written as 2ab/(a+b) when a and b have the same sign, 0 otherwise.
+template <typename T> __device__ __forceinline__ T vanleer(T a, T b) {
+  T p = a * b;
+  return (p > T(0)) ? (T(2) * p) / (a + b) : T(0);
+}
+
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+
+// round-to-nearest products and sums without contraction: the upwind-weight
+// fallback is decided by an exact zero of xi.r, which fused multiply-adds
+// would perturb
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+
+// Accumulator: plain sum in FP64, Neumaier-compensated sum in FP32.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void merge(double os, double) { s += os; }
+  __device__ __forceinline__ double hi() const { return s; }
+  __device__ __forceinline__ double lo() const { return 0.0; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float t = __fadd_rn(s, x);
+    c = __fadd_rn(c, (fabsf(s) >= fabsf(x)) ? __fadd_rn(__fsub_rn(s, t), x)
+                                             : __fadd_rn(__fsub_rn(x, t), s));
+    s = t;
+  }
+  __device__ __forceinline__ void merge(float os, float oc) {
+    add(os);
+    c = __fadd_rn(c, oc);
+  }
+  __device__ __forceinline__ float hi() const { return s; }
+  __device__ __forceinline__ float lo() const { return c; }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// ---------------------------------------------------------------------------
+// the sweep: transport, relaxation and moments
+// ---------------------------------------------------------------------------
+
+template <typename T> struct SweepArgs {
+  const T *__restrict__ f;
+  T *__restrict__ fn;
+  const T *__restrict__ mac;
+  const T *__restrict__ xi;   // [3][nvp]
+  const T *__restrict__ w;    // [nvp]
+  const T *__restrict__ finf; // [nvp][NC]
+  const uint8_t *__restrict__ ctype;
+  const int *__restrict__ dslot;
+  const int *__restrict__ dlinks;
+  const T *__restrict__ lval; // [nlink][nvp][NC]
+  double *__restrict__ part;  // [nchunk][NM][ncell]
+  long long ncell;
+  int n[3];
+  int nv, nvp, kloop;
+  T dt;
+  T rdx[3];
+  int update; // 1: step f -> fn and take the moments of fn; 0: moments of f
+  int shift;  // 1: moments about the stored bulk velocity U^n; 0: about zero
+};
+
+template <typename T, int NC>
+__device__ __forceinline__ void load_nc(const T *p, T *o) {
+#pragma unroll
+  for (int m = 0; m < NC; ++m) o[m] = p[m];
+}
+
+// value of the cell across face (a, s) of fluid cell c, as c sees it: the
+// freestream outside the domain (two halo layers), the link's ghost value for
+// a ghost neighbour (one ghost value per link), else the neighbour's f
+template <typename T, int NC>
+__device__ __forceinline__ void seen(const SweepArgs<T> &A, long long c, const int *ijk, int a,
+                                     int s, int k, T *out) {
+  int q = ijk[a] + s;
+  if (q < 0 || q >= A.n[a]) {
+    load_nc<T, NC>(A.finf + (size_t)k * NC, out);
+    return;
+  }
+  long long stride = (a == 0) ? 1LL : (a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1]);
+  long long nb = c + s * stride;
+  if (A.ctype[nb] == IBDVM_CELL_GHOST) {
+    // every fluid face neighbour of a ghost is a donor with a link in this
+    // direction; the guards only keep a corrupted table from reading out of bounds
+    const int slot = A.dslot[c];
+    const int l = (slot >= 0) ? A.dlinks[slot * 6 + 2 * a + (s > 0)] : -1;
+    load_nc<T, NC>((l >= 0) ? A.lval + ((size_t)l * A.nvp + k) * NC : A.finf + (size_t)k * NC, out);
+  } else {
+    load_nc<T, NC>(A.f + ((size_t)nb * A.nvp + k) * NC, out);
+  }
+}
+
+template <typename T> __device__ __forceinline__ T shfl_down(T v, int o) {
+  return __shfl_down_sync(0xffffffffu, v, o);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
+  constexpr int NC = Dims<D>::NC;
+  constexpr int NM = Dims<D>::NM;
+  __shared__ double red[kCellsPerBlock][2][NM];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long long c = (long long)blockIdx.x * kCellsPerBlock + ty;
+  const int chunk = blockIdx.y;
+  const bool active = (c < A.ncell) && (A.ctype[c] == IBDVM_CELL_FLUID);
+  Acc<T> acc[NM];
+  if (active) {
+    int ijk[3];
+    ijk[0] = (int)(c % A.n[0]);
+    ijk[1] = (int)((c / A.n[0]) % A.n[1]);
+    ijk[2] = (int)(c / ((long long)A.n[0] * A.n[1]));
+    const T *M = A.mac;
+    const long long nc = A.ncell;
+    T U[3], q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      U[a] = A.shift ? M[(kU0 + a) * nc + c] : T(0);
+      q[a] = M[(kQ0 + a) * nc + c];
+    }
+    const T pre = M[kPre * nc + c], invT = M[kInvT * nc + c], halfT = M[kHalfT * nc + c];
+    const T shA = M[kShA * nc + c], dtau = M[kDtTau * nc + c];
+    for (int j = 0; j < A.kloop; ++j) {
+      const int k = (chunk * A.kloop + j) * kThreadsPerCell + tx;
+      if (k >= A.nv) break;
+      T fc[NC];
+      load_nc<T, NC>(A.f + ((size_t)c * A.nvp + k) * NC, fc);
+      T cv[3] = {T(0), T(0), T(0)};
+      T c2 = T(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        cv[a] = A.xi[a * A.nvp + k] - U[a];
+        c2 += cv[a] * cv[a];
+      }
+      T fo[NC];
+      if (A.update) {
+        T div[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) div[m] = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const T xa = A.xi[a * A.nvp + k];
+          if (xa == T(0)) continue;
+          const int s = (xa > T(0)) ? 1 : -1;
+          T fb[NC], ff[NC], fin[NC];
+          seen<T, NC>(A, c, ijk, a, -s, k, fb);
+          seen<T, NC>(A, c, ijk, a, s, k, ff);
+          // upwind neighbour u = c - s e_a supplies the incoming face value
+          const int qa = ijk[a] - s;
+          if (qa < 0 || qa >= A.n[a]) {
+            load_nc<T, NC>(A.finf + (size_t)k * NC, fin); // halo: zero slope
+          } else {
+            long long stride = (a == 0) ? 1LL : (a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1]);
+            long long u = c - s * stride;
+            if (A.ctype[u] == IBDVM_CELL_GHOST) {
+              // ghost cell: link value with the one-sided slope toward the donor
+#pragma unroll
+              for (int m = 0; m < NC; ++m) fin[m] = T(0.5) * (fb[m] + fc[m]);
+            } else {
+              int iu[3] = {ijk[0], ijk[1], ijk[2]};
+              iu[a] = qa;
+              T fuu[NC];
+              seen<T, NC>(A, u, iu, a, -s, k, fuu);
+#pragma unroll
+              for (int m = 0; m < NC; ++m)
+                fin[m] = fb[m] + T(0.5) * vanleer(fb[m] - fuu[m], fc[m] - fb[m]);
+            }
+          }
+          const T coef = fabs(xa) * A.rdx[a];
+#pragma unroll
+          for (int m = 0; m < NC; ++m) {
+            T fout = fc[m] + T(0.5) * vanleer(fc[m] - fb[m], ff[m] - fc[m]);
+            div[m] += coef * (fout - fin[m]);
+          }
+        }
+        // Shakhov equilibrium (Sec. 4 reduced forms in 2D, Sec. 2.1 in 3D)
+        T cq = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) cq += cv[a] * q[a];
+        const T e = pre * exp_t(-c2 * invT);
+        const T corr = shA * cq;
+        const T tc = T(2) * c2 * invT;
+        if (D == 2) {
+          const T H = e * (T(1) + corr * (tc - T(4)));
+          const T B = halfT * e * (T(1) + corr * (tc - T(2)));
+          fo[0] = fc[0] - A.dt * div[0] + dtau * (H - fc[0]);
+          fo[NC - 1] = fc[NC - 1] - A.dt * div[NC - 1] + dtau * (B - fc[NC - 1]);
+        } else {
+          const T g = e * (T(1) + corr * (tc - T(5)));
+          fo[0] = fc[0] - A.dt * div[0] + dtau * (g - fc[0]);
+        }
+        T *dst = A.fn + ((size_t)c * A.nvp + k) * NC;
+#pragma unroll
+        for (int m = 0; m < NC; ++m) dst[m] = fo[m];
+      } else {
+#pragma unroll
+        for (int m = 0; m < NC; ++m) fo[m] = fc[m];
+      }
+      // moments about the current bulk velocity: c' = xi - U^n
+      const T wk = A.w[k];
+      const T wh = wk * fo[0];
+      const T wb = (D == 2) ? wk * fo[NC - 1] : T(0);
+      const T e2 = c2 * wh + wb;
+      acc[0].add(wh);
+      if (D == 2) {
+        acc[1].add(cv[0] * wh);
+        acc[2].add(cv[1] * wh);
+        acc[3].add(e2);
+        acc[4].add(cv[0] * cv[0] * wh);
+        acc[5].add(cv[0] * cv[1] * wh);
+        acc[6].add(cv[1] * cv[1] * wh);
+        acc[7].add(cv[0] * e2);
+        acc[8].add(cv[1] * e2);
+      } else {
+        acc[1].add(cv[0] * wh);
+        acc[2].add(cv[1] * wh);
+        acc[3].add(cv[2] * wh);
+        acc[4].add(e2);
+        acc[5].add(cv[0] * cv[0] * wh);
+        acc[6].add(cv[0] * cv[1] * wh);
+        acc[7].add(cv[0] * cv[2] * wh);
+        acc[8].add(cv[1] * cv[1] * wh);
+        acc[9].add(cv[1] * cv[2] * wh);
+        acc[10].add(cv[2] * cv[2] * wh);
+        acc[11].add(cv[0] * e2);
+        acc[12].add(cv[1] * e2);
+        acc[13].add(cv[2] * e2);
+      }
+    }
+  }
+  // reduce the moment sums of each cell over its 64 threads (two warps)
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    T h = acc[m].hi(), l = acc[m].lo();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T oh = shfl_down(h, o), ol = shfl_down(l, o);
+      Acc<T> t;
+      t.s = h;
+      if constexpr (sizeof(T) == 4) t.c = l;
+      t.merge(oh, ol);
+      h = t.hi();
+      l = t.lo();
+    }
+    if ((tx & 31) == 0) red[ty][tx >> 5][m] = (double)h + (double)l;
+  }
+  __syncthreads();
+  if (c < A.ncell && tx < NM) {
+    double v = active ? red[ty][0][tx] + red[ty][1][tx] : 0.0;
+    A.part[((size_t)chunk * NM + tx) * A.ncell + c] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// moments -> macroscopic state, Shakhov parameters, residual partial sums
+// ---------------------------------------------------------------------------
+
+template <typename T> struct FinalArgs {
+  const double *__restrict__ part;
+  T *__restrict__ mac;
+  const double *__restrict__ Wold; // [NW][ncell], may be null
+  double *__restrict__ Wnew;
+  const uint8_t *__restrict__ ctype;
+  double *__restrict__ resblk; // [nblock][2 NW]
+  int *__restrict__ flags;
+  long long ncell;
+  int nchunk;
+  int shift;
+  double mu0, omega, Pr, dt;
+};
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) finalize_kernel(FinalArgs<T> A) {
+  constexpr int NM = Dims<D>::NM;
+  constexpr int NW = Dims<D>::NW;
+  __shared__ double red[2 * NW][8];
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double rnum[NW], rden[NW];
+#pragma unroll
+  for (int i = 0; i < NW; ++i) rnum[i] = rden[i] = 0.0;
+  if (c < A.ncell && A.ctype[c] == IBDVM_CELL_FLUID) {
+    double M[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) M[m] = 0.0;
+    for (int ch = 0; ch < A.nchunk; ++ch)
+#pragma unroll
+      for (int m = 0; m < NM; ++m) M[m] += A.part[((size_t)ch * NM + m) * A.ncell + c];
+    const long long nc = A.ncell;
+    double V[3] = {0.0, 0.0, 0.0};
+    if (A.shift)
+      for (int a = 0; a < D; ++a) V[a] = (double)A.mac[(kU0 + a) * nc + c];
+    const double rho = M[0];
+    double M1[3] = {0, 0, 0}, d[3] = {0, 0, 0}, d2 = 0.0, VM1 = 0.0, V2 = 0.0;
+    for (int a = 0; a < D; ++a) {
+      M1[a] = M[1 + a];
+      d[a] = M1[a] / rho;
+      d2 += d[a] * d[a];
+      VM1 += V[a] * M1[a];
+      V2 += V[a] * V[a];
+    }
+    const double M2 = M[D + 1];
+    // second moments M_ab about V (symmetric, packed row-wise)
+    double Mab[3][3];
+    {
+      int p = D + 2;
+      for (int a = 0; a < D; ++a)
+        for (int b = a; b < D; ++b) {
+          Mab[a][b] = Mab[b][a] = M[p++];
+        }
+    }
+    const double *M3 = &M[D + 2 + D * (D + 1) / 2];
+    // conservative variables (Eq. moments1) and temperature (Eq. moments2) with
+    // three translational degrees of freedom: rho E = rho |U|^2 / 2 + 3/4 rho T
+    const double rhoE = 0.5 * (M2 + 2.0 * VM1 + V2 * rho);
+    const double T_ = (2.0 / 3.0) * (M2 - rho * d2) / rho;
+    double q[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < D; ++b) s += d[b] * Mab[a][b];
+      // heat flux (Eq. moments3) about U = V + d from the sums about V
+      q[a] = 0.5 * (M3[a] - d[a] * M2 - 2.0 * s + 2.0 * rho * d2 * d[a]);
+    }
+    double Wn[NW];
+    Wn[0] = rho;
+    for (int a = 0; a < D; ++a) Wn[1 + a] = rho * V[a] + M1[a];
+    Wn[D + 1] = rhoE;
+    const double p = 0.5 * rho * T_;
+    const double mu = A.mu0 * pow(T_, A.omega); // Eq. viscosity, T0 = 1
+    const double dtau = A.dt * p / mu;           // tau = mu / p
+    const bool bad = !(rho > 0.0) || !(T_ > 0.0) || !isfinite(rhoE) || !isfinite(dtau);
+    if (bad) atomicOr(A.flags, kFlagNonFinite);
+    if (dtau > 1.0) atomicOr(A.flags, kFlagUnstable);
+    T *Mc = A.mac;
+    Mc[kPre * nc + c] = (T)((D == 2) ? rho / (kPi * T_) : rho / pow(kPi * T_, 1.5));
+    for (int a = 0; a < 3; ++a) {
+      Mc[(kU0 + a) * nc + c] = (T)((a < D) ? V[a] + d[a] : 0.0);
+      Mc[(kQ0 + a) * nc + c] = (T)((a < D) ? q[a] : 0.0);
+    }
+    Mc[kInvT * nc + c] = (T)(1.0 / T_);
+    Mc[kHalfT * nc + c] = (T)(0.5 * T_);
+    Mc[kShA * nc + c] = (T)(4.0 * (1.0 - A.Pr) / (5.0 * rho * T_ * T_));
+    Mc[kDtTau * nc + c] = (T)dtau;
+    for (int a = 0; a < D; ++a) A.Wnew[(NW + a) * nc + c] = q[a];
+    for (int i = 0; i < NW; ++i) {
+      A.Wnew[i * nc + c] = Wn[i];
+      if (A.Wold) {
+        double dd = Wn[i] - A.Wold[i * nc + c];
+        rnum[i] = dd * dd;
+        rden[i] = fabs(Wn[i]);
+      }
+    }
+  }
+  if (A.resblk) {
+    // fixed-order block reduction of the residual sums
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      double a = rnum[i], b = rden[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+      }
+      if (lane == 0) {
+        red[i][wid] = a;
+        red[NW + i][wid] = b;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * NW) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
+      A.resblk[(size_t)blockIdx.x * 2 * NW + threadIdx.x] = s;
+    }
+  }
+}
+
+// res = max_i sqrt(sum_j dW_ij^2) / sum_j |W_ij| (Sec. 4), components with a
+// zero denominator skipped; one block, fixed summation order
+template <int NW>
+__global__ void residual_kernel(const double *__restrict__ resblk, int nblk, double *__restrict__ out) {
+  __shared__ double sh[256];
+  __shared__ double tot[2 * NW];
+  for (int i = 0; i < 2 * NW; ++i) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += resblk[(size_t)b * 2 * NW + i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) tot[i] = sh[0];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < NW; ++i) {
+      if (tot[NW + i] == 0.0) continue;
+      double v = sqrt(tot[i]) / tot[NW + i];
+      r = (v > r) ? v : r;
+    }
+    *out = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the ghost band
+// ---------------------------------------------------------------------------
+
+template <typename T> struct GhostArgs {
+  const T *__restrict__ f;
+  const T *__restrict__ finf;
+  const double *__restrict__ xiD; // [3][nvp]
+  const double *__restrict__ wD;  // [nvp]
+  const T *__restrict__ xiT;
+  const int *__restrict__ l_int;  // [nlink][8]: gidx, donor, aux, axis, side, ghost, s0, s1
+  const double *__restrict__ l_dbl; // [nlink][8]: c_sp, c_iw, c_gc, n0, n1, n2, S, -
+  const double *__restrict__ l_wg;  // [nlink][nvp]
+  const int *__restrict__ s_int;    // [nsurf][8]: cell, codes of the 6 face neighbours
+  const double *__restrict__ s_dbl; // [nsurf][8]: r (weights), |r|, x_j - x_g
+  T *__restrict__ lval;
+  T *__restrict__ fi;
+  T *__restrict__ fsp;
+  double *__restrict__ rhow;
+  double *__restrict__ dbg_fstar; // optional [nlink][nvp][NC] (FP64)
+  int nv, nvp;
+  int nvx[3];
+  double vx0[3], vh[3]; // first node and node spacing per axis (mirror interpolation)
+  double dx[3];
+  double Tw, Uw[3], accom;
+  int plain_average;
+};
+
+template <int NT> __device__ __forceinline__ double block_sum(double v, double *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < NT / 32; ++w) s += sh[w];
+    sh[NT / 32] = s;
+  }
+  __syncthreads();
+  return sh[NT / 32];
+}
+
+// pre-ghost slope of surface cell j along axis a: van Leer with two fluid or
+// halo neighbours, one-sided with one, zero with none
+template <typename T, int NC>
+__device__ __forceinline__ T preghost_slope(const GhostArgs<T> &G, int code_m, int code_p, T fj,
+                                            int k, int m, T rh) {
+  const bool hm = code_m != -2, hp = code_p != -2;
+  T fm = T(0), fp = T(0);
+  if (hm) fm = (code_m >= 0) ? G.f[((size_t)code_m * G.nvp + k) * NC + m] : G.finf[(size_t)k * NC + m];
+  if (hp) fp = (code_p >= 0) ? G.f[((size_t)code_p * G.nvp + k) * NC + m] : G.finf[(size_t)k * NC + m];
+  if (hm && hp) return vanleer((fj - fm) * rh, (fp - fj) * rh);
+  if (hm) return (fj - fm) * rh;
+  if (hp) return (fp - fj) * rh;
+  return T(0);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) ghost_band_kernel(GhostArgs<T> G) {
+  constexpr int NC = Dims<D>::NC;
+  __shared__ double sh[16];
+  const int l = blockIdx.x;
+  const int *li = G.l_int + 8 * l;
+  const double *ld = G.l_dbl + 8 * l;
+  const int donor = li[1], aux = li[2], s0 = li[6], s1 = li[7];
+  const int ns = s1 - s0;
+  const double c_sp = ld[0], c_iw = ld[1], c_gc = ld[2];
+  const double nw[3] = {ld[3], ld[4], ld[5]};
+  const double alpha = G.accom;
+  const double *wgl = G.l_wg + (size_t)l * G.nvp;
+  double Nsum = 0.0, Dsum = 0.0;
+  for (int k = threadIdx.x; k < G.nv; k += blockDim.x) {
+    // upwind weights, Eq. upwind (FP64 for the exact-zero decision in the FP64 path)
+    T xiT[3];
+    for (int a = 0; a < D; ++a) xiT[a] = G.xiT[a * G.nvp + k];
+    T wsum = T(0);
+    for (int j = 0; j < ns; ++j) {
+      const double *sd = G.s_dbl + 8 * (s0 + j);
+      T dot = T(0);
+      for (int a = 0; a < D; ++a) dot = add_rn(dot, div_rn(mul_rn(xiT[a], (T)sd[a]), (T)sd[3]));
+      T mx = dot > T(0) ? dot : T(0);
+      wsum = add_rn(wsum, mul_rn(mx, mx));
+    }
+    const bool fallback = G.plain_average || !(wsum != T(0));
+    T fgc[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) fgc[m] = T(0);
+    for (int j = 0; j < ns; ++j) {
+      const int *si = G.s_int + 8 * (s0 + j);
+      const double *sd = G.s_dbl + 8 * (s0 + j);
+      T wt;
+      if (fallback) {
+        wt = T(1) / T(ns);
+      } else {
+        T dot = T(0);
+        for (int a = 0; a < D; ++a) dot = add_rn(dot, div_rn(mul_rn(xiT[a], (T)sd[a]), (T)sd[3]));
+        T mx = dot > T(0) ? dot : T(0);
+        wt = mul_rn(mx, mx) / wsum;
+      }
+      const int jc = si[0];
+#pragma unroll
+      for (int m = 0; m < NC; ++m) {
+        const T fj = G.f[((size_t)jc * G.nvp + k) * NC + m];
+        T v = fj; // f_j - sigma_j . (x_j - x_g)
+        for (int a = 0; a < D; ++a) {
+          const double r = sd[4 + a];
+          if (r != 0.0) {
+            T sig = preghost_slope<T, NC>(G, si[1 + 2 * a], si[2 + 2 * a], fj, k, m, (T)(1.0 / G.dx[a]));
+            v -= sig * (T)r;
+          }
+        }
+        fgc[m] += wt * v;
+      }
+    }
+    // shifted point (Eq. fsp) and incident distribution at the wall (Eq. fw)
+    T fs[NC], fiv[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const T fd = G.f[((size_t)donor * G.nvp + k) * NC + m];
+      T sp = fd;
+      if (aux >= 0) sp = fd + (T)c_sp * (G.f[((size_t)aux * G.nvp + k) * NC + m] - fd);
+      fs[m] = sp;
+      fiv[m] = sp + (T)c_iw * (fgc[m] - sp);
+      G.fsp[((size_t)l * G.nvp + k) * NC + m] = sp;
+      G.fi[((size_t)l * G.nvp + k) * NC + m] = fiv[m];
+    }
+    // zero-net-mass-flux balance with the cut-cell split (Eq. rhowc), FP64
+    double xn = 0.0, c2 = 0.0;
+    for (int a = 0; a < D; ++a) {
+      const double x = G.xiD[a * G.nvp + k];
+      xn += x * nw[a];
+      c2 += (x - G.Uw[a]) * (x - G.Uw[a]);
+    }
+    const double Gw = ((D == 2) ? 1.0 / (kPi * G.Tw) : 1.0 / pow(kPi * G.Tw, 1.5)) * exp(-c2 / G.Tw);
+    const double wg = wgl[k], ws = G.wD[k] - wg;
+    Nsum += wg * xn * (double)fiv[0];
+    Dsum += ws * xn * Gw;
+  }
+  __syncthreads(); // scratch writes of this block are visible to the block
+  const double N = block_sum<256>(Nsum, sh);
+  const double Dd = block_sum<256>(Dsum, sh);
+  double Ssum = 0.0;
+  if (alpha < 1.0) {
+    // specular part: f^i at the mirrored velocity by multilinear interpolation
+    for (int k = threadIdx.x; k < G.nv; k += blockDim.x) {
+      double xn = 0.0;
+      for (int a = 0; a < D; ++a) xn += G.xiD[a * G.nvp + k] * nw[a];
+      double xm[3];
+      for (int a = 0; a < D; ++a) xm[a] = G.xiD[a * G.nvp + k] - 2.0 * xn * nw[a];
+      bool inside = true;
+      int i0[3] = {0, 0, 0};
+      double t[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        const double xl = G.vx0[a], xh = G.vx0[a] + G.vh[a] * (G.nvx[a] - 1);
+        if (xm[a] < xl || xm[a] > xh) inside = false;
+        double u = (xm[a] - xl) / G.vh[a];
+        int i = (int)floor(u);
+        i = min(max(i, 0), G.nvx[a] - 2);
+        i0[a] = i;
+        t[a] = u - i;
+      }
+      double v = 0.0;
+      if (inside)
+        for (int corner = 0; corner < (1 << D); ++corner) {
+          double wt = 1.0;
+          int id[3] = {0, 0, 0};
+          for (int a = 0; a < D; ++a) {
+            int b = (corner >> a) & 1;
+            id[a] = i0[a] + b;
+            wt *= b ? t[a] : 1.0 - t[a];
+          }
+          int kk = id[0] + G.nvx[0] * (id[1] + G.nvx[1] * id[2]);
+          v += wt * (double)G.fi[((size_t)l * G.nvp + kk) * NC];
+        }
+      Ssum += (G.wD[k] - wgl[k]) * xn * v;
+    }
+  }
+  const double S = (alpha < 1.0) ? block_sum<256>(Ssum, sh) : 0.0;
+  const double rho_w = (alpha > 0.0) ? -(N + (1.0 - alpha) * S) / (alpha * Dd) : 0.0;
+  if (threadIdx.x == 0) G.rhow[l] = rho_w;
+  // wall distribution (Eqs. general bc, Maxwell BC, fwc) and ghost value (Eq. extrapolation 2)
+  for (int k = threadIdx.x; k < G.nv; k += blockDim.x) {
+    double xn = 0.0, c2 = 0.0;
+    for (int a = 0; a < D; ++a) {
+      const double x = G.xiD[a * G.nvp + k];
+      xn += x * nw[a];
+      c2 += (x - G.Uw[a]) * (x - G.Uw[a]);
+    }
+    const double Gw = ((D == 2) ? 1.0 / (kPi * G.Tw) : 1.0 / pow(kPi * G.Tw, 1.5)) * exp(-c2 / G.Tw);
+    double fsv[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) fsv[m] = 0.0;
+    if (alpha < 1.0) {
+      double xm[3];
+      for (int a = 0; a < D; ++a) xm[a] = G.xiD[a * G.nvp + k] - 2.0 * xn * nw[a];
+      bool inside = true;
+      int i0[3] = {0, 0, 0};
+      double t[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        const double xl = G.vx0[a], xh = G.vx0[a] + G.vh[a] * (G.nvx[a] - 1);
+        if (xm[a] < xl || xm[a] > xh) inside = false;
+        double u = (xm[a] - xl) / G.vh[a];
+        int i = (int)floor(u);
+        i = min(max(i, 0), G.nvx[a] - 2);
+        i0[a] = i;
+        t[a] = u - i;
+      }
+      if (inside)
+        for (int corner = 0; corner < (1 << D); ++corner) {
+          double wt = 1.0;
+          int id[3] = {0, 0, 0};
+          for (int a = 0; a < D; ++a) {
+            int b = (corner >> a) & 1;
+            id[a] = i0[a] + b;
+            wt *= b ? t[a] : 1.0 - t[a];
+          }
+          int kk = id[0] + G.nvx[0] * (id[1] + G.nvx[1] * id[2]);
+#pragma unroll
+          for (int m = 0; m < NC; ++m) fsv[m] += wt * (double)G.fi[((size_t)l * G.nvp + kk) * NC + m];
+        }
+    }
+    const double wk = G.wD[k], wg = wgl[k], ws = wk - wg;
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const size_t o = ((size_t)l * G.nvp + k) * NC + m;
+      const double gw = (m == 0) ? Gw : 0.5 * G.Tw * Gw; // B_w = T_w / 2 H_w
+      const double fr = alpha * rho_w * gw + (1.0 - alpha) * fsv[m];
+      const double fiv = (double)G.fi[o];
+      const double fstar = (wk > 0.0) ? (wg * fiv + ws * fr) / wk : fiv;
+      const double spv = (double)G.fsp[o];
+      G.lval[o] = (T)(spv + c_gc * (fstar - spv));
+      if (G.dbg_fstar) G.dbg_fstar[o] = fstar;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forces: momentum and energy through the donor-ghost faces (FP64 sums)
+// ---------------------------------------------------------------------------
+
+template <typename T> struct ForceArgs {
+  SweepArgs<T> S;
+  const int *__restrict__ l_int;
+  const double *__restrict__ l_dbl;
+  const double *__restrict__ xiD;
+  const double *__restrict__ wD;
+  double *__restrict__ fpart; // [nlink][4]
+};
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) forces_kernel(ForceArgs<T> A) {
+  constexpr int NC = Dims<D>::NC;
+  __shared__ double sh[16];
+  const int l = blockIdx.x;
+  const int *li = A.l_int + 8 * l;
+  const int d = li[1], a = li[3], side = li[4];
+  const int sf = -side; // face of the donor toward the ghost
+  const double Sface = A.l_dbl[8 * l + 6];
+  const SweepArgs<T> &S = A.S;
+  int ijk[3];
+  ijk[0] = d % S.n[0];
+  ijk[1] = (d / S.n[0]) % S.n[1];
+  ijk[2] = d / (S.n[0] * S.n[1]);
+  double acc[4] = {0, 0, 0, 0};
+  for (int k = threadIdx.x; k < S.nv; k += blockDim.x) {
+    const double xin = A.xiD[a * S.nvp + k] * sf; // velocity into the solid
+    if (xin == 0.0) continue;
+    T fd[NC], fg[NC], face[NC];
+    load_nc<T, NC>(S.f + ((size_t)d * S.nvp + k) * NC, fd);
+    seen<T, NC>(S, d, ijk, a, sf, k, fg); // the link's ghost value
+    if (xin > 0.0) {
+      T fb[NC];
+      seen<T, NC>(S, d, ijk, a, -sf, k, fb);
+#pragma unroll
+      for (int m = 0; m < NC; ++m) face[m] = fd[m] + T(0.5) * vanleer(fd[m] - fb[m], fg[m] - fd[m]);
+    } else {
+#pragma unroll
+      for (int m = 0; m < NC; ++m) face[m] = T(0.5) * (fg[m] + fd[m]);
+    }
+    const double wk = A.wD[k];
+    double x2 = 0.0;
+    for (int b = 0; b < D; ++b) {
+      const double x = A.xiD[b * S.nvp + k];
+      x2 += x * x;
+      acc[b] += Sface * wk * x * xin * (double)face[0];
+    }
+    double e = 0.5 * x2 * (double)face[0];
+    if (D == 2) e += 0.5 * (double)face[NC - 1];
+    acc[3] += Sface * wk * e * xin;
+  }
+  for (int i = 0; i < 4; ++i) {
+    double s = block_sum<256>(acc[i], sh);
+    if (threadIdx.x == 0) A.fpart[4 * l + i] = s;
+  }
+}
+
+__global__ void forces_total_kernel(const double *__restrict__ fpart, int nlink, double *__restrict__ out) {
+  __shared__ double sh[256];
+  for (int i = 0; i < 4; ++i) {
+    double s = 0.0;
+    for (int l = threadIdx.x; l < nlink; l += blockDim.x) s += fpart[4 * l + i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = sh[0];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// initial state and format conversion
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void init_state_kernel(T *__restrict__ f0, T *__restrict__ f1, const T *__restrict__ finf,
+                                  long long ncell, int per_cell) {
+  const long long total = ncell * per_cell;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T v = finf[i % per_cell];
+    f0[i] = v;
+    f1[i] = v;
+  }
+}
+
+// dense FP64 [cells][nv][NC] <-> padded state [cells][nvp][NC] for a range of cells
+template <typename T>
+__global__ void convert_kernel(T *__restrict__ state, double *__restrict__ dense, long long c0,
+                               long long ncells, int nv, int nvp, int NC, int to_state) {
+  const long long total = ncells * (long long)nv * NC;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long cell = i / ((long long)nv * NC);
+    const long long r = i % ((long long)nv * NC);
+    const size_t si = ((size_t)(c0 + cell) * nvp) * NC + r;
+    if (to_state)
+      state[si] = (T)dense[i];
+    else
+      dense[i] = (double)state[si];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+
+template <typename T> SweepArgs<T> sweep_args(ibdvm_ctx *ctx, int update, int shift = 1) {
+  SweepArgs<T> A{};
+  A.f = static_cast<const T *>(ctx->f[ctx->cur]);
+  A.fn = static_cast<T *>(ctx->f[1 - ctx->cur]);
+  A.mac = static_cast<const T *>(ctx->mac);
+  A.xi = static_cast<const T *>(ctx->xiT);
+  A.w = static_cast<const T *>(ctx->wT);
+  A.finf = static_cast<const T *>(ctx->finf);
+  A.ctype = ctx->ctype;
+  A.dslot = ctx->dslot;
+  A.dlinks = ctx->dlinks;
+  A.lval = static_cast<const T *>(ctx->lval);
+  A.part = ctx->part;
+  A.ncell = ctx->ncell;
+  for (int a = 0; a < 3; ++a) {
+    A.n[a] = ctx->geom.n[a];
+    A.rdx[a] = (T)(1.0 / ctx->geom.dx[a]);
+  }
+  A.nv = ctx->nv;
+  A.nvp = ctx->nvp;
+  A.kloop = ctx->kloop;
+  A.dt = (T)ctx->geom.dt;
+  A.update = update;
+  A.shift = shift;
+  return A;
+}
+
+template <typename T, int D> cudaError_t sweep_t(ibdvm_ctx *ctx, int update, int shift) {
+  SweepArgs<T> A = sweep_args<T>(ctx, update, shift);
+  dim3 block(kThreadsPerCell, kCellsPerBlock);
+  dim3 grid((unsigned)((ctx->ncell + kCellsPerBlock - 1) / kCellsPerBlock), (unsigned)ctx->nchunk);
+  sweep_kernel<T, D><<<grid, block, 0, ctx->stream>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename T, int D> cudaError_t finalize_t(ibdvm_ctx *ctx, bool shift, bool residual) {
+  FinalArgs<T> A{};
+  A.part = ctx->part;
+  A.mac = static_cast<T *>(ctx->mac);
+  A.Wold = residual ? ctx->W[ctx->wcur] : nullptr;
+  A.Wnew = ctx->W[1 - ctx->wcur];
+  A.ctype = ctx->ctype;
+  A.resblk = residual ? ctx->resblk : nullptr;
+  A.flags = ctx->d_flags;
+  A.ncell = ctx->ncell;
+  A.nchunk = ctx->nchunk;
+  A.shift = shift ? 1 : 0;
+  A.mu0 = ctx->geom.mu0;
+  A.omega = ctx->geom.gas.omega_vhs;
+  A.Pr = ctx->geom.gas.Pr;
+  A.dt = ctx->geom.dt;
+  const int nblk = (int)((ctx->ncell + 255) / 256);
+  finalize_kernel<T, D><<<nblk, 256, 0, ctx->stream>>>(A);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (residual) {
+    residual_kernel<Dims<D>::NW><<<1, 256, 0, ctx->stream>>>(ctx->resblk, nblk, ctx->d_res);
+    e = cudaGetLastError();
+  }
+  ctx->wcur = 1 - ctx->wcur;
+  return e;
+}
+
+template <typename T, int D> cudaError_t ghost_t(ibdvm_ctx *ctx, double *dbg) {
+  if (ctx->nlink == 0) return cudaSuccess;
+  const Geom &g = ctx->geom;
+  GhostArgs<T> G{};
+  G.f = static_cast<const T *>(ctx->f[ctx->cur]);
+  G.finf = static_cast<const T *>(ctx->finf);
+  G.xiD = ctx->xiD;
+  G.wD = ctx->wD;
+  G.xiT = static_cast<const T *>(ctx->xiT);
+  G.l_int = ctx->l_int;
+  G.l_dbl = ctx->l_dbl;
+  G.l_wg = ctx->l_wg;
+  G.s_int = ctx->s_int;
+  G.s_dbl = ctx->s_dbl;
+  G.lval = static_cast<T *>(ctx->lval);
+  G.fi = static_cast<T *>(ctx->fi_scr);
+  G.fsp = static_cast<T *>(ctx->fsp_scr);
+  G.rhow = ctx->rhow;
+  G.dbg_fstar = dbg;
+  G.nv = ctx->nv;
+  G.nvp = ctx->nvp;
+  for (int a = 0; a < 3; ++a) {
+    G.nvx[a] = g.nvx[a];
+    G.dx[a] = g.dx[a];
+    G.Uw[a] = g.body.U_w[a];
+    // first node and spacing per axis of the node grid
+    const int stride = (a == 0) ? 1 : (a == 1 ? g.nvx[0] : g.nvx[0] * g.nvx[1]);
+    const double x0 = g.xi[3 * 0 + a];
+    const double x1 = g.xi[3 * ((g.nvx[a] - 1) * stride) + a];
+    G.vx0[a] = x0;
+    G.vh[a] = (g.nvx[a] > 1) ? (x1 - x0) / (g.nvx[a] - 1) : 1.0;
+  }
+  G.Tw = g.body.T_w;
+  G.accom = g.body.accom_alpha;
+  G.plain_average = (g.gas.flags & IBDVM_PLAIN_AVERAGE) ? 1 : 0;
+  ghost_band_kernel<T, D><<<ctx->nlink, 256, 0, ctx->stream>>>(G);
+  return cudaGetLastError();
+}
+
+template <typename T, int D> cudaError_t forces_t(ibdvm_ctx *ctx, double *dst) {
+  if (ctx->nlink == 0) return cudaMemsetAsync(dst, 0, 4 * sizeof(double), ctx->stream);
+  ForceArgs<T> A{};
+  A.S = sweep_args<T>(ctx, 0);
+  A.l_int = ctx->l_int;
+  A.l_dbl = ctx->l_dbl;
+  A.xiD = ctx->xiD;
+  A.wD = ctx->wD;
+  A.fpart = ctx->fpart;
+  forces_kernel<T, D><<<ctx->nlink, 256, 0, ctx->stream>>>(A);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  forces_total_kernel<<<1, 256, 0, ctx->stream>>>(ctx->fpart, ctx->nlink, dst);
+  return cudaGetLastError();
+}
+
+// CUDA events around a launch class when the context profiles its kernels
+struct Timed {
+  ibdvm_ctx *ctx;
+  int cls;
+  size_t start = 0;
+  bool on;
+  Timed(ibdvm_ctx *c, int k) : ctx(c), cls(k), on(c->profiling) {
+    if (!on) return;
+    if (ctx->ev_used + 2 > ctx->ev_pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          on = false;
+          return;
+        }
+        ctx->ev_pool.push_back(e);
+      }
+    }
+    start = ctx->ev_used;
+    ctx->ev_used += 2;
+    cudaEventRecord(ctx->ev_pool[start], ctx->stream);
+  }
+  ~Timed() {
+    if (!on) return;
+    cudaEventRecord(ctx->ev_pool[start + 1], ctx->stream);
+    ctx->ev_marks.emplace_back(cls, start);
+  }
+};
+
+template <typename F> cudaError_t dispatch(ibdvm_ctx *ctx, F &&fn) {
+  if (ctx->precision == IBDVM_FP64) {
+    if (ctx->dim == 2) return fn(double(), std::integral_constant<int, 2>());
+    return fn(double(), std::integral_constant<int, 3>());
+  }
+  if (ctx->dim == 2) return fn(float(), std::integral_constant<int, 2>());
+  return fn(float(), std::integral_constant<int, 3>());
+}
+
+} // namespace
+
+cudaError_t launch_init_state(ibdvm_ctx *ctx) {
+  const int per_cell = ctx->nvp * ctx->ncomp;
+  const long long total = ctx->ncell * per_cell;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
+  if (ctx->precision == IBDVM_FP64)
+    init_state_kernel<double><<<grid, 256, 0, ctx->stream>>>(
+        static_cast<double *>(ctx->f[0]), static_cast<double *>(ctx->f[1]),
+        static_cast<const double *>(ctx->finf), ctx->ncell, per_cell);
+  else
+    init_state_kernel<float><<<grid, 256, 0, ctx->stream>>>(
+        static_cast<float *>(ctx->f[0]), static_cast<float *>(ctx->f[1]),
+        static_cast<const float *>(ctx->finf), ctx->ncell, per_cell);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(ibdvm_ctx *ctx, bool shift, bool residual) {
+  Timed t(ctx, kKMoments);
+  ctx->kernel_launches[kKMoments] += residual ? 3 : 2;
+  return dispatch(ctx, [&](auto t, auto d) -> cudaError_t {
+    using T = decltype(t);
+    constexpr int D = decltype(d)::value;
+    cudaError_t e = sweep_t<T, D>(ctx, 0, shift ? 1 : 0);
+    if (e != cudaSuccess) return e;
+    return finalize_t<T, D>(ctx, shift, residual);
+  });
+}
+
+cudaError_t launch_ghost_band(ibdvm_ctx *ctx, double *dbg) {
+  if (ctx->nlink == 0) return cudaSuccess;
+  Timed t(ctx, kKGhost);
+  ctx->kernel_launches[kKGhost] += 1;
+  return dispatch(ctx, [&](auto t, auto d) -> cudaError_t {
+    using T = decltype(t);
+    constexpr int D = decltype(d)::value;
+    return ghost_t<T, D>(ctx, dbg);
+  });
+}
+
+cudaError_t launch_sweep(ibdvm_ctx *ctx) {
+  return dispatch(ctx, [&](auto t, auto d) -> cudaError_t {
+    using T = decltype(t);
+    constexpr int D = decltype(d)::value;
+    cudaError_t e;
+    {
+      Timed tm(ctx, kKSweep);
+      ctx->kernel_launches[kKSweep] += 1;
+      e = sweep_t<T, D>(ctx, 1, 1);
+    }
+    if (e != cudaSuccess) return e;
+    ctx->cur = 1 - ctx->cur;
+    Timed tm(ctx, kKMoments);
+    ctx->kernel_launches[kKMoments] += 2;
+    return finalize_t<T, D>(ctx, true, true);
+  });
+}
+
+cudaError_t launch_forces(ibdvm_ctx *ctx, double *dst) {
+  Timed t(ctx, kKForces);
+  ctx->kernel_launches[kKForces] += ctx->nlink ? 2 : 0;
+  return dispatch(ctx, [&](auto t, auto d) -> cudaError_t {
+    using T = decltype(t);
+    constexpr int D = decltype(d)::value;
+    return forces_t<T, D>(ctx, dst);
+  });
+}
+
+cudaError_t launch_convert(ibdvm_ctx *ctx, double *dense, long long c0, long long ncells, bool to_state) {
+  const long long total = ncells * (long long)ctx->nv * ctx->ncomp;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
+  if (total == 0) return cudaSuccess;
+  if (ctx->precision == IBDVM_FP64)
+    convert_kernel<double><<<grid, 256, 0, ctx->stream>>>(static_cast<double *>(ctx->f[ctx->cur]), dense, c0,
+                                                          ncells, ctx->nv, ctx->nvp, ctx->ncomp, to_state);
+  else
+    convert_kernel<float><<<grid, 256, 0, ctx->stream>>>(static_cast<float *>(ctx->f[ctx->cur]), dense, c0,
+                                                         ncells, ctx->nv, ctx->nvp, ctx->ncomp, to_state);
+  return cudaGetLastError();
+}
+
+} // namespace ibdvm

@@ -1,0 +1,405 @@
+"""Thin ctypes binding of libibdvm.so (the C-ABI declared in include/ibdvm.h).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  The binding raises when the library is missing; there is no CPU or
+PyTorch fallback.
+
+Case descriptions are plain dicts (see ``workloads``): dim, n, lo, hi, nv, vlo,
+vhi, rule, Kn, Ma, Pr, gamma, omega_vhs, alpha_vhs, rho_inf, T_inf, dir, cfl,
+dt, precision ("fp64" | "mixed"), cutcell, upwind (1 upwind weights, 2 the
+reverse unit vector, 0 plain average) and body = {kind, center, radii, angle,
+verts, accom, Tw, Uw, Lref}.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libibdvm.so")
+
+OK = 0
+STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_UNSTABLE", 5: "E_NONFINITE",
+          6: "E_NOTCONVERGED", 7: "E_TIMEOUT", 8: "E_STATE"}
+BODY = {"none": 0, "circle": 1, "ellipse": 2, "sphere": 3, "polygon": 4, "halfspace": 5}
+FLUID, GHOST, SOLID = 0, 1, 2
+NO_CUTCELL, PLAIN_AVERAGE, RHAT_GHOST_TO_FLUID = 1, 2, 4
+
+
+class IbdvmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3)]
+
+
+class VGridDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("rule", ctypes.c_int)]
+
+
+class GasDesc(ctypes.Structure):
+    _fields_ = [("Kn", ctypes.c_double), ("Ma", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("omega_vhs", ctypes.c_double),
+                ("alpha_vhs", ctypes.c_double), ("rho_inf", ctypes.c_double),
+                ("T_inf", ctypes.c_double), ("dir", ctypes.c_double * 3), ("cfl", ctypes.c_double),
+                ("dt", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class BodyDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("center", ctypes.c_double * 3),
+                ("radii", ctypes.c_double * 3), ("angle", ctypes.c_double),
+                ("verts", ctypes.POINTER(ctypes.c_double)), ("nverts", ctypes.c_int),
+                ("accom_alpha", ctypes.c_double), ("T_w", ctypes.c_double),
+                ("U_w", ctypes.c_double * 3), ("L_ref", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("ncomp", ctypes.c_int), ("ncell", ctypes.c_longlong),
+                ("nfluid", ctypes.c_longlong), ("nvel", ctypes.c_int), ("nvel_padded", ctypes.c_int),
+                ("nlink", ctypes.c_int), ("nghost", ctypes.c_int), ("dt", ctypes.c_double),
+                ("precision", ctypes.c_int), ("steps_done", ctypes.c_longlong),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_LL = ctypes.POINTER(ctypes.c_longlong)
+_U8 = ctypes.POINTER(ctypes.c_ubyte)
+_V = ctypes.c_void_p
+_S = ctypes.c_int
+
+SIGNATURES = {
+    "ibdvm_create_grid": ([ctypes.POINTER(GridDesc), ctypes.POINTER(VGridDesc),
+                           ctypes.POINTER(GasDesc), _V, ctypes.POINTER(_V)], _S),
+    "ibdvm_set_body": ([_V, ctypes.POINTER(BodyDesc)], _S),
+    "ibdvm_step": ([_V, ctypes.c_int, _D], _S),
+    "ibdvm_moments": ([_V, _D, _D, _U8], _S),
+    "ibdvm_forces": ([_V, _D, _D, _D, _D], _S),
+    "ibdvm_step_forces": ([_V, _D, _D, _D, _D], _S),
+    "ibdvm_set_profiling": ([_V, ctypes.c_int], _S),
+    "ibdvm_get_kernel_times": ([_V, _D, _LL], _S),
+    "ibdvm_reset_kernel_times": ([_V], _S),
+    "ibdvm_get_f": ([_V, _D], _S),
+    "ibdvm_set_f": ([_V, _D], _S),
+    "ibdvm_get_f_native": ([_V, _V, ctypes.c_size_t], _S),
+    "ibdvm_set_f_native": ([_V, _V, ctypes.c_size_t], _S),
+    "ibdvm_ghost_band": ([_V, _D, _D, _D, _D], _S),
+    "ibdvm_get_info": ([_V, ctypes.POINTER(Info)], _S),
+    "ibdvm_set_stream": ([_V, _V], _S),
+    "ibdvm_get_geom": ([_V], _V),
+    "ibdvm_destroy": ([_V], None),
+    "ibdvm_last_error": ([_V], ctypes.c_char_p),
+    "ibdvm_status_string": ([_S], ctypes.c_char_p),
+    "ibdvm_geom_build": ([ctypes.POINTER(GridDesc), ctypes.POINTER(VGridDesc), ctypes.POINTER(GasDesc),
+                          ctypes.POINTER(BodyDesc), ctypes.POINTER(_V)], _S),
+    "ibdvm_geom_sizes": ([_V, _LL], _S),
+    "ibdvm_geom_cells": ([_V, _U8], _S),
+    "ibdvm_geom_links": ([_V, _I, _I, _I, _I, _I, _D, _D], _S),
+    "ibdvm_geom_cut_table": ([_V, _D], _S),
+    "ibdvm_geom_velocities": ([_V, _D, _D], _S),
+    "ibdvm_geom_surface": ([_V, _I, _I, _I], _S),
+    "ibdvm_geom_dt": ([_V], ctypes.c_double),
+    "ibdvm_geom_destroy": ([_V], None),
+    "ibdvm_geom_last_error": ([], ctypes.c_char_p),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Loads libibdvm.so; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(
+                    f"libibdvm.so not found at {p}: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = ctypes.CDLL(p)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _a3(v, fill=0.0):
+    v = list(v) + [fill] * 3
+    return v[:3]
+
+
+def descriptors(case: dict):
+    """Marshal a case dict into the four C descriptors (plus owners of arrays)."""
+    dim = int(case["dim"])
+    g = GridDesc()
+    g.dim = dim
+    g.n[:] = [int(x) for x in _a3(case["n"], 1)]
+    g.lo[:] = _a3(case["lo"])
+    g.hi[:] = _a3(case["hi"], 1.0)
+    v = VGridDesc()
+    v.n[:] = [int(x) for x in _a3(case["nv"], 1)]
+    v.lo[:] = _a3(case["vlo"])
+    v.hi[:] = _a3(case["vhi"], 1.0)
+    v.rule = {"trapezoid": 0, "midpoint": 1}[case.get("rule", "trapezoid")]
+    s = GasDesc()
+    s.Kn = case["Kn"]
+    s.Ma = case["Ma"]
+    s.Pr = case.get("Pr", 2.0 / 3.0)
+    s.gamma = case.get("gamma", 5.0 / 3.0)
+    s.omega_vhs = case.get("omega_vhs", 0.81)
+    s.alpha_vhs = case.get("alpha_vhs", 1.0)
+    s.rho_inf = case.get("rho_inf", 1.0)
+    s.T_inf = case.get("T_inf", 1.0)
+    s.dir[:] = _a3(case.get("dir", [1.0, 0.0, 0.0]))
+    s.cfl = case.get("cfl", 0.5)
+    s.dt = case.get("dt", 0.0)
+    s.precision = {"fp64": 0, "mixed": 1}[case.get("precision", "fp64")]
+    flags = 0
+    if not int(case.get("cutcell", 1)):
+        flags |= NO_CUTCELL
+    up = int(case.get("upwind", 1))
+    if up == 0:
+        flags |= PLAIN_AVERAGE
+    elif up == 2:
+        flags |= RHAT_GHOST_TO_FLUID
+    s.flags = flags
+    body = case.get("body") or {"kind": "none"}
+    b = BodyDesc()
+    b.kind = BODY[body["kind"]]
+    b.center[:] = _a3(body.get("center", [0.0, 0.0, 0.0]))
+    b.radii[:] = _a3(body.get("radii", [0.0, 0.0, 0.0]))
+    b.angle = body.get("angle", 0.0)
+    keep = None
+    if body["kind"] == "polygon":
+        keep = np.ascontiguousarray(np.asarray(body["verts"], dtype=np.float64).reshape(-1))
+        b.verts = keep.ctypes.data_as(_D)
+        b.nverts = keep.size // 2
+    b.accom_alpha = body.get("accom", 1.0)
+    b.T_w = body.get("Tw", 1.0)
+    b.U_w[:] = _a3(body.get("Uw", [0.0, 0.0, 0.0]))
+    b.L_ref = body.get("Lref", 0.0)
+    return g, v, s, b, keep
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+class Geometry:
+    """Host-only geometry of a case (classification, links, cut table); no GPU."""
+
+    def __init__(self, case: dict):
+        self.lib = load()
+        g, v, s, b, self._keep = descriptors(case)
+        h = _V()
+        st = self.lib.ibdvm_geom_build(ctypes.byref(g), ctypes.byref(v), ctypes.byref(s),
+                                       ctypes.byref(b), ctypes.byref(h))
+        if st != OK:
+            raise IbdvmError(st, self.lib.ibdvm_geom_last_error().decode())
+        self.h = h
+        self._owned = True
+        self._read_sizes()
+
+    @classmethod
+    def _borrow(cls, lib, handle):
+        self = cls.__new__(cls)
+        self.lib = lib
+        self.h = _V(handle)
+        self._owned = False
+        self._read_sizes()
+        return self
+
+    def _read_sizes(self):
+        sz = np.zeros(8, dtype=np.int64)
+        self.lib.ibdvm_geom_sizes(self.h, sz.ctypes.data_as(_LL))
+        (self.ncell, self.nvel, self.ncomp, self.nlink, self.nghost, self.nfluid, self.nsurf,
+         self.nvel_padded) = (int(x) for x in sz)
+
+    def __del__(self):
+        if getattr(self, "_owned", False) and getattr(self, "h", None):
+            self.lib.ibdvm_geom_destroy(self.h)
+            self.h = None
+
+    @property
+    def dt(self):
+        return float(self.lib.ibdvm_geom_dt(self.h))
+
+    def cell_types(self):
+        t = np.zeros(self.ncell, dtype=np.uint8)
+        self.lib.ibdvm_geom_cells(self.h, t.ctypes.data_as(_U8))
+        return t
+
+    def links(self):
+        n = self.nlink
+        ints = [np.zeros(n, dtype=np.int32) for _ in range(5)]
+        xw = np.zeros((n, 3))
+        nw = np.zeros((n, 3))
+        self.lib.ibdvm_geom_links(self.h, *[a.ctypes.data_as(_I) for a in ints], _dp(xw), _dp(nw))
+        out = dict(zip(["ghost", "donor", "aux", "axis", "side"], ints))
+        out["xw"] = xw
+        out["nw"] = nw
+        return out
+
+    def cut_table(self):
+        wg = np.zeros((self.nlink, self.nvel))
+        self.lib.ibdvm_geom_cut_table(self.h, _dp(wg))
+        return wg
+
+    def velocities(self):
+        xi = np.zeros((self.nvel, 3))
+        w = np.zeros(self.nvel)
+        self.lib.ibdvm_geom_velocities(self.h, _dp(xi), _dp(w))
+        return xi, w
+
+    def surface_cells(self):
+        g = np.zeros(self.nghost, dtype=np.int32)
+        off = np.zeros(self.nghost + 1, dtype=np.int32)
+        cells = np.zeros(max(self.nsurf, 1), dtype=np.int32)
+        self.lib.ibdvm_geom_surface(self.h, g.ctypes.data_as(_I), off.ctypes.data_as(_I),
+                                    cells.ctypes.data_as(_I))
+        return g, off, cells[: self.nsurf]
+
+
+class Solver:
+    """One solver context on the current CUDA device (C-ABI handle)."""
+
+    def __init__(self, case: dict, stream: int | None = None):
+        self.lib = load()
+        self.case = dict(case)
+        g, v, s, b, keep = descriptors(case)
+        h = _V()
+        st = self.lib.ibdvm_create_grid(ctypes.byref(g), ctypes.byref(v), ctypes.byref(s),
+                                        _V(stream or 0), ctypes.byref(h))
+        if st != OK:
+            raise IbdvmError(st, self.lib.ibdvm_last_error(None).decode())
+        self.h = h
+        body = case.get("body") or {"kind": "none"}
+        if body["kind"] != "none":
+            self._check(self.lib.ibdvm_set_body(self.h, ctypes.byref(b)))
+        self._keep = keep
+        self.refresh_info()
+
+    def _check(self, st):
+        if st != OK:
+            raise IbdvmError(st, self.lib.ibdvm_last_error(self.h).decode())
+        return st
+
+    def refresh_info(self):
+        info = Info()
+        self._check(self.lib.ibdvm_get_info(self.h, ctypes.byref(info)))
+        self.info = info
+        self.dim, self.ncomp = info.dim, info.ncomp
+        self.ncell, self.nvel, self.nvel_padded = info.ncell, info.nvel, info.nvel_padded
+        self.nlink, self.nghost, self.dt = info.nlink, info.nghost, info.dt
+        self.precision = "fp64" if info.precision == 0 else "mixed"
+        return info
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ibdvm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_body(self, body: dict):
+        c = dict(self.case)
+        c["body"] = body
+        _, _, _, b, keep = descriptors(c)
+        self._check(self.lib.ibdvm_set_body(self.h, ctypes.byref(b)))
+        self._keep = keep
+        self.case = c
+        self.refresh_info()
+
+    def set_stream(self, stream: int | None):
+        self._check(self.lib.ibdvm_set_stream(self.h, _V(stream or 0)))
+
+    def step(self, nsteps: int = 1) -> float:
+        r = ctypes.c_double(0.0)
+        self._check(self.lib.ibdvm_step(self.h, int(nsteps), ctypes.byref(r)))
+        return r.value
+
+    def moments(self):
+        W = np.zeros((self.ncell, self.dim + 2))
+        q = np.zeros((self.ncell, self.dim))
+        t = np.zeros(self.ncell, dtype=np.uint8)
+        self._check(self.lib.ibdvm_moments(self.h, _dp(W), _dp(q), t.ctypes.data_as(_U8)))
+        return W, q, t
+
+    def forces(self):
+        F = np.zeros(3)
+        Q, CD, CL = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.ibdvm_forces(self.h, _dp(F), ctypes.byref(Q), ctypes.byref(CD),
+                                          ctypes.byref(CL)))
+        return F, Q.value, CD.value, CL.value
+
+    def step_forces(self):
+        F = np.zeros(3)
+        Q, CD, CL = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.ibdvm_step_forces(self.h, _dp(F), ctypes.byref(Q), ctypes.byref(CD),
+                                               ctypes.byref(CL)))
+        return F, Q.value, CD.value, CL.value
+
+    KERNEL_CLASSES = ("ghost_band", "sweep", "moments", "forces")
+
+    def set_profiling(self, on: bool = True):
+        self._check(self.lib.ibdvm_set_profiling(self.h, 1 if on else 0))
+
+    def kernel_times(self):
+        ms = np.zeros(8)
+        n = np.zeros(8, dtype=np.int64)
+        self._check(self.lib.ibdvm_get_kernel_times(self.h, _dp(ms), n.ctypes.data_as(_LL)))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def reset_kernel_times(self):
+        self._check(self.lib.ibdvm_reset_kernel_times(self.h))
+
+    def shape(self):
+        return (self.ncell, self.nvel, self.ncomp)
+
+    def get_f(self) -> np.ndarray:
+        f = np.zeros(self.shape())
+        self._check(self.lib.ibdvm_get_f(self.h, _dp(f)))
+        return f
+
+    def set_f(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.shape())
+        self._check(self.lib.ibdvm_set_f(self.h, _dp(f)))
+
+    def native_shape(self):
+        return (self.ncell, self.nvel_padded, self.ncomp)
+
+    def native_dtype(self):
+        return np.float64 if self.precision == "fp64" else np.float32
+
+    def get_f_native(self, out_ptr: int, nbytes: int):
+        self._check(self.lib.ibdvm_get_f_native(self.h, _V(out_ptr), ctypes.c_size_t(nbytes)))
+
+    def set_f_native(self, in_ptr: int, nbytes: int):
+        self._check(self.lib.ibdvm_set_f_native(self.h, _V(in_ptr), ctypes.c_size_t(nbytes)))
+
+    def ghost_band(self):
+        shp = (self.nlink, self.nvel, self.ncomp)
+        out = {k: np.zeros(shp) for k in ("fiw", "fstarw", "fstargc")}
+        rhow = np.zeros(max(self.nlink, 1))
+        self._check(self.lib.ibdvm_ghost_band(self.h, _dp(out["fiw"]), _dp(out["fstarw"]),
+                                              _dp(out["fstargc"]), _dp(rhow)))
+        out["rhow"] = rhow[: self.nlink]
+        return out
+
+    def geometry(self) -> Geometry:
+        return Geometry._borrow(self.lib, self.lib.ibdvm_get_geom(self.h))

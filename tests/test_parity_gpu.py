@@ -1,0 +1,273 @@
+"""GPU path (through the C-ABI) against the CPU oracle, element by element.
+
+Tolerances: the FP64 path must match the oracle within 1e-11 relative on f and
+W (max |difference| over fluid cells divided by the largest |value|); the
+mixed path (FP32 storage and transport) within 1e-5 on W and 1e-4 on C_D.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_20252_gb300 import ibdvm
+from paper_2512_20252_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def rel_err(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def compare(g, o, tol=TOL, wtol=None, forces=True, q=True):
+    t = o.cell_types()
+    fl = t == oracle.FLUID
+    fe = rel_err(g.get_f()[fl], o.get_f()[fl])
+    Wg, qg, tg = g.moments()
+    Wo, qo = o.moments()
+    np.testing.assert_array_equal(tg, t)
+    we = max(rel_err(Wg[fl, i], Wo[fl, i]) for i in range(Wo.shape[1]) if np.abs(Wo[fl, i]).max() > 1e-9)
+    assert fe < tol, fe
+    assert we < (wtol or tol), we
+    if q:
+        qe = float(np.abs(qg[fl] - qo[fl]).max() / max(np.abs(qo[fl]).max(), 1e-3))
+        assert qe < 1e3 * (wtol or tol), qe
+    if forces and o.nlink:
+        Fg, Qg, CDg, CLg = g.forces()
+        Fo, Qo, CDo, CLo = o.forces()
+        scale = np.abs(Fo).max()
+        assert np.abs(Fg - Fo).max() < 10 * (wtol or tol) * scale, (Fg, Fo)
+        assert abs(Qg - Qo) < 10 * (wtol or tol) * max(abs(Qo), 1e-6), (Qg, Qo)
+        assert abs(CDg - CDo) < 10 * (wtol or tol) * max(abs(CDo), 1e-6), (CDg, CDo)
+    return fe, we
+
+
+def pair(case, steps, f0=None):
+    g = ibdvm.Solver(case)
+    o = oracle.OracleCase(case)
+    if f0 is not None:
+        o.set_f(f0)
+        g.set_f(f0)
+    rg = g.step(steps)
+    ro = o.step(steps)
+    return g, o, rg, ro
+
+
+def perturbed(o, seed, amp=0.3):
+    rng = np.random.default_rng(seed)
+    return o.get_f() * (1.0 + amp * rng.uniform(-1.0, 1.0, size=o.shape()))
+
+
+def test_cylinder_48_fp64_parity():
+    """2D cylinder, 48^2 cells, 24^2 trapezoid velocities, Kn 0.1, Ma 0.3."""
+    case = wl.cylinder_48()
+    g, o, rg, ro = pair(case, 10)
+    compare(g, o)
+    assert rg == pytest.approx(ro, rel=1e-9)
+    g.close()
+
+
+@pytest.mark.parametrize("body", ["circle", "ellipse", "naca"])
+def test_perturbed_state_parity(body):
+    case = wl.small_2d(body, n=40 if body == "naca" else 24, nv=11, Kn=0.05, Ma=0.4)
+    o0 = oracle.OracleCase(case)
+    f0 = perturbed(o0, 11)
+    g, o, rg, ro = pair(case, 4, f0)
+    compare(g, o)
+    assert rg == pytest.approx(ro, rel=1e-9)
+
+
+@pytest.mark.parametrize("variant", ["midpoint", "nocut", "plain_average", "rhat_reverse",
+                                     "accom_0.6", "hot_moving_wall", "bgk", "odd_grid"])
+def test_method_variants_parity(variant):
+    case = wl.small_2d("ellipse", n=24, nv=10, Kn=0.08, Ma=0.5)
+    if variant == "midpoint":
+        case["rule"] = "midpoint"
+    elif variant == "nocut":
+        case["cutcell"] = 0
+    elif variant == "plain_average":
+        case["upwind"] = 0
+    elif variant == "rhat_reverse":
+        case["upwind"] = 2
+    elif variant == "accom_0.6":
+        case["body"]["accom"] = 0.6
+    elif variant == "hot_moving_wall":
+        case["body"]["Tw"] = 1.4
+        case["body"]["Uw"] = [0.1, -0.05, 0.0]
+    elif variant == "bgk":
+        case["Pr"] = 1.0
+    elif variant == "odd_grid":
+        case["n"] = [27, 19]
+        case["nv"] = [13, 9]
+        case["hi"] = [2.0, 1.6]
+        case["lo"] = [-2.2, -1.6]
+    o0 = oracle.OracleCase(case)
+    g, o, rg, ro = pair(case, 3, perturbed(o0, 5, 0.2))
+    compare(g, o)
+
+
+def test_ghost_band_parity():
+    case = wl.small_2d("naca", n=40, nv=12, Ma=0.6)
+    case["body"]["accom"] = 0.7
+    o = oracle.OracleCase(case)
+    f0 = perturbed(o, 9, 0.25)
+    o.set_f(f0)
+    g = ibdvm.Solver(case)
+    g.set_f(f0)
+    gb, ob = g.ghost_band(), o.ghost_band()
+    for k in ("fiw", "fstarw", "fstargc"):
+        assert rel_err(gb[k], ob[k]) < TOL, k
+    np.testing.assert_allclose(gb["rhow"], ob["rhow"], rtol=1e-12)
+
+
+def test_sphere_3d_parity():
+    case = wl._case(3, 14, 2.0, 8, 4.5, 0.1, 0.5, wl.sphere(0.6))
+    o0 = oracle.OracleCase(case)
+    g, o, rg, ro = pair(case, 3, perturbed(o0, 3, 0.2))
+    compare(g, o)
+    assert rg == pytest.approx(ro, rel=1e-9)
+
+
+@pytest.mark.slow
+def test_sphere_24_downscale_parity():
+    """The 3D sphere case downscaled to 24^3 cells and 12^3 velocities."""
+    case = wl.sphere_24()
+    g, o, rg, ro = pair(case, 2)
+    compare(g, o)
+
+
+def test_halfspace_3d_wall_at_domain_edge():
+    body = {"kind": "halfspace", "center": [-0.45, 0.0, 0.0], "radii": [0.8, 0.6, 0.0],
+            "accom": 0.5, "Tw": 1.2}
+    case = wl._case(3, 10, 1.0, 6, 4.0, 0.1, 0.3, body)
+    o0 = oracle.OracleCase(case)
+    g, o, _, _ = pair(case, 2, perturbed(o0, 4, 0.1))
+    compare(g, o)
+
+
+def test_no_body_and_tiny_grid():
+    case = wl._case(2, 4, 1.0, 2, 3.0, 0.2, 0.2, {"kind": "none"})
+    o0 = oracle.OracleCase(case)
+    g, o, _, _ = pair(case, 3, perturbed(o0, 2, 0.2))
+    compare(g, o, forces=False)
+
+
+def test_mixed_precision_against_fp64_oracle():
+    case = wl.cylinder_48()
+    case["precision"] = "mixed"
+    g, o, rg, ro = pair(case, 10)
+    t = o.cell_types()
+    fl = t == oracle.FLUID
+    Wg, _, _ = g.moments()
+    Wo, _ = o.moments()
+    for i in range(4):
+        if np.abs(Wo[fl, i]).max() > 1e-9:
+            assert rel_err(Wg[fl, i], Wo[fl, i]) < 1e-5, i
+    CDg = g.forces()[2]
+    CDo = o.forces()[2]
+    assert abs(CDg - CDo) < 1e-4 * abs(CDo)
+    assert rg == pytest.approx(ro, rel=1e-3)
+
+
+def test_state_roundtrip_and_errors():
+    case = wl.small_2d("circle", n=12, nv=6)
+    g = ibdvm.Solver(case)
+    o = oracle.OracleCase(case)
+    f0 = perturbed(o, 1)
+    g.set_f(f0)
+    np.testing.assert_array_equal(g.get_f(), f0)
+    with pytest.raises(ibdvm.IbdvmError) as e:
+        g.step(-1)
+    assert e.value.status == 1
+    # dt far beyond the relaxation time: forward Euler relaxation is refused
+    bad = dict(case)
+    bad["dt"] = 5.0
+    with pytest.raises(ibdvm.IbdvmError) as e:
+        ibdvm.Solver(bad)
+    assert e.value.status == 4
+
+
+def test_native_state_transfer():
+    torch = pytest.importorskip("torch")
+    case = wl.small_2d("circle", n=16, nv=8, precision="mixed")
+    g = ibdvm.Solver(case)
+    shp = g.native_shape()
+    buf = torch.empty(shp, dtype=torch.float32, pin_memory=True)
+    g.get_f_native(buf.data_ptr(), buf.numel() * 4)
+    f = g.get_f()
+    np.testing.assert_allclose(buf.numpy()[:, : g.nvel], f, rtol=1e-7)
+    buf.mul_(1.01)
+    g.set_f_native(buf.data_ptr(), buf.numel() * 4)
+    np.testing.assert_allclose(g.get_f(), buf.numpy()[:, : g.nvel].astype(np.float64), rtol=1e-7)
+
+
+def test_runs_on_a_torch_stream():
+    torch = pytest.importorskip("torch")
+    case = wl.small_2d("circle", n=16, nv=8)
+    s = torch.cuda.Stream()
+    g = ibdvm.Solver(case, stream=s.cuda_stream)
+    o = oracle.OracleCase(case)
+    g.step(2)
+    o.step(2)
+    compare(g, o)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads in the launch configuration the benchmark times:
+# properties that hold at any size (the oracle cannot run these sizes)
+# ---------------------------------------------------------------------------
+
+def _momentum_balance(g, steps=1):
+    W0, _, t = g.moments()
+    F, Q, _, _ = g.forces()
+    g.step(steps)
+    W1, _, _ = g.moments()
+    fl = t == ibdvm.FLUID
+    dV = np.prod([(g.case["hi"][a] - g.case["lo"][a]) / g.case["n"][a] for a in range(g.dim)])
+    dP = (W1[fl, 1:1 + g.dim] - W0[fl, 1:1 + g.dim]).sum(axis=0) * dV / g.dt
+    return dP, F[: g.dim], W1, t
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-7), ("mixed", 2e-2)])
+def test_cylinder_512_full_size_properties(precision, tol):
+    case = wl.cylinder_512(Kn=0.1, precision=precision)
+    g = ibdvm.Solver(case)
+    dP, F, W1, t = _momentum_balance(g)
+    # conservative face fluxes: the gas loses the momentum the body receives
+    np.testing.assert_allclose(dP, -F, rtol=tol, atol=tol * np.abs(F).max())
+    # mirror symmetry about y = 0
+    n = case["n"][0]
+    Wm = W1.reshape(n, n, -1)
+    sym = np.abs(Wm[::-1, :, 0] - Wm[:, :, 0]).max()
+    assert sym < (1e-12 if precision == "fp64" else 1e-5)
+    assert np.abs(Wm[::-1, :, 2] + Wm[:, :, 2]).max() < (1e-12 if precision == "fp64" else 1e-5)
+    # far from the body the freestream is untouched after one step
+    U = 0.5 * np.sqrt(5.0 / 6.0)
+    far = W1.reshape(n, n, -1)[:40, :40]
+    np.testing.assert_allclose(far[..., 0], 1.0, rtol=1e-5)
+    np.testing.assert_allclose(far[..., 1], U, rtol=1e-4)
+    g.close()
+
+
+def test_sphere_96_full_size_properties():
+    case = wl.sphere_96(precision="mixed")
+    g = ibdvm.Solver(case)
+    dP, F, W1, t = _momentum_balance(g)
+    np.testing.assert_allclose(dP, -F, rtol=3e-2, atol=3e-2 * np.abs(F).max())
+    n = case["n"][0]
+    Wm = W1.reshape(n, n, n, -1)
+    assert np.abs(Wm[:, ::-1, :, 0] - Wm[:, :, :, 0]).max() < 1e-5
+    assert np.abs(Wm[::-1, :, :, 0] - Wm[:, :, :, 0]).max() < 1e-5
+    g.close()
