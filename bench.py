@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    ap.add_argument("--cells", type=int, default=0,
+                    help="override the cells per axis (smaller cases for profiling captures)")
     return ap.parse_args()
 
 
@@ -211,6 +213,8 @@ def main():
     from paper_2512_20252_gb300 import ibdvm
 
     case = WORKLOADS[args.workload](args.precision)
+    if args.cells:
+        case["n"] = [args.cells] * case["dim"]
     stream = torch.cuda.Stream()
     solver = ibdvm.Solver(case, stream=stream.cuda_stream)
     info = solver.info
@@ -297,7 +301,8 @@ def main():
             "vs_baseline": None,
             "dtype": "f32" if esize == 4 else "f64",
             "data": "synthetic",
-            "config": {"workload": DESCRIPTIONS[args.workload], "precision": args.precision,
+            "config": {"workload": DESCRIPTIONS[args.workload] + (f" at {args.cells} cells per axis" if args.cells else ""),
+                       "precision": args.precision,
                        "cells": int(info.ncell), "fluid_cells": int(info.nfluid), "velocities": int(info.nvel),
                        "l2": f"inputs larger than L2 (f^n is {alg_bytes / 2 / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{world}"},
