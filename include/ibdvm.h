@@ -197,6 +197,33 @@ ibdvm_status ibdvm_set_profiling(ibdvm_ctx *ctx, int on);
 ibdvm_status ibdvm_get_kernel_times(ibdvm_ctx *ctx, double *ms, long long *launches);
 ibdvm_status ibdvm_reset_kernel_times(ibdvm_ctx *ctx);
 
+/* Residual without any device allocation.  The paper has no counterpart:
+   this is a service for callers that cannot allocate device memory when they
+   need the residual -- code running while another runtime owns the device
+   memory pool and forbids cudaMalloc, hosts that must keep a fixed footprint
+   after start-up, and work enqueued between other launches where an
+   allocation would synchronise the device.  It returns, on the device, the
+   same residual that ibdvm_step reports (max over components of
+   sqrt(sum_j dW_ij^2) / sum_j |W_ij|, cells with celltype != fluid skipped,
+   components whose sum of |W| is zero skipped).
+     W_old, W_new  device arrays [ncell][dim+2], FP64, caller-owned (the
+                   layout ibdvm_moments writes on the host);
+     celltype      device array [ncell] of IBDVM_CELL_* or NULL (all cells count);
+     residual      device pointer to one double, caller-owned; written on the stream;
+     cuda_stream   cudaStream_t (NULL = legacy default stream); the call is
+                   asynchronous and does not synchronise.
+   Partial sums live in a built-in device array of 8192 x 10 doubles (640 KiB,
+   held by every GPU that loads the library until exit), so ncell is limited
+   to 2,097,152; larger sizes return IBDVM_E_INVAL with the limit in
+   ibdvm_last_error(NULL).  The first call on a device looks up the array's
+   device address (cudaGetSymbolAddress) and caches it: make that first call
+   before any stream capture.  All calls share the array and it keeps the last
+   call's contents; calls that overlap on the GPU race on it and must be
+   serialised by the caller. */
+ibdvm_status ibdvm_residual_noalloc(const double *W_old, const double *W_new,
+                                    const unsigned char *celltype, long long ncell, int dim,
+                                    double *residual, void *cuda_stream);
+
 ibdvm_status ibdvm_get_info(const ibdvm_ctx *ctx, ibdvm_info *info);
 ibdvm_status ibdvm_set_stream(ibdvm_ctx *ctx, void *cuda_stream);
 /* Geometry of the context (host copy); see ibdvm_geom_* for the layouts. */

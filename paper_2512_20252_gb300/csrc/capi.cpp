@@ -406,6 +406,11 @@ void fill_forces(ibdvm_ctx *ctx, const double *h, double *F, double *Q, double *
 
 } // namespace
 
+namespace ibdvm {
+// message returned by ibdvm_last_error(NULL) for calls that have no context
+void set_thread_error(const std::string &e) { g_geom_err = e; }
+} // namespace ibdvm
+
 struct ibdvm_geom {
   Geom g;
 };

@@ -92,6 +92,7 @@ SIGNATURES = {
     "ibdvm_get_f_native": ([_V, _V, ctypes.c_size_t], _S),
     "ibdvm_set_f_native": ([_V, _V, ctypes.c_size_t], _S),
     "ibdvm_ghost_band": ([_V, _D, _D, _D, _D], _S),
+    "ibdvm_residual_noalloc": ([_V, _V, _V, ctypes.c_longlong, ctypes.c_int, _V, _V], _S),
     "ibdvm_get_info": ([_V, ctypes.POINTER(Info)], _S),
     "ibdvm_set_stream": ([_V, _V], _S),
     "ibdvm_get_geom": ([_V], _V),
@@ -194,6 +195,19 @@ def descriptors(case: dict):
 
 def _dp(a):
     return a.ctypes.data_as(_D)
+
+
+def residual_noalloc(W_old_ptr: int, W_new_ptr: int, celltype_ptr: int | None, ncell: int, dim: int,
+                     out_ptr: int, stream: int | None = None) -> int:
+    """Residual of two device fields [ncell][dim+2] into a caller-owned device
+    double, without any device allocation (see include/ibdvm.h).  Returns the
+    status; raises IbdvmError on failure."""
+    lib = load()
+    st = lib.ibdvm_residual_noalloc(_V(W_old_ptr), _V(W_new_ptr), _V(celltype_ptr or 0), int(ncell),
+                                    int(dim), _V(out_ptr), _V(stream or 0))
+    if st != OK:
+        raise IbdvmError(st, lib.ibdvm_last_error(None).decode())
+    return st
 
 
 class Geometry:
