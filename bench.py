@@ -121,6 +121,32 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+SWEEP_KERNELS = {0: ("sweep_kernel", "paper_2512_20252_gb300/csrc/kernels.cu"),
+                 1: ("sweep2d_tma_kernel", "paper_2512_20252_gb300/csrc/sweep_tma.cu")}
+
+
+def profiled_traffic(kernel: str, source: str, pairs: int):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary (profiles/<kernel>_*.md, measured on a smaller case and scaled by
+    the pairs processed), or None when the kernel source changed since."""
+    import glob
+    import hashlib
+
+    try:
+        sha = hashlib.sha1(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    for path in glob.glob(os.path.join(ROOT, "profiles", kernel + "_*.md")):
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_pair", "source_sha1"):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("source_sha1") == sha and "traffic_bytes_per_pair" in fields:
+            return float(fields["traffic_bytes_per_pair"]) * pairs
+    return None
+
+
 def dist_setup(nprocs: int):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -250,6 +276,7 @@ def main():
     total_pairs = pairs * args.steps * world
     value = total_pairs / (elapsed_ms / 1e3)
     sweep_ms, sweep_n = kt["sweep"]
+    kname, ksrc = SWEEP_KERNELS.get(int(info.sweep_variant), SWEEP_KERNELS[0])
     alg_bytes = pairs * ncomp * esize * 2  # read f^n, write f^{n+1}
     peak, peak_kind = peaks()
     achieved = alg_bytes / (sweep_ms / sweep_n / 1e3) / 1e9 if sweep_n else None
@@ -307,8 +334,9 @@ def main():
                        "l2": f"inputs larger than L2 (f^n is {alg_bytes / 2 / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
-                         "kernel": "sweep_kernel", "peak_kind": peak_kind,
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": profiled_traffic(kname, ksrc, pairs),
+                         "kernel": kname, "peak_kind": peak_kind,
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms / max(sweep_n, 1)},
             "kernel_ms": {k: v[0] for k, v in kt.items()},
             "gpu_launches": launches,

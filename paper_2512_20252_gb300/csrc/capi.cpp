@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -119,6 +120,8 @@ void free_all(ibdvm_ctx *ctx) {
   cfree_t(ctx->xiD);
   cfree_t(ctx->wD);
   cfree_t(ctx->ctype);
+  cfree_t(ctx->cmask);
+  cfree_t(ctx->partf);
   cfree_t(ctx->d_forces);
   cfree_t(ctx->d_step_forces);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -227,6 +230,24 @@ void upload_body(ibdvm_ctx *ctx) {
     }
   }
   std::vector<uint8_t> ctype(G.type.begin(), G.type.end());
+  // per-cell flags of the sweeps: a ghost across face (a, s) sets bit 2a + (s > 0)
+  std::vector<uint8_t> cmask(G.ncell, 0);
+  for (long long c = 0; c < G.ncell; ++c) {
+    if (G.type[c] != IBDVM_CELL_FLUID) {
+      cmask[c] = 64;
+      continue;
+    }
+    int ijk[3];
+    ijk_of(c, ijk);
+    for (int a = 0; a < D; ++a)
+      for (int s = 0; s < 2; ++s) {
+        int q[3] = {ijk[0], ijk[1], ijk[2]};
+        q[a] += s ? 1 : -1;
+        if (q[a] < 0 || q[a] >= G.n[a]) continue;
+        long long nb = q[0] + G.n[0] * (q[1] + static_cast<long long>(G.n[1]) * q[2]);
+        if (G.type[nb] == IBDVM_CELL_GHOST) cmask[c] |= static_cast<uint8_t>(1u << (2 * a + s));
+      }
+  }
   // allocate the new band first, so that a failure leaves the old one intact
   ibdvm_ctx tmp;
   tmp.stream = ctx->stream;
@@ -277,6 +298,7 @@ void upload_body(ibdvm_ctx *ctx) {
   upload(ctx, ctx->s_int, s_int, "upload surface table");
   upload(ctx, ctx->s_dbl, s_dbl, "upload surface vectors");
   upload(ctx, ctx->ctype, ctype, "upload cell classes");
+  upload(ctx, ctx->cmask, cmask, "upload cell flags");
   if (nl) {
     const size_t band = nl * static_cast<size_t>(nvp) * ctx->ncomp * ctx->esize;
     check(ctx, cudaMemsetAsync(ctx->lval, 0, band, ctx->stream), "clear ghost values");
@@ -302,6 +324,10 @@ int read_flags(ibdvm_ctx *ctx) {
 }
 
 ibdvm_status status_of_flags(ibdvm_ctx *ctx, int fl) {
+  if (fl & kFlagTimeout) {
+    ctx->err = "a bounded device wait in the sweep gave up (TMA copy did not arrive)";
+    return IBDVM_E_TIMEOUT;
+  }
   if (fl & kFlagNonFinite) {
     ctx->err = "non-finite or non-positive density/temperature in the moments";
     return IBDVM_E_NONFINITE;
@@ -465,7 +491,8 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     const int NM = nmoments(G.dim);
     // memory check before allocating
     const size_t fbytes = static_cast<size_t>(ctx->ncell) * ctx->nvp * ctx->ncomp * ctx->esize;
-    const size_t need = 2 * fbytes + static_cast<size_t>(ctx->ncell) *
+    const size_t need = 2 * fbytes + static_cast<size_t>(ctx->ncell) * (G.dim == 2 ? 40 * 9 : 0) +
+                        static_cast<size_t>(ctx->ncell) *
                                          (kMac * ctx->esize + 2 * (NW + G.dim) * 8 + ctx->nchunk * NM * 8 + 8);
     int dev = 0;
     check(ctx, cudaGetDevice(&dev), "cudaGetDevice");
@@ -489,6 +516,16 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     ctx->d_step_forces = dalloc<double>(ctx, 4, "step forces");
     check(ctx, cudaMemsetAsync(ctx->d_step_forces, 0, 4 * sizeof(double), ctx->stream), "clear");
     ctx->ctype = dalloc<uint8_t>(ctx, ctx->ncell, "cell classes");
+    ctx->cmask = dalloc<uint8_t>(ctx, ctx->ncell, "cell flags");
+    // the TMA sweep for 2D FP32 cases (IBDVM_NO_TMA=1 keeps the plain sweep)
+    const char *no_tma = std::getenv("IBDVM_NO_TMA");
+    if (tma_sweep_applicable(ctx) && !(no_tma && no_tma[0] == '1')) {
+      ctx->tma_nchunk = tma_sweep_nchunk(ctx);
+      ctx->partf = dalloc<float>(ctx, static_cast<size_t>(ctx->tma_nchunk) * nmoments(G.dim) * ctx->ncell,
+                                 "FP32 moment sums");
+      check(ctx, tma_sweep_prepare(ctx), "TMA sweep set-up");
+      ctx->use_tma = true;
+    }
     // velocity tables
     std::vector<double> xi3(3 * static_cast<size_t>(ctx->nvp), 0.0), w(ctx->nvp, 0.0);
     for (int k = 0; k < G.nv; ++k) {
@@ -776,6 +813,7 @@ ibdvm_status ibdvm_get_info(const ibdvm_ctx *ctx, ibdvm_info *info) {
   info->precision = ctx->precision;
   info->steps_done = ctx->steps;
   info->device_bytes = ctx->dev_bytes;
+  info->sweep_variant = ctx->use_tma ? 1 : 0;
   return IBDVM_OK;
 }
 

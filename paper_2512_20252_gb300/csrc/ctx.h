@@ -12,8 +12,9 @@
 
 namespace ibdvm {
 
-// Per-cell macroscopic slots (array of [kMac][ncell] in the storage type):
-// the Shakhov equilibrium parameters of the current state (Sec. 2.1, Sec. 4).
+// Per-cell macroscopic slots (array of [ncell][kMac] in the storage type, so a
+// cell's parameters are three aligned 16-byte vectors in FP32): the Shakhov
+// equilibrium parameters of the current state (Sec. 2.1, Sec. 4).
 enum MacSlot {
   kPre = 0,    // rho / (pi T)      (2D reduced)  or rho / (pi T)^{3/2}  (3D)
   kU0 = 1,     // U_x, U_y, U_z
@@ -29,7 +30,7 @@ enum MacSlot {
 enum KernelClass { kKGhost = 0, kKSweep = 1, kKMoments = 2, kKForces = 3, kKOther = 4 };
 
 // flags written by the moment kernel
-enum : int { kFlagNonFinite = 1, kFlagUnstable = 2 };
+enum : int { kFlagNonFinite = 1, kFlagUnstable = 2, kFlagTimeout = 4 };
 
 } // namespace ibdvm
 
@@ -56,7 +57,13 @@ struct ibdvm_ctx {
   double *xiD = nullptr, *wD = nullptr;
   // cell tables
   uint8_t *ctype = nullptr;
+  uint8_t *cmask = nullptr;  // per cell: ghost neighbour per face (bit 2a + (s > 0)), 64 = not fluid
   int *dslot = nullptr, *dlinks = nullptr;
+  // TMA sweep of 2D FP32 cases (sweep_tma.cu)
+  bool use_tma = false;
+  float *partf = nullptr;    // FP32 moment partial sums [nchunk][9][ncell]
+  int tma_nchunk = 0;
+  alignas(64) unsigned char tmap[2][128];
   // ghost band
   int nlink = 0, nghost = 0, nsurf = 0;
   int *l_int = nullptr;      // [nlink][8]
@@ -94,6 +101,12 @@ cudaError_t launch_moments(ibdvm_ctx *ctx, bool shift, bool residual);
 cudaError_t launch_ghost_band(ibdvm_ctx *ctx, double *dbg_fstarw);
 cudaError_t launch_sweep(ibdvm_ctx *ctx);
 cudaError_t launch_forces(ibdvm_ctx *ctx, double *dst);
+// TMA sweep (sweep_tma.cu)
+bool tma_sweep_applicable(const ibdvm_ctx *ctx);
+int tma_sweep_nchunk(const ibdvm_ctx *ctx);
+cudaError_t tma_sweep_prepare(ibdvm_ctx *ctx);
+cudaError_t tma_sweep_launch(ibdvm_ctx *ctx);
+
 // dense FP64 [ncells][nv][ncomp] (device) <-> cells [c0, c0 + ncells) of the current state
 cudaError_t launch_convert(ibdvm_ctx *ctx, double *dense, long long c0, long long ncells, bool to_state);
 

@@ -173,11 +173,11 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
     T U[3], q[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      U[a] = A.shift ? M[(kU0 + a) * nc + c] : T(0);
-      q[a] = M[(kQ0 + a) * nc + c];
+      U[a] = A.shift ? M[c * kMac + kU0 + a] : T(0);
+      q[a] = M[c * kMac + kQ0 + a];
     }
-    const T pre = M[kPre * nc + c], invT = M[kInvT * nc + c], halfT = M[kHalfT * nc + c];
-    const T shA = M[kShA * nc + c], dtau = M[kDtTau * nc + c];
+    const T pre = M[c * kMac + kPre], invT = M[c * kMac + kInvT], halfT = M[c * kMac + kHalfT];
+    const T shA = M[c * kMac + kShA], dtau = M[c * kMac + kDtTau];
     for (int j = 0; j < A.kloop; ++j) {
       const int k = (chunk * A.kloop + j) * kThreadsPerCell + tx;
       if (k >= A.nv) break;
@@ -313,8 +313,8 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
 // moments -> macroscopic state, Shakhov parameters, residual partial sums
 // ---------------------------------------------------------------------------
 
-template <typename T> struct FinalArgs {
-  const double *__restrict__ part;
+template <typename T, typename P = double> struct FinalArgs {
+  const P *__restrict__ part;
   T *__restrict__ mac;
   const double *__restrict__ Wold; // [NW][ncell], may be null
   double *__restrict__ Wnew;
@@ -327,8 +327,8 @@ template <typename T> struct FinalArgs {
   double mu0, omega, Pr, dt;
 };
 
-template <typename T, int D>
-__global__ void __launch_bounds__(256) finalize_kernel(FinalArgs<T> A) {
+template <typename T, int D, typename P>
+__global__ void __launch_bounds__(256) finalize_kernel(FinalArgs<T, P> A) {
   constexpr int NM = Dims<D>::NM;
   constexpr int NW = Dims<D>::NW;
   __shared__ double red[2 * NW][8];
@@ -342,11 +342,11 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs<T> A) {
     for (int m = 0; m < NM; ++m) M[m] = 0.0;
     for (int ch = 0; ch < A.nchunk; ++ch)
 #pragma unroll
-      for (int m = 0; m < NM; ++m) M[m] += A.part[((size_t)ch * NM + m) * A.ncell + c];
+      for (int m = 0; m < NM; ++m) M[m] += (double)A.part[((size_t)ch * NM + m) * A.ncell + c];
     const long long nc = A.ncell;
     double V[3] = {0.0, 0.0, 0.0};
     if (A.shift)
-      for (int a = 0; a < D; ++a) V[a] = (double)A.mac[(kU0 + a) * nc + c];
+      for (int a = 0; a < D; ++a) V[a] = (double)A.mac[c * kMac + kU0 + a];
     const double rho = M[0];
     double M1[3] = {0, 0, 0}, d[3] = {0, 0, 0}, d2 = 0.0, VM1 = 0.0, V2 = 0.0;
     for (int a = 0; a < D; ++a) {
@@ -389,15 +389,15 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs<T> A) {
     if (bad) atomicOr(A.flags, kFlagNonFinite);
     if (dtau > 1.0) atomicOr(A.flags, kFlagUnstable);
     T *Mc = A.mac;
-    Mc[kPre * nc + c] = (T)((D == 2) ? rho / (kPi * T_) : rho / pow(kPi * T_, 1.5));
+    Mc[c * kMac + kPre] = (T)((D == 2) ? rho / (kPi * T_) : rho / pow(kPi * T_, 1.5));
     for (int a = 0; a < 3; ++a) {
-      Mc[(kU0 + a) * nc + c] = (T)((a < D) ? V[a] + d[a] : 0.0);
-      Mc[(kQ0 + a) * nc + c] = (T)((a < D) ? q[a] : 0.0);
+      Mc[c * kMac + kU0 + a] = (T)((a < D) ? V[a] + d[a] : 0.0);
+      Mc[c * kMac + kQ0 + a] = (T)((a < D) ? q[a] : 0.0);
     }
-    Mc[kInvT * nc + c] = (T)(1.0 / T_);
-    Mc[kHalfT * nc + c] = (T)(0.5 * T_);
-    Mc[kShA * nc + c] = (T)(4.0 * (1.0 - A.Pr) / (5.0 * rho * T_ * T_));
-    Mc[kDtTau * nc + c] = (T)dtau;
+    Mc[c * kMac + kInvT] = (T)(1.0 / T_);
+    Mc[c * kMac + kHalfT] = (T)(0.5 * T_);
+    Mc[c * kMac + kShA] = (T)(4.0 * (1.0 - A.Pr) / (5.0 * rho * T_ * T_));
+    Mc[c * kMac + kDtTau] = (T)dtau;
     for (int a = 0; a < D; ++a) A.Wnew[(NW + a) * nc + c] = q[a];
     for (int i = 0; i < NW; ++i) {
       A.Wnew[i * nc + c] = Wn[i];
@@ -848,9 +848,13 @@ template <typename T, int D> cudaError_t sweep_t(ibdvm_ctx *ctx, int update, int
   return cudaGetLastError();
 }
 
-template <typename T, int D> cudaError_t finalize_t(ibdvm_ctx *ctx, bool shift, bool residual) {
-  FinalArgs<T> A{};
-  A.part = ctx->part;
+template <typename T, int D, typename P = double>
+cudaError_t finalize_t(ibdvm_ctx *ctx, bool shift, bool residual, const P *part = nullptr, int nchunk = 0) {
+  FinalArgs<T, P> A{};
+  if constexpr (std::is_same<P, double>::value)
+    A.part = part ? part : ctx->part;
+  else
+    A.part = part;
   A.mac = static_cast<T *>(ctx->mac);
   A.Wold = residual ? ctx->W[ctx->wcur] : nullptr;
   A.Wnew = ctx->W[1 - ctx->wcur];
@@ -858,14 +862,14 @@ template <typename T, int D> cudaError_t finalize_t(ibdvm_ctx *ctx, bool shift, 
   A.resblk = residual ? ctx->resblk : nullptr;
   A.flags = ctx->d_flags;
   A.ncell = ctx->ncell;
-  A.nchunk = ctx->nchunk;
+  A.nchunk = nchunk ? nchunk : ctx->nchunk;
   A.shift = shift ? 1 : 0;
   A.mu0 = ctx->geom.mu0;
   A.omega = ctx->geom.gas.omega_vhs;
   A.Pr = ctx->geom.gas.Pr;
   A.dt = ctx->geom.dt;
   const int nblk = (int)((ctx->ncell + 255) / 256);
-  finalize_kernel<T, D><<<nblk, 256, 0, ctx->stream>>>(A);
+  finalize_kernel<T, D, P><<<nblk, 256, 0, ctx->stream>>>(A);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (residual) {
@@ -1014,15 +1018,17 @@ cudaError_t launch_sweep(ibdvm_ctx *ctx) {
     using T = decltype(t);
     constexpr int D = decltype(d)::value;
     cudaError_t e;
+    const bool tma = std::is_same<T, float>::value && D == 2 && ctx->use_tma;
     {
       Timed tm(ctx, kKSweep);
       ctx->kernel_launches[kKSweep] += 1;
-      e = sweep_t<T, D>(ctx, 1, 1);
+      e = tma ? tma_sweep_launch(ctx) : sweep_t<T, D>(ctx, 1, 1);
     }
     if (e != cudaSuccess) return e;
     ctx->cur = 1 - ctx->cur;
     Timed tm(ctx, kKMoments);
     ctx->kernel_launches[kKMoments] += 2;
+    if (tma) return finalize_t<T, D, float>(ctx, true, true, ctx->partf, ctx->tma_nchunk);
     return finalize_t<T, D>(ctx, true, true);
   });
 }

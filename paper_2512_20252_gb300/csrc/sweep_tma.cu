@@ -1,0 +1,615 @@
+// sweep_tma.cu -- the transport / relaxation / moments sweep of 2D cases in
+// FP32 storage (the mixed path), staged through shared memory by TMA.
+//
+// Same arithmetic as sweep_kernel in kernels.cu (Sec. 2.2 Eqs. reconstruction
+// and limiter, Sec. 4 reduced Shakhov equilibria, forward Euler, Eqs.
+// moments1-3 by quadrature), organised for GB300:
+//
+//   * a block owns TX = 8 columns of cells (one warp per column), a chunk of
+//     KC = 32 * KPT velocities (lane l owns velocities l, l + 32, ..., so every
+//     shared-memory access of a warp is 256 contiguous bytes), and marches up
+//     a range of rows;
+//   * every row of the block (its TX columns plus two halo columns on each
+//     side, all KC velocities) arrives in shared memory by one TMA tensor copy
+//     (cp.async.bulk.tensor.3d) into a ring of NST stages guarded by
+//     mbarriers, issued NST - 3 rows ahead, so HBM is read once per row and
+//     the x stencil comes from shared memory;
+//   * each lane keeps its column's y stencil in registers (f at rows y..y+2
+//     and the reconstructed faces of rows y-1..y+1); the row loop is unrolled
+//     three times so that the ring rotates by renaming, without moves;
+//   * x faces are exchanged through shared memory: every warp publishes the
+//     face value of its own cell on the downwind side and reads its upwind
+//     neighbour's as the inflow face; the faces of the two halo columns are
+//     spread over all threads of the block (one velocity each);
+//   * the nine moment sums of the new state (about the stored bulk velocity)
+//     are reduced over the 32 lanes by a butterfly (each shuffle round halves
+//     the values a lane holds) and written as FP32 partial sums per velocity
+//     chunk; the finalize kernel adds the chunks in FP64.
+//
+// Conditions that are the same for a whole warp (a ghost neighbour, the
+// domain edge, a cell that is not fluid) select between a fast path and a
+// general path per warp, never per velocity.  Every mbarrier wait is bounded:
+// on timeout the block sets an error flag, drains its copies (bounded) and
+// returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+
+#include "ctx.h"
+
+namespace ibdvm {
+namespace {
+
+constexpr int TX = 8;       // interior columns per block, one warp each
+constexpr int NST = 6;      // TMA row stages
+constexpr int COLS = TX + 4;
+constexpr int NTHREADS = TX * 32;
+constexpr int NM = 9;       // moment sums (2D)
+constexpr long kSpinLimit = 1L << 22; // bounded mbarrier waits
+
+template <int KPT> struct Cfg {
+  static constexpr int KC = 32 * KPT;
+  static constexpr int KC2 = 2 * KC; // floats of one column in a staged row
+  static constexpr int STAGE_FLOATS = COLS * KC2;
+  static constexpr int STAGE_BYTES = STAGE_FLOATS * 4;
+  static constexpr int PHI_FLOATS = (TX + 2) * KC2;
+  static constexpr size_t SMEM = (size_t)(NST * STAGE_FLOATS + 2 * PHI_FLOATS + KC2 + KC + 2 * TX * kMac) * 4 + NST * 8;
+};
+
+struct TmaArgs {
+  float *__restrict__ fn;
+  const float *__restrict__ f;
+  const float *__restrict__ mac;  // [ncell][kMac]
+  const float *__restrict__ xi;   // [3][nvp]
+  const float *__restrict__ w;    // [nvp]
+  const float *__restrict__ finf; // [nvp][2]
+  const uint8_t *__restrict__ cmask;
+  const int *__restrict__ dslot;
+  const int *__restrict__ dlinks;
+  const float *__restrict__ lval; // [nlink][nvp][2]
+  float *__restrict__ part;       // [nchunk][NM][ncell]
+  int *__restrict__ err;
+  long long ncell;
+  int nx, ny, nvp, nv, rows;
+  float dt, rdx, rdy;
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_row(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false after kSpinLimit polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+  if (mbar_try(bar, parity)) return true;
+  for (long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Half the van Leer slope times the cell width for the (h, b) pair, from the
+// one-sided differences a = f - f_lo and b = f_hi - f (Eq. limiter):
+// ab / (a + b) where a and b have the same sign, 0 otherwise.  Packed FP32
+// arithmetic on both components at once.
+__device__ __forceinline__ float2 vl_half2(float2 a, float2 b) {
+  const float2 p = __fmul2_rn(a, b);
+  const float2 s = __fadd2_rn(a, b);
+  const float2 v = __fmul2_rn(p, make_float2(rcp_approx(s.x), rcp_approx(s.y)));
+  return make_float2(p.x > 0.f ? v.x : 0.f, p.y > 0.f ? v.y : 0.f);
+}
+__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
+// x - y for packed pairs, as one packed FMA
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+// reconstructed face on the downwind side when up / dn are the upwind and
+// downwind neighbours: f + half slope in the direction of motion
+__device__ __forceinline__ float2 face_dir(float2 f, float2 up, float2 dn) {
+  return __fadd2_rn(f, vl_half2(sub2(f, up), sub2(dn, f)));
+}
+// the same with lo / hi neighbours and the packed sign s2 = (s, s) of the velocity
+__device__ __forceinline__ float2 face2(float2 f, float2 lo, float2 hi, float2 s2) {
+  return __ffma2_rn(s2, vl_half2(sub2(f, lo), sub2(hi, f)), f);
+}
+
+__device__ __forceinline__ float2 link_value(const TmaArgs &A, long long c, int dir, int k) {
+  const int slot = A.dslot[c];
+  const int l = (slot >= 0) ? A.dlinks[slot * 6 + dir] : -1;
+  const float *p = (l >= 0) ? A.lval + ((size_t)l * A.nvp + k) * 2 : A.finf + (size_t)k * 2;
+  return make_float2(p[0], p[1]);
+}
+
+enum : uint8_t { kXm = 1, kXp = 2, kYm = 4, kYp = 8, kNotFluid = 64, kGhostAny = 15 };
+
+template <int KPT> using Ring = float2[KPT];
+
+// Shared state of one block's march, passed to the per-row body.
+template <int KPT> struct March {
+  const TmaArgs &A;
+  const CUtensorMap *tm;
+  float *stage, *phix, *sfinf, *sxi;
+  uint64_t *full;
+  int warp, lane, x0, x, k0, y0, y1, ylast;
+  int st;       // stage of row y
+  unsigned pb;  // parity of that stage's current use
+  bool col_in;
+  long long nc;
+  float xix[KPT], xiy[KPT], wk[KPT];
+  float2 ax2[KPT], ay2[KPT]; // dt |xi_a| / dx_a, packed for (h, b)
+  float2 sy2[KPT];           // sign of xi_y, packed
+  float *smac;               // [2][TX][kMac]: cell parameters of rows y and y + 1
+  float pre_mac;             // lanes 0..kMac-1: one parameter of the next row's cell
+  uint8_t mask_next2;        // flags of (x, y + 2)
+  bool abort_local;
+};
+
+// velocity q of a lane: k = k0 + lane + 32 q, so a warp touches 32 consecutive
+// (h, b) pairs per access (256 contiguous bytes, no bank conflicts)
+template <int KPT> __device__ __forceinline__ int klo(const March<KPT> &M, int q) { return M.lane + 32 * q; }
+template <int KPT> __device__ __forceinline__ int kof(const March<KPT> &M, int q) { return M.k0 + klo(M, q); }
+
+template <int KPT> __device__ __forceinline__ float2 sm2(const float *base, int kk) {
+  return *reinterpret_cast<const float2 *>(base + 2 * kk);
+}
+
+template <int KPT> __device__ __forceinline__ void issue_row(March<KPT> &M, int r, int st) {
+  using C = Cfg<KPT>;
+  mbar_expect_tx(&M.full[st], C::STAGE_BYTES);
+  tma_row(M.stage + st * C::STAGE_FLOATS, M.tm, 2 * M.k0, M.x0 - 2, r, &M.full[st]);
+}
+
+template <int KPT> __device__ __forceinline__ uint8_t cmask_of(const March<KPT> &M, int cx, int r) {
+  if (cx < 0 || cx >= M.A.nx || r < 0 || r >= M.A.ny) return 0;
+  return M.A.cmask[cx + (long long)M.A.nx * r];
+}
+
+// downwind x face of column cx at row y for chunk velocity kk, with the
+// domain edge, ghost neighbours and cells that are not fluid
+template <int KPT>
+__device__ __forceinline__ float2 phi_x_one(const March<KPT> &M, const float *srow, int cx, int scol, int y,
+                                            uint8_t m, int kk, float xi) {
+  using C = Cfg<KPT>;
+  if (cx < 0 || cx >= M.A.nx) return sm2<KPT>(M.sfinf, kk); // halo column: freestream, zero slope
+  if (m & kNotFluid) return make_float2(0.f, 0.f);
+  const float *pc = srow + scol * C::KC2;
+  const float2 f = sm2<KPT>(pc, kk);
+  float2 lo = (cx - 1 < 0) ? sm2<KPT>(M.sfinf, kk) : sm2<KPT>(pc - C::KC2, kk);
+  float2 hi = (cx + 1 >= M.A.nx) ? sm2<KPT>(M.sfinf, kk) : sm2<KPT>(pc + C::KC2, kk);
+  if (m & (kXm | kXp)) {
+    const long long c = cx + (long long)M.A.nx * y;
+    if (m & kXm) lo = link_value(M.A, c, 0, M.k0 + kk);
+    if (m & kXp) hi = link_value(M.A, c, 1, M.k0 + kk);
+  }
+  return face2(f, lo, hi, dup(copysignf(1.f, xi)));
+}
+
+// downwind y face of row r, cell (x, r): fr = f(r), lo = f(r-1), hi = f(r+1)
+template <int KPT>
+__device__ __forceinline__ void phi_y(const March<KPT> &M, int r, uint8_t m, const Ring<KPT> &fr,
+                                      const Ring<KPT> &lo, const Ring<KPT> &hi, Ring<KPT> &out) {
+  if (r < 0 || r >= M.A.ny || !M.col_in) { // halo row: freestream, zero slope
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) out[q] = sm2<KPT>(M.sfinf, klo(M, q));
+    return;
+  }
+  if (m & kNotFluid) {
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) out[q] = make_float2(0.f, 0.f);
+    return;
+  }
+  if (!(m & (kYm | kYp))) { // fast path
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) out[q] = face2(fr[q], lo[q], hi[q], M.sy2[q]);
+    return;
+  }
+  const long long c = M.x + (long long)M.A.nx * r;
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) {
+    const float2 l = (m & kYm) ? link_value(M.A, c, 2, kof(M, q)) : lo[q];
+    const float2 h = (m & kYp) ? link_value(M.A, c, 3, kof(M, q)) : hi[q];
+    out[q] = face2(fr[q], l, h, M.sy2[q]);
+  }
+}
+
+// One row y of the march.  Ring arguments: Ra = f(y), Rb = f(y+1), Rc <- f(y+2);
+// Pa = phi(y-1), Pb = phi(y), Pc <- phi(y+1); mc = flags of (x, y), carried to
+// the next row as the flags of (x, y+1).  Returns false when the block aborts.
+template <int KPT>
+__device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, Ring<KPT> &Ra, Ring<KPT> &Rb,
+                                    Ring<KPT> &Rc, Ring<KPT> &Pa, Ring<KPT> &Pb, Ring<KPT> &Pc) {
+  using C = Cfg<KPT>;
+  const TmaArgs &A = M.A;
+  const long long cell = M.x + (long long)A.nx * y;
+  const uint8_t m0 = mc;
+  const bool fluid = !(m0 & kNotFluid);
+  // prefetch for the next row: one cell parameter per lane, the flags of (x, y + 3);
+  // this row's parameters were staged in shared memory by the previous row
+  const float pre_next = (M.lane < kMac && M.col_in && y + 1 < A.ny)
+                             ? __ldg(A.mac + (cell + A.nx) * kMac + M.lane) : 0.f;
+  const uint8_t mn = M.mask_next2; // flags of (x, y + 1), loaded a row ahead
+  const uint8_t mn3 = M.col_in ? ((y + 2 < A.ny) ? cmask_of(M, M.x, y + 2) : 0) : kNotFluid;
+  // stages of rows y and y + 2
+  const int st = M.st;
+  int st2 = st + 2;
+  unsigned pb2 = M.pb;
+  if (st2 >= NST) {
+    st2 -= NST;
+    pb2 ^= 1u;
+  }
+  // (1) own column of row y + 2 (the y stencil)
+  if (y + 2 < A.ny && !mbar_wait(&M.full[st2], pb2)) M.abort_local = true;
+  if (y + 2 < A.ny && M.col_in) {
+    const float *src = M.stage + st2 * C::STAGE_FLOATS + (M.warp + 2) * C::KC2;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) Rc[q] = sm2<KPT>(src, klo(M, q));
+  } else {
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) Rc[q] = sm2<KPT>(M.sfinf, klo(M, q));
+  }
+  const float *srow = M.stage + st * C::STAGE_FLOATS; // row y, [COLS][KC][2]
+  float *ph = M.phix + par * C::PHI_FLOATS;            // [TX + 2][KC][2]
+  // (2) downwind x face of the own cell
+  Ring<KPT> PX;
+  if (M.col_in && fluid && !(m0 & (kXm | kXp)) && M.x > 0 && M.x + 1 < A.nx) {
+    const float *pc = srow + (M.warp + 2) * C::KC2;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int o = (M.xix[q] >= 0.f) ? C::KC2 : -C::KC2; // toward the downwind neighbour
+      PX[q] = face_dir(Ra[q], sm2<KPT>(pc - o, klo(M, q)), sm2<KPT>(pc + o, klo(M, q)));
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < KPT; ++q)
+      PX[q] = phi_x_one(M, srow, M.x, M.warp + 2, y, M.col_in ? m0 : 0, klo(M, q), M.xix[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) *reinterpret_cast<float2 *>(ph + (M.warp + 1) * C::KC2 + 2 * klo(M, q)) = PX[q];
+  // the halo column that is upwind of the block for each velocity: x0 - 1
+  // for xi_x >= 0, x0 + TX otherwise; one velocity per thread
+  for (int kk = threadIdx.x; kk < C::KC; kk += NTHREADS) {
+    const float xi = M.sxi[kk];
+    const bool left = xi >= 0.f;
+    const int hc = left ? M.x0 - 1 : M.x0 + TX;
+    const float2 o = phi_x_one(M, srow, hc, left ? 1 : TX + 2, y, cmask_of(M, hc, y), kk, xi);
+    *reinterpret_cast<float2 *>(ph + (left ? 0 : TX + 1) * C::KC2 + 2 * kk) = o;
+  }
+  // (3) downwind y face of row y + 1
+  phi_y(M, y + 1, mn, Rb, Ra, Rc, Pc);
+  // (4) barrier: x faces published, the stage of row y - 1 released; all
+  //     threads agree on an abort
+  if (__syncthreads_or(M.abort_local ? 1 : 0)) return false;
+  if (threadIdx.x == 0 && y + NST - 1 < M.ylast) {
+    fence_proxy_async();
+    issue_row(M, y + NST - 1, st == 0 ? NST - 1 : st - 1);
+  }
+  // (5) update of the own cell and its moment sums
+  float2 a03 = make_float2(0.f, 0.f), a17 = a03, a28 = a03, a45 = a03;
+  float a6 = 0.f;
+  if (fluid) {
+    const float4 *pm = reinterpret_cast<const float4 *>(M.smac + (par * TX + M.warp) * kMac);
+    const float4 p0 = pm[0], p1 = pm[1], p2 = pm[2];
+    const float pre = p0.x, U0 = p0.y, U1 = p0.z;
+    const float invT = p1.x, halfT = p1.y, shA = p1.z, q0 = p1.w;
+    const float q1 = p2.x, dtau = p2.z;
+    const float Tc = 2.f * halfT;
+    const float2 omd = dup(1.f - dtau), dt2 = dup(dtau);
+    const bool ghosty = (m0 & kGhostAny) != 0;
+    Ring<KPT> out;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      // inflow faces: the upwind neighbour's downwind face
+      const bool posx = M.xix[q] >= 0.f, posy = M.xiy[q] >= 0.f;
+      float2 ix = sm2<KPT>(ph + (M.warp + (posx ? 0 : 2)) * C::KC2, klo(M, q));
+      float2 iy = posy ? Pa[q] : Pc[q];
+      if (ghosty) { // a ghost upwind neighbour: mean of its link value and this cell
+        if (posx ? (m0 & kXm) : (m0 & kXp)) {
+          const float2 g = link_value(A, cell, posx ? 0 : 1, kof(M, q));
+          ix = __fmul2_rn(dup(0.5f), __fadd2_rn(g, Ra[q]));
+        }
+        if (posy ? (m0 & kYm) : (m0 & kYp)) {
+          const float2 g = link_value(A, cell, posy ? 2 : 3, kof(M, q));
+          iy = __fmul2_rn(dup(0.5f), __fadd2_rn(g, Ra[q]));
+        }
+      }
+      // Shakhov equilibrium (Sec. 4 reduced forms) from the stored state:
+      // (H, B) = (e, T/2 e) + m (2t - 4, T t - T), t = c^2 / T
+      const float cx = M.xix[q] - U0, cy = M.xiy[q] - U1;
+      const float c2 = fmaf(cx, cx, cy * cy);
+      const float t = c2 * invT;
+      const float e = pre * __expf(-t);
+      const float mm = e * shA * fmaf(cx, q0, cy * q1);
+      const float2 G = make_float2(fmaf(mm, fmaf(2.f, t, -4.f), e), fmaf(mm, fmaf(Tc, t, -Tc), halfT * e));
+      // forward Euler: relaxation and the flux divergence of both axes,
+      // |xi_a| dt / dx_a (inflow face - outflow face)
+      float2 n = __ffma2_rn(Ra[q], omd, __fmul2_rn(dt2, G));
+      n = __ffma2_rn(M.ax2[q], sub2(ix, PX[q]), n);
+      n = __ffma2_rn(M.ay2[q], sub2(iy, Pb[q]), n);
+      out[q] = n;
+      // moments of the new state about the stored bulk velocity
+      const float wh = M.wk[q] * n.x;
+      const float e2 = fmaf(c2, wh, M.wk[q] * n.y); // w (c^2 h + b)
+      a03.x += wh;
+      a03.y += e2;
+      a17.x = fmaf(cx, wh, a17.x);
+      a17.y = fmaf(cx, e2, a17.y);
+      a28.x = fmaf(cy, wh, a28.x);
+      a28.y = fmaf(cy, e2, a28.y);
+      const float cxwh = cx * wh;
+      a45.x = fmaf(cx, cxwh, a45.x);
+      a45.y = fmaf(cy, cxwh, a45.y);
+      a6 = fmaf(cy * cy, wh, a6);
+    }
+    float *dst = A.fn + ((size_t)cell * A.nvp + M.k0) * 2;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) *reinterpret_cast<float2 *>(dst + 2 * klo(M, q)) = out[q];
+  }
+  // (6) butterfly reduction of the sums over the 32 lanes: three rounds halve
+  //     the eight values a lane holds, two more finish the one it keeps; the
+  //     ninth sum is a plain xor tree
+  {
+    const float acc[NM] = {a03.x, a17.x, a28.x, a03.y, a45.x, a45.y, a6, a17.y, a28.y};
+    const int lane = M.lane;
+    float v4[4];
+    const bool b16 = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float keep = b16 ? acc[4 + i] : acc[i];
+      const float send = b16 ? acc[i] : acc[4 + i];
+      v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float v2[2];
+    const bool b8 = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float keep = b8 ? v4[2 + i] : v4[i];
+      const float send = b8 ? v4[i] : v4[2 + i];
+      v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const bool b4 = lane & 4;
+    float v1 = (b4 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b4 ? v2[0] : v2[1], 4);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+    float s8 = acc[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
+    if (M.col_in) {
+      float *pp = A.part + (size_t)(M.k0 / C::KC) * NM * M.nc + cell;
+      if ((lane & 3) == 0) pp[(size_t)(lane >> 2) * M.nc] = v1;
+      if (lane == 1) pp[(size_t)8 * M.nc] = s8;
+    }
+  }
+  if (M.lane < kMac) M.smac[((par ^ 1) * TX + M.warp) * kMac + M.lane] = pre_next;
+  M.mask_next2 = mn3;
+  mc = mn;
+  if (++M.st == NST) {
+    M.st = 0;
+    M.pb ^= 1u;
+  }
+  return true;
+}
+
+template <int KPT>
+__global__ void __launch_bounds__(NTHREADS, 2) sweep2d_tma_kernel(const __grid_constant__ CUtensorMap tmf,
+                                                                  TmaArgs A) {
+  using C = Cfg<KPT>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  March<KPT> M{A, &tmf};
+  M.stage = reinterpret_cast<float *>(smem_raw);
+  M.phix = M.stage + NST * C::STAGE_FLOATS;
+  M.sfinf = M.phix + 2 * C::PHI_FLOATS;
+  M.sxi = M.sfinf + C::KC2;
+  M.smac = M.sxi + C::KC;
+  M.full = reinterpret_cast<uint64_t *>(M.smac + 2 * TX * kMac);
+  M.warp = threadIdx.x >> 5;
+  M.lane = threadIdx.x & 31;
+  M.x0 = blockIdx.x * TX;
+  M.k0 = blockIdx.y * C::KC;
+  M.y0 = blockIdx.z * A.rows;
+  M.y1 = min(A.ny, M.y0 + A.rows);
+  M.ylast = min(A.ny, M.y1 + 2); // rows this block reads: [y0, ylast)
+  M.x = M.x0 + M.warp;
+  M.col_in = M.x < A.nx;
+  M.nc = A.ncell;
+  M.st = 0;
+  M.pb = 0;
+  M.abort_local = false;
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) {
+    const int k = kof(M, q);
+    const bool valid = k < A.nv;
+    // padding velocities: an enormous speed makes the equilibrium vanish,
+    // zero flux coefficients and zero weight keep them out of everything
+    M.xix[q] = valid ? A.xi[k] : 1e18f;
+    M.xiy[q] = valid ? A.xi[A.nvp + k] : 1e18f;
+    M.wk[q] = valid ? A.w[k] : 0.f;
+    M.ax2[q] = dup(valid ? A.dt * fabsf(M.xix[q]) * A.rdx : 0.f);
+    M.ay2[q] = dup(valid ? A.dt * fabsf(M.xiy[q]) * A.rdy : 0.f);
+    M.sy2[q] = dup(copysignf(1.f, M.xiy[q]));
+  }
+  // parameters of the first row's cells, and the flags of row y0 + 1
+  if (M.lane < kMac)
+    M.smac[M.warp * kMac + M.lane] = M.col_in ? A.mac[(M.x + (long long)A.nx * M.y0) * kMac + M.lane] : 0.f;
+  M.mask_next2 = M.col_in ? ((M.y0 + 1 < A.ny) ? cmask_of(M, M.x, M.y0 + 1) : 0) : kNotFluid;
+  for (int i = threadIdx.x; i < C::KC2; i += NTHREADS) M.sfinf[i] = A.finf[2 * M.k0 + i];
+  for (int i = threadIdx.x; i < C::KC; i += NTHREADS) M.sxi[i] = A.xi[M.k0 + i];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(&M.full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int r = M.y0; r < min(M.ylast, M.y0 + NST - 1); ++r) issue_row(M, r, r - M.y0);
+
+  // own-column ring for rows y0-2 .. y0+1, straight from global memory
+  auto own = [&](int r, Ring<KPT> &v) {
+    if (r < 0 || r >= A.ny || !M.col_in) {
+#pragma unroll
+      for (int q = 0; q < KPT; ++q) v[q] = sm2<KPT>(M.sfinf, klo(M, q));
+    } else {
+      const float *src = A.f + ((size_t)(M.x + (long long)A.nx * r) * A.nvp + M.k0) * 2;
+#pragma unroll
+      for (int q = 0; q < KPT; ++q) v[q] = *reinterpret_cast<const float2 *>(src + 2 * klo(M, q));
+    }
+  };
+  Ring<KPT> R0, R1, R2, P0, P1, P2;
+  {
+    Ring<KPT> Rm2;
+    own(M.y0 - 2, Rm2);
+    own(M.y0 - 1, R2);
+    own(M.y0, R0);
+    own(M.y0 + 1, R1);
+    phi_y(M, M.y0 - 1, M.col_in ? cmask_of(M, M.x, M.y0 - 1) : kNotFluid, R2, Rm2, R0, P0);
+    phi_y(M, M.y0, M.col_in ? cmask_of(M, M.x, M.y0) : kNotFluid, R0, R2, R1, P1);
+  }
+  // rows y0 and y0+1 are read from shared memory by the x stencil
+  for (int r = M.y0; r < min(M.ylast, M.y0 + 2); ++r)
+    if (!mbar_wait(&M.full[r - M.y0], 0)) M.abort_local = true;
+  uint8_t mc = M.col_in ? cmask_of(M, M.x, M.y0) : kNotFluid;
+  int y = M.y0;
+  int par = 0;
+  bool ok = true;
+  // three rows per trip: the ring rotates by renaming
+  while (ok && y < M.y1) {
+    ok = row(M, y, par, mc, R0, R1, R2, P0, P1, P2);
+    if (!ok || ++y >= M.y1) break;
+    par ^= 1;
+    ok = row(M, y, par, mc, R1, R2, R0, P1, P2, P0);
+    if (!ok || ++y >= M.y1) break;
+    par ^= 1;
+    ok = row(M, y, par, mc, R2, R0, R1, P2, P0, P1);
+    ++y;
+    par ^= 1;
+  }
+  if (!ok && threadIdx.x == 0) {
+    atomicOr(A.err, kFlagTimeout);
+    // drain: rows issued but not yet waited for must land (or time out
+    // again) before the block's shared memory is released
+    const int issued_end = min(M.ylast, y + NST - 1);
+    for (int r = max(M.y0 + 2, y + 2); r < issued_end; ++r) {
+      const int j = r - M.y0;
+      mbar_wait(&M.full[j % NST], (j / NST) & 1);
+    }
+  }
+}
+
+// driver entry point for the tensor-map encoder, looked up once
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+} // namespace
+
+// The TMA sweep applies to 2D cases in FP32 storage with the velocity count
+// padded to a multiple of 64.
+bool tma_sweep_applicable(const ibdvm_ctx *ctx) {
+  return ctx->dim == 2 && ctx->precision == IBDVM_MIXED && (ctx->nvp % 64) == 0 && encoder() != nullptr;
+}
+
+int tma_sweep_kpt(const ibdvm_ctx *ctx) { return (ctx->nvp % 128 == 0) ? 4 : 2; }
+int tma_sweep_nchunk(const ibdvm_ctx *ctx) { return ctx->nvp / (32 * tma_sweep_kpt(ctx)); }
+
+cudaError_t tma_sweep_prepare(ibdvm_ctx *ctx) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const int kpt = tma_sweep_kpt(ctx);
+  const int kc = 32 * kpt;
+  for (int b = 0; b < 2; ++b) {
+    CUtensorMap *tm = reinterpret_cast<CUtensorMap *>(ctx->tmap[b]);
+    cuuint64_t dims[3] = {(cuuint64_t)ctx->nvp * 2, (cuuint64_t)ctx->geom.n[0], (cuuint64_t)ctx->geom.n[1]};
+    cuuint64_t strides[2] = {(cuuint64_t)ctx->nvp * 2 * 4, (cuuint64_t)ctx->geom.n[0] * ctx->nvp * 2 * 4};
+    cuuint32_t box[3] = {(cuuint32_t)(2 * kc), (cuuint32_t)COLS, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ctx->f[b], dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  if (kpt == 4)
+    return cudaFuncSetAttribute(sweep2d_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<4>::SMEM);
+  return cudaFuncSetAttribute(sweep2d_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<2>::SMEM);
+}
+
+cudaError_t tma_sweep_launch(ibdvm_ctx *ctx) {
+  TmaArgs A{};
+  A.f = static_cast<const float *>(ctx->f[ctx->cur]);
+  A.fn = static_cast<float *>(ctx->f[1 - ctx->cur]);
+  A.mac = static_cast<const float *>(ctx->mac);
+  A.xi = static_cast<const float *>(ctx->xiT);
+  A.w = static_cast<const float *>(ctx->wT);
+  A.finf = static_cast<const float *>(ctx->finf);
+  A.cmask = ctx->cmask;
+  A.dslot = ctx->dslot;
+  A.dlinks = ctx->dlinks;
+  A.lval = static_cast<const float *>(ctx->lval);
+  A.part = ctx->partf;
+  A.err = ctx->d_flags;
+  A.ncell = ctx->ncell;
+  A.nx = ctx->geom.n[0];
+  A.ny = ctx->geom.n[1];
+  A.nvp = ctx->nvp;
+  A.nv = ctx->nv;
+  A.dt = (float)ctx->geom.dt;
+  A.rdx = (float)(1.0 / ctx->geom.dx[0]);
+  A.rdy = (float)(1.0 / ctx->geom.dx[1]);
+  const int kpt = tma_sweep_kpt(ctx);
+  const int nstrip = (A.nx + TX - 1) / TX;
+  const int nchunk = ctx->nvp / (32 * kpt);
+  // rows per block: enough blocks for several waves of two blocks per SM
+  int nrb = 1;
+  while ((long long)nstrip * nchunk * nrb < 8LL * 152 && A.ny / (nrb * 2) >= 32) nrb *= 2;
+  A.rows = (A.ny + nrb - 1) / nrb;
+  dim3 grid(nstrip, nchunk, (A.ny + A.rows - 1) / A.rows);
+  const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(ctx->tmap[ctx->cur]);
+  if (kpt == 4)
+    sweep2d_tma_kernel<4><<<grid, NTHREADS, Cfg<4>::SMEM, ctx->stream>>>(*tm, A);
+  else
+    sweep2d_tma_kernel<2><<<grid, NTHREADS, Cfg<2>::SMEM, ctx->stream>>>(*tm, A);
+  return cudaGetLastError();
+}
+
+} // namespace ibdvm

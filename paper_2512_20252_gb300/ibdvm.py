@@ -66,7 +66,7 @@ class Info(ctypes.Structure):
                 ("nfluid", ctypes.c_longlong), ("nvel", ctypes.c_int), ("nvel_padded", ctypes.c_int),
                 ("nlink", ctypes.c_int), ("nghost", ctypes.c_int), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int), ("steps_done", ctypes.c_longlong),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("sweep_variant", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)

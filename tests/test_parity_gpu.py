@@ -271,3 +271,64 @@ def test_sphere_96_full_size_properties():
     assert np.abs(Wm[:, ::-1, :, 0] - Wm[:, :, :, 0]).max() < 1e-5
     assert np.abs(Wm[::-1, :, :, 0] - Wm[:, :, :, 0]).max() < 1e-5
     g.close()
+
+
+# ---------------------------------------------------------------------------
+# the TMA-staged sweep of 2D FP32 cases
+# ---------------------------------------------------------------------------
+
+def _solver_env(case, no_tma: bool):
+    import os
+
+    old = os.environ.get("IBDVM_NO_TMA")
+    os.environ["IBDVM_NO_TMA"] = "1" if no_tma else "0"
+    try:
+        return ibdvm.Solver(case)
+    finally:
+        if old is None:
+            del os.environ["IBDVM_NO_TMA"]
+        else:
+            os.environ["IBDVM_NO_TMA"] = old
+
+
+@pytest.mark.parametrize("shape", ["square_kpt4", "ragged_kpt2", "short_rows", "naca_kpt4", "odd_nv"])
+def test_tma_sweep_against_oracle_and_plain_sweep(shape):
+    if shape == "square_kpt4":
+        case = wl.small_2d("circle", n=40, nv=16, Ma=0.4)           # 256 velocities: 4 per lane
+    elif shape == "ragged_kpt2":
+        case = wl.small_2d("ellipse", n=24, nv=8, Ma=0.6)           # 64 velocities: 2 per lane
+        case["n"] = [27, 21]
+        case["lo"], case["hi"] = [-2.2, -1.7], [2.0, 1.9]
+    elif shape == "short_rows":
+        case = wl.small_2d("circle", n=20, nv=12, Ma=0.3)
+        case["n"] = [36, 9]
+        case["lo"], case["hi"] = [-3.0, -0.75], [3.0, 0.75]
+        case["body"] = wl.circle(0.4)
+    elif shape == "naca_kpt4":
+        case = wl.small_2d("naca", n=48, nv=16, Ma=0.5)
+    else:
+        case = wl.small_2d("circle", n=32, nv=11, Ma=0.5)           # 121 velocities, padded to 128
+    case["precision"] = "mixed"
+    o = oracle.OracleCase(case)
+    f0 = perturbed(o, 21, 0.2)
+    o.set_f(f0)
+    g = _solver_env(case, False)
+    p = _solver_env(case, True)
+    g.set_f(f0)
+    p.set_f(f0)
+    rg = g.step(4)
+    rp = p.step(4)
+    ro = o.step(4)
+    t = o.cell_types()
+    fl = t == oracle.FLUID
+    fo = o.get_f()[fl]
+    assert rel_err(g.get_f()[fl], fo) < 2e-5
+    assert rel_err(g.get_f()[fl], p.get_f()[fl]) < 2e-5
+    Wg, _, _ = g.moments()
+    Wo, _ = o.moments()
+    for i in range(4):
+        if np.abs(Wo[fl, i]).max() > 1e-9:
+            assert rel_err(Wg[fl, i], Wo[fl, i]) < 1e-5, i
+    assert rg == pytest.approx(ro, rel=1e-3)
+    kt = g.kernel_times()
+    assert kt["sweep"][1] == 4
