@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--cells", type=int, default=0,
                     help="override the cells per axis (smaller cases for profiling captures)")
+    ap.add_argument("--error-report", type=int, default=0, metavar="STEPS",
+                    help="instead of timing: run the workload STEPS steps in the mixed and the FP64 "
+                         "GPU paths and print the relative differences of W, C_D, C_L, Q and the residual")
     return ap.parse_args()
 
 
@@ -212,11 +215,51 @@ def run_reference(args, world, rank):
     return 0
 
 
+def error_report(args):
+    """Mixed path (FP32 f, FP32 transport and relaxation with compensated
+    sums, FP64 wall balance, forces and residual) against the FP64 path on the
+    same workload; the FP64 path itself matches the CPU oracle within 1e-11
+    (tests/test_parity_gpu.py)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    from paper_2512_20252_gb300 import ibdvm
+
+    out = {}
+    for prec in ("fp64", "mixed"):
+        case = WORKLOADS[args.workload](prec)
+        if args.cells:
+            case["n"] = [args.cells] * case["dim"]
+        s = ibdvm.Solver(case, stream=torch.cuda.Stream().cuda_stream)
+        res = s.step(args.error_report)
+        W, q, t = s.moments()
+        F, Q, CD, CL = s.forces()
+        out[prec] = dict(W=W[t == 0], res=res, CD=CD, CL=CL, Q=Q, F=F)
+        s.close()
+    a, b = out["mixed"], out["fp64"]
+    werr = [float(np.abs(a["W"][:, i] - b["W"][:, i]).max() / np.abs(b["W"][:, i]).max())
+            for i in range(b["W"].shape[1])]
+    rel = lambda x, y: float(abs(x - y) / max(abs(y), 1e-300))
+    line = {"report": "mixed vs fp64", "workload": DESCRIPTIONS[args.workload], "steps": args.error_report,
+            "W_rel_err": werr, "CD_rel_err": rel(a["CD"], b["CD"]), "CL_abs_err": abs(a["CL"] - b["CL"]),
+            "Q_rel_err": rel(a["Q"], b["Q"]), "residual_rel_err": rel(a["res"], b["res"]),
+            "fp64": {"CD": b["CD"], "CL": b["CL"], "Q": b["Q"], "residual": b["res"]},
+            "mixed": {"CD": a["CD"], "CL": a["CL"], "Q": a["Q"], "residual": a["res"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.error_report:
+        return error_report(args)
 
     import numpy as np
     import torch

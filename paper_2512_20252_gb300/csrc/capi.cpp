@@ -103,7 +103,15 @@ void free_body(ibdvm_ctx *ctx) {
   ctx->lval = ctx->fi_scr = ctx->fsp_scr = nullptr;
 }
 
+void drop_graphs(ibdvm_ctx *ctx) {
+  for (int i = 0; i < 4; ++i) {
+    if (ctx->graph2[i]) cudaGraphExecDestroy(ctx->graph2[i]);
+    ctx->graph2[i] = nullptr;
+  }
+}
+
 void free_all(ibdvm_ctx *ctx) {
+  drop_graphs(ctx);
   free_body(ctx);
   cfree(ctx->f[0]);
   cfree(ctx->f[1]);
@@ -593,6 +601,7 @@ ibdvm_status ibdvm_set_body(ibdvm_ctx *ctx, const ibdvm_body_desc *body) {
     ctx->err = err;
     return IBDVM_E_INVAL;
   }
+  drop_graphs(ctx);
   Geom old = std::move(ctx->geom);
   ctx->geom = std::move(G2);
   try {
@@ -619,15 +628,48 @@ ibdvm_status ibdvm_step(ibdvm_ctx *ctx, int nsteps, double *residual_out) {
     return IBDVM_OK;
   }
   check(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), ctx->stream), "clear flags");
-  for (int i = 0; i < nsteps; ++i) {
-    // ghost band on f^n, the surface force of the fluxes this step applies,
-    // then transport, relaxation and the moments of f^{n+1}
+  // one step: the ghost band on f^n, the surface force of the fluxes this
+  // step applies, then transport, relaxation and the moments of f^{n+1}
+  auto one_step = [&]() {
     check(ctx, launch_ghost_band(ctx, nullptr), "ghost band kernel");
     check(ctx, launch_forces(ctx, ctx->d_step_forces), "forces kernel");
     check(ctx, launch_sweep(ctx), "sweep kernel");
-    if (ctx->ev_used > 4096) { // keep the event pool bounded on long calls
-      sync(ctx, "step");
+  };
+  int done = 0;
+  // pairs of steps replay a captured CUDA graph (not while profiling, and
+  // not on the legacy default stream, which cannot be captured)
+  if (nsteps >= 2 && ctx->graphs_enabled && !ctx->profiling && ctx->stream != nullptr) {
+    const int key = ctx->cur * 2 + ctx->wcur;
+    if (!ctx->graph2[key]) {
+      long long before[8];
+      for (int i = 0; i < 8; ++i) before[i] = ctx->kernel_launches[i];
+      cudaGraph_t g = nullptr;
+      check(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin graph capture");
+      try {
+        one_step();
+        one_step();
+      } catch (const Fail &) {
+        cudaStreamEndCapture(ctx->stream, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      check(ctx, cudaStreamEndCapture(ctx->stream, &g), "end graph capture");
+      cudaError_t e = cudaGraphInstantiate(&ctx->graph2[key], g, 0);
+      cudaGraphDestroy(g);
+      check(ctx, e, "instantiate step graph");
+      for (int i = 0; i < 8; ++i) {
+        ctx->graph2_launches[key][i] = ctx->kernel_launches[i] - before[i];
+        ctx->kernel_launches[i] = before[i]; // counted when replayed
+      }
     }
+    for (; done + 2 <= nsteps; done += 2) {
+      check(ctx, cudaGraphLaunch(ctx->graph2[key], ctx->stream), "replay step graph");
+      for (int i = 0; i < 8; ++i) ctx->kernel_launches[i] += ctx->graph2_launches[key][i];
+    }
+  }
+  for (; done < nsteps; ++done) {
+    one_step();
+    if (ctx->ev_used > 4096) sync(ctx, "step"); // keep the event pool bounded on long calls
   }
   double res = 0.0;
   int fl = 0;

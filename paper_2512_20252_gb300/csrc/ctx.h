@@ -86,6 +86,11 @@ struct ibdvm_ctx {
   std::vector<std::pair<int, size_t>> ev_marks; // (kernel class, index of the start event)
   double kernel_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long kernel_launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // CUDA graphs of two consecutive steps, keyed by the parities of the state
+  // and moment buffers at their start; replayed by ibdvm_step
+  bool graphs_enabled = true;
+  cudaGraphExec_t graph2[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long graph2_launches[4][8] = {};
   // bookkeeping
   long long steps = 0;
   size_t dev_bytes = 0;
