@@ -125,7 +125,8 @@ class ClockSampler:
 
 
 SWEEP_KERNELS = {0: ("sweep_kernel", "paper_2512_20252_gb300/csrc/kernels.cu"),
-                 1: ("sweep2d_tma_kernel", "paper_2512_20252_gb300/csrc/sweep_tma.cu")}
+                 1: ("sweep2d_tma_kernel", "paper_2512_20252_gb300/csrc/sweep_tma.cu"),
+                 2: ("sweep3d_tma_kernel", "paper_2512_20252_gb300/csrc/sweep3d_tma.cu")}
 
 
 def profiled_traffic(kernel: str, source: str, pairs: int):

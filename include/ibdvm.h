@@ -130,7 +130,8 @@ typedef struct {
   int precision;
   long long steps_done;
   size_t device_bytes;
-  int sweep_variant; /* 0: plain sweep (kernels.cu), 1: TMA-staged 2D FP32 sweep (sweep_tma.cu) */
+  int sweep_variant; /* 0: plain sweep (kernels.cu), 1: TMA-staged 2D FP32 sweep (sweep_tma.cu),
+                        2: TMA-staged 3D FP32 sweep (sweep3d_tma.cu) */
 } ibdvm_info;
 
 /* Creates a context: velocity grid, freestream Maxwellian in every cell, no

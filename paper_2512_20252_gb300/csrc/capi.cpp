@@ -499,7 +499,7 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     const int NM = nmoments(G.dim);
     // memory check before allocating
     const size_t fbytes = static_cast<size_t>(ctx->ncell) * ctx->nvp * ctx->ncomp * ctx->esize;
-    const size_t need = 2 * fbytes + static_cast<size_t>(ctx->ncell) * (G.dim == 2 ? 40 * 9 : 0) +
+    const size_t need = 2 * fbytes + static_cast<size_t>(ctx->ncell) * ctx->nvp / 32 * (G.dim == 2 ? 9 : 14) +
                         static_cast<size_t>(ctx->ncell) *
                                          (kMac * ctx->esize + 2 * (NW + G.dim) * 8 + ctx->nchunk * NM * 8 + 8);
     int dev = 0;
@@ -527,11 +527,13 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     ctx->cmask = dalloc<uint8_t>(ctx, ctx->ncell, "cell flags");
     // the TMA sweep for 2D FP32 cases (IBDVM_NO_TMA=1 keeps the plain sweep)
     const char *no_tma = std::getenv("IBDVM_NO_TMA");
-    if (tma_sweep_applicable(ctx) && !(no_tma && no_tma[0] == '1')) {
-      ctx->tma_nchunk = tma_sweep_nchunk(ctx);
+    const bool tma_off = no_tma && no_tma[0] == '1';
+    if (!tma_off && (tma_sweep_applicable(ctx) || tma3_sweep_applicable(ctx))) {
+      const bool two = G.dim == 2;
+      ctx->tma_nchunk = two ? tma_sweep_nchunk(ctx) : tma3_sweep_nchunk(ctx);
       ctx->partf = dalloc<float>(ctx, static_cast<size_t>(ctx->tma_nchunk) * nmoments(G.dim) * ctx->ncell,
                                  "FP32 moment sums");
-      check(ctx, tma_sweep_prepare(ctx), "TMA sweep set-up");
+      check(ctx, two ? tma_sweep_prepare(ctx) : tma3_sweep_prepare(ctx), "TMA sweep set-up");
       ctx->use_tma = true;
     }
     // velocity tables
@@ -855,7 +857,7 @@ ibdvm_status ibdvm_get_info(const ibdvm_ctx *ctx, ibdvm_info *info) {
   info->precision = ctx->precision;
   info->steps_done = ctx->steps;
   info->device_bytes = ctx->dev_bytes;
-  info->sweep_variant = ctx->use_tma ? 1 : 0;
+  info->sweep_variant = ctx->use_tma ? (ctx->dim == 2 ? 1 : 2) : 0;
   return IBDVM_OK;
 }
 

@@ -64,6 +64,7 @@ struct ibdvm_ctx {
   float *partf = nullptr;    // FP32 moment partial sums [nchunk][9][ncell]
   int tma_nchunk = 0;
   alignas(64) unsigned char tmap[2][128];
+  alignas(64) unsigned char tmap3[2][3][128]; // 3D: tile, x halo strip, y halo strip per buffer
   // ghost band
   int nlink = 0, nghost = 0, nsurf = 0;
   int *l_int = nullptr;      // [nlink][8]
@@ -111,6 +112,11 @@ bool tma_sweep_applicable(const ibdvm_ctx *ctx);
 int tma_sweep_nchunk(const ibdvm_ctx *ctx);
 cudaError_t tma_sweep_prepare(ibdvm_ctx *ctx);
 cudaError_t tma_sweep_launch(ibdvm_ctx *ctx);
+// TMA sweep of 3D FP32 cases (sweep3d_tma.cu)
+bool tma3_sweep_applicable(const ibdvm_ctx *ctx);
+int tma3_sweep_nchunk(const ibdvm_ctx *ctx);
+cudaError_t tma3_sweep_prepare(ibdvm_ctx *ctx);
+cudaError_t tma3_sweep_launch(ibdvm_ctx *ctx);
 
 // dense FP64 [ncells][nv][ncomp] (device) <-> cells [c0, c0 + ncells) of the current state
 cudaError_t launch_convert(ibdvm_ctx *ctx, double *dense, long long c0, long long ncells, bool to_state);

@@ -1018,11 +1018,11 @@ cudaError_t launch_sweep(ibdvm_ctx *ctx) {
     using T = decltype(t);
     constexpr int D = decltype(d)::value;
     cudaError_t e;
-    const bool tma = std::is_same<T, float>::value && D == 2 && ctx->use_tma;
+    const bool tma = std::is_same<T, float>::value && ctx->use_tma;
     {
       Timed tm(ctx, kKSweep);
       ctx->kernel_launches[kKSweep] += 1;
-      e = tma ? tma_sweep_launch(ctx) : sweep_t<T, D>(ctx, 1, 1);
+      e = tma ? (D == 2 ? tma_sweep_launch(ctx) : tma3_sweep_launch(ctx)) : sweep_t<T, D>(ctx, 1, 1);
     }
     if (e != cudaSuccess) return e;
     ctx->cur = 1 - ctx->cur;

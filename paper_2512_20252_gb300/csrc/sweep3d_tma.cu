@@ -1,0 +1,660 @@
+// sweep3d_tma.cu -- the transport / relaxation / moments sweep of 3D cases in
+// FP32 storage (the mixed path), staged through shared memory by TMA.
+//
+// Same arithmetic as sweep_kernel in kernels.cu (Sec. 2.2 Eqs. reconstruction
+// and limiter, the Shakhov equilibrium of Sec. 2.1 in the non-dimensional
+// form of Sec. 4, forward Euler, Eqs. moments1-3 by quadrature), organised for
+// GB300:
+//
+//   * a block owns a 4 x 4 tile of (x, y) columns of cells (16 warps, one per
+//     column) and a chunk of KC = 32 * KPT velocities (lane l owns velocities
+//     l, l + 32, ...), and marches along z;
+//   * every z plane of the block arrives in shared memory as a cross-shaped
+//     slab: the 4 x 4 tile and two halo strips of two cells on each side in x
+//     and in y (48 cells x KC velocities), five TMA tensor copies
+//     (cp.async.bulk.tensor.4d) on one mbarrier per stage of a 5-stage ring;
+//   * each lane keeps its column's z stencil in registers (f at planes z..z+2
+//     and the reconstructed faces of planes z-1..z+1), rotated by renaming in a
+//     three-way unrolled loop;
+//   * x and y faces are exchanged through shared memory: every warp publishes
+//     the downwind faces of its cell; the faces of the halo cells on the
+//     upwind side of the tile are spread over all threads;
+//   * the fourteen moment sums (about the stored bulk velocity) are reduced
+//     over the 32 lanes by a butterfly and written as FP32 partial sums per
+//     velocity chunk; the finalize kernel adds the chunks in FP64.
+//
+// Conditions that hold for a whole warp (ghost neighbours, the domain edge, a
+// cell that is not fluid) select a general path per warp.  Every mbarrier
+// wait is bounded: on timeout the block sets an error flag, drains its copies
+// (bounded) and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+
+#include "ctx.h"
+
+namespace ibdvm {
+namespace {
+
+constexpr int TX = 4, TY = 4;   // tile of columns, one warp each
+constexpr int NW = TX * TY;     // warps per block
+constexpr int NTHREADS = NW * 32;
+constexpr int NST = 5;          // TMA plane stages
+constexpr int NCELL = TX * TY + 2 * (2 * TY) + 2 * (2 * TX); // cells of the cross-shaped slab (48)
+constexpr int NM = 14;          // moment sums (3D)
+constexpr long kSpinLimit = 1L << 22;
+
+// slot of slab cell (i, j), i in [-2, TX+2), j in [-2, TY+2), cross-shaped
+__device__ __forceinline__ int slot(int i, int j) {
+  if (i >= 0 && i < TX && j >= 0 && j < TY) return j * TX + i;              // centre [y][x]
+  if (i < 0) return TX * TY + j * 2 + (i + 2);                              // x halo low  [y][2]
+  if (i >= TX) return TX * TY + 2 * TY + j * 2 + (i - TX);                  // x halo high [y][2]
+  if (j < 0) return TX * TY + 4 * TY + (j + 2) * TX + i;                    // y halo low  [2][x]
+  return TX * TY + 4 * TY + 2 * TX + (j - TY) * TX + i;                      // y halo high [2][x]
+}
+
+template <int KPT> struct Cfg {
+  static constexpr int KC = 32 * KPT;
+  static constexpr int STAGE_FLOATS = NCELL * KC;
+  static constexpr int STAGE_BYTES = STAGE_FLOATS * 4;
+  static constexpr int PX_FLOATS = (TX + 2) * TY * KC; // x faces: [y][x+1][k]
+  static constexpr int PY_FLOATS = TX * (TY + 2) * KC; // y faces: [y+1][x][k]
+  static constexpr size_t SMEM =
+      (size_t)(NST * STAGE_FLOATS + 2 * (PX_FLOATS + PY_FLOATS) + 4 * KC + 2 * NW * kMac) * 4 +
+      2 * NTHREADS * sizeof(int4) + NST * 8;
+};
+
+struct Tma3Args {
+  float *__restrict__ fn;
+  const float *__restrict__ f;
+  const float *__restrict__ mac;  // [ncell][kMac]
+  const float *__restrict__ xi;   // [3][nvp]
+  const float *__restrict__ w;    // [nvp]
+  const float *__restrict__ finf; // [nvp]
+  const uint8_t *__restrict__ cmask;
+  const int *__restrict__ dslot;
+  const int *__restrict__ dlinks;
+  const float *__restrict__ lval; // [nlink][nvp]
+  float *__restrict__ part;       // [nchunk][NM][ncell]
+  int *__restrict__ err;
+  long long ncell;
+  int nx, ny, nz, nvp, nv, zrows;
+  float dt, rdx, rdy, rdz;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
+                                        uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+  if (mbar_try(bar, parity)) return true;
+  for (long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// half the van Leer slope times the cell width from the one-sided differences
+// a = f - f_up and b = f_dn - f along the direction of motion (Eq. limiter)
+__device__ __forceinline__ float vl_half(float a, float b) {
+  const float p = a * b;
+  const float v = p * rcp_approx(a + b);
+  return p > 0.f ? v : 0.f;
+}
+// downwind face value: f plus half the slope along the motion
+__device__ __forceinline__ float face(float f, float up, float dn) { return f + vl_half(f - up, dn - f); }
+
+__device__ __forceinline__ float link_value(const Tma3Args &A, long long c, int dir, int k) {
+  const int s = A.dslot[c];
+  const int l = (s >= 0) ? A.dlinks[s * 6 + dir] : -1;
+  return (l >= 0) ? A.lval[(size_t)l * A.nvp + k] : A.finf[k];
+}
+
+enum : uint8_t { kNotFluid = 64, kGhostAny = 63 };
+
+template <int KPT> using Ring = float[KPT];
+
+// Every thread owns two halo faces per plane, both for chunk velocity
+// kk = threadIdx.x % KC: the downwind x face of the upwind x-halo cell of row
+// threadIdx.x / KC, and the downwind y face of the upwind y-halo cell of column
+// threadIdx.x / KC.  All but the cells' flags is the same for every plane and
+// is packed once into shared memory (int4 per face):
+//   x: stage offset of f | (offset of the upwind neighbour + 1) << 16
+//   y: offset of the downwind neighbour + 1 | face buffer offset << 16
+//      (a neighbour offset of 0 after the + 1 means the freestream value)
+//   z: the halo cell's index within a plane, or -1 outside the domain
+template <int KPT> struct March3 {
+  const Tma3Args &A;
+  const CUtensorMap *tc, *tx, *ty; // tensor maps: tile, x halo strip, y halo strip
+  float *stage, *phx, *phy, *sfinf, *sxi, *syi, *smac;
+  uint64_t *full;
+  int warp, lane, ti, tj, x0, y0, x, y, k0, z0, z1, zlast;
+  int st;
+  unsigned pb;
+  bool col_in;
+  long long nc, plane;
+  float xix[KPT], xiy[KPT], xiz[KPT], wk[KPT], ax[KPT], ay[KPT], az[KPT];
+  uint8_t mask_next;
+  bool abort_local;
+  const int4 *duty; // [2][NTHREADS]: x faces, then y faces
+};
+
+template <int KPT> __device__ __forceinline__ int klo(const March3<KPT> &M, int q) { return M.lane + 32 * q; }
+template <int KPT> __device__ __forceinline__ int kof(const March3<KPT> &M, int q) { return M.k0 + klo(M, q); }
+
+template <int KPT> __device__ __forceinline__ void issue_plane(March3<KPT> &M, int z, int st) {
+  using C = Cfg<KPT>;
+  float *dst = M.stage + st * C::STAGE_FLOATS;
+  uint64_t *bar = &M.full[st];
+  mbar_expect_tx(bar, C::STAGE_BYTES);
+  const int kc = M.k0;
+  tma_box(dst + slot(0, 0) * C::KC, M.tc, kc, M.x0, M.y0, z, bar);
+  tma_box(dst + slot(-2, 0) * C::KC, M.tx, kc, M.x0 - 2, M.y0, z, bar);
+  tma_box(dst + slot(TX, 0) * C::KC, M.tx, kc, M.x0 + TX, M.y0, z, bar);
+  tma_box(dst + slot(0, -2) * C::KC, M.ty, kc, M.x0, M.y0 - 2, z, bar);
+  tma_box(dst + slot(0, TY) * C::KC, M.ty, kc, M.x0, M.y0 + TY, z, bar);
+}
+
+template <int KPT> __device__ __forceinline__ uint8_t cmask3(const March3<KPT> &M, int cx, int cy, int cz) {
+  const Tma3Args &A = M.A;
+  if (cx < 0 || cx >= A.nx || cy < 0 || cy >= A.ny || cz < 0 || cz >= A.nz) return 0;
+  return A.cmask[cx + (long long)A.nx * (cy + (long long)A.ny * cz)];
+}
+
+// downwind face along axis a (0: x, 1: y) of slab cell (i, j) at plane z for
+// chunk velocity kk, general path: domain edge, ghost neighbours, non-fluid
+template <int KPT>
+__device__ __forceinline__ float face_general(const March3<KPT> &M, const float *sp, int a, int i, int j, int z,
+                                              int kk, float xi) {
+  using C = Cfg<KPT>;
+  const Tma3Args &A = M.A;
+  const int cx = M.x0 + i, cy = M.y0 + j;
+  if (cx < 0 || cx >= A.nx || cy < 0 || cy >= A.ny) return M.sfinf[kk]; // halo: freestream, zero slope
+  const uint8_t m = cmask3(M, cx, cy, z);
+  if (m & kNotFluid) return 0.f;
+  const int s = (xi >= 0.f) ? 1 : -1;
+  const int di = (a == 0) ? s : 0, dj = (a == 1) ? s : 0;
+  const float f = sp[slot(i, j) * C::KC + kk];
+  const int ca = (a == 0) ? cx : cy, na = (a == 0) ? A.nx : A.ny;
+  const long long c = cx + (long long)A.nx * (cy + (long long)A.ny * z);
+  float up, dn;
+  // upwind neighbour (against the motion) and downwind neighbour
+  if (m & (1u << (2 * a + (s > 0 ? 0 : 1)))) up = link_value(A, c, 2 * a + (s > 0 ? 0 : 1), M.k0 + kk);
+  else if (ca - s < 0 || ca - s >= na) up = M.sfinf[kk];
+  else up = sp[slot(i - di, j - dj) * C::KC + kk];
+  if (m & (1u << (2 * a + (s > 0 ? 1 : 0)))) dn = link_value(A, c, 2 * a + (s > 0 ? 1 : 0), M.k0 + kk);
+  else if (ca + s < 0 || ca + s >= na) dn = M.sfinf[kk];
+  else dn = sp[slot(i + di, j + dj) * C::KC + kk];
+  return face(f, up, dn);
+}
+
+// downwind z face of plane r for the own column: fr = f(r), lo = f(r-1), hi = f(r+1)
+template <int KPT>
+__device__ __forceinline__ void phi_z(const March3<KPT> &M, int r, uint8_t m, const Ring<KPT> &fr,
+                                      const Ring<KPT> &lo, const Ring<KPT> &hi, Ring<KPT> &out) {
+  const Tma3Args &A = M.A;
+  if (r < 0 || r >= A.nz || !M.col_in) {
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) out[q] = M.sfinf[klo(M, q)];
+    return;
+  }
+  if (m & kNotFluid) {
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) out[q] = 0.f;
+    return;
+  }
+  const long long c = M.plane + (long long)r * A.nx * A.ny;
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) {
+    float l = lo[q], h = hi[q];
+    if (m & 16) l = link_value(A, c, 4, kof(M, q));
+    if (m & 32) h = link_value(A, c, 5, kof(M, q));
+    out[q] = (M.xiz[q] >= 0.f) ? face(fr[q], l, h) : face(fr[q], h, l);
+  }
+}
+
+// the halo face of axis a owned by this thread at plane z
+template <int KPT, int a>
+__device__ __forceinline__ void halo_face(const March3<KPT> &M, const float *sp, int z, float *dst) {
+  using C = Cfg<KPT>;
+  const Tma3Args &A = M.A;
+  const int4 d = M.duty[a * NTHREADS + threadIdx.x];
+  const int kk = threadIdx.x % C::KC;
+  const int out = d.y >> 16;
+  if (d.z < 0) { // outside the domain: freestream, zero slope
+    dst[out] = M.sfinf[kk];
+    return;
+  }
+  const uint8_t m = A.cmask[d.z + (long long)z * A.nx * A.ny];
+  if (m & (kNotFluid | (3u << (2 * a)))) { // rare: not fluid, or a ghost neighbour along the axis
+    const float xi = (a == 0) ? M.sxi[kk] : M.syi[kk];
+    const int line = threadIdx.x / C::KC;
+    const int i = (a == 0) ? ((xi >= 0.f) ? -1 : TX) : line;
+    const int j = (a == 0) ? line : ((xi >= 0.f) ? -1 : TY);
+    dst[out] = face_general(M, sp, a, i, j, z, kk, xi);
+    return;
+  }
+  const int up = d.x >> 16, dn = d.y & 0xffff;
+  const float f = sp[d.x & 0xffff];
+  const float fu = up ? sp[up - 1] : M.sfinf[kk];
+  const float fd = dn ? sp[dn - 1] : M.sfinf[kk];
+  dst[out] = face(f, fu, fd);
+}
+
+template <int KPT>
+__device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8_t &mc, Ring<KPT> &Ra,
+                                           Ring<KPT> &Rb, Ring<KPT> &Rc, Ring<KPT> &Pa, Ring<KPT> &Pb,
+                                           Ring<KPT> &Pc) {
+  using C = Cfg<KPT>;
+  const Tma3Args &A = M.A;
+  const long long cell = M.plane + (long long)z * A.nx * A.ny;
+  const uint8_t m0 = mc;
+  const bool fluid = !(m0 & kNotFluid);
+  const float pre_next =
+      (M.lane < kMac && M.col_in && z + 1 < A.nz) ? __ldg(A.mac + (cell + (long long)A.nx * A.ny) * kMac + M.lane) : 0.f;
+  const uint8_t mn = M.mask_next;
+  const uint8_t mn2 = M.col_in ? ((z + 2 < A.nz) ? cmask3(M, M.x, M.y, z + 2) : 0) : kNotFluid;
+  const int st = M.st;
+  int st2 = st + 2;
+  unsigned pb2 = M.pb;
+  if (st2 >= NST) {
+    st2 -= NST;
+    pb2 ^= 1u;
+  }
+  // (1) own column at plane z + 2 (the z stencil)
+  if (z + 2 < A.nz && !mbar_wait(&M.full[st2], pb2)) M.abort_local = true;
+  if (z + 2 < A.nz && M.col_in) {
+    const float *src = M.stage + st2 * C::STAGE_FLOATS + slot(M.ti, M.tj) * C::KC;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) Rc[q] = src[klo(M, q)];
+  } else {
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) Rc[q] = M.sfinf[klo(M, q)];
+  }
+  const float *sp = M.stage + st * C::STAGE_FLOATS;
+  float *phx = M.phx + par * C::PX_FLOATS; // [TY][TX + 2][KC]
+  float *phy = M.phy + par * C::PY_FLOATS; // [TY + 2][TX][KC]
+  // (2) downwind x and y faces of the own cell
+  float PX[KPT], PY[KPT];
+  const bool fast = M.col_in && fluid && !(m0 & 15) && M.x > 0 && M.x + 1 < A.nx && M.y > 0 && M.y + 1 < A.ny;
+  if (fast) {
+    const float *px_lo = sp + slot(M.ti - 1, M.tj) * C::KC, *px_hi = sp + slot(M.ti + 1, M.tj) * C::KC;
+    const float *py_lo = sp + slot(M.ti, M.tj - 1) * C::KC, *py_hi = sp + slot(M.ti, M.tj + 1) * C::KC;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int kk = klo(M, q);
+      const float xl = px_lo[kk], xh = px_hi[kk], yl = py_lo[kk], yh = py_hi[kk];
+      PX[q] = (M.xix[q] >= 0.f) ? face(Ra[q], xl, xh) : face(Ra[q], xh, xl);
+      PY[q] = (M.xiy[q] >= 0.f) ? face(Ra[q], yl, yh) : face(Ra[q], yh, yl);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      PX[q] = face_general(M, sp, 0, M.ti, M.tj, z, klo(M, q), M.xix[q]);
+      PY[q] = face_general(M, sp, 1, M.ti, M.tj, z, klo(M, q), M.xiy[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) {
+    phx[(M.tj * (TX + 2) + M.ti + 1) * C::KC + klo(M, q)] = PX[q];
+    phy[((M.tj + 1) * TX + M.ti) * C::KC + klo(M, q)] = PY[q];
+  }
+  // halo faces on the upwind side of the tile (TY rows in x, TX columns in y)
+  halo_face<KPT, 0>(M, sp, z, phx);
+  halo_face<KPT, 1>(M, sp, z, phy);
+  // (3) downwind z face of plane z + 1
+  phi_z(M, z + 1, mn, Rb, Ra, Rc, Pc);
+  // (4) barrier: faces published, the stage of plane z - 1 released
+  if (__syncthreads_or(M.abort_local ? 1 : 0)) return false;
+  if (threadIdx.x == 0 && z + NST - 1 < M.zlast) {
+    fence_proxy_async();
+    issue_plane(M, z + NST - 1, st == 0 ? NST - 1 : st - 1);
+  }
+  // (5) update of the own cell and its moment sums
+  float acc[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) acc[m] = 0.f;
+  if (fluid) {
+    const float4 *pm = reinterpret_cast<const float4 *>(M.smac + (par * NW + M.warp) * kMac);
+    const float4 p0 = pm[0], p1 = pm[1], p2 = pm[2];
+    const float pre = p0.x, U0 = p0.y, U1 = p0.z, U2 = p0.w;
+    const float invT = p1.x, shA = p1.z, q0 = p1.w;
+    const float q1 = p2.x, q2 = p2.y, dtau = p2.z;
+    const float omd = 1.f - dtau;
+    const bool ghosty = (m0 & kGhostAny) != 0;
+    float out[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int kk = klo(M, q);
+      const bool px = M.xix[q] >= 0.f, py = M.xiy[q] >= 0.f, pz = M.xiz[q] >= 0.f;
+      float ix = phx[(M.tj * (TX + 2) + M.ti + (px ? 0 : 2)) * C::KC + kk];
+      float iy = phy[((M.tj + (py ? 0 : 2)) * TX + M.ti) * C::KC + kk];
+      float iz = pz ? Pa[q] : Pc[q];
+      if (ghosty) { // ghost upwind neighbour: mean of its link value and this cell
+        const int dx = px ? 0 : 1, dy = py ? 2 : 3, dz = pz ? 4 : 5;
+        if (m0 & (1u << dx)) ix = 0.5f * (link_value(A, cell, dx, kof(M, q)) + Ra[q]);
+        if (m0 & (1u << dy)) iy = 0.5f * (link_value(A, cell, dy, kof(M, q)) + Ra[q]);
+        if (m0 & (1u << dz)) iz = 0.5f * (link_value(A, cell, dz, kof(M, q)) + Ra[q]);
+      }
+      // Shakhov equilibrium g (1 + A c.q (2 c^2/T - 5)) from the stored state
+      const float cx = M.xix[q] - U0, cy = M.xiy[q] - U1, cz = M.xiz[q] - U2;
+      const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+      const float t = c2 * invT;
+      const float e = pre * __expf(-t);
+      const float cq = fmaf(cx, q0, fmaf(cy, q1, cz * q2));
+      const float g = fmaf(e * shA * cq, fmaf(2.f, t, -5.f), e);
+      float n = fmaf(Ra[q], omd, dtau * g);
+      n = fmaf(M.ax[q], ix - PX[q], n);
+      n = fmaf(M.ay[q], iy - PY[q], n);
+      n = fmaf(M.az[q], iz - Pb[q], n);
+      out[q] = n;
+      const float wf = M.wk[q] * n, e2 = c2 * wf;
+      const float cxw = cx * wf, cyw = cy * wf;
+      acc[0] += wf;
+      acc[1] += cxw;
+      acc[2] += cyw;
+      acc[3] = fmaf(cz, wf, acc[3]);
+      acc[4] += e2;
+      acc[5] = fmaf(cx, cxw, acc[5]);
+      acc[6] = fmaf(cy, cxw, acc[6]);
+      acc[7] = fmaf(cz, cxw, acc[7]);
+      acc[8] = fmaf(cy, cyw, acc[8]);
+      acc[9] = fmaf(cz, cyw, acc[9]);
+      acc[10] = fmaf(cz * cz, wf, acc[10]);
+      acc[11] = fmaf(cx, e2, acc[11]);
+      acc[12] = fmaf(cy, e2, acc[12]);
+      acc[13] = fmaf(cz, e2, acc[13]);
+    }
+    float *dst = A.fn + (size_t)cell * A.nvp + M.k0;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) dst[klo(M, q)] = out[q];
+  }
+  // (6) butterfly of the 16 (14 used) sums over the 32 lanes
+  {
+    const int lane = M.lane;
+    float v8[8];
+    const bool b16 = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float keep = b16 ? acc[8 + i] : acc[i];
+      const float send = b16 ? acc[i] : acc[8 + i];
+      v8[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float v4[4];
+    const bool b8 = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float keep = b8 ? v8[4 + i] : v8[i];
+      const float send = b8 ? v8[i] : v8[4 + i];
+      v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float v2[2];
+    const bool b4 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float keep = b4 ? v4[2 + i] : v4[i];
+      const float send = b4 ? v4[i] : v4[2 + i];
+      v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const bool b2 = lane & 2;
+    float v1 = (b2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? v2[0] : v2[1], 2);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+    // lane l holds sum index 8 b4(l) + 4 b3(l) + 2 b2(l) + b1(l) = l >> 1
+    const int idx = lane >> 1;
+    if (M.col_in && (lane & 1) == 0 && idx < NM)
+      A.part[((size_t)(M.k0 / C::KC) * NM + idx) * M.nc + cell] = v1;
+  }
+  if (M.lane < kMac) M.smac[((par ^ 1) * NW + M.warp) * kMac + M.lane] = pre_next;
+  M.mask_next = mn2;
+  mc = mn;
+  if (++M.st == NST) {
+    M.st = 0;
+    M.pb ^= 1u;
+  }
+  return true;
+}
+
+template <int KPT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tmc, const __grid_constant__ CUtensorMap tmx,
+                       const __grid_constant__ CUtensorMap tmy, Tma3Args A) {
+  using C = Cfg<KPT>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  March3<KPT> M{A, &tmc, &tmx, &tmy};
+  M.stage = reinterpret_cast<float *>(smem_raw);
+  M.phx = M.stage + NST * C::STAGE_FLOATS;
+  M.phy = M.phx + 2 * C::PX_FLOATS;
+  M.sfinf = M.phy + 2 * C::PY_FLOATS;
+  M.sxi = M.sfinf + C::KC;
+  M.syi = M.sxi + C::KC;
+  M.smac = M.syi + 2 * C::KC;
+  M.duty = reinterpret_cast<const int4 *>(M.smac + 2 * NW * kMac);
+  M.full = reinterpret_cast<uint64_t *>(const_cast<int4 *>(M.duty) + 2 * NTHREADS);
+  M.warp = threadIdx.x >> 5;
+  M.lane = threadIdx.x & 31;
+  M.ti = M.warp % TX;
+  M.tj = M.warp / TX;
+  const int ntx = (A.nx + TX - 1) / TX;
+  M.x0 = (blockIdx.x % ntx) * TX;
+  M.y0 = (blockIdx.x / ntx) * TY;
+  M.x = M.x0 + M.ti;
+  M.y = M.y0 + M.tj;
+  M.col_in = M.x < A.nx && M.y < A.ny;
+  M.k0 = blockIdx.y * C::KC;
+  M.z0 = blockIdx.z * A.zrows;
+  M.z1 = min(A.nz, M.z0 + A.zrows);
+  M.zlast = min(A.nz, M.z1 + 2);
+  M.nc = A.ncell;
+  M.plane = M.x + (long long)A.nx * M.y;
+  M.st = 0;
+  M.pb = 0;
+  M.abort_local = false;
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) {
+    const int k = kof(M, q);
+    const bool valid = k < A.nv;
+    M.xix[q] = valid ? A.xi[k] : 1e18f;
+    M.xiy[q] = valid ? A.xi[A.nvp + k] : 1e18f;
+    M.xiz[q] = valid ? A.xi[2 * A.nvp + k] : 1e18f;
+    M.wk[q] = valid ? A.w[k] : 0.f;
+    M.ax[q] = valid ? A.dt * fabsf(M.xix[q]) * A.rdx : 0.f;
+    M.ay[q] = valid ? A.dt * fabsf(M.xiy[q]) * A.rdy : 0.f;
+    M.az[q] = valid ? A.dt * fabsf(M.xiz[q]) * A.rdz : 0.f;
+  }
+  for (int i = threadIdx.x; i < C::KC; i += NTHREADS) {
+    M.sfinf[i] = A.finf[M.k0 + i];
+    M.sxi[i] = A.xi[M.k0 + i];
+    M.syi[i] = A.xi[A.nvp + M.k0 + i];
+  }
+  {
+    static_assert(TX * C::KC == NTHREADS && TY * C::KC == NTHREADS, "two halo faces per thread");
+    const int kk = threadIdx.x % C::KC, line = threadIdx.x / C::KC;
+    int4 *duty = const_cast<int4 *>(M.duty);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const float xi = A.xi[a * A.nvp + M.k0 + kk];
+      const int s = (xi >= 0.f) ? 1 : -1;
+      const int i = (a == 0) ? ((s > 0) ? -1 : TX) : line;
+      const int j = (a == 0) ? line : ((s > 0) ? -1 : TY);
+      const int di = (a == 0) ? s : 0, dj = (a == 1) ? s : 0;
+      const int cx = M.x0 + i, cy = M.y0 + j;
+      const bool outside = cx < 0 || cx >= A.nx || cy < 0 || cy >= A.ny;
+      const int ca = (a == 0) ? cx : cy, na = (a == 0) ? A.nx : A.ny;
+      const int f_off = slot(i, j) * C::KC + kk;
+      const int up = (outside || ca - s < 0 || ca - s >= na) ? 0 : slot(i - di, j - dj) * C::KC + kk + 1;
+      const int dn = (outside || ca + s < 0 || ca + s >= na) ? 0 : slot(i + di, j + dj) * C::KC + kk + 1;
+      const int out = (a == 0) ? (j * (TX + 2) + i + 1) * C::KC + kk : ((j + 1) * TX + i) * C::KC + kk;
+      duty[a * NTHREADS + threadIdx.x] =
+          make_int4(f_off | (up << 16), dn | (out << 16), outside ? -1 : cx + A.nx * cy, 0);
+    }
+  }
+  if (M.lane < kMac)
+    M.smac[M.warp * kMac + M.lane] =
+        M.col_in ? A.mac[(M.plane + (long long)M.z0 * A.nx * A.ny) * kMac + M.lane] : 0.f;
+  M.mask_next = M.col_in ? ((M.z0 + 1 < A.nz) ? cmask3(M, M.x, M.y, M.z0 + 1) : 0) : kNotFluid;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(&M.full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int r = M.z0; r < min(M.zlast, M.z0 + NST - 1); ++r) issue_plane(M, r, r - M.z0);
+  auto own = [&](int r, Ring<KPT> &v) {
+    if (r < 0 || r >= A.nz || !M.col_in) {
+#pragma unroll
+      for (int q = 0; q < KPT; ++q) v[q] = M.sfinf[klo(M, q)];
+    } else {
+      const float *src = A.f + (size_t)(M.plane + (long long)r * A.nx * A.ny) * A.nvp + M.k0;
+#pragma unroll
+      for (int q = 0; q < KPT; ++q) v[q] = src[klo(M, q)];
+    }
+  };
+  Ring<KPT> R0, R1, R2, P0, P1, P2;
+  {
+    Ring<KPT> Rm2;
+    own(M.z0 - 2, Rm2);
+    own(M.z0 - 1, R2);
+    own(M.z0, R0);
+    own(M.z0 + 1, R1);
+    phi_z(M, M.z0 - 1, M.col_in ? cmask3(M, M.x, M.y, M.z0 - 1) : kNotFluid, R2, Rm2, R0, P0);
+    phi_z(M, M.z0, M.col_in ? cmask3(M, M.x, M.y, M.z0) : kNotFluid, R0, R2, R1, P1);
+  }
+  for (int r = M.z0; r < min(M.zlast, M.z0 + 2); ++r)
+    if (!mbar_wait(&M.full[r - M.z0], 0)) M.abort_local = true;
+  uint8_t mc = M.col_in ? cmask3(M, M.x, M.y, M.z0) : kNotFluid;
+  int z = M.z0, par = 0;
+  bool ok = true;
+  // one copy of the plane body (a small kernel keeps the instruction cache
+  // warm); the ring rotates by moves
+  for (; z < M.z1; ++z) {
+    ok = plane_step(M, z, par, mc, R0, R1, R2, P0, P1, P2);
+    if (!ok) break;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      R0[q] = R1[q];
+      R1[q] = R2[q];
+      P0[q] = P1[q];
+      P1[q] = P2[q];
+    }
+    par ^= 1;
+  }
+  if (!ok && threadIdx.x == 0) {
+    atomicOr(A.err, kFlagTimeout);
+    const int issued_end = min(M.zlast, z + NST - 1);
+    for (int r = max(M.z0 + 2, z + 2); r < issued_end; ++r) {
+      const int j = r - M.z0;
+      mbar_wait(&M.full[j % NST], (j / NST) & 1);
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder3() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+constexpr int kKpt3 = 4;
+
+} // namespace
+
+bool tma3_sweep_applicable(const ibdvm_ctx *ctx) {
+  return ctx->dim == 3 && ctx->precision == IBDVM_MIXED && (ctx->nvp % (32 * kKpt3)) == 0 && encoder3() != nullptr;
+}
+
+int tma3_sweep_nchunk(const ibdvm_ctx *ctx) { return ctx->nvp / (32 * kKpt3); }
+
+cudaError_t tma3_sweep_prepare(ibdvm_ctx *ctx) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder3();
+  if (!enc) return cudaErrorNotSupported;
+  const int kc = 32 * kKpt3;
+  const Geom &g = ctx->geom;
+  for (int b = 0; b < 2; ++b) {
+    cuuint64_t dims[4] = {(cuuint64_t)ctx->nvp, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+    cuuint64_t strides[3] = {(cuuint64_t)ctx->nvp * 4, (cuuint64_t)g.n[0] * ctx->nvp * 4,
+                             (cuuint64_t)g.n[1] * g.n[0] * ctx->nvp * 4};
+    const cuuint32_t boxes[3][4] = {{(cuuint32_t)kc, TX, TY, 1}, {(cuuint32_t)kc, 2, TY, 1}, {(cuuint32_t)kc, TX, 2, 1}};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int m = 0; m < 3; ++m) {
+      CUtensorMap *tm = reinterpret_cast<CUtensorMap *>(ctx->tmap3[b][m]);
+      CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->f[b], dims, strides, boxes[m], estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+  }
+  return cudaFuncSetAttribute(sweep3d_tma_kernel<kKpt3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Cfg<kKpt3>::SMEM);
+}
+
+cudaError_t tma3_sweep_launch(ibdvm_ctx *ctx) {
+  Tma3Args A{};
+  A.f = static_cast<const float *>(ctx->f[ctx->cur]);
+  A.fn = static_cast<float *>(ctx->f[1 - ctx->cur]);
+  A.mac = static_cast<const float *>(ctx->mac);
+  A.xi = static_cast<const float *>(ctx->xiT);
+  A.w = static_cast<const float *>(ctx->wT);
+  A.finf = static_cast<const float *>(ctx->finf);
+  A.cmask = ctx->cmask;
+  A.dslot = ctx->dslot;
+  A.dlinks = ctx->dlinks;
+  A.lval = static_cast<const float *>(ctx->lval);
+  A.part = ctx->partf;
+  A.err = ctx->d_flags;
+  A.ncell = ctx->ncell;
+  A.nx = ctx->geom.n[0];
+  A.ny = ctx->geom.n[1];
+  A.nz = ctx->geom.n[2];
+  A.nvp = ctx->nvp;
+  A.nv = ctx->nv;
+  A.dt = (float)ctx->geom.dt;
+  A.rdx = (float)(1.0 / ctx->geom.dx[0]);
+  A.rdy = (float)(1.0 / ctx->geom.dx[1]);
+  A.rdz = (float)(1.0 / ctx->geom.dx[2]);
+  const int ntiles = ((A.nx + TX - 1) / TX) * ((A.ny + TY - 1) / TY);
+  const int nchunk = ctx->nvp / (32 * kKpt3);
+  int nzb = 1;
+  while ((long long)ntiles * nchunk * nzb < 4LL * 152 && A.nz / (nzb * 2) >= 16) nzb *= 2;
+  A.zrows = (A.nz + nzb - 1) / nzb;
+  dim3 grid(ntiles, nchunk, (A.nz + A.zrows - 1) / A.zrows);
+  const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(ctx->tmap3[ctx->cur][0]);
+  sweep3d_tma_kernel<kKpt3><<<grid, NTHREADS, Cfg<kKpt3>::SMEM, ctx->stream>>>(tm[0], tm[1], tm[2], A);
+  return cudaGetLastError();
+}
+
+} // namespace ibdvm
