@@ -37,11 +37,15 @@ WORKLOADS = {
     "sphere_96": lambda p: __import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).sphere_96(p),
     "cylinder_48": lambda p: dict(__import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).cylinder_48(),
                                   precision=p),
+    "batched_2d": None,  # a list of cases: see bench_batch
 }
 DESCRIPTIONS = {
     "cylinder_512": "2D cylinder r=0.5, 512x512 cells on [-8,8]^2, 48x48 trapezoid velocities on [-6,6]^2, Kn=0.1, Ma=0.5",
     "sphere_96": "3D sphere r=0.5, 96^3 cells on [-4,4]^3, 20^3 trapezoid velocities on [-5,5]^3, Kn=0.1, Ma=0.5",
     "cylinder_48": "2D cylinder r=0.5, 48x48 cells on [-4,4]^2, 24x24 trapezoid velocities on [-5,5]^2, Kn=0.1, Ma=0.3",
+    "batched_2d": "64 seeded 2D cases (seed 0): n ~ U{64..384} cells per axis on [-4,4]^2, m ~ U{16..40} "
+                  "velocities per axis on [-6,6]^2, circle / ellipse (aspect U[1,3]) / NACA0012 (AoA U[0,10] deg), "
+                  "Kn 10^U[-2,0], Ma U[0.1,0.8], mixed precision, one batch",
 }
 
 
@@ -58,6 +62,9 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--cells", type=int, default=0,
                     help="override the cells per axis (smaller cases for profiling captures)")
+    ap.add_argument("--ncases", type=int, default=64, help="batched_2d: number of cases")
+    ap.add_argument("--tune-steps", type=int, default=4,
+                    help="batched_2d: steps per autotuner trial (0 = no tuning)")
     ap.add_argument("--error-report", type=int, default=0, metavar="STEPS",
                     help="instead of timing: run the workload STEPS steps in the mixed and the FP64 "
                          "GPU paths and print the relative differences of W, C_D, C_L, Q and the residual")
@@ -124,6 +131,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+BATCH_KERNEL = ("sweep2d_tma_batch_kernel", "paper_2512_20252_gb300/csrc/sweep_tma.cu")
 SWEEP_KERNELS = {0: ("sweep_kernel", "paper_2512_20252_gb300/csrc/kernels.cu"),
                  1: ("sweep2d_tma_kernel", "paper_2512_20252_gb300/csrc/sweep_tma.cu"),
                  2: ("sweep3d_tma_kernel", "paper_2512_20252_gb300/csrc/sweep3d_tma.cu")}
@@ -187,7 +195,7 @@ def time_oracle(case: dict, budget_s: float, max_steps: int | None = None):
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    case = WORKLOADS[args.workload](args.precision)
+    case = batch_cases(args)[0] if args.workload == "batched_2d" else WORKLOADS[args.workload](args.precision)
     sample = cpu_sample_case(case)
     import oracle
 
@@ -254,6 +262,132 @@ def error_report(args):
     return 0
 
 
+def batch_cases(args, precision="mixed"):
+    from paper_2512_20252_gb300 import workloads
+
+    cases = workloads.batched_2d(0, ncases=args.ncases, precision=precision)
+    if args.cells:  # a smaller copy for profiling captures: cells per axis scaled down
+        for c in cases:
+            c["n"] = [max(16, c["n"][0] * args.cells // 384)] * 2
+    return cases
+
+
+def bench_batch(args, world, rank, local, pg):
+    """The batched form: every case of the batch advanced by grouped launches
+    (one persistent sweep launch over the packed work list per step)."""
+    import numpy as np
+    import torch
+
+    from paper_2512_20252_gb300 import ibdvm
+
+    cases = batch_cases(args)
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    solvers = [ibdvm.Solver(c, stream=stream.cuda_stream) for c in cases]
+    batch = ibdvm.Batch(stream=stream.cuda_stream)
+    for s in solvers:
+        batch.add(s)
+    setup_s = time.perf_counter() - t0
+    pairs = sum(int(s.info.nfluid) * int(s.info.nvel) for s in solvers)
+    alg_bytes = sum(int(s.info.nfluid) * int(s.info.nvel) * 2 * 4 * 2 for s in solvers)
+    state_bytes = sum(int(s.ncell) * int(s.nvel_padded) * 2 * 4 for s in solvers)
+    best_ms = batch.tune(args.tune_steps) if args.tune_steps else None
+    tiling = batch.tiling()
+    batch.step(max(args.warmup, 3))
+    batch.set_profiling(True)
+    batch.reset_kernel_times()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    res, sts = batch.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    kt = batch.kernel_times()
+    batch.set_profiling(False)
+    if pg:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = pairs * args.steps * world / (elapsed_ms / 1e3)
+    sweep_ms, sweep_n = kt["sweep"]
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (sweep_ms / sweep_n / 1e3) / 1e9 if sweep_n else None
+    launches = sum(n for _, n in kt.values())
+    F, Q, CD, CL = batch.forces()
+
+    # end to end through the C-ABI with host buffers: every step uploads each
+    # member's f^n from pinned host memory, advances the batch one step and
+    # reads every member's W^{n+1} back
+    hbufs = []
+    for s in solvers:
+        hb = torch.empty(s.native_shape(), dtype=torch.float32, pin_memory=True)
+        s.get_f_native(hb.data_ptr(), hb.numel() * 4)
+        hbufs.append(hb)
+    h2d = sum(hb.numel() * 4 for hb in hbufs)
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        for s, hb in zip(solvers, hbufs):
+            s.set_f_native(hb.data_ptr(), hb.numel() * 4)
+        batch.step(1)
+        d2h = 0
+        for s in solvers:
+            W, q, _ = s.moments()
+            d2h += W.nbytes + q.nbytes + 8
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = pairs * e2e_steps * world / e2e_s
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sample = cpu_sample_case(cases[0])
+        v, n, el, oc = time_oracle(sample, args.cpu_sample_seconds)
+        cpu = {"value": v, "unit": "cell-velocity updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} oracle steps ({el:.1f} s) of case 0's gas, body and velocity grid "
+                         f"on {sample['n'][0]} cells per axis ({oc.nfluid} fluid cells x {oc.nvel} velocities)"}
+    if rank == 0:
+        line = {
+            "metric": "DVM cell x velocity updates/s", "value": value, "unit": "cell-velocity updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": DESCRIPTIONS["batched_2d"].replace("64 seeded", f"{args.ncases} seeded")
+                       + (f", cells scaled by {args.cells}/384" if args.cells else ""),
+                       "precision": "mixed", "cases": len(solvers), "pairs": pairs,
+                       "state_gb": 2 * state_bytes / 1e9, "tiling": tiling, "tuned_ms_per_step": best_ms,
+                       "setup_s": setup_s,
+                       "l2": f"inputs larger than L2 (f^n is {state_bytes / 1e9:.2f} GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": profiled_traffic(BATCH_KERNEL[0], BATCH_KERNEL[1], pairs),
+                         "kernel": BATCH_KERNEL[0], "peak_kind": peak_kind,
+                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms / max(sweep_n, 1)},
+            "kernel_ms": {k: v[0] for k, v in kt.items()},
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "cpu_baseline": cpu, "clocks": clocks,
+            "max_residual": float(np.max(res)), "statuses_ok": bool(np.all(sts == 0)),
+            "CD_range": [float(np.min(CD)), float(np.max(CD))],
+        }
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for s in solvers:
+        s.close()
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args.gpus)
@@ -282,6 +416,12 @@ def main():
     torch.cuda.set_device(local)
     from paper_2512_20252_gb300 import ibdvm
 
+    if args.workload == "batched_2d":
+        rc = bench_batch(args, world, rank, local, pg)
+        if pg:
+            pg.barrier()
+            pg.destroy_process_group()
+        return rc
     case = WORKLOADS[args.workload](args.precision)
     if args.cells:
         case["n"] = [args.cells] * case["dim"]

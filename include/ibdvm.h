@@ -235,6 +235,87 @@ const char *ibdvm_last_error(const ibdvm_ctx *ctx);
 const char *ibdvm_status_string(ibdvm_status s);
 
 /* ------------------------------------------------------------------------
+ * Batched form: many 2D cases of uneven size advanced together.  The paper
+ * solves one case at a time; batching changes no arithmetic.  A member's
+ * step is the one ibdvm_step takes (the same kernel bodies), launched for all
+ * members at once:
+ *   - one grouped ghost-band launch over every member's links (Sec. 3.2);
+ *   - one grouped force launch, plus one block per member for the totals;
+ *   - one persistent transport / relaxation / moment sweep (Sec. 2.2, Sec. 4)
+ *     over a packed work list of (member, 8-column strip, velocity chunk, row
+ *     range) items, largest first, which the blocks take from a device counter;
+ *   - one grouped finalize launch, plus one block per member for its residual.
+ * Pairs of steps replay captured CUDA graphs.
+ *
+ * Members are 2D contexts in FP32 storage (IBDVM_MIXED) with the TMA sweep
+ * (ibdvm_info.sweep_variant == 1), bound to the batch's stream.  A batch
+ * references its members and does not own them; a context belongs to at most
+ * one batch, and ibdvm_destroy takes a member out of its batch.  Members can be
+ * added and removed between steps (continuous batching): a change of
+ * membership, of a member's body or of the tiling rebuilds the batch's device
+ * tables (small uploads, synchronous) and drops its graphs.  Not thread-safe.
+ * ------------------------------------------------------------------------ */
+typedef struct ibdvm_batch ibdvm_batch;
+
+/* Errors: IBDVM_E_INVAL (out is NULL), IBDVM_E_NOMEM. */
+ibdvm_status ibdvm_batch_create(void *cuda_stream, ibdvm_batch **out);
+/* Appends ctx.  Errors: IBDVM_E_INVAL (NULL, not 2D FP32 with the TMA sweep,
+   or bound to another stream), IBDVM_E_STATE (already a member of a batch). */
+ibdvm_status ibdvm_batch_add(ibdvm_batch *b, ibdvm_ctx *ctx);
+/* Removes ctx; later members move up one place.  Errors: IBDVM_E_INVAL (not a
+   member of b). */
+ibdvm_status ibdvm_batch_remove(ibdvm_batch *b, ibdvm_ctx *ctx);
+/* Number of members (-1 for NULL) and member i in order of addition (NULL if
+   out of range). */
+int ibdvm_batch_size(const ibdvm_batch *b);
+ibdvm_ctx *ibdvm_batch_member(const ibdvm_batch *b, int i);
+
+/* Advances every member nsteps steps.  residuals[m] (nullable) receives the
+   residual of member m's last step, statuses[m] (nullable) its status
+   (IBDVM_OK, IBDVM_E_UNSTABLE, IBDVM_E_NONFINITE, IBDVM_E_TIMEOUT).  Returns
+   IBDVM_OK when every member is OK, else the status of the first member that
+   is not (its index is in the message); the members' states are then the ones
+   after the last step, as with ibdvm_step.  IBDVM_E_CUDA on a failed launch;
+   IBDVM_E_INVAL for nsteps < 0. */
+ibdvm_status ibdvm_batch_step(ibdvm_batch *b, int nsteps, double *residuals, int *statuses);
+
+/* Surface force and heat flux of the face fluxes that the last batched step
+   applied, per member: F[m][3], Q[m], CD[m], CL[m] (each nullable), normalised
+   as in ibdvm_forces.  Zeros for a member that has not stepped since the
+   batch last rebuilt its tables (a change of membership, body or tiling). */
+ibdvm_status ibdvm_batch_forces(ibdvm_batch *b, double *F, double *Q, double *CD, double *CL);
+
+/* Tiling of the sweep's work items.  rows: target rows per item (0 = whole
+   columns); kpt: velocities per lane, 4 (chunks of 128 velocities where the
+   member's padded velocity count is a multiple of 128, else 64), 2 (chunks of
+   64) or 0 (= 4).  get_tiling also reports the number of work items, the
+   persistent grid and whether graphs are in use. */
+typedef struct {
+  int rows, kpt, nitems, grid, graphs;
+} ibdvm_batch_tiling;
+ibdvm_status ibdvm_batch_set_tiling(ibdvm_batch *b, int rows, int kpt);
+ibdvm_status ibdvm_batch_get_tiling(const ibdvm_batch *b, ibdvm_batch_tiling *out);
+
+/* Autotuner: for each candidate tiling (rows in {16, 32, 64, 128, whole
+   columns} x kpt in {4, 2}) times steps_per_trial batched steps (even,
+   >= 2) with CUDA events on the batch's stream, after one untimed pair of
+   steps, and keeps the fastest.  The trials are real steps: every member
+   advances 10 x (steps_per_trial + 2) steps.  best_ms (nullable) receives
+   the kept tiling's time per step.  Errors: as ibdvm_batch_step;
+   IBDVM_E_INVAL for a bad steps_per_trial; IBDVM_E_STATE with no members. */
+ibdvm_status ibdvm_batch_tune(ibdvm_batch *b, int steps_per_trial, double *best_ms);
+
+/* Kernel timing of the batched launches, classes as ibdvm_get_kernel_times;
+   steps are not captured in graphs while profiling is on. */
+ibdvm_status ibdvm_batch_set_profiling(ibdvm_batch *b, int on);
+ibdvm_status ibdvm_batch_get_kernel_times(ibdvm_batch *b, double *ms, long long *launches);
+ibdvm_status ibdvm_batch_reset_kernel_times(ibdvm_batch *b);
+
+/* Releases the batch's tables and graphs; the members stay valid. */
+void ibdvm_batch_destroy(ibdvm_batch *b);
+const char *ibdvm_batch_last_error(const ibdvm_batch *b);
+
+/* ------------------------------------------------------------------------
  * Host-only geometry (no GPU needed): the classification, links, surface
  * cells and cut-cell table that ibdvm_set_body builds.
  * ------------------------------------------------------------------------ */

@@ -499,7 +499,7 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     const int NM = nmoments(G.dim);
     // memory check before allocating
     const size_t fbytes = static_cast<size_t>(ctx->ncell) * ctx->nvp * ctx->ncomp * ctx->esize;
-    const size_t need = 2 * fbytes + static_cast<size_t>(ctx->ncell) * ctx->nvp / 32 * (G.dim == 2 ? 9 : 14) +
+    const size_t need = 2 * fbytes + static_cast<size_t>(ctx->ncell) * (ctx->nvp / 64 + 1) * 4 * (G.dim == 2 ? 9 : 14) +
                         static_cast<size_t>(ctx->ncell) *
                                          (kMac * ctx->esize + 2 * (NW + G.dim) * 8 + ctx->nchunk * NM * 8 + 8);
     int dev = 0;
@@ -531,8 +531,9 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     if (!tma_off && (tma_sweep_applicable(ctx) || tma3_sweep_applicable(ctx))) {
       const bool two = G.dim == 2;
       ctx->tma_nchunk = two ? tma_sweep_nchunk(ctx) : tma3_sweep_nchunk(ctx);
-      ctx->partf = dalloc<float>(ctx, static_cast<size_t>(ctx->tma_nchunk) * nmoments(G.dim) * ctx->ncell,
-                                 "FP32 moment sums");
+      // 2D: room for 64-velocity chunks, the finest tiling a batch may choose
+      const size_t nch = two ? static_cast<size_t>(ctx->nvp / 64) : static_cast<size_t>(ctx->tma_nchunk);
+      ctx->partf = dalloc<float>(ctx, nch * nmoments(G.dim) * ctx->ncell, "FP32 moment sums");
       check(ctx, two ? tma_sweep_prepare(ctx) : tma3_sweep_prepare(ctx), "TMA sweep set-up");
       ctx->use_tma = true;
     }
@@ -604,6 +605,7 @@ ibdvm_status ibdvm_set_body(ibdvm_ctx *ctx, const ibdvm_body_desc *body) {
     return IBDVM_E_INVAL;
   }
   drop_graphs(ctx);
+  ++ctx->body_gen;
   Geom old = std::move(ctx->geom);
   ctx->geom = std::move(G2);
   try {
@@ -863,6 +865,10 @@ ibdvm_status ibdvm_get_info(const ibdvm_ctx *ctx, ibdvm_info *info) {
 
 ibdvm_status ibdvm_set_stream(ibdvm_ctx *ctx, void *cuda_stream) {
   IBDVM_GUARD(ctx)
+  if (ctx->batch && static_cast<cudaStream_t>(cuda_stream) != ctx->stream) {
+    ctx->err = "a batch member stays on the batch's stream";
+    return IBDVM_E_STATE;
+  }
   sync(ctx, "drain the old stream");
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   return IBDVM_OK;
@@ -875,6 +881,7 @@ const ibdvm_geom *ibdvm_get_geom(const ibdvm_ctx *ctx) {
 
 void ibdvm_destroy(ibdvm_ctx *ctx) {
   if (!ctx) return;
+  if (ctx->batch) batch_detach(ctx);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   free_all(ctx);
@@ -980,3 +987,9 @@ void ibdvm_geom_destroy(ibdvm_geom *g) { delete g; }
 const char *ibdvm_geom_last_error(void) { return g_geom_err.c_str(); }
 
 } // extern "C"
+
+namespace ibdvm {
+void force_outputs(const ibdvm_ctx *ctx, const double *h, double *F, double *Q, double *CD, double *CL) {
+  fill_forces(const_cast<ibdvm_ctx *>(ctx), h, F, Q, CD, CL);
+}
+} // namespace ibdvm

@@ -34,6 +34,8 @@ enum : int { kFlagNonFinite = 1, kFlagUnstable = 2, kFlagTimeout = 4 };
 
 } // namespace ibdvm
 
+struct ibdvm_batch; // batch.cpp
+
 struct ibdvm_ctx {
   ibdvm::Geom geom;
   cudaStream_t stream = nullptr;
@@ -92,6 +94,10 @@ struct ibdvm_ctx {
   bool graphs_enabled = true;
   cudaGraphExec_t graph2[4] = {nullptr, nullptr, nullptr, nullptr};
   long long graph2_launches[4][8] = {};
+  // the batch this context is a member of, and a counter of body changes
+  // (a batch rebuilds its tables when it changes)
+  ibdvm_batch *batch = nullptr;
+  unsigned body_gen = 0;
   // bookkeeping
   long long steps = 0;
   size_t dev_bytes = 0;
@@ -117,6 +123,45 @@ bool tma3_sweep_applicable(const ibdvm_ctx *ctx);
 int tma3_sweep_nchunk(const ibdvm_ctx *ctx);
 cudaError_t tma3_sweep_prepare(ibdvm_ctx *ctx);
 cudaError_t tma3_sweep_launch(ibdvm_ctx *ctx);
+
+// Grouped launches over the members of a batch (kernels.cu; FP32 storage, one
+// dimension per batch).  Each member has two argument blocks, for the buffer
+// parities after an even and an odd number of batched steps; the launch names
+// the parity.  Member m writes its residual to res[m], ORs its flags into
+// flags[m] and its step forces go to forces[4 m .. 4 m + 3].
+struct GroupTables {
+  int dim = 2, ncase = 0;
+  void *ghost = nullptr, *force = nullptr, *fin = nullptr; // [ncase][2] argument blocks
+  int *link_start = nullptr, *fin_start = nullptr;         // [ncase + 1] block prefix sums
+  int link_blocks = 0, fin_blocks = 0;
+};
+cudaError_t group_build(const std::vector<ibdvm_ctx *> &cases, const std::vector<int> &nchunk, double *res,
+                        int *flags, double *forces, GroupTables &t, cudaStream_t s);
+void group_free(GroupTables &t);
+cudaError_t group_ghost(const GroupTables &t, int par, cudaStream_t s);
+cudaError_t group_forces(const GroupTables &t, int par, cudaStream_t s);
+cudaError_t group_finalize(const GroupTables &t, int par, cudaStream_t s);
+
+// The batched TMA sweep of 2D FP32 members (sweep_tma.cu): one persistent
+// launch over a packed work list of (member, column strip, velocity chunk,
+// row range) items.  kpt[m] = 2 or 4 velocities per lane for member m; rows =
+// target rows per item (0: whole columns).
+struct SweepTables {
+  void *args = nullptr, *tmaps = nullptr, *items = nullptr; // [ncase][2], [ncase][2], [nitems]
+  int *next = nullptr; // work counter
+  int nitems = 0, grid = 0;
+};
+bool tma_batch_member_ok(const ibdvm_ctx *ctx);
+int tma_batch_kpt_max(const ibdvm_ctx *ctx);
+cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::vector<int> &kpt, int rows,
+                            int *flags, SweepTables &t, cudaStream_t s);
+void tma_batch_free(SweepTables &t);
+cudaError_t tma_batch_launch(const SweepTables &t, int par, cudaStream_t s);
+
+// batch.cpp: takes a context that is being destroyed out of its batch
+void batch_detach(ibdvm_ctx *ctx);
+// capi.cpp: F[3], Q, CD, CL (each nullable) from the force sums h[4] of ctx
+void force_outputs(const ibdvm_ctx *ctx, const double *h, double *F, double *Q, double *CD, double *CL);
 
 // dense FP64 [ncells][nv][ncomp] (device) <-> cells [c0, c0 + ncells) of the current state
 cudaError_t launch_convert(ibdvm_ctx *ctx, double *dense, long long c0, long long ncells, bool to_state);

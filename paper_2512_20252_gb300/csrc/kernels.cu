@@ -325,14 +325,16 @@ template <typename T, typename P = double> struct FinalArgs {
   int nchunk;
   int shift;
   double mu0, omega, Pr, dt;
+  int nblk;         // blocks of the finalize launch (residual partial sums)
+  double *res_out;  // residual of the step
 };
 
 template <typename T, int D, typename P>
-__global__ void __launch_bounds__(256) finalize_kernel(FinalArgs<T, P> A) {
+__device__ __forceinline__ void finalize_body(const FinalArgs<T, P> &A, const int blk) {
   constexpr int NM = Dims<D>::NM;
   constexpr int NW = Dims<D>::NW;
   __shared__ double red[2 * NW][8];
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long c = (long long)blk * blockDim.x + threadIdx.x;
   double rnum[NW], rden[NW];
 #pragma unroll
   for (int i = 0; i < NW; ++i) rnum[i] = rden[i] = 0.0;
@@ -428,15 +430,20 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs<T, P> A) {
     if (threadIdx.x < 2 * NW) {
       double s = 0.0;
       for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
-      A.resblk[(size_t)blockIdx.x * 2 * NW + threadIdx.x] = s;
+      A.resblk[(size_t)blk * 2 * NW + threadIdx.x] = s;
     }
   }
+}
+
+template <typename T, int D, typename P>
+__global__ void __launch_bounds__(256) finalize_kernel(FinalArgs<T, P> A) {
+  finalize_body<T, D, P>(A, blockIdx.x);
 }
 
 // res = max_i sqrt(sum_j dW_ij^2) / sum_j |W_ij| (Sec. 4), components with a
 // zero denominator skipped; one block, fixed summation order
 template <int NW>
-__global__ void residual_kernel(const double *__restrict__ resblk, int nblk, double *__restrict__ out) {
+__device__ __forceinline__ void residual_body(const double *__restrict__ resblk, int nblk, double *__restrict__ out) {
   __shared__ double sh[256];
   __shared__ double tot[2 * NW];
   for (int i = 0; i < 2 * NW; ++i) {
@@ -460,6 +467,11 @@ __global__ void residual_kernel(const double *__restrict__ resblk, int nblk, dou
     }
     *out = r;
   }
+}
+
+template <int NW>
+__global__ void residual_kernel(const double *__restrict__ resblk, int nblk, double *__restrict__ out) {
+  residual_body<NW>(resblk, nblk, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -522,10 +534,9 @@ __device__ __forceinline__ T preghost_slope(const GhostArgs<T> &G, int code_m, i
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256) ghost_band_kernel(GhostArgs<T> G) {
+__device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int l) {
   constexpr int NC = Dims<D>::NC;
   __shared__ double sh[16];
-  const int l = blockIdx.x;
   const int *li = G.l_int + 8 * l;
   const double *ld = G.l_dbl + 8 * l;
   const int donor = li[1], aux = li[2], s0 = li[6], s1 = li[7];
@@ -700,6 +711,11 @@ __global__ void __launch_bounds__(256) ghost_band_kernel(GhostArgs<T> G) {
   }
 }
 
+template <typename T, int D>
+__global__ void __launch_bounds__(256) ghost_band_kernel(GhostArgs<T> G) {
+  ghost_band_body<T, D>(G, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // forces: momentum and energy through the donor-ghost faces (FP64 sums)
 // ---------------------------------------------------------------------------
@@ -711,13 +727,14 @@ template <typename T> struct ForceArgs {
   const double *__restrict__ xiD;
   const double *__restrict__ wD;
   double *__restrict__ fpart; // [nlink][4]
+  int nlink;
+  double *__restrict__ dst;   // [4]: F_x, F_y, F_z, Q
 };
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256) forces_kernel(ForceArgs<T> A) {
+__device__ __forceinline__ void forces_body(const ForceArgs<T> &A, const int l) {
   constexpr int NC = Dims<D>::NC;
   __shared__ double sh[16];
-  const int l = blockIdx.x;
   const int *li = A.l_int + 8 * l;
   const int d = li[1], a = li[3], side = li[4];
   const int sf = -side; // face of the donor toward the ghost
@@ -760,7 +777,13 @@ __global__ void __launch_bounds__(256) forces_kernel(ForceArgs<T> A) {
   }
 }
 
-__global__ void forces_total_kernel(const double *__restrict__ fpart, int nlink, double *__restrict__ out) {
+template <typename T, int D>
+__global__ void __launch_bounds__(256) forces_kernel(ForceArgs<T> A) {
+  forces_body<T, D>(A, blockIdx.x);
+}
+
+__device__ __forceinline__ void forces_total_body(const double *__restrict__ fpart, int nlink,
+                                                  double *__restrict__ out) {
   __shared__ double sh[256];
   for (int i = 0; i < 4; ++i) {
     double s = 0.0;
@@ -774,6 +797,69 @@ __global__ void forces_total_kernel(const double *__restrict__ fpart, int nlink,
     if (threadIdx.x == 0) out[i] = sh[0];
     __syncthreads();
   }
+}
+
+__global__ void forces_total_kernel(const double *__restrict__ fpart, int nlink, double *__restrict__ out) {
+  forces_total_body(fpart, nlink, out);
+}
+
+// ---------------------------------------------------------------------------
+// grouped launches: one launch over the members of a batch.  Virtual block b
+// belongs to case c with start[c] <= b < start[c + 1]; every case has two
+// argument blocks, for the buffer parities after an even and an odd number of
+// steps, and the launch names the parity.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int group_case(const int *__restrict__ start, int ncase, int b) {
+  int lo = 0, hi = ncase - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) ghost_band_grouped(const GhostArgs<T> *__restrict__ tab,
+                                                          const int *__restrict__ start, int ncase, int par) {
+  __shared__ GhostArgs<T> sG;
+  const int c = group_case(start, ncase, blockIdx.x);
+  if (threadIdx.x == 0) sG = tab[2 * c + par];
+  __syncthreads();
+  ghost_band_body<T, D>(sG, blockIdx.x - __ldg(start + c));
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) forces_grouped(const ForceArgs<T> *__restrict__ tab,
+                                                      const int *__restrict__ start, int ncase, int par) {
+  __shared__ ForceArgs<T> sA;
+  const int c = group_case(start, ncase, blockIdx.x);
+  if (threadIdx.x == 0) sA = tab[2 * c + par];
+  __syncthreads();
+  forces_body<T, D>(sA, blockIdx.x - __ldg(start + c));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) forces_total_grouped(const ForceArgs<T> *__restrict__ tab, int par) {
+  const ForceArgs<T> &A = tab[2 * blockIdx.x + par];
+  forces_total_body(A.fpart, A.nlink, A.dst);
+}
+
+template <typename T, int D, typename P>
+__global__ void __launch_bounds__(256) finalize_grouped(const FinalArgs<T, P> *__restrict__ tab,
+                                                        const int *__restrict__ start, int ncase, int par) {
+  __shared__ FinalArgs<T, P> sA;
+  const int c = group_case(start, ncase, blockIdx.x);
+  if (threadIdx.x == 0) sA = tab[2 * c + par];
+  __syncthreads();
+  finalize_body<T, D, P>(sA, blockIdx.x - __ldg(start + c));
+}
+
+template <typename T, int D, typename P>
+__global__ void __launch_bounds__(256) residual_grouped(const FinalArgs<T, P> *__restrict__ tab, int par) {
+  const FinalArgs<T, P> &A = tab[2 * blockIdx.x + par];
+  residual_body<Dims<D>::NW>(A.resblk, A.nblk, A.res_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -813,10 +899,11 @@ __global__ void convert_kernel(T *__restrict__ state, double *__restrict__ dense
 // launch helpers
 // ---------------------------------------------------------------------------
 
-template <typename T> SweepArgs<T> sweep_args(ibdvm_ctx *ctx, int update, int shift = 1) {
+template <typename T> SweepArgs<T> sweep_args(const ibdvm_ctx *ctx, int update, int shift = 1, int cur = -1) {
+  if (cur < 0) cur = ctx->cur;
   SweepArgs<T> A{};
-  A.f = static_cast<const T *>(ctx->f[ctx->cur]);
-  A.fn = static_cast<T *>(ctx->f[1 - ctx->cur]);
+  A.f = static_cast<const T *>(ctx->f[cur]);
+  A.fn = static_cast<T *>(ctx->f[1 - cur]);
   A.mac = static_cast<const T *>(ctx->mac);
   A.xi = static_cast<const T *>(ctx->xiT);
   A.w = static_cast<const T *>(ctx->wT);
@@ -848,43 +935,53 @@ template <typename T, int D> cudaError_t sweep_t(ibdvm_ctx *ctx, int update, int
   return cudaGetLastError();
 }
 
-template <typename T, int D, typename P = double>
-cudaError_t finalize_t(ibdvm_ctx *ctx, bool shift, bool residual, const P *part = nullptr, int nchunk = 0) {
+// arguments of the finalize kernel for moment buffer parity wcur
+template <typename T, typename P>
+FinalArgs<T, P> final_args(const ibdvm_ctx *ctx, int wcur, bool shift, bool residual, const P *part, int nchunk) {
   FinalArgs<T, P> A{};
-  if constexpr (std::is_same<P, double>::value)
-    A.part = part ? part : ctx->part;
-  else
-    A.part = part;
+  A.part = part;
   A.mac = static_cast<T *>(ctx->mac);
-  A.Wold = residual ? ctx->W[ctx->wcur] : nullptr;
-  A.Wnew = ctx->W[1 - ctx->wcur];
+  A.Wold = residual ? ctx->W[wcur] : nullptr;
+  A.Wnew = ctx->W[1 - wcur];
   A.ctype = ctx->ctype;
   A.resblk = residual ? ctx->resblk : nullptr;
   A.flags = ctx->d_flags;
   A.ncell = ctx->ncell;
-  A.nchunk = nchunk ? nchunk : ctx->nchunk;
+  A.nchunk = nchunk;
   A.shift = shift ? 1 : 0;
   A.mu0 = ctx->geom.mu0;
   A.omega = ctx->geom.gas.omega_vhs;
   A.Pr = ctx->geom.gas.Pr;
   A.dt = ctx->geom.dt;
-  const int nblk = (int)((ctx->ncell + 255) / 256);
-  finalize_kernel<T, D, P><<<nblk, 256, 0, ctx->stream>>>(A);
+  A.nblk = (int)((ctx->ncell + 255) / 256);
+  A.res_out = ctx->d_res;
+  return A;
+}
+
+template <typename T, int D, typename P = double>
+cudaError_t finalize_t(ibdvm_ctx *ctx, bool shift, bool residual, const P *part = nullptr, int nchunk = 0) {
+  const P *pp;
+  if constexpr (std::is_same<P, double>::value)
+    pp = part ? part : ctx->part;
+  else
+    pp = part;
+  const FinalArgs<T, P> A = final_args<T, P>(ctx, ctx->wcur, shift, residual, pp, nchunk ? nchunk : ctx->nchunk);
+  finalize_kernel<T, D, P><<<A.nblk, 256, 0, ctx->stream>>>(A);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (residual) {
-    residual_kernel<Dims<D>::NW><<<1, 256, 0, ctx->stream>>>(ctx->resblk, nblk, ctx->d_res);
+    residual_kernel<Dims<D>::NW><<<1, 256, 0, ctx->stream>>>(ctx->resblk, A.nblk, ctx->d_res);
     e = cudaGetLastError();
   }
   ctx->wcur = 1 - ctx->wcur;
   return e;
 }
 
-template <typename T, int D> cudaError_t ghost_t(ibdvm_ctx *ctx, double *dbg) {
-  if (ctx->nlink == 0) return cudaSuccess;
+// arguments of the ghost-band kernel for state buffer parity cur
+template <typename T> GhostArgs<T> ghost_args(const ibdvm_ctx *ctx, int cur, double *dbg) {
   const Geom &g = ctx->geom;
   GhostArgs<T> G{};
-  G.f = static_cast<const T *>(ctx->f[ctx->cur]);
+  G.f = static_cast<const T *>(ctx->f[cur]);
   G.finf = static_cast<const T *>(ctx->finf);
   G.xiD = ctx->xiD;
   G.wD = ctx->wD;
@@ -915,20 +1012,32 @@ template <typename T, int D> cudaError_t ghost_t(ibdvm_ctx *ctx, double *dbg) {
   G.Tw = g.body.T_w;
   G.accom = g.body.accom_alpha;
   G.plain_average = (g.gas.flags & IBDVM_PLAIN_AVERAGE) ? 1 : 0;
-  ghost_band_kernel<T, D><<<ctx->nlink, 256, 0, ctx->stream>>>(G);
+  return G;
+}
+
+template <typename T, int D> cudaError_t ghost_t(ibdvm_ctx *ctx, double *dbg) {
+  if (ctx->nlink == 0) return cudaSuccess;
+  ghost_band_kernel<T, D><<<ctx->nlink, 256, 0, ctx->stream>>>(ghost_args<T>(ctx, ctx->cur, dbg));
   return cudaGetLastError();
 }
 
-template <typename T, int D> cudaError_t forces_t(ibdvm_ctx *ctx, double *dst) {
-  if (ctx->nlink == 0) return cudaMemsetAsync(dst, 0, 4 * sizeof(double), ctx->stream);
+// arguments of the force kernels for state buffer parity cur
+template <typename T> ForceArgs<T> force_args(const ibdvm_ctx *ctx, int cur, double *dst) {
   ForceArgs<T> A{};
-  A.S = sweep_args<T>(ctx, 0);
+  A.S = sweep_args<T>(ctx, 0, 1, cur);
   A.l_int = ctx->l_int;
   A.l_dbl = ctx->l_dbl;
   A.xiD = ctx->xiD;
   A.wD = ctx->wD;
   A.fpart = ctx->fpart;
-  forces_kernel<T, D><<<ctx->nlink, 256, 0, ctx->stream>>>(A);
+  A.nlink = ctx->nlink;
+  A.dst = dst;
+  return A;
+}
+
+template <typename T, int D> cudaError_t forces_t(ibdvm_ctx *ctx, double *dst) {
+  if (ctx->nlink == 0) return cudaMemsetAsync(dst, 0, 4 * sizeof(double), ctx->stream);
+  forces_kernel<T, D><<<ctx->nlink, 256, 0, ctx->stream>>>(force_args<T>(ctx, ctx->cur, dst));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   forces_total_kernel<<<1, 256, 0, ctx->stream>>>(ctx->fpart, ctx->nlink, dst);
@@ -1053,6 +1162,108 @@ cudaError_t launch_convert(ibdvm_ctx *ctx, double *dense, long long c0, long lon
   else
     convert_kernel<float><<<grid, 256, 0, ctx->stream>>>(static_cast<float *>(ctx->f[ctx->cur]), dense, c0,
                                                          ncells, ctx->nv, ctx->nvp, ctx->ncomp, to_state);
+  return cudaGetLastError();
+}
+
+} // namespace ibdvm
+
+// ---------------------------------------------------------------------------
+// grouped launches over the members of a batch
+// ---------------------------------------------------------------------------
+
+namespace ibdvm {
+
+namespace {
+template <typename T> cudaError_t upload_table(const std::vector<T> &h, void *&d, cudaStream_t s) {
+  cudaError_t e = cudaMalloc(&d, std::max<size_t>(h.size(), 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (h.empty()) return cudaSuccess;
+  return cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+} // namespace
+
+void group_free(GroupTables &t) {
+  void *ps[] = {t.ghost, t.force, t.fin, t.link_start, t.fin_start};
+  for (void *p : ps)
+    if (p) cudaFree(p);
+  t = GroupTables{};
+}
+
+cudaError_t group_build(const std::vector<ibdvm_ctx *> &cases, const std::vector<int> &nchunk, double *res,
+                        int *flags, double *forces, GroupTables &t, cudaStream_t s) {
+  group_free(t);
+  const int n = static_cast<int>(cases.size());
+  t.ncase = n;
+  t.dim = n ? cases[0]->dim : 2;
+  std::vector<int> ls(n + 1, 0), fs(n + 1, 0);
+  std::vector<GhostArgs<float>> g(2 * n);
+  std::vector<ForceArgs<float>> fa(2 * n);
+  std::vector<FinalArgs<float, float>> fi(2 * n);
+  for (int i = 0; i < n; ++i) {
+    const ibdvm_ctx *ctx = cases[i];
+    ls[i + 1] = ls[i] + ctx->nlink;
+    fs[i + 1] = fs[i] + static_cast<int>((ctx->ncell + 255) / 256);
+    for (int p = 0; p < 2; ++p) {
+      g[2 * i + p] = ghost_args<float>(ctx, ctx->cur ^ p, nullptr);
+      fa[2 * i + p] = force_args<float>(ctx, ctx->cur ^ p, forces + 4 * i);
+      FinalArgs<float, float> A = final_args<float, float>(ctx, ctx->wcur ^ p, true, true, ctx->partf, nchunk[i]);
+      A.flags = flags + i;
+      A.res_out = res + i;
+      fi[2 * i + p] = A;
+    }
+  }
+  t.link_blocks = ls[n];
+  t.fin_blocks = fs[n];
+  cudaError_t e;
+  if ((e = upload_table(g, t.ghost, s)) != cudaSuccess) return e;
+  if ((e = upload_table(fa, t.force, s)) != cudaSuccess) return e;
+  if ((e = upload_table(fi, t.fin, s)) != cudaSuccess) return e;
+  void *p0 = nullptr, *p1 = nullptr;
+  if ((e = upload_table(ls, p0, s)) != cudaSuccess) return e;
+  t.link_start = static_cast<int *>(p0);
+  if ((e = upload_table(fs, p1, s)) != cudaSuccess) return e;
+  t.fin_start = static_cast<int *>(p1);
+  return cudaStreamSynchronize(s); // the host tables go out of scope
+}
+
+cudaError_t group_ghost(const GroupTables &t, int par, cudaStream_t s) {
+  if (t.link_blocks == 0) return cudaSuccess;
+  const auto *tab = static_cast<const GhostArgs<float> *>(t.ghost);
+  if (t.dim == 2)
+    ghost_band_grouped<float, 2><<<t.link_blocks, 256, 0, s>>>(tab, t.link_start, t.ncase, par);
+  else
+    ghost_band_grouped<float, 3><<<t.link_blocks, 256, 0, s>>>(tab, t.link_start, t.ncase, par);
+  return cudaGetLastError();
+}
+
+cudaError_t group_forces(const GroupTables &t, int par, cudaStream_t s) {
+  if (t.ncase == 0) return cudaSuccess;
+  const auto *tab = static_cast<const ForceArgs<float> *>(t.force);
+  if (t.link_blocks > 0) {
+    if (t.dim == 2)
+      forces_grouped<float, 2><<<t.link_blocks, 256, 0, s>>>(tab, t.link_start, t.ncase, par);
+    else
+      forces_grouped<float, 3><<<t.link_blocks, 256, 0, s>>>(tab, t.link_start, t.ncase, par);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  forces_total_grouped<float><<<t.ncase, 256, 0, s>>>(tab, par);
+  return cudaGetLastError();
+}
+
+cudaError_t group_finalize(const GroupTables &t, int par, cudaStream_t s) {
+  if (t.ncase == 0) return cudaSuccess;
+  const auto *tab = static_cast<const FinalArgs<float, float> *>(t.fin);
+  if (t.dim == 2)
+    finalize_grouped<float, 2, float><<<t.fin_blocks, 256, 0, s>>>(tab, t.fin_start, t.ncase, par);
+  else
+    finalize_grouped<float, 3, float><<<t.fin_blocks, 256, 0, s>>>(tab, t.fin_start, t.ncase, par);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (t.dim == 2)
+    residual_grouped<float, 2, float><<<t.ncase, 256, 0, s>>>(tab, par);
+  else
+    residual_grouped<float, 3, float><<<t.ncase, 256, 0, s>>>(tab, par);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,9 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "ctx.h"
 
@@ -85,6 +87,9 @@ __device__ __forceinline__ unsigned smem_addr(const void *p) {
 }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -425,12 +430,15 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
   return true;
 }
 
+// The march of one block over columns [x0, x0 + TX), chunk velocities
+// [k0, k0 + KC) and rows [y0, y1).  reinit: the block's mbarriers hold an
+// earlier march (all of whose copies have landed) and are invalidated first.
+// Returns false when the block aborted on a timed-out wait.
 template <int KPT>
-__global__ void __launch_bounds__(NTHREADS, 2) sweep2d_tma_kernel(const __grid_constant__ CUtensorMap tmf,
-                                                                  TmaArgs A) {
+__device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf, int x0, int k0, int y0, int y1,
+                                        unsigned char *smem_raw, bool reinit) {
   using C = Cfg<KPT>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  March<KPT> M{A, &tmf};
+  March<KPT> M{A, tmf};
   M.stage = reinterpret_cast<float *>(smem_raw);
   M.phix = M.stage + NST * C::STAGE_FLOATS;
   M.sfinf = M.phix + 2 * C::PHI_FLOATS;
@@ -439,10 +447,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) sweep2d_tma_kernel(const __grid_c
   M.full = reinterpret_cast<uint64_t *>(M.smac + 2 * TX * kMac);
   M.warp = threadIdx.x >> 5;
   M.lane = threadIdx.x & 31;
-  M.x0 = blockIdx.x * TX;
-  M.k0 = blockIdx.y * C::KC;
-  M.y0 = blockIdx.z * A.rows;
-  M.y1 = min(A.ny, M.y0 + A.rows);
+  M.x0 = x0;
+  M.k0 = k0;
+  M.y0 = y0;
+  M.y1 = y1;
   M.ylast = min(A.ny, M.y1 + 2); // rows this block reads: [y0, ylast)
   M.x = M.x0 + M.warp;
   M.col_in = M.x < A.nx;
@@ -470,7 +478,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) sweep2d_tma_kernel(const __grid_c
   for (int i = threadIdx.x; i < C::KC2; i += NTHREADS) M.sfinf[i] = A.finf[2 * M.k0 + i];
   for (int i = threadIdx.x; i < C::KC; i += NTHREADS) M.sxi[i] = A.xi[M.k0 + i];
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) mbar_init(&M.full[s], 1);
+    for (int s = 0; s < NST; ++s) {
+      if (reinit) mbar_inval(&M.full[s]);
+      mbar_init(&M.full[s], 1);
+    }
     fence_mbar_init();
   }
   __syncthreads();
@@ -526,6 +537,51 @@ __global__ void __launch_bounds__(NTHREADS, 2) sweep2d_tma_kernel(const __grid_c
       const int j = r - M.y0;
       mbar_wait(&M.full[j % NST], (j / NST) & 1);
     }
+  }
+  return ok;
+}
+
+template <int KPT>
+__global__ void __launch_bounds__(NTHREADS, 2) sweep2d_tma_kernel(const __grid_constant__ CUtensorMap tmf,
+                                                                  TmaArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int y0 = blockIdx.z * A.rows;
+  march2d<KPT>(A, &tmf, blockIdx.x * TX, blockIdx.y * Cfg<KPT>::KC, y0, min(A.ny, y0 + A.rows), smem_raw, false);
+}
+
+// One item of the batched sweep: a march of one member case.
+struct WorkItem {
+  int cas;    // member index
+  int x0, k0; // first column and first chunk velocity
+  int y0, y1; // rows
+  int kpt;    // velocities per lane (2 or 4)
+  int pad[2];
+};
+
+// The batched sweep: a persistent grid whose blocks take work items in order
+// from a shared counter (items sorted by decreasing size).  Member c at step
+// parity par uses args[2 c + par] and tmaps[2 c + par].
+__global__ void __launch_bounds__(NTHREADS, 2)
+    sweep2d_tma_batch_kernel(const TmaArgs *__restrict__ args, const CUtensorMap *__restrict__ tmaps,
+                             const WorkItem *__restrict__ items, int nitems, int *__restrict__ next, int par) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ TmaArgs sA;
+  __shared__ int s_item;
+  bool reinit = false;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int i = s_item;
+    if (i >= nitems) break;
+    const WorkItem it = items[i];
+    if (threadIdx.x == 0) sA = args[2 * it.cas + par];
+    __syncthreads();
+    const CUtensorMap *tm = tmaps + 2 * it.cas + par;
+    const bool ok = (it.kpt == 4) ? march2d<4>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit)
+                                  : march2d<2>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
+    if (!ok) break; // uniform: the abort vote is block-wide
+    reinit = true;
+    __syncthreads(); // the item's shared memory and arguments are released
   }
 }
 
@@ -609,6 +665,125 @@ cudaError_t tma_sweep_launch(ibdvm_ctx *ctx) {
     sweep2d_tma_kernel<4><<<grid, NTHREADS, Cfg<4>::SMEM, ctx->stream>>>(*tm, A);
   else
     sweep2d_tma_kernel<2><<<grid, NTHREADS, Cfg<2>::SMEM, ctx->stream>>>(*tm, A);
+  return cudaGetLastError();
+}
+
+bool tma_batch_member_ok(const ibdvm_ctx *ctx) {
+  return ctx->dim == 2 && ctx->precision == IBDVM_MIXED && (ctx->nvp % 64) == 0 && ctx->partf != nullptr &&
+         encoder() != nullptr;
+}
+
+int tma_batch_kpt_max(const ibdvm_ctx *ctx) { return (ctx->nvp % 128 == 0) ? 4 : 2; }
+
+void tma_batch_free(SweepTables &t) {
+  void *ps[] = {t.args, t.tmaps, t.items, t.next};
+  for (void *p : ps)
+    if (p) cudaFree(p);
+  t = SweepTables{};
+}
+
+cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::vector<int> &kpt, int rows,
+                            int *flags, SweepTables &t, cudaStream_t s) {
+  tma_batch_free(t);
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const int n = static_cast<int>(cases.size());
+  std::vector<TmaArgs> args(2 * n);
+  std::vector<CUtensorMap> maps(2 * n);
+  std::vector<WorkItem> items;
+  for (int i = 0; i < n; ++i) {
+    const ibdvm_ctx *ctx = cases[i];
+    const int kc = 32 * kpt[i];
+    for (int p = 0; p < 2; ++p) {
+      const int cur = ctx->cur ^ p;
+      TmaArgs &A = args[2 * i + p];
+      A = TmaArgs{};
+      A.f = static_cast<const float *>(ctx->f[cur]);
+      A.fn = static_cast<float *>(ctx->f[1 - cur]);
+      A.mac = static_cast<const float *>(ctx->mac);
+      A.xi = static_cast<const float *>(ctx->xiT);
+      A.w = static_cast<const float *>(ctx->wT);
+      A.finf = static_cast<const float *>(ctx->finf);
+      A.cmask = ctx->cmask;
+      A.dslot = ctx->dslot;
+      A.dlinks = ctx->dlinks;
+      A.lval = static_cast<const float *>(ctx->lval);
+      A.part = ctx->partf;
+      A.err = flags + i;
+      A.ncell = ctx->ncell;
+      A.nx = ctx->geom.n[0];
+      A.ny = ctx->geom.n[1];
+      A.nvp = ctx->nvp;
+      A.nv = ctx->nv;
+      A.rows = 0;
+      A.dt = (float)ctx->geom.dt;
+      A.rdx = (float)(1.0 / ctx->geom.dx[0]);
+      A.rdy = (float)(1.0 / ctx->geom.dx[1]);
+      cuuint64_t dims[3] = {(cuuint64_t)ctx->nvp * 2, (cuuint64_t)A.nx, (cuuint64_t)A.ny};
+      cuuint64_t strides[2] = {(cuuint64_t)ctx->nvp * 2 * 4, (cuuint64_t)A.nx * ctx->nvp * 2 * 4};
+      cuuint32_t box[3] = {(cuuint32_t)(2 * kc), (cuuint32_t)COLS, 1};
+      cuuint32_t estr[3] = {1, 1, 1};
+      CUresult r = enc(&maps[2 * i + p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ctx->f[cur], dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    // items: column strips x velocity chunks x row ranges of about `rows` rows
+    const int nx = ctx->geom.n[0], ny = ctx->geom.n[1];
+    const int nrb = (rows <= 0 || rows >= ny) ? 1 : (ny + rows - 1) / rows;
+    const int per = (ny + nrb - 1) / nrb;
+    for (int x0 = 0; x0 < nx; x0 += TX)
+      for (int k0 = 0; k0 < ctx->nvp; k0 += kc)
+        for (int y0 = 0; y0 < ny; y0 += per) {
+          WorkItem it{};
+          it.cas = i;
+          it.x0 = x0;
+          it.k0 = k0;
+          it.y0 = y0;
+          it.y1 = std::min(ny, y0 + per);
+          it.kpt = kpt[i];
+          items.push_back(it);
+        }
+  }
+  // largest items first, so the last items to start are the short ones
+  std::stable_sort(items.begin(), items.end(), [](const WorkItem &a, const WorkItem &b) {
+    return (long long)(a.y1 - a.y0) * a.kpt > (long long)(b.y1 - b.y0) * b.kpt;
+  });
+  cudaError_t e;
+  auto up = [&](const void *h, size_t bytes, void *&d) -> cudaError_t {
+    cudaError_t r = cudaMalloc(&d, std::max<size_t>(bytes, 16));
+    if (r != cudaSuccess || bytes == 0) return r;
+    return cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s);
+  };
+  if ((e = up(args.data(), args.size() * sizeof(TmaArgs), t.args)) != cudaSuccess) return e;
+  if ((e = up(maps.data(), maps.size() * sizeof(CUtensorMap), t.tmaps)) != cudaSuccess) return e;
+  if ((e = up(items.data(), items.size() * sizeof(WorkItem), t.items)) != cudaSuccess) return e;
+  void *nx = nullptr;
+  if ((e = cudaMalloc(&nx, sizeof(int))) != cudaSuccess) return e;
+  t.next = static_cast<int *>(nx);
+  t.nitems = static_cast<int>(items.size());
+  const int smem = (int)std::max(Cfg<4>::SMEM, Cfg<2>::SMEM);
+  if ((e = cudaFuncSetAttribute(sweep2d_tma_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+      cudaSuccess)
+    return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep2d_tma_batch_kernel, NTHREADS, smem)) !=
+      cudaSuccess)
+    return e;
+  t.grid = std::max(1, std::min(t.nitems, nsm * std::max(per_sm, 1)));
+  return cudaStreamSynchronize(s); // the host tables go out of scope
+}
+
+cudaError_t tma_batch_launch(const SweepTables &t, int par, cudaStream_t s) {
+  if (t.nitems == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(t.next, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int smem = (int)std::max(Cfg<4>::SMEM, Cfg<2>::SMEM);
+  sweep2d_tma_batch_kernel<<<t.grid, NTHREADS, smem, s>>>(
+      static_cast<const TmaArgs *>(t.args), static_cast<const CUtensorMap *>(t.tmaps),
+      static_cast<const WorkItem *>(t.items), t.nitems, t.next, par);
   return cudaGetLastError();
 }
 

@@ -61,6 +61,11 @@ class BodyDesc(ctypes.Structure):
                 ("U_w", ctypes.c_double * 3), ("L_ref", ctypes.c_double)]
 
 
+class BatchTiling(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int), ("kpt", ctypes.c_int), ("nitems", ctypes.c_int),
+                ("grid", ctypes.c_int), ("graphs", ctypes.c_int)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("ncomp", ctypes.c_int), ("ncell", ctypes.c_longlong),
                 ("nfluid", ctypes.c_longlong), ("nvel", ctypes.c_int), ("nvel_padded", ctypes.c_int),
@@ -110,6 +115,21 @@ SIGNATURES = {
     "ibdvm_geom_dt": ([_V], ctypes.c_double),
     "ibdvm_geom_destroy": ([_V], None),
     "ibdvm_geom_last_error": ([], ctypes.c_char_p),
+    "ibdvm_batch_create": ([_V, ctypes.POINTER(_V)], _S),
+    "ibdvm_batch_add": ([_V, _V], _S),
+    "ibdvm_batch_remove": ([_V, _V], _S),
+    "ibdvm_batch_size": ([_V], ctypes.c_int),
+    "ibdvm_batch_member": ([_V, ctypes.c_int], _V),
+    "ibdvm_batch_step": ([_V, ctypes.c_int, _D, _I], _S),
+    "ibdvm_batch_forces": ([_V, _D, _D, _D, _D], _S),
+    "ibdvm_batch_set_tiling": ([_V, ctypes.c_int, ctypes.c_int], _S),
+    "ibdvm_batch_get_tiling": ([_V, ctypes.POINTER(BatchTiling)], _S),
+    "ibdvm_batch_tune": ([_V, ctypes.c_int, _D], _S),
+    "ibdvm_batch_set_profiling": ([_V, ctypes.c_int], _S),
+    "ibdvm_batch_get_kernel_times": ([_V, _D, _LL], _S),
+    "ibdvm_batch_reset_kernel_times": ([_V], _S),
+    "ibdvm_batch_destroy": ([_V], None),
+    "ibdvm_batch_last_error": ([_V], ctypes.c_char_p),
 }
 
 _lock = threading.Lock()
@@ -417,3 +437,91 @@ class Solver:
 
     def geometry(self) -> Geometry:
         return Geometry._borrow(self.lib, self.lib.ibdvm_get_geom(self.h))
+
+
+class Batch:
+    """A batch of 2D FP32 solvers advanced by grouped launches (C-ABI handle).
+
+    Holds references to its member Solvers; members join and leave between
+    steps (continuous batching)."""
+
+    KERNEL_CLASSES = Solver.KERNEL_CLASSES
+
+    def __init__(self, stream: int | None = None):
+        self.lib = load()
+        h = _V()
+        st = self.lib.ibdvm_batch_create(_V(stream or 0), ctypes.byref(h))
+        if st != OK:
+            raise IbdvmError(st, "ibdvm_batch_create failed")
+        self.h = h
+        self.members: list[Solver] = []
+
+    def _check(self, st):
+        if st != OK:
+            raise IbdvmError(st, self.lib.ibdvm_batch_last_error(self.h).decode())
+        return st
+
+    def add(self, solver: Solver):
+        self._check(self.lib.ibdvm_batch_add(self.h, solver.h))
+        self.members.append(solver)
+
+    def remove(self, solver: Solver):
+        self._check(self.lib.ibdvm_batch_remove(self.h, solver.h))
+        self.members = [m for m in self.members if m is not solver]
+
+    def __len__(self):
+        return len(self.members)
+
+    def step(self, nsteps: int = 1, check: bool = True):
+        """Advances every member; returns (residuals, statuses) per member."""
+        n = len(self.members)
+        res = np.zeros(max(n, 1))
+        sts = np.zeros(max(n, 1), dtype=np.int32)
+        st = self.lib.ibdvm_batch_step(self.h, int(nsteps), _dp(res), sts.ctypes.data_as(_I))
+        if check:
+            self._check(st)
+        return res[:n], sts[:n]
+
+    def forces(self):
+        n = max(len(self.members), 1)
+        F, Q, CD, CL = np.zeros((n, 3)), np.zeros(n), np.zeros(n), np.zeros(n)
+        self._check(self.lib.ibdvm_batch_forces(self.h, _dp(F), _dp(Q), _dp(CD), _dp(CL)))
+        m = len(self.members)
+        return F[:m], Q[:m], CD[:m], CL[:m]
+
+    def set_tiling(self, rows: int = 0, kpt: int = 0):
+        self._check(self.lib.ibdvm_batch_set_tiling(self.h, int(rows), int(kpt)))
+
+    def tiling(self):
+        t = BatchTiling()
+        self._check(self.lib.ibdvm_batch_get_tiling(self.h, ctypes.byref(t)))
+        return {k: getattr(t, k) for k, _ in BatchTiling._fields_}
+
+    def tune(self, steps_per_trial: int = 4) -> float:
+        best = ctypes.c_double(0.0)
+        self._check(self.lib.ibdvm_batch_tune(self.h, int(steps_per_trial), ctypes.byref(best)))
+        return best.value
+
+    def set_profiling(self, on: bool = True):
+        self._check(self.lib.ibdvm_batch_set_profiling(self.h, 1 if on else 0))
+
+    def kernel_times(self):
+        ms = np.zeros(8)
+        n = np.zeros(8, dtype=np.int64)
+        self._check(self.lib.ibdvm_batch_get_kernel_times(self.h, _dp(ms), n.ctypes.data_as(_LL)))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def reset_kernel_times(self):
+        self._check(self.lib.ibdvm_batch_reset_kernel_times(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ibdvm_batch_destroy(self.h)
+            self.h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
