@@ -38,6 +38,7 @@ WORKLOADS = {
     "cylinder_48": lambda p: dict(__import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).cylinder_48(),
                                   precision=p),
     "batched_2d": None,  # a list of cases: see bench_batch
+    "served": None,      # a request stream: see bench_serve
 }
 DESCRIPTIONS = {
     "cylinder_512": "2D cylinder r=0.5, 512x512 cells on [-8,8]^2, 48x48 trapezoid velocities on [-6,6]^2, Kn=0.1, Ma=0.5",
@@ -46,6 +47,8 @@ DESCRIPTIONS = {
     "batched_2d": "64 seeded 2D cases (seed 0): n ~ U{64..384} cells per axis on [-4,4]^2, m ~ U{16..40} "
                   "velocities per axis on [-6,6]^2, circle / ellipse (aspect U[1,3]) / NACA0012 (AoA U[0,10] deg), "
                   "Kn 10^U[-2,0], Ma U[0.1,0.8], mixed precision, one batch",
+    "served": "Poisson request stream (seed 0, 20 requests/s): 80% 2D cases shaped like the batched workload, "
+              "20% 3D spheres with 32..64 cells and 12..20 velocities per axis; continuous batching by HBM budget",
 }
 
 
@@ -65,6 +68,11 @@ def parse():
     ap.add_argument("--ncases", type=int, default=64, help="batched_2d: number of cases")
     ap.add_argument("--tune-steps", type=int, default=4,
                     help="batched_2d: steps per autotuner trial (0 = no tuning)")
+    ap.add_argument("--nreq", type=int, default=8, help="served: number of requests")
+    ap.add_argument("--serve-tol", type=float, default=1e-6, help="served: residual target")
+    ap.add_argument("--serve-max-steps", type=int, default=200, help="served: step cap per request")
+    ap.add_argument("--serve-round", type=int, default=20, help="served: steps per scheduling round")
+    ap.add_argument("--no-fp64-serve", action="store_true", help="served: skip the sequential FP64 form")
     ap.add_argument("--error-report", type=int, default=0, metavar="STEPS",
                     help="instead of timing: run the workload STEPS steps in the mixed and the FP64 "
                          "GPU paths and print the relative differences of W, C_D, C_L, Q and the residual")
@@ -195,7 +203,14 @@ def time_oracle(case: dict, budget_s: float, max_steps: int | None = None):
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    case = batch_cases(args)[0] if args.workload == "batched_2d" else WORKLOADS[args.workload](args.precision)
+    if args.workload == "batched_2d":
+        case = batch_cases(args)[0]
+    elif args.workload == "served":
+        from paper_2512_20252_gb300 import workloads
+
+        case = workloads.served_stream(0, nreq=1)[0][1]
+    else:
+        case = WORKLOADS[args.workload](args.precision)
     sample = cpu_sample_case(case)
     import oracle
 
@@ -388,6 +403,84 @@ def bench_batch(args, world, rank, local, pg):
     return 0
 
 
+def serve_stream(server, stream):
+    """Drives a server with arrivals at their times; returns per-request
+    (arrival, result) with times on the server's clock."""
+    t_start = server.clock()
+    pending = list(stream)
+    ids = []
+    active = queued = 0
+    while pending or active or queued:
+        now = server.clock() - t_start
+        while pending and pending[0][0] <= now:
+            t_arr, case = pending.pop(0)
+            ids.append((t_arr, server.submit(case)))
+        if not active and not queued and pending:
+            time.sleep(max(0.0, pending[0][0] - (server.clock() - t_start)))
+            continue
+        active, queued, _ = server.poll()
+    return [(t_start + t_arr, server.result(i)) for t_arr, i in ids]
+
+
+def latency_stats(rows):
+    import numpy as np
+
+    lat = np.array([r["t_done"] - t for t, r in rows])
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "max_s": float(lat.max())}
+
+
+def bench_serve(args, rank):
+    """Serving: the request stream through the batched server and, on the same
+    stream, through the plain form (one request at a time, FP64 path)."""
+    import numpy as np
+
+    from paper_2512_20252_gb300 import ibdvm
+    from paper_2512_20252_gb300 import workloads
+
+    stream = workloads.served_stream(0, nreq=args.nreq, rate=20.0)
+
+    def pairs_of(case):
+        import math
+
+        return math.prod(case["n"]) * math.prod(case["nv"])
+
+    out = {}
+    forms = [("batched_mixed", False)] + ([] if args.no_fp64_serve else [("sequential_fp64", True)])
+    for name, seq in forms:
+        srv = ibdvm.Server(tol=args.serve_tol, max_steps=args.serve_max_steps, steps_per_round=args.serve_round,
+                           sequential_fp64=seq)
+        t0 = srv.clock()
+        rows = serve_stream(srv, stream)
+        t1 = max(r["t_done"] for _, r in rows)
+        srv.close()
+        work = sum(pairs_of(c) * r["steps"] for (_, c), (_, r) in zip(stream, rows))
+        out[name] = dict(latency_stats(rows), makespan_s=t1 - t0, throughput=work / (t1 - t0),
+                         converged=int(sum(r["status"] == 0 for _, r in rows)),
+                         capped=int(sum(r["status"] == 6 for _, r in rows)),
+                         failed=int(sum(r["status"] not in (0, 6) for _, r in rows)),
+                         steps=[int(r["steps"]) for _, r in rows],
+                         CD=[float(r["CD"]) for _, r in rows], Q=[float(r["Q"]) for _, r in rows])
+    b = out["batched_mixed"]
+    line = {"metric": "served p50/p99 time-to-converge (s); throughput in cell-velocity updates/s",
+            "value": b["throughput"], "unit": "cell-velocity updates/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "latency_p50_s": b["p50_s"], "latency_p99_s": b["p99_s"],
+            "config": {"workload": DESCRIPTIONS["served"], "requests": args.nreq, "tol": args.serve_tol,
+                       "max_steps": args.serve_max_steps, "steps_per_round": args.serve_round,
+                       "offered_load_rps": 20.0, "work": "all cells x velocities x steps"},
+            "forms": out}
+    if "sequential_fp64" in out:
+        f = out["sequential_fp64"]
+        line["vs_sequential_fp64"] = {"throughput_ratio": b["throughput"] / f["throughput"],
+                                      "p99_ratio": f["p99_s"] / b["p99_s"],
+                                      "CD_max_rel_err": max(abs(x - y) / max(abs(y), 1e-300)
+                                                            for x, y in zip(b["CD"], f["CD"]))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args.gpus)
@@ -416,8 +509,8 @@ def main():
     torch.cuda.set_device(local)
     from paper_2512_20252_gb300 import ibdvm
 
-    if args.workload == "batched_2d":
-        rc = bench_batch(args, world, rank, local, pg)
+    if args.workload in ("batched_2d", "served"):
+        rc = bench_batch(args, world, rank, local, pg) if args.workload == "batched_2d" else bench_serve(args, rank)
         if pg:
             pg.barrier()
             pg.destroy_process_group()

@@ -235,32 +235,36 @@ const char *ibdvm_last_error(const ibdvm_ctx *ctx);
 const char *ibdvm_status_string(ibdvm_status s);
 
 /* ------------------------------------------------------------------------
- * Batched form: many 2D cases of uneven size advanced together.  The paper
+ * Batched form: many cases of uneven size advanced together.  The paper
  * solves one case at a time; batching changes no arithmetic.  A member's
  * step is the one ibdvm_step takes (the same kernel bodies), launched for all
  * members at once:
  *   - one grouped ghost-band launch over every member's links (Sec. 3.2);
  *   - one grouped force launch, plus one block per member for the totals;
  *   - one persistent transport / relaxation / moment sweep (Sec. 2.2, Sec. 4)
- *     over a packed work list of (member, 8-column strip, velocity chunk, row
- *     range) items, largest first, which the blocks take from a device counter;
+ *     over a packed work list of items, largest first, which the blocks take
+ *     from a device counter: (member, 8-column strip, velocity chunk, row
+ *     range) in 2D, (member, 4 x 4 column tile, 128-velocity chunk, plane
+ *     range) in 3D;
  *   - one grouped finalize launch, plus one block per member for its residual.
  * Pairs of steps replay captured CUDA graphs.
  *
- * Members are 2D contexts in FP32 storage (IBDVM_MIXED) with the TMA sweep
- * (ibdvm_info.sweep_variant == 1), bound to the batch's stream.  A batch
- * references its members and does not own them; a context belongs to at most
- * one batch, and ibdvm_destroy takes a member out of its batch.  Members can be
- * added and removed between steps (continuous batching): a change of
- * membership, of a member's body or of the tiling rebuilds the batch's device
- * tables (small uploads, synchronous) and drops its graphs.  Not thread-safe.
+ * Members are contexts in FP32 storage (IBDVM_MIXED) with the TMA sweep
+ * (ibdvm_info.sweep_variant 1 in 2D, 2 in 3D), all of one dimension, bound to
+ * the batch's stream.  A batch references its members and does not own them;
+ * a context belongs to at most one batch, and ibdvm_destroy takes a member
+ * out of its batch.  Members can be added and removed between steps
+ * (continuous batching): a change of membership, of a member's body or of the
+ * tiling rebuilds the batch's device tables (small uploads, synchronous) and
+ * drops its graphs.  Not thread-safe.
  * ------------------------------------------------------------------------ */
 typedef struct ibdvm_batch ibdvm_batch;
 
 /* Errors: IBDVM_E_INVAL (out is NULL), IBDVM_E_NOMEM. */
 ibdvm_status ibdvm_batch_create(void *cuda_stream, ibdvm_batch **out);
-/* Appends ctx.  Errors: IBDVM_E_INVAL (NULL, not 2D FP32 with the TMA sweep,
-   or bound to another stream), IBDVM_E_STATE (already a member of a batch). */
+/* Appends ctx.  Errors: IBDVM_E_INVAL (NULL, not FP32 with the TMA sweep,
+   another dimension than the members, or bound to another stream),
+   IBDVM_E_STATE (already a member of a batch). */
 ibdvm_status ibdvm_batch_add(ibdvm_batch *b, ibdvm_ctx *ctx);
 /* Removes ctx; later members move up one place.  Errors: IBDVM_E_INVAL (not a
    member of b). */
@@ -285,10 +289,11 @@ ibdvm_status ibdvm_batch_step(ibdvm_batch *b, int nsteps, double *residuals, int
    batch last rebuilt its tables (a change of membership, body or tiling). */
 ibdvm_status ibdvm_batch_forces(ibdvm_batch *b, double *F, double *Q, double *CD, double *CL);
 
-/* Tiling of the sweep's work items.  rows: target rows per item (0 = whole
-   columns); kpt: velocities per lane, 4 (chunks of 128 velocities where the
-   member's padded velocity count is a multiple of 128, else 64), 2 (chunks of
-   64) or 0 (= 4).  get_tiling also reports the number of work items, the
+/* Tiling of the sweep's work items.  rows: target rows (3D: planes) per item
+   (0 = whole columns); kpt: velocities per lane in 2D, 4 (chunks of 128
+   velocities where the member's padded velocity count is a multiple of 128,
+   else 64), 2 (chunks of 64) or 0 (= 4); 3D members always take chunks of
+   128.  get_tiling also reports the number of work items, the
    persistent grid and whether graphs are in use. */
 typedef struct {
   int rows, kpt, nitems, grid, graphs;
@@ -297,10 +302,10 @@ ibdvm_status ibdvm_batch_set_tiling(ibdvm_batch *b, int rows, int kpt);
 ibdvm_status ibdvm_batch_get_tiling(const ibdvm_batch *b, ibdvm_batch_tiling *out);
 
 /* Autotuner: for each candidate tiling (rows in {16, 32, 64, 128, whole
-   columns} x kpt in {4, 2}) times steps_per_trial batched steps (even,
-   >= 2) with CUDA events on the batch's stream, after one untimed pair of
-   steps, and keeps the fastest.  The trials are real steps: every member
-   advances 10 x (steps_per_trial + 2) steps.  best_ms (nullable) receives
+   columns} x kpt in {4, 2}; 3D: kpt 4 only) times steps_per_trial batched
+   steps (even, >= 2) with CUDA events on the batch's stream, after one
+   untimed pair of steps, and keeps the fastest.  The trials are real steps:
+   every member advances 10 x (steps_per_trial + 2) steps (3D: 5 x).  best_ms (nullable) receives
    the kept tiling's time per step.  Errors: as ibdvm_batch_step;
    IBDVM_E_INVAL for a bad steps_per_trial; IBDVM_E_STATE with no members. */
 ibdvm_status ibdvm_batch_tune(ibdvm_batch *b, int steps_per_trial, double *best_ms);
@@ -314,6 +319,67 @@ ibdvm_status ibdvm_batch_reset_kernel_times(ibdvm_batch *b);
 /* Releases the batch's tables and graphs; the members stay valid. */
 void ibdvm_batch_destroy(ibdvm_batch *b);
 const char *ibdvm_batch_last_error(const ibdvm_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop over many solves.  Requests (a case: grid,
+ * velocity grid, gas, body) are queued on submission and admitted first come
+ * first served while the device bytes of the admitted cases stay within an
+ * HBM budget; each admitted request is a context in FP32 storage that joins a
+ * batch (one for 2D, one for 3D cases, on two streams, so their launches
+ * overlap on the device); every poll advances all admitted requests by a
+ * round of steps, then retires those whose residual (Sec. 4 criterion) is
+ * below the tolerance, those that failed and those that reached the step cap,
+ * with the surface force and heat flux of their last state (ibdvm_forces),
+ * and frees their memory for the queue.  A request's result does not depend on
+ * the other requests (a member of a batch steps as it would alone).
+ * sequential_fp64 = 1 gives the plain form for comparison: one request at a
+ * time, in the FP64 path, without batching.  Not thread-safe.
+ * ------------------------------------------------------------------------ */
+typedef struct ibdvm_server ibdvm_server;
+
+typedef struct {
+  double tol;            /* residual below which a request is done (e.g. 1e-6) */
+  long long max_steps;   /* a request still above tol after max_steps ends with IBDVM_E_NOTCONVERGED */
+  int steps_per_round;   /* steps per poll between convergence checks (even, >= 2) */
+  size_t hbm_budget;     /* device bytes the admitted cases may hold; 0 = 90% of the free memory at creation */
+  int max_active;        /* requests on the device at once; 0 = no cap */
+  int sequential_fp64;   /* 1: one request at a time in the FP64 path (the plain form) */
+} ibdvm_server_desc;
+
+typedef struct {
+  long long id;
+  int done;              /* 1 when the request has left the device */
+  int status;            /* IBDVM_OK (converged), IBDVM_E_NOTCONVERGED (step cap), or the error */
+  long long steps;       /* steps taken */
+  double residual;       /* residual of the last step */
+  double F[3], Q, CD, CL; /* as ibdvm_forces, on the final state */
+  double t_submit, t_admit, t_done; /* seconds since the server was created (-1: not yet) */
+  size_t device_bytes;   /* device bytes of the request's context */
+} ibdvm_result;
+
+/* Errors: IBDVM_E_INVAL (bad descriptor: tol < 0, max_steps < 1, odd or
+   small steps_per_round), IBDVM_E_NOMEM, IBDVM_E_CUDA. */
+ibdvm_status ibdvm_server_create(const ibdvm_server_desc *desc, ibdvm_server **out);
+/* Queues a request; the descriptors are copied (gas->precision is replaced by
+   the server's).  id receives the request's id (consecutive from 0).
+   Errors: IBDVM_E_INVAL (NULL or invalid descriptor: the grid and velocity
+   grid are checked here, the body when the request is admitted). */
+ibdvm_status ibdvm_server_submit(ibdvm_server *s, const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *vgrid,
+                                 const ibdvm_gas_desc *gas, const ibdvm_body_desc *body, long long *id);
+/* One scheduling round: admits queued requests, advances the admitted ones by
+   steps_per_round steps and retires the finished ones.  Outputs (nullable):
+   requests on the device, in the queue, and finished in this round.  A
+   request that fails is retired with its status; the call itself fails only
+   on a CUDA error of the loop. */
+ibdvm_status ibdvm_server_poll(ibdvm_server *s, int *nactive, int *nqueued, int *nfinished);
+/* The state of request id (done = 0 while queued or on the device).
+   Errors: IBDVM_E_INVAL (unknown id). */
+ibdvm_status ibdvm_server_result(ibdvm_server *s, long long id, ibdvm_result *out);
+/* Seconds since the server was created (the clock of the result times). */
+double ibdvm_server_clock(const ibdvm_server *s);
+/* Destroys the server and every context it still holds. */
+void ibdvm_server_destroy(ibdvm_server *s);
+const char *ibdvm_server_last_error(const ibdvm_server *s);
 
 /* ------------------------------------------------------------------------
  * Host-only geometry (no GPU needed): the classification, links, surface

@@ -1,9 +1,9 @@
 // batch.cpp -- the batched form of the C-ABI (declared in include/ibdvm.h).
 //
-// A batch advances many 2D FP32 contexts of uneven size with one launch per
-// kernel class and step: the grouped ghost-band, force and finalize kernels
-// (kernels.cu) and the persistent TMA sweep over a packed work list
-// (sweep_tma.cu).  The batch keeps per-member device tables with two argument
+// A batch advances many FP32 contexts of uneven size (all 2D or all 3D) with
+// one launch per kernel class and step: the grouped ghost-band, force and
+// finalize kernels (kernels.cu) and the persistent TMA sweep over a packed
+// work list (sweep_tma.cu, sweep3d_tma.cu).  The batch keeps per-member device tables with two argument
 // blocks each (the buffer parities after an even and an odd number of steps),
 // rebuilt when the membership, a member's body or the tiling changes, and
 // replays pairs of steps from captured CUDA graphs.
@@ -139,6 +139,7 @@ void ensure_capacity(ibdvm_batch *b) {
 }
 
 int member_kpt(const ibdvm_batch *b, const ibdvm_ctx *ctx) {
+  if (ctx->dim == 3) return 4; // the 3D sweep takes 128-velocity chunks
   const int want = (b->kpt == 2) ? 2 : 4;
   return (want == 4 && tma_batch_kpt_max(ctx) == 4) ? 4 : 2;
 }
@@ -322,6 +323,24 @@ void batch_detach(ibdvm_ctx *ctx) {
 }
 } // namespace ibdvm
 
+namespace ibdvm {
+ibdvm_status batch_enqueue(ibdvm_batch *b, int nsteps) {
+  BATCH_GUARD(b)
+  if (b->members.empty() || nsteps <= 0) return IBDVM_OK;
+  build(b);
+  bcheck(b, cudaMemsetAsync(b->d_flags, 0, b->members.size() * sizeof(int), b->stream), "clear flags");
+  advance(b, nsteps);
+  return IBDVM_OK;
+  BATCH_END
+}
+
+ibdvm_status batch_collect(ibdvm_batch *b, double *residuals, int *statuses) {
+  BATCH_GUARD(b)
+  return collect(b, residuals, statuses);
+  BATCH_END
+}
+} // namespace ibdvm
+
 extern "C" {
 
 ibdvm_status ibdvm_batch_create(void *cuda_stream, ibdvm_batch **out) {
@@ -345,7 +364,11 @@ ibdvm_status ibdvm_batch_add(ibdvm_batch *b, ibdvm_ctx *ctx) {
     return IBDVM_E_STATE;
   }
   if (!ctx->use_tma || !tma_batch_member_ok(ctx)) {
-    b->err = "batch members are 2D contexts in FP32 storage with the TMA sweep";
+    b->err = "batch members are contexts in FP32 storage with the TMA sweep";
+    return IBDVM_E_INVAL;
+  }
+  if (!b->members.empty() && b->members[0]->dim != ctx->dim) {
+    b->err = "the members of a batch have one dimension";
     return IBDVM_E_INVAL;
   }
   if (ctx->stream != b->stream) {
@@ -454,6 +477,7 @@ ibdvm_status ibdvm_batch_tune(ibdvm_batch *b, int steps_per_trial, double *best_
   }
   const int rows_c[5] = {16, 32, 64, 128, 0};
   const int kpt_c[2] = {4, 2};
+  const int nkpt = (b->members[0]->dim == 3) ? 1 : 2; // 3D: 128-velocity chunks only
   cudaEvent_t e0, e1;
   bcheck(b, cudaEventCreate(&e0), "create event");
   bcheck(b, cudaEventCreate(&e1), "create event");
@@ -461,8 +485,9 @@ ibdvm_status ibdvm_batch_tune(ibdvm_batch *b, int steps_per_trial, double *best_
   int best_rows = b->rows, best_kpt = b->kpt;
   ibdvm_status st = IBDVM_OK;
   try {
-    for (int kp : kpt_c)
+    for (int ik = 0; ik < nkpt; ++ik)
       for (int r : rows_c) {
+        const int kp = kpt_c[ik];
         b->rows = r;
         b->kpt = kp;
         b->dirty = true;

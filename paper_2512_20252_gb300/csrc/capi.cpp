@@ -989,6 +989,22 @@ const char *ibdvm_geom_last_error(void) { return g_geom_err.c_str(); }
 } // extern "C"
 
 namespace ibdvm {
+size_t estimate_ctx_bytes(const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *vgrid, const ibdvm_gas_desc *gas) {
+  Geom G;
+  std::string err;
+  if (!build_grid(*grid, *vgrid, *gas, G, err)) return 0;
+  const size_t es = (gas->precision == IBDVM_FP64) ? 8 : 4;
+  const size_t nc = static_cast<size_t>(G.ncell), nvp = static_cast<size_t>(G.nvp);
+  const int D = G.dim, NW = D + 2, NM = nmoments(D);
+  size_t b = 2 * nc * nvp * G.ncomp * es;                               // f^n, f^{n+1}
+  b += nc * (nvp / 64 + 1) * 4 * NM;                                     // FP32 moment partial sums
+  b += nc * (kMac * es + 2 * (NW + D) * 8 + (nvp / 64 + 1) * NM * 8 + 16); // per-cell state, FP64 sums
+  // the ghost band: at most D n^(D-1) links for a body that fits the domain
+  const double nl = D * std::pow(static_cast<double>(nc), (D - 1.0) / D);
+  b += static_cast<size_t>(nl) * (nvp * (3 * G.ncomp * es + 8) + 256);
+  return b + nvp * 64 + (1u << 20);
+}
+
 void force_outputs(const ibdvm_ctx *ctx, const double *h, double *F, double *Q, double *CD, double *CL) {
   fill_forces(const_cast<ibdvm_ctx *>(ctx), h, F, Q, CD, CL);
 }

@@ -149,7 +149,7 @@ cudaError_t group_finalize(const GroupTables &t, int par, cudaStream_t s);
 struct SweepTables {
   void *args = nullptr, *tmaps = nullptr, *items = nullptr; // [ncase][2], [ncase][2], [nitems]
   int *next = nullptr; // work counter
-  int nitems = 0, grid = 0;
+  int nitems = 0, grid = 0, dim = 2;
 };
 bool tma_batch_member_ok(const ibdvm_ctx *ctx);
 int tma_batch_kpt_max(const ibdvm_ctx *ctx);
@@ -157,9 +157,20 @@ cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::ve
                             int *flags, SweepTables &t, cudaStream_t s);
 void tma_batch_free(SweepTables &t);
 cudaError_t tma_batch_launch(const SweepTables &t, int par, cudaStream_t s);
+// 3D members (sweep3d_tma.cu): 128-velocity chunks; zrows = target planes per
+// item (0: whole columns)
+cudaError_t tma3_batch_build(const std::vector<ibdvm_ctx *> &cases, int zrows, int *flags, SweepTables &t,
+                             cudaStream_t s);
+cudaError_t tma3_batch_launch(const SweepTables &t, int par, cudaStream_t s);
 
 // batch.cpp: takes a context that is being destroyed out of its batch
 void batch_detach(ibdvm_ctx *ctx);
+// batch.cpp: enqueues nsteps batched steps without waiting for them, and
+// waits for them and reads every member's residual and status
+ibdvm_status batch_enqueue(ibdvm_batch *b, int nsteps);
+ibdvm_status batch_collect(ibdvm_batch *b, double *residuals, int *statuses);
+// capi.cpp: an upper estimate of the device bytes of a context (before its body is placed)
+size_t estimate_ctx_bytes(const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *vgrid, const ibdvm_gas_desc *gas);
 // capi.cpp: F[3], Q, CD, CL (each nullable) from the force sums h[4] of ctx
 void force_outputs(const ibdvm_ctx *ctx, const double *h, double *F, double *Q, double *CD, double *CL);
 

@@ -31,7 +31,9 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "ctx.h"
 
@@ -89,6 +91,9 @@ __device__ __forceinline__ unsigned smem_addr(const void *p) {
 }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -443,13 +448,17 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
   return true;
 }
 
+// The march of one block over the tile of columns at (x0, y0), chunk
+// velocities [k0, k0 + KC) and planes [z0, z1).  tm[0..2]: tensor maps of the
+// tile and of the x and y halo strips.  reinit: the block's mbarriers hold an
+// earlier march (all of whose copies have landed) and are invalidated first.
+// Returns false when the block aborted on a timed-out wait.
 template <int KPT>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tmc, const __grid_constant__ CUtensorMap tmx,
-                       const __grid_constant__ CUtensorMap tmy, Tma3Args A) {
+__device__ __forceinline__ bool march3d(const Tma3Args &A, const CUtensorMap *tmc, const CUtensorMap *tmx,
+                                        const CUtensorMap *tmy, int x0, int y0, int k0, int z0, int z1,
+                                        unsigned char *smem_raw, bool reinit) {
   using C = Cfg<KPT>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  March3<KPT> M{A, &tmc, &tmx, &tmy};
+  March3<KPT> M{A, tmc, tmx, tmy};
   M.stage = reinterpret_cast<float *>(smem_raw);
   M.phx = M.stage + NST * C::STAGE_FLOATS;
   M.phy = M.phx + 2 * C::PX_FLOATS;
@@ -463,15 +472,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   M.lane = threadIdx.x & 31;
   M.ti = M.warp % TX;
   M.tj = M.warp / TX;
-  const int ntx = (A.nx + TX - 1) / TX;
-  M.x0 = (blockIdx.x % ntx) * TX;
-  M.y0 = (blockIdx.x / ntx) * TY;
+  M.x0 = x0;
+  M.y0 = y0;
   M.x = M.x0 + M.ti;
   M.y = M.y0 + M.tj;
   M.col_in = M.x < A.nx && M.y < A.ny;
-  M.k0 = blockIdx.y * C::KC;
-  M.z0 = blockIdx.z * A.zrows;
-  M.z1 = min(A.nz, M.z0 + A.zrows);
+  M.k0 = k0;
+  M.z0 = z0;
+  M.z1 = z1;
   M.zlast = min(A.nz, M.z1 + 2);
   M.nc = A.ncell;
   M.plane = M.x + (long long)A.nx * M.y;
@@ -522,7 +530,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         M.col_in ? A.mac[(M.plane + (long long)M.z0 * A.nx * A.ny) * kMac + M.lane] : 0.f;
   M.mask_next = M.col_in ? ((M.z0 + 1 < A.nz) ? cmask3(M, M.x, M.y, M.z0 + 1) : 0) : kNotFluid;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) mbar_init(&M.full[s], 1);
+    for (int s = 0; s < NST; ++s) {
+      if (reinit) mbar_inval(&M.full[s]);
+      mbar_init(&M.full[s], 1);
+    }
     fence_mbar_init();
   }
   __syncthreads();
@@ -574,6 +585,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int j = r - M.z0;
       mbar_wait(&M.full[j % NST], (j / NST) & 1);
     }
+  }
+  return ok;
+}
+
+template <int KPT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tmc, const __grid_constant__ CUtensorMap tmx,
+                       const __grid_constant__ CUtensorMap tmy, Tma3Args A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int ntx = (A.nx + TX - 1) / TX;
+  const int z0 = blockIdx.z * A.zrows;
+  march3d<KPT>(A, &tmc, &tmx, &tmy, (blockIdx.x % ntx) * TX, (blockIdx.x / ntx) * TY, blockIdx.y * Cfg<KPT>::KC,
+               z0, min(A.nz, z0 + A.zrows), smem_raw, false);
+}
+
+// One item of the batched 3D sweep: a march of one member case.
+struct WorkItem3 {
+  int cas;        // member index
+  int x0, y0, k0; // tile origin and first chunk velocity
+  int z0, z1;     // planes
+  int pad[2];
+};
+
+// The batched 3D sweep: a persistent grid whose blocks take work items in
+// order from a shared counter.  Member c at step parity par uses
+// args[2 c + par] and the tensor maps tmaps[3 (2 c + par) + 0..2].
+__global__ void __launch_bounds__(NTHREADS, 1)
+    sweep3d_tma_batch_kernel(const Tma3Args *__restrict__ args, const CUtensorMap *__restrict__ tmaps,
+                             const WorkItem3 *__restrict__ items, int nitems, int *__restrict__ next, int par) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ Tma3Args sA;
+  __shared__ int s_item;
+  bool reinit = false;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int i = s_item;
+    if (i >= nitems) break;
+    const WorkItem3 it = items[i];
+    if (threadIdx.x == 0) sA = args[2 * it.cas + par];
+    __syncthreads();
+    const CUtensorMap *tm = tmaps + 3 * (2 * it.cas + par);
+    const bool ok = march3d<4>(sA, tm, tm + 1, tm + 2, it.x0, it.y0, it.k0, it.z0, it.z1, smem_raw, reinit);
+    if (!ok) break; // uniform: the abort vote is block-wide
+    reinit = true;
+    __syncthreads(); // the item's shared memory and arguments are released
   }
 }
 
@@ -654,6 +711,114 @@ cudaError_t tma3_sweep_launch(ibdvm_ctx *ctx) {
   dim3 grid(ntiles, nchunk, (A.nz + A.zrows - 1) / A.zrows);
   const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(ctx->tmap3[ctx->cur][0]);
   sweep3d_tma_kernel<kKpt3><<<grid, NTHREADS, Cfg<kKpt3>::SMEM, ctx->stream>>>(tm[0], tm[1], tm[2], A);
+  return cudaGetLastError();
+}
+
+cudaError_t tma3_batch_build(const std::vector<ibdvm_ctx *> &cases, int zrows, int *flags, SweepTables &t,
+                             cudaStream_t s) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder3();
+  if (!enc) return cudaErrorNotSupported;
+  const int n = static_cast<int>(cases.size());
+  const int kc = 32 * kKpt3;
+  std::vector<Tma3Args> args(2 * n);
+  std::vector<CUtensorMap> maps(6 * n);
+  std::vector<WorkItem3> items;
+  for (int i = 0; i < n; ++i) {
+    const ibdvm_ctx *ctx = cases[i];
+    const Geom &g = ctx->geom;
+    for (int p = 0; p < 2; ++p) {
+      const int cur = ctx->cur ^ p;
+      Tma3Args &A = args[2 * i + p];
+      A = Tma3Args{};
+      A.f = static_cast<const float *>(ctx->f[cur]);
+      A.fn = static_cast<float *>(ctx->f[1 - cur]);
+      A.mac = static_cast<const float *>(ctx->mac);
+      A.xi = static_cast<const float *>(ctx->xiT);
+      A.w = static_cast<const float *>(ctx->wT);
+      A.finf = static_cast<const float *>(ctx->finf);
+      A.cmask = ctx->cmask;
+      A.dslot = ctx->dslot;
+      A.dlinks = ctx->dlinks;
+      A.lval = static_cast<const float *>(ctx->lval);
+      A.part = ctx->partf;
+      A.err = flags + i;
+      A.ncell = ctx->ncell;
+      A.nx = g.n[0];
+      A.ny = g.n[1];
+      A.nz = g.n[2];
+      A.nvp = ctx->nvp;
+      A.nv = ctx->nv;
+      A.zrows = 0;
+      A.dt = (float)g.dt;
+      A.rdx = (float)(1.0 / g.dx[0]);
+      A.rdy = (float)(1.0 / g.dx[1]);
+      A.rdz = (float)(1.0 / g.dx[2]);
+      cuuint64_t dims[4] = {(cuuint64_t)ctx->nvp, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+      cuuint64_t strides[3] = {(cuuint64_t)ctx->nvp * 4, (cuuint64_t)g.n[0] * ctx->nvp * 4,
+                               (cuuint64_t)g.n[1] * g.n[0] * ctx->nvp * 4};
+      const cuuint32_t boxes[3][4] = {{(cuuint32_t)kc, TX, TY, 1}, {(cuuint32_t)kc, 2, TY, 1}, {(cuuint32_t)kc, TX, 2, 1}};
+      cuuint32_t estr[4] = {1, 1, 1, 1};
+      for (int m = 0; m < 3; ++m) {
+        CUresult r = enc(&maps[3 * (2 * i + p) + m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->f[cur], dims, strides,
+                         boxes[m], estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+      }
+    }
+    const int nz = g.n[2];
+    const int nzb = (zrows <= 0 || zrows >= nz) ? 1 : (nz + zrows - 1) / zrows;
+    const int per = (nz + nzb - 1) / nzb;
+    for (int y0 = 0; y0 < g.n[1]; y0 += TY)
+      for (int x0 = 0; x0 < g.n[0]; x0 += TX)
+        for (int k0 = 0; k0 < ctx->nvp; k0 += kc)
+          for (int z0 = 0; z0 < nz; z0 += per) {
+            WorkItem3 it{};
+            it.cas = i;
+            it.x0 = x0;
+            it.y0 = y0;
+            it.k0 = k0;
+            it.z0 = z0;
+            it.z1 = std::min(nz, z0 + per);
+            items.push_back(it);
+          }
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const WorkItem3 &a, const WorkItem3 &b) { return a.z1 - a.z0 > b.z1 - b.z0; });
+  cudaError_t e;
+  auto up = [&](const void *h, size_t bytes, void *&d) -> cudaError_t {
+    cudaError_t r = cudaMalloc(&d, std::max<size_t>(bytes, 16));
+    if (r != cudaSuccess || bytes == 0) return r;
+    return cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s);
+  };
+  if ((e = up(args.data(), args.size() * sizeof(Tma3Args), t.args)) != cudaSuccess) return e;
+  if ((e = up(maps.data(), maps.size() * sizeof(CUtensorMap), t.tmaps)) != cudaSuccess) return e;
+  if ((e = up(items.data(), items.size() * sizeof(WorkItem3), t.items)) != cudaSuccess) return e;
+  void *nx = nullptr;
+  if ((e = cudaMalloc(&nx, sizeof(int))) != cudaSuccess) return e;
+  t.next = static_cast<int *>(nx);
+  t.nitems = static_cast<int>(items.size());
+  t.dim = 3;
+  const int smem = (int)Cfg<kKpt3>::SMEM;
+  if ((e = cudaFuncSetAttribute(sweep3d_tma_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+      cudaSuccess)
+    return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep3d_tma_batch_kernel, NTHREADS, smem)) !=
+      cudaSuccess)
+    return e;
+  t.grid = std::max(1, std::min(t.nitems, nsm * std::max(per_sm, 1)));
+  return cudaStreamSynchronize(s); // the host tables go out of scope
+}
+
+cudaError_t tma3_batch_launch(const SweepTables &t, int par, cudaStream_t s) {
+  if (t.nitems == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(t.next, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  sweep3d_tma_batch_kernel<<<t.grid, NTHREADS, Cfg<kKpt3>::SMEM, s>>>(
+      static_cast<const Tma3Args *>(t.args), static_cast<const CUtensorMap *>(t.tmaps),
+      static_cast<const WorkItem3 *>(t.items), t.nitems, t.next, par);
   return cudaGetLastError();
 }
 

@@ -669,11 +669,12 @@ cudaError_t tma_sweep_launch(ibdvm_ctx *ctx) {
 }
 
 bool tma_batch_member_ok(const ibdvm_ctx *ctx) {
-  return ctx->dim == 2 && ctx->precision == IBDVM_MIXED && (ctx->nvp % 64) == 0 && ctx->partf != nullptr &&
-         encoder() != nullptr;
+  if (ctx->precision != IBDVM_MIXED || ctx->partf == nullptr || encoder() == nullptr) return false;
+  if (ctx->dim == 2) return (ctx->nvp % 64) == 0;
+  return tma3_sweep_applicable(ctx);
 }
 
-int tma_batch_kpt_max(const ibdvm_ctx *ctx) { return (ctx->nvp % 128 == 0) ? 4 : 2; }
+int tma_batch_kpt_max(const ibdvm_ctx *ctx) { return (ctx->dim == 3 || ctx->nvp % 128 == 0) ? 4 : 2; }
 
 void tma_batch_free(SweepTables &t) {
   void *ps[] = {t.args, t.tmaps, t.items, t.next};
@@ -685,6 +686,7 @@ void tma_batch_free(SweepTables &t) {
 cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::vector<int> &kpt, int rows,
                             int *flags, SweepTables &t, cudaStream_t s) {
   tma_batch_free(t);
+  if (!cases.empty() && cases[0]->dim == 3) return tma3_batch_build(cases, rows, flags, t, s);
   PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
   if (!enc) return cudaErrorNotSupported;
   const int n = static_cast<int>(cases.size());
@@ -777,6 +779,7 @@ cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::ve
 }
 
 cudaError_t tma_batch_launch(const SweepTables &t, int par, cudaStream_t s) {
+  if (t.dim == 3) return tma3_batch_launch(t, par, s);
   if (t.nitems == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(t.next, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;

@@ -61,6 +61,19 @@ class BodyDesc(ctypes.Structure):
                 ("U_w", ctypes.c_double * 3), ("L_ref", ctypes.c_double)]
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_steps", ctypes.c_longlong), ("steps_per_round", ctypes.c_int),
+                ("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int), ("sequential_fp64", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("done", ctypes.c_int), ("status", ctypes.c_int),
+                ("steps", ctypes.c_longlong), ("residual", ctypes.c_double), ("F", ctypes.c_double * 3),
+                ("Q", ctypes.c_double), ("CD", ctypes.c_double), ("CL", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
 class BatchTiling(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int), ("kpt", ctypes.c_int), ("nitems", ctypes.c_int),
                 ("grid", ctypes.c_int), ("graphs", ctypes.c_int)]
@@ -130,6 +143,14 @@ SIGNATURES = {
     "ibdvm_batch_reset_kernel_times": ([_V], _S),
     "ibdvm_batch_destroy": ([_V], None),
     "ibdvm_batch_last_error": ([_V], ctypes.c_char_p),
+    "ibdvm_server_create": ([ctypes.POINTER(ServerDesc), ctypes.POINTER(_V)], _S),
+    "ibdvm_server_submit": ([_V, ctypes.POINTER(GridDesc), ctypes.POINTER(VGridDesc), ctypes.POINTER(GasDesc),
+                             ctypes.POINTER(BodyDesc), _LL], _S),
+    "ibdvm_server_poll": ([_V, _I, _I, _I], _S),
+    "ibdvm_server_result": ([_V, ctypes.c_longlong, ctypes.POINTER(Result)], _S),
+    "ibdvm_server_clock": ([_V], ctypes.c_double),
+    "ibdvm_server_destroy": ([_V], None),
+    "ibdvm_server_last_error": ([_V], ctypes.c_char_p),
 }
 
 _lock = threading.Lock()
@@ -519,6 +540,64 @@ class Batch:
             self.lib.ibdvm_batch_destroy(self.h)
             self.h = None
             self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The serving loop (C-ABI handle): requests are queued, admitted by HBM
+    budget into a 2D and a 3D batch, advanced a round per poll and retired
+    when converged, failed or capped.  sequential_fp64=True is the plain form:
+    one request at a time in the FP64 path."""
+
+    def __init__(self, tol=1e-6, max_steps=20000, steps_per_round=50, hbm_budget=0, max_active=0,
+                 sequential_fp64=False):
+        self.lib = load()
+        d = ServerDesc(float(tol), int(max_steps), int(steps_per_round), int(hbm_budget), int(max_active),
+                       1 if sequential_fp64 else 0)
+        h = _V()
+        st = self.lib.ibdvm_server_create(ctypes.byref(d), ctypes.byref(h))
+        if st != OK:
+            raise IbdvmError(st, "ibdvm_server_create failed")
+        self.h = h
+
+    def _check(self, st):
+        if st != OK:
+            raise IbdvmError(st, self.lib.ibdvm_server_last_error(self.h).decode())
+        return st
+
+    def submit(self, case: dict) -> int:
+        g, v, s, b, keep = descriptors(case)
+        body = case.get("body") or {"kind": "none"}
+        rid = ctypes.c_longlong(-1)
+        self._check(self.lib.ibdvm_server_submit(self.h, ctypes.byref(g), ctypes.byref(v), ctypes.byref(s),
+                                                 ctypes.byref(b) if body["kind"] != "none" else None,
+                                                 ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self):
+        a, q, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.ibdvm_server_poll(self.h, ctypes.byref(a), ctypes.byref(q), ctypes.byref(f)))
+        return a.value, q.value, f.value
+
+    def result(self, rid: int) -> dict:
+        r = Result()
+        self._check(self.lib.ibdvm_server_result(self.h, int(rid), ctypes.byref(r)))
+        d = {k: getattr(r, k) for k, _ in Result._fields_}
+        d["F"] = list(r.F)
+        return d
+
+    def clock(self) -> float:
+        return self.lib.ibdvm_server_clock(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ibdvm_server_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -208,15 +208,15 @@ def test_batch_rejects_bad_members(torch):
     with pytest.raises(ibdvm.IbdvmError) as e:
         b.add(fp64)
     assert e.value.status == 1
-    s3 = ibdvm.Solver(wl._case(3, 8, 2.0, 8, 4.5, 0.1, 0.5, wl.sphere(0.6), precision="mixed"),
-                      stream=stream.cuda_stream)
-    with pytest.raises(ibdvm.IbdvmError):
-        b.add(s3)
     ok = ibdvm.Solver(wl.small_2d("circle", n=12, nv=8, precision="mixed"), stream=other.cuda_stream)
     with pytest.raises(ibdvm.IbdvmError):
         b.add(ok)  # bound to another stream
     ok.set_stream(stream.cuda_stream)
     b.add(ok)
+    s3 = ibdvm.Solver(wl._case(3, 8, 2.0, 8, 4.5, 0.1, 0.5, wl.sphere(0.6), precision="mixed"),
+                      stream=stream.cuda_stream)
+    with pytest.raises(ibdvm.IbdvmError):
+        b.add(s3)  # the members of a batch have one dimension
     b2 = ibdvm.Batch(stream=stream.cuda_stream)
     with pytest.raises(ibdvm.IbdvmError) as e:
         b2.add(ok)
