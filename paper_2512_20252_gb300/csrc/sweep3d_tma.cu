@@ -7,15 +7,18 @@
 // GB300:
 //
 //   * a block owns a 4 x 4 tile of (x, y) columns of cells (16 warps, one per
-//     column) and a chunk of KC = 32 * KPT velocities (lane l owns velocities
-//     l, l + 32, ...), and marches along z;
+//     column) and a chunk of KC = 32 * KPT velocities (lane l owns the pairs of
+//     neighbouring velocities 2 l + 64 j, 2 l + 64 j + 1), and marches along z;
+//     every per-velocity operation works on such a pair with Blackwell's packed
+//     FP32 instructions (__ffma2_rn and friends) and 64-bit loads and stores;
 //   * every z plane of the block arrives in shared memory as a cross-shaped
 //     slab: the 4 x 4 tile and two halo strips of two cells on each side in x
 //     and in y (48 cells x KC velocities), five TMA tensor copies
 //     (cp.async.bulk.tensor.4d) on one mbarrier per stage of a 5-stage ring;
 //   * each lane keeps its column's z stencil in registers (f at planes z..z+2
-//     and the reconstructed faces of planes z-1..z+1), rotated by renaming in a
-//     three-way unrolled loop;
+//     and the reconstructed faces of planes z-1..z+1);
+//   * a face is f + s vl(f - f_lo, f_hi - f) with s the sign of the velocity
+//     (the van Leer half slope is symmetric and odd), so no face is selected;
 //   * x and y faces are exchanged through shared memory: every warp publishes
 //     the downwind faces of its cell; the faces of the halo cells on the
 //     upwind side of the tile are spread over all threads;
@@ -138,15 +141,37 @@ __device__ __forceinline__ float vl_half(float a, float b) {
 // downwind face value: f plus half the slope along the motion
 __device__ __forceinline__ float face(float f, float up, float dn) { return f + vl_half(f - up, dn - f); }
 
+// the same for a pair of velocities (packed FP32)
+__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+__device__ __forceinline__ float2 vl_half2(float2 a, float2 b) {
+  const float2 p = __fmul2_rn(a, b);
+  const float2 s = __fadd2_rn(a, b);
+  const float2 v = __fmul2_rn(p, make_float2(rcp_approx(s.x), rcp_approx(s.y)));
+  return make_float2(p.x > 0.f ? v.x : 0.f, p.y > 0.f ? v.y : 0.f);
+}
+// downwind face from the low and high neighbours and the sign s of the velocity:
+// f + s vl(f - lo, hi - f) equals f + vl(f - up, dn - f) since vl is symmetric and odd
+__device__ __forceinline__ float2 face2(float2 f, float2 lo, float2 hi, float2 s) {
+  return __ffma2_rn(s, vl_half2(sub2(f, lo), sub2(hi, f)), f);
+}
+__device__ __forceinline__ float2 lds2(const float *base, int kk) { return *reinterpret_cast<const float2 *>(base + kk); }
+
 __device__ __forceinline__ float link_value(const Tma3Args &A, long long c, int dir, int k) {
   const int s = A.dslot[c];
   const int l = (s >= 0) ? A.dlinks[s * 6 + dir] : -1;
   return (l >= 0) ? A.lval[(size_t)l * A.nvp + k] : A.finf[k];
 }
+// the link values of velocities k, k + 1 (k even)
+__device__ __forceinline__ float2 link_value2(const Tma3Args &A, long long c, int dir, int k) {
+  const int s = A.dslot[c];
+  const int l = (s >= 0) ? A.dlinks[s * 6 + dir] : -1;
+  return *reinterpret_cast<const float2 *>((l >= 0) ? A.lval + (size_t)l * A.nvp + k : A.finf + k);
+}
 
 enum : uint8_t { kNotFluid = 64, kGhostAny = 63 };
 
-template <int KPT> using Ring = float[KPT];
+template <int KPT> using Ring = float2[KPT / 2];
 
 // Every thread owns two halo faces per plane, both for chunk velocity
 // kk = threadIdx.x % KC: the downwind x face of the upwind x-halo cell of row
@@ -167,14 +192,16 @@ template <int KPT> struct March3 {
   unsigned pb;
   bool col_in;
   long long nc, plane;
-  float xix[KPT], xiy[KPT], xiz[KPT], wk[KPT], ax[KPT], ay[KPT], az[KPT];
+  // per velocity pair: xi, weight, dt |xi_a| / dx_a, sign of xi_a
+  float2 xix[KPT / 2], xiy[KPT / 2], xiz[KPT / 2], wk[KPT / 2], ax[KPT / 2], ay[KPT / 2], az[KPT / 2];
+  float2 sx[KPT / 2], sy[KPT / 2], sz[KPT / 2];
   uint8_t mask_next;
   bool abort_local;
   const int4 *duty; // [2][NTHREADS]: x faces, then y faces
 };
 
-template <int KPT> __device__ __forceinline__ int klo(const March3<KPT> &M, int q) { return M.lane + 32 * q; }
-template <int KPT> __device__ __forceinline__ int kof(const March3<KPT> &M, int q) { return M.k0 + klo(M, q); }
+// chunk-local index of the first velocity of pair j of the lane
+template <int KPT> __device__ __forceinline__ int kp(const March3<KPT> &M, int j) { return 2 * M.lane + 64 * j; }
 
 template <int KPT> __device__ __forceinline__ void issue_plane(March3<KPT> &M, int z, int st) {
   using C = Cfg<KPT>;
@@ -222,6 +249,31 @@ __device__ __forceinline__ float face_general(const March3<KPT> &M, const float 
   return face(f, up, dn);
 }
 
+// the same for the velocity pair at chunk index kk of the own cell (i, j),
+// from the low and high neighbours along the axis and the signs s
+template <int KPT>
+__device__ __forceinline__ float2 face_general2(const March3<KPT> &M, const float *sp, int a, int i, int j, int z,
+                                                int kk, float2 s) {
+  using C = Cfg<KPT>;
+  const Tma3Args &A = M.A;
+  const int cx = M.x0 + i, cy = M.y0 + j;
+  if (cx < 0 || cx >= A.nx || cy < 0 || cy >= A.ny) return lds2(M.sfinf, kk);
+  const uint8_t m = cmask3(M, cx, cy, z);
+  if (m & kNotFluid) return make_float2(0.f, 0.f);
+  const int di = (a == 0) ? 1 : 0, dj = (a == 1) ? 1 : 0;
+  const float2 f = lds2(sp + slot(i, j) * C::KC, kk);
+  const int ca = (a == 0) ? cx : cy, na = (a == 0) ? A.nx : A.ny;
+  const long long c = cx + (long long)A.nx * (cy + (long long)A.ny * z);
+  float2 lo, hi;
+  if (m & (1u << (2 * a))) lo = link_value2(A, c, 2 * a, M.k0 + kk);
+  else if (ca - 1 < 0) lo = lds2(M.sfinf, kk);
+  else lo = lds2(sp + slot(i - di, j - dj) * C::KC, kk);
+  if (m & (1u << (2 * a + 1))) hi = link_value2(A, c, 2 * a + 1, M.k0 + kk);
+  else if (ca + 1 >= na) hi = lds2(M.sfinf, kk);
+  else hi = lds2(sp + slot(i + di, j + dj) * C::KC, kk);
+  return face2(f, lo, hi, s);
+}
+
 // downwind z face of plane r for the own column: fr = f(r), lo = f(r-1), hi = f(r+1)
 template <int KPT>
 __device__ __forceinline__ void phi_z(const March3<KPT> &M, int r, uint8_t m, const Ring<KPT> &fr,
@@ -229,21 +281,25 @@ __device__ __forceinline__ void phi_z(const March3<KPT> &M, int r, uint8_t m, co
   const Tma3Args &A = M.A;
   if (r < 0 || r >= A.nz || !M.col_in) {
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) out[q] = M.sfinf[klo(M, q)];
+    for (int j = 0; j < KPT / 2; ++j) out[j] = lds2(M.sfinf, kp(M, j));
     return;
   }
   if (m & kNotFluid) {
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) out[q] = 0.f;
+    for (int j = 0; j < KPT / 2; ++j) out[j] = make_float2(0.f, 0.f);
+    return;
+  }
+  if (!(m & 48)) {
+#pragma unroll
+    for (int j = 0; j < KPT / 2; ++j) out[j] = face2(fr[j], lo[j], hi[j], M.sz[j]);
     return;
   }
   const long long c = M.plane + (long long)r * A.nx * A.ny;
 #pragma unroll
-  for (int q = 0; q < KPT; ++q) {
-    float l = lo[q], h = hi[q];
-    if (m & 16) l = link_value(A, c, 4, kof(M, q));
-    if (m & 32) h = link_value(A, c, 5, kof(M, q));
-    out[q] = (M.xiz[q] >= 0.f) ? face(fr[q], l, h) : face(fr[q], h, l);
+  for (int j = 0; j < KPT / 2; ++j) {
+    const float2 l = (m & 16) ? link_value2(A, c, 4, M.k0 + kp(M, j)) : lo[j];
+    const float2 h = (m & 32) ? link_value2(A, c, 5, M.k0 + kp(M, j)) : hi[j];
+    out[j] = face2(fr[j], l, h, M.sz[j]);
   }
 }
 
@@ -300,38 +356,37 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
   if (z + 2 < A.nz && M.col_in) {
     const float *src = M.stage + st2 * C::STAGE_FLOATS + slot(M.ti, M.tj) * C::KC;
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) Rc[q] = src[klo(M, q)];
+    for (int j = 0; j < KPT / 2; ++j) Rc[j] = lds2(src, kp(M, j));
   } else {
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) Rc[q] = M.sfinf[klo(M, q)];
+    for (int j = 0; j < KPT / 2; ++j) Rc[j] = lds2(M.sfinf, kp(M, j));
   }
   const float *sp = M.stage + st * C::STAGE_FLOATS;
   float *phx = M.phx + par * C::PX_FLOATS; // [TY][TX + 2][KC]
   float *phy = M.phy + par * C::PY_FLOATS; // [TY + 2][TX][KC]
   // (2) downwind x and y faces of the own cell
-  float PX[KPT], PY[KPT];
+  float2 PX[KPT / 2], PY[KPT / 2];
   const bool fast = M.col_in && fluid && !(m0 & 15) && M.x > 0 && M.x + 1 < A.nx && M.y > 0 && M.y + 1 < A.ny;
   if (fast) {
     const float *px_lo = sp + slot(M.ti - 1, M.tj) * C::KC, *px_hi = sp + slot(M.ti + 1, M.tj) * C::KC;
     const float *py_lo = sp + slot(M.ti, M.tj - 1) * C::KC, *py_hi = sp + slot(M.ti, M.tj + 1) * C::KC;
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      const int kk = klo(M, q);
-      const float xl = px_lo[kk], xh = px_hi[kk], yl = py_lo[kk], yh = py_hi[kk];
-      PX[q] = (M.xix[q] >= 0.f) ? face(Ra[q], xl, xh) : face(Ra[q], xh, xl);
-      PY[q] = (M.xiy[q] >= 0.f) ? face(Ra[q], yl, yh) : face(Ra[q], yh, yl);
+    for (int j = 0; j < KPT / 2; ++j) {
+      const int kk = kp(M, j);
+      PX[j] = face2(Ra[j], lds2(px_lo, kk), lds2(px_hi, kk), M.sx[j]);
+      PY[j] = face2(Ra[j], lds2(py_lo, kk), lds2(py_hi, kk), M.sy[j]);
     }
   } else {
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      PX[q] = face_general(M, sp, 0, M.ti, M.tj, z, klo(M, q), M.xix[q]);
-      PY[q] = face_general(M, sp, 1, M.ti, M.tj, z, klo(M, q), M.xiy[q]);
+    for (int j = 0; j < KPT / 2; ++j) {
+      PX[j] = face_general2(M, sp, 0, M.ti, M.tj, z, kp(M, j), M.sx[j]);
+      PY[j] = face_general2(M, sp, 1, M.ti, M.tj, z, kp(M, j), M.sy[j]);
     }
   }
 #pragma unroll
-  for (int q = 0; q < KPT; ++q) {
-    phx[(M.tj * (TX + 2) + M.ti + 1) * C::KC + klo(M, q)] = PX[q];
-    phy[((M.tj + 1) * TX + M.ti) * C::KC + klo(M, q)] = PY[q];
+  for (int j = 0; j < KPT / 2; ++j) {
+    *reinterpret_cast<float2 *>(phx + (M.tj * (TX + 2) + M.ti + 1) * C::KC + kp(M, j)) = PX[j];
+    *reinterpret_cast<float2 *>(phy + ((M.tj + 1) * TX + M.ti) * C::KC + kp(M, j)) = PY[j];
   }
   // halo faces on the upwind side of the tile (TY rows in x, TX columns in y)
   halo_face<KPT, 0>(M, sp, z, phx);
@@ -344,7 +399,7 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
     fence_proxy_async();
     issue_plane(M, z + NST - 1, st == 0 ? NST - 1 : st - 1);
   }
-  // (5) update of the own cell and its moment sums
+  // (5) update of the own cell and its moment sums (per velocity pair)
   float acc[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) acc[m] = 0.f;
@@ -354,54 +409,70 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
     const float pre = p0.x, U0 = p0.y, U1 = p0.z, U2 = p0.w;
     const float invT = p1.x, shA = p1.z, q0 = p1.w;
     const float q1 = p2.x, q2 = p2.y, dtau = p2.z;
-    const float omd = 1.f - dtau;
+    const float2 omd = dup(1.f - dtau), dt2 = dup(dtau);
     const bool ghosty = (m0 & kGhostAny) != 0;
-    float out[KPT];
+    const float *xl = phx + (M.tj * (TX + 2) + M.ti) * C::KC, *xr = xl + 2 * C::KC;
+    const float *yl = phy + (M.tj * TX + M.ti) * C::KC, *yr = yl + 2 * TX * C::KC;
+    float2 a[NM];
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      const int kk = klo(M, q);
-      const bool px = M.xix[q] >= 0.f, py = M.xiy[q] >= 0.f, pz = M.xiz[q] >= 0.f;
-      float ix = phx[(M.tj * (TX + 2) + M.ti + (px ? 0 : 2)) * C::KC + kk];
-      float iy = phy[((M.tj + (py ? 0 : 2)) * TX + M.ti) * C::KC + kk];
-      float iz = pz ? Pa[q] : Pc[q];
+    for (int m = 0; m < NM; ++m) a[m] = make_float2(0.f, 0.f);
+    Ring<KPT> out;
+#pragma unroll
+    for (int j = 0; j < KPT / 2; ++j) {
+      const int kk = kp(M, j);
+      // inflow faces: the upwind neighbour's downwind face, per velocity
+      const float2 fxl = lds2(xl, kk), fxr = lds2(xr, kk), fyl = lds2(yl, kk), fyr = lds2(yr, kk);
+      float2 ix = make_float2(M.sx[j].x > 0.f ? fxl.x : fxr.x, M.sx[j].y > 0.f ? fxl.y : fxr.y);
+      float2 iy = make_float2(M.sy[j].x > 0.f ? fyl.x : fyr.x, M.sy[j].y > 0.f ? fyl.y : fyr.y);
+      float2 iz = make_float2(M.sz[j].x > 0.f ? Pa[j].x : Pc[j].x, M.sz[j].y > 0.f ? Pa[j].y : Pc[j].y);
       if (ghosty) { // ghost upwind neighbour: mean of its link value and this cell
-        const int dx = px ? 0 : 1, dy = py ? 2 : 3, dz = pz ? 4 : 5;
-        if (m0 & (1u << dx)) ix = 0.5f * (link_value(A, cell, dx, kof(M, q)) + Ra[q]);
-        if (m0 & (1u << dy)) iy = 0.5f * (link_value(A, cell, dy, kof(M, q)) + Ra[q]);
-        if (m0 & (1u << dz)) iz = 0.5f * (link_value(A, cell, dz, kof(M, q)) + Ra[q]);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int k = M.k0 + kk + e;
+          const float fc = e ? Ra[j].y : Ra[j].x;
+          const int dx = ((e ? M.sx[j].y : M.sx[j].x) > 0.f) ? 0 : 1;
+          const int dy = ((e ? M.sy[j].y : M.sy[j].x) > 0.f) ? 2 : 3;
+          const int dz = ((e ? M.sz[j].y : M.sz[j].x) > 0.f) ? 4 : 5;
+          if (m0 & (1u << dx)) (e ? ix.y : ix.x) = 0.5f * (link_value(A, cell, dx, k) + fc);
+          if (m0 & (1u << dy)) (e ? iy.y : iy.x) = 0.5f * (link_value(A, cell, dy, k) + fc);
+          if (m0 & (1u << dz)) (e ? iz.y : iz.x) = 0.5f * (link_value(A, cell, dz, k) + fc);
+        }
       }
       // Shakhov equilibrium g (1 + A c.q (2 c^2/T - 5)) from the stored state
-      const float cx = M.xix[q] - U0, cy = M.xiy[q] - U1, cz = M.xiz[q] - U2;
-      const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-      const float t = c2 * invT;
-      const float e = pre * __expf(-t);
-      const float cq = fmaf(cx, q0, fmaf(cy, q1, cz * q2));
-      const float g = fmaf(e * shA * cq, fmaf(2.f, t, -5.f), e);
-      float n = fmaf(Ra[q], omd, dtau * g);
-      n = fmaf(M.ax[q], ix - PX[q], n);
-      n = fmaf(M.ay[q], iy - PY[q], n);
-      n = fmaf(M.az[q], iz - Pb[q], n);
-      out[q] = n;
-      const float wf = M.wk[q] * n, e2 = c2 * wf;
-      const float cxw = cx * wf, cyw = cy * wf;
-      acc[0] += wf;
-      acc[1] += cxw;
-      acc[2] += cyw;
-      acc[3] = fmaf(cz, wf, acc[3]);
-      acc[4] += e2;
-      acc[5] = fmaf(cx, cxw, acc[5]);
-      acc[6] = fmaf(cy, cxw, acc[6]);
-      acc[7] = fmaf(cz, cxw, acc[7]);
-      acc[8] = fmaf(cy, cyw, acc[8]);
-      acc[9] = fmaf(cz, cyw, acc[9]);
-      acc[10] = fmaf(cz * cz, wf, acc[10]);
-      acc[11] = fmaf(cx, e2, acc[11]);
-      acc[12] = fmaf(cy, e2, acc[12]);
-      acc[13] = fmaf(cz, e2, acc[13]);
+      const float2 cx = __fadd2_rn(M.xix[j], dup(-U0)), cy = __fadd2_rn(M.xiy[j], dup(-U1)),
+                   cz = __fadd2_rn(M.xiz[j], dup(-U2));
+      const float2 c2 = __ffma2_rn(cx, cx, __ffma2_rn(cy, cy, __fmul2_rn(cz, cz)));
+      const float2 t = __fmul2_rn(c2, dup(invT));
+      const float2 e = __fmul2_rn(dup(pre), make_float2(__expf(-t.x), __expf(-t.y)));
+      const float2 cq = __ffma2_rn(cx, dup(q0), __ffma2_rn(cy, dup(q1), __fmul2_rn(cz, dup(q2))));
+      const float2 g = __ffma2_rn(__fmul2_rn(__fmul2_rn(e, dup(shA)), cq), __ffma2_rn(dup(2.f), t, dup(-5.f)), e);
+      float2 n = __ffma2_rn(Ra[j], omd, __fmul2_rn(dt2, g));
+      n = __ffma2_rn(M.ax[j], sub2(ix, PX[j]), n);
+      n = __ffma2_rn(M.ay[j], sub2(iy, PY[j]), n);
+      n = __ffma2_rn(M.az[j], sub2(iz, Pb[j]), n);
+      out[j] = n;
+      const float2 wf = __fmul2_rn(M.wk[j], n), e2 = __fmul2_rn(c2, wf);
+      const float2 cxw = __fmul2_rn(cx, wf), cyw = __fmul2_rn(cy, wf);
+      a[0] = __fadd2_rn(a[0], wf);
+      a[1] = __fadd2_rn(a[1], cxw);
+      a[2] = __fadd2_rn(a[2], cyw);
+      a[3] = __ffma2_rn(cz, wf, a[3]);
+      a[4] = __fadd2_rn(a[4], e2);
+      a[5] = __ffma2_rn(cx, cxw, a[5]);
+      a[6] = __ffma2_rn(cy, cxw, a[6]);
+      a[7] = __ffma2_rn(cz, cxw, a[7]);
+      a[8] = __ffma2_rn(cy, cyw, a[8]);
+      a[9] = __ffma2_rn(cz, cyw, a[9]);
+      a[10] = __ffma2_rn(__fmul2_rn(cz, cz), wf, a[10]);
+      a[11] = __ffma2_rn(cx, e2, a[11]);
+      a[12] = __ffma2_rn(cy, e2, a[12]);
+      a[13] = __ffma2_rn(cz, e2, a[13]);
     }
+#pragma unroll
+    for (int m = 0; m < NM; ++m) acc[m] = a[m].x + a[m].y;
     float *dst = A.fn + (size_t)cell * A.nvp + M.k0;
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) dst[klo(M, q)] = out[q];
+    for (int j = 0; j < KPT / 2; ++j) *reinterpret_cast<float2 *>(dst + kp(M, j)) = out[j];
   }
   // (6) butterfly of the 16 (14 used) sums over the 32 lanes
   {
@@ -487,16 +558,37 @@ __device__ __forceinline__ bool march3d(const Tma3Args &A, const CUtensorMap *tm
   M.pb = 0;
   M.abort_local = false;
 #pragma unroll
-  for (int q = 0; q < KPT; ++q) {
-    const int k = kof(M, q);
-    const bool valid = k < A.nv;
-    M.xix[q] = valid ? A.xi[k] : 1e18f;
-    M.xiy[q] = valid ? A.xi[A.nvp + k] : 1e18f;
-    M.xiz[q] = valid ? A.xi[2 * A.nvp + k] : 1e18f;
-    M.wk[q] = valid ? A.w[k] : 0.f;
-    M.ax[q] = valid ? A.dt * fabsf(M.xix[q]) * A.rdx : 0.f;
-    M.ay[q] = valid ? A.dt * fabsf(M.xiy[q]) * A.rdy : 0.f;
-    M.az[q] = valid ? A.dt * fabsf(M.xiz[q]) * A.rdz : 0.f;
+  for (int j = 0; j < KPT / 2; ++j) {
+    float v[10][2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k = M.k0 + kp(M, j) + e;
+      const bool valid = k < A.nv;
+      // padding velocities: an enormous speed makes the equilibrium vanish,
+      // zero flux coefficients and zero weight keep them out of everything
+      const float x = valid ? A.xi[k] : 1e18f, y = valid ? A.xi[A.nvp + k] : 1e18f,
+                  zz = valid ? A.xi[2 * A.nvp + k] : 1e18f;
+      v[0][e] = x;
+      v[1][e] = y;
+      v[2][e] = zz;
+      v[3][e] = valid ? A.w[k] : 0.f;
+      v[4][e] = valid ? A.dt * fabsf(x) * A.rdx : 0.f;
+      v[5][e] = valid ? A.dt * fabsf(y) * A.rdy : 0.f;
+      v[6][e] = valid ? A.dt * fabsf(zz) * A.rdz : 0.f;
+      v[7][e] = copysignf(1.f, x);
+      v[8][e] = copysignf(1.f, y);
+      v[9][e] = copysignf(1.f, zz);
+    }
+    M.xix[j] = make_float2(v[0][0], v[0][1]);
+    M.xiy[j] = make_float2(v[1][0], v[1][1]);
+    M.xiz[j] = make_float2(v[2][0], v[2][1]);
+    M.wk[j] = make_float2(v[3][0], v[3][1]);
+    M.ax[j] = make_float2(v[4][0], v[4][1]);
+    M.ay[j] = make_float2(v[5][0], v[5][1]);
+    M.az[j] = make_float2(v[6][0], v[6][1]);
+    M.sx[j] = make_float2(v[7][0], v[7][1]);
+    M.sy[j] = make_float2(v[8][0], v[8][1]);
+    M.sz[j] = make_float2(v[9][0], v[9][1]);
   }
   for (int i = threadIdx.x; i < C::KC; i += NTHREADS) {
     M.sfinf[i] = A.finf[M.k0 + i];
@@ -542,11 +634,11 @@ __device__ __forceinline__ bool march3d(const Tma3Args &A, const CUtensorMap *tm
   auto own = [&](int r, Ring<KPT> &v) {
     if (r < 0 || r >= A.nz || !M.col_in) {
 #pragma unroll
-      for (int q = 0; q < KPT; ++q) v[q] = M.sfinf[klo(M, q)];
+      for (int j = 0; j < KPT / 2; ++j) v[j] = lds2(M.sfinf, kp(M, j));
     } else {
       const float *src = A.f + (size_t)(M.plane + (long long)r * A.nx * A.ny) * A.nvp + M.k0;
 #pragma unroll
-      for (int q = 0; q < KPT; ++q) v[q] = src[klo(M, q)];
+      for (int j = 0; j < KPT / 2; ++j) v[j] = *reinterpret_cast<const float2 *>(src + kp(M, j));
     }
   };
   Ring<KPT> R0, R1, R2, P0, P1, P2;
@@ -570,11 +662,11 @@ __device__ __forceinline__ bool march3d(const Tma3Args &A, const CUtensorMap *tm
     ok = plane_step(M, z, par, mc, R0, R1, R2, P0, P1, P2);
     if (!ok) break;
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      R0[q] = R1[q];
-      R1[q] = R2[q];
-      P0[q] = P1[q];
-      P1[q] = P2[q];
+    for (int j = 0; j < KPT / 2; ++j) {
+      R0[j] = R1[j];
+      R1[j] = R2[j];
+      P0[j] = P1[j];
+      P1[j] = P2[j];
     }
     par ^= 1;
   }
