@@ -122,7 +122,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
 }
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
   if (mbar_try(bar, parity)) return true;
-  for (long i = 0; i < kSpinLimit; ++i)
+  for (int i = 0; i < (int)kSpinLimit; ++i)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -197,6 +197,13 @@ template <int KPT> struct March3 {
   float2 sx[KPT / 2], sy[KPT / 2], sz[KPT / 2];
   uint8_t mask_next;
   bool abort_local;
+  bool inner_xy;     // the column is fluid-capable away from the x and y domain edges
+  long long nxy;     // cells per plane
+  // running pointers of the current plane z, advanced by one plane per step
+  const uint8_t *cm_plane; // flags of plane z
+  const float *mac_next;   // this lane's parameter of the cell at plane z + 1
+  float *fn_cell;          // f^{n+1} of the own cell, first chunk velocity
+  float *part_cell;        // moment partial sums of the own cell, sum index lane >> 1
   const int4 *duty; // [2][NTHREADS]: x faces, then y faces
 };
 
@@ -315,7 +322,7 @@ __device__ __forceinline__ void halo_face(const March3<KPT> &M, const float *sp,
     dst[out] = M.sfinf[kk];
     return;
   }
-  const uint8_t m = A.cmask[d.z + (long long)z * A.nx * A.ny];
+  const uint8_t m = M.cm_plane[d.z];
   if (m & (kNotFluid | (3u << (2 * a)))) { // rare: not fluid, or a ghost neighbour along the axis
     const float xi = (a == 0) ? M.sxi[kk] : M.syi[kk];
     const int line = threadIdx.x / C::KC;
@@ -337,13 +344,12 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
                                            Ring<KPT> &Pc) {
   using C = Cfg<KPT>;
   const Tma3Args &A = M.A;
-  const long long cell = M.plane + (long long)z * A.nx * A.ny;
+  const long long cell = M.plane + (long long)z * M.nxy;
   const uint8_t m0 = mc;
   const bool fluid = !(m0 & kNotFluid);
-  const float pre_next =
-      (M.lane < kMac && M.col_in && z + 1 < A.nz) ? __ldg(A.mac + (cell + (long long)A.nx * A.ny) * kMac + M.lane) : 0.f;
+  const float pre_next = (M.lane < kMac && M.col_in && z + 1 < A.nz) ? __ldg(M.mac_next) : 0.f;
   const uint8_t mn = M.mask_next;
-  const uint8_t mn2 = M.col_in ? ((z + 2 < A.nz) ? cmask3(M, M.x, M.y, z + 2) : 0) : kNotFluid;
+  const uint8_t mn2 = M.col_in ? ((z + 2 < A.nz) ? M.cm_plane[2 * M.nxy + M.plane] : 0) : kNotFluid;
   const int st = M.st;
   int st2 = st + 2;
   unsigned pb2 = M.pb;
@@ -366,7 +372,7 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
   float *phy = M.phy + par * C::PY_FLOATS; // [TY + 2][TX][KC]
   // (2) downwind x and y faces of the own cell
   float2 PX[KPT / 2], PY[KPT / 2];
-  const bool fast = M.col_in && fluid && !(m0 & 15) && M.x > 0 && M.x + 1 < A.nx && M.y > 0 && M.y + 1 < A.ny;
+  const bool fast = M.inner_xy && fluid && !(m0 & 15);
   if (fast) {
     const float *px_lo = sp + slot(M.ti - 1, M.tj) * C::KC, *px_hi = sp + slot(M.ti + 1, M.tj) * C::KC;
     const float *py_lo = sp + slot(M.ti, M.tj - 1) * C::KC, *py_hi = sp + slot(M.ti, M.tj + 1) * C::KC;
@@ -470,9 +476,8 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
     }
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = a[m].x + a[m].y;
-    float *dst = A.fn + (size_t)cell * A.nvp + M.k0;
 #pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) *reinterpret_cast<float2 *>(dst + kp(M, j)) = out[j];
+    for (int j = 0; j < KPT / 2; ++j) *reinterpret_cast<float2 *>(M.fn_cell + kp(M, j)) = out[j];
   }
   // (6) butterfly of the 16 (14 used) sums over the 32 lanes
   {
@@ -505,13 +510,15 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
     float v1 = (b2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? v2[0] : v2[1], 2);
     v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
     // lane l holds sum index 8 b4(l) + 4 b3(l) + 2 b2(l) + b1(l) = l >> 1
-    const int idx = lane >> 1;
-    if (M.col_in && (lane & 1) == 0 && idx < NM)
-      A.part[((size_t)(M.k0 / C::KC) * NM + idx) * M.nc + cell] = v1;
+    if (M.col_in && (lane & 1) == 0 && (lane >> 1) < NM) *M.part_cell = v1;
   }
   if (M.lane < kMac) M.smac[((par ^ 1) * NW + M.warp) * kMac + M.lane] = pre_next;
   M.mask_next = mn2;
   mc = mn;
+  M.cm_plane += M.nxy;
+  M.mac_next += M.nxy * kMac;
+  M.fn_cell += M.nxy * A.nvp;
+  M.part_cell += M.nxy;
   if (++M.st == NST) {
     M.st = 0;
     M.pb ^= 1u;
@@ -554,6 +561,13 @@ __device__ __forceinline__ bool march3d(const Tma3Args &A, const CUtensorMap *tm
   M.zlast = min(A.nz, M.z1 + 2);
   M.nc = A.ncell;
   M.plane = M.x + (long long)A.nx * M.y;
+  M.nxy = (long long)A.nx * A.ny;
+  M.inner_xy = M.col_in && M.x > 0 && M.x + 1 < A.nx && M.y > 0 && M.y + 1 < A.ny;
+  M.cm_plane = A.cmask + (long long)M.z0 * M.nxy;
+  M.mac_next = A.mac + (M.plane + (long long)(M.z0 + 1) * M.nxy) * kMac + (M.lane < kMac ? M.lane : 0);
+  M.fn_cell = A.fn + (size_t)(M.plane + (long long)M.z0 * M.nxy) * A.nvp + M.k0;
+  M.part_cell = A.part + ((size_t)(M.k0 / C::KC) * NM + ((M.lane >> 1) < NM ? (M.lane >> 1) : 0)) * M.nc + M.plane +
+                (long long)M.z0 * M.nxy;
   M.st = 0;
   M.pb = 0;
   M.abort_local = false;
