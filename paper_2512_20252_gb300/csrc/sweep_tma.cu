@@ -120,7 +120,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
 // bounded wait: false after kSpinLimit polls
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
   if (mbar_try(bar, parity)) return true;
-  for (long i = 0; i < kSpinLimit; ++i)
+  for (int i = 0; i < (int)kSpinLimit; ++i)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -183,6 +183,15 @@ template <int KPT> struct March {
   float pre_mac;             // lanes 0..kMac-1: one parameter of the next row's cell
   uint8_t mask_next2;        // flags of (x, y + 2)
   bool abort_local;
+  bool inner_x;              // the column is inside the domain, away from its x edges
+  // the halo column face this thread owns (threads below KC): chunk velocity,
+  // column, its slot in a staged row, its face slot
+  int h_kk, h_col, h_scol, h_out;
+  // running pointers of row y, advanced by one row per step
+  const uint8_t *cm_row;     // flags of row y
+  const float *mac_next;     // this lane's parameter of the cell at row y + 1
+  float *fn_cell;            // f^{n+1} of the own cell, first chunk velocity
+  float *part_cell;          // moment partial sums of the own cell (sum index of the lane)
 };
 
 // velocity q of a lane: k = k0 + lane + 32 q, so a warp touches 32 consecutive
@@ -266,10 +275,9 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
   const bool fluid = !(m0 & kNotFluid);
   // prefetch for the next row: one cell parameter per lane, the flags of (x, y + 3);
   // this row's parameters were staged in shared memory by the previous row
-  const float pre_next = (M.lane < kMac && M.col_in && y + 1 < A.ny)
-                             ? __ldg(A.mac + (cell + A.nx) * kMac + M.lane) : 0.f;
+  const float pre_next = (M.lane < kMac && M.col_in && y + 1 < A.ny) ? __ldg(M.mac_next) : 0.f;
   const uint8_t mn = M.mask_next2; // flags of (x, y + 1), loaded a row ahead
-  const uint8_t mn3 = M.col_in ? ((y + 2 < A.ny) ? cmask_of(M, M.x, y + 2) : 0) : kNotFluid;
+  const uint8_t mn3 = M.col_in ? ((y + 2 < A.ny) ? M.cm_row[2 * A.nx + M.x] : 0) : kNotFluid;
   // stages of rows y and y + 2
   const int st = M.st;
   int st2 = st + 2;
@@ -292,13 +300,12 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
   float *ph = M.phix + par * C::PHI_FLOATS;            // [TX + 2][KC][2]
   // (2) downwind x face of the own cell
   Ring<KPT> PX;
-  if (M.col_in && fluid && !(m0 & (kXm | kXp)) && M.x > 0 && M.x + 1 < A.nx) {
+  if (M.inner_x && fluid && !(m0 & (kXm | kXp))) {
     const float *pc = srow + (M.warp + 2) * C::KC2;
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      const int o = (M.xix[q] >= 0.f) ? C::KC2 : -C::KC2; // toward the downwind neighbour
-      PX[q] = face_dir(Ra[q], sm2<KPT>(pc - o, klo(M, q)), sm2<KPT>(pc + o, klo(M, q)));
-    }
+    for (int q = 0; q < KPT; ++q)
+      PX[q] = face2(Ra[q], sm2<KPT>(pc - C::KC2, klo(M, q)), sm2<KPT>(pc + C::KC2, klo(M, q)),
+                    dup(copysignf(1.f, M.xix[q])));
   } else {
 #pragma unroll
     for (int q = 0; q < KPT; ++q)
@@ -308,12 +315,11 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
   for (int q = 0; q < KPT; ++q) *reinterpret_cast<float2 *>(ph + (M.warp + 1) * C::KC2 + 2 * klo(M, q)) = PX[q];
   // the halo column that is upwind of the block for each velocity: x0 - 1
   // for xi_x >= 0, x0 + TX otherwise; one velocity per thread
-  for (int kk = threadIdx.x; kk < C::KC; kk += NTHREADS) {
-    const float xi = M.sxi[kk];
-    const bool left = xi >= 0.f;
-    const int hc = left ? M.x0 - 1 : M.x0 + TX;
-    const float2 o = phi_x_one(M, srow, hc, left ? 1 : TX + 2, y, cmask_of(M, hc, y), kk, xi);
-    *reinterpret_cast<float2 *>(ph + (left ? 0 : TX + 1) * C::KC2 + 2 * kk) = o;
+  static_assert(Cfg<KPT>::KC <= NTHREADS, "one halo face per thread at most");
+  if (threadIdx.x < C::KC) {
+    const uint8_t hm = (M.h_col >= 0 && M.h_col < A.nx) ? M.cm_row[M.h_col] : 0;
+    const float2 o = phi_x_one(M, srow, M.h_col, M.h_scol, y, hm, M.h_kk, M.sxi[M.h_kk]);
+    *reinterpret_cast<float2 *>(ph + M.h_out) = o;
   }
   // (3) downwind y face of row y + 1
   phi_y(M, y + 1, mn, Rb, Ra, Rc, Pc);
@@ -381,9 +387,8 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
       a45.y = fmaf(cy, cxwh, a45.y);
       a6 = fmaf(cy * cy, wh, a6);
     }
-    float *dst = A.fn + ((size_t)cell * A.nvp + M.k0) * 2;
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) *reinterpret_cast<float2 *>(dst + 2 * klo(M, q)) = out[q];
+    for (int q = 0; q < KPT; ++q) *reinterpret_cast<float2 *>(M.fn_cell + 2 * klo(M, q)) = out[q];
   }
   // (6) butterfly reduction of the sums over the 32 lanes: three rounds halve
   //     the eight values a lane holds, two more finish the one it keeps; the
@@ -415,14 +420,17 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
     if (M.col_in) {
-      float *pp = A.part + (size_t)(M.k0 / C::KC) * NM * M.nc + cell;
-      if ((lane & 3) == 0) pp[(size_t)(lane >> 2) * M.nc] = v1;
-      if (lane == 1) pp[(size_t)8 * M.nc] = s8;
+      if ((lane & 3) == 0) *M.part_cell = v1;
+      if (lane == 1) *M.part_cell = s8;
     }
   }
   if (M.lane < kMac) M.smac[((par ^ 1) * TX + M.warp) * kMac + M.lane] = pre_next;
   M.mask_next2 = mn3;
   mc = mn;
+  M.cm_row += A.nx;
+  M.mac_next += (size_t)A.nx * kMac;
+  M.fn_cell += (size_t)A.nx * A.nvp * 2;
+  M.part_cell += A.nx;
   if (++M.st == NST) {
     M.st = 0;
     M.pb ^= 1u;
@@ -455,6 +463,22 @@ __device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf
   M.x = M.x0 + M.warp;
   M.col_in = M.x < A.nx;
   M.nc = A.ncell;
+  M.inner_x = M.col_in && M.x > 0 && M.x + 1 < A.nx;
+  M.cm_row = A.cmask + (long long)A.nx * M.y0;
+  M.mac_next = A.mac + (M.x + (long long)A.nx * (M.y0 + 1)) * kMac + (M.lane < kMac ? M.lane : 0);
+  M.fn_cell = A.fn + ((size_t)(M.x + (long long)A.nx * M.y0) * A.nvp + M.k0) * 2;
+  {
+    // lanes 4 i write sum i (i < 8); lane 1 writes the ninth sum
+    const int sidx = ((M.lane & 3) == 0) ? (M.lane >> 2) : 8;
+    M.part_cell = A.part + ((size_t)(M.k0 / C::KC) * NM + sidx) * M.nc + M.x + (long long)A.nx * M.y0;
+  }
+  if (threadIdx.x < C::KC) {
+    M.h_kk = threadIdx.x;
+    const bool left = A.xi[M.k0 + M.h_kk] >= 0.f; // the halo column upwind of the block
+    M.h_col = left ? M.x0 - 1 : M.x0 + TX;
+    M.h_scol = left ? 1 : TX + 2;
+    M.h_out = (left ? 0 : TX + 1) * C::KC2 + 2 * M.h_kk;
+  }
   M.st = 0;
   M.pb = 0;
   M.abort_local = false;
