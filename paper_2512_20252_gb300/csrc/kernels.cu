@@ -384,22 +384,38 @@ __device__ __forceinline__ void finalize_body(const FinalArgs<T, P> &A, const in
     Wn[0] = rho;
     for (int a = 0; a < D; ++a) Wn[1 + a] = rho * V[a] + M1[a];
     Wn[D + 1] = rhoE;
-    const double p = 0.5 * rho * T_;
-    const double mu = A.mu0 * pow(T_, A.omega); // Eq. viscosity, T0 = 1
-    const double dtau = A.dt * p / mu;           // tau = mu / p
+    T *Mc = A.mac;
+    double dtau;
+    if constexpr (std::is_same<T, float>::value) {
+      // the mixed path stores the Shakhov parameters in FP32: take them in
+      // FP32 (W, q and the residual above stay FP64)
+      const float Tf = (float)T_, rf = (float)rho;
+      const float mu = (float)A.mu0 * powf(Tf, (float)A.omega); // Eq. viscosity, T0 = 1
+      const float dtf = (float)A.dt * (0.5f * rf * Tf) / mu;     // tau = mu / p
+      dtau = dtf;
+      const float piT = (float)kPi * Tf;
+      Mc[c * kMac + kPre] = (D == 2) ? rf / piT : rf / (piT * sqrtf(piT));
+      Mc[c * kMac + kInvT] = 1.f / Tf;
+      Mc[c * kMac + kHalfT] = 0.5f * Tf;
+      Mc[c * kMac + kShA] = 4.f * (1.f - (float)A.Pr) / (5.f * rf * Tf * Tf);
+      Mc[c * kMac + kDtTau] = dtf;
+    } else {
+      const double p = 0.5 * rho * T_;
+      const double mu = A.mu0 * pow(T_, A.omega); // Eq. viscosity, T0 = 1
+      dtau = A.dt * p / mu;                         // tau = mu / p
+      Mc[c * kMac + kPre] = (T)((D == 2) ? rho / (kPi * T_) : rho / pow(kPi * T_, 1.5));
+      Mc[c * kMac + kInvT] = (T)(1.0 / T_);
+      Mc[c * kMac + kHalfT] = (T)(0.5 * T_);
+      Mc[c * kMac + kShA] = (T)(4.0 * (1.0 - A.Pr) / (5.0 * rho * T_ * T_));
+      Mc[c * kMac + kDtTau] = (T)dtau;
+    }
     const bool bad = !(rho > 0.0) || !(T_ > 0.0) || !isfinite(rhoE) || !isfinite(dtau);
     if (bad) atomicOr(A.flags, kFlagNonFinite);
     if (dtau > 1.0) atomicOr(A.flags, kFlagUnstable);
-    T *Mc = A.mac;
-    Mc[c * kMac + kPre] = (T)((D == 2) ? rho / (kPi * T_) : rho / pow(kPi * T_, 1.5));
     for (int a = 0; a < 3; ++a) {
       Mc[c * kMac + kU0 + a] = (T)((a < D) ? V[a] + d[a] : 0.0);
       Mc[c * kMac + kQ0 + a] = (T)((a < D) ? q[a] : 0.0);
     }
-    Mc[c * kMac + kInvT] = (T)(1.0 / T_);
-    Mc[c * kMac + kHalfT] = (T)(0.5 * T_);
-    Mc[c * kMac + kShA] = (T)(4.0 * (1.0 - A.Pr) / (5.0 * rho * T_ * T_));
-    Mc[c * kMac + kDtTau] = (T)dtau;
     for (int a = 0; a < D; ++a) A.Wnew[(NW + a) * nc + c] = q[a];
     for (int i = 0; i < NW; ++i) {
       A.Wnew[i * nc + c] = Wn[i];

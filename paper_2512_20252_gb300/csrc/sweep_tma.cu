@@ -15,8 +15,8 @@
 //     mbarriers, issued NST - 3 rows ahead, so HBM is read once per row and
 //     the x stencil comes from shared memory;
 //   * each lane keeps its column's y stencil in registers (f at rows y..y+2
-//     and the reconstructed faces of rows y-1..y+1); the row loop is unrolled
-//     three times so that the ring rotates by renaming, without moves;
+//     and the reconstructed faces of rows y-1..y+1), rotated by moves (one copy
+//     of the row body keeps the instruction cache warm);
 //   * x faces are exchanged through shared memory: every warp publishes the
 //     face value of its own cell on the downwind side and reads its upwind
 //     neighbour's as the inflow face; the faces of the two halo columns are
@@ -540,16 +540,16 @@ __device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf
   int y = M.y0;
   int par = 0;
   bool ok = true;
-  // three rows per trip: the ring rotates by renaming
-  while (ok && y < M.y1) {
+  for (; y < M.y1; ++y) {
     ok = row(M, y, par, mc, R0, R1, R2, P0, P1, P2);
-    if (!ok || ++y >= M.y1) break;
-    par ^= 1;
-    ok = row(M, y, par, mc, R1, R2, R0, P1, P2, P0);
-    if (!ok || ++y >= M.y1) break;
-    par ^= 1;
-    ok = row(M, y, par, mc, R2, R0, R1, P2, P0, P1);
-    ++y;
+    if (!ok) break;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      R0[q] = R1[q];
+      R1[q] = R2[q];
+      P0[q] = P1[q];
+      P1[q] = P2[q];
+    }
     par ^= 1;
   }
   if (!ok && threadIdx.x == 0) {
