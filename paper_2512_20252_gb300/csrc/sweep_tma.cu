@@ -177,8 +177,8 @@ template <int KPT> struct March {
   bool col_in;
   long long nc;
   float xix[KPT], xiy[KPT], wk[KPT];
-  float2 ax2[KPT], ay2[KPT]; // dt |xi_a| / dx_a, packed for (h, b)
-  float2 sy2[KPT];           // sign of xi_y, packed
+  float ax[KPT], ay[KPT];    // dt |xi_a| / dx_a
+  float sy[KPT];             // sign of xi_y
   float *smac;               // [2][TX][kMac]: cell parameters of rows y and y + 1
   float pre_mac;             // lanes 0..kMac-1: one parameter of the next row's cell
   uint8_t mask_next2;        // flags of (x, y + 2)
@@ -250,7 +250,7 @@ __device__ __forceinline__ void phi_y(const March<KPT> &M, int r, uint8_t m, con
   }
   if (!(m & (kYm | kYp))) { // fast path
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) out[q] = face2(fr[q], lo[q], hi[q], M.sy2[q]);
+    for (int q = 0; q < KPT; ++q) out[q] = face2(fr[q], lo[q], hi[q], dup(M.sy[q]));
     return;
   }
   const long long c = M.x + (long long)M.A.nx * r;
@@ -258,7 +258,7 @@ __device__ __forceinline__ void phi_y(const March<KPT> &M, int r, uint8_t m, con
   for (int q = 0; q < KPT; ++q) {
     const float2 l = (m & kYm) ? link_value(M.A, c, 2, kof(M, q)) : lo[q];
     const float2 h = (m & kYp) ? link_value(M.A, c, 3, kof(M, q)) : hi[q];
-    out[q] = face2(fr[q], l, h, M.sy2[q]);
+    out[q] = face2(fr[q], l, h, dup(M.sy[q]));
   }
 }
 
@@ -370,8 +370,8 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
       // forward Euler: relaxation and the flux divergence of both axes,
       // |xi_a| dt / dx_a (inflow face - outflow face)
       float2 n = __ffma2_rn(Ra[q], omd, __fmul2_rn(dt2, G));
-      n = __ffma2_rn(M.ax2[q], sub2(ix, PX[q]), n);
-      n = __ffma2_rn(M.ay2[q], sub2(iy, Pb[q]), n);
+      n = __ffma2_rn(dup(M.ax[q]), sub2(ix, PX[q]), n);
+      n = __ffma2_rn(dup(M.ay[q]), sub2(iy, Pb[q]), n);
       out[q] = n;
       // moments of the new state about the stored bulk velocity
       const float wh = M.wk[q] * n.x;
@@ -491,9 +491,9 @@ __device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf
     M.xix[q] = valid ? A.xi[k] : 1e18f;
     M.xiy[q] = valid ? A.xi[A.nvp + k] : 1e18f;
     M.wk[q] = valid ? A.w[k] : 0.f;
-    M.ax2[q] = dup(valid ? A.dt * fabsf(M.xix[q]) * A.rdx : 0.f);
-    M.ay2[q] = dup(valid ? A.dt * fabsf(M.xiy[q]) * A.rdy : 0.f);
-    M.sy2[q] = dup(copysignf(1.f, M.xiy[q]));
+    M.ax[q] = valid ? A.dt * fabsf(M.xix[q]) * A.rdx : 0.f;
+    M.ay[q] = valid ? A.dt * fabsf(M.xiy[q]) * A.rdy : 0.f;
+    M.sy[q] = copysignf(1.f, M.xiy[q]);
   }
   // parameters of the first row's cells, and the flags of row y0 + 1
   if (M.lane < kMac)
