@@ -226,6 +226,18 @@ ibdvm_status ibdvm_residual_noalloc(const double *W_old, const double *W_new,
                                     const unsigned char *celltype, long long ncell, int dim,
                                     double *residual, void *cuda_stream);
 
+/* Check of the bounded device waits (the paper has no counterpart).  The
+   TMA-staged sweeps wait on mbarriers for their tile copies with a bound and
+   report IBDVM_E_TIMEOUT instead of hanging when a copy never arrives; this
+   runs that same bounded wait in a one-block kernel on a barrier that expects
+   16 bytes, delivered by a bulk copy (deliver != 0: returns IBDVM_OK) or never
+   delivered (deliver == 0: the wait gives up after spin_limit polls and the
+   call returns IBDVM_E_TIMEOUT, the context of the device still usable).
+   seconds (nullable) receives the wall time of the call.  spin_limit in
+   [0, 2^18] (a poll suspends a few microseconds on GB300, so 2^18 polls are about
+   one second, the bound of the sweeps); errors: IBDVM_E_INVAL, IBDVM_E_CUDA. */
+ibdvm_status ibdvm_selftest_bounded_wait(int deliver, int spin_limit, double *seconds, void *cuda_stream);
+
 ibdvm_status ibdvm_get_info(const ibdvm_ctx *ctx, ibdvm_info *info);
 ibdvm_status ibdvm_set_stream(ibdvm_ctx *ctx, void *cuda_stream);
 /* Geometry of the context (host copy); see ibdvm_geom_* for the layouts. */
@@ -349,7 +361,8 @@ typedef struct {
 typedef struct {
   long long id;
   int done;              /* 1 when the request has left the device */
-  int status;            /* IBDVM_OK (converged), IBDVM_E_NOTCONVERGED (step cap), or the error */
+  int status;            /* IBDVM_OK (converged), IBDVM_E_NOTCONVERGED (step cap), IBDVM_E_STATE
+                            (cancelled), or the error */
   long long steps;       /* steps taken */
   double residual;       /* residual of the last step */
   double F[3], Q, CD, CL; /* as ibdvm_forces, on the final state */
@@ -372,6 +385,12 @@ ibdvm_status ibdvm_server_submit(ibdvm_server *s, const ibdvm_grid_desc *grid, c
    request that fails is retired with its status; the call itself fails only
    on a CUDA error of the loop. */
 ibdvm_status ibdvm_server_poll(ibdvm_server *s, int *nactive, int *nqueued, int *nfinished);
+/* Cancels request id between polls: a queued request leaves the queue, an
+   admitted one leaves the device (its memory is freed) with the force and
+   heat flux of its current state; either is done with status IBDVM_E_STATE.
+   Cancelling a finished request does nothing.  The other requests are not
+   affected.  Errors: IBDVM_E_INVAL (unknown id). */
+ibdvm_status ibdvm_server_cancel(ibdvm_server *s, long long id);
 /* The state of request id (done = 0 while queued or on the device).
    Errors: IBDVM_E_INVAL (unknown id). */
 ibdvm_status ibdvm_server_result(ibdvm_server *s, long long id, ibdvm_result *out);

@@ -274,6 +274,30 @@ ibdvm_status ibdvm_server_poll(ibdvm_server *s, int *nactive, int *nqueued, int 
   return IBDVM_OK;
 }
 
+ibdvm_status ibdvm_server_cancel(ibdvm_server *s, long long id) {
+  if (!s) return IBDVM_E_INVAL;
+  s->err.clear();
+  auto it = s->all.find(id);
+  if (it == s->all.end()) {
+    s->err = "unknown request id";
+    return IBDVM_E_INVAL;
+  }
+  Req *q = it->second;
+  if (q->r.done) return IBDVM_OK;
+  auto qi = std::find(s->queue.begin(), s->queue.end(), q);
+  if (qi != s->queue.end()) { // not admitted yet
+    s->queue.erase(qi);
+    q->r.status = IBDVM_E_STATE;
+    q->r.done = 1;
+    q->r.t_done = now(s);
+    return IBDVM_OK;
+  }
+  // on the device: its batch is idle between polls, so it leaves at once
+  finish(s, q, IBDVM_E_STATE);
+  s->active.erase(std::remove(s->active.begin(), s->active.end(), q), s->active.end());
+  return IBDVM_OK;
+}
+
 ibdvm_status ibdvm_server_result(ibdvm_server *s, long long id, ibdvm_result *out) {
   if (!s || !out) return IBDVM_E_INVAL;
   auto it = s->all.find(id);

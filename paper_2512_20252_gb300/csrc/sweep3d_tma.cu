@@ -39,9 +39,12 @@
 #include <vector>
 
 #include "ctx.h"
+#include "tma_sync.cuh"
 
 namespace ibdvm {
 namespace {
+
+using namespace dev;
 
 constexpr int TX = 4, TY = 4;   // tile of columns, one warp each
 constexpr int NW = TX * TY;     // warps per block
@@ -49,7 +52,6 @@ constexpr int NTHREADS = NW * 32;
 constexpr int NST = 5;          // TMA plane stages
 constexpr int NCELL = TX * TY + 2 * (2 * TY) + 2 * (2 * TX); // cells of the cross-shaped slab (48)
 constexpr int NM = 14;          // moment sums (3D)
-constexpr long kSpinLimit = 1L << 22;
 
 // slot of slab cell (i, j), i in [-2, TX+2), j in [-2, TY+2), cross-shaped
 __device__ __forceinline__ int slot(int i, int j) {
@@ -89,20 +91,6 @@ struct Tma3Args {
   float dt, rdx, rdy, rdz;
 };
 
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
-  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
 __device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
                                         uint64_t *bar) {
   asm volatile(
@@ -110,26 +98,6 @@ __device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *tm, int c0
           smem_addr(dst)),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
       : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-  if (mbar_try(bar, parity)) return true;
-  for (int i = 0; i < (int)kSpinLimit; ++i)
-    if (mbar_try(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
 }
 // half the van Leer slope times the cell width from the one-sided differences
 // a = f - f_up and b = f_dn - f along the direction of motion (Eq. limiter)
@@ -141,20 +109,6 @@ __device__ __forceinline__ float vl_half(float a, float b) {
 // downwind face value: f plus half the slope along the motion
 __device__ __forceinline__ float face(float f, float up, float dn) { return f + vl_half(f - up, dn - f); }
 
-// the same for a pair of velocities (packed FP32)
-__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
-__device__ __forceinline__ float2 vl_half2(float2 a, float2 b) {
-  const float2 p = __fmul2_rn(a, b);
-  const float2 s = __fadd2_rn(a, b);
-  const float2 v = __fmul2_rn(p, make_float2(rcp_approx(s.x), rcp_approx(s.y)));
-  return make_float2(p.x > 0.f ? v.x : 0.f, p.y > 0.f ? v.y : 0.f);
-}
-// downwind face from the low and high neighbours and the sign s of the velocity:
-// f + s vl(f - lo, hi - f) equals f + vl(f - up, dn - f) since vl is symmetric and odd
-__device__ __forceinline__ float2 face2(float2 f, float2 lo, float2 hi, float2 s) {
-  return __ffma2_rn(s, vl_half2(sub2(f, lo), sub2(hi, f)), f);
-}
 __device__ __forceinline__ float2 lds2(const float *base, int kk) { return *reinterpret_cast<const float2 *>(base + kk); }
 
 __device__ __forceinline__ float link_value(const Tma3Args &A, long long c, int dir, int k) {

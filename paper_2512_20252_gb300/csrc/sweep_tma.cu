@@ -40,16 +40,18 @@
 #include <vector>
 
 #include "ctx.h"
+#include "tma_sync.cuh"
 
 namespace ibdvm {
 namespace {
+
+using namespace dev;
 
 constexpr int TX = 8;       // interior columns per block, one warp each
 constexpr int NST = 6;      // TMA row stages
 constexpr int COLS = TX + 4;
 constexpr int NTHREADS = TX * 32;
 constexpr int NM = 9;       // moment sums (2D)
-constexpr long kSpinLimit = 1L << 22; // bounded mbarrier waits
 
 template <int KPT> struct Cfg {
   static constexpr int KC = 32 * KPT;
@@ -82,25 +84,6 @@ struct TmaArgs {
 // PTX helpers
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
-  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
 __device__ __forceinline__ void tma_row(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, uint64_t *bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
@@ -108,51 +91,8 @@ __device__ __forceinline__ void tma_row(void *dst, const CUtensorMap *tm, int c0
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
       : "memory");
 }
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: false after kSpinLimit polls
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-  if (mbar_try(bar, parity)) return true;
-  for (int i = 0; i < (int)kSpinLimit; ++i)
-    if (mbar_try(bar, parity)) return true;
-  return false;
-}
 
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
 
-// Half the van Leer slope times the cell width for the (h, b) pair, from the
-// one-sided differences a = f - f_lo and b = f_hi - f (Eq. limiter):
-// ab / (a + b) where a and b have the same sign, 0 otherwise.  Packed FP32
-// arithmetic on both components at once.
-__device__ __forceinline__ float2 vl_half2(float2 a, float2 b) {
-  const float2 p = __fmul2_rn(a, b);
-  const float2 s = __fadd2_rn(a, b);
-  const float2 v = __fmul2_rn(p, make_float2(rcp_approx(s.x), rcp_approx(s.y)));
-  return make_float2(p.x > 0.f ? v.x : 0.f, p.y > 0.f ? v.y : 0.f);
-}
-__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
-// x - y for packed pairs, as one packed FMA
-__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
-// reconstructed face on the downwind side when up / dn are the upwind and
-// downwind neighbours: f + half slope in the direction of motion
-__device__ __forceinline__ float2 face_dir(float2 f, float2 up, float2 dn) {
-  return __fadd2_rn(f, vl_half2(sub2(f, up), sub2(dn, f)));
-}
-// the same with lo / hi neighbours and the packed sign s2 = (s, s) of the velocity
-__device__ __forceinline__ float2 face2(float2 f, float2 lo, float2 hi, float2 s2) {
-  return __ffma2_rn(s2, vl_half2(sub2(f, lo), sub2(hi, f)), f);
-}
 
 __device__ __forceinline__ float2 link_value(const TmaArgs &A, long long c, int dir, int k) {
   const int slot = A.dslot[c];

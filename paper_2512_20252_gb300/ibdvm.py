@@ -112,6 +112,7 @@ SIGNATURES = {
     "ibdvm_ghost_band": ([_V, _D, _D, _D, _D], _S),
     "ibdvm_residual_noalloc": ([_V, _V, _V, ctypes.c_longlong, ctypes.c_int, _V, _V], _S),
     "ibdvm_get_info": ([_V, ctypes.POINTER(Info)], _S),
+    "ibdvm_selftest_bounded_wait": ([ctypes.c_int, ctypes.c_int, _D, _V], _S),
     "ibdvm_set_stream": ([_V, _V], _S),
     "ibdvm_get_geom": ([_V], _V),
     "ibdvm_destroy": ([_V], None),
@@ -148,6 +149,7 @@ SIGNATURES = {
                              ctypes.POINTER(BodyDesc), _LL], _S),
     "ibdvm_server_poll": ([_V, _I, _I, _I], _S),
     "ibdvm_server_result": ([_V, ctypes.c_longlong, ctypes.POINTER(Result)], _S),
+    "ibdvm_server_cancel": ([_V, ctypes.c_longlong], _S),
     "ibdvm_server_clock": ([_V], ctypes.c_double),
     "ibdvm_server_destroy": ([_V], None),
     "ibdvm_server_last_error": ([_V], ctypes.c_char_p),
@@ -236,6 +238,15 @@ def descriptors(case: dict):
 
 def _dp(a):
     return a.ctypes.data_as(_D)
+
+
+def selftest_bounded_wait(deliver: bool, spin_limit: int, stream: int | None = None):
+    """Runs the bounded mbarrier wait of the TMA sweeps on a barrier whose
+    bytes are delivered or never delivered; returns (status, seconds)."""
+    lib = load()
+    sec = ctypes.c_double(0.0)
+    st = lib.ibdvm_selftest_bounded_wait(1 if deliver else 0, int(spin_limit), ctypes.byref(sec), _V(stream or 0))
+    return st, sec.value
 
 
 def residual_noalloc(W_old_ptr: int, W_new_ptr: int, celltype_ptr: int | None, ncell: int, dim: int,
@@ -583,6 +594,9 @@ class Server:
         a, q, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.ibdvm_server_poll(self.h, ctypes.byref(a), ctypes.byref(q), ctypes.byref(f)))
         return a.value, q.value, f.value
+
+    def cancel(self, rid: int):
+        self._check(self.lib.ibdvm_server_cancel(self.h, int(rid)))
 
     def result(self, rid: int) -> dict:
         r = Result()

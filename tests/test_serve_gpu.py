@@ -147,3 +147,28 @@ def test_bad_server_descriptors():
     with pytest.raises(ibdvm.IbdvmError):
         srv.submit(bad)
     srv.close()
+
+
+def test_cancelled_request_leaves_and_the_others_are_unaffected():
+    cases = requests()[:3]
+    ref = ibdvm.Server(tol=0.0, max_steps=30, steps_per_round=10)
+    rr = run(ref, [cases[0], cases[2]])
+    ref.close()
+    srv = ibdvm.Server(tol=0.0, max_steps=30, steps_per_round=10)
+    ids = [srv.submit(c) for c in cases]
+    srv.poll()                 # all three admitted, 10 steps
+    srv.cancel(ids[1])         # leaves the device between polls
+    queued = srv.submit(cases[1])
+    srv.cancel(queued)         # leaves the queue before admission
+    for _ in range(10):
+        na, nq, _ = srv.poll()
+        if na == 0 and nq == 0:
+            break
+    r = [srv.result(i) for i in ids]
+    rq = srv.result(queued)
+    srv.close()
+    assert r[1]["done"] == 1 and r[1]["status"] == 8 and r[1]["steps"] == 10
+    assert rq["done"] == 1 and rq["status"] == 8 and rq["steps"] == 0 and rq["t_admit"] < 0
+    for a, b in zip((r[0], r[2]), rr):
+        assert a["status"] == b["status"] == 6 and a["steps"] == b["steps"] == 30
+        assert (a["CD"], a["CL"], a["Q"]) == (b["CD"], b["CL"], b["Q"])
