@@ -150,6 +150,7 @@ template <int KPT> struct March3 {
   float2 xix[KPT / 2], xiy[KPT / 2], xiz[KPT / 2], wk[KPT / 2], ax[KPT / 2], ay[KPT / 2], az[KPT / 2];
   float2 sx[KPT / 2], sy[KPT / 2], sz[KPT / 2];
   uint8_t mask_next;
+  uint16_t hm_next;  // flags of this thread's two halo cells at plane z (x | y << 8)
   bool abort_local;
   bool inner_xy;     // the column is fluid-capable away from the x and y domain edges
   long long nxy;     // cells per plane
@@ -265,31 +266,38 @@ __device__ __forceinline__ void phi_z(const March3<KPT> &M, int r, uint8_t m, co
 }
 
 // the halo face of axis a owned by this thread at plane z
+// the general halo face of axis a owned by this thread at plane z (not fluid,
+// or a ghost neighbour along the axis)
 template <int KPT, int a>
-__device__ __forceinline__ void halo_face(const March3<KPT> &M, const float *sp, int z, float *dst) {
+__device__ __forceinline__ float halo_face_general(const March3<KPT> &M, const float *sp, int z) {
   using C = Cfg<KPT>;
-  const Tma3Args &A = M.A;
-  const int4 d = M.duty[a * NTHREADS + threadIdx.x];
   const int kk = threadIdx.x % C::KC;
-  const int out = d.y >> 16;
-  if (d.z < 0) { // outside the domain: freestream, zero slope
-    dst[out] = M.sfinf[kk];
-    return;
-  }
-  const uint8_t m = M.cm_plane[d.z];
-  if (m & (kNotFluid | (3u << (2 * a)))) { // rare: not fluid, or a ghost neighbour along the axis
-    const float xi = (a == 0) ? M.sxi[kk] : M.syi[kk];
-    const int line = threadIdx.x / C::KC;
-    const int i = (a == 0) ? ((xi >= 0.f) ? -1 : TX) : line;
-    const int j = (a == 0) ? line : ((xi >= 0.f) ? -1 : TY);
-    dst[out] = face_general(M, sp, a, i, j, z, kk, xi);
-    return;
-  }
-  const int up = d.x >> 16, dn = d.y & 0xffff;
-  const float f = sp[d.x & 0xffff];
-  const float fu = up ? sp[up - 1] : M.sfinf[kk];
-  const float fd = dn ? sp[dn - 1] : M.sfinf[kk];
-  dst[out] = face(f, fu, fd);
+  const float xi = (a == 0) ? M.sxi[kk] : M.syi[kk];
+  const int line = threadIdx.x / C::KC;
+  const int i = (a == 0) ? ((xi >= 0.f) ? -1 : TX) : line;
+  const int j = (a == 0) ? line : ((xi >= 0.f) ? -1 : TY);
+  return face_general(M, sp, a, i, j, z, kk, xi);
+}
+
+// the two halo faces this thread owns at plane z (x, then y), evaluated as one
+// packed pair; hm = the flags of the two halo cells at plane z (or 0 outside)
+template <int KPT>
+__device__ __forceinline__ void halo_faces(const March3<KPT> &M, const float *sp, int z, uint16_t hm, float *phx,
+                                           float *phy) {
+  using C = Cfg<KPT>;
+  const int4 dx = M.duty[threadIdx.x], dy = M.duty[NTHREADS + threadIdx.x];
+  const int kk = threadIdx.x % C::KC;
+  const float fin = M.sfinf[kk];
+  const uint8_t mx = hm & 0xff, my = hm >> 8;
+  // per face: freestream outside the domain, the general path where needed
+  const bool gx = dx.z >= 0 && (mx & (kNotFluid | 3u)), gy = dy.z >= 0 && (my & (kNotFluid | 12u));
+  const int ux = dx.x >> 16, nx = dx.y & 0xffff, uy = dy.x >> 16, ny = dy.y & 0xffff;
+  const float2 f = make_float2(sp[dx.x & 0xffff], sp[dy.x & 0xffff]);
+  const float2 up = make_float2(ux ? sp[ux - 1] : fin, uy ? sp[uy - 1] : fin);
+  const float2 dn = make_float2(nx ? sp[nx - 1] : fin, ny ? sp[ny - 1] : fin);
+  const float2 o = __fadd2_rn(f, vl_half2(sub2(f, up), sub2(dn, f)));
+  phx[dx.y >> 16] = (dx.z < 0) ? fin : (gx ? halo_face_general<KPT, 0>(M, sp, z) : o.x);
+  phy[dy.y >> 16] = (dy.z < 0) ? fin : (gy ? halo_face_general<KPT, 1>(M, sp, z) : o.y);
 }
 
 template <int KPT>
@@ -349,8 +357,15 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
     *reinterpret_cast<float2 *>(phy + ((M.tj + 1) * TX + M.ti) * C::KC + kp(M, j)) = PY[j];
   }
   // halo faces on the upwind side of the tile (TY rows in x, TX columns in y)
-  halo_face<KPT, 0>(M, sp, z, phx);
-  halo_face<KPT, 1>(M, sp, z, phy);
+  {
+    const uint16_t hm = M.hm_next;
+    // the flags of the two halo cells at the next plane, a plane ahead of use
+    const int hx = M.duty[threadIdx.x].z, hy = M.duty[NTHREADS + threadIdx.x].z;
+    M.hm_next = (z + 1 < A.nz) ? (uint16_t)((hx >= 0 ? M.cm_plane[M.nxy + hx] : 0) |
+                                            ((hy >= 0 ? M.cm_plane[M.nxy + hy] : 0) << 8))
+                               : (uint16_t)0;
+    halo_faces(M, sp, z, hm, phx, phy);
+  }
   // (3) downwind z face of plane z + 1
   phi_z(M, z + 1, mn, Rb, Ra, Rc, Pc);
   // (4) barrier: faces published, the stage of plane z - 1 released
@@ -584,6 +599,10 @@ __device__ __forceinline__ bool march3d(const Tma3Args &A, const CUtensorMap *tm
       duty[a * NTHREADS + threadIdx.x] =
           make_int4(f_off | (up << 16), dn | (out << 16), outside ? -1 : cx + A.nx * cy, 0);
     }
+  }
+  {
+    const int hx = M.duty[threadIdx.x].z, hy = M.duty[NTHREADS + threadIdx.x].z;
+    M.hm_next = (uint16_t)((hx >= 0 ? M.cm_plane[hx] : 0) | ((hy >= 0 ? M.cm_plane[hy] : 0) << 8));
   }
   if (M.lane < kMac)
     M.smac[M.warp * kMac + M.lane] =
