@@ -95,11 +95,11 @@ template <typename T> std::vector<T> cast(const std::vector<double> &v) {
 
 void free_body(ibdvm_ctx *ctx) {
   void *ps[] = {ctx->dslot, ctx->dlinks, ctx->l_int, ctx->l_dbl, ctx->l_wg, ctx->g_int, ctx->s_int,
-                ctx->s_dbl, ctx->lval, ctx->fi_scr, ctx->fsp_scr, ctx->rhow, ctx->fpart};
+                ctx->s_dbl, ctx->lval, ctx->fi_scr, ctx->fsp_scr, ctx->rhow, ctx->fpart, ctx->gw_unit};
   for (void *p : ps)
     if (p) cudaFree(p);
   ctx->dslot = ctx->dlinks = ctx->l_int = ctx->g_int = ctx->s_int = nullptr;
-  ctx->l_dbl = ctx->l_wg = ctx->s_dbl = ctx->rhow = ctx->fpart = nullptr;
+  ctx->l_dbl = ctx->l_wg = ctx->s_dbl = ctx->rhow = ctx->fpart = ctx->gw_unit = nullptr;
   ctx->lval = ctx->fi_scr = ctx->fsp_scr = nullptr;
 }
 
@@ -235,6 +235,7 @@ void upload_body(ibdvm_ctx *ctx) {
       }
       sd[3] = std::sqrt(rl);
       for (int a = 0; a < D; ++a) sd[4 + a] = (ij[a] - ig[a]) * G.dx[a];
+      sd[7] = 1.0 / sd[3];
     }
   }
   std::vector<uint8_t> ctype(G.type.begin(), G.type.end());
@@ -273,6 +274,7 @@ void upload_body(ibdvm_ctx *ctx) {
     tmp.fsp_scr = dalloc<char>(&tmp, band, "shifted-point scratch");
     tmp.rhow = dalloc<double>(&tmp, nl, "wall density");
     tmp.fpart = dalloc<double>(&tmp, 4 * nl, "force partial sums");
+    tmp.gw_unit = dalloc<double>(&tmp, nvp, "wall Maxwellian");
   } catch (const Fail &f) {
     ctx->err = tmp.err;
     free_body(&tmp);
@@ -292,8 +294,9 @@ void upload_body(ibdvm_ctx *ctx) {
   ctx->fsp_scr = tmp.fsp_scr;
   ctx->rhow = tmp.rhow;
   ctx->fpart = tmp.fpart;
+  ctx->gw_unit = tmp.gw_unit;
   tmp.dslot = tmp.dlinks = tmp.l_int = tmp.s_int = nullptr;
-  tmp.l_dbl = tmp.l_wg = tmp.s_dbl = tmp.rhow = tmp.fpart = nullptr;
+  tmp.l_dbl = tmp.l_wg = tmp.s_dbl = tmp.rhow = tmp.fpart = tmp.gw_unit = nullptr;
   tmp.lval = tmp.fi_scr = tmp.fsp_scr = nullptr;
   ctx->nlink = static_cast<int>(nl);
   ctx->nghost = static_cast<int>(G.ghosts.size());
@@ -305,6 +308,22 @@ void upload_body(ibdvm_ctx *ctx) {
   upload(ctx, ctx->l_wg, l_wg, "upload cut table");
   upload(ctx, ctx->s_int, s_int, "upload surface table");
   upload(ctx, ctx->s_dbl, s_dbl, "upload surface vectors");
+  {
+    // unit-density wall Maxwellian per velocity (Eq. boundary maxwell; the 2D
+    // reduced H_w of Sec. 4): depends on the wall only, so tabulated once
+    std::vector<double> gw(nvp, 0.0);
+    const double Tw = G.body.T_w;
+    const double norm = (D == 2) ? 1.0 / (kPi * Tw) : 1.0 / std::pow(kPi * Tw, 1.5);
+    for (int k = 0; k < G.nv; ++k) {
+      double c2 = 0.0;
+      for (int a = 0; a < D; ++a) {
+        const double c = G.xi[3 * k + a] - G.body.U_w[a];
+        c2 += c * c;
+      }
+      gw[k] = norm * std::exp(-c2 / Tw);
+    }
+    upload(ctx, ctx->gw_unit, gw, "upload wall Maxwellian");
+  }
   upload(ctx, ctx->ctype, ctype, "upload cell classes");
   upload(ctx, ctx->cmask, cmask, "upload cell flags");
   if (nl) {

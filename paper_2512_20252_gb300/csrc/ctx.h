@@ -80,6 +80,7 @@ struct ibdvm_ctx {
   void *fsp_scr = nullptr;   // [nlink][nvp][ncomp] shifted-point value
   double *rhow = nullptr;    // [nlink]
   double *fpart = nullptr;   // [nlink][4] force partial sums
+  double *gw_unit = nullptr; // [nvp] unit-density wall Maxwellian H_w / g_w of the body's wall
   double *d_forces = nullptr; // [4]
   double *d_step_forces = nullptr; // [4] forces of the fluxes the last step applied
   // kernel timing (CUDA events around each launch class, when enabled)

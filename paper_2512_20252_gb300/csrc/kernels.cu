@@ -504,7 +504,8 @@ template <typename T> struct GhostArgs {
   const double *__restrict__ l_dbl; // [nlink][8]: c_sp, c_iw, c_gc, n0, n1, n2, S, -
   const double *__restrict__ l_wg;  // [nlink][nvp]
   const int *__restrict__ s_int;    // [nsurf][8]: cell, codes of the 6 face neighbours
-  const double *__restrict__ s_dbl; // [nsurf][8]: r (weights), |r|, x_j - x_g
+  const double *__restrict__ s_dbl; // [nsurf][8]: r (weights), |r|, x_j - x_g, 1 / |r|
+  const double *__restrict__ gwu;   // [nvp] unit-density wall Maxwellian
   T *__restrict__ lval;
   T *__restrict__ fi;
   T *__restrict__ fsp;
@@ -569,8 +570,10 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
     T wsum = T(0);
     for (int j = 0; j < ns; ++j) {
       const double *sd = G.s_dbl + 8 * (s0 + j);
-      T dot = T(0);
-      for (int a = 0; a < D; ++a) dot = add_rn(dot, div_rn(mul_rn(xiT[a], (T)sd[a]), (T)sd[3]));
+      // xi.r without contraction: tangential velocities give an exact zero
+      T xr = T(0);
+      for (int a = 0; a < D; ++a) xr = add_rn(xr, mul_rn(xiT[a], (T)sd[a]));
+      const T dot = mul_rn(xr, (T)sd[7]);
       T mx = dot > T(0) ? dot : T(0);
       wsum = add_rn(wsum, mul_rn(mx, mx));
     }
@@ -585,8 +588,9 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
       if (fallback) {
         wt = T(1) / T(ns);
       } else {
-        T dot = T(0);
-        for (int a = 0; a < D; ++a) dot = add_rn(dot, div_rn(mul_rn(xiT[a], (T)sd[a]), (T)sd[3]));
+        T xr = T(0);
+        for (int a = 0; a < D; ++a) xr = add_rn(xr, mul_rn(xiT[a], (T)sd[a]));
+        const T dot = mul_rn(xr, (T)sd[7]);
         T mx = dot > T(0) ? dot : T(0);
         wt = mul_rn(mx, mx) / wsum;
       }
@@ -618,13 +622,9 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
       G.fi[((size_t)l * G.nvp + k) * NC + m] = fiv[m];
     }
     // zero-net-mass-flux balance with the cut-cell split (Eq. rhowc), FP64
-    double xn = 0.0, c2 = 0.0;
-    for (int a = 0; a < D; ++a) {
-      const double x = G.xiD[a * G.nvp + k];
-      xn += x * nw[a];
-      c2 += (x - G.Uw[a]) * (x - G.Uw[a]);
-    }
-    const double Gw = ((D == 2) ? 1.0 / (kPi * G.Tw) : 1.0 / pow(kPi * G.Tw, 1.5)) * exp(-c2 / G.Tw);
+    double xn = 0.0;
+    for (int a = 0; a < D; ++a) xn += G.xiD[a * G.nvp + k] * nw[a];
+    const double Gw = G.gwu[k];
     const double wg = wgl[k], ws = G.wD[k] - wg;
     Nsum += wg * xn * (double)fiv[0];
     Dsum += ws * xn * Gw;
@@ -673,13 +673,9 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
   if (threadIdx.x == 0) G.rhow[l] = rho_w;
   // wall distribution (Eqs. general bc, Maxwell BC, fwc) and ghost value (Eq. extrapolation 2)
   for (int k = threadIdx.x; k < G.nv; k += blockDim.x) {
-    double xn = 0.0, c2 = 0.0;
-    for (int a = 0; a < D; ++a) {
-      const double x = G.xiD[a * G.nvp + k];
-      xn += x * nw[a];
-      c2 += (x - G.Uw[a]) * (x - G.Uw[a]);
-    }
-    const double Gw = ((D == 2) ? 1.0 / (kPi * G.Tw) : 1.0 / pow(kPi * G.Tw, 1.5)) * exp(-c2 / G.Tw);
+    double xn = 0.0;
+    for (int a = 0; a < D; ++a) xn += G.xiD[a * G.nvp + k] * nw[a];
+    const double Gw = G.gwu[k];
     double fsv[NC];
 #pragma unroll
     for (int m = 0; m < NC; ++m) fsv[m] = 0.0;
@@ -1007,6 +1003,7 @@ template <typename T> GhostArgs<T> ghost_args(const ibdvm_ctx *ctx, int cur, dou
   G.l_wg = ctx->l_wg;
   G.s_int = ctx->s_int;
   G.s_dbl = ctx->s_dbl;
+  G.gwu = ctx->gw_unit;
   G.lval = static_cast<T *>(ctx->lval);
   G.fi = static_cast<T *>(ctx->fi_scr);
   G.fsp = static_cast<T *>(ctx->fsp_scr);
