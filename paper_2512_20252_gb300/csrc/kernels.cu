@@ -340,11 +340,23 @@ __device__ __forceinline__ void finalize_body(const FinalArgs<T, P> &A, const in
   for (int i = 0; i < NW; ++i) rnum[i] = rden[i] = 0.0;
   if (c < A.ncell && A.ctype[c] == IBDVM_CELL_FLUID) {
     double M[NM];
+    if constexpr (std::is_same<P, float>::value) {
+      // FP32 partial sums of the velocity chunks: added in order by a
+      // Neumaier-compensated FP32 sum and widened once (GB300's FP64 rate is a
+      // small fraction of its FP32 rate)
+      Acc<float> acc[NM];
+      for (int ch = 0; ch < A.nchunk; ++ch)
 #pragma unroll
-    for (int m = 0; m < NM; ++m) M[m] = 0.0;
-    for (int ch = 0; ch < A.nchunk; ++ch)
+        for (int m = 0; m < NM; ++m) acc[m].add(A.part[((size_t)ch * NM + m) * A.ncell + c]);
 #pragma unroll
-      for (int m = 0; m < NM; ++m) M[m] += (double)A.part[((size_t)ch * NM + m) * A.ncell + c];
+      for (int m = 0; m < NM; ++m) M[m] = acc[m].value();
+    } else {
+#pragma unroll
+      for (int m = 0; m < NM; ++m) M[m] = 0.0;
+      for (int ch = 0; ch < A.nchunk; ++ch)
+#pragma unroll
+        for (int m = 0; m < NM; ++m) M[m] += (double)A.part[((size_t)ch * NM + m) * A.ncell + c];
+    }
     const long long nc = A.ncell;
     double V[3] = {0.0, 0.0, 0.0};
     if (A.shift)
