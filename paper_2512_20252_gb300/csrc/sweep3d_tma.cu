@@ -388,9 +388,6 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
     const bool ghosty = (m0 & kGhostAny) != 0;
     const float *xl = phx + (M.tj * (TX + 2) + M.ti) * C::KC, *xr = xl + 2 * C::KC;
     const float *yl = phy + (M.tj * TX + M.ti) * C::KC, *yr = yl + 2 * TX * C::KC;
-    float2 a[NM];
-#pragma unroll
-    for (int m = 0; m < NM; ++m) a[m] = make_float2(0.f, 0.f);
     Ring<KPT> out;
 #pragma unroll
     for (int j = 0; j < KPT / 2; ++j) {
@@ -428,23 +425,27 @@ __device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8
       out[j] = n;
       const float2 wf = __fmul2_rn(M.wk[j], n), e2 = __fmul2_rn(c2, wf);
       const float2 cxw = __fmul2_rn(cx, wf), cyw = __fmul2_rn(cy, wf);
-      a[0] = __fadd2_rn(a[0], wf);
-      a[1] = __fadd2_rn(a[1], cxw);
-      a[2] = __fadd2_rn(a[2], cyw);
-      a[3] = __ffma2_rn(cz, wf, a[3]);
-      a[4] = __fadd2_rn(a[4], e2);
-      a[5] = __ffma2_rn(cx, cxw, a[5]);
-      a[6] = __ffma2_rn(cy, cxw, a[6]);
-      a[7] = __ffma2_rn(cz, cxw, a[7]);
-      a[8] = __ffma2_rn(cy, cyw, a[8]);
-      a[9] = __ffma2_rn(cz, cyw, a[9]);
-      a[10] = __ffma2_rn(__fmul2_rn(cz, cz), wf, a[10]);
-      a[11] = __ffma2_rn(cx, e2, a[11]);
-      a[12] = __ffma2_rn(cy, e2, a[12]);
-      a[13] = __ffma2_rn(cz, e2, a[13]);
-    }
+      const float2 czz = __fmul2_rn(cz, cz);
 #pragma unroll
-    for (int m = 0; m < NM; ++m) acc[m] = a[m].x + a[m].y;
+      for (int e = 0; e < 2; ++e) {
+        const float w1 = e ? wf.y : wf.x, x1 = e ? cx.y : cx.x, y1 = e ? cy.y : cy.x, z1 = e ? cz.y : cz.x;
+        const float xw = e ? cxw.y : cxw.x, yw = e ? cyw.y : cyw.x, ee = e ? e2.y : e2.x;
+        acc[0] += w1;
+        acc[1] += xw;
+        acc[2] += yw;
+        acc[3] = fmaf(z1, w1, acc[3]);
+        acc[4] += ee;
+        acc[5] = fmaf(x1, xw, acc[5]);
+        acc[6] = fmaf(y1, xw, acc[6]);
+        acc[7] = fmaf(z1, xw, acc[7]);
+        acc[8] = fmaf(y1, yw, acc[8]);
+        acc[9] = fmaf(z1, yw, acc[9]);
+        acc[10] = fmaf(e ? czz.y : czz.x, w1, acc[10]);
+        acc[11] = fmaf(x1, ee, acc[11]);
+        acc[12] = fmaf(y1, ee, acc[12]);
+        acc[13] = fmaf(z1, ee, acc[13]);
+      }
+    }
 #pragma unroll
     for (int j = 0; j < KPT / 2; ++j) *reinterpret_cast<float2 *>(M.fn_cell + kp(M, j)) = out[j];
   }
