@@ -151,6 +151,7 @@ struct SweepTables {
   void *args = nullptr, *tmaps = nullptr, *items = nullptr; // [ncase][2], [ncase][2], [nitems]
   int *next = nullptr; // work counter
   int nitems = 0, grid = 0, dim = 2;
+  int ksel = 0;        // 2D: velocities per lane of every item (4 or 2), 0 for a mix
 };
 bool tma_batch_member_ok(const ibdvm_ctx *ctx);
 int tma_batch_kpt_max(const ibdvm_ctx *ctx);

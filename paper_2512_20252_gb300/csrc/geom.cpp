@@ -319,8 +319,9 @@ bool build_grid(const ibdvm_grid_desc &g, const ibdvm_vgrid_desc &v, const ibdvm
   }
   G.rule = v.rule;
   G.nv = static_cast<int>(nv);
-  // padding of the velocity count: 64, or 128 for the 3D FP32 sweep's chunks
-  const int pad = (g.dim == 3 && gas.precision == IBDVM_MIXED) ? 2 * kVelPad : kVelPad;
+  // padding of the velocity count: 64, or 128 for the FP32 sweeps' chunks of
+  // 128 velocities (the padded velocities carry zero weight and no flux)
+  const int pad = (gas.precision == IBDVM_MIXED) ? 2 * kVelPad : kVelPad;
   G.nvp = (G.nv + pad - 1) / pad * pad;
   // per-axis nodes, weights and dual boxes (Eq. quadrature)
   std::vector<double> ax[3], al[3], ah[3];

@@ -524,7 +524,9 @@ struct WorkItem {
 
 // The batched sweep: a persistent grid whose blocks take work items in order
 // from a shared counter (items sorted by decreasing size).  Member c at step
-// parity par uses args[2 c + par] and tmaps[2 c + par].
+// parity par uses args[2 c + par] and tmaps[2 c + par].  KSEL = 4 or 2 when
+// every item takes that many velocities per lane, 0 for a mix.
+template <int KSEL>
 __global__ void __launch_bounds__(NTHREADS, 2)
     sweep2d_tma_batch_kernel(const TmaArgs *__restrict__ args, const CUtensorMap *__restrict__ tmaps,
                              const WorkItem *__restrict__ items, int nitems, int *__restrict__ next, int par) {
@@ -541,8 +543,14 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     if (threadIdx.x == 0) sA = args[2 * it.cas + par];
     __syncthreads();
     const CUtensorMap *tm = tmaps + 2 * it.cas + par;
-    const bool ok = (it.kpt == 4) ? march2d<4>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit)
-                                  : march2d<2>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
+    bool ok;
+    if constexpr (KSEL == 4)
+      ok = march2d<4>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
+    else if constexpr (KSEL == 2)
+      ok = march2d<2>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
+    else
+      ok = (it.kpt == 4) ? march2d<4>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit)
+                         : march2d<2>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
     if (!ok) break; // uniform: the abort vote is block-wide
     reinit = true;
     __syncthreads(); // the item's shared memory and arguments are released
@@ -728,16 +736,23 @@ cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::ve
   if ((e = cudaMalloc(&nx, sizeof(int))) != cudaSuccess) return e;
   t.next = static_cast<int *>(nx);
   t.nitems = static_cast<int>(items.size());
+  {
+    bool all4 = true, all2 = true;
+    for (int k : kpt) {
+      all4 = all4 && k == 4;
+      all2 = all2 && k == 2;
+    }
+    t.ksel = all4 ? 4 : (all2 ? 2 : 0);
+  }
   const int smem = (int)std::max(Cfg<4>::SMEM, Cfg<2>::SMEM);
-  if ((e = cudaFuncSetAttribute(sweep2d_tma_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
-      cudaSuccess)
-    return e;
+  const void *fn = (t.ksel == 4) ? (const void *)sweep2d_tma_batch_kernel<4>
+                   : (t.ksel == 2) ? (const void *)sweep2d_tma_batch_kernel<2>
+                                   : (const void *)sweep2d_tma_batch_kernel<0>;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep2d_tma_batch_kernel, NTHREADS, smem)) !=
-      cudaSuccess)
-    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NTHREADS, smem)) != cudaSuccess) return e;
   t.grid = std::max(1, std::min(t.nitems, nsm * std::max(per_sm, 1)));
   return cudaStreamSynchronize(s); // the host tables go out of scope
 }
@@ -748,9 +763,15 @@ cudaError_t tma_batch_launch(const SweepTables &t, int par, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(t.next, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   const int smem = (int)std::max(Cfg<4>::SMEM, Cfg<2>::SMEM);
-  sweep2d_tma_batch_kernel<<<t.grid, NTHREADS, smem, s>>>(
-      static_cast<const TmaArgs *>(t.args), static_cast<const CUtensorMap *>(t.tmaps),
-      static_cast<const WorkItem *>(t.items), t.nitems, t.next, par);
+  const TmaArgs *a = static_cast<const TmaArgs *>(t.args);
+  const CUtensorMap *m = static_cast<const CUtensorMap *>(t.tmaps);
+  const WorkItem *it = static_cast<const WorkItem *>(t.items);
+  if (t.ksel == 4)
+    sweep2d_tma_batch_kernel<4><<<t.grid, NTHREADS, smem, s>>>(a, m, it, t.nitems, t.next, par);
+  else if (t.ksel == 2)
+    sweep2d_tma_batch_kernel<2><<<t.grid, NTHREADS, smem, s>>>(a, m, it, t.nitems, t.next, par);
+  else
+    sweep2d_tma_batch_kernel<0><<<t.grid, NTHREADS, smem, s>>>(a, m, it, t.nitems, t.next, par);
   return cudaGetLastError();
 }
 
