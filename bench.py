@@ -167,6 +167,24 @@ def profiled_traffic(kernel: str, source: str, pairs: int):
     return None
 
 
+def max_over_ranks(x: float, pg, device: str = "cuda") -> float:
+    """The largest x over all ranks (every rank gets it); x itself without a
+    process group."""
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(pairs_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the pairs every rank advanced (replicas of the
+    same case) divided by the slowest rank's time."""
+    return pairs_per_rank * steps * world / seconds
+
+
 def dist_setup(nprocs: int):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -328,11 +346,8 @@ def bench_batch(args, world, rank, local, pg):
     clocks = sampler.stop()
     kt = batch.kernel_times()
     batch.set_profiling(False)
-    if pg:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = pairs * args.steps * world / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(elapsed_ms, pg)
+    value = job_value(pairs, args.steps, world, elapsed_ms / 1e3)
     sweep_ms, sweep_n = kt["sweep"]
     peak, peak_kind = peaks()
     achieved = alg_bytes / (sweep_ms / sweep_n / 1e3) / 1e9 if sweep_n else None
@@ -362,7 +377,8 @@ def bench_batch(args, world, rank, local, pg):
             d2h += W.nbytes + q.nbytes + 8
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value = pairs * e2e_steps * world / e2e_s
+    e2e_s = max_over_ranks(e2e_s, pg)
+    e2e_value = job_value(pairs, e2e_steps, world, e2e_s)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -546,12 +562,8 @@ def main():
     clocks = sampler.stop()
     kt = solver.kernel_times()
     solver.set_profiling(False)
-    if pg:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    total_pairs = pairs * args.steps * world
-    value = total_pairs / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(elapsed_ms, pg)
+    value = job_value(pairs, args.steps, world, elapsed_ms / 1e3)
     sweep_ms, sweep_n = kt["sweep"]
     kname, ksrc = SWEEP_KERNELS.get(int(info.sweep_variant), SWEEP_KERNELS[0])
     alg_bytes = pairs * ncomp * esize * 2  # read f^n, write f^{n+1}
@@ -577,12 +589,9 @@ def main():
         W, q, _ = solver.moments()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, pg)
     d2h = W.nbytes + q.nbytes + 8
-    e2e_value = pairs * e2e_steps * world / e2e_s
+    e2e_value = job_value(pairs, e2e_steps, world, e2e_s)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -1,0 +1,62 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks on 127.0.0.1 agree on
+the slowest rank's time, and the whole-job value counts every rank's pairs
+(replicas only: the ranks exchange nothing but the timing)."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w, r, local = bench.dist_setup(world)
+    ms = bench.max_over_ranks(10.0 + 5.0 * rank, dist, "cpu")
+    value = bench.job_value(1000, 4, w, ms / 1e3)
+    q.put((r, w, local, ms, value))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time_and_sum_the_work():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[0] for o in out] == [0, 1] and all(o[1] == 2 for o in out)
+    assert [o[2] for o in out] == [0, 1]
+    for _, _, _, ms, value in out:
+        assert ms == 15.0                                  # max over ranks
+        assert value == pytest.approx(1000 * 4 * 2 / 0.015)  # both replicas' pairs / slowest time
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.max_over_ranks(3.5, None) == 3.5
+    assert bench.job_value(10, 2, 1, 0.5) == 40.0
