@@ -627,9 +627,11 @@ cudaError_t tma_sweep_launch(ibdvm_ctx *ctx) {
   const int kpt = tma_sweep_kpt(ctx);
   const int nstrip = (A.nx + TX - 1) / TX;
   const int nchunk = ctx->nvp / (32 * kpt);
-  // rows per block: enough blocks for several waves of two blocks per SM
-  int nrb = 1;
-  while ((long long)nstrip * nchunk * nrb < 8LL * 152 && A.ny / (nrb * 2) >= 32) nrb *= 2;
+  // rows per block: about 64 (many short marches leave a short tail: on
+  // 512^2 x 48^2, 64 rows per block beat 128, 256 and 32), and enough blocks
+  // for several waves of two blocks per SM
+  int nrb = (A.ny + 63) / 64;
+  while ((long long)nstrip * nchunk * nrb < 8LL * 152 && A.ny / (nrb * 2) >= 16) nrb *= 2;
   A.rows = (A.ny + nrb - 1) / nrb;
   dim3 grid(nstrip, nchunk, (A.ny + A.rows - 1) / A.rows);
   const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(ctx->tmap[ctx->cur]);
