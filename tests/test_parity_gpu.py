@@ -388,3 +388,51 @@ def test_tma3_sweep_against_oracle_and_plain_sweep(shape):
         if np.abs(Wo[fl, i]).max() > 1e-9:
             assert rel_err(Wg[fl, i], Wo[fl, i]) < 1e-5, i
     assert rg == pytest.approx(ro, rel=1e-3)
+
+
+# ---------------------------------------------------------------------------
+# full step counts of the FP64 configurations, against the oracle's stored
+# state (tests/golden/make_oracle_goldens.py runs only the oracle)
+# ---------------------------------------------------------------------------
+
+def _golden(name):
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    out = {"cells": [], "W": []}
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        key, *vals = line.split()
+        if key in ("residual", "Q", "CD", "CL"):
+            out[key] = float(vals[0])
+        elif key == "F":
+            out["F"] = np.array([float(v) for v in vals])
+        else:
+            out["cells"].append(int(key))
+            out["W"].append([float(v) for v in vals])
+    out["cells"] = np.array(out["cells"])
+    out["W"] = np.array(out["W"])
+    return out
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,make,steps", [("cylinder48_fp64_200steps.txt", wl.cylinder_48, 200),
+                                             ("sphere24_fp64_50steps.txt", wl.sphere_24, 50)])
+def test_full_configuration_fp64_against_the_oracle(name, make, steps):
+    gold = _golden(name)
+    g = ibdvm.Solver(make())
+    res = g.step(steps)
+    W, _, _ = g.moments()
+    Wg = W[gold["cells"]]
+    Wo = gold["W"]
+    for i in range(Wo.shape[1]):
+        if np.abs(Wo[:, i]).max() > 1e-9:
+            assert rel_err(Wg[:, i], Wo[:, i]) < TOL, i
+    assert res == pytest.approx(gold["residual"], rel=1e-8)
+    F, Q, CD, CL = g.forces()
+    scale = np.abs(gold["F"]).max()
+    assert np.abs(F - gold["F"]).max() < 10 * TOL * scale
+    assert abs(Q - gold["Q"]) < 10 * TOL * max(abs(gold["Q"]), 1e-6)
+    assert abs(CD - gold["CD"]) < 10 * TOL * abs(gold["CD"])
+    g.close()
