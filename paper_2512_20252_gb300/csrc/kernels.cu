@@ -36,6 +36,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kThreadsPerCell = 64; // threads over velocities for one cell
 constexpr int kCellsPerBlock = 4;   // cells of one sweep block
 constexpr int kBlock = kThreadsPerCell * kCellsPerBlock;
+constexpr int kGhostThreads = 512; // threads over the velocities of one link
 
 template <int D> struct Dims {
   static constexpr int NC = (D == 2) ? 2 : 1;   // components: (h, b) or f
@@ -565,7 +566,7 @@ __device__ __forceinline__ T preghost_slope(const GhostArgs<T> &G, int code_m, i
 template <typename T, int D>
 __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int l) {
   constexpr int NC = Dims<D>::NC;
-  __shared__ double sh[16];
+  __shared__ double sh[kGhostThreads / 32 + 1];
   const int *li = G.l_int + 8 * l;
   const double *ld = G.l_dbl + 8 * l;
   const int donor = li[1], aux = li[2], s0 = li[6], s1 = li[7];
@@ -642,8 +643,8 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
     Dsum += ws * xn * Gw;
   }
   __syncthreads(); // scratch writes of this block are visible to the block
-  const double N = block_sum<256>(Nsum, sh);
-  const double Dd = block_sum<256>(Dsum, sh);
+  const double N = block_sum<kGhostThreads>(Nsum, sh);
+  const double Dd = block_sum<kGhostThreads>(Dsum, sh);
   double Ssum = 0.0;
   if (alpha < 1.0) {
     // specular part: f^i at the mirrored velocity by multilinear interpolation
@@ -680,7 +681,7 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
       Ssum += (G.wD[k] - wgl[k]) * xn * v;
     }
   }
-  const double S = (alpha < 1.0) ? block_sum<256>(Ssum, sh) : 0.0;
+  const double S = (alpha < 1.0) ? block_sum<kGhostThreads>(Ssum, sh) : 0.0;
   const double rho_w = (alpha > 0.0) ? -(N + (1.0 - alpha) * S) / (alpha * Dd) : 0.0;
   if (threadIdx.x == 0) G.rhow[l] = rho_w;
   // wall distribution (Eqs. general bc, Maxwell BC, fwc) and ghost value (Eq. extrapolation 2)
@@ -736,7 +737,7 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256) ghost_band_kernel(GhostArgs<T> G) {
+__global__ void __launch_bounds__(kGhostThreads) ghost_band_kernel(GhostArgs<T> G) {
   ghost_band_body<T, D>(G, blockIdx.x);
 }
 
@@ -845,7 +846,7 @@ __device__ __forceinline__ int group_case(const int *__restrict__ start, int nca
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256) ghost_band_grouped(const GhostArgs<T> *__restrict__ tab,
+__global__ void __launch_bounds__(kGhostThreads) ghost_band_grouped(const GhostArgs<T> *__restrict__ tab,
                                                           const int *__restrict__ start, int ncase, int par) {
   __shared__ GhostArgs<T> sG;
   const int c = group_case(start, ncase, blockIdx.x);
@@ -1042,7 +1043,7 @@ template <typename T> GhostArgs<T> ghost_args(const ibdvm_ctx *ctx, int cur, dou
 
 template <typename T, int D> cudaError_t ghost_t(ibdvm_ctx *ctx, double *dbg) {
   if (ctx->nlink == 0) return cudaSuccess;
-  ghost_band_kernel<T, D><<<ctx->nlink, 256, 0, ctx->stream>>>(ghost_args<T>(ctx, ctx->cur, dbg));
+  ghost_band_kernel<T, D><<<ctx->nlink, kGhostThreads, 0, ctx->stream>>>(ghost_args<T>(ctx, ctx->cur, dbg));
   return cudaGetLastError();
 }
 
@@ -1255,9 +1256,9 @@ cudaError_t group_ghost(const GroupTables &t, int par, cudaStream_t s) {
   if (t.link_blocks == 0) return cudaSuccess;
   const auto *tab = static_cast<const GhostArgs<float> *>(t.ghost);
   if (t.dim == 2)
-    ghost_band_grouped<float, 2><<<t.link_blocks, 256, 0, s>>>(tab, t.link_start, t.ncase, par);
+    ghost_band_grouped<float, 2><<<t.link_blocks, kGhostThreads, 0, s>>>(tab, t.link_start, t.ncase, par);
   else
-    ghost_band_grouped<float, 3><<<t.link_blocks, 256, 0, s>>>(tab, t.link_start, t.ncase, par);
+    ghost_band_grouped<float, 3><<<t.link_blocks, kGhostThreads, 0, s>>>(tab, t.link_start, t.ncase, par);
   return cudaGetLastError();
 }
 
