@@ -127,6 +127,8 @@ template <int KPT> struct March {
   // the halo column face this thread owns (threads below KC): chunk velocity,
   // column, its slot in a staged row, its face slot
   int h_kk, h_col, h_scol, h_out;
+  bool h_in, h_fast;         // the column lies in the domain; and away from its x edges
+  float2 h_s2;               // sign of that velocity's xi_x, packed
   // running pointers of row y, advanced by one row per step
   const uint8_t *cm_row;     // flags of row y
   const float *mac_next;     // this lane's parameter of the cell at row y + 1
@@ -228,13 +230,12 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
   }
   // (1) own column of row y + 2 (the y stencil)
   if (y + 2 < A.ny && !mbar_wait(&M.full[st2], pb2)) M.abort_local = true;
-  if (y + 2 < A.ny && M.col_in) {
-    const float *src = M.stage + st2 * C::STAGE_FLOATS + (M.warp + 2) * C::KC2;
+  {
+    // the own column of row y + 2, or the freestream past the domain edge
+    const float *src = (y + 2 < A.ny && M.col_in) ? M.stage + st2 * C::STAGE_FLOATS + (M.warp + 2) * C::KC2
+                                                  : M.sfinf;
 #pragma unroll
     for (int q = 0; q < KPT; ++q) Rc[q] = sm2<KPT>(src, klo(M, q));
-  } else {
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) Rc[q] = sm2<KPT>(M.sfinf, klo(M, q));
   }
   const float *srow = M.stage + st * C::STAGE_FLOATS; // row y, [COLS][KC][2]
   float *ph = M.phix + par * C::PHI_FLOATS;            // [TX + 2][KC][2]
@@ -257,8 +258,16 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
   // for xi_x >= 0, x0 + TX otherwise; one velocity per thread
   static_assert(Cfg<KPT>::KC <= NTHREADS, "one halo face per thread at most");
   if (threadIdx.x < C::KC) {
-    const uint8_t hm = (M.h_col >= 0 && M.h_col < A.nx) ? M.cm_row[M.h_col] : 0;
-    const float2 o = phi_x_one(M, srow, M.h_col, M.h_scol, y, hm, M.h_kk, M.sxi[M.h_kk]);
+    const uint8_t hm = M.h_in ? M.cm_row[M.h_col] : 0;
+    float2 o;
+    if (M.h_fast && !(hm & (kNotFluid | kXm | kXp))) {
+      // interior halo column, fluid, no ghost along x: f and its neighbours
+      // from the staged row, the sign of the velocity decides the side
+      const float *pc = srow + M.h_scol * C::KC2;
+      o = face2(sm2<KPT>(pc, M.h_kk), sm2<KPT>(pc - C::KC2, M.h_kk), sm2<KPT>(pc + C::KC2, M.h_kk), M.h_s2);
+    } else {
+      o = phi_x_one(M, srow, M.h_col, M.h_scol, y, hm, M.h_kk, M.sxi[M.h_kk]);
+    }
     *reinterpret_cast<float2 *>(ph + M.h_out) = o;
   }
   // (3) downwind y face of row y + 1
@@ -418,6 +427,9 @@ __device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf
     M.h_col = left ? M.x0 - 1 : M.x0 + TX;
     M.h_scol = left ? 1 : TX + 2;
     M.h_out = (left ? 0 : TX + 1) * C::KC2 + 2 * M.h_kk;
+    M.h_in = M.h_col >= 0 && M.h_col < A.nx;
+    M.h_fast = M.h_col >= 1 && M.h_col + 1 < A.nx;
+    M.h_s2 = dup(left ? 1.f : -1.f);
   }
   M.st = 0;
   M.pb = 0;
