@@ -167,6 +167,28 @@ def profiled_traffic(kernel: str, source: str, pairs: int):
     return None
 
 
+# GB300's FP64 rate (nominal: 1.25 TFLOP/s dense, FMA = 2 flops); no measured
+# FP64 peak is recorded, so the FP64 path is reported against this figure
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def profiled_fp64_flops_per_pair(dim: int):
+    """FP64 operations per (cell, velocity) pair of the FP64 sweep (an FMA
+    counted as two), from the committed ncu count of its executed FP64
+    instructions (profiles/sweep_kernel_fp64_*.md), or None."""
+    import glob
+
+    for path in glob.glob(os.path.join(ROOT, "profiles", "sweep_kernel_fp64_*.md")):
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.split(":")[0] in ("fp64_flops_per_pair", "dim"):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("dim") == str(dim) and "fp64_flops_per_pair" in fields:
+            return float(fields["fp64_flops_per_pair"])
+    return None
+
+
 def max_over_ranks(x: float, pg, device: str = "cuda") -> float:
     """The largest x over all ranks (every rank gets it); x itself without a
     process group."""
@@ -600,6 +622,19 @@ def main():
         cpu = {"value": v, "unit": "cell-velocity updates/s", "cores": 1, "kind": "oracle",
                "sample": f"{n} oracle steps ({el:.1f} s) of the workload's gas, body and velocity grid "
                          f"on {sample['n'][0]} cells per axis ({oc.nfluid} fluid cells x {oc.nvel} velocities)"}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": profiled_traffic(kname, ksrc, pairs),
+                "kernel": kname, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms / max(sweep_n, 1)}
+    fpp = profiled_fp64_flops_per_pair(int(info.dim)) if args.precision == "fp64" else None
+    if fpp and sweep_n:
+        # the FP64 path is bound by GB300's FP64 arithmetic rate, not by HBM
+        tf = fpp * pairs / (sweep_ms / sweep_n / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tf / FP64_NOMINAL_TFLOPS, "traffic": profiled_traffic(kname, ksrc, pairs),
+                    "kernel": kname, "peak_kind": "nominal FP64", "fp64_flops_per_pair": fpp,
+                    "hbm_achieved_gbs": achieved, "avg_launch_ms": sweep_ms / max(sweep_n, 1)}
     if rank == 0:
         line = {
             "metric": "DVM cell x velocity updates/s",
@@ -619,11 +654,7 @@ def main():
                        "cells": int(info.ncell), "fluid_cells": int(info.nfluid), "velocities": int(info.nvel),
                        "l2": f"inputs larger than L2 (f^n is {alg_bytes / 2 / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None,
-                         "traffic": profiled_traffic(kname, ksrc, pairs),
-                         "kernel": kname, "peak_kind": peak_kind,
-                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms / max(sweep_n, 1)},
+            "roofline": roofline,
             "kernel_ms": {k: v[0] for k, v in kt.items()},
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": nbytes,
