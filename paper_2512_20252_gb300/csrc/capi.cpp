@@ -132,6 +132,15 @@ void free_all(ibdvm_ctx *ctx) {
   cfree_t(ctx->partf);
   cfree_t(ctx->d_forces);
   cfree_t(ctx->d_step_forces);
+  for (cudaEvent_t &e : ctx->copy_ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
+  if (ctx->copy_stream) {
+    cudaStreamDestroy(ctx->copy_stream);
+    ctx->copy_stream = nullptr;
+  }
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   ctx->ev_pool.clear();
   ctx->ev_marks.clear();
@@ -339,8 +348,39 @@ void upload_body(ibdvm_ctx *ctx) {
 // bulk velocity just found), so the macroscopic state matches f exactly
 void refresh_moments(ibdvm_ctx *ctx) {
   check(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), ctx->stream), "clear flags");
-  check(ctx, launch_moments(ctx, false, false), "moments kernel");
-  check(ctx, launch_moments(ctx, true, false), "moments kernel");
+  check(ctx, launch_refresh_range(ctx, 0, ctx->ncell), "moments kernel");
+}
+
+// f^n from host memory in kUploadParts cell ranges on a copy stream; the
+// moments of each range are taken on the context's stream as soon as its
+// bytes have arrived (a cell's moments depend on its own row only), so the
+// refresh hides behind the copy. Small states take one copy.
+void upload_refresh(ibdvm_ctx *ctx, const void *host, size_t bytes) {
+  const long long nc = ctx->ncell;
+  const size_t row = static_cast<size_t>(ctx->nvp) * ctx->ncomp * ctx->esize;
+  char *dst = static_cast<char *>(ctx->f[ctx->cur]);
+  const char *src = static_cast<const char *>(host);
+  check(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), ctx->stream), "clear flags");
+  if (bytes < (size_t(64) << 20) || nc < kUploadParts) {
+    check(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream), "copy f");
+    check(ctx, launch_refresh_range(ctx, 0, nc), "moments kernel");
+    return;
+  }
+  if (!ctx->copy_stream) {
+    check(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream");
+    for (cudaEvent_t &e : ctx->copy_ev) check(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "copy event");
+  }
+  // the copy starts after the work already on the context's stream
+  check(ctx, cudaEventRecord(ctx->copy_ev[kUploadParts], ctx->stream), "record");
+  check(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ev[kUploadParts], 0), "wait");
+  for (int i = 0; i < kUploadParts; ++i) {
+    const long long c0 = nc * i / kUploadParts, c1 = nc * (i + 1) / kUploadParts;
+    check(ctx, cudaMemcpyAsync(dst + c0 * row, src + c0 * row, (c1 - c0) * row, cudaMemcpyHostToDevice,
+                               ctx->copy_stream), "copy f");
+    check(ctx, cudaEventRecord(ctx->copy_ev[i], ctx->copy_stream), "record");
+    check(ctx, cudaStreamWaitEvent(ctx->stream, ctx->copy_ev[i], 0), "wait");
+    check(ctx, launch_refresh_range(ctx, c0, c1), "moments kernel");
+  }
 }
 
 int read_flags(ibdvm_ctx *ctx) {
@@ -715,15 +755,17 @@ ibdvm_status ibdvm_moments(ibdvm_ctx *ctx, double *W, double *q, unsigned char *
   const int D = ctx->dim, NW = D + 2;
   const long long nc = ctx->ncell;
   if (W || q) {
-    std::vector<double> h(static_cast<size_t>(NW + D) * nc);
-    check(ctx, cudaMemcpyAsync(h.data(), ctx->W[ctx->wcur], h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream), "read W");
+    // rows per cell are formed on the device, in the moment partial-sum
+    // buffer (free between steps, at least (D + 2 + D) ncell doubles)
+    double *Wo = ctx->part, *qo = ctx->part + static_cast<size_t>(NW) * nc;
+    check(ctx, launch_interleave(ctx, W ? Wo : nullptr, q ? qo : nullptr), "interleave W");
+    if (W)
+      check(ctx, cudaMemcpyAsync(W, Wo, static_cast<size_t>(NW) * nc * 8, cudaMemcpyDeviceToHost, ctx->stream),
+            "read W");
+    if (q)
+      check(ctx, cudaMemcpyAsync(q, qo, static_cast<size_t>(D) * nc * 8, cudaMemcpyDeviceToHost, ctx->stream),
+            "read q");
     sync(ctx, "read W");
-    for (long long c = 0; c < nc; ++c) {
-      if (W)
-        for (int i = 0; i < NW; ++i) W[c * NW + i] = h[i * nc + c];
-      if (q)
-        for (int a = 0; a < D; ++a) q[c * D + a] = h[(NW + a) * nc + c];
-    }
   }
   if (celltype) std::copy(ctx->geom.type.begin(), ctx->geom.type.end(), celltype);
   return IBDVM_OK;
@@ -819,8 +861,7 @@ ibdvm_status ibdvm_set_f_native(ibdvm_ctx *ctx, const void *host, size_t bytes) 
     ctx->err = "set_f_native: bytes must be ncell * nvel_padded * ncomp * element size";
     return IBDVM_E_INVAL;
   }
-  check(ctx, cudaMemcpyAsync(ctx->f[ctx->cur], host, bytes, cudaMemcpyHostToDevice, ctx->stream), "copy f");
-  refresh_moments(ctx);
+  upload_refresh(ctx, host, bytes);
   return status_of_flags(ctx, read_flags(ctx));
   IBDVM_END
 }

@@ -29,6 +29,9 @@ enum MacSlot {
 // kernel classes of the timing counters
 enum KernelClass { kKGhost = 0, kKSweep = 1, kKMoments = 2, kKForces = 3, kKOther = 4 };
 
+// cell ranges of a pipelined host upload of the state (ibdvm_set_f_native)
+constexpr int kUploadParts = 8;
+
 // flags written by the moment kernel
 enum : int { kFlagNonFinite = 1, kFlagUnstable = 2, kFlagTimeout = 4 };
 
@@ -45,7 +48,7 @@ struct ibdvm_ctx {
   // state and per-cell data
   void *f[2] = {nullptr, nullptr};
   int cur = 0;
-  void *mac = nullptr;       // [kMac][ncell]
+  void *mac = nullptr;       // [ncell][kMac]
   double *W[2] = {nullptr, nullptr}; // [dim+2][ncell]
   int wcur = 0;
   double *part = nullptr;    // moment partial sums [nchunk][NM][ncell]
@@ -99,6 +102,9 @@ struct ibdvm_ctx {
   // (a batch rebuilds its tables when it changes)
   ibdvm_batch *batch = nullptr;
   unsigned body_gen = 0;
+  // host uploads of the state in cell ranges (a copy stream, one event per range)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[ibdvm::kUploadParts + 1] = {};
   // bookkeeping
   long long steps = 0;
   size_t dev_bytes = 0;
@@ -110,7 +116,11 @@ namespace ibdvm {
 // Kernel launchers (kernels.cu).  All enqueue on ctx->stream and return the
 // launch status.
 cudaError_t launch_init_state(ibdvm_ctx *ctx);
-cudaError_t launch_moments(ibdvm_ctx *ctx, bool shift, bool residual);
+// moments of f^n, W^n and the Shakhov parameters of the cells [c0, c1),
+// without transport (two passes: about zero, then about the bulk velocity)
+cudaError_t launch_refresh_range(ibdvm_ctx *ctx, long long c0, long long c1);
+// W^n and q^n as rows per cell ([ncell][D + 2] and [ncell][D], device)
+cudaError_t launch_interleave(ibdvm_ctx *ctx, double *Wo, double *qo);
 cudaError_t launch_ghost_band(ibdvm_ctx *ctx, double *dbg_fstarw);
 cudaError_t launch_sweep(ibdvm_ctx *ctx);
 cudaError_t launch_forces(ibdvm_ctx *ctx, double *dst);

@@ -311,6 +311,135 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
 }
 
 // ---------------------------------------------------------------------------
+// moments of a stored state, without transport (after a state is loaded or a
+// body is set): one warp per cell reads the cell's row of velocities with
+// 16-byte loads, several in flight per lane; plain sums over the velocities of
+// one group of loads, compensated (FP32) sums over the groups, and a
+// compensated butterfly over the lanes. The moment sums are those of the
+// sweep, written as one velocity chunk.
+// ---------------------------------------------------------------------------
+
+template <typename T> struct MomArgs {
+  const T *__restrict__ f;   // [ncell][nvp][NC]
+  const T *__restrict__ mac; // [ncell][kMac]
+  const T *__restrict__ xi;  // [3][nvp]
+  const T *__restrict__ w;   // [nvp]
+  const uint8_t *__restrict__ ctype;
+  double *__restrict__ part; // [NM][ncell]
+  long long ncell;
+  long long c0, c1; // the cells [c0, c1) of this launch
+  int nv, nvp;
+  int shift; // 1: moments about the stored bulk velocity U^n; 0: about zero
+};
+
+constexpr int kMomWarps = 8;  // cells of one moments block
+constexpr int kMomUnroll = 4; // 16-byte loads in flight per lane
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using type = float4;
+  static __device__ __forceinline__ void unpack(const float4 &q, float *e) {
+    e[0] = q.x;
+    e[1] = q.y;
+    e[2] = q.z;
+    e[3] = q.w;
+  }
+};
+template <> struct Vec16<double> {
+  using type = double2;
+  static __device__ __forceinline__ void unpack(const double2 &q, double *e) {
+    e[0] = q.x;
+    e[1] = q.y;
+  }
+};
+
+template <typename T, int D>
+__global__ void __launch_bounds__(32 * kMomWarps, (D == 2 && sizeof(T) == 4) ? 4 : 2) moments_kernel(MomArgs<T> A) {
+  constexpr int NC = Dims<D>::NC;
+  constexpr int NM = Dims<D>::NM;
+  constexpr int V = 16 / (int)sizeof(T); // elements of one load
+  constexpr int VPL = V / NC;            // velocities of one load
+  using Q = typename Vec16<T>::type;
+  const int lane = threadIdx.x & 31;
+  const long long c = A.c0 + (long long)blockIdx.x * kMomWarps + (threadIdx.x >> 5);
+  if (c >= A.c1) return; // the whole warp
+  double out = 0.0;
+  if (A.ctype[c] == IBDVM_CELL_FLUID) {
+    T U[3] = {T(0), T(0), T(0)};
+    if (A.shift)
+#pragma unroll
+      for (int a = 0; a < D; ++a) U[a] = A.mac[c * kMac + kU0 + a];
+    const Q *row = reinterpret_cast<const Q *>(A.f + (size_t)c * A.nvp * NC);
+    const int nvec = A.nvp * NC / V; // loads in the row (the padding makes it whole)
+    Acc<T> acc[NM];
+    for (int v0 = 0; v0 < nvec; v0 += 32 * kMomUnroll) {
+      Q buf[kMomUnroll];
+#pragma unroll
+      for (int u = 0; u < kMomUnroll; ++u) {
+        const int v = v0 + u * 32 + lane;
+        if (v < nvec) buf[u] = row[v];
+      }
+      T s[NM];
+#pragma unroll
+      for (int m = 0; m < NM; ++m) s[m] = T(0);
+#pragma unroll
+      for (int u = 0; u < kMomUnroll; ++u) {
+        const int v = v0 + u * 32 + lane;
+        if (v >= nvec) continue;
+        T e[V];
+        Vec16<T>::unpack(buf[u], e);
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) {
+          const int k = v * VPL + j;
+          const bool live = k < A.nv; // padded velocities hold no mass
+          const T wk = A.w[k];
+          const T wh = live ? wk * e[j * NC] : T(0);
+          const T wb = (D == 2 && live) ? wk * e[j * NC + NC - 1] : T(0);
+          T cv[3] = {T(0), T(0), T(0)};
+          T c2 = T(0);
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            cv[a] = A.xi[a * A.nvp + k] - U[a];
+            c2 += cv[a] * cv[a];
+          }
+          const T e2 = c2 * wh + wb;
+          s[0] += wh;
+#pragma unroll
+          for (int a = 0; a < D; ++a) s[1 + a] += cv[a] * wh;
+          s[1 + D] += e2;
+          int m = 2 + D;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) s[m++] += cv[a] * cv[b] * wh;
+#pragma unroll
+          for (int a = 0; a < D; ++a) s[m + a] += cv[a] * e2;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < NM; ++m) acc[m].add(s[m]);
+    }
+    // butterfly over the lanes; every lane ends with the cell's sums
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      T h = acc[m].hi(), l = acc[m].lo();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+        Acc<T> t;
+        t.s = h;
+        if constexpr (sizeof(T) == 4) t.c = l;
+        t.merge(oh, ol);
+        h = t.hi();
+        l = t.lo();
+      }
+      if (lane == m) out = (double)h + (double)l;
+    }
+  }
+  if (lane < NM) A.part[(size_t)lane * A.ncell + c] = out;
+}
+
+// ---------------------------------------------------------------------------
 // moments -> macroscopic state, Shakhov parameters, residual partial sums
 // ---------------------------------------------------------------------------
 
@@ -328,6 +457,7 @@ template <typename T, typename P = double> struct FinalArgs {
   double mu0, omega, Pr, dt;
   int nblk;         // blocks of the finalize launch (residual partial sums)
   double *res_out;  // residual of the step
+  long long c0, c1; // the cells [c0, c1) of this launch
 };
 
 template <typename T, int D, typename P>
@@ -335,11 +465,11 @@ __device__ __forceinline__ void finalize_body(const FinalArgs<T, P> &A, const in
   constexpr int NM = Dims<D>::NM;
   constexpr int NW = Dims<D>::NW;
   __shared__ double red[2 * NW][8];
-  const long long c = (long long)blk * blockDim.x + threadIdx.x;
+  const long long c = A.c0 + (long long)blk * blockDim.x + threadIdx.x;
   double rnum[NW], rden[NW];
 #pragma unroll
   for (int i = 0; i < NW; ++i) rnum[i] = rden[i] = 0.0;
-  if (c < A.ncell && A.ctype[c] == IBDVM_CELL_FLUID) {
+  if (c < A.c1 && A.ctype[c] == IBDVM_CELL_FLUID) {
     double M[NM];
     if constexpr (std::is_same<P, float>::value) {
       // FP32 partial sums of the velocity chunks: added in order by a
@@ -980,6 +1110,8 @@ FinalArgs<T, P> final_args(const ibdvm_ctx *ctx, int wcur, bool shift, bool resi
   A.dt = ctx->geom.dt;
   A.nblk = (int)((ctx->ncell + 255) / 256);
   A.res_out = ctx->d_res;
+  A.c0 = 0;
+  A.c1 = ctx->ncell;
   return A;
 }
 
@@ -1125,16 +1257,63 @@ cudaError_t launch_init_state(ibdvm_ctx *ctx) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_moments(ibdvm_ctx *ctx, bool shift, bool residual) {
+cudaError_t launch_refresh_range(ibdvm_ctx *ctx, long long c0, long long c1) {
+  if (c1 <= c0) return cudaSuccess;
   Timed t(ctx, kKMoments);
-  ctx->kernel_launches[kKMoments] += residual ? 3 : 2;
+  ctx->kernel_launches[kKMoments] += 4;
   return dispatch(ctx, [&](auto t, auto d) -> cudaError_t {
     using T = decltype(t);
     constexpr int D = decltype(d)::value;
-    cudaError_t e = sweep_t<T, D>(ctx, 0, shift ? 1 : 0);
-    if (e != cudaSuccess) return e;
-    return finalize_t<T, D>(ctx, shift, residual);
+    // first pass about zero (W into W[1 - wcur]), second about the bulk
+    // velocity that pass stored (W into W[wcur])
+    for (int pass = 0; pass < 2; ++pass) {
+      MomArgs<T> M{};
+      M.f = static_cast<const T *>(ctx->f[ctx->cur]);
+      M.mac = static_cast<const T *>(ctx->mac);
+      M.xi = static_cast<const T *>(ctx->xiT);
+      M.w = static_cast<const T *>(ctx->wT);
+      M.ctype = ctx->ctype;
+      M.part = ctx->part;
+      M.ncell = ctx->ncell;
+      M.c0 = c0;
+      M.c1 = c1;
+      M.nv = ctx->nv;
+      M.nvp = ctx->nvp;
+      M.shift = pass;
+      const unsigned grid = (unsigned)((c1 - c0 + kMomWarps - 1) / kMomWarps);
+      moments_kernel<T, D><<<grid, 32 * kMomWarps, 0, ctx->stream>>>(M);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      FinalArgs<T, double> A =
+          final_args<T, double>(ctx, pass == 0 ? ctx->wcur : 1 - ctx->wcur, pass == 1, false, ctx->part, 1);
+      A.c0 = c0;
+      A.c1 = c1;
+      A.nblk = (int)((c1 - c0 + 255) / 256);
+      finalize_kernel<T, D, double><<<A.nblk, 256, 0, ctx->stream>>>(A);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   });
+}
+
+// rows of W^n and q^n per cell, [ncell][D + 2] and [ncell][D], from the
+// per-quantity layout [D + 2 + D][ncell]
+__global__ void __launch_bounds__(256) interleave_kernel(const double *__restrict__ W, double *__restrict__ Wo,
+                                                         double *__restrict__ qo, long long nc, int NW, int D) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  if (Wo)
+    for (int i = 0; i < NW; ++i) Wo[c * NW + i] = W[i * nc + c];
+  if (qo)
+    for (int a = 0; a < D; ++a) qo[c * D + a] = W[(NW + a) * nc + c];
+}
+
+cudaError_t launch_interleave(ibdvm_ctx *ctx, double *Wo, double *qo) {
+  const long long nc = ctx->ncell;
+  interleave_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, ctx->stream>>>(ctx->W[ctx->wcur], Wo, qo, nc,
+                                                                          ctx->dim + 2, ctx->dim);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ghost_band(ibdvm_ctx *ctx, double *dbg) {

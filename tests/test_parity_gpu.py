@@ -213,6 +213,47 @@ def test_native_state_transfer():
     np.testing.assert_allclose(g.get_f(), buf.numpy()[:, : g.nvel].astype(np.float64), rtol=1e-7)
 
 
+@pytest.mark.parametrize("kind", ["2d_mixed", "3d_mixed", "2d_fp64"])
+def test_pipelined_state_upload(kind):
+    """A state of 64 MiB or more is uploaded in cell ranges, the moments of each
+    range taken as soon as its bytes arrive: W and q equal those of the
+    one-copy path (ibdvm_set_f, the same kernels over all cells at once) and
+    the oracle's moments of the same f."""
+    torch = pytest.importorskip("torch")
+    if kind == "2d_mixed":
+        case = wl.small_2d("circle", n=128, nv=32, precision="mixed")
+    elif kind == "2d_fp64":
+        case = wl.small_2d("ellipse", n=96, nv=32)
+    else:
+        case = wl._case(3, 36, 2.0, 8, 4.5, 0.1, 0.5, wl.sphere(0.6), precision="mixed")
+    g = ibdvm.Solver(case)
+    g.step(3)
+    esize = 4 if g.precision == "mixed" else 8
+    buf = torch.empty(g.native_shape(), dtype=torch.float32 if esize == 4 else torch.float64, pin_memory=True)
+    assert buf.numel() * esize >= 64 << 20
+    g.get_f_native(buf.data_ptr(), buf.numel() * esize)
+    rng = np.random.default_rng(7)
+    scale = torch.from_numpy(1.0 + 0.02 * rng.random(buf.shape[0])).to(buf.dtype)
+    buf.mul_(scale[:, None, None])
+    g.set_f_native(buf.data_ptr(), buf.numel() * esize)
+    W1, q1, t = g.moments()
+    f = buf.numpy()[:, : g.nvel].astype(np.float64)
+    g.set_f(f)
+    W2, q2, _ = g.moments()
+    np.testing.assert_array_equal(W1, W2)
+    np.testing.assert_array_equal(q1, q2)
+    o = oracle.OracleCase(case)
+    o.set_f(f)
+    Wo, qo = o.moments()
+    fl = t == ibdvm.FLUID
+    tol = TOL if esize == 8 else 1e-5
+    for i in range(g.dim + 2):
+        if np.abs(Wo[fl, i]).max() > 1e-9:
+            assert rel_err(W1[fl, i], Wo[fl, i]) < tol, i
+    qe = float(np.abs(q1[fl] - qo[fl]).max() / max(np.abs(qo[fl]).max(), 1e-3))
+    assert qe < 1e3 * tol, qe
+
+
 def test_runs_on_a_torch_stream():
     torch = pytest.importorskip("torch")
     case = wl.small_2d("circle", n=16, nv=8)
