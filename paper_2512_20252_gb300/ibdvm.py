@@ -399,12 +399,26 @@ class Solver:
         self._check(self.lib.ibdvm_step(self.h, int(nsteps), ctypes.byref(r)))
         return r.value
 
-    def moments(self):
-        W = np.zeros((self.ncell, self.dim + 2))
-        q = np.zeros((self.ncell, self.dim))
-        t = np.zeros(self.ncell, dtype=np.uint8)
-        self._check(self.lib.ibdvm_moments(self.h, _dp(W), _dp(q), t.ctypes.data_as(_U8)))
+    def moments(self, W=None, q=None, with_types=True):
+        """W^n [ncell][D + 2], q^n [ncell][D] and the cell types.  W and q may
+        be caller-owned C-contiguous float64 arrays of those shapes, filled in
+        place (in pinned host memory the read is one direct copy per array);
+        with_types=False skips the cell types (None is returned for them)."""
+        W = self._out(W, (self.ncell, self.dim + 2), "W")
+        q = self._out(q, (self.ncell, self.dim), "q")
+        t = np.zeros(self.ncell, dtype=np.uint8) if with_types else None
+        self._check(self.lib.ibdvm_moments(self.h, _dp(W), _dp(q),
+                                           t.ctypes.data_as(_U8) if with_types else None))
         return W, q, t
+
+    @staticmethod
+    def _out(a, shape, name):
+        if a is None:
+            return np.zeros(shape)
+        if a.dtype != np.float64 or tuple(a.shape) != shape or not a.flags["C_CONTIGUOUS"] \
+                or not a.flags["WRITEABLE"]:
+            raise ValueError(f"{name} must be a writeable C-contiguous float64 array of shape {shape}")
+        return a
 
     def forces(self):
         F = np.zeros(3)

@@ -111,3 +111,18 @@ def test_product_cut_measures_closed_forms(lib):
         g = ibdvm.Geometry(case)
         o = oracle.OracleCase(case)
         np.testing.assert_allclose(g.cut_table(), o.cut_table(), rtol=0, atol=1e-14)
+
+
+def test_caller_owned_moment_outputs_are_checked():
+    """Solver.moments fills caller-owned arrays only when they are writeable,
+    C-contiguous float64 arrays of the right shape (checked before any call)."""
+    ok = np.zeros((10, 4))
+    assert ibdvm.Solver._out(ok, (10, 4), "W") is ok
+    assert ibdvm.Solver._out(None, (10, 2), "q").shape == (10, 2)
+    for bad in (np.zeros((10, 3)), np.zeros((10, 4), dtype=np.float32), np.zeros((4, 10)).T):
+        with pytest.raises(ValueError):
+            ibdvm.Solver._out(bad, (10, 4), "W")
+    ro = np.zeros((10, 4))
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        ibdvm.Solver._out(ro, (10, 4), "W")

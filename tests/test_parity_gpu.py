@@ -211,6 +211,14 @@ def test_native_state_transfer():
     buf.mul_(1.01)
     g.set_f_native(buf.data_ptr(), buf.numel() * 4)
     np.testing.assert_allclose(g.get_f(), buf.numpy()[:, : g.nvel].astype(np.float64), rtol=1e-7)
+    # the moments into caller-owned pinned arrays equal those into fresh ones
+    W, q, t = g.moments()
+    Wp = torch.empty(W.shape, dtype=torch.float64, pin_memory=True).numpy()
+    qp = torch.empty(q.shape, dtype=torch.float64, pin_memory=True).numpy()
+    W2, q2, t2 = g.moments(Wp, qp, with_types=False)
+    assert W2 is Wp and q2 is qp and t2 is None
+    np.testing.assert_array_equal(Wp, W)
+    np.testing.assert_array_equal(qp, q)
 
 
 @pytest.mark.parametrize("kind", ["2d_mixed", "3d_mixed", "2d_fp64"])
