@@ -481,6 +481,114 @@ def test_p8_specular_wall():
 
 
 # ---------------------------------------------------------------------------
+# Wall-point quantities: moments of the wall distribution (Sec. 2.1, 2.3, 4)
+# ---------------------------------------------------------------------------
+
+WQ = {k: i for i, k in enumerate(oracle.OracleCase.WALL_COLUMNS)}
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_wall_quantities_in_equilibrium(dim):
+    """Gas at rest at the wall temperature: the wall density balance returns
+    rho_w = rho (the full-range flux of a Maxwellian at rest vanishes on the
+    symmetric grid), so f*_w is the gas Maxwellian in every box, cut or not,
+    and its moments are the Maxwellian's closed forms: rho, U = 0, T = T_w,
+    p = rho T / 2 (the normal stress of a Maxwellian), no shear, no heat flux,
+    C_p = 2 (p - p_0) / (rho_0 U_0^2)."""
+    rho, T = 1.3, 1.15
+    if dim == 2:
+        cfg = case2d(n=16, nv=40, V=7.0, L=1.5, Ma=0.4, body=wl.circle(0.55, Tw=T))
+    else:
+        cfg = case3d(n=12, nv=22, V=6.5, L=1.5, Ma=0.4, body=wl.sphere(0.6, Tw=T))
+    oc = oracle.OracleCase(cfg)
+    M = oc.maxwellian(rho, [0.0] * dim, T)
+    f = np.broadcast_to(M, oc.shape()).copy()
+    wq = oc.wall_quantities(f)
+    assert oc.nlink > 8
+    U0 = 0.4 * math.sqrt(5.0 / 6.0)
+    # the trapezoid error of second moments on the coarser 3D grid is ~2e-11
+    tol = 1e-11 if dim == 2 else 1e-10
+    np.testing.assert_allclose(wq[:, WQ["rho"]], rho, rtol=tol)
+    for k in ("slip_x", "slip_y", "slip_z", "tau_x", "tau_y", "tau_z", "q_n", "T_jump"):
+        assert np.abs(wq[:, WQ[k]]).max() < tol, k
+    np.testing.assert_allclose(wq[:, WQ["T"]], T, rtol=tol)
+    np.testing.assert_allclose(wq[:, WQ["p"]], 0.5 * rho * T, rtol=tol)
+    np.testing.assert_allclose(wq[:, WQ["Cp"]], 2.0 * (0.5 * rho * T - 0.5) / U0**2, rtol=10 * tol)
+
+
+@pytest.mark.parametrize("u", [0.0, 0.35])
+def test_wall_quantities_flat_wall_closed_forms(u):
+    """A Maxwellian gas (rho, T, drift u along the wall) on a diffuse flat wall
+    at rest at T_w: f*_w is the gas Maxwellian on the incident half and
+    rho_w G_w on the reflected half, rho_w = rho sqrt(T / T_w).  Half-range
+    Gaussian integrals give, with U = rho u / (rho + rho_w) the slip,
+      rho_wall = (rho + rho_w) / 2,   p = (rho T + rho_w T_w) / 4,
+      T_wall = [rho (3T/2 + (u - U)^2) + rho_w (3T_w/2 + U^2)] / [3/2 (rho + rho_w)],
+      tau = -rho u sqrt(T) / (2 sqrt(pi)),
+      q_n = rho sqrt(T) [2 (T_w - T) + U^2 - (u - U)^2] / (4 sqrt(pi))
+    (the heat flux about the gas velocity at the wall, which differs from the
+    energy flux in the wall's frame by U tau); no normal velocity, and nothing
+    along the wall at rest.  The midpoint rule converges at second order."""
+    rho, T, Tw = 1.2, 1.1, 0.8
+    rw = rho * math.sqrt(T / Tw)
+    U = rho * u / (rho + rw)
+    sp = math.sqrt(math.pi)
+    expect = {"rho": (rho + rw) / 2.0, "p": (rho * T + rw * Tw) / 4.0,
+              "T": (rho * (1.5 * T + (u - U) ** 2) + rw * (1.5 * Tw + U * U)) / (1.5 * (rho + rw)),
+              "q_n": rho * math.sqrt(T) * (2.0 * (Tw - T) + U * U - (u - U) ** 2) / (4.0 * sp)}
+    if u:
+        expect.update({"slip_y": U, "tau_y": -rho * u * math.sqrt(T) / (2.0 * sp)})
+    if u == 0.0:
+        assert expect["T"] == pytest.approx(math.sqrt(T * Tw), rel=1e-15)
+    errs = []
+    for nv in (40, 80):
+        body = {"kind": "halfspace", "center": [0.0501, 0.0, 0.0], "radii": [1.0, 0.0, 0.0], "Tw": Tw,
+                "accom": 1.0}
+        oc = oracle.OracleCase(case2d(n=8, nv=nv, V=6.0, body=body, rule="midpoint"))
+        f = np.broadcast_to(oc.maxwellian(rho, (0, u), T), oc.shape()).copy()
+        wq = oc.wall_quantities(f)
+        errs.append([np.abs(wq[:, WQ[k]] - v).max() / abs(v) for k, v in expect.items()])
+        zero = ("slip_x", "tau_x") + (() if u else ("slip_y", "tau_y"))
+        for k in zero:
+            assert np.abs(wq[:, WQ[k]]).max() < 1e-13, k
+        np.testing.assert_allclose(wq[:, WQ["T_jump"]], wq[:, WQ["T"]] - Tw, rtol=0, atol=1e-15)
+    errs = np.array(errs)
+    assert errs[0].max() < 1e-2, errs[0]
+    assert np.all(errs[1] < errs[0] / 3.0), errs
+
+
+def test_wall_quantities_specular_wall():
+    """alpha = 0 on an axis-aligned wall: f*_w is the mirror image of the
+    incident gas, so the gas at the wall keeps the incident tangential
+    velocity and the wall feels no shear."""
+    body = {"kind": "halfspace", "center": [0.0501, 0.0, 0.0], "radii": [1.0, 0.0, 0.0], "Tw": 1.0,
+            "accom": 0.0}
+    oc = oracle.OracleCase(case2d(n=8, nv=40, V=7.0, body=body, Ma=0.3))
+    f = np.broadcast_to(oc.maxwellian(1.0, (-0.3, 0.25), 1.1), oc.shape()).copy()
+    wq = oc.wall_quantities(f)
+    np.testing.assert_allclose(wq[:, WQ["slip_y"]], 0.25, rtol=1e-10)
+    assert np.abs(wq[:, WQ["slip_x"]]).max() < 1e-13
+    assert np.abs(wq[:, WQ["tau_y"]]).max() < 1e-13
+
+
+@pytest.mark.parametrize("cutcell", [1, 0])
+def test_wall_quantities_no_flow_through_the_wall(cutcell):
+    """A cylinder in a stream: the wall density balance leaves no mass flux
+    through the wall, so the gas velocity at every wall point is tangential,
+    and the tangential stress is normal to n by construction."""
+    cfg = case2d(n=20, nv=24, V=6.0, L=2.0, Ma=0.5, body=wl.circle(0.6), cutcell=cutcell)
+    oc = oracle.OracleCase(cfg)
+    oc.step(5)
+    wq = oc.wall_quantities()
+    nw = oc.links()["nw"]
+    slip = wq[:, [WQ["slip_x"], WQ["slip_y"], WQ["slip_z"]]]
+    tau = wq[:, [WQ["tau_x"], WQ["tau_y"], WQ["tau_z"]]]
+    assert np.abs(np.sum(slip * nw, axis=1)).max() < 1e-13
+    assert np.abs(np.sum(tau * nw, axis=1)).max() < 1e-14
+    assert np.all(wq[:, WQ["rho"]] > 0) and np.all(wq[:, WQ["T"]] > 0)
+
+
+# ---------------------------------------------------------------------------
 # Transport, relaxation, residual and forces (Sec. 2.2, Sec. 4)
 # ---------------------------------------------------------------------------
 
