@@ -190,6 +190,44 @@ ibdvm_status ibdvm_set_f_native(ibdvm_ctx *ctx, const void *host, size_t bytes);
 ibdvm_status ibdvm_ghost_band(ibdvm_ctx *ctx, double *fiw, double *fstarw, double *fstargc,
                               double *rhow);
 
+/* Wall-point quantities of the current state, one row of IBDVM_WALL_COLS
+   doubles per link (links in the order of ibdvm_geom_links, whose xw and nw
+   give each row's intersect point and unit normal into the gas).  Each row
+   holds moments (Sec. 2.1, Eqs. moments1-3) of the wall distribution f*_w of
+   Sec. 2.3 (Eqs. general bc, Maxwell BC, fwc) at the intersect point: the
+   surface pressure, shear stress, heat flux, slip and temperature jump the
+   paper reports along walls (Sec. 4.2-4.4), and C_p of Sec. 4.3.  With h the
+   mass-carrying component (f in 3D), b the second reduced one (0 in 3D) and
+   the velocity-box weights w (the cut boxes of f*_w already hold the blend of
+   their incident and reflected parts):
+     IBDVM_WALL_RHO     rho = sum w h
+     IBDVM_WALL_SLIP    3 values: U - U_w, U = sum w xi h / rho
+     IBDVM_WALL_T       T with 3/2 rho T = sum w (|c|^2 h + b), c = xi - U
+     IBDVM_WALL_TJUMP   T - T_w
+     IBDVM_WALL_P       p = n.P.n, P_ab = sum w c_a c_b h (normal stress)
+     IBDVM_WALL_TAU     3 values: P.n - p n (tangential stress)
+     IBDVM_WALL_QN      n.q, q = 1/2 sum w c (|c|^2 h + b) (Eq. moments3)
+     IBDVM_WALL_CP      2 (p - p_0) / (rho_0 |U_0|^2), p_0 = rho_0 T_0 / 2;
+                        NaN without a free-stream velocity
+   Computed on the device (the ghost band writes f*_w in FP64 into a scratch
+   buffer of nlink * nvel_padded * ncomp doubles, allocated for the call, and
+   one block per link reduces it in FP64); the state is not changed.  out is
+   caller-owned host memory of nlink * IBDVM_WALL_COLS doubles; nothing is
+   written when the body has no links.  E_INVAL for a NULL out, E_NOMEM when
+   the scratch buffer cannot be allocated. */
+enum {
+  IBDVM_WALL_RHO = 0,
+  IBDVM_WALL_SLIP = 1,
+  IBDVM_WALL_T = 4,
+  IBDVM_WALL_TJUMP = 5,
+  IBDVM_WALL_P = 6,
+  IBDVM_WALL_TAU = 7,
+  IBDVM_WALL_QN = 10,
+  IBDVM_WALL_CP = 11,
+  IBDVM_WALL_COLS = 12
+};
+ibdvm_status ibdvm_wall(ibdvm_ctx *ctx, double *out);
+
 /* Kernel timing.  With profiling on, every kernel launch class is bracketed
    by CUDA events on the context's stream; ms[8] receives the accumulated
    device time and launches[8] the number of kernel launches per class

@@ -905,6 +905,34 @@ ibdvm_status ibdvm_ghost_band(ibdvm_ctx *ctx, double *fiw, double *fstarw, doubl
   IBDVM_END
 }
 
+ibdvm_status ibdvm_wall(ibdvm_ctx *ctx, double *out) {
+  IBDVM_GUARD(ctx)
+  if (!out) {
+    ctx->err = "wall: out is NULL";
+    return IBDVM_E_INVAL;
+  }
+  static_assert(IBDVM_WALL_COLS == kWallCols, "wall columns");
+  const size_t nl = ctx->nlink;
+  if (nl == 0) return IBDVM_OK;
+  const size_t scr = nl * ctx->nvp * ctx->ncomp + nl * kWallCols;
+  double *fstar = dalloc<double>(ctx, scr, "wall-point scratch buffer");
+  ctx->dev_bytes -= scr * sizeof(double);
+  double *dout = fstar + nl * ctx->nvp * ctx->ncomp;
+  ibdvm_status st = IBDVM_OK;
+  try {
+    check(ctx, launch_ghost_band(ctx, fstar), "ghost band kernel");
+    check(ctx, launch_wall(ctx, fstar, dout), "wall kernel");
+    check(ctx, cudaMemcpyAsync(out, dout, nl * kWallCols * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+          "read wall quantities");
+    sync(ctx, "wall quantities");
+  } catch (const Fail &f) {
+    st = f.st;
+  }
+  cudaFree(fstar);
+  return st;
+  IBDVM_END
+}
+
 ibdvm_status ibdvm_get_info(const ibdvm_ctx *ctx, ibdvm_info *info) {
   if (!ctx || !info) return IBDVM_E_INVAL;
   info->dim = ctx->dim;

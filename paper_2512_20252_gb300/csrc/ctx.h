@@ -29,6 +29,9 @@ enum MacSlot {
 // kernel classes of the timing counters
 enum KernelClass { kKGhost = 0, kKSweep = 1, kKMoments = 2, kKForces = 3, kKOther = 4 };
 
+// columns of the wall-point quantities (ibdvm_wall)
+constexpr int kWallCols = 12;
+
 // cell ranges of a pipelined host upload of the state (ibdvm_set_f_native)
 constexpr int kUploadParts = 8;
 
@@ -121,6 +124,9 @@ cudaError_t launch_init_state(ibdvm_ctx *ctx);
 cudaError_t launch_refresh_range(ibdvm_ctx *ctx, long long c0, long long c1);
 // W^n and q^n as rows per cell ([ncell][D + 2] and [ncell][D], device)
 cudaError_t launch_interleave(ibdvm_ctx *ctx, double *Wo, double *qo);
+// wall-point quantities per link ([nlink][kWallCols], device) from the wall
+// distribution f*_w written by the ghost band ([nlink][nvp][ncomp], FP64)
+cudaError_t launch_wall(ibdvm_ctx *ctx, const double *fstar, double *out);
 cudaError_t launch_ghost_band(ibdvm_ctx *ctx, double *dbg_fstarw);
 cudaError_t launch_sweep(ibdvm_ctx *ctx);
 cudaError_t launch_forces(ibdvm_ctx *ctx, double *dst);

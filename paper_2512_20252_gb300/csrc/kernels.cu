@@ -21,6 +21,7 @@
 // transport and relaxation with compensated FP32 moment sums; FP64 wall
 // balance, forces and residual).
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include <algorithm>
 #include <cmath>
@@ -872,6 +873,102 @@ __global__ void __launch_bounds__(kGhostThreads) ghost_band_kernel(GhostArgs<T> 
 }
 
 // ---------------------------------------------------------------------------
+// wall points: moments of the wall distribution f*_w (FP64)
+// ---------------------------------------------------------------------------
+
+struct WallArgs {
+  const double *__restrict__ fstar; // [nlink][nvp][NC], f*_w of the ghost band
+  const double *__restrict__ xiD;   // [3][nvp]
+  const double *__restrict__ wD;    // [nvp]
+  const double *__restrict__ l_dbl; // [nlink][8]; the wall normal at 3..5
+  double *__restrict__ out;         // [nlink][kWallCols]
+  int nv, nvp;
+  double Tw, Uw[3];
+  double p0, dyn0; // free-stream pressure rho_0 T_0 / 2 and rho_0 |U_0|^2
+};
+
+constexpr int kWallThreads = 256;
+
+// One block per link: rho and U from the first pass, then the central
+// moments about U (temperature, stress tensor, heat flux of Eq. moments3) and
+// the wall-point quantities from them.  The cut boxes of f*_w already hold the
+// blend of the incident and reflected parts, so the plain weights give the
+// cut-corrected moments.
+template <int D> __global__ void __launch_bounds__(kWallThreads) wall_kernel(WallArgs A) {
+  constexpr int NC = Dims<D>::NC;
+  constexpr int NP = D * (D + 1) / 2; // independent stress components
+  __shared__ double sh[kWallThreads / 32 + 1];
+  const int l = blockIdx.x;
+  const double *fs = A.fstar + (size_t)l * A.nvp * NC;
+  double s0 = 0.0, s1[3] = {0.0, 0.0, 0.0};
+  for (int k = threadIdx.x; k < A.nv; k += blockDim.x) {
+    const double wh = A.wD[k] * fs[(size_t)k * NC];
+    s0 += wh;
+#pragma unroll
+    for (int a = 0; a < D; ++a) s1[a] += A.xiD[a * A.nvp + k] * wh;
+  }
+  const double rho = block_sum<kWallThreads>(s0, sh);
+  double U[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int a = 0; a < D; ++a) U[a] = block_sum<kWallThreads>(s1[a], sh) / rho;
+  double se = 0.0, sp[NP], sq[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < NP; ++i) sp[i] = 0.0;
+  for (int k = threadIdx.x; k < A.nv; k += blockDim.x) {
+    const double h = fs[(size_t)k * NC], b = (NC == 2) ? fs[(size_t)k * NC + 1] : 0.0;
+    double c[3], c2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      c[a] = A.xiD[a * A.nvp + k] - U[a];
+      c2 += c[a] * c[a];
+    }
+    const double wk = A.wD[k], wh = wk * h, we = wk * (c2 * h + b);
+    se += we;
+    int i = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int bb = a; bb < D; ++bb) sp[i++] += c[a] * c[bb] * wh;
+#pragma unroll
+    for (int a = 0; a < D; ++a) sq[a] += c[a] * we;
+  }
+  const double E = block_sum<kWallThreads>(se, sh);
+  double P[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  {
+    int i = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int bb = a; bb < D; ++bb) {
+        const double v = block_sum<kWallThreads>(sp[i++], sh);
+        P[a][bb] = P[bb][a] = v;
+      }
+  }
+  double q[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int a = 0; a < D; ++a) q[a] = 0.5 * block_sum<kWallThreads>(sq[a], sh);
+  if (threadIdx.x == 0) {
+    const double *n = A.l_dbl + 8 * (size_t)l + 3;
+    double Pn[3], p = 0.0, qn = 0.0;
+    for (int a = 0; a < 3; ++a) Pn[a] = P[a][0] * n[0] + P[a][1] * n[1] + P[a][2] * n[2];
+    for (int a = 0; a < 3; ++a) {
+      p += n[a] * Pn[a];
+      qn += n[a] * q[a];
+    }
+    const double T = 2.0 * E / (3.0 * rho);
+    double *o = A.out + (size_t)l * kWallCols;
+    o[0] = rho;
+    for (int a = 0; a < 3; ++a) o[1 + a] = U[a] - A.Uw[a];
+    o[4] = T;
+    o[5] = T - A.Tw;
+    o[6] = p;
+    for (int a = 0; a < 3; ++a) o[7 + a] = Pn[a] - p * n[a];
+    o[10] = qn;
+    o[11] = (A.dyn0 > 0.0) ? 2.0 * (p - A.p0) / A.dyn0 : CUDART_NAN;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // forces: momentum and energy through the donor-ghost faces (FP64 sums)
 // ---------------------------------------------------------------------------
 
@@ -1325,6 +1422,29 @@ cudaError_t launch_ghost_band(ibdvm_ctx *ctx, double *dbg) {
     constexpr int D = decltype(d)::value;
     return ghost_t<T, D>(ctx, dbg);
   });
+}
+
+cudaError_t launch_wall(ibdvm_ctx *ctx, const double *fstar, double *out) {
+  if (ctx->nlink == 0) return cudaSuccess;
+  const Geom &g = ctx->geom;
+  WallArgs A{};
+  A.fstar = fstar;
+  A.xiD = ctx->xiD;
+  A.wD = ctx->wD;
+  A.l_dbl = ctx->l_dbl;
+  A.out = out;
+  A.nv = ctx->nv;
+  A.nvp = ctx->nvp;
+  A.Tw = g.body.T_w;
+  for (int a = 0; a < 3; ++a) A.Uw[a] = g.body.U_w[a];
+  A.p0 = 0.5 * g.gas.rho_inf * g.gas.T_inf;
+  A.dyn0 = g.gas.rho_inf * (g.Uinf[0] * g.Uinf[0] + g.Uinf[1] * g.Uinf[1] + g.Uinf[2] * g.Uinf[2]);
+  ctx->kernel_launches[kKOther] += 1;
+  if (ctx->dim == 2)
+    wall_kernel<2><<<ctx->nlink, kWallThreads, 0, ctx->stream>>>(A);
+  else
+    wall_kernel<3><<<ctx->nlink, kWallThreads, 0, ctx->stream>>>(A);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(ibdvm_ctx *ctx) {

@@ -110,6 +110,7 @@ SIGNATURES = {
     "ibdvm_get_f_native": ([_V, _V, ctypes.c_size_t], _S),
     "ibdvm_set_f_native": ([_V, _V, ctypes.c_size_t], _S),
     "ibdvm_ghost_band": ([_V, _D, _D, _D, _D], _S),
+    "ibdvm_wall": ([_V, _D], _S),
     "ibdvm_residual_noalloc": ([_V, _V, _V, ctypes.c_longlong, ctypes.c_int, _V, _V], _S),
     "ibdvm_get_info": ([_V, ctypes.POINTER(Info)], _S),
     "ibdvm_selftest_bounded_wait": ([ctypes.c_int, ctypes.c_int, _D, _V], _S),
@@ -480,6 +481,19 @@ class Solver:
                                               _dp(out["fstargc"]), _dp(rhow)))
         out["rhow"] = rhow[: self.nlink]
         return out
+
+    WALL_COLUMNS = ("rho", "slip_x", "slip_y", "slip_z", "T", "T_jump", "p", "tau_x", "tau_y", "tau_z",
+                    "q_n", "Cp")
+
+    def wall(self) -> np.ndarray:
+        """Wall-point quantities per link ([nlink][12], columns WALL_COLUMNS):
+        density, slip velocity, temperature and its jump, normal and
+        tangential stress, normal heat flux and C_p from the moments of the
+        wall distribution at each link's intersect point (geometry().links()
+        gives the points and normals)."""
+        out = np.zeros((max(self.nlink, 1), len(self.WALL_COLUMNS)))
+        self._check(self.lib.ibdvm_wall(self.h, _dp(out)))
+        return out[: self.nlink]
 
     def geometry(self) -> Geometry:
         return Geometry._borrow(self.lib, self.lib.ibdvm_get_geom(self.h))

@@ -262,6 +262,60 @@ def test_pipelined_state_upload(kind):
     assert qe < 1e3 * tol, qe
 
 
+WALL = {k: i for i, k in enumerate(ibdvm.Solver.WALL_COLUMNS)}
+
+
+def _no_flow_through_the_wall(wq, nw):
+    """The wall density balance leaves no mass flux through any wall point:
+    the gas velocity there is tangential, as is the tangential stress."""
+    slip = wq[:, WALL["slip_x"]:WALL["slip_z"] + 1]
+    tau = wq[:, WALL["tau_x"]:WALL["tau_z"] + 1]
+    assert np.all(wq[:, WALL["rho"]] > 0) and np.all(wq[:, WALL["T"]] > 0)
+    assert np.abs(np.sum(slip * nw, axis=1)).max() < 1e-10 * max(np.abs(slip).max(), 1e-3)
+    assert np.abs(np.sum(tau * nw, axis=1)).max() < 1e-12 * np.abs(wq[:, WALL["p"]]).max()
+
+
+@pytest.mark.parametrize("dim,precision", [(2, "fp64"), (3, "fp64"), (2, "mixed"), (3, "mixed")])
+def test_wall_quantities_against_the_oracle(dim, precision):
+    """Wall-point quantities (moments of f*_w per link) through the C-ABI
+    against the oracle, after a few steps of a flow past the body."""
+    if dim == 2:
+        case = wl.small_2d("circle", n=24, nv=12, Ma=0.5, precision=precision)
+    else:
+        case = wl._case(3, 12, 2.0, 8, 4.5, 0.1, 0.5, wl.sphere(0.6), precision=precision)
+    g = ibdvm.Solver(case)
+    o = oracle.OracleCase(case)
+    g.step(4)
+    o.step(4)
+    wg = g.wall()
+    wo = o.wall_quantities()
+    assert wg.shape == wo.shape == (o.nlink, len(ibdvm.Solver.WALL_COLUMNS)) and o.nlink > 8
+    assert list(ibdvm.Solver.WALL_COLUMNS) == list(o.WALL_COLUMNS)
+    tol = TOL if precision == "fp64" else 1e-4
+    for i, c in enumerate(o.WALL_COLUMNS):
+        err = np.abs(wg[:, i] - wo[:, i]).max() / max(np.abs(wo[:, i]).max(), 1e-3)
+        assert err < tol, (c, err)
+    _no_flow_through_the_wall(wg, g.geometry().links()["nw"])
+    g.close()
+
+
+def test_wall_quantities_without_a_body_or_a_free_stream():
+    """No links: nothing to report.  Ma = 0: C_p is undefined (NaN), the rest
+    is the equilibrium of a gas at rest at the wall temperature."""
+    g = ibdvm.Solver(wl._case(2, 12, 1.0, 8, 4.0, 0.1, 0.3, {"kind": "none"}))
+    assert g.wall().shape == (0, 12)
+    g.close()
+    g = ibdvm.Solver(wl.small_2d("circle", n=16, nv=16, Ma=0.0))
+    wq = g.wall()
+    assert np.all(np.isnan(wq[:, WALL["Cp"]]))
+    # to the truncated tails of the Maxwellian on [-4.5, 4.5] (exp(-4.5^2) =
+    # 1.6e-9 for the mass, a few times more for the second moment)
+    np.testing.assert_allclose(wq[:, WALL["rho"]], 1.0, rtol=1e-8)
+    np.testing.assert_allclose(wq[:, WALL["p"]], 0.5, rtol=1e-7)
+    assert np.abs(wq[:, WALL["slip_x"]:WALL["slip_z"] + 1]).max() < 1e-12
+    g.close()
+
+
 def test_runs_on_a_torch_stream():
     torch = pytest.importorskip("torch")
     case = wl.small_2d("circle", n=16, nv=8)
@@ -307,6 +361,19 @@ def test_cylinder_512_full_size_properties(precision, tol):
     far = W1.reshape(n, n, -1)[:40, :40]
     np.testing.assert_allclose(far[..., 0], 1.0, rtol=1e-5)
     np.testing.assert_allclose(far[..., 1], U, rtol=1e-4)
+    # wall points: no flow through the wall, and mirror links agree
+    wq = g.wall()
+    lk = g.geometry().links()
+    _no_flow_through_the_wall(wq, lk["nw"])
+    key = {(round(x, 9), round(y, 9)): i for i, (x, y, _) in enumerate(lk["xw"])}
+    mir = np.array([key[(round(x, 9), round(-y, 9))] for x, y, _ in lk["xw"]])
+    stol = 1e-11 if precision == "fp64" else 1e-5
+    for c in ("rho", "T", "p", "slip_x", "tau_x"):
+        i = WALL[c]
+        assert np.abs(wq[mir, i] - wq[:, i]).max() < stol * np.abs(wq[:, i]).max(), c
+    for c in ("slip_y", "tau_y"):
+        i = WALL[c]
+        assert np.abs(wq[mir, i] + wq[:, i]).max() < stol * np.abs(wq[:, i]).max(), c
     g.close()
 
 
@@ -319,6 +386,7 @@ def test_sphere_96_full_size_properties():
     Wm = W1.reshape(n, n, n, -1)
     assert np.abs(Wm[:, ::-1, :, 0] - Wm[:, :, :, 0]).max() < 1e-5
     assert np.abs(Wm[::-1, :, :, 0] - Wm[:, :, :, 0]).max() < 1e-5
+    _no_flow_through_the_wall(g.wall(), g.geometry().links()["nw"])
     g.close()
 
 
