@@ -84,6 +84,9 @@ class _Params(ctypes.Structure):
         ("Lref", ctypes.c_double),
         ("cutcell", ctypes.c_int),
         ("upwind", ctypes.c_int),
+        ("wall", ctypes.c_int * 6),
+        ("wall_T", ctypes.c_double * 6),
+        ("wall_U", (ctypes.c_double * 3) * 6),
     ]
 
 
@@ -118,6 +121,7 @@ def _load():
                 "or_moments": ([V, _D, _D], None),
                 "or_forces": ([V, _D, _D, _D, _D], None),
                 "or_ghost_band": ([V, _D, _D, _D, _D, _D, _D, _D], None),
+                "or_domain_wall_density": ([V, _D, _D], None),
                 "or_mu0": ([ctypes.c_double] * 3, ctypes.c_double),
                 "or_vanleer": ([ctypes.c_double] * 2, ctypes.c_double),
                 "or_cell_moments": ([V, _D, _D], None),
@@ -182,6 +186,13 @@ def _params(cfg: dict) -> tuple[_Params, object]:
     p.Lref = body.get("Lref", 0.0)
     p.cutcell = int(cfg.get("cutcell", 1))
     p.upwind = int(cfg.get("upwind", 1))
+    # domain faces (x-, x+, y-, y+, z-, z+): None = freestream halo, or a
+    # diffuse wall {"Tw": T, "Uw": [u, v, w]}
+    for i, wall in enumerate(cfg.get("domain_walls") or [None] * 6):
+        if wall:
+            p.wall[i] = 1
+            p.wall_T[i] = float(wall.get("Tw", 1.0))
+            p.wall_U[i][:] = _arr3(list(wall.get("Uw", [0.0, 0.0, 0.0])))
     return p, keep
 
 
@@ -296,6 +307,16 @@ class OracleCase:
             _dp(rhow),
         )
         out["rhow"] = rhow[: self.nlink]
+        return out
+
+    def domain_wall_density(self, f: np.ndarray | None = None) -> np.ndarray:
+        """rho_w of every diffuse domain face, [cell][6] (faces 2a + (s > 0));
+        0 where the face is not a diffuse wall of a fluid cell."""
+        if f is None:
+            f = self.get_f()
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.shape())
+        out = np.zeros((self.ncell, 6))
+        self.lib.or_domain_wall_density(self.h, _dp(f), _dp(out))
         return out
 
     # wall points ------------------------------------------------------------

@@ -51,10 +51,17 @@
  *   C18 residual components whose sum of |W| is zero are skipped.
  *   C19 surface force and heat flux: momentum and energy carried through the
  *       donor-ghost faces by the face fluxes the update applies.
+ *   C24 a domain face may instead be a diffuse wall (Sec. 2.3 with alpha = 1
+ *       on the plane of the face, normal into the domain): its two halo
+ *       layers hold, for velocities entering the domain through the face,
+ *       rho_w times the unit-density wall Maxwellian, and for the others the
+ *       boundary cell's own value (so the outgoing face value is the cell
+ *       value: the limiter sees a zero difference); rho_w makes the mass flux
+ *       through the face zero with those face values.
  *
- * Parity unpinned: C4-C7, C9, C10, C14, C16-C19 are choices the paper does
- * not fix; they are pinned only by agreement with an independent
- * implementation, not by the paper.
+ * Parity unpinned: C4-C7, C9, C10, C14, C16-C19 and the first-order
+ * outgoing face of C24 are choices the paper does not fix; they are pinned
+ * only by agreement with an independent implementation, not by the paper.
  */
 #include "ibdvm_oracle.h"
 
@@ -101,6 +108,8 @@ struct or_case {
   or_ghost *ghosts;
   double *wg;   /* incident-side measure per link and velocity */
   double *lval; /* ghost value f*_gc per link, velocity, component */
+  double *wrho; /* rho_w of the diffuse domain faces of the state last given (C24), [cell][6] */
+  int any_wall;
   double dt, mu0, Uinf[3];
 };
 
@@ -742,6 +751,8 @@ or_case *or_create(const or_params *p)
     }
   }
   C->lval = (double *)xcalloc((size_t)nl * C->nv * C->ncomp, sizeof(double));
+  C->wrho = (double *)xcalloc((size_t)C->nc * 6, sizeof(double));
+  for (int i = 0; i < 2 * C->dim; ++i) C->any_wall |= (p->wall[i] != 0);
   return C;
 }
 
@@ -763,7 +774,70 @@ void or_destroy(or_case *C)
   free(C->ghost_of);
   free(C->wg);
   free(C->lval);
+  free(C->wrho);
   free(C);
+}
+
+/* ------------------------------------------------------------------------ */
+/* the domain halo: freestream (C17) or diffuse walls (C24)                  */
+/* ------------------------------------------------------------------------ */
+
+/* unit-density Maxwellian of domain face i at velocity node k, component m */
+static double wall_maxwellian(const or_case *C, int i, int k, int m)
+{
+  double T = C->p.wall_T[i], c2 = 0.0;
+  for (int a = 0; a < C->dim; ++a) {
+    double c = C->xi[3 * k + a] - C->p.wall_U[i][a];
+    c2 += c * c;
+  }
+  if (C->dim == 2) {
+    double H = exp(-c2 / T) / (M_PI * T);
+    return (m == 0) ? H : 0.5 * T * H;
+  }
+  return exp(-c2 / T) / pow(M_PI * T, 1.5);
+}
+
+/* rho_w of every diffuse domain face of fluid cells for the state f: the
+   mass flux out of the domain through the face, carried by the cell's own
+   value, is returned by rho_w times the wall Maxwellian (Eq. dnpc on the
+   face, incident set s xi_a > 0) */
+static void domain_walls(const or_case *C, const double *f)
+{
+  if (!C->any_wall) return;
+  for (long c = 0; c < C->nc; ++c) {
+    for (int i = 0; i < 6; ++i) C->wrho[c * 6 + i] = 0.0;
+    if (C->type[c] != OR_FLUID) continue;
+    for (int a = 0; a < C->dim; ++a)
+      for (int s = -1; s <= 1; s += 2) {
+        int i = 2 * a + (s > 0);
+        if (!C->p.wall[i] || neighbour(C, c, a, s) >= 0) continue;
+        double out = 0.0, in = 0.0;
+        for (int k = 0; k < C->nv; ++k) {
+          double xs = s * C->xi[3 * k + a];
+          if (xs > 0.0)
+            out += C->w[k] * xs * F(C, (double *)f, c, k)[0];
+          else if (xs < 0.0)
+            in += C->w[k] * xs * wall_maxwellian(C, i, k, 0);
+        }
+        C->wrho[c * 6 + i] = -out / in;
+      }
+  }
+}
+
+void or_domain_wall_density(const or_case *C, const double *f, double *out)
+{
+  domain_walls(C, f);
+  for (long i = 0; i < C->nc * 6; ++i) out[i] = C->any_wall ? C->wrho[i] : 0.0;
+}
+
+/* value of the halo cells across domain face (a, s) of cell c (both layers
+   hold the same value); domain_walls has been run on f */
+static double halo_value(const or_case *C, const double *f, long c, int a, int s, int k, int m)
+{
+  int i = 2 * a + (s > 0);
+  if (!C->p.wall[i]) return C->finf[k * C->ncomp + m];
+  if (s * C->xi[3 * k + a] < 0.0) return C->wrho[c * 6 + i] * wall_maxwellian(C, i, k, m);
+  return F(C, (double *)f, c, k)[m];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -778,8 +852,8 @@ static double preghost_slope(const or_case *C, const double *f, long j, int a, i
   long jm = neighbour(C, j, a, -1), jp = neighbour(C, j, a, +1);
   int have_m = (jm < 0) || C->type[jm] == OR_FLUID;
   int have_p = (jp < 0) || C->type[jp] == OR_FLUID;
-  double fm = (jm < 0) ? C->finf[k * C->ncomp + m] : (have_m ? F(C, (double *)f, jm, k)[m] : 0.0);
-  double fp = (jp < 0) ? C->finf[k * C->ncomp + m] : (have_p ? F(C, (double *)f, jp, k)[m] : 0.0);
+  double fm = (jm < 0) ? halo_value(C, f, j, a, -1, k, m) : (have_m ? F(C, (double *)f, jm, k)[m] : 0.0);
+  double fp = (jp < 0) ? halo_value(C, f, j, a, +1, k, m) : (have_p ? F(C, (double *)f, jp, k)[m] : 0.0);
   double h = C->dx[a];
   if (have_m && have_p) return or_vanleer((fj - fm) / h, (fp - fj) / h);
   if (have_m) return (fj - fm) / h;
@@ -875,6 +949,7 @@ void or_ghost_band(const or_case *C, const double *f, double *fgc_out, double *f
   double *fs = (double *)xcalloc((size_t)nv * nc, sizeof(double));
   double *Gw = (double *)xcalloc((size_t)nv * nc, sizeof(double));
   double alpha = C->p.accom;
+  domain_walls(C, f); /* the halo values the pre-ghost slopes see */
   for (int gi = 0; gi < C->nghost; ++gi) {
     const or_ghost *G = &C->ghosts[gi];
     /* step 2: intermediate ghost value f_gc (shared by the ghost's links) */
@@ -956,11 +1031,12 @@ static int find_link(const or_case *C, long g, long d)
 }
 
 /* value of the cell across face (a, s) of fluid cell c as this cell sees it:
-   halo -> freestream (C17); ghost -> the link's ghost value (C4) */
+   halo -> freestream (C17) or diffuse wall (C24); ghost -> the link's ghost
+   value (C4) */
 static double seen_value(const or_case *C, const double *f, long c, int a, int s, int k, int m)
 {
   long nb = neighbour(C, c, a, s);
-  if (nb < 0) return C->finf[k * C->ncomp + m];
+  if (nb < 0) return halo_value(C, f, c, a, s, k, m);
   if (C->type[nb] == OR_FLUID) return F(C, (double *)f, nb, k)[m];
   int l = find_link(C, nb, c);
   return C->lval[((size_t)l * C->nv + k) * C->ncomp + m];
@@ -987,7 +1063,7 @@ static double face_value(const or_case *C, const double *f, long c, int a, int s
   long nb = neighbour(C, c, a, s);
   if (nb < 0) {
     /* halo cell: its neighbours are the next halo cell and c */
-    double fh = C->finf[k * C->ncomp + m];
+    double fh = halo_value(C, f, c, a, s, k, m);
     double sig;
     if (s > 0) /* left neighbour c, right neighbour the next halo cell */
       sig = or_vanleer((fh - fc) / h, (fh - fh) / h);

@@ -65,6 +65,11 @@ typedef struct {
   int upwind;  /* 1: upwind weights with r pointing from the fluid cell to the ghost cell,
                   2: upwind weights with r pointing from the ghost cell to the fluid cell,
                   0: plain average 1/N_S */
+  /* domain faces 2a + (s > 0) (x-, x+, y-, y+, z-, z+): 0 = two freestream
+     halo layers (C17), 1 = diffuse wall at wall_T with velocity wall_U (C24) */
+  int wall[6];
+  double wall_T[6];
+  double wall_U[6][3];
 } or_params;
 
 typedef struct or_case or_case;
@@ -99,6 +104,11 @@ int or_step(or_case *C, int nsteps, double *residual);
 void or_moments(const or_case *C, double *W, double *q);
 /* surface force and heat flux, Eq. moments applied to the face fluxes on the link faces */
 void or_forces(const or_case *C, double *F3, double *Q, double *CD, double *CL);
+
+/* wall density rho_w of every diffuse domain face of the given state,
+   out[cell * 6 + 2a + (s > 0)] (0 where the face is not a diffuse wall of a
+   fluid cell) */
+void or_domain_wall_density(const or_case *C, const double *f, double *out);
 
 /* the ghost band on the given state (Sec. 3.2.1 steps 1-4) */
 void or_ghost_band(const or_case *C, const double *f, double *fgc, double *fsp, double *fiw,

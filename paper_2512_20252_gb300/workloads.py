@@ -110,6 +110,26 @@ def cylinder_512(Kn=0.1, precision="mixed", steps=200):
     return _case(2, 512, 8.0, 48, 6.0, Kn, 0.5, circle(0.5), precision=precision, steps=steps)
 
 
+def box_walls(dim=2, Tw=1.0, lid=None, lid_T=None):
+    """Diffuse walls on every domain face (x-, x+, y-, y+, z-, z+) at Tw; lid:
+    the velocity of the top face (y+ in 2D, z+ in 3D), its temperature lid_T."""
+    walls = [{"Tw": Tw, "Uw": [0.0, 0.0, 0.0]} for _ in range(2 * dim)] + [None] * (6 - 2 * dim)
+    top = 2 * (dim - 1) + 1
+    if lid is not None:
+        walls[top] = {"Tw": Tw if lid_T is None else lid_T, "Uw": list(lid) + [0.0] * (3 - len(lid))}
+    return walls
+
+
+def cavity(n=64, nv=40, Kn=0.075, lid=0.15, precision="fp64", steps=200, cutcell=1, body=True):
+    """Lid-driven cavity with a stationary cylinder at its centre (Sec. 4.1):
+    [0,1]^2 on n^2 cells, diffuse walls at T_w = 1, the top wall moving at
+    U_w = lid along x, a cylinder of diameter 0.25 at (0.5, 0.5) with T_w = 1,
+    nv^2 velocities on [-5,5]^2, Kn 0.075, the gas initially at rest."""
+    b = circle(0.125, center=(0.5, 0.5)) if body else {"kind": "none"}
+    return _case(2, n, ([0.0, 0.0], [1.0, 1.0]), nv, 5.0, Kn, 0.0, b, precision=precision, steps=steps,
+                 cutcell=cutcell, domain_walls=box_walls(2, 1.0, lid=(lid, 0.0)))
+
+
 def sphere_96(precision="mixed", steps=200):
     """3D flow past a sphere: 96^3 cells on [-4,4]^3, r = 0.5, 20^3 velocities on
     [-5,5]^3, Kn 0.1, Ma 0.5."""

@@ -589,6 +589,73 @@ def test_wall_quantities_no_flow_through_the_wall(cutcell):
 
 
 # ---------------------------------------------------------------------------
+# Diffuse domain walls (Sec. 2.3 on the faces of the domain; reading C24)
+# ---------------------------------------------------------------------------
+
+def box(dim, n, nv, V, Kn, body=None, lid=None, Tw=1.0, **kw):
+    make = case2d if dim == 2 else case3d
+    return make(n=n, nv=nv, V=V, L=([0.0] * dim, [1.0] * dim), Kn=Kn, body=body,
+                domain_walls=wl.box_walls(dim, Tw, lid=lid), **kw)
+
+
+@pytest.mark.parametrize("dim,Kn", [(2, 1e12), (2, 0.1), (3, 1e12)])
+def test_closed_box_at_rest_stays_at_rest(dim, Kn):
+    """A Maxwellian at rest at the wall temperature in a box of diffuse walls:
+    every wall density equals the gas density (the half-range fluxes of a
+    Maxwellian at rest cancel on the symmetric grid), every face value is the
+    Maxwellian, and the state does not move: exactly without collisions, to
+    the quadrature level of the Shakhov term with them."""
+    n = 8 if dim == 2 else 6
+    cfg = box(dim, n, 20 if dim == 2 else 12, 6.0, Kn, Tw=1.1)
+    oc = oracle.OracleCase(cfg)
+    f0 = np.broadcast_to(oc.maxwellian(1.2, [0.0] * dim, 1.1), oc.shape()).copy()
+    oc.set_f(f0)
+    rw = oc.domain_wall_density()
+    assert np.count_nonzero(rw) == 2 * dim * n ** (dim - 1)
+    np.testing.assert_allclose(rw[rw != 0], 1.2, rtol=1e-14)
+    oc.step(10)
+    tol = 1e-14 if Kn > 1e6 else 1e-9
+    assert np.abs(oc.get_f() - f0).max() < tol * np.abs(f0).max()
+
+
+def test_closed_box_conserves_mass():
+    """No mass crosses a diffuse wall, so a closed box keeps its mass to
+    rounding (collisionless, so the Shakhov quadrature error does not enter),
+    with a moving lid and walls at two temperatures."""
+    cfg = case2d(n=12, nv=16, V=5.0, L=([0.0, 0.0], [1.0, 1.0]), Kn=1e12)
+    cfg["domain_walls"] = wl.box_walls(2, 0.8, lid=(0.3, 0.0), lid_T=1.3)
+    oc = oracle.OracleCase(cfg)
+    xi, w = oc.velocities()
+    m0 = np.sum(oc.get_f()[:, :, 0] @ w)
+    oc.step(30)
+    f = oc.get_f()
+    m1 = np.sum(f[:, :, 0] @ w)
+    assert abs(m1 - m0) < 1e-13 * m0
+    # the lid has set the gas in motion and the walls have changed its energy
+    assert np.abs(f[:, :, 0] @ (w * xi[:, 0])).max() > 1e-3
+
+
+@pytest.mark.parametrize("Uw", [0.0, 0.4])
+def test_domain_wall_density_closed_form(Uw):
+    """Gas at rest (rho, T) on a diffuse domain wall at T_w moving along
+    itself: rho_w = rho sqrt(T / T_w) (the half-range flux of the wall
+    Maxwellian does not depend on its tangential velocity); the midpoint rule
+    converges to it at second order."""
+    rho, T, Tw = 1.2, 1.1, 0.9
+    errs = []
+    for nv in (40, 80):
+        cfg = case2d(n=6, nv=nv, V=6.0, rule="midpoint", L=([0.0, 0.0], [1.0, 1.0]))
+        cfg["domain_walls"] = [{"Tw": Tw, "Uw": [0.0, Uw, 0.0]}] + [None] * 5   # the x- face only
+        oc = oracle.OracleCase(cfg)
+        f = np.broadcast_to(oc.maxwellian(rho, (0, 0), T), oc.shape()).copy()
+        rw = oc.domain_wall_density(f)
+        assert np.count_nonzero(rw) == 6 and np.count_nonzero(rw[:, 1:]) == 0
+        errs.append(np.abs(rw[rw != 0] - rho * math.sqrt(T / Tw)).max())
+    assert errs[0] < 5e-3
+    assert errs[1] < errs[0] / 3.0
+
+
+# ---------------------------------------------------------------------------
 # Transport, relaxation, residual and forces (Sec. 2.2, Sec. 4)
 # ---------------------------------------------------------------------------
 
