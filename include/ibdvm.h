@@ -147,6 +147,35 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
    nothing else: f is kept.  Errors: IBDVM_E_INVAL, IBDVM_E_NOMEM, IBDVM_E_CUDA. */
 ibdvm_status ibdvm_set_body(ibdvm_ctx *ctx, const ibdvm_body_desc *body);
 
+/* Domain faces, index 2a + (s > 0): x-, x+, y-, y+, z-, z+.  A freestream face
+   has two halo layers holding the freestream Maxwellian (the default).  A
+   diffuse wall face is the Maxwell wall of Sec. 2.3 with alpha = 1 on the
+   plane of the face (normal into the domain): for velocities entering the
+   domain through it, both halo layers hold rho_w times the unit-density wall
+   Maxwellian at (T_w, U_w) (2D reduced: H_w = exp(-|xi - U_w|^2 / T_w) /
+   (pi T_w), B_w = T_w / 2 H_w); for the other velocities they hold the
+   boundary cell's own value, so the outgoing face value is the cell value;
+   rho_w (FP64, per boundary cell, from f^n each step) makes the mass flux
+   through the face zero, the velocities split by the plane xi_a = 0 (the
+   lid-driven cavity of Sec. 4.1). */
+enum { IBDVM_FACE_FREESTREAM = 0, IBDVM_FACE_DIFFUSE_WALL = 1 };
+typedef struct {
+  int kind[6];       /* IBDVM_FACE_*; the z faces of a 2D grid must be freestream */
+  double T_w[6];     /* wall temperature (> 0) of a diffuse wall face */
+  double U_w[6][3];  /* wall velocity; its normal component does not move the split plane */
+} ibdvm_domain_desc;
+
+/* Sets the domain faces.  Cases with a diffuse domain wall run the generic
+   sweep kernel (the TMA sweeps handle freestream faces only) and cannot be
+   batch members.  The state is kept.  With any wall the library allocates
+   (2 ncell / n[a] summed over the D axes) * nvel_padded * ncomp elements of
+   the storage type for the halo values, and frees them with the context or
+   on the next call.
+   Errors: IBDVM_E_INVAL (a bad kind, a z wall in 2D, T_w <= 0 or a
+   non-finite U_w; nothing changes), IBDVM_E_STATE (the context is a batch
+   member), IBDVM_E_NOMEM. */
+ibdvm_status ibdvm_set_domain(ibdvm_ctx *ctx, const ibdvm_domain_desc *d);
+
 /* Advances nsteps forward-Euler steps (Sec. 4): ghost band, then transport
    and relaxation of every fluid cell, then the moments.  residual_out
    (nullable) receives the residual of the last step (Sec. 4 convergence

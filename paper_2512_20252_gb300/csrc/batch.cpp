@@ -364,7 +364,7 @@ ibdvm_status ibdvm_batch_add(ibdvm_batch *b, ibdvm_ctx *ctx) {
     return IBDVM_E_STATE;
   }
   if (!ctx->use_tma || !tma_batch_member_ok(ctx)) {
-    b->err = "batch members are contexts in FP32 storage with the TMA sweep";
+    b->err = "batch members are contexts in FP32 storage with the TMA sweep (no diffuse domain walls)";
     return IBDVM_E_INVAL;
   }
   if (!b->members.empty() && b->members[0]->dim != ctx->dim) {

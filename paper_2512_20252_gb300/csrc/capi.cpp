@@ -132,6 +132,7 @@ void free_all(ibdvm_ctx *ctx) {
   cfree_t(ctx->partf);
   cfree_t(ctx->d_forces);
   cfree_t(ctx->d_step_forces);
+  cfree(ctx->whalo);
   for (cudaEvent_t &e : ctx->copy_ev)
     if (e) {
       cudaEventDestroy(e);
@@ -228,7 +229,7 @@ void upload_body(ibdvm_ctx *ctx) {
             int q[3] = {ij[0], ij[1], ij[2]};
             q[a] += s ? 1 : -1;
             if (q[a] < 0 || q[a] >= G.n[a]) {
-              code = -1; // domain halo: freestream
+              code = -1; // domain halo: freestream or a diffuse domain wall
             } else {
               long long nb = q[0] + G.n[0] * (q[1] + static_cast<long long>(G.n[1]) * q[2]);
               if (G.type[nb] == IBDVM_CELL_FLUID) code = static_cast<int>(nb);
@@ -595,6 +596,7 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
       ctx->partf = dalloc<float>(ctx, nch * nmoments(G.dim) * ctx->ncell, "FP32 moment sums");
       check(ctx, two ? tma_sweep_prepare(ctx) : tma3_sweep_prepare(ctx), "TMA sweep set-up");
       ctx->use_tma = true;
+      ctx->tma_ok = true;
     }
     // velocity tables
     std::vector<double> xi3(3 * static_cast<size_t>(ctx->nvp), 0.0), w(ctx->nvp, 0.0);
@@ -677,6 +679,68 @@ ibdvm_status ibdvm_set_body(ibdvm_ctx *ctx, const ibdvm_body_desc *body) {
   }
   refresh_moments(ctx);
   return status_of_flags(ctx, read_flags(ctx));
+  IBDVM_END
+}
+
+ibdvm_status ibdvm_set_domain(ibdvm_ctx *ctx, const ibdvm_domain_desc *d) {
+  IBDVM_GUARD(ctx)
+  if (!d) {
+    ctx->err = "domain description is NULL";
+    return IBDVM_E_INVAL;
+  }
+  if (ctx->batch) {
+    ctx->err = "set_domain: the context is a member of a batch; remove it first";
+    return IBDVM_E_STATE;
+  }
+  const int D = ctx->dim;
+  int mask = 0;
+  for (int i = 0; i < 6; ++i) {
+    const int kind = d->kind[i];
+    if (kind != IBDVM_FACE_FREESTREAM && kind != IBDVM_FACE_DIFFUSE_WALL) {
+      ctx->err = "set_domain: kind must be IBDVM_FACE_FREESTREAM or IBDVM_FACE_DIFFUSE_WALL";
+      return IBDVM_E_INVAL;
+    }
+    if (kind != IBDVM_FACE_DIFFUSE_WALL) continue;
+    if (i >= 2 * D) {
+      ctx->err = "set_domain: a 2D grid has no z faces";
+      return IBDVM_E_INVAL;
+    }
+    if (!(d->T_w[i] > 0.0) || !std::isfinite(d->T_w[i]) || !std::isfinite(d->U_w[i][0]) ||
+        !std::isfinite(d->U_w[i][1]) || !std::isfinite(d->U_w[i][2])) {
+      ctx->err = "set_domain: a wall needs T_w > 0 and a finite U_w";
+      return IBDVM_E_INVAL;
+    }
+    mask |= 1 << i;
+  }
+  const Geom &G = ctx->geom;
+  long long off[7] = {};
+  for (int i = 0; i < 6; ++i) off[i + 1] = off[i] + ((i < 2 * D) ? ctx->ncell / G.n[i >> 1] : 0);
+  void *halo = nullptr;
+  if (mask) {
+    const size_t bytes = static_cast<size_t>(off[6]) * ctx->nvp * ctx->ncomp * ctx->esize;
+    if (cudaMalloc(&halo, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->err = "set_domain: device allocation of the wall halo (" + std::to_string(bytes) + " bytes) failed";
+      return IBDVM_E_NOMEM;
+    }
+    ctx->dev_bytes += bytes;
+  }
+  if (ctx->whalo) {
+    sync(ctx, "drain before replacing the wall halo");
+    cudaFree(ctx->whalo);
+    ctx->dev_bytes -= static_cast<size_t>(ctx->wall_off[6]) * ctx->nvp * ctx->ncomp * ctx->esize;
+  }
+  ctx->whalo = halo;
+  ctx->wall_mask = mask;
+  for (int i = 0; i < 7; ++i) ctx->wall_off[i] = mask ? off[i] : 0;
+  for (int i = 0; i < 6; ++i) {
+    ctx->wall_T[i] = (mask >> i & 1) ? d->T_w[i] : 1.0;
+    for (int a = 0; a < 3; ++a) ctx->wall_U[i][a] = (mask >> i & 1) ? d->U_w[i][a] : 0.0;
+  }
+  // walls are read by the plain sweep; the TMA sweeps see the freestream halo
+  ctx->use_tma = ctx->tma_ok && !mask;
+  drop_graphs(ctx);
+  return IBDVM_OK;
   IBDVM_END
 }
 

@@ -105,6 +105,15 @@ struct ibdvm_ctx {
   // (a batch rebuilds its tables when it changes)
   ibdvm_batch *batch = nullptr;
   unsigned body_gen = 0;
+  // diffuse domain walls: faces 2a + (s > 0) in wall_mask, their wall state,
+  // the first halo slot of each face (wall_off[6] = all slots) and the halo
+  // values [slots][nvp][ncomp] in the storage type
+  int wall_mask = 0;
+  double wall_T[6] = {1, 1, 1, 1, 1, 1};
+  double wall_U[6][3] = {};
+  long long wall_off[7] = {};
+  void *whalo = nullptr;
+  bool tma_ok = false; // the TMA sweep was set up (it serves cases without domain walls)
   // host uploads of the state in cell ranges (a copy stream, one event per range)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_ev[ibdvm::kUploadParts + 1] = {};

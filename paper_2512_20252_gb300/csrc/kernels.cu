@@ -100,6 +100,32 @@ template <> struct Acc<float> {
 // the sweep: transport, relaxation and moments
 // ---------------------------------------------------------------------------
 
+// The domain halo (two layers across every domain face, Sec. 2.2): the
+// freestream Maxwellian, or, across a diffuse domain wall, the values the wall
+// gives both layers (rho_w M_w for velocities entering the domain, the
+// boundary cell's own value for the others), one slot of nvp x NC values per
+// boundary cell, refreshed from f^n by domain_wall_kernel.
+template <typename T> struct HaloArgs {
+  const T *__restrict__ whalo; // [slots][nvp][NC]; null without diffuse walls
+  long long off[6];            // first slot of face 2a + (s > 0)
+  int mask;                    // bit 2a + (s > 0): that face is a diffuse wall
+};
+
+// slot offset of cell ijk within the slots of a face normal to axis a
+__device__ __forceinline__ long long face_slot(const int *n, const int *ijk, int a) {
+  return (a == 0) ? ijk[1] + (long long)n[1] * ijk[2]
+                  : (a == 1) ? ijk[0] + (long long)n[0] * ijk[2] : ijk[0] + (long long)n[0] * ijk[1];
+}
+
+// the halo value across face (a, s) of the boundary cell ijk, velocity k, component m
+template <typename T>
+__device__ __forceinline__ T halo_value(const HaloArgs<T> &H, const T *finf, const int *n, const int *ijk, int a,
+                                        int s, int nvp, int nc, int k, int m) {
+  const int i = 2 * a + (s > 0);
+  if (!((H.mask >> i) & 1)) return finf[(size_t)k * nc + m];
+  return H.whalo[((size_t)(H.off[i] + face_slot(n, ijk, a)) * nvp + k) * nc + m];
+}
+
 template <typename T> struct SweepArgs {
   const T *__restrict__ f;
   T *__restrict__ fn;
@@ -119,6 +145,7 @@ template <typename T> struct SweepArgs {
   T rdx[3];
   int update; // 1: step f -> fn and take the moments of fn; 0: moments of f
   int shift;  // 1: moments about the stored bulk velocity U^n; 0: about zero
+  HaloArgs<T> H;
 };
 
 template <typename T, int NC>
@@ -135,7 +162,8 @@ __device__ __forceinline__ void seen(const SweepArgs<T> &A, long long c, const i
                                      int s, int k, T *out) {
   int q = ijk[a] + s;
   if (q < 0 || q >= A.n[a]) {
-    load_nc<T, NC>(A.finf + (size_t)k * NC, out);
+#pragma unroll
+    for (int m = 0; m < NC; ++m) out[m] = halo_value(A.H, A.finf, A.n, ijk, a, s, A.nvp, NC, k, m);
     return;
   }
   long long stride = (a == 0) ? 1LL : (a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1]);
@@ -208,7 +236,9 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
           // upwind neighbour u = c - s e_a supplies the incoming face value
           const int qa = ijk[a] - s;
           if (qa < 0 || qa >= A.n[a]) {
-            load_nc<T, NC>(A.finf + (size_t)k * NC, fin); // halo: zero slope
+            // halo: both layers hold the same value, zero slope
+#pragma unroll
+            for (int m = 0; m < NC; ++m) fin[m] = halo_value(A.H, A.finf, A.n, ijk, a, -s, A.nvp, NC, k, m);
           } else {
             long long stride = (a == 0) ? 1LL : (a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1]);
             long long u = c - s * stride;
@@ -661,6 +691,8 @@ template <typename T> struct GhostArgs {
   double dx[3];
   double Tw, Uw[3], accom;
   int plain_average;
+  HaloArgs<T> H; // the domain halo the pre-ghost slopes see
+  int n[3];
 };
 
 template <int NT> __device__ __forceinline__ double block_sum(double v, double *sh) {
@@ -683,11 +715,21 @@ template <int NT> __device__ __forceinline__ double block_sum(double v, double *
 // halo neighbours, one-sided with one, zero with none
 template <typename T, int NC>
 __device__ __forceinline__ T preghost_slope(const GhostArgs<T> &G, int code_m, int code_p, T fj,
-                                            int k, int m, T rh) {
+                                            int k, int m, T rh, int jc, int a) {
   const bool hm = code_m != -2, hp = code_p != -2;
   T fm = T(0), fp = T(0);
-  if (hm) fm = (code_m >= 0) ? G.f[((size_t)code_m * G.nvp + k) * NC + m] : G.finf[(size_t)k * NC + m];
-  if (hp) fp = (code_p >= 0) ? G.f[((size_t)code_p * G.nvp + k) * NC + m] : G.finf[(size_t)k * NC + m];
+  int ijk[3] = {0, 0, 0};
+  if (code_m == -1 || code_p == -1) { // a domain halo neighbour
+    ijk[0] = jc % G.n[0];
+    ijk[1] = (jc / G.n[0]) % G.n[1];
+    ijk[2] = jc / (G.n[0] * G.n[1]);
+  }
+  if (hm)
+    fm = (code_m >= 0) ? G.f[((size_t)code_m * G.nvp + k) * NC + m]
+                       : halo_value(G.H, G.finf, G.n, ijk, a, -1, G.nvp, NC, k, m);
+  if (hp)
+    fp = (code_p >= 0) ? G.f[((size_t)code_p * G.nvp + k) * NC + m]
+                       : halo_value(G.H, G.finf, G.n, ijk, a, +1, G.nvp, NC, k, m);
   if (hm && hp) return vanleer((fj - fm) * rh, (fp - fj) * rh);
   if (hm) return (fj - fm) * rh;
   if (hp) return (fp - fj) * rh;
@@ -746,7 +788,7 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
         for (int a = 0; a < D; ++a) {
           const double r = sd[4 + a];
           if (r != 0.0) {
-            T sig = preghost_slope<T, NC>(G, si[1 + 2 * a], si[2 + 2 * a], fj, k, m, (T)(1.0 / G.dx[a]));
+            T sig = preghost_slope<T, NC>(G, si[1 + 2 * a], si[2 + 2 * a], fj, k, m, (T)(1.0 / G.dx[a]), jc, a);
             v -= sig * (T)r;
           }
         }
@@ -870,6 +912,88 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
 template <typename T, int D>
 __global__ void __launch_bounds__(kGhostThreads) ghost_band_kernel(GhostArgs<T> G) {
   ghost_band_body<T, D>(G, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// diffuse domain walls: the halo values of every boundary cell of a wall face
+// ---------------------------------------------------------------------------
+
+template <typename T> struct DomainArgs {
+  const T *__restrict__ f;
+  const uint8_t *__restrict__ ctype;
+  const double *__restrict__ xiD; // [3][nvp]
+  const double *__restrict__ wD;  // [nvp]
+  T *__restrict__ whalo;          // [slots][nvp][NC]
+  long long off[7];               // first slot of each face; off[6] = all slots
+  int mask;
+  int n[3];
+  int nv, nvp;
+  double Tw[6], Uw[6][3];
+};
+
+constexpr int kDomainThreads = 256;
+
+// One block per slot of a wall face: the boundary cell's mass flux out of the
+// domain through the face, carried by its own value (sum over s xi_a > 0), is
+// returned by rho_w times the face's unit-density wall Maxwellian (the plane
+// xi_a = 0 splits the velocities; FP64 sums); the halo then holds rho_w M_w
+// for the entering velocities and the cell's own value for the others.
+template <typename T, int D> __global__ void __launch_bounds__(kDomainThreads) domain_wall_kernel(DomainArgs<T> A) {
+  constexpr int NC = Dims<D>::NC;
+  __shared__ double sh[kDomainThreads / 32 + 1];
+  const long long slot = blockIdx.x;
+  int i = 0;
+  while (i < 5 && slot >= A.off[i + 1]) ++i;
+  if (!((A.mask >> i) & 1)) return; // a freestream face: no slots in use
+  const int a = i >> 1, s = (i & 1) ? 1 : -1;
+  const long long t = slot - A.off[i];
+  int ijk[3];
+  const int u = (a == 0) ? 1 : 0, v = (a == 2) ? 1 : 2; // the transverse axes, in order
+  ijk[a] = (s > 0) ? A.n[a] - 1 : 0;
+  ijk[u] = (int)(t % A.n[u]);
+  ijk[v] = (int)(t / A.n[u]);
+  const long long c = ijk[0] + (long long)A.n[0] * (ijk[1] + (long long)A.n[1] * ijk[2]);
+  T *dst = A.whalo + (size_t)slot * A.nvp * NC;
+  const T *fc = A.f + (size_t)c * A.nvp * NC;
+  if (A.ctype[c] != IBDVM_CELL_FLUID) { // never read: the cell has no faces of its own
+    for (int k = threadIdx.x; k < A.nvp * NC; k += blockDim.x) dst[k] = T(0);
+    return;
+  }
+  const double Tw = A.Tw[i];
+  const double norm = (D == 2) ? 1.0 / (kPi * Tw) : 1.0 / pow(kPi * Tw, 1.5);
+  double so = 0.0, si = 0.0;
+  for (int k = threadIdx.x; k < A.nv; k += blockDim.x) {
+    const double xs = s * A.xiD[a * A.nvp + k];
+    if (xs > 0.0) {
+      so += A.wD[k] * xs * (double)fc[(size_t)k * NC];
+    } else if (xs < 0.0) {
+      double c2 = 0.0;
+      for (int b = 0; b < D; ++b) {
+        const double cb = A.xiD[b * A.nvp + k] - A.Uw[i][b];
+        c2 += cb * cb;
+      }
+      si += A.wD[k] * xs * norm * exp(-c2 / Tw);
+    }
+  }
+  const double out = block_sum<kDomainThreads>(so, sh);
+  const double in = block_sum<kDomainThreads>(si, sh);
+  const double rho_w = -out / in;
+  for (int k = threadIdx.x; k < A.nvp; k += blockDim.x) {
+    const double xs = (k < A.nv) ? s * A.xiD[a * A.nvp + k] : 0.0;
+    if (xs < 0.0) {
+      double c2 = 0.0;
+      for (int b = 0; b < D; ++b) {
+        const double cb = A.xiD[b * A.nvp + k] - A.Uw[i][b];
+        c2 += cb * cb;
+      }
+      const double H = rho_w * norm * exp(-c2 / Tw);
+      dst[(size_t)k * NC] = (T)H;
+      if (NC == 2) dst[(size_t)k * NC + NC - 1] = (T)(0.5 * Tw * H); // B_w = T_w / 2 H_w
+    } else {
+#pragma unroll
+      for (int m = 0; m < NC; ++m) dst[(size_t)k * NC + m] = fc[(size_t)k * NC + m];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1151,6 +1275,15 @@ __global__ void convert_kernel(T *__restrict__ state, double *__restrict__ dense
 // launch helpers
 // ---------------------------------------------------------------------------
 
+// the domain halo of a context (the freestream, or its diffuse walls)
+template <typename T> HaloArgs<T> halo_args(const ibdvm_ctx *ctx) {
+  HaloArgs<T> H{};
+  H.whalo = static_cast<const T *>(ctx->whalo);
+  H.mask = ctx->wall_mask;
+  for (int i = 0; i < 6; ++i) H.off[i] = ctx->wall_off[i];
+  return H;
+}
+
 template <typename T> SweepArgs<T> sweep_args(const ibdvm_ctx *ctx, int update, int shift = 1, int cur = -1) {
   if (cur < 0) cur = ctx->cur;
   SweepArgs<T> A{};
@@ -1176,6 +1309,7 @@ template <typename T> SweepArgs<T> sweep_args(const ibdvm_ctx *ctx, int update, 
   A.dt = (T)ctx->geom.dt;
   A.update = update;
   A.shift = shift;
+  A.H = halo_args<T>(ctx);
   return A;
 }
 
@@ -1267,7 +1401,30 @@ template <typename T> GhostArgs<T> ghost_args(const ibdvm_ctx *ctx, int cur, dou
   G.Tw = g.body.T_w;
   G.accom = g.body.accom_alpha;
   G.plain_average = (g.gas.flags & IBDVM_PLAIN_AVERAGE) ? 1 : 0;
+  G.H = halo_args<T>(ctx);
+  for (int a = 0; a < 3; ++a) G.n[a] = g.n[a];
   return G;
+}
+
+template <typename T, int D> cudaError_t domain_t(ibdvm_ctx *ctx) {
+  const Geom &g = ctx->geom;
+  DomainArgs<T> A{};
+  A.f = static_cast<const T *>(ctx->f[ctx->cur]);
+  A.ctype = ctx->ctype;
+  A.xiD = ctx->xiD;
+  A.wD = ctx->wD;
+  A.whalo = static_cast<T *>(ctx->whalo);
+  for (int i = 0; i < 7; ++i) A.off[i] = ctx->wall_off[i];
+  A.mask = ctx->wall_mask;
+  for (int a = 0; a < 3; ++a) A.n[a] = g.n[a];
+  A.nv = ctx->nv;
+  A.nvp = ctx->nvp;
+  for (int i = 0; i < 6; ++i) {
+    A.Tw[i] = ctx->wall_T[i];
+    for (int a = 0; a < 3; ++a) A.Uw[i][a] = ctx->wall_U[i][a];
+  }
+  domain_wall_kernel<T, D><<<(unsigned)ctx->wall_off[6], kDomainThreads, 0, ctx->stream>>>(A);
+  return cudaGetLastError();
 }
 
 template <typename T, int D> cudaError_t ghost_t(ibdvm_ctx *ctx, double *dbg) {
@@ -1414,12 +1571,18 @@ cudaError_t launch_interleave(ibdvm_ctx *ctx, double *Wo, double *qo) {
 }
 
 cudaError_t launch_ghost_band(ibdvm_ctx *ctx, double *dbg) {
-  if (ctx->nlink == 0) return cudaSuccess;
+  if (ctx->nlink == 0 && ctx->wall_mask == 0) return cudaSuccess;
   Timed t(ctx, kKGhost);
-  ctx->kernel_launches[kKGhost] += 1;
+  // the halo values of diffuse domain walls first: the pre-ghost slopes and
+  // the sweep read them
+  ctx->kernel_launches[kKGhost] += (ctx->wall_mask ? 1 : 0) + (ctx->nlink ? 1 : 0);
   return dispatch(ctx, [&](auto t, auto d) -> cudaError_t {
     using T = decltype(t);
     constexpr int D = decltype(d)::value;
+    if (ctx->wall_mask) {
+      cudaError_t e = domain_t<T, D>(ctx);
+      if (e != cudaSuccess) return e;
+    }
     return ghost_t<T, D>(ctx, dbg);
   });
 }

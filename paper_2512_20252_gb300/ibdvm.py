@@ -7,8 +7,9 @@ PyTorch fallback.
 Case descriptions are plain dicts (see ``workloads``): dim, n, lo, hi, nv, vlo,
 vhi, rule, Kn, Ma, Pr, gamma, omega_vhs, alpha_vhs, rho_inf, T_inf, dir, cfl,
 dt, precision ("fp64" | "mixed"), cutcell, upwind (1 upwind weights, 2 the
-reverse unit vector, 0 plain average) and body = {kind, center, radii, angle,
-verts, accom, Tw, Uw, Lref}.
+reverse unit vector, 0 plain average), body = {kind, center, radii, angle,
+verts, accom, Tw, Uw, Lref} and domain_walls (six entries for the faces x-,
+x+, y-, y+, z-, z+: None for a freestream face, {Tw, Uw} for a diffuse wall).
 """
 from __future__ import annotations
 
@@ -61,6 +62,23 @@ class BodyDesc(ctypes.Structure):
                 ("U_w", ctypes.c_double * 3), ("L_ref", ctypes.c_double)]
 
 
+class DomainDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int * 6), ("T_w", ctypes.c_double * 6), ("U_w", (ctypes.c_double * 3) * 6)]
+
+
+def domain_descriptor(walls) -> DomainDesc:
+    """The faces x-, x+, y-, y+, z-, z+: None = freestream, {Tw, Uw} = diffuse wall."""
+    d = DomainDesc()
+    for i, wall in enumerate(walls or []):
+        d.T_w[i] = 1.0
+        if wall:
+            d.kind[i] = 1
+            d.T_w[i] = float(wall.get("Tw", 1.0))
+            u = list(wall.get("Uw", [0.0, 0.0, 0.0])) + [0.0] * 3
+            d.U_w[i][:] = [float(x) for x in u[:3]]
+    return d
+
+
 class ServerDesc(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_steps", ctypes.c_longlong), ("steps_per_round", ctypes.c_int),
                 ("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int), ("sequential_fp64", ctypes.c_int)]
@@ -111,6 +129,7 @@ SIGNATURES = {
     "ibdvm_set_f_native": ([_V, _V, ctypes.c_size_t], _S),
     "ibdvm_ghost_band": ([_V, _D, _D, _D, _D], _S),
     "ibdvm_wall": ([_V, _D], _S),
+    "ibdvm_set_domain": ([_V, _V], _S),
     "ibdvm_residual_noalloc": ([_V, _V, _V, ctypes.c_longlong, ctypes.c_int, _V, _V], _S),
     "ibdvm_get_info": ([_V, ctypes.POINTER(Info)], _S),
     "ibdvm_selftest_bounded_wait": ([ctypes.c_int, ctypes.c_int, _D, _V], _S),
@@ -354,8 +373,17 @@ class Solver:
         body = case.get("body") or {"kind": "none"}
         if body["kind"] != "none":
             self._check(self.lib.ibdvm_set_body(self.h, ctypes.byref(b)))
+        if any(case.get("domain_walls") or []):
+            self.set_domain(case["domain_walls"])
         self._keep = keep
         self.refresh_info()
+
+    def set_domain(self, walls):
+        """Domain faces x-, x+, y-, y+, z-, z+: None = freestream halo,
+        {"Tw": T, "Uw": [u, v, w]} = diffuse wall (ibdvm_set_domain)."""
+        d = domain_descriptor(walls)
+        self._check(self.lib.ibdvm_set_domain(self.h, ctypes.byref(d)))
+        self.case["domain_walls"] = list(walls)
 
     def _check(self, st):
         if st != OK:

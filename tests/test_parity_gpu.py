@@ -4,6 +4,8 @@ Tolerances: the FP64 path must match the oracle within 1e-11 relative on f and
 W (max |difference| over fluid cells divided by the largest |value|); the
 mixed path (FP32 storage and transport) within 1e-5 on W and 1e-4 on C_D.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -314,6 +316,105 @@ def test_wall_quantities_without_a_body_or_a_free_stream():
     np.testing.assert_allclose(wq[:, WALL["p"]], 0.5, rtol=1e-7)
     assert np.abs(wq[:, WALL["slip_x"]:WALL["slip_z"] + 1]).max() < 1e-12
     g.close()
+
+
+# ---------------------------------------------------------------------------
+# diffuse domain walls (the lid-driven cavity of Sec. 4.1; reading C24)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("mixed", 1e-5)])
+def test_cavity_against_the_oracle(precision, tol):
+    """Lid-driven cavity with the cylinder at its centre: walls on all four
+    faces, the lid moving, against the oracle."""
+    case = wl.cavity(n=24, nv=16, precision=precision)
+    g, o, rg, ro = pair(case, 12)
+    if precision == "fp64":
+        compare(g, o, tol=tol, wtol=tol, forces=False)  # no free stream: no C_D
+    else:
+        # W against its scale: the momentum of a flow the lid drives is of
+        # order rho_0 U_w = 0.15 (after 12 steps it is still much smaller)
+        fl = o.cell_types() == oracle.FLUID
+        assert rel_err(g.get_f()[fl], o.get_f()[fl]) < tol
+        Wg, _, _ = g.moments()
+        Wo, _ = o.moments()
+        for i in range(4):
+            scale = max(np.abs(Wo[fl, i]).max(), 0.15)
+            assert np.abs(Wg[fl, i] - Wo[fl, i]).max() < tol * scale, i
+    _compare_force_and_heat(g, o, tol)
+    assert rg == pytest.approx(ro, rel=1e-9 if precision == "fp64" else 1e-3)
+    assert g.info.sweep_variant == 0  # the generic sweep serves cases with walls
+
+
+def _compare_force_and_heat(g, o, tol, scale=0.1):
+    """Force and heat flux on the body, relative to their largest value and at
+    least to scale (about p L: before the lid's disturbance reaches the body
+    both are rounding noise)."""
+    Fg, Qg, _, _ = g.forces()
+    Fo, Qo, _, _ = o.forces()
+    assert np.abs(Fg - Fo).max() < 10 * tol * max(np.abs(Fo).max(), scale), (Fg, Fo)
+    assert abs(Qg - Qo) < 10 * tol * max(abs(Qo), scale), (Qg, Qo)
+
+
+def test_box_with_walls_3d_against_the_oracle():
+    case = wl._case(3, 10, ([0.0] * 3, [1.0] * 3), 8, 4.5, 0.1, 0.0, wl.sphere(0.2, center=(0.5, 0.5, 0.5)),
+                    domain_walls=wl.box_walls(3, 1.0, lid=(0.2, 0.0)))
+    g, o, _, _ = pair(case, 6)
+    compare(g, o, forces=False)
+    _compare_force_and_heat(g, o, TOL)
+
+
+def test_closed_box_keeps_its_mass():
+    """No mass crosses a diffuse wall: a collisionless closed box with a moving
+    lid and walls at two temperatures keeps its mass to rounding."""
+    case = wl._case(2, 32, ([0.0, 0.0], [1.0, 1.0]), 16, 5.0, 1e12, 0.0, {"kind": "none"},
+                    domain_walls=wl.box_walls(2, 0.8, lid=(0.3, 0.0), lid_T=1.3))
+    g = ibdvm.Solver(case)
+    W0, _, _ = g.moments()
+    g.step(40)
+    W1, _, _ = g.moments()
+    assert abs(W1[:, 0].sum() - W0[:, 0].sum()) < 1e-13 * W0[:, 0].sum()
+    assert np.abs(W1[:, 1]).max() > 1e-3
+    g.close()
+
+
+def test_domain_descriptor_errors_and_batches():
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    case = wl.small_2d("circle", n=16, nv=8, precision="mixed")
+    g = ibdvm.Solver(case, stream=stream.cuda_stream)
+    assert g.info.sweep_variant != 0
+    for bad in ([{"Tw": 0.0}] + [None] * 5,                       # T_w <= 0
+                [None] * 4 + [{"Tw": 1.0}, None],                 # a z wall in 2D
+                [{"Tw": 1.0, "Uw": [float("nan"), 0.0, 0.0]}] + [None] * 5):
+        with pytest.raises(ibdvm.IbdvmError) as e:
+            g.set_domain(bad)
+        assert e.value.status == 1
+    d = ibdvm.domain_descriptor([None] * 6)
+    d.kind[0] = 7
+    assert g.lib.ibdvm_set_domain(g.h, ctypes.byref(d)) == 1
+    # walls: the generic sweep, and no batch membership
+    g.set_domain(wl.box_walls(2, 1.0, lid=(0.1, 0.0)))
+    g.refresh_info()
+    assert g.info.sweep_variant == 0
+    b = ibdvm.Batch(stream=stream.cuda_stream)
+    with pytest.raises(ibdvm.IbdvmError):
+        b.add(g)
+    # no walls again: the TMA sweep, bit-identical to a case that never had walls
+    g.set_domain([None] * 6)
+    g.refresh_info()
+    assert g.info.sweep_variant != 0
+    twin = ibdvm.Solver(case, stream=stream.cuda_stream)
+    twin.set_f(g.get_f())
+    g.step(5)
+    twin.step(5)
+    np.testing.assert_array_equal(g.get_f(), twin.get_f())
+    b.add(g)
+    with pytest.raises(ibdvm.IbdvmError) as e:
+        g.set_domain(wl.box_walls(2, 1.0))
+    assert e.value.status == 8
+    b.close()
+    g.close()
+    twin.close()
 
 
 def test_runs_on_a_torch_stream():
