@@ -363,7 +363,7 @@ ibdvm_status ibdvm_batch_add(ibdvm_batch *b, ibdvm_ctx *ctx) {
     b->err = "the context is already a member of a batch";
     return IBDVM_E_STATE;
   }
-  if (!ctx->use_tma || !tma_batch_member_ok(ctx)) {
+  if (!ctx->use_tma || !tma_batch_member_ok(ctx) || ctx->wall_mask) {
     b->err = "batch members are contexts in FP32 storage with the TMA sweep (no diffuse domain walls)";
     return IBDVM_E_INVAL;
   }

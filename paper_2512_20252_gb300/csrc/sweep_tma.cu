@@ -78,6 +78,11 @@ struct TmaArgs {
   long long ncell;
   int nx, ny, nvp, nv, rows;
   float dt, rdx, rdy;
+  // diffuse domain walls: faces 2a + (s > 0) in wmask, the halo values of
+  // their boundary cells [slot][nvp][2] from the first slot woff[face]
+  const float *__restrict__ whalo;
+  long long woff[4];
+  int wmask;
 };
 
 // ---------------------------------------------------------------------------
@@ -145,6 +150,21 @@ template <int KPT> __device__ __forceinline__ float2 sm2(const float *base, int 
   return *reinterpret_cast<const float2 *>(base + 2 * kk);
 }
 
+// the values of the halo cells across face i = 2a + (s > 0) of the boundary
+// cell at transverse index t (the row for x faces, the column for y faces),
+// from the chunk's first velocity: the slot a diffuse wall wrote this step,
+// or the freestream (both halo layers hold the same values)
+// (W: the case has diffuse domain walls; without, the code is that of the
+// freestream halo alone)
+template <int KPT, bool W> __device__ __forceinline__ const float *halo_ptr(const March<KPT> &M, int i, int t) {
+  if constexpr (!W) {
+    return M.sfinf;
+  } else {
+    if (!((M.A.wmask >> i) & 1)) return M.sfinf;
+    return M.A.whalo + ((size_t)(M.A.woff[i] + t) * M.A.nvp + M.k0) * 2;
+  }
+}
+
 template <int KPT> __device__ __forceinline__ void issue_row(March<KPT> &M, int r, int st) {
   using C = Cfg<KPT>;
   mbar_expect_tx(&M.full[st], C::STAGE_BYTES);
@@ -158,16 +178,17 @@ template <int KPT> __device__ __forceinline__ uint8_t cmask_of(const March<KPT> 
 
 // downwind x face of column cx at row y for chunk velocity kk, with the
 // domain edge, ghost neighbours and cells that are not fluid
-template <int KPT>
+template <int KPT, bool W>
 __device__ __forceinline__ float2 phi_x_one(const March<KPT> &M, const float *srow, int cx, int scol, int y,
                                             uint8_t m, int kk, float xi) {
   using C = Cfg<KPT>;
-  if (cx < 0 || cx >= M.A.nx) return sm2<KPT>(M.sfinf, kk); // halo column: freestream, zero slope
+  // halo column: its value, zero slope
+  if (cx < 0 || cx >= M.A.nx) return sm2<KPT>(halo_ptr<KPT, W>(M, cx < 0 ? 0 : 1, y), kk);
   if (m & kNotFluid) return make_float2(0.f, 0.f);
   const float *pc = srow + scol * C::KC2;
   const float2 f = sm2<KPT>(pc, kk);
-  float2 lo = (cx - 1 < 0) ? sm2<KPT>(M.sfinf, kk) : sm2<KPT>(pc - C::KC2, kk);
-  float2 hi = (cx + 1 >= M.A.nx) ? sm2<KPT>(M.sfinf, kk) : sm2<KPT>(pc + C::KC2, kk);
+  float2 lo = (cx - 1 < 0) ? sm2<KPT>(halo_ptr<KPT, W>(M, 0, y), kk) : sm2<KPT>(pc - C::KC2, kk);
+  float2 hi = (cx + 1 >= M.A.nx) ? sm2<KPT>(halo_ptr<KPT, W>(M, 1, y), kk) : sm2<KPT>(pc + C::KC2, kk);
   if (m & (kXm | kXp)) {
     const long long c = cx + (long long)M.A.nx * y;
     if (m & kXm) lo = link_value(M.A, c, 0, M.k0 + kk);
@@ -177,12 +198,13 @@ __device__ __forceinline__ float2 phi_x_one(const March<KPT> &M, const float *sr
 }
 
 // downwind y face of row r, cell (x, r): fr = f(r), lo = f(r-1), hi = f(r+1)
-template <int KPT>
+template <int KPT, bool W>
 __device__ __forceinline__ void phi_y(const March<KPT> &M, int r, uint8_t m, const Ring<KPT> &fr,
                                       const Ring<KPT> &lo, const Ring<KPT> &hi, Ring<KPT> &out) {
-  if (r < 0 || r >= M.A.ny || !M.col_in) { // halo row: freestream, zero slope
+  if (r < 0 || r >= M.A.ny || !M.col_in) { // halo row: its value, zero slope
+    const float *h = M.col_in ? halo_ptr<KPT, W>(M, r < 0 ? 2 : 3, M.x) : M.sfinf;
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) out[q] = sm2<KPT>(M.sfinf, klo(M, q));
+    for (int q = 0; q < KPT; ++q) out[q] = sm2<KPT>(h, klo(M, q));
     return;
   }
   if (m & kNotFluid) {
@@ -190,16 +212,20 @@ __device__ __forceinline__ void phi_y(const March<KPT> &M, int r, uint8_t m, con
     for (int q = 0; q < KPT; ++q) out[q] = make_float2(0.f, 0.f);
     return;
   }
-  if (!(m & (kYm | kYp))) { // fast path
+  // the last row under a top wall: the ring holds the freestream past the
+  // edge; the wall's halo slot holds the value across it
+  const bool top = W && (r == M.A.ny - 1) && (M.A.wmask & 8);
+  if (!(m & (kYm | kYp)) && !top) { // fast path
 #pragma unroll
     for (int q = 0; q < KPT; ++q) out[q] = face2(fr[q], lo[q], hi[q], dup(M.sy[q]));
     return;
   }
   const long long c = M.x + (long long)M.A.nx * r;
+  const float *th = top ? halo_ptr<KPT, W>(M, 3, M.x) : M.sfinf;
 #pragma unroll
   for (int q = 0; q < KPT; ++q) {
     const float2 l = (m & kYm) ? link_value(M.A, c, 2, kof(M, q)) : lo[q];
-    const float2 h = (m & kYp) ? link_value(M.A, c, 3, kof(M, q)) : hi[q];
+    const float2 h = (m & kYp) ? link_value(M.A, c, 3, kof(M, q)) : (top ? sm2<KPT>(th, klo(M, q)) : hi[q]);
     out[q] = face2(fr[q], l, h, dup(M.sy[q]));
   }
 }
@@ -207,7 +233,7 @@ __device__ __forceinline__ void phi_y(const March<KPT> &M, int r, uint8_t m, con
 // One row y of the march.  Ring arguments: Ra = f(y), Rb = f(y+1), Rc <- f(y+2);
 // Pa = phi(y-1), Pb = phi(y), Pc <- phi(y+1); mc = flags of (x, y), carried to
 // the next row as the flags of (x, y+1).  Returns false when the block aborts.
-template <int KPT>
+template <int KPT, bool W>
 __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, Ring<KPT> &Ra, Ring<KPT> &Rb,
                                     Ring<KPT> &Rc, Ring<KPT> &Pa, Ring<KPT> &Pb, Ring<KPT> &Pc) {
   using C = Cfg<KPT>;
@@ -232,6 +258,7 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
   if (y + 2 < A.ny && !mbar_wait(&M.full[st2], pb2)) M.abort_local = true;
   {
     // the own column of row y + 2, or the freestream past the domain edge
+    // (where the top face is a wall, phi_y reads its halo for the last row)
     const float *src = (y + 2 < A.ny && M.col_in) ? M.stage + st2 * C::STAGE_FLOATS + (M.warp + 2) * C::KC2
                                                   : M.sfinf;
 #pragma unroll
@@ -250,7 +277,7 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
   } else {
 #pragma unroll
     for (int q = 0; q < KPT; ++q)
-      PX[q] = phi_x_one(M, srow, M.x, M.warp + 2, y, M.col_in ? m0 : 0, klo(M, q), M.xix[q]);
+      PX[q] = phi_x_one<KPT, W>(M, srow, M.x, M.warp + 2, y, M.col_in ? m0 : 0, klo(M, q), M.xix[q]);
   }
 #pragma unroll
   for (int q = 0; q < KPT; ++q) *reinterpret_cast<float2 *>(ph + (M.warp + 1) * C::KC2 + 2 * klo(M, q)) = PX[q];
@@ -266,12 +293,12 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
       const float *pc = srow + M.h_scol * C::KC2;
       o = face2(sm2<KPT>(pc, M.h_kk), sm2<KPT>(pc - C::KC2, M.h_kk), sm2<KPT>(pc + C::KC2, M.h_kk), M.h_s2);
     } else {
-      o = phi_x_one(M, srow, M.h_col, M.h_scol, y, hm, M.h_kk, M.sxi[M.h_kk]);
+      o = phi_x_one<KPT, W>(M, srow, M.h_col, M.h_scol, y, hm, M.h_kk, M.sxi[M.h_kk]);
     }
     *reinterpret_cast<float2 *>(ph + M.h_out) = o;
   }
   // (3) downwind y face of row y + 1
-  phi_y(M, y + 1, mn, Rb, Ra, Rc, Pc);
+  phi_y<KPT, W>(M, y + 1, mn, Rb, Ra, Rc, Pc);
   // (4) barrier: x faces published, the stage of row y - 1 released; all
   //     threads agree on an abort
   if (__syncthreads_or(M.abort_local ? 1 : 0)) return false;
@@ -391,7 +418,7 @@ __device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, 
 // [k0, k0 + KC) and rows [y0, y1).  reinit: the block's mbarriers hold an
 // earlier march (all of whose copies have landed) and are invalidated first.
 // Returns false when the block aborted on a timed-out wait.
-template <int KPT>
+template <int KPT, bool W>
 __device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf, int x0, int k0, int y0, int y1,
                                         unsigned char *smem_raw, bool reinit) {
   using C = Cfg<KPT>;
@@ -467,8 +494,9 @@ __device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf
   // own-column ring for rows y0-2 .. y0+1, straight from global memory
   auto own = [&](int r, Ring<KPT> &v) {
     if (r < 0 || r >= A.ny || !M.col_in) {
+      const float *h = M.col_in ? halo_ptr<KPT, W>(M, r < 0 ? 2 : 3, M.x) : M.sfinf;
 #pragma unroll
-      for (int q = 0; q < KPT; ++q) v[q] = sm2<KPT>(M.sfinf, klo(M, q));
+      for (int q = 0; q < KPT; ++q) v[q] = sm2<KPT>(h, klo(M, q));
     } else {
       const float *src = A.f + ((size_t)(M.x + (long long)A.nx * r) * A.nvp + M.k0) * 2;
 #pragma unroll
@@ -482,8 +510,8 @@ __device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf
     own(M.y0 - 1, R2);
     own(M.y0, R0);
     own(M.y0 + 1, R1);
-    phi_y(M, M.y0 - 1, M.col_in ? cmask_of(M, M.x, M.y0 - 1) : kNotFluid, R2, Rm2, R0, P0);
-    phi_y(M, M.y0, M.col_in ? cmask_of(M, M.x, M.y0) : kNotFluid, R0, R2, R1, P1);
+    phi_y<KPT, W>(M, M.y0 - 1, M.col_in ? cmask_of(M, M.x, M.y0 - 1) : kNotFluid, R2, Rm2, R0, P0);
+    phi_y<KPT, W>(M, M.y0, M.col_in ? cmask_of(M, M.x, M.y0) : kNotFluid, R0, R2, R1, P1);
   }
   // rows y0 and y0+1 are read from shared memory by the x stencil
   for (int r = M.y0; r < min(M.ylast, M.y0 + 2); ++r)
@@ -493,7 +521,7 @@ __device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf
   int par = 0;
   bool ok = true;
   for (; y < M.y1; ++y) {
-    ok = row(M, y, par, mc, R0, R1, R2, P0, P1, P2);
+    ok = row<KPT, W>(M, y, par, mc, R0, R1, R2, P0, P1, P2);
     if (!ok) break;
 #pragma unroll
     for (int q = 0; q < KPT; ++q) {
@@ -517,12 +545,12 @@ __device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf
   return ok;
 }
 
-template <int KPT>
+template <int KPT, bool W>
 __global__ void __launch_bounds__(NTHREADS, 2) sweep2d_tma_kernel(const __grid_constant__ CUtensorMap tmf,
                                                                   TmaArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int y0 = blockIdx.z * A.rows;
-  march2d<KPT>(A, &tmf, blockIdx.x * TX, blockIdx.y * Cfg<KPT>::KC, y0, min(A.ny, y0 + A.rows), smem_raw, false);
+  march2d<KPT, W>(A, &tmf, blockIdx.x * TX, blockIdx.y * Cfg<KPT>::KC, y0, min(A.ny, y0 + A.rows), smem_raw, false);
 }
 
 // One item of the batched sweep: a march of one member case.
@@ -557,12 +585,12 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const CUtensorMap *tm = tmaps + 2 * it.cas + par;
     bool ok;
     if constexpr (KSEL == 4)
-      ok = march2d<4>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
+      ok = march2d<4, false>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
     else if constexpr (KSEL == 2)
-      ok = march2d<2>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
+      ok = march2d<2, false>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
     else
-      ok = (it.kpt == 4) ? march2d<4>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit)
-                         : march2d<2>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
+      ok = (it.kpt == 4) ? march2d<4, false>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit)
+                         : march2d<2, false>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
     if (!ok) break; // uniform: the abort vote is block-wide
     reinit = true;
     __syncthreads(); // the item's shared memory and arguments are released
@@ -609,9 +637,12 @@ cudaError_t tma_sweep_prepare(ibdvm_ctx *ctx) {
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
-  if (kpt == 4)
-    return cudaFuncSetAttribute(sweep2d_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<4>::SMEM);
-  return cudaFuncSetAttribute(sweep2d_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<2>::SMEM);
+  const int s4 = (int)Cfg<4>::SMEM, s2 = (int)Cfg<2>::SMEM;
+  cudaError_t e = (kpt == 4) ? cudaFuncSetAttribute(sweep2d_tma_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4)
+                             : cudaFuncSetAttribute(sweep2d_tma_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
+  if (e != cudaSuccess) return e;
+  return (kpt == 4) ? cudaFuncSetAttribute(sweep2d_tma_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4)
+                    : cudaFuncSetAttribute(sweep2d_tma_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
 }
 
 cudaError_t tma_sweep_launch(ibdvm_ctx *ctx) {
@@ -636,6 +667,9 @@ cudaError_t tma_sweep_launch(ibdvm_ctx *ctx) {
   A.dt = (float)ctx->geom.dt;
   A.rdx = (float)(1.0 / ctx->geom.dx[0]);
   A.rdy = (float)(1.0 / ctx->geom.dx[1]);
+  A.whalo = static_cast<const float *>(ctx->whalo);
+  A.wmask = ctx->wall_mask;
+  for (int i = 0; i < 4; ++i) A.woff[i] = ctx->wall_off[i];
   const int kpt = tma_sweep_kpt(ctx);
   const int nstrip = (A.nx + TX - 1) / TX;
   const int nchunk = ctx->nvp / (32 * kpt);
@@ -647,10 +681,17 @@ cudaError_t tma_sweep_launch(ibdvm_ctx *ctx) {
   A.rows = (A.ny + nrb - 1) / nrb;
   dim3 grid(nstrip, nchunk, (A.ny + A.rows - 1) / A.rows);
   const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(ctx->tmap[ctx->cur]);
-  if (kpt == 4)
-    sweep2d_tma_kernel<4><<<grid, NTHREADS, Cfg<4>::SMEM, ctx->stream>>>(*tm, A);
-  else
-    sweep2d_tma_kernel<2><<<grid, NTHREADS, Cfg<2>::SMEM, ctx->stream>>>(*tm, A);
+  // cases with diffuse domain walls read their halo at the domain edges
+  if (A.wmask) {
+    if (kpt == 4)
+      sweep2d_tma_kernel<4, true><<<grid, NTHREADS, Cfg<4>::SMEM, ctx->stream>>>(*tm, A);
+    else
+      sweep2d_tma_kernel<2, true><<<grid, NTHREADS, Cfg<2>::SMEM, ctx->stream>>>(*tm, A);
+  } else if (kpt == 4) {
+    sweep2d_tma_kernel<4, false><<<grid, NTHREADS, Cfg<4>::SMEM, ctx->stream>>>(*tm, A);
+  } else {
+    sweep2d_tma_kernel<2, false><<<grid, NTHREADS, Cfg<2>::SMEM, ctx->stream>>>(*tm, A);
+  }
   return cudaGetLastError();
 }
 

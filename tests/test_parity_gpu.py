@@ -341,8 +341,11 @@ def test_cavity_against_the_oracle(precision, tol):
             scale = max(np.abs(Wo[fl, i]).max(), 0.15)
             assert np.abs(Wg[fl, i] - Wo[fl, i]).max() < tol * scale, i
     _compare_force_and_heat(g, o, tol)
-    assert rg == pytest.approx(ro, rel=1e-9 if precision == "fp64" else 1e-3)
-    assert g.info.sweep_variant == 0  # the generic sweep serves cases with walls
+    # the residual is the change of W over one step, early in the cavity about
+    # 1e-4 of W, so the FP32 rounding of both states shows at the 1e-3 level
+    assert rg == pytest.approx(ro, rel=1e-9 if precision == "fp64" else 3e-3)
+    # the 2D TMA sweep reads the wall halo; FP64 runs the generic sweep
+    assert g.info.sweep_variant == (1 if precision == "mixed" else 0)
 
 
 def _compare_force_and_heat(g, o, tol, scale=0.1):
@@ -355,12 +358,25 @@ def _compare_force_and_heat(g, o, tol, scale=0.1):
     assert abs(Qg - Qo) < 10 * tol * max(abs(Qo), scale), (Qg, Qo)
 
 
-def test_box_with_walls_3d_against_the_oracle():
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("mixed", 1e-5)])
+def test_box_with_walls_3d_against_the_oracle(precision, tol):
+    """3D: walls on all six faces, the top one moving (the 3D TMA sweep keeps
+    the freestream halo, so the mixed case runs the generic sweep)."""
     case = wl._case(3, 10, ([0.0] * 3, [1.0] * 3), 8, 4.5, 0.1, 0.0, wl.sphere(0.2, center=(0.5, 0.5, 0.5)),
-                    domain_walls=wl.box_walls(3, 1.0, lid=(0.2, 0.0)))
+                    domain_walls=wl.box_walls(3, 1.0, lid=(0.2, 0.0)), precision=precision)
     g, o, _, _ = pair(case, 6)
-    compare(g, o, forces=False)
-    _compare_force_and_heat(g, o, TOL)
+    if precision == "fp64":
+        compare(g, o, forces=False)
+    else:
+        fl = o.cell_types() == oracle.FLUID
+        assert rel_err(g.get_f()[fl], o.get_f()[fl]) < tol
+        Wg, _, _ = g.moments()
+        Wo, _ = o.moments()
+        for i in range(5):
+            scale = max(np.abs(Wo[fl, i]).max(), 0.2)
+            assert np.abs(Wg[fl, i] - Wo[fl, i]).max() < tol * scale, i
+    _compare_force_and_heat(g, o, tol)
+    assert g.info.sweep_variant == 0
 
 
 def test_closed_box_keeps_its_mass():
@@ -392,17 +408,17 @@ def test_domain_descriptor_errors_and_batches():
     d = ibdvm.domain_descriptor([None] * 6)
     d.kind[0] = 7
     assert g.lib.ibdvm_set_domain(g.h, ctypes.byref(d)) == 1
-    # walls: the generic sweep, and no batch membership
+    # walls: the 2D TMA sweep reads their halo; no batch membership
     g.set_domain(wl.box_walls(2, 1.0, lid=(0.1, 0.0)))
     g.refresh_info()
-    assert g.info.sweep_variant == 0
+    assert g.info.sweep_variant == 1
     b = ibdvm.Batch(stream=stream.cuda_stream)
     with pytest.raises(ibdvm.IbdvmError):
         b.add(g)
-    # no walls again: the TMA sweep, bit-identical to a case that never had walls
+    # no walls again: bit-identical to a case that never had walls
     g.set_domain([None] * 6)
     g.refresh_info()
-    assert g.info.sweep_variant != 0
+    assert g.info.sweep_variant == 1
     twin = ibdvm.Solver(case, stream=stream.cuda_stream)
     twin.set_f(g.get_f())
     g.step(5)
