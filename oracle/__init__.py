@@ -87,6 +87,7 @@ class _Params(ctypes.Structure):
         ("wall", ctypes.c_int * 6),
         ("wall_T", ctypes.c_double * 6),
         ("wall_U", (ctypes.c_double * 3) * 6),
+        ("vnodes", ctypes.POINTER(ctypes.c_double) * 3),
     ]
 
 
@@ -158,7 +159,7 @@ def _params(cfg: dict) -> tuple[_Params, object]:
     p.nv[:] = [int(x) for x in _arr3(cfg["nv"], 1)]
     p.vlo[:] = _arr3(cfg["vlo"])
     p.vhi[:] = _arr3(cfg["vhi"], 1.0)
-    p.rule = {"trapezoid": 0, "midpoint": 1}[cfg.get("rule", "trapezoid")]
+    p.rule = {"trapezoid": 0, "midpoint": 1, "nodes": 2}[cfg.get("rule", "trapezoid")]
     p.Kn = cfg["Kn"]
     p.Ma = cfg["Ma"]
     p.Pr = cfg.get("Pr", 2.0 / 3.0)
@@ -175,11 +176,21 @@ def _params(cfg: dict) -> tuple[_Params, object]:
     p.center[:] = _arr3(body.get("center", [0.0, 0.0, 0.0]))
     p.radii[:] = _arr3(body.get("radii", [0.0, 0.0, 0.0]))
     p.angle = body.get("angle", 0.0)
-    keep = None
+    keep = []
     if body["kind"] == "polygon":
-        keep = np.ascontiguousarray(np.asarray(body["verts"], dtype=np.float64).reshape(-1))
-        p.verts = _dp(keep)
-        p.nverts = keep.size // 2
+        verts = np.ascontiguousarray(np.asarray(body["verts"], dtype=np.float64).reshape(-1))
+        keep.append(verts)
+        p.verts = _dp(verts)
+        p.nverts = verts.size // 2
+    if p.rule == 2:
+        # explicit velocity nodes per axis (C25): nv and the interval follow them
+        for a in range(dim):
+            nodes = np.ascontiguousarray(np.asarray(cfg["vnodes"][a], dtype=np.float64))
+            keep.append(nodes)
+            p.vnodes[a] = _dp(nodes)
+            p.nv[a] = nodes.size
+            p.vlo[a] = float(nodes[0])
+            p.vhi[a] = float(nodes[-1])
     p.accom = body.get("accom", 1.0)
     p.Tw = body.get("Tw", 1.0)
     p.Uw[:] = _arr3(body.get("Uw", [0.0, 0.0, 0.0]))

@@ -51,6 +51,12 @@
  *   C18 residual components whose sum of |W| is zero are skipped.
  *   C19 surface force and heat flux: momentum and energy carried through the
  *       donor-ghost faces by the face fluxes the update applies.
+ *   C25 a non-uniform velocity grid is the tensor product of per-axis node
+ *       lists (a stretched Cartesian grid, standing in for the locally
+ *       refined mesh of Sec. 4.4): the interval of an axis is [x_0, x_n-1],
+ *       each node owns the box between the midpoints to its neighbours (the
+ *       trapezoid rule on non-uniform nodes), and the specular interpolation
+ *       (C13) brackets a velocity by bisection on each axis.
  *   C24 a domain face may instead be a diffuse wall (Sec. 2.3 with alpha = 1
  *       on the plane of the face, normal into the domain): its two halo
  *       layers hold, for velocities entering the domain through the face,
@@ -296,11 +302,19 @@ void or_cell_moments(const or_case *C, const double *fc, double *out)
    integer m, so that a grid symmetric about zero is exactly antisymmetric in
    floating point (xi_{n-1-i} = -xi_i); the upwind-weight fallback and the
    incident/reflected split are decided by exact zeros that need this. */
-static void axis_nodes(int n, double lo, double hi, int rule, double *x, double *w, double *bl,
-                       double *bh)
+static void axis_nodes(int n, double lo, double hi, int rule, const double *given, double *x, double *w,
+                       double *bl, double *bh)
 {
   double c = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
-  if (rule == 0) {
+  if (rule == 2) {
+    /* given nodes: each owns the box between the midpoints to its neighbours */
+    for (int i = 0; i < n; ++i) x[i] = given[i];
+    for (int i = 0; i < n; ++i) {
+      bl[i] = (i == 0) ? x[0] : 0.5 * (x[i - 1] + x[i]);
+      bh[i] = (i == n - 1) ? x[n - 1] : 0.5 * (x[i] + x[i + 1]);
+      w[i] = bh[i] - bl[i];
+    }
+  } else if (rule == 0) {
     double d = (hi - lo) / (n - 1);
     for (int i = 0; i < n; ++i) {
       x[i] = c + (2 * i - (n - 1)) * (hw / (n - 1));
@@ -581,7 +595,7 @@ or_case *or_create(const or_params *p)
     al[a] = (double *)xcalloc(m, sizeof(double));
     ah[a] = (double *)xcalloc(m, sizeof(double));
     if (a < D)
-      axis_nodes(m, p->vlo[a], p->vhi[a], p->rule, ax[a], aw[a], al[a], ah[a]);
+      axis_nodes(m, p->vlo[a], p->vhi[a], p->rule, p->vnodes[a], ax[a], aw[a], al[a], ah[a]);
     else {
       ax[a][0] = 0.0;
       aw[a][0] = 1.0;
@@ -916,6 +930,21 @@ static double interp_velocity(const or_case *C, const double *fi, const double *
     double x0 = C->xi[3 * 0 + a];
     double x1 = C->xi[3 * ((na - 1) * stride) + a];
     if (xq[a] < x0 || xq[a] > x1) return 0.0;
+    if (C->p.rule == 2) {
+      /* non-uniform nodes (C25): the bracketing interval by bisection */
+      int lo = 0, hi = na - 1;
+      while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (C->xi[3 * (mid * stride) + a] <= xq[a])
+          lo = mid;
+        else
+          hi = mid;
+      }
+      double xl = C->xi[3 * (lo * stride) + a], xh = C->xi[3 * (hi * stride) + a];
+      i0[a] = lo;
+      t[a] = (xq[a] - xl) / (xh - xl);
+      continue;
+    }
     double d = (na > 1) ? (x1 - x0) / (na - 1) : 1.0;
     double u = (xq[a] - x0) / d;
     int i = (int)floor(u);

@@ -43,7 +43,8 @@ typedef struct {
   int dim;
   int n[3];
   double lo[3], hi[3];
-  /* velocity grid: nv[a] nodes on [vlo[a], vhi[a]], rule 0 = trapezoid, 1 = composite midpoint */
+  /* velocity grid: nv[a] nodes on [vlo[a], vhi[a]], rule 0 = trapezoid, 1 = composite midpoint,
+     2 = the nodes vnodes[a][0 .. nv[a]-1] (strictly increasing; C25) */
   int nv[3];
   double vlo[3], vhi[3];
   int rule;
@@ -70,6 +71,8 @@ typedef struct {
   int wall[6];
   double wall_T[6];
   double wall_U[6][3];
+  /* rule 2: the nodes of each axis */
+  const double *vnodes[3];
 } or_params;
 
 typedef struct or_case or_case;

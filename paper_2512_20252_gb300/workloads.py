@@ -110,6 +110,36 @@ def cylinder_512(Kn=0.1, precision="mixed", steps=200):
     return _case(2, 512, 8.0, 48, 6.0, Kn, 0.5, circle(0.5), precision=precision, steps=steps)
 
 
+def stretched_axis(n, V, h_min):
+    """n velocity nodes on [-V, V], symmetric about 0, spaced h_min at the
+    centre and growing geometrically toward the ends (a stretched grid,
+    refined where the distributions of a gas near rest vary fastest)."""
+    if n % 2:
+        raise ValueError("an even node count keeps 0 between two nodes")
+    m = n // 2
+    # half-spacings h_min q^i, i < m, sum to V - h_min / 2 past the first node
+    lo, hi = 1.0, 10.0
+    for _ in range(200):
+        q = 0.5 * (lo + hi)
+        s = h_min * (q ** (m - 1) - 1.0) / (q - 1.0) if q != 1.0 else h_min * (m - 1)
+        lo, hi = (q, hi) if h_min / 2 + s < V else (lo, q)
+    q = 0.5 * (lo + hi)
+    half = [h_min / 2]
+    for i in range(1, m):
+        half.append(half[-1] + h_min * q ** (i - 1))
+    half = np.array(half) * (V / half[-1])
+    return list(-half[::-1]) + list(half)
+
+
+def stretched(case, h_min):
+    """The case on stretched velocity grids (the same node count and interval
+    per axis, spacing h_min at the centre)."""
+    c = dict(case)
+    c["rule"] = "nodes"
+    c["vnodes"] = [stretched_axis(int(c["nv"][a]), float(c["vhi"][a]), h_min) for a in range(c["dim"])]
+    return c
+
+
 def box_walls(dim=2, Tw=1.0, lid=None, lid_T=None):
     """Diffuse walls on every domain face (x-, x+, y-, y+, z-, z+) at Tw; lid:
     the velocity of the top face (y+ in 2D, z+ in 3D), its temperature lid_T."""

@@ -589,6 +589,68 @@ def test_wall_quantities_no_flow_through_the_wall(cutcell):
 
 
 # ---------------------------------------------------------------------------
+# Non-uniform (stretched) velocity grids (reading C25)
+# ---------------------------------------------------------------------------
+
+def test_explicit_uniform_nodes_are_the_trapezoid_rule():
+    """Nodes given explicitly at the trapezoid positions give the trapezoid
+    rule: the same nodes and weights (each node's box reaches halfway to its
+    neighbours, half boxes at the ends), the same cut tables and the same
+    steps."""
+    base = case2d(n=16, nv=20, V=5.0, L=2.0, Ma=0.4, body=wl.circle(0.6))
+    # exactly antisymmetric nodes, as the trapezoid rule's are: the upwind
+    # weights' fallback is decided by exact zeros of xi.r (reading C10)
+    pos = np.linspace(-5.0, 5.0, 20)[10:]
+    given = dict(base, rule="nodes", vnodes=[list(np.concatenate([-pos[::-1], pos]))] * 2)
+    a, b = oracle.OracleCase(base), oracle.OracleCase(given)
+    xa, wa = a.velocities()
+    xb, wb = b.velocities()
+    np.testing.assert_allclose(xb, xa, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(wb, wa, rtol=1e-13)
+    np.testing.assert_allclose(b.cut_table(), a.cut_table(), rtol=0, atol=1e-13)
+    a.step(3)
+    b.step(3)
+    np.testing.assert_allclose(b.get_f(), a.get_f(), rtol=0, atol=1e-12 * np.abs(a.get_f()).max())
+
+
+def test_stretched_grid_moments_converge_at_second_order():
+    """The trapezoid rule on a smoothly stretched grid: the moments of a
+    drifting Maxwellian converge to the closed forms at second order as the
+    stretched family is refined (node count doubled, central spacing halved)."""
+    rho, U, T = 1.3, (0.4, -0.25), 1.2
+    errs = []
+    for n in (32, 64, 128):
+        oc = oracle.OracleCase(wl.stretched(case2d(nv=n, V=7.0), 3.2 / n))
+        m = oc.cell_moments(oc.maxwellian(rho, U, T))
+        errs.append([abs(m["rho"] - rho) / rho, abs(m["T"] - T) / T,
+                     abs(m["rhoU"][0] - rho * U[0]) / (rho * abs(U[0]))])
+    errs = np.array(errs)
+    orders = np.log2(errs[:-1] / errs[1:])
+    assert orders.min() > 1.8, orders
+
+
+def test_specular_wall_on_a_stretched_grid():
+    """alpha = 0 on an axis-aligned wall, a symmetric stretched grid: every
+    mirrored velocity is a node (found by bisection), so f*_w is the exact
+    mirror image of the incident distribution and no mass or tangential
+    momentum crosses the wall."""
+    body = {"kind": "halfspace", "center": [0.0501, 0.0, 0.0], "radii": [1.0, 0.0, 0.0], "Tw": 1.0,
+            "accom": 0.0}
+    nv = 20
+    oc = oracle.OracleCase(wl.stretched(case2d(n=8, nv=nv, V=6.0, body=body), 0.25))
+    f = np.broadcast_to(oc.maxwellian(1.0, (-0.3, 0.25), 1.1), oc.shape()).copy()
+    gb = oc.ghost_band(f)
+    xi, w = oc.velocities()
+    fs = gb["fstarw"][:, :, 0]
+    fi = gb["fiw"][:, :, 0]
+    assert np.abs(fs @ (w * xi[:, 0])).max() < 1e-14
+    assert np.abs(fs @ (w * xi[:, 0] * xi[:, 1])).max() < 1e-14
+    mirror = (np.arange(nv * nv) // nv) * nv + (nv - 1 - np.arange(nv * nv) % nv)
+    refl = xi[:, 0] > 0
+    np.testing.assert_allclose(fs[:, refl], fi[:, mirror][:, refl], rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
 # Diffuse domain walls (Sec. 2.3 on the faces of the domain; reading C24)
 # ---------------------------------------------------------------------------
 
