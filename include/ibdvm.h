@@ -59,7 +59,7 @@ typedef enum {
   IBDVM_E_STATE = 8         /* the call is not valid in the current state */
 } ibdvm_status;
 
-enum { IBDVM_RULE_TRAPEZOID = 0, IBDVM_RULE_MIDPOINT = 1 };
+enum { IBDVM_RULE_TRAPEZOID = 0, IBDVM_RULE_MIDPOINT = 1, IBDVM_RULE_NODES = 2 };
 enum { IBDVM_FP64 = 0, IBDVM_MIXED = 1 };
 enum {
   IBDVM_BODY_NONE = 0,
@@ -87,11 +87,18 @@ typedef struct {
 /* Velocity grid (Eq. quadrature): n[a] nodes per axis on [lo[a], hi[a]],
    rule = IBDVM_RULE_TRAPEZOID (nodes at both ends) or IBDVM_RULE_MIDPOINT
    (composite midpoint, Sec. 3.2.3).  Each node owns the dual box
-   [xi - dxi/2, xi + dxi/2] clipped to the interval; its measure is the weight. */
+   [xi - dxi/2, xi + dxi/2] clipped to the interval; its measure is the weight.
+   rule = IBDVM_RULE_NODES: a non-uniform (stretched) grid standing in for the
+   locally refined velocity mesh of Sec. 4.4, the tensor product of the n[a]
+   strictly increasing finite nodes nodes[a][0 .. n[a]-1] of each axis (lo
+   and hi are ignored: the interval is [nodes[a][0], nodes[a][n[a]-1]]);
+   each node owns the box between the midpoints to its neighbours (the
+   trapezoid rule on non-uniform nodes).  The library copies the nodes. */
 typedef struct {
   int n[3];
   double lo[3], hi[3];
   int rule;
+  const double *nodes[3]; /* IBDVM_RULE_NODES only (else ignored) */
 } ibdvm_vgrid_desc;
 
 /* Gas and run parameters (Sec. 4): Knudsen and Mach numbers, Prandtl number,

@@ -293,7 +293,17 @@ bool build_grid(const ibdvm_grid_desc &g, const ibdvm_vgrid_desc &v, const ibdvm
         err = "vgrid.n[a] must be in [2, 4096]";
         return false;
       }
-      if (!(v.hi[a] > v.lo[a])) {
+      if (v.rule == IBDVM_RULE_NODES) {
+        if (!v.nodes[a]) {
+          err = "vgrid.nodes[a] is required for IBDVM_RULE_NODES";
+          return false;
+        }
+        for (int i = 0; i < v.n[a]; ++i)
+          if (!std::isfinite(v.nodes[a][i]) || (i > 0 && !(v.nodes[a][i] > v.nodes[a][i - 1]))) {
+            err = "vgrid.nodes[a] must be finite and strictly increasing";
+            return false;
+          }
+      } else if (!(v.hi[a] > v.lo[a])) {
         err = "vgrid.lo < vgrid.hi required";
         return false;
       }
@@ -307,8 +317,8 @@ bool build_grid(const ibdvm_grid_desc &g, const ibdvm_vgrid_desc &v, const ibdvm
     }
     G.ncell *= G.n[a];
   }
-  if (v.rule != IBDVM_RULE_TRAPEZOID && v.rule != IBDVM_RULE_MIDPOINT) {
-    err = "vgrid.rule must be trapezoid (0) or midpoint (1)";
+  if (v.rule != IBDVM_RULE_TRAPEZOID && v.rule != IBDVM_RULE_MIDPOINT && v.rule != IBDVM_RULE_NODES) {
+    err = "vgrid.rule must be trapezoid (0), midpoint (1) or nodes (2)";
     return false;
   }
   long long nv = 1;
@@ -337,7 +347,14 @@ bool build_grid(const ibdvm_grid_desc &g, const ibdvm_vgrid_desc &v, const ibdvm
       continue;
     }
     double lo = v.lo[a], hi = v.hi[a];
-    if (v.rule == IBDVM_RULE_TRAPEZOID) {
+    if (v.rule == IBDVM_RULE_NODES) {
+      // given nodes: each owns the box between the midpoints to its neighbours
+      for (int i = 0; i < m; ++i) ax[a][i] = v.nodes[a][i];
+      for (int i = 0; i < m; ++i) {
+        al[a][i] = (i == 0) ? ax[a][0] : 0.5 * (ax[a][i - 1] + ax[a][i]);
+        ah[a][i] = (i == m - 1) ? ax[a][m - 1] : 0.5 * (ax[a][i] + ax[a][i + 1]);
+      }
+    } else if (v.rule == IBDVM_RULE_TRAPEZOID) {
       double h = (hi - lo) / (m - 1);
       for (int i = 0; i < m; ++i) {
         ax[a][i] = centred(lo, hi, 2L * i - (m - 1), m - 1);

@@ -693,6 +693,7 @@ template <typename T> struct GhostArgs {
   int plain_average;
   HaloArgs<T> H; // the domain halo the pre-ghost slopes see
   int n[3];
+  int nodes_rule; // non-uniform velocity nodes (the specular interpolation bisects)
 };
 
 template <int NT> __device__ __forceinline__ double block_sum(double v, double *sh) {
@@ -734,6 +735,39 @@ __device__ __forceinline__ T preghost_slope(const GhostArgs<T> &G, int code_m, i
   if (hm) return (fj - fm) * rh;
   if (hp) return (fp - fj) * rh;
   return T(0);
+}
+
+// the node interval of the velocity grid holding coordinate x along axis a:
+// the lower node i and the fraction t of the multilinear interpolation
+// (C13); false when x lies outside the grid.  Uniform axes by division,
+// non-uniform ones (given nodes) by bisection on the node coordinates.
+template <typename T>
+__device__ __forceinline__ bool mirror_bracket(const GhostArgs<T> &G, int a, double x, int &i0, double &t) {
+  const int n = G.nvx[a];
+  if (G.nodes_rule) {
+    const int stride = (a == 0) ? 1 : (a == 1 ? G.nvx[0] : G.nvx[0] * G.nvx[1]);
+    const double *xa = G.xiD + (size_t)a * G.nvp;
+    if (x < xa[0] || x > xa[(size_t)(n - 1) * stride]) return false;
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) / 2;
+      if (xa[(size_t)mid * stride] <= x)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const double xl = xa[(size_t)lo * stride], xh = xa[(size_t)hi * stride];
+    i0 = lo;
+    t = (x - xl) / (xh - xl);
+    return true;
+  }
+  const double xl = G.vx0[a], xh = G.vx0[a] + G.vh[a] * (n - 1);
+  const double u = (x - xl) / G.vh[a];
+  int i = (int)floor(u);
+  i = min(max(i, 0), n - 2);
+  i0 = i;
+  t = u - i;
+  return !(x < xl || x > xh);
 }
 
 template <typename T, int D>
@@ -829,15 +863,8 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
       bool inside = true;
       int i0[3] = {0, 0, 0};
       double t[3] = {0, 0, 0};
-      for (int a = 0; a < D; ++a) {
-        const double xl = G.vx0[a], xh = G.vx0[a] + G.vh[a] * (G.nvx[a] - 1);
-        if (xm[a] < xl || xm[a] > xh) inside = false;
-        double u = (xm[a] - xl) / G.vh[a];
-        int i = (int)floor(u);
-        i = min(max(i, 0), G.nvx[a] - 2);
-        i0[a] = i;
-        t[a] = u - i;
-      }
+      for (int a = 0; a < D; ++a)
+        if (!mirror_bracket(G, a, xm[a], i0[a], t[a])) inside = false;
       double v = 0.0;
       if (inside)
         for (int corner = 0; corner < (1 << D); ++corner) {
@@ -871,15 +898,8 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
       bool inside = true;
       int i0[3] = {0, 0, 0};
       double t[3] = {0, 0, 0};
-      for (int a = 0; a < D; ++a) {
-        const double xl = G.vx0[a], xh = G.vx0[a] + G.vh[a] * (G.nvx[a] - 1);
-        if (xm[a] < xl || xm[a] > xh) inside = false;
-        double u = (xm[a] - xl) / G.vh[a];
-        int i = (int)floor(u);
-        i = min(max(i, 0), G.nvx[a] - 2);
-        i0[a] = i;
-        t[a] = u - i;
-      }
+      for (int a = 0; a < D; ++a)
+        if (!mirror_bracket(G, a, xm[a], i0[a], t[a])) inside = false;
       if (inside)
         for (int corner = 0; corner < (1 << D); ++corner) {
           double wt = 1.0;
@@ -1403,6 +1423,7 @@ template <typename T> GhostArgs<T> ghost_args(const ibdvm_ctx *ctx, int cur, dou
   G.plain_average = (g.gas.flags & IBDVM_PLAIN_AVERAGE) ? 1 : 0;
   G.H = halo_args<T>(ctx);
   for (int a = 0; a < 3; ++a) G.n[a] = g.n[a];
+  G.nodes_rule = (g.rule == IBDVM_RULE_NODES) ? 1 : 0;
   return G;
 }
 

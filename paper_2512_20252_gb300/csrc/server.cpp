@@ -35,6 +35,7 @@ struct Req {
   ibdvm_body_desc body{};
   bool has_body = false;
   std::vector<double> verts;
+  std::vector<double> vnodes[3]; // velocity nodes of IBDVM_RULE_NODES (the request owns a copy)
   ibdvm_ctx *ctx = nullptr;
   bool batched = false;
   size_t bytes = 0;
@@ -179,6 +180,11 @@ ibdvm_status ibdvm_server_submit(ibdvm_server *s, const ibdvm_grid_desc *grid, c
     q->grid = *grid;
     q->vgrid = *vgrid;
     q->gas = *gas;
+    if (vgrid->rule == IBDVM_RULE_NODES)
+      for (int a = 0; a < grid->dim && a < 3; ++a) {
+        if (vgrid->nodes[a] && vgrid->n[a] > 0) q->vnodes[a].assign(vgrid->nodes[a], vgrid->nodes[a] + vgrid->n[a]);
+        q->vgrid.nodes[a] = q->vnodes[a].empty() ? nullptr : q->vnodes[a].data();
+      }
     q->gas.precision = s->d.sequential_fp64 ? IBDVM_FP64 : IBDVM_MIXED;
     if (estimate_ctx_bytes(&q->grid, &q->vgrid, &q->gas) == 0) {
       delete q;

@@ -43,7 +43,7 @@ class GridDesc(ctypes.Structure):
 
 class VGridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
-                ("rule", ctypes.c_int)]
+                ("rule", ctypes.c_int), ("nodes", ctypes.POINTER(ctypes.c_double) * 3)]
 
 
 class GasDesc(ctypes.Structure):
@@ -215,7 +215,16 @@ def descriptors(case: dict):
     v.n[:] = [int(x) for x in _a3(case["nv"], 1)]
     v.lo[:] = _a3(case["vlo"])
     v.hi[:] = _a3(case["vhi"], 1.0)
-    v.rule = {"trapezoid": 0, "midpoint": 1}[case.get("rule", "trapezoid")]
+    v.rule = {"trapezoid": 0, "midpoint": 1, "nodes": 2}[case.get("rule", "trapezoid")]
+    node_arrays = []
+    if v.rule == 2:
+        # explicit velocity nodes per axis: the node counts and the interval follow them
+        for a in range(dim):
+            nodes = np.ascontiguousarray(np.asarray(case["vnodes"][a], dtype=np.float64))
+            node_arrays.append(nodes)
+            v.nodes[a] = _dp(nodes)
+            v.n[a] = nodes.size
+            v.lo[a], v.hi[a] = float(nodes[0]), float(nodes[-1])
     s = GasDesc()
     s.Kn = case["Kn"]
     s.Ma = case["Ma"]
@@ -253,7 +262,7 @@ def descriptors(case: dict):
     b.T_w = body.get("Tw", 1.0)
     b.U_w[:] = _a3(body.get("Uw", [0.0, 0.0, 0.0]))
     b.L_ref = body.get("Lref", 0.0)
-    return g, v, s, b, keep
+    return g, v, s, b, (keep, node_arrays)
 
 
 def _dp(a):

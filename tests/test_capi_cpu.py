@@ -56,6 +56,9 @@ def _cases():
                                 {"kind": "halfspace", "center": [0.05, 0.02, 0.0],
                                  "radii": [0.6, 0.48, 0.64], "accom": 0.7, "Tw": 1.2}),
         "naca_aoa": wl._case(2, 96, 2.0, 6, 4.0, 0.1, 0.5, wl.naca0012(2.0, 8.0, 80)),
+        # non-uniform (stretched) velocity grids
+        "stretched2d": wl.stretched(wl._case(2, 24, 2.0, 16, 5.0, 0.1, 0.4, wl.circle(0.6)), 0.3),
+        "stretched3d": wl.stretched(wl._case(3, 10, 2.0, 10, 4.5, 0.1, 0.3, wl.sphere(0.7)), 0.4),
     }
     return out
 
@@ -84,6 +87,15 @@ def test_geometry_matches_oracle(lib, name):
     np.testing.assert_array_equal(gg, og)
     np.testing.assert_array_equal(go_, oo)
     np.testing.assert_array_equal(gc, oc)
+
+
+def test_geometry_rejects_bad_velocity_nodes(lib):
+    base = wl.stretched(wl.small_2d("circle"), 0.4)
+    for nodes in ([0.0, 1.0, 1.0, 2.0], [0.0, float("nan"), 1.0, 2.0], [2.0, 1.0, 0.0, -1.0]):
+        bad = dict(base, vnodes=[nodes, base["vnodes"][1]])
+        with pytest.raises(ibdvm.IbdvmError) as e:
+            ibdvm.Geometry(bad)
+        assert e.value.status == 1
 
 
 def test_geometry_rejects_bad_input(lib):

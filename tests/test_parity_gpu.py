@@ -319,6 +319,29 @@ def test_wall_quantities_without_a_body_or_a_free_stream():
 
 
 # ---------------------------------------------------------------------------
+# non-uniform (stretched) velocity grids (reading C25)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,precision,accom", [(2, "fp64", 1.0), (2, "fp64", 0.6), (3, "fp64", 1.0),
+                                                 (2, "mixed", 1.0), (3, "mixed", 1.0)])
+def test_stretched_velocity_grid_against_the_oracle(dim, precision, accom):
+    """Velocity nodes clustered about 0 (spacing growing geometrically toward
+    the ends); alpha < 1 exercises the bisection of the specular part."""
+    if dim == 2:
+        base = wl._case(2, 24, 2.0, 16, 5.0, 0.1, 0.4, wl.circle(0.6, accom=accom), precision=precision)
+        case = wl.stretched(base, 0.3)
+    else:
+        base = wl._case(3, 10, 2.0, 10, 4.5, 0.1, 0.3, wl.sphere(0.7, accom=accom), precision=precision)
+        case = wl.stretched(base, 0.4)
+    g, o, rg, ro = pair(case, 6)
+    if precision == "fp64":
+        compare(g, o)
+        assert rg == pytest.approx(ro, rel=1e-9)
+    else:
+        compare(g, o, tol=1e-5, wtol=1e-5)
+
+
+# ---------------------------------------------------------------------------
 # diffuse domain walls (the lid-driven cavity of Sec. 4.1; reading C24)
 # ---------------------------------------------------------------------------
 
