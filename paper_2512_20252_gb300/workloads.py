@@ -166,6 +166,13 @@ def sphere_96(precision="mixed", steps=200):
     return _case(3, 96, 4.0, 20, 5.0, 0.1, 0.5, sphere(0.5), precision=precision, steps=steps)
 
 
+def sphere_96_stretched(precision="mixed", steps=200):
+    """The 96^3 sphere (Ma 0.5, Kn 0.1) on a stretched velocity grid: 20^3
+    nodes on [-5,5]^3, spacing 0.25 at the centre (0.53 on the uniform grid)
+    growing toward the ends."""
+    return stretched(sphere_96(precision=precision, steps=steps), 0.25)
+
+
 def sphere_24(precision="fp64", steps=50):
     """The 3D sphere downscaled to 24^3 cells and 12^3 velocities (50 steps)."""
     return _case(3, 24, 4.0, 12, 5.0, 0.1, 0.5, sphere(0.5), precision=precision, steps=steps)
