@@ -231,3 +231,21 @@ def test_batch_rejects_bad_members(torch):
     assert list(st) == [0]
     b2.close()
     b.close()
+
+
+def test_stretched_velocity_grid_member(torch):
+    """A member on a stretched velocity grid (partly specular wall: the
+    specular part bisects the node grid) steps in the batch exactly as alone."""
+    stream = torch.cuda.Stream()
+    a = wl.stretched(wl._case(2, 32, 2.0, 16, 4.5, 0.1, 0.4, wl.circle(0.7, accom=0.7), precision="mixed"), 0.3)
+    cases = [a, mixed_cases()[1]]
+    solo, mem = twins(torch, cases, stream)
+    b = ibdvm.Batch(stream=stream.cuda_stream)
+    for m in mem:
+        b.add(m)
+    rb, st = b.step(4)
+    rs = [s.step(4) for s in solo]
+    assert list(st) == [0, 0] and list(rb) == rs
+    for s, m in zip(solo, mem):
+        assert_same(s, m)
+    b.close()
