@@ -88,6 +88,7 @@ class _Params(ctypes.Structure):
         ("wall_T", ctypes.c_double * 6),
         ("wall_U", (ctypes.c_double * 3) * 6),
         ("vnodes", ctypes.POINTER(ctypes.c_double) * 3),
+        ("ghost_nonneg", ctypes.c_int),
     ]
 
 
@@ -197,6 +198,7 @@ def _params(cfg: dict) -> tuple[_Params, object]:
     p.Lref = body.get("Lref", 0.0)
     p.cutcell = int(cfg.get("cutcell", 1))
     p.upwind = int(cfg.get("upwind", 1))
+    p.ghost_nonneg = int(cfg.get("ghost_nonneg", 0))
     # domain faces (x-, x+, y-, y+, z-, z+): None = freestream halo, or a
     # diffuse wall {"Tw": T, "Uw": [u, v, w]}
     for i, wall in enumerate(cfg.get("domain_walls") or [None] * 6):

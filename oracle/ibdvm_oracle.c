@@ -57,6 +57,13 @@
  *       each node owns the box between the midpoints to its neighbours (the
  *       trapezoid rule on non-uniform nodes), and the specular interpolation
  *       (C13) brackets a velocity by bisection on each axis.
+ *   C26 optional (default off): a ghost value of Eq. extrapolation 2 below
+ *       zero is set to zero.  The extrapolation from the shifted point
+ *       through the wall value (up to threefold) can turn negative where the
+ *       wall distribution is small, and a nearly empty donor cell in a
+ *       strong expansion then loses positivity; a distribution function is
+ *       nonnegative, and with nonnegative ghost values the limited upwind
+ *       transport keeps it so.
  *   C24 a domain face may instead be a diffuse wall (Sec. 2.3 with alpha = 1
  *       on the plane of the face, normal into the domain): its two halo
  *       layers hold, for velocities entering the domain through the face,
@@ -1029,6 +1036,7 @@ void or_ghost_band(const or_case *C, const double *f, double *fgc_out, double *f
           double fr = alpha * rhow * Gw[i] + (1.0 - alpha) * fs[i];
           double fstar = (C->w[k] > 0.0) ? (wg * fi[i] + ws * fr) / C->w[k] : fi[i];
           double fgs = fsp[i] + (fstar - fsp[i]) / (L->yw - L->ysp) * (L->yg - L->ysp);
+          if (C->p.ghost_nonneg && fgs < 0.0) fgs = 0.0; /* C26 */
           size_t o = ((size_t)l * nv + k) * nc + m;
           if (fgc_out) fgc_out[o] = fgc[i];
           if (fsp_out) fsp_out[o] = fsp[i];

@@ -73,6 +73,8 @@ typedef struct {
   double wall_U[6][3];
   /* rule 2: the nodes of each axis */
   const double *vnodes[3];
+  /* 1: ghost values below zero are set to zero (C26) */
+  int ghost_nonneg;
 } or_params;
 
 typedef struct or_case or_case;

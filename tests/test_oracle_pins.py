@@ -589,6 +589,44 @@ def test_wall_quantities_no_flow_through_the_wall(cutcell):
 
 
 # ---------------------------------------------------------------------------
+# Optional nonnegative ghost values (reading C26)
+# ---------------------------------------------------------------------------
+
+def _supersonic_cylinder(**kw):
+    return wl._case(2, 48, 4.0, 16, 7.29, 0.03, 3.834, wl.circle(0.5, Tw=5.9), **kw)
+
+
+def test_nonnegative_ghost_values_are_the_clamped_extrapolation():
+    """With the option, a ghost value is that of Eq. extrapolation 2, set to
+    zero where it is negative; everything the ghost value is built from
+    (f_gc, f_sp, f^i_w, rho_w, f*_w) is unchanged.  A supersonic cylinder at
+    the hot wall of Sec. 4.4 has thousands of negative ghost values after
+    one step."""
+    a = oracle.OracleCase(_supersonic_cylinder())
+    a.step(1)
+    f = a.get_f()
+    b = oracle.OracleCase(_supersonic_cylinder(ghost_nonneg=1))
+    ga, gb = a.ghost_band(f), b.ghost_band(f)
+    assert (ga["fstargc"] < 0).sum() > 1000
+    for k in ("fgc", "fsp", "fiw", "fstarw", "rhow"):
+        np.testing.assert_array_equal(gb[k], ga[k], err_msg=k)
+    np.testing.assert_array_equal(gb["fstargc"], np.maximum(ga["fstargc"], 0.0))
+
+
+def test_nonnegative_ghost_values_change_nothing_when_none_is_negative():
+    """A gas at rest at the wall temperature: every ghost value is the
+    Maxwellian (positive), so the option leaves every step unchanged.  (Even
+    the subsonic cylinder has some negative ghost values, where the wall
+    distribution jumps in velocity space: the option is off by default.)"""
+    case = dict(wl.cylinder_48(), Ma=0.0)
+    a, b = oracle.OracleCase(case), oracle.OracleCase(dict(case, ghost_nonneg=1))
+    a.step(5)
+    b.step(5)
+    assert a.ghost_band()["fstargc"].min() >= 0.0
+    np.testing.assert_array_equal(b.get_f(), a.get_f())
+
+
+# ---------------------------------------------------------------------------
 # Non-uniform (stretched) velocity grids (reading C25)
 # ---------------------------------------------------------------------------
 
