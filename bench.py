@@ -42,6 +42,8 @@ WORKLOADS = {
         n=64, nv=100, precision=p),
     "sphere_96_stretched": lambda p: __import__("paper_2512_20252_gb300.workloads",
                                                 fromlist=["x"]).sphere_96_stretched(p),
+    "sphere_supersonic": lambda p: __import__("paper_2512_20252_gb300.workloads",
+                                              fromlist=["x"]).sphere_supersonic(precision=p),
     "batched_2d": None,  # a list of cases: see bench_batch
     "served": None,      # a request stream: see bench_serve
 }
@@ -49,6 +51,8 @@ DESCRIPTIONS = {
     "cylinder_512": "2D cylinder r=0.5, 512x512 cells on [-8,8]^2, 48x48 trapezoid velocities on [-6,6]^2, Kn=0.1, Ma=0.5",
     "sphere_96": "3D sphere r=0.5, 96^3 cells on [-4,4]^3, 20^3 trapezoid velocities on [-5,5]^3, Kn=0.1, Ma=0.5",
     "cylinder_48": "2D cylinder r=0.5, 48x48 cells on [-4,4]^2, 24x24 trapezoid velocities on [-5,5]^2, Kn=0.1, Ma=0.3",
+    "sphere_supersonic": "3D sphere r=0.5, 64^3 cells on [-4,4]^3, Ma=3.834, Kn=0.03, T_w=5.90, 24^3 stretched "
+                         "velocities on [-7.29,7.29]^3 (central spacing 0.2275), nonnegative ghost values",
     "sphere_96_stretched": "3D sphere r=0.5, 96^3 cells on [-4,4]^3, 20^3 stretched velocities on [-5,5]^3 "
                            "(central spacing 0.25), Kn=0.1, Ma=0.5",
     "cavity_64": "2D lid-driven cavity [0,1]^2 with a cylinder of diameter 0.25 at its centre, 64x64 cells, "

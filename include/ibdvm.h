@@ -74,7 +74,9 @@ enum { IBDVM_CELL_FLUID = 0, IBDVM_CELL_GHOST = 1, IBDVM_CELL_SOLID = 2 };
 enum {
   IBDVM_NO_CUTCELL = 1,        /* incident/reflected by the node sign of xi.n only (no Sec. 3.2.3) */
   IBDVM_PLAIN_AVERAGE = 2,     /* weights 1/N_S instead of Eq. upwind (ablation) */
-  IBDVM_RHAT_GHOST_TO_FLUID = 4 /* Eq. upwind with r pointing from the ghost to the fluid cell */
+  IBDVM_RHAT_GHOST_TO_FLUID = 4, /* Eq. upwind with r pointing from the ghost to the fluid cell */
+  IBDVM_GHOST_NONNEG = 8         /* ghost values of Eq. extrapolation 2 below zero are set to zero
+                                    (off by default: keeps the supersonic cases of Sec. 4.4 positive) */
 };
 
 /* Uniform Cartesian grid: dim = 2 or 3, n[a] cells on [lo[a], hi[a]]. */

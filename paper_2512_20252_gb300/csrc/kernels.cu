@@ -694,6 +694,7 @@ template <typename T> struct GhostArgs {
   HaloArgs<T> H; // the domain halo the pre-ghost slopes see
   int n[3];
   int nodes_rule; // non-uniform velocity nodes (the specular interpolation bisects)
+  int ghost_nonneg; // ghost values below zero are set to zero
 };
 
 template <int NT> __device__ __forceinline__ double block_sum(double v, double *sh) {
@@ -923,7 +924,9 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
       const double fiv = (double)G.fi[o];
       const double fstar = (wk > 0.0) ? (wg * fiv + ws * fr) / wk : fiv;
       const double spv = (double)G.fsp[o];
-      G.lval[o] = (T)(spv + c_gc * (fstar - spv));
+      double gv = spv + c_gc * (fstar - spv);
+      if (G.ghost_nonneg && gv < 0.0) gv = 0.0; // optional nonnegative ghost values
+      G.lval[o] = (T)gv;
       if (G.dbg_fstar) G.dbg_fstar[o] = fstar;
     }
   }
@@ -1424,6 +1427,7 @@ template <typename T> GhostArgs<T> ghost_args(const ibdvm_ctx *ctx, int cur, dou
   G.H = halo_args<T>(ctx);
   for (int a = 0; a < 3; ++a) G.n[a] = g.n[a];
   G.nodes_rule = (g.rule == IBDVM_RULE_NODES) ? 1 : 0;
+  G.ghost_nonneg = (g.gas.flags & IBDVM_GHOST_NONNEG) ? 1 : 0;
   return G;
 }
 

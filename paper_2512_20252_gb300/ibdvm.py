@@ -7,7 +7,8 @@ PyTorch fallback.
 Case descriptions are plain dicts (see ``workloads``): dim, n, lo, hi, nv, vlo,
 vhi, rule, Kn, Ma, Pr, gamma, omega_vhs, alpha_vhs, rho_inf, T_inf, dir, cfl,
 dt, precision ("fp64" | "mixed"), cutcell, upwind (1 upwind weights, 2 the
-reverse unit vector, 0 plain average), body = {kind, center, radii, angle,
+reverse unit vector, 0 plain average), ghost_nonneg (1: ghost values below
+zero set to zero), body = {kind, center, radii, angle,
 verts, accom, Tw, Uw, Lref} and domain_walls (six entries for the faces x-,
 x+, y-, y+, z-, z+: None for a freestream face, {Tw, Uw} for a diffuse wall).
 """
@@ -27,7 +28,7 @@ STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_UNSTABLE", 5: 
           6: "E_NOTCONVERGED", 7: "E_TIMEOUT", 8: "E_STATE"}
 BODY = {"none": 0, "circle": 1, "ellipse": 2, "sphere": 3, "polygon": 4, "halfspace": 5}
 FLUID, GHOST, SOLID = 0, 1, 2
-NO_CUTCELL, PLAIN_AVERAGE, RHAT_GHOST_TO_FLUID = 1, 2, 4
+NO_CUTCELL, PLAIN_AVERAGE, RHAT_GHOST_TO_FLUID, GHOST_NONNEG = 1, 2, 4, 8
 
 
 class IbdvmError(RuntimeError):
@@ -246,6 +247,8 @@ def descriptors(case: dict):
         flags |= PLAIN_AVERAGE
     elif up == 2:
         flags |= RHAT_GHOST_TO_FLUID
+    if int(case.get("ghost_nonneg", 0)):
+        flags |= GHOST_NONNEG
     s.flags = flags
     body = case.get("body") or {"kind": "none"}
     b = BodyDesc()

@@ -166,6 +166,19 @@ def sphere_96(precision="mixed", steps=200):
     return _case(3, 96, 4.0, 20, 5.0, 0.1, 0.5, sphere(0.5), precision=precision, steps=steps)
 
 
+def sphere_supersonic(n=64, nv=24, precision="mixed", steps=200):
+    """The supersonic sphere of Sec. 4.4 on a uniform grid: Ma 3.834, Kn 0.03,
+    T_w = 1 + (gamma - 1) Ma^2 / 2, n^3 cells on [-4,4]^3, r = 0.5, nv^3
+    velocities on a stretched grid over [-3 sqrt(T_w), 3 sqrt(T_w)]^3 with
+    central spacing 0.2275 (the paper's smallest), nonnegative ghost values
+    (an impulsive start on this grid loses positivity without them)."""
+    Ma, gamma = 3.834, 5.0 / 3.0
+    Tw = 1.0 + 0.5 * (gamma - 1.0) * Ma * Ma
+    c = _case(3, n, 4.0, nv, 3.0 * np.sqrt(Tw), 0.03, Ma, sphere(0.5, Tw=Tw), precision=precision,
+              steps=steps, ghost_nonneg=1)
+    return stretched(c, 0.2275)
+
+
 def sphere_96_stretched(precision="mixed", steps=200):
     """The 96^3 sphere (Ma 0.5, Kn 0.1) on a stretched velocity grid: 20^3
     nodes on [-5,5]^3, spacing 0.25 at the centre (0.53 on the uniform grid)

@@ -319,6 +319,39 @@ def test_wall_quantities_without_a_body_or_a_free_stream():
 
 
 # ---------------------------------------------------------------------------
+# optional nonnegative ghost values (reading C26)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nonnegative_ghost_values_against_the_oracle(precision):
+    """A supersonic cylinder at the hot wall of Sec. 4.4, where thousands of
+    ghost values would be negative: with the option, against the oracle."""
+    case = wl._case(2, 48, 4.0, 16, 7.29, 0.03, 3.834, wl.circle(0.5, Tw=5.9), precision=precision,
+                    ghost_nonneg=1)
+    g, o, _, _ = pair(case, 4)
+    if precision == "fp64":
+        compare(g, o)
+    else:
+        compare(g, o, tol=1e-5, wtol=1e-5)
+    assert g.ghost_band()["fstargc"].min() >= 0.0
+
+
+def test_supersonic_sphere_stays_positive():
+    """The supersonic sphere of Sec. 4.4 (Ma 3.834, T_w = 5.9) started from
+    the freestream on 64^3 cells, stretched 24^3 velocities: with
+    nonnegative ghost values 100 steps keep a positive density and
+    temperature everywhere (without them the first 10 steps fail)."""
+    s = ibdvm.Solver(wl.sphere_supersonic())
+    s.step(100)
+    W, _, t = s.moments()
+    fl = t == ibdvm.FLUID
+    assert np.all(np.isfinite(W[fl])) and W[fl, 0].min() > 0.0
+    wq = s.wall()
+    assert np.all(wq[:, WALL["T"]] > 0) and np.all(wq[:, WALL["rho"]] > 0)
+    s.close()
+
+
+# ---------------------------------------------------------------------------
 # non-uniform (stretched) velocity grids (reading C25)
 # ---------------------------------------------------------------------------
 
