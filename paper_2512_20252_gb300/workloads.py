@@ -179,6 +179,18 @@ def sphere_supersonic(n=64, nv=24, precision="mixed", steps=200):
     return stretched(c, 0.2275)
 
 
+def naca_supersonic(cells_per_unit=100, nv=60, precision="mixed", steps=200):
+    """The NACA0012 airfoil of Sec. 4.3: Ma 2, Kn 0.026, T_w = 1, angle of
+    attack 0, chord 1 with the leading edge at the origin, the domain
+    [-3,7] x [-7,7] on a uniform grid of cells_per_unit cells per unit length
+    (1000 x 1400 by default), nv^2 velocities on [-4,8] x [-6,6] (the thin
+    body empties no cell: the ghost values of the paper stay positive)."""
+    n = [10 * cells_per_unit, 14 * cells_per_unit]
+    body = naca0012(1.0, 0.0, 400, center=(0.25, 0.0))
+    return _case(2, n, ([-3.0, -7.0], [7.0, 7.0]), nv, ([-4.0, -6.0], [8.0, 6.0]), 0.026, 2.0, body,
+                 precision=precision, steps=steps)
+
+
 def sphere_96_stretched(precision="mixed", steps=200):
     """The 96^3 sphere (Ma 0.5, Kn 0.1) on a stretched velocity grid: 20^3
     nodes on [-5,5]^3, spacing 0.25 at the centre (0.53 on the uniform grid)
