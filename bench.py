@@ -46,6 +46,8 @@ WORKLOADS = {
                                               fromlist=["x"]).sphere_supersonic(precision=p),
     "naca_supersonic": lambda p: __import__("paper_2512_20252_gb300.workloads",
                                             fromlist=["x"]).naca_supersonic(precision=p),
+    "cylinder_hypersonic": lambda p: __import__("paper_2512_20252_gb300.workloads",
+                                                fromlist=["x"]).cylinder_hypersonic(precision=p),
     "batched_2d": None,  # a list of cases: see bench_batch
     "served": None,      # a request stream: see bench_serve
 }
@@ -53,6 +55,8 @@ DESCRIPTIONS = {
     "cylinder_512": "2D cylinder r=0.5, 512x512 cells on [-8,8]^2, 48x48 trapezoid velocities on [-6,6]^2, Kn=0.1, Ma=0.5",
     "sphere_96": "3D sphere r=0.5, 96^3 cells on [-4,4]^3, 20^3 trapezoid velocities on [-5,5]^3, Kn=0.1, Ma=0.5",
     "cylinder_48": "2D cylinder r=0.5, 48x48 cells on [-4,4]^2, 24x24 trapezoid velocities on [-5,5]^2, Kn=0.1, Ma=0.3",
+    "cylinder_hypersonic": "2D cylinder r=1, 1536x1536 cells on [-16,16]^2, 60x60 trapezoid velocities on "
+                           "[-10,10]^2, Kn=0.1, Ma=5, T_w=1, nonnegative ghost values",
     "naca_supersonic": "2D NACA0012 airfoil (chord 1, AoA 0, T_w=1), Ma=2, Kn=0.026, 1000x1400 cells on "
                        "[-3,7]x[-7,7], 60x60 trapezoid velocities on [-4,8]x[-6,6]",
     "sphere_supersonic": "3D sphere r=0.5, 64^3 cells on [-4,4]^3, Ma=3.834, Kn=0.03, T_w=5.90, 24^3 stretched "

@@ -179,6 +179,16 @@ def sphere_supersonic(n=64, nv=24, precision="mixed", steps=200):
     return stretched(c, 0.2275)
 
 
+def cylinder_hypersonic(n=1536, nv=60, precision="mixed", steps=200):
+    """The hypersonic cylinder of Sec. 4.2: Ma 5, Kn 0.1, radius 1 (the
+    reference length), T_w = 1, the domain [-16,16]^2 on a uniform n^2 grid
+    (the paper refines to 0.01 at the wall), nv^2 velocities on
+    [-10,10]^2, nonnegative ghost values (an impulsive start loses
+    positivity in the wake without them)."""
+    return _case(2, n, 16.0, nv, 10.0, 0.1, 5.0, circle(1.0), precision=precision, steps=steps,
+                 ghost_nonneg=1)
+
+
 def naca_supersonic(cells_per_unit=100, nv=60, precision="mixed", steps=200):
     """The NACA0012 airfoil of Sec. 4.3: Ma 2, Kn 0.026, T_w = 1, angle of
     attack 0, chord 1 with the leading edge at the origin, the domain
