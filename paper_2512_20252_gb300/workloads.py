@@ -6,13 +6,17 @@ of the method's arithmetic, so both the CUDA path and the CPU oracle can be
 driven from the same dicts.
 
 Case dict keys: dim, n, lo, hi (physical grid); nv, vlo, vhi, rule (velocity
-grid, rule "trapezoid" or "midpoint"); Kn, Ma, Pr, gamma, omega_vhs, alpha_vhs,
-rho_inf, T_inf, dir, cfl, dt (gas, non-dimensional as in Sec. 4 of the paper);
-body = {kind, center, radii, angle, verts, accom, Tw, Uw, Lref}; cutcell,
-upwind (method switches); precision ("fp64" or "mixed"); steps.
+grid, rule "trapezoid", "midpoint" or "nodes" with vnodes = the nodes of each
+axis); Kn, Ma, Pr, gamma, omega_vhs, alpha_vhs, rho_inf, T_inf, dir, cfl, dt
+(gas, non-dimensional as in Sec. 4 of the paper); body = {kind, center,
+radii, angle, verts, accom, Tw, Uw, Lref}; domain_walls (six faces: None or
+{Tw, Uw}); cutcell, upwind, ghost_nonneg (method switches); precision
+("fp64" or "mixed"); steps.
 
-The workloads stand in for the paper's cases (Sec. 4: cylinder, airfoil,
-sphere); the paper measures on no public dataset.
+The workloads stand in for the paper's cases (Sec. 4: the cavity with a
+cylinder, the hypersonic cylinder, the supersonic airfoil and sphere, on
+uniform grids) and for the sizes of the benchmark configurations; the paper
+measures on no public dataset.
 """
 from __future__ import annotations
 
@@ -95,7 +99,7 @@ def naca0012(chord=1.0, aoa_deg=0.0, npts=80, center=(0.0, 0.0), **wall):
 
 
 # -------------------------------------------------------------------------
-# the five workloads
+# workloads: the benchmark configurations and the paper's cases
 # -------------------------------------------------------------------------
 
 def cylinder_48():
