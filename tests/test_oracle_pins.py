@@ -589,6 +589,51 @@ def test_wall_quantities_no_flow_through_the_wall(cutcell):
 
 
 # ---------------------------------------------------------------------------
+# Symmetries of the discrete problem
+# ---------------------------------------------------------------------------
+
+def _symmetric_case(direction):
+    cfg = case2d(n=20, nv=16, V=5.0, L=2.0, Ma=0.45, Kn=0.1, body=wl.circle(0.6))
+    cfg["dir"] = list(direction) + [0.0]
+    return cfg
+
+
+def test_mirror_symmetry_of_a_symmetric_flow():
+    """A cylinder at the centre of a symmetric grid in a stream along x: the
+    discrete problem is mirror-symmetric about y = 0 (symmetric cells,
+    velocity nodes, links and weights), so after several steps rho and rho E
+    are even and rho U_y odd in y, to rounding."""
+    oc = oracle.OracleCase(_symmetric_case((1.0, 0.0)))
+    oc.step(8)
+    W, _ = oc.moments()
+    Wm = W.reshape(20, 20, 4)
+    scale = np.abs(Wm).max(axis=(0, 1))
+    for i, sign in ((0, 1), (1, 1), (2, -1), (3, 1)):
+        assert np.abs(Wm[::-1, :, i] - sign * Wm[:, :, i]).max() < 1e-13 * scale[i], i
+    assert np.abs(Wm[:, :, 2]).max() > 1e-4  # the body deflects the stream
+
+
+def test_axis_exchange_symmetry():
+    """A stream along y is the stream along x reflected across the diagonal:
+    the cells, the velocity grid and the body map onto themselves with x and
+    y exchanged, so W along y at (i, j) is W along x at (j, i) with the two
+    momentum components exchanged.  Any treatment of one axis that differs
+    from the other (links, upwind weights, slopes, fluxes) breaks it."""
+    a = oracle.OracleCase(_symmetric_case((1.0, 0.0)))
+    b = oracle.OracleCase(_symmetric_case((0.0, 1.0)))
+    a.step(6)
+    b.step(6)
+    Wa, qa = a.moments()
+    Wb, qb = b.moments()
+    Wa = Wa.reshape(20, 20, 4)   # [y][x][component]
+    Wb = Wb.reshape(20, 20, 4)
+    swapped = Wa.transpose(1, 0, 2)[:, :, [0, 2, 1, 3]]
+    np.testing.assert_allclose(Wb, swapped, rtol=0, atol=1e-12 * np.abs(Wa).max())
+    qs = qa.reshape(20, 20, 2).transpose(1, 0, 2)[:, :, ::-1]
+    np.testing.assert_allclose(qb.reshape(20, 20, 2), qs, rtol=0, atol=1e-12 * max(np.abs(qa).max(), 1e-3))
+
+
+# ---------------------------------------------------------------------------
 # Optional nonnegative ghost values (reading C26)
 # ---------------------------------------------------------------------------
 
