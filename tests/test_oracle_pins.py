@@ -633,6 +633,25 @@ def test_axis_exchange_symmetry():
     np.testing.assert_allclose(qb.reshape(20, 20, 2), qs, rtol=0, atol=1e-12 * max(np.abs(qa).max(), 1e-3))
 
 
+def test_axis_exchange_symmetry_3d():
+    """3D: a stream along z past a centred sphere is the stream along x with
+    x and z exchanged."""
+    def case(direction):
+        cfg = case3d(n=10, nv=8, V=4.5, L=1.5, Ma=0.4, Kn=0.1, body=wl.sphere(0.5))
+        cfg["dir"] = list(direction)
+        return cfg
+    a = oracle.OracleCase(case((1.0, 0.0, 0.0)))
+    b = oracle.OracleCase(case((0.0, 0.0, 1.0)))
+    a.step(4)
+    b.step(4)
+    Wa, _ = a.moments()
+    Wb, _ = b.moments()
+    Wa = Wa.reshape(10, 10, 10, 5)   # [z][y][x][component]
+    Wb = Wb.reshape(10, 10, 10, 5)
+    swapped = Wa.transpose(2, 1, 0, 3)[..., [0, 3, 2, 1, 4]]
+    np.testing.assert_allclose(Wb, swapped, rtol=0, atol=1e-12 * np.abs(Wa).max())
+
+
 # ---------------------------------------------------------------------------
 # Optional nonnegative ghost values (reading C26)
 # ---------------------------------------------------------------------------
