@@ -550,6 +550,26 @@ def test_cylinder_512_full_size_properties(precision, tol):
     g.close()
 
 
+def test_cylinder_512_axis_exchange():
+    """The TMA sweep treats x (faces exchanged through shared memory) and y
+    (the march, faces in registers) by different code: a stream along y must
+    still be the stream along x with the axes exchanged, at the workload's
+    full size, to FP32 rounding."""
+    ca = wl.cylinder_512(Kn=0.1, precision="mixed")
+    cb = dict(ca, dir=[0.0, 1.0, 0.0])
+    a = ibdvm.Solver(ca)
+    a.step(20)
+    Wa = a.moments()[0].reshape(512, 512, 4)
+    a.close()
+    b = ibdvm.Solver(cb)
+    b.step(20)
+    Wb = b.moments()[0].reshape(512, 512, 4)
+    b.close()
+    swapped = Wa.transpose(1, 0, 2)[:, :, [0, 2, 1, 3]]
+    for i in range(4):
+        assert np.abs(Wb[:, :, i] - swapped[:, :, i]).max() < 1e-5 * np.abs(swapped[:, :, i]).max(), i
+
+
 def test_sphere_96_full_size_properties():
     case = wl.sphere_96(precision="mixed")
     g = ibdvm.Solver(case)
