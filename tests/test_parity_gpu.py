@@ -570,6 +570,24 @@ def test_cylinder_512_axis_exchange():
         assert np.abs(Wb[:, :, i] - swapped[:, :, i]).max() < 1e-5 * np.abs(swapped[:, :, i]).max(), i
 
 
+def test_sphere_96_axis_exchange():
+    """The 3D TMA sweep marches along z and exchanges x and y faces through
+    shared memory: a stream along z must be the stream along x with x and z
+    exchanged, at full size, to FP32 rounding."""
+    ca = wl.sphere_96(precision="mixed")
+    cb = dict(ca, dir=[0.0, 0.0, 1.0])
+    out = []
+    for c in (ca, cb):
+        s = ibdvm.Solver(c)
+        s.step(6)
+        out.append(s.moments()[0].reshape(96, 96, 96, 5))
+        s.close()
+    Wa, Wb = out
+    swapped = Wa.transpose(2, 1, 0, 3)[..., [0, 3, 2, 1, 4]]
+    for i in range(5):
+        assert np.abs(Wb[..., i] - swapped[..., i]).max() < 1e-5 * np.abs(swapped[..., i]).max(), i
+
+
 def test_sphere_96_full_size_properties():
     case = wl.sphere_96(precision="mixed")
     g = ibdvm.Solver(case)
