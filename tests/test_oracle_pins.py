@@ -557,6 +557,29 @@ def test_wall_quantities_flat_wall_closed_forms(u):
     assert np.all(errs[1] < errs[0] / 3.0), errs
 
 
+def test_wall_quantities_flat_wall_closed_forms_3d():
+    """The same closed forms in 3D (the third translational degree of freedom
+    is carried by f itself instead of b): a gas at rest on a diffuse flat
+    wall, midpoint rule, second order."""
+    rho, T, Tw = 1.2, 1.1, 0.8
+    rw = rho * math.sqrt(T / Tw)
+    expect = {"rho": (rho + rw) / 2.0, "p": (rho * T + rw * Tw) / 4.0, "T": math.sqrt(T * Tw),
+              "q_n": rho * math.sqrt(T) * (Tw - T) / (2.0 * math.sqrt(math.pi))}
+    errs = []
+    for nv in (16, 32):
+        body = {"kind": "halfspace", "center": [0.0501, 0.0, 0.0], "radii": [1.0, 0.0, 0.0], "Tw": Tw,
+                "accom": 1.0}
+        oc = oracle.OracleCase(case3d(n=4, nv=nv, V=5.5, body=body, rule="midpoint"))
+        f = np.broadcast_to(oc.maxwellian(rho, (0, 0, 0), T), oc.shape()).copy()
+        wq = oc.wall_quantities(f)
+        errs.append([np.abs(wq[:, WQ[k]] - v).max() / abs(v) for k, v in expect.items()])
+        for k in ("slip_x", "slip_y", "slip_z", "tau_x", "tau_y", "tau_z"):
+            assert np.abs(wq[:, WQ[k]]).max() < 1e-13, k
+    errs = np.array(errs)
+    assert errs[0].max() < 6e-2, errs[0]
+    assert np.all(errs[1] < errs[0] / 3.0), errs
+
+
 def test_wall_quantities_specular_wall():
     """alpha = 0 on an axis-aligned wall: f*_w is the mirror image of the
     incident gas, so the gas at the wall keeps the incident tangential
@@ -731,6 +754,17 @@ def test_stretched_grid_moments_converge_at_second_order():
     assert orders.min() > 1.8, orders
 
 
+def test_stretched_grid_moments_converge_at_second_order_3d():
+    rho, U, T = 0.9, (0.3, -0.2, 0.1), 1.1
+    errs = []
+    for n in (32, 64):
+        oc = oracle.OracleCase(wl.stretched(case3d(nv=n, V=6.5), 3.2 / n))
+        m = oc.cell_moments(oc.maxwellian(rho, U, T))
+        errs.append([abs(m["rho"] - rho) / rho, abs(m["T"] - T) / T])
+    errs = np.array(errs)
+    assert np.all(np.log2(errs[0] / errs[1]) > 1.7), errs
+
+
 def test_specular_wall_on_a_stretched_grid():
     """alpha = 0 on an axis-aligned wall, a symmetric stretched grid: every
     mirrored velocity is a node (found by bisection), so f*_w is the exact
@@ -797,6 +831,17 @@ def test_closed_box_conserves_mass():
     assert abs(m1 - m0) < 1e-13 * m0
     # the lid has set the gas in motion and the walls have changed its energy
     assert np.abs(f[:, :, 0] @ (w * xi[:, 0])).max() > 1e-3
+
+
+def test_closed_box_conserves_mass_3d():
+    cfg = case3d(n=6, nv=8, V=4.5, L=([0.0] * 3, [1.0] * 3), Kn=1e12)
+    cfg["domain_walls"] = wl.box_walls(3, 0.9, lid=(0.3, 0.1), lid_T=1.2)
+    oc = oracle.OracleCase(cfg)
+    xi, w = oc.velocities()
+    m0 = np.sum(oc.get_f()[:, :, 0] @ w)
+    oc.step(10)
+    m1 = np.sum(oc.get_f()[:, :, 0] @ w)
+    assert abs(m1 - m0) < 1e-13 * m0
 
 
 @pytest.mark.parametrize("Uw", [0.0, 0.4])
