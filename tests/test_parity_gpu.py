@@ -322,12 +322,16 @@ def test_wall_quantities_without_a_body_or_a_free_stream():
 # optional nonnegative ghost values (reading C26)
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_nonnegative_ghost_values_against_the_oracle(precision):
-    """A supersonic cylinder at the hot wall of Sec. 4.4, where thousands of
-    ghost values would be negative: with the option, against the oracle."""
-    case = wl._case(2, 48, 4.0, 16, 7.29, 0.03, 3.834, wl.circle(0.5, Tw=5.9), precision=precision,
-                    ghost_nonneg=1)
+@pytest.mark.parametrize("dim,precision", [(2, "fp64"), (2, "mixed"), (3, "fp64")])
+def test_nonnegative_ghost_values_against_the_oracle(dim, precision):
+    """A supersonic cylinder (sphere in 3D) at the hot wall of Sec. 4.4, where
+    many ghost values would be negative: with the option, against the oracle."""
+    if dim == 2:
+        case = wl._case(2, 48, 4.0, 16, 7.29, 0.03, 3.834, wl.circle(0.5, Tw=5.9), precision=precision,
+                        ghost_nonneg=1)
+    else:
+        case = wl._case(3, 14, 2.0, 8, 7.29, 0.03, 3.834, wl.sphere(0.6, Tw=5.9), precision=precision,
+                        ghost_nonneg=1)
     g, o, _, _ = pair(case, 4)
     if precision == "fp64":
         compare(g, o)
