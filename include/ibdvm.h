@@ -218,10 +218,22 @@ ibdvm_status ibdvm_set_f(ibdvm_ctx *ctx, const double *f);
 
 /* State transfer in the storage precision and layout: f[cell][k_padded][comp]
    of double (FP64) or float (mixed); bytes must equal
-   ncell * nvel_padded * ncomp * sizeof(element).  Pinned host memory makes
-   these copies asynchronous-capable; they complete before returning. */
+   ncell * nvel_padded * ncomp * sizeof(element).  Velocity k (natural order,
+   x index fastest) sits at position pos[k] of ibdvm_velocity_positions; the
+   other positions are padding, zero in every state the library writes.
+   Pinned host memory makes these copies asynchronous-capable; they complete
+   before returning. */
 ibdvm_status ibdvm_get_f_native(ibdvm_ctx *ctx, void *host, size_t bytes);
 ibdvm_status ibdvm_set_f_native(ibdvm_ctx *ctx, const void *host, size_t bytes);
+
+/* The native position of every velocity: pos[nvel] (caller-owned) receives,
+   for velocity k in the natural order of the velocity grid, its index in
+   [0, nvel_padded) along the velocity axis of the native layout.  It is k
+   itself, except for 3D cases in FP32 storage with the TMA sweep, which store
+   the velocities grouped by the signs of their components (octants, each
+   padded to whole sweep chunks) so that every chunk has one upwind direction
+   per axis.  A layout choice of this library; the paper prescribes none. */
+ibdvm_status ibdvm_velocity_positions(const ibdvm_ctx *ctx, int *pos);
 
 /* The ghost band of the current state (Sec. 3.2.1 steps 1-4) for every link:
    incident distribution at the intersect point fiw, wall distribution fstarw,

@@ -139,7 +139,7 @@ void ensure_capacity(ibdvm_batch *b) {
 }
 
 int member_kpt(const ibdvm_batch *b, const ibdvm_ctx *ctx) {
-  if (ctx->dim == 3) return 4; // the 3D sweep takes 128-velocity chunks
+  if (ctx->dim == 3) return 0; // the 3D sweep takes the chunks of the context's octant layout
   const int want = (b->kpt == 2) ? 2 : 4;
   return (want == 4 && tma_batch_kpt_max(ctx) == 4) ? 4 : 2;
 }
@@ -157,7 +157,8 @@ void build(ibdvm_batch *b) {
   std::vector<int> kpt(n), nchunk(n);
   for (size_t i = 0; i < n; ++i) {
     kpt[i] = member_kpt(b, b->members[i]);
-    nchunk[i] = b->members[i]->nvp / (32 * kpt[i]);
+    const ibdvm_ctx *ctx = b->members[i];
+    nchunk[i] = (ctx->dim == 3) ? ctx->tma_nchunk : ctx->nvp / (32 * kpt[i]);
   }
   bcheck(b, group_build(b->members, nchunk, b->d_res, b->d_flags, b->d_forces, b->gt, b->stream),
          "build the grouped launch tables");

@@ -127,6 +127,9 @@ void free_all(ibdvm_ctx *ctx) {
   cfree(ctx->finf);
   cfree_t(ctx->xiD);
   cfree_t(ctx->wD);
+  cfree_t(ctx->kst);
+  cfree_t(ctx->oct_const);
+  cfree_t(ctx->oct_sign);
   cfree_t(ctx->ctype);
   cfree_t(ctx->cmask);
   cfree_t(ctx->partf);
@@ -200,7 +203,7 @@ void upload_body(ibdvm_ctx *ctx) {
     for (int b = 0; b < D; ++b)
       if (b != L.axis) S *= G.dx[b];
     ld[6] = S;
-    std::copy(G.wg.begin() + l * G.nv, G.wg.begin() + (l + 1) * G.nv, l_wg.begin() + l * nvp);
+    for (int i = 0; i < G.nv; ++i) l_wg[l * nvp + ctx->kst_h[i]] = G.wg[l * G.nv + i];
   }
   // surface entries: neighbour codes and the vectors of the weights and slopes
   const int mode = (G.gas.flags & IBDVM_RHAT_GHOST_TO_FLUID) ? 2 : 1;
@@ -330,7 +333,7 @@ void upload_body(ibdvm_ctx *ctx) {
         const double c = G.xi[3 * k + a] - G.body.U_w[a];
         c2 += c * c;
       }
-      gw[k] = norm * std::exp(-c2 / Tw);
+      gw[ctx->kst_h[k]] = norm * std::exp(-c2 / Tw);
     }
     upload(ctx, ctx->gw_unit, gw, "upload wall Maxwellian");
   }
@@ -548,6 +551,22 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     ctx->nv = G.nv;
     ctx->nvp = G.nvp;
     ctx->ncell = G.ncell;
+    // the stored order of the velocities: natural, or grouped by octant for
+    // the 3D TMA sweep (IBDVM_NO_TMA=1 keeps the plain sweep and the natural order)
+    const char *no_tma = std::getenv("IBDVM_NO_TMA");
+    const bool tma_off = no_tma && no_tma[0] == '1';
+    ctx->kst_h.resize(G.nv);
+    for (int i = 0; i < G.nv; ++i) ctx->kst_h[i] = i;
+    if (!tma_off && G.dim == 3 && gas->precision == IBDVM_MIXED) {
+      std::vector<int> kst;
+      int nvp = 0;
+      const int kc = tma3_octant_layout(G, kst, nvp);
+      if (kc > 0) {
+        ctx->oct_kc = kc;
+        ctx->kst_h = std::move(kst);
+        ctx->nvp = nvp;
+      }
+    }
     ctx->esize = (ctx->precision == IBDVM_FP64) ? sizeof(double) : sizeof(float);
     // velocity chunks: one chunk per cell unless the grid is too small to fill the GPU
     const long long cell_blocks = (ctx->ncell + 3) / 4;
@@ -585,9 +604,18 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     check(ctx, cudaMemsetAsync(ctx->d_step_forces, 0, 4 * sizeof(double), ctx->stream), "clear");
     ctx->ctype = dalloc<uint8_t>(ctx, ctx->ncell, "cell classes");
     ctx->cmask = dalloc<uint8_t>(ctx, ctx->ncell, "cell flags");
-    // the TMA sweep for 2D FP32 cases (IBDVM_NO_TMA=1 keeps the plain sweep)
-    const char *no_tma = std::getenv("IBDVM_NO_TMA");
-    const bool tma_off = no_tma && no_tma[0] == '1';
+    ctx->kst = dalloc<int>(ctx, G.nv, "velocity positions");
+    upload(ctx, ctx->kst, ctx->kst_h, "upload velocity positions");
+    if (ctx->oct_kc) {
+      std::vector<float> vconst;
+      std::vector<uint8_t> sign;
+      tma3_octant_tables(G, ctx->kst_h, ctx->nvp, ctx->oct_kc, vconst, sign);
+      ctx->oct_const = dalloc<float>(ctx, vconst.size(), "velocity constants");
+      ctx->oct_sign = dalloc<uint8_t>(ctx, sign.size(), "chunk signs");
+      upload(ctx, ctx->oct_const, vconst, "upload velocity constants");
+      upload(ctx, ctx->oct_sign, sign, "upload chunk signs");
+    }
+    // the TMA sweeps of FP32 cases
     if (!tma_off && (tma_sweep_applicable(ctx) || tma3_sweep_applicable(ctx))) {
       const bool two = G.dim == 2;
       ctx->tma_nchunk = two ? tma_sweep_nchunk(ctx) : tma3_sweep_nchunk(ctx);
@@ -599,12 +627,20 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
       ctx->tma_ok = true;
     }
     // velocity tables
+    // (stored positions; padding positions hold zeros)
     std::vector<double> xi3(3 * static_cast<size_t>(ctx->nvp), 0.0), w(ctx->nvp, 0.0);
-    for (int k = 0; k < G.nv; ++k) {
-      for (int a = 0; a < 3; ++a) xi3[a * static_cast<size_t>(ctx->nvp) + k] = G.xi[3 * k + a];
-      w[k] = G.w[k];
+    for (int i = 0; i < G.nv; ++i) {
+      const size_t k = ctx->kst_h[i];
+      for (int a = 0; a < 3; ++a) xi3[a * static_cast<size_t>(ctx->nvp) + k] = G.xi[3 * i + a];
+      w[k] = G.w[i];
     }
-    std::vector<double> finf = maxwellian(G, gas->rho_inf, G.Uinf, gas->T_inf);
+    std::vector<double> finf(static_cast<size_t>(ctx->nvp) * G.ncomp, 0.0);
+    {
+      const std::vector<double> nat = maxwellian(G, gas->rho_inf, G.Uinf, gas->T_inf);
+      for (int i = 0; i < G.nv; ++i)
+        for (int m = 0; m < G.ncomp; ++m)
+          finf[static_cast<size_t>(ctx->kst_h[i]) * G.ncomp + m] = nat[static_cast<size_t>(i) * G.ncomp + m];
+    }
     ctx->xiD = dalloc<double>(ctx, xi3.size(), "velocities");
     ctx->wD = dalloc<double>(ctx, w.size(), "weights");
     upload(ctx, ctx->xiD, xi3, "upload velocities");
@@ -930,6 +966,12 @@ ibdvm_status ibdvm_set_f_native(ibdvm_ctx *ctx, const void *host, size_t bytes) 
   IBDVM_END
 }
 
+ibdvm_status ibdvm_velocity_positions(const ibdvm_ctx *ctx, int *pos) {
+  if (!ctx || !pos) return IBDVM_E_INVAL;
+  std::copy(ctx->kst_h.begin(), ctx->kst_h.end(), pos);
+  return IBDVM_OK;
+}
+
 ibdvm_status ibdvm_ghost_band(ibdvm_ctx *ctx, double *fiw, double *fstarw, double *fstargc, double *rhow) {
   IBDVM_GUARD(ctx)
   const size_t nl = ctx->nlink;
@@ -955,7 +997,7 @@ ibdvm_status ibdvm_ghost_band(ibdvm_ctx *ctx, double *fiw, double *fstarw, doubl
     for (size_t l = 0; l < nl; ++l)
       for (size_t k = 0; k < nv; ++k)
         for (size_t m = 0; m < nc; ++m) {
-          size_t src = (l * nvp + k) * nc + m, dst = (l * nv + k) * nc + m;
+          size_t src = (l * nvp + ctx->kst_h[k]) * nc + m, dst = (l * nv + k) * nc + m;
           if (fiw) fiw[dst] = val(hi, src);
           if (fstarw) fstarw[dst] = hs[src];
           if (fstargc) fstargc[dst] = val(hg, src);
@@ -1146,7 +1188,13 @@ size_t estimate_ctx_bytes(const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *v
   std::string err;
   if (!build_grid(*grid, *vgrid, *gas, G, err)) return 0;
   const size_t es = (gas->precision == IBDVM_FP64) ? 8 : 4;
-  const size_t nc = static_cast<size_t>(G.ncell), nvp = static_cast<size_t>(G.nvp);
+  size_t nvp = static_cast<size_t>(G.nvp);
+  if (G.dim == 3 && gas->precision == IBDVM_MIXED) { // the octant layout of the 3D TMA sweep
+    std::vector<int> kst;
+    int np = 0;
+    if (tma3_octant_layout(G, kst, np) > 0) nvp = static_cast<size_t>(np);
+  }
+  const size_t nc = static_cast<size_t>(G.ncell);
   const int D = G.dim, NW = D + 2, NM = nmoments(D);
   size_t b = 2 * nc * nvp * G.ncomp * es;                               // f^n, f^{n+1}
   b += nc * (nvp / 64 + 1) * 4 * NM;                                     // FP32 moment partial sums

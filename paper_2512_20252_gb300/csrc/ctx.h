@@ -60,9 +60,18 @@ struct ibdvm_ctx {
   int nresblk = 0;
   double *d_res = nullptr;   // residual scalar
   int *d_flags = nullptr;
-  // velocity tables
+  // velocity tables, indexed by the stored position of a velocity
   void *xiT = nullptr, *wT = nullptr, *finf = nullptr;
   double *xiD = nullptr, *wD = nullptr;
+  // stored position of every velocity in its natural order (x index fastest):
+  // the identity, or, for the octant layout of the 3D FP32 sweep, velocities
+  // grouped by the signs of their components with each group padded to a
+  // whole number of sweep chunks (padding positions hold zero weight and zero f)
+  int *kst = nullptr;          // [nv] device
+  std::vector<int> kst_h;      // [nv] host copy
+  int oct_kc = 0;              // octant layout: velocities per sweep chunk (0: natural order)
+  float *oct_const = nullptr;  // octant layout: per stored velocity |a_x|, |a_y|, |a_z|, w (FP32)
+  uint8_t *oct_sign = nullptr; // octant layout: per chunk, bit a set when component a is negative
   // cell tables
   uint8_t *ctype = nullptr;
   uint8_t *cmask = nullptr;  // per cell: ghost neighbour per face (bit 2a + (s > 0)), 64 = not fluid
@@ -144,7 +153,14 @@ bool tma_sweep_applicable(const ibdvm_ctx *ctx);
 int tma_sweep_nchunk(const ibdvm_ctx *ctx);
 cudaError_t tma_sweep_prepare(ibdvm_ctx *ctx);
 cudaError_t tma_sweep_launch(ibdvm_ctx *ctx);
-// TMA sweep of 3D FP32 cases (sweep3d_tma.cu)
+// TMA sweep of 3D FP32 cases (sweep3d_tma.cu).  The sweep takes velocity
+// chunks whose components have one sign each: tma3_octant_layout gives the
+// stored position of every velocity of G (natural order), the padded count and
+// the chunk size (0 when the sweep is not available on this device);
+// tma3_octant_tables fills the per-velocity constants and per-chunk signs.
+int tma3_octant_layout(const Geom &G, std::vector<int> &kst, int &nvp);
+void tma3_octant_tables(const Geom &G, const std::vector<int> &kst, int nvp, int kc,
+                        std::vector<float> &vconst, std::vector<uint8_t> &sign);
 bool tma3_sweep_applicable(const ibdvm_ctx *ctx);
 int tma3_sweep_nchunk(const ibdvm_ctx *ctx);
 cudaError_t tma3_sweep_prepare(ibdvm_ctx *ctx);

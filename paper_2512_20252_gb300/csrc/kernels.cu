@@ -137,6 +137,7 @@ template <typename T> struct SweepArgs {
   const int *__restrict__ dslot;
   const int *__restrict__ dlinks;
   const T *__restrict__ lval; // [nlink][nvp][NC]
+  const int *__restrict__ kst; // [nv] stored position of each velocity (natural order)
   double *__restrict__ part;  // [nchunk][NM][ncell]
   long long ncell;
   int n[3];
@@ -209,8 +210,9 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
     const T pre = M[c * kMac + kPre], invT = M[c * kMac + kInvT], halfT = M[c * kMac + kHalfT];
     const T shA = M[c * kMac + kShA], dtau = M[c * kMac + kDtTau];
     for (int j = 0; j < A.kloop; ++j) {
-      const int k = (chunk * A.kloop + j) * kThreadsPerCell + tx;
-      if (k >= A.nv) break;
+      const int iv = (chunk * A.kloop + j) * kThreadsPerCell + tx;
+      if (iv >= A.nv) break;
+      const int k = A.kst[iv];
       T fc[NC];
       load_nc<T, NC>(A.f + ((size_t)c * A.nvp + k) * NC, fc);
       T cv[3] = {T(0), T(0), T(0)};
@@ -422,8 +424,8 @@ __global__ void __launch_bounds__(32 * kMomWarps, (D == 2 && sizeof(T) == 4) ? 4
 #pragma unroll
         for (int j = 0; j < VPL; ++j) {
           const int k = v * VPL + j;
-          const bool live = k < A.nv; // padded velocities hold no mass
           const T wk = A.w[k];
+          const bool live = wk != T(0); // padding positions hold no mass
           const T wh = live ? wk * e[j * NC] : T(0);
           const T wb = (D == 2 && live) ? wk * e[j * NC + NC - 1] : T(0);
           T cv[3] = {T(0), T(0), T(0)};
@@ -680,6 +682,7 @@ template <typename T> struct GhostArgs {
   const int *__restrict__ s_int;    // [nsurf][8]: cell, codes of the 6 face neighbours
   const double *__restrict__ s_dbl; // [nsurf][8]: r (weights), |r|, x_j - x_g, 1 / |r|
   const double *__restrict__ gwu;   // [nvp] unit-density wall Maxwellian
+  const int *__restrict__ kst;      // [nv] stored position of each velocity (natural order)
   T *__restrict__ lval;
   T *__restrict__ fi;
   T *__restrict__ fsp;
@@ -748,16 +751,18 @@ __device__ __forceinline__ bool mirror_bracket(const GhostArgs<T> &G, int a, dou
   if (G.nodes_rule) {
     const int stride = (a == 0) ? 1 : (a == 1 ? G.nvx[0] : G.nvx[0] * G.nvx[1]);
     const double *xa = G.xiD + (size_t)a * G.nvp;
-    if (x < xa[0] || x > xa[(size_t)(n - 1) * stride]) return false;
+    // node i of the axis is the velocity of natural index i * stride
+    auto node = [&](int i) { return xa[G.kst[i * stride]]; };
+    if (x < node(0) || x > node(n - 1)) return false;
     int lo = 0, hi = n - 1;
     while (hi - lo > 1) {
       const int mid = (lo + hi) / 2;
-      if (xa[(size_t)mid * stride] <= x)
+      if (node(mid) <= x)
         lo = mid;
       else
         hi = mid;
     }
-    const double xl = xa[(size_t)lo * stride], xh = xa[(size_t)hi * stride];
+    const double xl = node(lo), xh = node(hi);
     i0 = lo;
     t = (x - xl) / (xh - xl);
     return true;
@@ -784,7 +789,8 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
   const double alpha = G.accom;
   const double *wgl = G.l_wg + (size_t)l * G.nvp;
   double Nsum = 0.0, Dsum = 0.0;
-  for (int k = threadIdx.x; k < G.nv; k += blockDim.x) {
+  for (int iv = threadIdx.x; iv < G.nv; iv += blockDim.x) {
+    const int k = G.kst[iv];
     // upwind weights, Eq. upwind (FP64 for the exact-zero decision in the FP64 path)
     T xiT[3];
     for (int a = 0; a < D; ++a) xiT[a] = G.xiT[a * G.nvp + k];
@@ -856,7 +862,8 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
   double Ssum = 0.0;
   if (alpha < 1.0) {
     // specular part: f^i at the mirrored velocity by multilinear interpolation
-    for (int k = threadIdx.x; k < G.nv; k += blockDim.x) {
+    for (int iv = threadIdx.x; iv < G.nv; iv += blockDim.x) {
+      const int k = G.kst[iv];
       double xn = 0.0;
       for (int a = 0; a < D; ++a) xn += G.xiD[a * G.nvp + k] * nw[a];
       double xm[3];
@@ -876,7 +883,7 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
             id[a] = i0[a] + b;
             wt *= b ? t[a] : 1.0 - t[a];
           }
-          int kk = id[0] + G.nvx[0] * (id[1] + G.nvx[1] * id[2]);
+          const int kk = G.kst[id[0] + G.nvx[0] * (id[1] + G.nvx[1] * id[2])];
           v += wt * (double)G.fi[((size_t)l * G.nvp + kk) * NC];
         }
       Ssum += (G.wD[k] - wgl[k]) * xn * v;
@@ -886,7 +893,8 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
   const double rho_w = (alpha > 0.0) ? -(N + (1.0 - alpha) * S) / (alpha * Dd) : 0.0;
   if (threadIdx.x == 0) G.rhow[l] = rho_w;
   // wall distribution (Eqs. general bc, Maxwell BC, fwc) and ghost value (Eq. extrapolation 2)
-  for (int k = threadIdx.x; k < G.nv; k += blockDim.x) {
+  for (int iv = threadIdx.x; iv < G.nv; iv += blockDim.x) {
+    const int k = G.kst[iv];
     double xn = 0.0;
     for (int a = 0; a < D; ++a) xn += G.xiD[a * G.nvp + k] * nw[a];
     const double Gw = G.gwu[k];
@@ -910,7 +918,7 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
             id[a] = i0[a] + b;
             wt *= b ? t[a] : 1.0 - t[a];
           }
-          int kk = id[0] + G.nvx[0] * (id[1] + G.nvx[1] * id[2]);
+          const int kk = G.kst[id[0] + G.nvx[0] * (id[1] + G.nvx[1] * id[2])];
 #pragma unroll
           for (int m = 0; m < NC; ++m) fsv[m] += wt * (double)G.fi[((size_t)l * G.nvp + kk) * NC + m];
         }
@@ -947,6 +955,7 @@ template <typename T> struct DomainArgs {
   const double *__restrict__ xiD; // [3][nvp]
   const double *__restrict__ wD;  // [nvp]
   T *__restrict__ whalo;          // [slots][nvp][NC]
+  const int *__restrict__ kst;    // [nv] stored position of each velocity (natural order)
   long long off[7];               // first slot of each face; off[6] = all slots
   int mask;
   int n[3];
@@ -985,7 +994,8 @@ template <typename T, int D> __global__ void __launch_bounds__(kDomainThreads) d
   const double Tw = A.Tw[i];
   const double norm = (D == 2) ? 1.0 / (kPi * Tw) : 1.0 / pow(kPi * Tw, 1.5);
   double so = 0.0, si = 0.0;
-  for (int k = threadIdx.x; k < A.nv; k += blockDim.x) {
+  for (int iv = threadIdx.x; iv < A.nv; iv += blockDim.x) {
+    const int k = A.kst[iv];
     const double xs = s * A.xiD[a * A.nvp + k];
     if (xs > 0.0) {
       so += A.wD[k] * xs * (double)fc[(size_t)k * NC];
@@ -1002,7 +1012,7 @@ template <typename T, int D> __global__ void __launch_bounds__(kDomainThreads) d
   const double in = block_sum<kDomainThreads>(si, sh);
   const double rho_w = -out / in;
   for (int k = threadIdx.x; k < A.nvp; k += blockDim.x) {
-    const double xs = (k < A.nv) ? s * A.xiD[a * A.nvp + k] : 0.0;
+    const double xs = s * A.xiD[a * A.nvp + k]; // zero at padding positions
     if (xs < 0.0) {
       double c2 = 0.0;
       for (int b = 0; b < D; ++b) {
@@ -1028,6 +1038,7 @@ struct WallArgs {
   const double *__restrict__ xiD;   // [3][nvp]
   const double *__restrict__ wD;    // [nvp]
   const double *__restrict__ l_dbl; // [nlink][8]; the wall normal at 3..5
+  const int *__restrict__ kst;      // [nv] stored position of each velocity (natural order)
   double *__restrict__ out;         // [nlink][kWallCols]
   int nv, nvp;
   double Tw, Uw[3];
@@ -1048,7 +1059,8 @@ template <int D> __global__ void __launch_bounds__(kWallThreads) wall_kernel(Wal
   const int l = blockIdx.x;
   const double *fs = A.fstar + (size_t)l * A.nvp * NC;
   double s0 = 0.0, s1[3] = {0.0, 0.0, 0.0};
-  for (int k = threadIdx.x; k < A.nv; k += blockDim.x) {
+  for (int iv = threadIdx.x; iv < A.nv; iv += blockDim.x) {
+    const int k = A.kst[iv];
     const double wh = A.wD[k] * fs[(size_t)k * NC];
     s0 += wh;
 #pragma unroll
@@ -1061,7 +1073,8 @@ template <int D> __global__ void __launch_bounds__(kWallThreads) wall_kernel(Wal
   double se = 0.0, sp[NP], sq[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int i = 0; i < NP; ++i) sp[i] = 0.0;
-  for (int k = threadIdx.x; k < A.nv; k += blockDim.x) {
+  for (int iv = threadIdx.x; iv < A.nv; iv += blockDim.x) {
+    const int k = A.kst[iv];
     const double h = fs[(size_t)k * NC], b = (NC == 2) ? fs[(size_t)k * NC + 1] : 0.0;
     double c[3], c2 = 0.0;
 #pragma unroll
@@ -1144,7 +1157,8 @@ __device__ __forceinline__ void forces_body(const ForceArgs<T> &A, const int l) 
   ijk[1] = (d / S.n[0]) % S.n[1];
   ijk[2] = d / (S.n[0] * S.n[1]);
   double acc[4] = {0, 0, 0, 0};
-  for (int k = threadIdx.x; k < S.nv; k += blockDim.x) {
+  for (int iv = threadIdx.x; iv < S.nv; iv += blockDim.x) {
+    const int k = S.kst[iv];
     const double xin = A.xiD[a * S.nvp + k] * sf; // velocity into the solid
     if (xin == 0.0) continue;
     T fd[NC], fg[NC], face[NC];
@@ -1277,16 +1291,18 @@ __global__ void init_state_kernel(T *__restrict__ f0, T *__restrict__ f1, const 
   }
 }
 
-// dense FP64 [cells][nv][NC] <-> padded state [cells][nvp][NC] for a range of cells
+// dense FP64 [cells][nv][NC] in the natural velocity order <-> the state
+// [cells][nvp][NC] at the stored positions, for a range of cells
 template <typename T>
-__global__ void convert_kernel(T *__restrict__ state, double *__restrict__ dense, long long c0,
-                               long long ncells, int nv, int nvp, int NC, int to_state) {
+__global__ void convert_kernel(T *__restrict__ state, double *__restrict__ dense, const int *__restrict__ kst,
+                               long long c0, long long ncells, int nv, int nvp, int NC, int to_state) {
   const long long total = ncells * (long long)nv * NC;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long cell = i / ((long long)nv * NC);
     const long long r = i % ((long long)nv * NC);
-    const size_t si = ((size_t)(c0 + cell) * nvp) * NC + r;
+    const int iv = (int)(r / NC), m = (int)(r % NC);
+    const size_t si = ((size_t)(c0 + cell) * nvp + kst[iv]) * NC + m;
     if (to_state)
       state[si] = (T)dense[i];
     else
@@ -1320,6 +1336,7 @@ template <typename T> SweepArgs<T> sweep_args(const ibdvm_ctx *ctx, int update, 
   A.dslot = ctx->dslot;
   A.dlinks = ctx->dlinks;
   A.lval = static_cast<const T *>(ctx->lval);
+  A.kst = ctx->kst;
   A.part = ctx->part;
   A.ncell = ctx->ncell;
   for (int a = 0; a < 3; ++a) {
@@ -1403,6 +1420,7 @@ template <typename T> GhostArgs<T> ghost_args(const ibdvm_ctx *ctx, int cur, dou
   G.s_int = ctx->s_int;
   G.s_dbl = ctx->s_dbl;
   G.gwu = ctx->gw_unit;
+  G.kst = ctx->kst;
   G.lval = static_cast<T *>(ctx->lval);
   G.fi = static_cast<T *>(ctx->fi_scr);
   G.fsp = static_cast<T *>(ctx->fsp_scr);
@@ -1439,6 +1457,7 @@ template <typename T, int D> cudaError_t domain_t(ibdvm_ctx *ctx) {
   A.xiD = ctx->xiD;
   A.wD = ctx->wD;
   A.whalo = static_cast<T *>(ctx->whalo);
+  A.kst = ctx->kst;
   for (int i = 0; i < 7; ++i) A.off[i] = ctx->wall_off[i];
   A.mask = ctx->wall_mask;
   for (int a = 0; a < 3; ++a) A.n[a] = g.n[a];
@@ -1620,6 +1639,7 @@ cudaError_t launch_wall(ibdvm_ctx *ctx, const double *fstar, double *out) {
   A.xiD = ctx->xiD;
   A.wD = ctx->wD;
   A.l_dbl = ctx->l_dbl;
+  A.kst = ctx->kst;
   A.out = out;
   A.nv = ctx->nv;
   A.nvp = ctx->nvp;
@@ -1670,10 +1690,10 @@ cudaError_t launch_convert(ibdvm_ctx *ctx, double *dense, long long c0, long lon
   const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
   if (total == 0) return cudaSuccess;
   if (ctx->precision == IBDVM_FP64)
-    convert_kernel<double><<<grid, 256, 0, ctx->stream>>>(static_cast<double *>(ctx->f[ctx->cur]), dense, c0,
+    convert_kernel<double><<<grid, 256, 0, ctx->stream>>>(static_cast<double *>(ctx->f[ctx->cur]), dense, ctx->kst, c0,
                                                           ncells, ctx->nv, ctx->nvp, ctx->ncomp, to_state);
   else
-    convert_kernel<float><<<grid, 256, 0, ctx->stream>>>(static_cast<float *>(ctx->f[ctx->cur]), dense, c0,
+    convert_kernel<float><<<grid, 256, 0, ctx->stream>>>(static_cast<float *>(ctx->f[ctx->cur]), dense, ctx->kst, c0,
                                                          ncells, ctx->nv, ctx->nvp, ctx->ncomp, to_state);
   return cudaGetLastError();
 }

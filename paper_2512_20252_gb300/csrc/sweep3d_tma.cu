@@ -4,28 +4,36 @@
 // Same arithmetic as sweep_kernel in kernels.cu (Sec. 2.2 Eqs. reconstruction
 // and limiter, the Shakhov equilibrium of Sec. 2.1 in the non-dimensional
 // form of Sec. 4, forward Euler, Eqs. moments1-3 by quadrature), organised for
-// GB300:
+// GB300 around the octant layout of the velocities:
 //
+//   * velocities are stored grouped by the signs of their three components,
+//     each group padded to a whole number of chunks of KC = 32 VPL velocities,
+//     so every velocity of a chunk has the same upwind direction along x, y
+//     and z: the upwind halo side, the inflow faces and the march direction
+//     are the same for the whole block, and no per-velocity selection remains;
 //   * a block owns a 4 x 4 tile of (x, y) columns of cells (16 warps, one per
-//     column) and a chunk of KC = 32 * KPT velocities (lane l owns the pairs of
-//     neighbouring velocities 2 l + 64 j, 2 l + 64 j + 1), and marches along z;
-//     every per-velocity operation works on such a pair with Blackwell's packed
-//     FP32 instructions (__ffma2_rn and friends) and 64-bit loads and stores;
-//   * every z plane of the block arrives in shared memory as a cross-shaped
-//     slab: the 4 x 4 tile and two halo strips of two cells on each side in x
-//     and in y (48 cells x KC velocities), five TMA tensor copies
-//     (cp.async.bulk.tensor.4d) on one mbarrier per stage of a 5-stage ring;
-//   * each lane keeps its column's z stencil in registers (f at planes z..z+2
-//     and the reconstructed faces of planes z-1..z+1);
-//   * a face is f + s vl(f - f_lo, f_hi - f) with s the sign of the velocity
-//     (the van Leer half slope is symmetric and odd), so no face is selected;
-//   * x and y faces are exchanged through shared memory: every warp publishes
-//     the downwind faces of its cell; the faces of the halo cells on the
-//     upwind side of the tile are spread over all threads;
-//   * the fourteen moment sums (about the stored bulk velocity) are reduced
-//     over the 32 lanes by a butterfly and written as FP32 partial sums per
-//     velocity chunk; the finalize kernel adds the chunks in FP64.
+//     column) and one chunk; lane l owns the velocities 4 l + 128 g + e
+//     (g < VPL / 4, e < 4), so stage reads, face exchange and stores are
+//     16-byte accesses and the arithmetic runs on pairs of velocities with
+//     Blackwell's packed FP32 instructions (__ffma2_rn and friends);
+//   * the block marches along z in the direction of the chunk's z velocities,
+//     so the z inflow face of a plane is the z outflow face of the previous
+//     one (kept in registers with the z stencil);
+//   * every plane arrives in shared memory by three TMA tensor copies
+//     (cp.async.bulk.tensor.4d) on one mbarrier per stage of a 3-stage ring:
+//     the tile's rows extended by two upwind cells and one downwind cell in x
+//     (one box), and two upwind rows and one downwind row in y (two boxes);
+//   * x and y outflow faces are exchanged through shared memory (two buffers):
+//     while a plane is updated the faces of the next plane are published, so
+//     one block barrier per plane suffices; the faces of the upwind halo cells
+//     (one column in x, one row in y) are spread over the warps;
+//   * the moment sums (about the stored bulk velocity) are accumulated per
+//     lane, reduced over the warp by a butterfly once per plane and written as
+//     FP32 partial sums per chunk; the finalize kernel adds the chunks with a
+//     compensated sum and widens them to FP64.
 //
+// Padding positions of the layout carry zero weight and a huge flux
+// coefficient, so their equilibrium vanishes and their f stays zero.
 // Conditions that hold for a whole warp (ghost neighbours, the domain edge, a
 // cell that is not fluid) select a general path per warp.  Every mbarrier
 // wait is bounded: on timeout the block sets an error flag, drains its copies
@@ -35,6 +43,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <vector>
 
@@ -46,50 +55,49 @@ namespace {
 
 using namespace dev;
 
-constexpr int TX = 4, TY = 4;   // tile of columns, one warp each
-constexpr int NW = TX * TY;     // warps per block
+constexpr int TX = 4, TY = 4;          // tile of columns, one warp each
+constexpr int NW = TX * TY;            // warps per block
 constexpr int NTHREADS = NW * 32;
-constexpr int NST = 5;          // TMA plane stages
-constexpr int NCELL = TX * TY + 2 * (2 * TY) + 2 * (2 * TX); // cells of the cross-shaped slab (48)
-constexpr int NM = 14;          // moment sums (3D)
+constexpr int NST = 3;                 // TMA plane stages
+constexpr int NM = 14;                 // moment sums (3D)
+constexpr int XW = TX + 3;             // an x-extended row of a stage: 2 upwind cells, the tile row, 1 downwind
+constexpr int NSLOT = XW * TY + 3 * TX; // cells of a stage: the extended rows and three y halo rows (40)
+constexpr float kLn2 = 0.693147180559945309f;
+constexpr float kLog2e = 1.442695040888963407f;
+constexpr double kPadSpeed = 1e8; // |xi_a| given to padding positions: their equilibrium is exactly zero
 
-// slot of slab cell (i, j), i in [-2, TX+2), j in [-2, TY+2), cross-shaped
-__device__ __forceinline__ int slot(int i, int j) {
-  if (i >= 0 && i < TX && j >= 0 && j < TY) return j * TX + i;              // centre [y][x]
-  if (i < 0) return TX * TY + j * 2 + (i + 2);                              // x halo low  [y][2]
-  if (i >= TX) return TX * TY + 2 * TY + j * 2 + (i - TX);                  // x halo high [y][2]
-  if (j < 0) return TX * TY + 4 * TY + (j + 2) * TX + i;                    // y halo low  [2][x]
-  return TX * TY + 4 * TY + 2 * TX + (j - TY) * TX + i;                      // y halo high [2][x]
-}
-
-template <int KPT> struct Cfg {
-  static constexpr int KC = 32 * KPT;
-  static constexpr int STAGE_FLOATS = NCELL * KC;
-  static constexpr int STAGE_BYTES = STAGE_FLOATS * 4;
-  static constexpr int PX_FLOATS = (TX + 2) * TY * KC; // x faces: [y][x+1][k]
-  static constexpr int PY_FLOATS = TX * (TY + 2) * KC; // y faces: [y+1][x][k]
-  static constexpr size_t SMEM =
-      (size_t)(NST * STAGE_FLOATS + 2 * (PX_FLOATS + PY_FLOATS) + 4 * KC + 2 * NW * kMac) * 4 +
-      2 * NTHREADS * sizeof(int4) + NST * 8;
+template <int VPL> struct Cfg {
+  static_assert(VPL == 4 || VPL == 8, "four or eight velocities per lane");
+  static constexpr int NG = VPL / 4;            // groups of four consecutive velocities per lane
+  static constexpr int KC = 32 * VPL;           // velocities of a chunk
+  static constexpr int STAGE = NSLOT * KC;      // floats of a plane stage
+  static constexpr int FX = TY * (TX + 2) * KC; // x outflow faces [y][x + 1][k]
+  static constexpr int FY = (TY + 2) * TX * KC; // y outflow faces [y + 1][x][k]
+  static constexpr int CONST = NG * 4 * 128;    // per group and quantity a float4 per lane
+  static constexpr size_t SMEM = (size_t)(NST * STAGE + 2 * FX + 2 * FY + CONST + KC + 2 * NW * kMac) * 4 + NST * 8;
 };
+static_assert(Cfg<8>::SMEM <= 232448, "shared memory of a block");
 
-struct Tma3Args {
+struct Oct3Args {
   float *__restrict__ fn;
   const float *__restrict__ f;
-  const float *__restrict__ mac;  // [ncell][kMac]
-  const float *__restrict__ xi;   // [3][nvp]
-  const float *__restrict__ w;    // [nvp]
-  const float *__restrict__ finf; // [nvp]
+  const float *__restrict__ mac;     // [ncell][kMac]
+  const float *__restrict__ vconst;  // [nvp][4]: |a_x|, |a_y|, |a_z|, w with |a_a| = dt |xi_a| / dx_a
+  const uint8_t *__restrict__ csign; // [nchunk]: bit a when component a of the chunk's velocities is negative
+  const float *__restrict__ finf;    // [nvp]
   const uint8_t *__restrict__ cmask;
   const int *__restrict__ dslot;
   const int *__restrict__ dlinks;
-  const float *__restrict__ lval; // [nlink][nvp]
-  float *__restrict__ part;       // [nchunk][NM][ncell]
+  const float *__restrict__ lval;    // [nlink][nvp]
+  float *__restrict__ part;          // [nchunk][NM][ncell]
   int *__restrict__ err;
   long long ncell;
-  int nx, ny, nz, nvp, nv, zrows;
-  float dt, rdx, rdy, rdz;
+  int nx, ny, nz, nvp, zrows;
+  int kc;       // velocities of a chunk (256 or 128)
+  float sig[3]; // dx_a / dt: |xi_a| = |a_a| sig[a]
 };
+
+enum : uint8_t { kNotFluid = 64 };
 
 __device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
                                         uint64_t *bar) {
@@ -99,603 +107,472 @@ __device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *tm, int c0
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
       : "memory");
 }
-// half the van Leer slope times the cell width from the one-sided differences
-// a = f - f_up and b = f_dn - f along the direction of motion (Eq. limiter)
-__device__ __forceinline__ float vl_half(float a, float b) {
-  const float p = a * b;
-  const float v = p * rcp_approx(a + b);
-  return p > 0.f ? v : 0.f;
+
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+// 2^x (the hardware base-2 exponential)
+__device__ __forceinline__ float ex2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
-// downwind face value: f plus half the slope along the motion
-__device__ __forceinline__ float face(float f, float up, float dn) { return f + vl_half(f - up, dn - f); }
-
-__device__ __forceinline__ float2 lds2(const float *base, int kk) { return *reinterpret_cast<const float2 *>(base + kk); }
-
-__device__ __forceinline__ float link_value(const Tma3Args &A, long long c, int dir, int k) {
+// downwind face f + vl(f - up, dn - f): the upwind cell's value plus half its
+// van Leer slope times the cell width (Eqs. reconstruction and limiter)
+__device__ __forceinline__ float2 face2u(float2 f, float2 up, float2 dn) {
+  return __fadd2_rn(f, vl_half2(sub2(f, up), sub2(dn, f)));
+}
+__device__ __forceinline__ float4 face4(float4 f, float4 up, float4 dn) {
+  return cat4(face2u(lo2(f), lo2(up), lo2(dn)), face2u(hi2(f), hi2(up), hi2(dn)));
+}
+// moment accumulators of a lane: scalars (packed pairs of accumulators cost
+// thirteen more registers, which the block does not have)
+using ACC = float;
+__device__ __forceinline__ void acc_add(float &a, float2 v) { a += v.x + v.y; }
+__device__ __forceinline__ void acc_fma(float &a, float2 u, float2 v) { a = fmaf(u.y, v.y, fmaf(u.x, v.x, a)); }
+__device__ __forceinline__ float acc_value(float a) { return a; }
+__device__ __forceinline__ float4 mean4(float4 a, float4 b) {
+  return make_float4(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z), 0.5f * (a.w + b.w));
+}
+// ghost values of the link across face dir (bit numbering of cmask) of cell c
+// for the four velocities from stored position k
+__device__ __forceinline__ float4 link4(const Oct3Args &A, long long c, int dir, int k) {
   const int s = A.dslot[c];
   const int l = (s >= 0) ? A.dlinks[s * 6 + dir] : -1;
-  return (l >= 0) ? A.lval[(size_t)l * A.nvp + k] : A.finf[k];
-}
-// the link values of velocities k, k + 1 (k even)
-__device__ __forceinline__ float2 link_value2(const Tma3Args &A, long long c, int dir, int k) {
-  const int s = A.dslot[c];
-  const int l = (s >= 0) ? A.dlinks[s * 6 + dir] : -1;
-  return *reinterpret_cast<const float2 *>((l >= 0) ? A.lval + (size_t)l * A.nvp + k : A.finf + k);
+  return *reinterpret_cast<const float4 *>((l >= 0) ? A.lval + (size_t)l * A.nvp + k : A.finf + k);
 }
 
-enum : uint8_t { kNotFluid = 64, kGhostAny = 63 };
-
-template <int KPT> using Ring = float2[KPT / 2];
-
-// Every thread owns two halo faces per plane, both for chunk velocity
-// kk = threadIdx.x % KC: the downwind x face of the upwind x-halo cell of row
-// threadIdx.x / KC, and the downwind y face of the upwind y-halo cell of column
-// threadIdx.x / KC.  All but the cells' flags is the same for every plane and
-// is packed once into shared memory (int4 per face):
-//   x: stage offset of f | (offset of the upwind neighbour + 1) << 16
-//   y: offset of the downwind neighbour + 1 | face buffer offset << 16
-//      (a neighbour offset of 0 after the + 1 means the freestream value)
-//   z: the halo cell's index within a plane, or -1 outside the domain
-template <int KPT> struct March3 {
-  const Tma3Args &A;
-  const CUtensorMap *tc, *tx, *ty; // tensor maps: tile, x halo strip, y halo strip
-  float *stage, *phx, *phy, *sfinf, *sxi, *syi, *smac;
-  uint64_t *full;
-  int warp, lane, ti, tj, x0, y0, x, y, k0, z0, z1, zlast;
-  int st;
-  unsigned pb;
-  bool col_in;
-  long long nc, plane;
-  // per velocity pair: xi, weight, dt |xi_a| / dx_a, sign of xi_a
-  float2 xix[KPT / 2], xiy[KPT / 2], xiz[KPT / 2], wk[KPT / 2], ax[KPT / 2], ay[KPT / 2], az[KPT / 2];
-  float2 sx[KPT / 2], sy[KPT / 2], sz[KPT / 2];
-  uint8_t mask_next;
-  uint16_t hm_next;  // flags of this thread's two halo cells at plane z (x | y << 8)
-  bool abort_local;
-  bool inner_xy;     // the column is fluid-capable away from the x and y domain edges
-  long long nxy;     // cells per plane
-  // running pointers of the current plane z, advanced by one plane per step
-  const uint8_t *cm_plane; // flags of plane z
-  const float *mac_next;   // this lane's parameter of the cell at plane z + 1
-  float *fn_cell;          // f^{n+1} of the own cell, first chunk velocity
-  float *part_cell;        // moment partial sums of the own cell, sum index lane >> 1
-  const int4 *duty; // [2][NTHREADS]: x faces, then y faces
-};
-
-// chunk-local index of the first velocity of pair j of the lane
-template <int KPT> __device__ __forceinline__ int kp(const March3<KPT> &M, int j) { return 2 * M.lane + 64 * j; }
-
-template <int KPT> __device__ __forceinline__ void issue_plane(March3<KPT> &M, int z, int st) {
-  using C = Cfg<KPT>;
-  float *dst = M.stage + st * C::STAGE_FLOATS;
-  uint64_t *bar = &M.full[st];
-  mbar_expect_tx(bar, C::STAGE_BYTES);
-  const int kc = M.k0;
-  tma_box(dst + slot(0, 0) * C::KC, M.tc, kc, M.x0, M.y0, z, bar);
-  tma_box(dst + slot(-2, 0) * C::KC, M.tx, kc, M.x0 - 2, M.y0, z, bar);
-  tma_box(dst + slot(TX, 0) * C::KC, M.tx, kc, M.x0 + TX, M.y0, z, bar);
-  tma_box(dst + slot(0, -2) * C::KC, M.ty, kc, M.x0, M.y0 - 2, z, bar);
-  tma_box(dst + slot(0, TY) * C::KC, M.ty, kc, M.x0, M.y0 + TY, z, bar);
-}
-
-template <int KPT> __device__ __forceinline__ uint8_t cmask3(const March3<KPT> &M, int cx, int cy, int cz) {
-  const Tma3Args &A = M.A;
-  if (cx < 0 || cx >= A.nx || cy < 0 || cy >= A.ny || cz < 0 || cz >= A.nz) return 0;
-  return A.cmask[cx + (long long)A.nx * (cy + (long long)A.ny * cz)];
-}
-
-// downwind face along axis a (0: x, 1: y) of slab cell (i, j) at plane z for
-// chunk velocity kk, general path: domain edge, ghost neighbours, non-fluid
-template <int KPT>
-__device__ __forceinline__ float face_general(const March3<KPT> &M, const float *sp, int a, int i, int j, int z,
-                                              int kk, float xi) {
-  using C = Cfg<KPT>;
-  const Tma3Args &A = M.A;
-  const int cx = M.x0 + i, cy = M.y0 + j;
-  if (cx < 0 || cx >= A.nx || cy < 0 || cy >= A.ny) return M.sfinf[kk]; // halo: freestream, zero slope
-  const uint8_t m = cmask3(M, cx, cy, z);
-  if (m & kNotFluid) return 0.f;
-  const int s = (xi >= 0.f) ? 1 : -1;
-  const int di = (a == 0) ? s : 0, dj = (a == 1) ? s : 0;
-  const float f = sp[slot(i, j) * C::KC + kk];
-  const int ca = (a == 0) ? cx : cy, na = (a == 0) ? A.nx : A.ny;
-  const long long c = cx + (long long)A.nx * (cy + (long long)A.ny * z);
-  float up, dn;
-  // upwind neighbour (against the motion) and downwind neighbour
-  if (m & (1u << (2 * a + (s > 0 ? 0 : 1)))) up = link_value(A, c, 2 * a + (s > 0 ? 0 : 1), M.k0 + kk);
-  else if (ca - s < 0 || ca - s >= na) up = M.sfinf[kk];
-  else up = sp[slot(i - di, j - dj) * C::KC + kk];
-  if (m & (1u << (2 * a + (s > 0 ? 1 : 0)))) dn = link_value(A, c, 2 * a + (s > 0 ? 1 : 0), M.k0 + kk);
-  else if (ca + s < 0 || ca + s >= na) dn = M.sfinf[kk];
-  else dn = sp[slot(i + di, j + dj) * C::KC + kk];
-  return face(f, up, dn);
-}
-
-// the same for the velocity pair at chunk index kk of the own cell (i, j),
-// from the low and high neighbours along the axis and the signs s
-template <int KPT>
-__device__ __forceinline__ float2 face_general2(const March3<KPT> &M, const float *sp, int a, int i, int j, int z,
-                                                int kk, float2 s) {
-  using C = Cfg<KPT>;
-  const Tma3Args &A = M.A;
-  const int cx = M.x0 + i, cy = M.y0 + j;
-  if (cx < 0 || cx >= A.nx || cy < 0 || cy >= A.ny) return lds2(M.sfinf, kk);
-  const uint8_t m = cmask3(M, cx, cy, z);
-  if (m & kNotFluid) return make_float2(0.f, 0.f);
-  const int di = (a == 0) ? 1 : 0, dj = (a == 1) ? 1 : 0;
-  const float2 f = lds2(sp + slot(i, j) * C::KC, kk);
-  const int ca = (a == 0) ? cx : cy, na = (a == 0) ? A.nx : A.ny;
-  const long long c = cx + (long long)A.nx * (cy + (long long)A.ny * z);
-  float2 lo, hi;
-  if (m & (1u << (2 * a))) lo = link_value2(A, c, 2 * a, M.k0 + kk);
-  else if (ca - 1 < 0) lo = lds2(M.sfinf, kk);
-  else lo = lds2(sp + slot(i - di, j - dj) * C::KC, kk);
-  if (m & (1u << (2 * a + 1))) hi = link_value2(A, c, 2 * a + 1, M.k0 + kk);
-  else if (ca + 1 >= na) hi = lds2(M.sfinf, kk);
-  else hi = lds2(sp + slot(i + di, j + dj) * C::KC, kk);
-  return face2(f, lo, hi, s);
-}
-
-// downwind z face of plane r for the own column: fr = f(r), lo = f(r-1), hi = f(r+1)
-template <int KPT>
-__device__ __forceinline__ void phi_z(const March3<KPT> &M, int r, uint8_t m, const Ring<KPT> &fr,
-                                      const Ring<KPT> &lo, const Ring<KPT> &hi, Ring<KPT> &out) {
-  const Tma3Args &A = M.A;
-  if (r < 0 || r >= A.nz || !M.col_in) {
-#pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) out[j] = lds2(M.sfinf, kp(M, j));
-    return;
-  }
-  if (m & kNotFluid) {
-#pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) out[j] = make_float2(0.f, 0.f);
-    return;
-  }
-  if (!(m & 48)) {
-#pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) out[j] = face2(fr[j], lo[j], hi[j], M.sz[j]);
-    return;
-  }
-  const long long c = M.plane + (long long)r * A.nx * A.ny;
-#pragma unroll
-  for (int j = 0; j < KPT / 2; ++j) {
-    const float2 l = (m & 16) ? link_value2(A, c, 4, M.k0 + kp(M, j)) : lo[j];
-    const float2 h = (m & 32) ? link_value2(A, c, 5, M.k0 + kp(M, j)) : hi[j];
-    out[j] = face2(fr[j], l, h, M.sz[j]);
-  }
-}
-
-// the halo face of axis a owned by this thread at plane z
-// the general halo face of axis a owned by this thread at plane z (not fluid,
-// or a ghost neighbour along the axis)
-template <int KPT, int a>
-__device__ __forceinline__ float halo_face_general(const March3<KPT> &M, const float *sp, int z) {
-  using C = Cfg<KPT>;
-  const int kk = threadIdx.x % C::KC;
-  const float xi = (a == 0) ? M.sxi[kk] : M.syi[kk];
-  const int line = threadIdx.x / C::KC;
-  const int i = (a == 0) ? ((xi >= 0.f) ? -1 : TX) : line;
-  const int j = (a == 0) ? line : ((xi >= 0.f) ? -1 : TY);
-  return face_general(M, sp, a, i, j, z, kk, xi);
-}
-
-// the two halo faces this thread owns at plane z (x, then y), evaluated as one
-// packed pair; hm = the flags of the two halo cells at plane z (or 0 outside)
-template <int KPT>
-__device__ __forceinline__ void halo_faces(const March3<KPT> &M, const float *sp, int z, uint16_t hm, float *phx,
-                                           float *phy) {
-  using C = Cfg<KPT>;
-  const int4 dx = M.duty[threadIdx.x], dy = M.duty[NTHREADS + threadIdx.x];
-  const int kk = threadIdx.x % C::KC;
-  const float fin = M.sfinf[kk];
-  const uint8_t mx = hm & 0xff, my = hm >> 8;
-  // per face: freestream outside the domain, the general path where needed
-  const bool gx = dx.z >= 0 && (mx & (kNotFluid | 3u)), gy = dy.z >= 0 && (my & (kNotFluid | 12u));
-  const int ux = dx.x >> 16, nx = dx.y & 0xffff, uy = dy.x >> 16, ny = dy.y & 0xffff;
-  const float2 f = make_float2(sp[dx.x & 0xffff], sp[dy.x & 0xffff]);
-  const float2 up = make_float2(ux ? sp[ux - 1] : fin, uy ? sp[uy - 1] : fin);
-  const float2 dn = make_float2(nx ? sp[nx - 1] : fin, ny ? sp[ny - 1] : fin);
-  const float2 o = __fadd2_rn(f, vl_half2(sub2(f, up), sub2(dn, f)));
-  phx[dx.y >> 16] = (dx.z < 0) ? fin : (gx ? halo_face_general<KPT, 0>(M, sp, z) : o.x);
-  phy[dy.y >> 16] = (dy.z < 0) ? fin : (gy ? halo_face_general<KPT, 1>(M, sp, z) : o.y);
-}
-
-template <int KPT>
-__device__ __forceinline__ bool plane_step(March3<KPT> &M, int z, int par, uint8_t &mc, Ring<KPT> &Ra,
-                                           Ring<KPT> &Rb, Ring<KPT> &Rc, Ring<KPT> &Pa, Ring<KPT> &Pb,
-                                           Ring<KPT> &Pc) {
-  using C = Cfg<KPT>;
-  const Tma3Args &A = M.A;
-  const long long cell = M.plane + (long long)z * M.nxy;
-  const uint8_t m0 = mc;
-  const bool fluid = !(m0 & kNotFluid);
-  const float pre_next = (M.lane < kMac && M.col_in && z + 1 < A.nz) ? __ldg(M.mac_next) : 0.f;
-  const uint8_t mn = M.mask_next;
-  const uint8_t mn2 = M.col_in ? ((z + 2 < A.nz) ? M.cm_plane[2 * M.nxy + M.plane] : 0) : kNotFluid;
-  const int st = M.st;
-  int st2 = st + 2;
-  unsigned pb2 = M.pb;
-  if (st2 >= NST) {
-    st2 -= NST;
-    pb2 ^= 1u;
-  }
-  // (1) own column at plane z + 2 (the z stencil)
-  if (z + 2 < A.nz && !mbar_wait(&M.full[st2], pb2)) M.abort_local = true;
-  if (z + 2 < A.nz && M.col_in) {
-    const float *src = M.stage + st2 * C::STAGE_FLOATS + slot(M.ti, M.tj) * C::KC;
-#pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) Rc[j] = lds2(src, kp(M, j));
-  } else {
-#pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) Rc[j] = lds2(M.sfinf, kp(M, j));
-  }
-  const float *sp = M.stage + st * C::STAGE_FLOATS;
-  float *phx = M.phx + par * C::PX_FLOATS; // [TY][TX + 2][KC]
-  float *phy = M.phy + par * C::PY_FLOATS; // [TY + 2][TX][KC]
-  // (2) downwind x and y faces of the own cell
-  float2 PX[KPT / 2], PY[KPT / 2];
-  const bool fast = M.inner_xy && fluid && !(m0 & 15);
-  if (fast) {
-    const float *px_lo = sp + slot(M.ti - 1, M.tj) * C::KC, *px_hi = sp + slot(M.ti + 1, M.tj) * C::KC;
-    const float *py_lo = sp + slot(M.ti, M.tj - 1) * C::KC, *py_hi = sp + slot(M.ti, M.tj + 1) * C::KC;
-#pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) {
-      const int kk = kp(M, j);
-      PX[j] = face2(Ra[j], lds2(px_lo, kk), lds2(px_hi, kk), M.sx[j]);
-      PY[j] = face2(Ra[j], lds2(py_lo, kk), lds2(py_hi, kk), M.sy[j]);
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) {
-      PX[j] = face_general2(M, sp, 0, M.ti, M.tj, z, kp(M, j), M.sx[j]);
-      PY[j] = face_general2(M, sp, 1, M.ti, M.tj, z, kp(M, j), M.sy[j]);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < KPT / 2; ++j) {
-    *reinterpret_cast<float2 *>(phx + (M.tj * (TX + 2) + M.ti + 1) * C::KC + kp(M, j)) = PX[j];
-    *reinterpret_cast<float2 *>(phy + ((M.tj + 1) * TX + M.ti) * C::KC + kp(M, j)) = PY[j];
-  }
-  // halo faces on the upwind side of the tile (TY rows in x, TX columns in y)
-  {
-    const uint16_t hm = M.hm_next;
-    // the flags of the two halo cells at the next plane, a plane ahead of use
-    const int hx = M.duty[threadIdx.x].z, hy = M.duty[NTHREADS + threadIdx.x].z;
-    M.hm_next = (z + 1 < A.nz) ? (uint16_t)((hx >= 0 ? M.cm_plane[M.nxy + hx] : 0) |
-                                            ((hy >= 0 ? M.cm_plane[M.nxy + hy] : 0) << 8))
-                               : (uint16_t)0;
-    halo_faces(M, sp, z, hm, phx, phy);
-  }
-  // (3) downwind z face of plane z + 1
-  phi_z(M, z + 1, mn, Rb, Ra, Rc, Pc);
-  // (4) barrier: faces published, the stage of plane z - 1 released
-  if (__syncthreads_or(M.abort_local ? 1 : 0)) return false;
-  if (threadIdx.x == 0 && z + NST - 1 < M.zlast) {
-    fence_proxy_async();
-    issue_plane(M, z + NST - 1, st == 0 ? NST - 1 : st - 1);
-  }
-  // (5) update of the own cell and its moment sums (per velocity pair)
-  float acc[16];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) acc[m] = 0.f;
-  if (fluid) {
-    const float4 *pm = reinterpret_cast<const float4 *>(M.smac + (par * NW + M.warp) * kMac);
-    const float4 p0 = pm[0], p1 = pm[1], p2 = pm[2];
-    const float pre = p0.x, U0 = p0.y, U1 = p0.z, U2 = p0.w;
-    const float invT = p1.x, shA = p1.z, q0 = p1.w;
-    const float q1 = p2.x, q2 = p2.y, dtau = p2.z;
-    const float2 omd = dup(1.f - dtau), dt2 = dup(dtau);
-    const bool ghosty = (m0 & kGhostAny) != 0;
-    const float *xl = phx + (M.tj * (TX + 2) + M.ti) * C::KC, *xr = xl + 2 * C::KC;
-    const float *yl = phy + (M.tj * TX + M.ti) * C::KC, *yr = yl + 2 * TX * C::KC;
-    Ring<KPT> out;
-#pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) {
-      const int kk = kp(M, j);
-      // inflow faces: the upwind neighbour's downwind face, per velocity
-      const float2 fxl = lds2(xl, kk), fxr = lds2(xr, kk), fyl = lds2(yl, kk), fyr = lds2(yr, kk);
-      float2 ix = make_float2(M.sx[j].x > 0.f ? fxl.x : fxr.x, M.sx[j].y > 0.f ? fxl.y : fxr.y);
-      float2 iy = make_float2(M.sy[j].x > 0.f ? fyl.x : fyr.x, M.sy[j].y > 0.f ? fyl.y : fyr.y);
-      float2 iz = make_float2(M.sz[j].x > 0.f ? Pa[j].x : Pc[j].x, M.sz[j].y > 0.f ? Pa[j].y : Pc[j].y);
-      if (ghosty) { // ghost upwind neighbour: mean of its link value and this cell
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int k = M.k0 + kk + e;
-          const float fc = e ? Ra[j].y : Ra[j].x;
-          const int dx = ((e ? M.sx[j].y : M.sx[j].x) > 0.f) ? 0 : 1;
-          const int dy = ((e ? M.sy[j].y : M.sy[j].x) > 0.f) ? 2 : 3;
-          const int dz = ((e ? M.sz[j].y : M.sz[j].x) > 0.f) ? 4 : 5;
-          if (m0 & (1u << dx)) (e ? ix.y : ix.x) = 0.5f * (link_value(A, cell, dx, k) + fc);
-          if (m0 & (1u << dy)) (e ? iy.y : iy.x) = 0.5f * (link_value(A, cell, dy, k) + fc);
-          if (m0 & (1u << dz)) (e ? iz.y : iz.x) = 0.5f * (link_value(A, cell, dz, k) + fc);
-        }
-      }
-      // Shakhov equilibrium g (1 + A c.q (2 c^2/T - 5)) from the stored state
-      const float2 cx = __fadd2_rn(M.xix[j], dup(-U0)), cy = __fadd2_rn(M.xiy[j], dup(-U1)),
-                   cz = __fadd2_rn(M.xiz[j], dup(-U2));
-      const float2 c2 = __ffma2_rn(cx, cx, __ffma2_rn(cy, cy, __fmul2_rn(cz, cz)));
-      const float2 t = __fmul2_rn(c2, dup(invT));
-      const float2 e = __fmul2_rn(dup(pre), make_float2(__expf(-t.x), __expf(-t.y)));
-      const float2 cq = __ffma2_rn(cx, dup(q0), __ffma2_rn(cy, dup(q1), __fmul2_rn(cz, dup(q2))));
-      const float2 g = __ffma2_rn(__fmul2_rn(__fmul2_rn(e, dup(shA)), cq), __ffma2_rn(dup(2.f), t, dup(-5.f)), e);
-      float2 n = __ffma2_rn(Ra[j], omd, __fmul2_rn(dt2, g));
-      n = __ffma2_rn(M.ax[j], sub2(ix, PX[j]), n);
-      n = __ffma2_rn(M.ay[j], sub2(iy, PY[j]), n);
-      n = __ffma2_rn(M.az[j], sub2(iz, Pb[j]), n);
-      out[j] = n;
-      const float2 wf = __fmul2_rn(M.wk[j], n), e2 = __fmul2_rn(c2, wf);
-      const float2 cxw = __fmul2_rn(cx, wf), cyw = __fmul2_rn(cy, wf);
-      const float2 czz = __fmul2_rn(cz, cz);
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const float w1 = e ? wf.y : wf.x, x1 = e ? cx.y : cx.x, y1 = e ? cy.y : cy.x, z1 = e ? cz.y : cz.x;
-        const float xw = e ? cxw.y : cxw.x, yw = e ? cyw.y : cyw.x, ee = e ? e2.y : e2.x;
-        acc[0] += w1;
-        acc[1] += xw;
-        acc[2] += yw;
-        acc[3] = fmaf(z1, w1, acc[3]);
-        acc[4] += ee;
-        acc[5] = fmaf(x1, xw, acc[5]);
-        acc[6] = fmaf(y1, xw, acc[6]);
-        acc[7] = fmaf(z1, xw, acc[7]);
-        acc[8] = fmaf(y1, yw, acc[8]);
-        acc[9] = fmaf(z1, yw, acc[9]);
-        acc[10] = fmaf(e ? czz.y : czz.x, w1, acc[10]);
-        acc[11] = fmaf(x1, ee, acc[11]);
-        acc[12] = fmaf(y1, ee, acc[12]);
-        acc[13] = fmaf(z1, ee, acc[13]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) *reinterpret_cast<float2 *>(M.fn_cell + kp(M, j)) = out[j];
-  }
-  // (6) butterfly of the 16 (14 used) sums over the 32 lanes
-  {
-    const int lane = M.lane;
-    float v8[8];
-    const bool b16 = lane & 16;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float keep = b16 ? acc[8 + i] : acc[i];
-      const float send = b16 ? acc[i] : acc[8 + i];
-      v8[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-    float v4[4];
-    const bool b8 = lane & 8;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float keep = b8 ? v8[4 + i] : v8[i];
-      const float send = b8 ? v8[i] : v8[4 + i];
-      v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    float v2[2];
-    const bool b4 = lane & 4;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float keep = b4 ? v4[2 + i] : v4[i];
-      const float send = b4 ? v4[i] : v4[2 + i];
-      v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    const bool b2 = lane & 2;
-    float v1 = (b2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? v2[0] : v2[1], 2);
-    v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
-    // lane l holds sum index 8 b4(l) + 4 b3(l) + 2 b2(l) + b1(l) = l >> 1
-    if (M.col_in && (lane & 1) == 0 && (lane >> 1) < NM) *M.part_cell = v1;
-  }
-  if (M.lane < kMac) M.smac[((par ^ 1) * NW + M.warp) * kMac + M.lane] = pre_next;
-  M.mask_next = mn2;
-  mc = mn;
-  M.cm_plane += M.nxy;
-  M.mac_next += M.nxy * kMac;
-  M.fn_cell += M.nxy * A.nvp;
-  M.part_cell += M.nxy;
-  if (++M.st == NST) {
-    M.st = 0;
-    M.pb ^= 1u;
-  }
-  return true;
-}
-
-// The march of one block over the tile of columns at (x0, y0), chunk
-// velocities [k0, k0 + KC) and planes [z0, z1).  tm[0..2]: tensor maps of the
-// tile and of the x and y halo strips.  reinit: the block's mbarriers hold an
-// earlier march (all of whose copies have landed) and are invalidated first.
-// Returns false when the block aborted on a timed-out wait.
-template <int KPT>
-__device__ __forceinline__ bool march3d(const Tma3Args &A, const CUtensorMap *tmc, const CUtensorMap *tmx,
-                                        const CUtensorMap *tmy, int x0, int y0, int k0, int z0, int z1,
+// The march of one block over the tile of columns at (x0, y0), chunk `chunk`
+// and planes [za, zb), in the direction of the chunk's z velocities.
+// tm[0..2]: tensor maps of the x-extended rows (TX + 3 cells x TY rows), of a
+// pair of y halo rows and of a single y halo row (TX cells each).  reinit: the
+// block's mbarriers hold an earlier march (all of whose copies have landed)
+// and are invalidated first.  Returns false when the block aborted on a
+// timed-out wait.
+template <int VPL>
+__device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tmx, const CUtensorMap *tmp,
+                                        const CUtensorMap *tms, int x0, int y0, int chunk, int za, int zb,
                                         unsigned char *smem_raw, bool reinit) {
-  using C = Cfg<KPT>;
-  March3<KPT> M{A, tmc, tmx, tmy};
-  M.stage = reinterpret_cast<float *>(smem_raw);
-  M.phx = M.stage + NST * C::STAGE_FLOATS;
-  M.phy = M.phx + 2 * C::PX_FLOATS;
-  M.sfinf = M.phy + 2 * C::PY_FLOATS;
-  M.sxi = M.sfinf + C::KC;
-  M.syi = M.sxi + C::KC;
-  M.smac = M.syi + 2 * C::KC;
-  M.duty = reinterpret_cast<const int4 *>(M.smac + 2 * NW * kMac);
-  M.full = reinterpret_cast<uint64_t *>(const_cast<int4 *>(M.duty) + 2 * NTHREADS);
-  M.warp = threadIdx.x >> 5;
-  M.lane = threadIdx.x & 31;
-  M.ti = M.warp % TX;
-  M.tj = M.warp / TX;
-  M.x0 = x0;
-  M.y0 = y0;
-  M.x = M.x0 + M.ti;
-  M.y = M.y0 + M.tj;
-  M.col_in = M.x < A.nx && M.y < A.ny;
-  M.k0 = k0;
-  M.z0 = z0;
-  M.z1 = z1;
-  M.zlast = min(A.nz, M.z1 + 2);
-  M.nc = A.ncell;
-  M.plane = M.x + (long long)A.nx * M.y;
-  M.nxy = (long long)A.nx * A.ny;
-  M.inner_xy = M.col_in && M.x > 0 && M.x + 1 < A.nx && M.y > 0 && M.y + 1 < A.ny;
-  M.cm_plane = A.cmask + (long long)M.z0 * M.nxy;
-  M.mac_next = A.mac + (M.plane + (long long)(M.z0 + 1) * M.nxy) * kMac + (M.lane < kMac ? M.lane : 0);
-  M.fn_cell = A.fn + (size_t)(M.plane + (long long)M.z0 * M.nxy) * A.nvp + M.k0;
-  M.part_cell = A.part + ((size_t)(M.k0 / C::KC) * NM + ((M.lane >> 1) < NM ? (M.lane >> 1) : 0)) * M.nc + M.plane +
-                (long long)M.z0 * M.nxy;
-  M.st = 0;
-  M.pb = 0;
-  M.abort_local = false;
-#pragma unroll
-  for (int j = 0; j < KPT / 2; ++j) {
-    float v[10][2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int k = M.k0 + kp(M, j) + e;
-      const bool valid = k < A.nv;
-      // padding velocities: an enormous speed makes the equilibrium vanish,
-      // zero flux coefficients and zero weight keep them out of everything
-      const float x = valid ? A.xi[k] : 1e18f, y = valid ? A.xi[A.nvp + k] : 1e18f,
-                  zz = valid ? A.xi[2 * A.nvp + k] : 1e18f;
-      v[0][e] = x;
-      v[1][e] = y;
-      v[2][e] = zz;
-      v[3][e] = valid ? A.w[k] : 0.f;
-      v[4][e] = valid ? A.dt * fabsf(x) * A.rdx : 0.f;
-      v[5][e] = valid ? A.dt * fabsf(y) * A.rdy : 0.f;
-      v[6][e] = valid ? A.dt * fabsf(zz) * A.rdz : 0.f;
-      v[7][e] = copysignf(1.f, x);
-      v[8][e] = copysignf(1.f, y);
-      v[9][e] = copysignf(1.f, zz);
-    }
-    M.xix[j] = make_float2(v[0][0], v[0][1]);
-    M.xiy[j] = make_float2(v[1][0], v[1][1]);
-    M.xiz[j] = make_float2(v[2][0], v[2][1]);
-    M.wk[j] = make_float2(v[3][0], v[3][1]);
-    M.ax[j] = make_float2(v[4][0], v[4][1]);
-    M.ay[j] = make_float2(v[5][0], v[5][1]);
-    M.az[j] = make_float2(v[6][0], v[6][1]);
-    M.sx[j] = make_float2(v[7][0], v[7][1]);
-    M.sy[j] = make_float2(v[8][0], v[8][1]);
-    M.sz[j] = make_float2(v[9][0], v[9][1]);
+  using C = Cfg<VPL>;
+  constexpr int NG = C::NG, KC = C::KC;
+  float *stage = reinterpret_cast<float *>(smem_raw);
+  float *fxb = stage + NST * C::STAGE; // two buffers of x faces, then two of y faces
+  float *fyb = fxb + 2 * C::FX;
+  float *scon = fyb + 2 * C::FY;
+  float *sfinf = scon + C::CONST;
+  float *smac = sfinf + KC;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smac + 2 * NW * kMac);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ti = warp % TX, tj = warp / TX;
+  const int k0 = chunk * KC;
+  const unsigned sg = A.csign[chunk];
+  const int sx = (sg & 1u) ? -1 : 1, sy = (sg & 2u) ? -1 : 1, d = (sg & 4u) ? -1 : 1; // d: the march direction
+  const float2 sigx = dup(sx * A.sig[0]), sigy = dup(sy * A.sig[1]), sigz = dup(d * A.sig[2]);
+  const int ox = (sx > 0) ? 2 : 1; // position of tile column 0 in an extended row
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const long long nxy = (long long)nx * ny;
+  // stage slot of tile-relative cell (i, j)
+  auto slot = [&](int i, int j) -> int {
+    if (j >= 0 && j < TY) return j * XW + i + ox;
+    const int yr = (sy > 0) ? ((j < 0) ? j + 2 : 2) : ((j < 0) ? 0 : j - TY + 1);
+    return XW * TY + yr * TX + i;
+  };
+  // flag bits of a ghost across the upwind / downwind face along each axis
+  const unsigned gux = 1u << (sx < 0), gdx = 1u << (sx > 0);
+  const unsigned guy = 4u << (sy < 0), gdy = 4u << (sy > 0);
+  const unsigned guz = 16u << (d < 0), gdz = 16u << (d > 0);
+  const int dux = 0 + (sx < 0), ddx = 0 + (sx > 0), duy = 2 + (sy < 0), ddy = 2 + (sy > 0);
+  const int duz = 4 + (d < 0), ddz = 4 + (d > 0);
+
+  // the own column
+  const int x = x0 + ti, y = y0 + tj;
+  const bool col_in = x < nx && y < ny;
+  const bool inner = col_in && x - 1 >= 0 && x + 1 < nx && y - 1 >= 0 && y + 1 < ny;
+  const int so = slot(ti, tj), syu = slot(ti, tj - sy), syd = slot(ti, tj + sy);
+  const long long plane0 = x + (long long)nx * y;
+  const int fx_own = (tj * (TX + 2) + ti + 1) * KC, fx_in = fx_own - sx * KC;
+  const int fy_own = ((tj + 1) * TX + ti) * KC, fy_in = fy_own - sy * TX * KC;
+
+  // the halo duty of this warp: the upwind halo cell h of the tile (x halo
+  // column for h < 4, y halo row for h >= 4) and the group hg of its velocities
+  const bool hduty = (VPL == 8) || warp < 8;
+  const int h = (VPL == 8) ? (warp >> 1) : (warp & 7), hg = (VPL == 8) ? (warp & 1) : 0;
+  const bool hxa = h < TX; // a face along x
+  const int hi = hxa ? ((sx > 0) ? -1 : TX) : h - TX;
+  const int hj = hxa ? h : ((sy > 0) ? -1 : TY);
+  const int hs = hxa ? sx : sy;
+  const int hc = slot(hi, hj), hup = hxa ? hc - sx : slot(hi, hj - sy), hdn = hxa ? hc + sx : slot(hi, hj + sy);
+  const int hx = x0 + hi, hy = y0 + hj;
+  const bool h_in = hduty && hx >= 0 && hx < nx && hy >= 0 && hy < ny;
+  const bool h_up_in = hxa ? (hx - hs >= 0 && hx - hs < nx) : (hy - hs >= 0 && hy - hs < ny);
+  const unsigned hgu = hxa ? gux : guy, hgd = hxa ? gdx : gdy;
+  const int hdu = hxa ? dux : duy, hdd = hxa ? ddx : ddy;
+  const int hout = hxa ? (hj * (TX + 2) + hi + 1) * KC : 2 * C::FX + ((hj + 1) * TX + hi) * KC; // from fxb
+  const long long hplane0 = h_in ? hx + (long long)nx * hy : 0;
+  const int ho = 128 * hg + 4 * lane;
+
+  // planes: march index m = 0..M-1 is plane p0 + d m; stage m holds plane
+  // p0 + d m (also m = M: the z neighbour of the last plane)
+  const int M = zb - za;
+  const int p0 = (d > 0) ? za : zb - 1;
+  auto plane_in = [&](int m) { const int p = p0 + d * m; return p >= 0 && p < nz; };
+
+  // velocity constants (quantity-major per group) and the free stream of the chunk
+  for (int t = threadIdx.x; t < NG * 32; t += NTHREADS) {
+    const int g = t >> 5, l = t & 31;
+    const float4 *src = reinterpret_cast<const float4 *>(A.vconst) + (k0 + 128 * g + 4 * l);
+    const float4 v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3];
+    sts4(scon + ((g * 4 + 0) * 32 + l) * 4, make_float4(v0.x, v1.x, v2.x, v3.x));
+    sts4(scon + ((g * 4 + 1) * 32 + l) * 4, make_float4(v0.y, v1.y, v2.y, v3.y));
+    sts4(scon + ((g * 4 + 2) * 32 + l) * 4, make_float4(v0.z, v1.z, v2.z, v3.z));
+    sts4(scon + ((g * 4 + 3) * 32 + l) * 4, make_float4(v0.w, v1.w, v2.w, v3.w));
   }
-  for (int i = threadIdx.x; i < C::KC; i += NTHREADS) {
-    M.sfinf[i] = A.finf[M.k0 + i];
-    M.sxi[i] = A.xi[M.k0 + i];
-    M.syi[i] = A.xi[A.nvp + M.k0 + i];
-  }
-  {
-    static_assert(TX * C::KC == NTHREADS && TY * C::KC == NTHREADS, "two halo faces per thread");
-    const int kk = threadIdx.x % C::KC, line = threadIdx.x / C::KC;
-    int4 *duty = const_cast<int4 *>(M.duty);
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const float xi = A.xi[a * A.nvp + M.k0 + kk];
-      const int s = (xi >= 0.f) ? 1 : -1;
-      const int i = (a == 0) ? ((s > 0) ? -1 : TX) : line;
-      const int j = (a == 0) ? line : ((s > 0) ? -1 : TY);
-      const int di = (a == 0) ? s : 0, dj = (a == 1) ? s : 0;
-      const int cx = M.x0 + i, cy = M.y0 + j;
-      const bool outside = cx < 0 || cx >= A.nx || cy < 0 || cy >= A.ny;
-      const int ca = (a == 0) ? cx : cy, na = (a == 0) ? A.nx : A.ny;
-      const int f_off = slot(i, j) * C::KC + kk;
-      const int up = (outside || ca - s < 0 || ca - s >= na) ? 0 : slot(i - di, j - dj) * C::KC + kk + 1;
-      const int dn = (outside || ca + s < 0 || ca + s >= na) ? 0 : slot(i + di, j + dj) * C::KC + kk + 1;
-      const int out = (a == 0) ? (j * (TX + 2) + i + 1) * C::KC + kk : ((j + 1) * TX + i) * C::KC + kk;
-      duty[a * NTHREADS + threadIdx.x] =
-          make_int4(f_off | (up << 16), dn | (out << 16), outside ? -1 : cx + A.nx * cy, 0);
-    }
-  }
-  {
-    const int hx = M.duty[threadIdx.x].z, hy = M.duty[NTHREADS + threadIdx.x].z;
-    M.hm_next = (uint16_t)((hx >= 0 ? M.cm_plane[hx] : 0) | ((hy >= 0 ? M.cm_plane[hy] : 0) << 8));
-  }
-  if (M.lane < kMac)
-    M.smac[M.warp * kMac + M.lane] =
-        M.col_in ? A.mac[(M.plane + (long long)M.z0 * A.nx * A.ny) * kMac + M.lane] : 0.f;
-  M.mask_next = M.col_in ? ((M.z0 + 1 < A.nz) ? cmask3(M, M.x, M.y, M.z0 + 1) : 0) : kNotFluid;
+  for (int i = threadIdx.x; i < KC; i += NTHREADS) sfinf[i] = A.finf[k0 + i];
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
-      if (reinit) mbar_inval(&M.full[s]);
-      mbar_init(&M.full[s], 1);
+      if (reinit) mbar_inval(&full[s]);
+      mbar_init(&full[s], 1);
     }
     fence_mbar_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int r = M.z0; r < min(M.zlast, M.z0 + NST - 1); ++r) issue_plane(M, r, r - M.z0);
-  auto own = [&](int r, Ring<KPT> &v) {
-    if (r < 0 || r >= A.nz || !M.col_in) {
+  const int ys_pair = (sy > 0) ? y0 - 2 : y0 + TY, ys_single = (sy > 0) ? y0 + TY : y0 - 1;
+  const int yr_pair = (sy > 0) ? 0 : 1, yr_single = (sy > 0) ? 2 : 0;
+  auto issue = [&](int m) {
+    float *dst = stage + (m % NST) * C::STAGE;
+    uint64_t *bar = &full[m % NST];
+    const int z = p0 + d * m;
+    mbar_expect_tx(bar, C::STAGE * 4);
+    tma_box(dst, tmx, k0, x0 - ox, y0, z, bar);
+    tma_box(dst + (XW * TY + yr_pair * TX) * KC, tmp, k0, x0, ys_pair, z, bar);
+    tma_box(dst + (XW * TY + yr_single * TX) * KC, tms, k0, x0, ys_single, z, bar);
+  };
+  int issued = -1; // the last stage issued (thread 0)
+  if (threadIdx.x == 0 && M > 0)
+    for (int m = 0; m < NST && m <= M && plane_in(m); ++m) {
+      issue(m);
+      issued = m;
+    }
+
+  auto own = [&](int p, float4 *v) {
+    if (!col_in || p < 0 || p >= nz) {
 #pragma unroll
-      for (int j = 0; j < KPT / 2; ++j) v[j] = lds2(M.sfinf, kp(M, j));
+      for (int g = 0; g < NG; ++g) v[g] = lds4(sfinf + 128 * g + 4 * lane);
     } else {
-      const float *src = A.f + (size_t)(M.plane + (long long)r * A.nx * A.ny) * A.nvp + M.k0;
+      const float *src = A.f + (size_t)(plane0 + (long long)p * nxy) * A.nvp + k0 + 4 * lane;
 #pragma unroll
-      for (int j = 0; j < KPT / 2; ++j) v[j] = *reinterpret_cast<const float2 *>(src + kp(M, j));
+      for (int g = 0; g < NG; ++g) v[g] = __ldg(reinterpret_cast<const float4 *>(src + 128 * g));
     }
   };
-  Ring<KPT> R0, R1, R2, P0, P1, P2;
+  auto cflag = [&](int p) -> unsigned {
+    return (col_in && p >= 0 && p < nz) ? A.cmask[plane0 + (long long)p * nxy] : kNotFluid;
+  };
+  auto hflag = [&](int p) -> unsigned {
+    return (h_in && p >= 0 && p < nz) ? A.cmask[hplane0 + (long long)p * nxy] : kNotFluid;
+  };
+  // the z stencil of the own column: f at plane p - d and the z outflow face
+  // of plane p - d (the inflow of plane p), per group
+  float4 Rp[NG], P[NG];
   {
-    Ring<KPT> Rm2;
-    own(M.z0 - 2, Rm2);
-    own(M.z0 - 1, R2);
-    own(M.z0, R0);
-    own(M.z0 + 1, R1);
-    phi_z(M, M.z0 - 1, M.col_in ? cmask3(M, M.x, M.y, M.z0 - 1) : kNotFluid, R2, Rm2, R0, P0);
-    phi_z(M, M.z0, M.col_in ? cmask3(M, M.x, M.y, M.z0) : kNotFluid, R0, R2, R1, P1);
-  }
-  for (int r = M.z0; r < min(M.zlast, M.z0 + 2); ++r)
-    if (!mbar_wait(&M.full[r - M.z0], 0)) M.abort_local = true;
-  uint8_t mc = M.col_in ? cmask3(M, M.x, M.y, M.z0) : kNotFluid;
-  int z = M.z0, par = 0;
-  bool ok = true;
-  // one copy of the plane body (a small kernel keeps the instruction cache
-  // warm); the ring rotates by moves
-  for (; z < M.z1; ++z) {
-    ok = plane_step(M, z, par, mc, R0, R1, R2, P0, P1, P2);
-    if (!ok) break;
+    float4 Rpp[NG], Rc[NG];
+    own(p0 - 2 * d, Rpp);
+    own(p0 - d, Rp);
+    own(p0, Rc);
+    const int r = p0 - d;
+    const unsigned mr = cflag(r);
+    const long long cr = plane0 + (long long)r * nxy;
 #pragma unroll
-    for (int j = 0; j < KPT / 2; ++j) {
-      R0[j] = R1[j];
-      R1[j] = R2[j];
-      P0[j] = P1[j];
-      P1[j] = P2[j];
+    for (int g = 0; g < NG; ++g) {
+      const int k = k0 + 128 * g + 4 * lane;
+      if (!col_in || r < 0 || r >= nz) P[g] = lds4(sfinf + 128 * g + 4 * lane);
+      else if (mr & kNotFluid) P[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+      else P[g] = face4(Rp[g], (mr & guz) ? link4(A, cr, duz, k) : Rpp[g], (mr & gdz) ? link4(A, cr, ddz, k) : Rc[g]);
     }
-    par ^= 1;
+  }
+  if (lane < kMac)
+    smac[warp * kMac + lane] = col_in ? A.mac[(plane0 + (long long)p0 * nxy) * kMac + lane] : 0.f;
+
+  // x and y outflow faces of plane index m (own cell and the warp's halo
+  // cell) from stage m into face buffer b
+  auto publish = [&](int m, unsigned mcm, unsigned hmm, int b) {
+    const int p = p0 + d * m;
+    const float *sp = stage + (m % NST) * C::STAGE;
+    const long long cell = plane0 + (long long)p * nxy;
+    float *fxo = fxb + b * C::FX + fx_own, *fyo = fyb + b * C::FY + fy_own;
+    const float *rc = col_in ? sp + so * KC + 4 * lane : sfinf + 4 * lane;
+    if (inner && !(mcm & (kNotFluid | 15u))) {
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const int o = 128 * g + 4 * lane;
+        const float4 fc = lds4(rc + 128 * g);
+        sts4(fxo + 128 * g + 4 * lane, face4(fc, lds4(sp + (so - sx) * KC + o), lds4(sp + (so + sx) * KC + o)));
+        sts4(fyo + 128 * g + 4 * lane, face4(fc, lds4(sp + syu * KC + o), lds4(sp + syd * KC + o)));
+      }
+    } else {
+      const bool fluid = col_in && !(mcm & kNotFluid);
+      const bool xu_in = x - sx >= 0 && x - sx < nx, xd_in = x + sx >= 0 && x + sx < nx;
+      const bool yu_in = y - sy >= 0 && y - sy < ny, yd_in = y + sy >= 0 && y + sy < ny;
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const int o = 128 * g + 4 * lane, k = k0 + o;
+        float4 FX, FY;
+        if (!col_in) {
+          FX = FY = lds4(sfinf + o); // outside the domain: the free stream, zero slope
+        } else if (!fluid) {
+          FX = FY = make_float4(0.f, 0.f, 0.f, 0.f); // never read: neighbours see the link values
+        } else {
+          const float4 fin = lds4(sfinf + o);
+          const float4 xu = (mcm & gux) ? link4(A, cell, dux, k) : (xu_in ? lds4(sp + (so - sx) * KC + o) : fin);
+          const float4 xd = (mcm & gdx) ? link4(A, cell, ddx, k) : (xd_in ? lds4(sp + (so + sx) * KC + o) : fin);
+          const float4 yu = (mcm & guy) ? link4(A, cell, duy, k) : (yu_in ? lds4(sp + syu * KC + o) : fin);
+          const float4 yd = (mcm & gdy) ? link4(A, cell, ddy, k) : (yd_in ? lds4(sp + syd * KC + o) : fin);
+          const float4 fc = lds4(rc + 128 * g);
+          FX = face4(fc, xu, xd);
+          FY = face4(fc, yu, yd);
+        }
+        sts4(fxo + o, FX);
+        sts4(fyo + o, FY);
+      }
+    }
+    if (hduty) {
+      float4 out;
+      if (h_in && h_up_in && !(hmm & (kNotFluid | hgu | hgd))) {
+        out = face4(lds4(sp + hc * KC + ho), lds4(sp + hup * KC + ho), lds4(sp + hdn * KC + ho));
+      } else if (!h_in) {
+        out = lds4(sfinf + ho);
+      } else if (hmm & kNotFluid) {
+        out = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        const long long hcell = hplane0 + (long long)p * nxy;
+        const float4 up =
+            (hmm & hgu) ? link4(A, hcell, hdu, k0 + ho) : (h_up_in ? lds4(sp + hup * KC + ho) : lds4(sfinf + ho));
+        const float4 dn = (hmm & hgd) ? link4(A, hcell, hdd, k0 + ho) : lds4(sp + hdn * KC + ho);
+        out = face4(lds4(sp + hc * KC + ho), up, dn);
+      }
+      // the halo cell's face goes into buffer b of its axis
+      sts4(fxb + b * (hxa ? C::FX : C::FY) + hout + ho, out);
+    }
+  };
+
+  bool abort_local = false;
+  int waited = -1; // the last stage this thread waited for successfully
+  unsigned mc0 = cflag(p0), mc1 = cflag(p0 + d);
+  unsigned hm1 = hflag(p0 + d);
+  if (M > 0) {
+    if (mbar_wait(&full[0], 0)) waited = 0;
+    else abort_local = true;
+    publish(0, mc0, hflag(p0), 0);
+  }
+  float *fn_cell = A.fn + (size_t)(plane0 + (long long)p0 * nxy) * A.nvp + k0 + 4 * lane;
+  float *part_cell =
+      A.part + ((size_t)chunk * NM + ((lane >> 1) < NM ? (lane >> 1) : 0)) * A.ncell + plane0 + (long long)p0 * nxy;
+  const long long step_cells = d * nxy;
+  bool ok = !__syncthreads_or(abort_local ? 1 : 0);
+  int m = 0;
+  for (; ok && m < M; ++m) {
+    const int p = p0 + d * m, par = m & 1;
+    const bool nin = plane_in(m + 1);
+    const long long cell = plane0 + (long long)p * nxy;
+    // prefetch: flags two planes ahead, the Shakhov parameters of the next plane
+    const unsigned mc2 = cflag(p + 2 * d), hm2 = hflag(p + 2 * d);
+    const float macn = (lane < kMac && col_in && nin) ? __ldg(A.mac + (cell + d * nxy) * kMac + lane) : 0.f;
+    if (nin) {
+      if (mbar_wait(&full[(m + 1) % NST], ((m + 1) / NST) & 1)) waited = m + 1;
+      else abort_local = true;
+    }
+    // (1) the faces of the next plane, into the other buffer
+    if (m + 1 < M && !abort_local) publish(m + 1, mc1, hm1, par ^ 1);
+    // (2) update of the own cell at plane p and its moment sums (13 independent
+    // sums: the sum of w c^2 f is the trace of the second moments)
+    const float *sp = stage + (m % NST) * C::STAGE;
+    const float *sp1 = stage + ((m + 1) % NST) * C::STAGE;
+    const float *rc = col_in ? sp + so * KC + 4 * lane : sfinf + 4 * lane;
+    const float *rn = (nin && col_in) ? sp1 + so * KC + 4 * lane : sfinf + 4 * lane;
+    const float *fxo_b = fxb + par * C::FX, *fyo_b = fyb + par * C::FY;
+    const bool fluid = col_in && !(mc0 & kNotFluid) && !abort_local;
+    ACC acc[13];
+#pragma unroll
+    for (int i = 0; i < 13; ++i) acc[i] = ACC{};
+    if (fluid) {
+      const float4 *pm = reinterpret_cast<const float4 *>(smac + (par * NW + warp) * kMac);
+      const float4 c0v = pm[0], c1v = pm[1], c2v = pm[2];
+      const float2 mUx = dup(-c0v.y), mUy = dup(-c0v.z), mUz = dup(-c0v.w);
+      const float2 nl2 = dup(-c1v.x * kLog2e); // -log2(e) / T
+      // the Shakhov factor A (1 - Pr) folded into the heat flux
+      const float2 q0 = dup(c1v.z * c1v.w), q1 = dup(c1v.z * c2v.x), q2 = dup(c1v.z * c2v.y);
+      const float2 dt2 = dup(c2v.z);
+      const float2 pre2 = dup(c0v.x);
+      const bool ghosty = (mc0 & 63u) != 0;
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const int o = 128 * g + 4 * lane;
+        const float4 ax4 = lds4(scon + ((g * 4 + 0) * 32 + lane) * 4);
+        const float4 ay4 = lds4(scon + ((g * 4 + 1) * 32 + lane) * 4);
+        const float4 az4 = lds4(scon + ((g * 4 + 2) * 32 + lane) * 4);
+        const float4 w4 = lds4(scon + ((g * 4 + 3) * 32 + lane) * 4);
+        const float4 fc = lds4(rc + 128 * g), fnx = lds4(rn + 128 * g);
+        const float4 fxo = lds4(fxo_b + fx_own + o), fyo = lds4(fyo_b + fy_own + o);
+        float4 fxi = lds4(fxo_b + fx_in + o), fyi = lds4(fyo_b + fy_in + o), fzi = P[g];
+        // z outflow face of this plane (the inflow of the next)
+        float4 fzo;
+        if (!(mc0 & (guz | gdz))) {
+          fzo = face4(fc, Rp[g], fnx);
+        } else {
+          fzo = face4(fc, (mc0 & guz) ? link4(A, cell, duz, k0 + o) : Rp[g],
+                      (mc0 & gdz) ? link4(A, cell, ddz, k0 + o) : fnx);
+        }
+        if (ghosty) { // a ghost upwind neighbour: the mean of its link value and this cell (one-sided slope)
+          if (mc0 & gux) fxi = mean4(link4(A, cell, dux, k0 + o), fc);
+          if (mc0 & guy) fyi = mean4(link4(A, cell, duy, k0 + o), fc);
+          if (mc0 & guz) fzi = mean4(link4(A, cell, duz, k0 + o), fc);
+        }
+        P[g] = fzo;
+        Rp[g] = fc; // f at plane p: the z upwind value of the next plane
+        float2 out[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float2 ax = q ? hi2(ax4) : lo2(ax4), ay = q ? hi2(ay4) : lo2(ay4), az = q ? hi2(az4) : lo2(az4);
+          const float2 wk = q ? hi2(w4) : lo2(w4), f = q ? hi2(fc) : lo2(fc);
+          // Shakhov equilibrium g (1 + A c.q (2 c^2 / T - 5)) from the stored state
+          const float2 cx = __ffma2_rn(ax, sigx, mUx), cy = __ffma2_rn(ay, sigy, mUy), cz = __ffma2_rn(az, sigz, mUz);
+          const float2 c2 = __ffma2_rn(cx, cx, __ffma2_rn(cy, cy, __fmul2_rn(cz, cz)));
+          const float2 tn = __fmul2_rn(c2, nl2); // -c^2 / T log2(e)
+          const float2 e = __fmul2_rn(pre2, make_float2(ex2(tn.x), ex2(tn.y)));
+          const float2 cq = __ffma2_rn(cx, q0, __ffma2_rn(cy, q1, __fmul2_rn(cz, q2)));
+          const float2 poly = __ffma2_rn(tn, dup(-2.f * kLn2), dup(-5.f)); // 2 c^2 / T - 5
+          const float2 geq = __ffma2_rn(__fmul2_rn(e, cq), poly, e);
+          // forward Euler: relaxation, then the flux differences along x, y, z
+          float2 n = __ffma2_rn(dt2, sub2(geq, f), f);
+          n = __ffma2_rn(ax, sub2(q ? hi2(fxi) : lo2(fxi), q ? hi2(fxo) : lo2(fxo)), n);
+          n = __ffma2_rn(ay, sub2(q ? hi2(fyi) : lo2(fyi), q ? hi2(fyo) : lo2(fyo)), n);
+          n = __ffma2_rn(az, sub2(q ? hi2(fzi) : lo2(fzi), q ? hi2(fzo) : lo2(fzo)), n);
+          out[q] = n;
+          // moment sums about the stored bulk velocity (Eqs. moments1-3)
+          const float2 wf = __fmul2_rn(wk, n);
+          const float2 cxw = __fmul2_rn(cx, wf), cyw = __fmul2_rn(cy, wf), czw = __fmul2_rn(cz, wf);
+          const float2 e2 = __fmul2_rn(c2, wf);
+          acc_add(acc[0], wf);
+          acc_add(acc[1], cxw);
+          acc_add(acc[2], cyw);
+          acc_add(acc[3], czw);
+          acc_fma(acc[4], cx, cxw);
+          acc_fma(acc[5], cy, cxw);
+          acc_fma(acc[6], cz, cxw);
+          acc_fma(acc[7], cy, cyw);
+          acc_fma(acc[8], cz, cyw);
+          acc_fma(acc[9], cz, czw);
+          acc_fma(acc[10], cx, e2);
+          acc_fma(acc[11], cy, e2);
+          acc_fma(acc[12], cz, e2);
+        }
+        *reinterpret_cast<float4 *>(fn_cell + 128 * g) = cat4(out[0], out[1]);
+      }
+    } else {
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        P[g] = col_in ? make_float4(0.f, 0.f, 0.f, 0.f) : lds4(sfinf + 128 * g + 4 * lane);
+        Rp[g] = lds4(rc + 128 * g);
+      }
+    }
+    // (3) butterfly of the 16 (14 used) sums over the 32 lanes, in the order of
+    // the finalize kernel: 1, c, c^2, c_a c_b (xx xy xz yy yz zz), c c^2
+    {
+      float v16[16];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v16[i] = acc_value(acc[i]);
+#pragma unroll
+      for (int i = 4; i < 13; ++i) v16[i + 1] = acc_value(acc[i]);
+      v16[4] = v16[5] + v16[8] + v16[10];
+      v16[14] = v16[15] = 0.f;
+      float v8[8];
+      const bool b16 = lane & 16;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float keep = b16 ? v16[8 + i] : v16[i];
+        const float send = b16 ? v16[i] : v16[8 + i];
+        v8[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+      float v4[4];
+      const bool b8 = lane & 8;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float keep = b8 ? v8[4 + i] : v8[i];
+        const float send = b8 ? v8[i] : v8[4 + i];
+        v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      float v2[2];
+      const bool b4 = lane & 4;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float keep = b4 ? v4[2 + i] : v4[i];
+        const float send = b4 ? v4[i] : v4[2 + i];
+        v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      const bool b2 = lane & 2;
+      float v1 = (b2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? v2[0] : v2[1], 2);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+      // lane l holds sum index 8 b4(l) + 4 b3(l) + 2 b2(l) + b1(l) = l >> 1
+      if (col_in && (lane & 1) == 0 && (lane >> 1) < NM) *part_cell = v1;
+    }
+    // (4) advance: the flags and parameters of the next planes
+    if (lane < kMac) smac[((par ^ 1) * NW + warp) * kMac + lane] = macn;
+    mc0 = mc1;
+    mc1 = mc2;
+    hm1 = hm2;
+    fn_cell += step_cells * A.nvp;
+    part_cell += step_cells;
+    // faces of the next plane published, this plane's buffer and stage m consumed
+    if (__syncthreads_or(abort_local ? 1 : 0)) {
+      ok = false;
+      break;
+    }
+    // the stage of plane index m + NST into the slot of stage m
+    if (threadIdx.x == 0 && m + NST <= M && plane_in(m + NST)) {
+      fence_proxy_async();
+      issue(m + NST);
+      issued = m + NST;
+    }
   }
   if (!ok && threadIdx.x == 0) {
     atomicOr(A.err, kFlagTimeout);
-    const int issued_end = min(M.zlast, z + NST - 1);
-    for (int r = max(M.z0 + 2, z + 2); r < issued_end; ++r) {
-      const int j = r - M.z0;
-      mbar_wait(&M.full[j % NST], (j / NST) & 1);
-    }
+    for (int q = waited + 1; q <= issued; ++q) mbar_wait(&full[q % NST], (q / NST) & 1);
   }
   return ok;
 }
 
-template <int KPT>
+template <int VPL>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tmc, const __grid_constant__ CUtensorMap tmx,
-                       const __grid_constant__ CUtensorMap tmy, Tma3Args A) {
+    sweep3d_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmp,
+                       const __grid_constant__ CUtensorMap tms, Oct3Args A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int ntx = (A.nx + TX - 1) / TX;
-  const int z0 = blockIdx.z * A.zrows;
-  march3d<KPT>(A, &tmc, &tmx, &tmy, (blockIdx.x % ntx) * TX, (blockIdx.x / ntx) * TY, blockIdx.y * Cfg<KPT>::KC,
-               z0, min(A.nz, z0 + A.zrows), smem_raw, false);
+  const int za = blockIdx.z * A.zrows;
+  march3o<VPL>(A, &tmx, &tmp, &tms, (blockIdx.x % ntx) * TX, (blockIdx.x / ntx) * TY, blockIdx.y, za,
+               min(A.nz, za + A.zrows), smem_raw, false);
 }
 
 // One item of the batched 3D sweep: a march of one member case.
 struct WorkItem3 {
-  int cas;        // member index
-  int x0, y0, k0; // tile origin and first chunk velocity
-  int z0, z1;     // planes
+  int cas;     // member index
+  int x0, y0;  // tile origin
+  int chunk;   // velocity chunk
+  int za, zb;  // planes
   int pad[2];
 };
 
 // The batched 3D sweep: a persistent grid whose blocks take work items in
 // order from a shared counter.  Member c at step parity par uses
-// args[2 c + par] and the tensor maps tmaps[3 (2 c + par) + 0..2].
+// args[2 c + par] and the tensor maps tmaps[3 (2 c + par) + 0..2].  VPL = 0:
+// the members have chunks of either width, chosen per item.
+template <int VPL>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    sweep3d_tma_batch_kernel(const Tma3Args *__restrict__ args, const CUtensorMap *__restrict__ tmaps,
+    sweep3d_tma_batch_kernel(const Oct3Args *__restrict__ args, const CUtensorMap *__restrict__ tmaps,
                              const WorkItem3 *__restrict__ items, int nitems, int *__restrict__ next, int par) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ Tma3Args sA;
+  __shared__ Oct3Args sA;
   __shared__ int s_item;
   bool reinit = false;
   for (;;) {
@@ -707,7 +584,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (threadIdx.x == 0) sA = args[2 * it.cas + par];
     __syncthreads();
     const CUtensorMap *tm = tmaps + 3 * (2 * it.cas + par);
-    const bool ok = march3d<4>(sA, tm, tm + 1, tm + 2, it.x0, it.y0, it.k0, it.z0, it.z1, smem_raw, reinit);
+    bool ok;
+    if constexpr (VPL == 0)
+      ok = (sA.kc == 256) ? march3o<8>(sA, tm, tm + 1, tm + 2, it.x0, it.y0, it.chunk, it.za, it.zb, smem_raw, reinit)
+                          : march3o<4>(sA, tm, tm + 1, tm + 2, it.x0, it.y0, it.chunk, it.za, it.zb, smem_raw, reinit);
+    else
+      ok = march3o<VPL>(sA, tm, tm + 1, tm + 2, it.x0, it.y0, it.chunk, it.za, it.zb, smem_raw, reinit);
     if (!ok) break; // uniform: the abort vote is block-wide
     reinit = true;
     __syncthreads(); // the item's shared memory and arguments are released
@@ -726,71 +608,131 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder3() {
   return fn;
 }
 
-constexpr int kKpt3 = 4;
-
-} // namespace
-
-bool tma3_sweep_applicable(const ibdvm_ctx *ctx) {
-  return ctx->dim == 3 && ctx->precision == IBDVM_MIXED && (ctx->nvp % (32 * kKpt3)) == 0 && encoder3() != nullptr;
-}
-
-int tma3_sweep_nchunk(const ibdvm_ctx *ctx) { return ctx->nvp / (32 * kKpt3); }
-
-cudaError_t tma3_sweep_prepare(ibdvm_ctx *ctx) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder3();
-  if (!enc) return cudaErrorNotSupported;
-  const int kc = 32 * kKpt3;
-  const Geom &g = ctx->geom;
-  for (int b = 0; b < 2; ++b) {
-    cuuint64_t dims[4] = {(cuuint64_t)ctx->nvp, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
-    cuuint64_t strides[3] = {(cuuint64_t)ctx->nvp * 4, (cuuint64_t)g.n[0] * ctx->nvp * 4,
-                             (cuuint64_t)g.n[1] * g.n[0] * ctx->nvp * 4};
-    const cuuint32_t boxes[3][4] = {{(cuuint32_t)kc, TX, TY, 1}, {(cuuint32_t)kc, 2, TY, 1}, {(cuuint32_t)kc, TX, 2, 1}};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    for (int m = 0; m < 3; ++m) {
-      CUtensorMap *tm = reinterpret_cast<CUtensorMap *>(ctx->tmap3[b][m]);
-      CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->f[b], dims, strides, boxes[m], estr,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    }
+// the three tensor maps of a state buffer: x-extended rows, a pair of y rows, a single y row
+CUresult encode_maps(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap *out, void *f, const Geom &g, int nvp,
+                     int kc) {
+  cuuint64_t dims[4] = {(cuuint64_t)nvp, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+  cuuint64_t strides[3] = {(cuuint64_t)nvp * 4, (cuuint64_t)g.n[0] * nvp * 4, (cuuint64_t)g.n[1] * g.n[0] * nvp * 4};
+  const cuuint32_t boxes[3][4] = {{(cuuint32_t)kc, XW, TY, 1}, {(cuuint32_t)kc, TX, 2, 1}, {(cuuint32_t)kc, TX, 1, 1}};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  for (int m = 0; m < 3; ++m) {
+    CUresult r = enc(&out[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, f, dims, strides, boxes[m], estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return r;
   }
-  return cudaFuncSetAttribute(sweep3d_tma_kernel<kKpt3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Cfg<kKpt3>::SMEM);
+  return CUDA_SUCCESS;
 }
 
-cudaError_t tma3_sweep_launch(ibdvm_ctx *ctx) {
-  Tma3Args A{};
-  A.f = static_cast<const float *>(ctx->f[ctx->cur]);
-  A.fn = static_cast<float *>(ctx->f[1 - ctx->cur]);
+Oct3Args oct_args(const ibdvm_ctx *ctx, int cur, int *err) {
+  Oct3Args A{};
+  A.f = static_cast<const float *>(ctx->f[cur]);
+  A.fn = static_cast<float *>(ctx->f[1 - cur]);
   A.mac = static_cast<const float *>(ctx->mac);
-  A.xi = static_cast<const float *>(ctx->xiT);
-  A.w = static_cast<const float *>(ctx->wT);
+  A.vconst = ctx->oct_const;
+  A.csign = ctx->oct_sign;
   A.finf = static_cast<const float *>(ctx->finf);
   A.cmask = ctx->cmask;
   A.dslot = ctx->dslot;
   A.dlinks = ctx->dlinks;
   A.lval = static_cast<const float *>(ctx->lval);
   A.part = ctx->partf;
-  A.err = ctx->d_flags;
+  A.err = err;
   A.ncell = ctx->ncell;
   A.nx = ctx->geom.n[0];
   A.ny = ctx->geom.n[1];
   A.nz = ctx->geom.n[2];
   A.nvp = ctx->nvp;
-  A.nv = ctx->nv;
-  A.dt = (float)ctx->geom.dt;
-  A.rdx = (float)(1.0 / ctx->geom.dx[0]);
-  A.rdy = (float)(1.0 / ctx->geom.dx[1]);
-  A.rdz = (float)(1.0 / ctx->geom.dx[2]);
+  A.zrows = 0;
+  A.kc = ctx->oct_kc;
+  for (int a = 0; a < 3; ++a) A.sig[a] = (float)(ctx->geom.dx[a] / ctx->geom.dt);
+  return A;
+}
+
+} // namespace
+
+int tma3_octant_layout(const Geom &G, std::vector<int> &kst, int &nvp) {
+  if (G.dim != 3 || encoder3() == nullptr) return 0;
+  // velocities of each octant (bit a: component a negative), in natural order
+  std::vector<int> oct[8];
+  for (int i = 0; i < G.nv; ++i) {
+    int o = 0;
+    for (int a = 0; a < 3; ++a)
+      if (G.xi[3 * i + a] < 0.0) o |= 1 << a;
+    oct[o].push_back(i);
+  }
+  auto padded = [&](int kc) {
+    long long n = 0;
+    for (const auto &v : oct) n += (static_cast<long long>(v.size()) + kc - 1) / kc * kc;
+    return n;
+  };
+  // chunks of 256 velocities unless 128 wastes clearly less padding
+  const int kc = (padded(256) <= padded(128) + padded(128) / 32) ? 256 : 128;
+  kst.assign(G.nv, 0);
+  int pos = 0;
+  for (const auto &v : oct) {
+    if (v.empty()) continue;
+    for (size_t j = 0; j < v.size(); ++j) kst[v[j]] = pos + static_cast<int>(j);
+    pos += (static_cast<int>(v.size()) + kc - 1) / kc * kc;
+  }
+  nvp = pos;
+  return kc;
+}
+
+void tma3_octant_tables(const Geom &G, const std::vector<int> &kst, int nvp, int kc, std::vector<float> &vconst,
+                        std::vector<uint8_t> &sign) {
+  vconst.assign(static_cast<size_t>(nvp) * 4, 0.f);
+  // padding positions: w = 0 and a speed that makes the equilibrium vanish
+  for (int k = 0; k < nvp; ++k)
+    for (int a = 0; a < 3; ++a) vconst[4 * static_cast<size_t>(k) + a] = (float)(kPadSpeed * G.dt / G.dx[a]);
+  sign.assign(nvp / kc, 0);
+  std::vector<char> seen(nvp / kc, 0);
+  for (int i = 0; i < G.nv; ++i) {
+    const size_t k = static_cast<size_t>(kst[i]);
+    int o = 0;
+    for (int a = 0; a < 3; ++a) {
+      const double xa = G.xi[3 * i + a];
+      vconst[4 * k + a] = (float)(G.dt * std::fabs(xa) / G.dx[a]);
+      if (xa < 0.0) o |= 1 << a;
+    }
+    vconst[4 * k + 3] = (float)G.w[i];
+    sign[k / kc] = static_cast<uint8_t>(o);
+  }
+}
+
+bool tma3_sweep_applicable(const ibdvm_ctx *ctx) {
+  return ctx->dim == 3 && ctx->precision == IBDVM_MIXED && ctx->oct_kc > 0 && encoder3() != nullptr;
+}
+
+int tma3_sweep_nchunk(const ibdvm_ctx *ctx) { return ctx->nvp / ctx->oct_kc; }
+
+cudaError_t tma3_sweep_prepare(ibdvm_ctx *ctx) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder3();
+  if (!enc || ctx->oct_kc <= 0) return cudaErrorNotSupported;
+  for (int b = 0; b < 2; ++b)
+    if (encode_maps(enc, reinterpret_cast<CUtensorMap *>(ctx->tmap3[b][0]), ctx->f[b], ctx->geom, ctx->nvp,
+                    ctx->oct_kc) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(sweep3d_tma_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Cfg<8>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sweep3d_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<4>::SMEM);
+}
+
+cudaError_t tma3_sweep_launch(ibdvm_ctx *ctx) {
+  Oct3Args A = oct_args(ctx, ctx->cur, ctx->d_flags);
   const int ntiles = ((A.nx + TX - 1) / TX) * ((A.ny + TY - 1) / TY);
-  const int nchunk = ctx->nvp / (32 * kKpt3);
+  const int nchunk = ctx->nvp / ctx->oct_kc;
+  // planes split when the grid is too small to fill the GPU
   int nzb = 1;
-  while ((long long)ntiles * nchunk * nzb < 4LL * 152 && A.nz / (nzb * 2) >= 16) nzb *= 2;
+  while ((long long)ntiles * nchunk * nzb < 2LL * 152 && A.nz / (nzb * 2) >= 16) nzb *= 2;
   A.zrows = (A.nz + nzb - 1) / nzb;
   dim3 grid(ntiles, nchunk, (A.nz + A.zrows - 1) / A.zrows);
   const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(ctx->tmap3[ctx->cur][0]);
-  sweep3d_tma_kernel<kKpt3><<<grid, NTHREADS, Cfg<kKpt3>::SMEM, ctx->stream>>>(tm[0], tm[1], tm[2], A);
+  if (ctx->oct_kc == 256)
+    sweep3d_tma_kernel<8><<<grid, NTHREADS, Cfg<8>::SMEM, ctx->stream>>>(tm[0], tm[1], tm[2], A);
+  else
+    sweep3d_tma_kernel<4><<<grid, NTHREADS, Cfg<4>::SMEM, ctx->stream>>>(tm[0], tm[1], tm[2], A);
   return cudaGetLastError();
 }
 
@@ -799,78 +741,48 @@ cudaError_t tma3_batch_build(const std::vector<ibdvm_ctx *> &cases, int zrows, i
   PFN_cuTensorMapEncodeTiled_v12000 enc = encoder3();
   if (!enc) return cudaErrorNotSupported;
   const int n = static_cast<int>(cases.size());
-  const int kc = 32 * kKpt3;
-  std::vector<Tma3Args> args(2 * n);
+  std::vector<Oct3Args> args(2 * n);
   std::vector<CUtensorMap> maps(6 * n);
   std::vector<WorkItem3> items;
+  bool all8 = true, all4 = true;
   for (int i = 0; i < n; ++i) {
     const ibdvm_ctx *ctx = cases[i];
+    if (ctx->oct_kc <= 0) return cudaErrorInvalidValue;
+    all8 = all8 && ctx->oct_kc == 256;
+    all4 = all4 && ctx->oct_kc == 128;
     const Geom &g = ctx->geom;
     for (int p = 0; p < 2; ++p) {
       const int cur = ctx->cur ^ p;
-      Tma3Args &A = args[2 * i + p];
-      A = Tma3Args{};
-      A.f = static_cast<const float *>(ctx->f[cur]);
-      A.fn = static_cast<float *>(ctx->f[1 - cur]);
-      A.mac = static_cast<const float *>(ctx->mac);
-      A.xi = static_cast<const float *>(ctx->xiT);
-      A.w = static_cast<const float *>(ctx->wT);
-      A.finf = static_cast<const float *>(ctx->finf);
-      A.cmask = ctx->cmask;
-      A.dslot = ctx->dslot;
-      A.dlinks = ctx->dlinks;
-      A.lval = static_cast<const float *>(ctx->lval);
-      A.part = ctx->partf;
-      A.err = flags + i;
-      A.ncell = ctx->ncell;
-      A.nx = g.n[0];
-      A.ny = g.n[1];
-      A.nz = g.n[2];
-      A.nvp = ctx->nvp;
-      A.nv = ctx->nv;
-      A.zrows = 0;
-      A.dt = (float)g.dt;
-      A.rdx = (float)(1.0 / g.dx[0]);
-      A.rdy = (float)(1.0 / g.dx[1]);
-      A.rdz = (float)(1.0 / g.dx[2]);
-      cuuint64_t dims[4] = {(cuuint64_t)ctx->nvp, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
-      cuuint64_t strides[3] = {(cuuint64_t)ctx->nvp * 4, (cuuint64_t)g.n[0] * ctx->nvp * 4,
-                               (cuuint64_t)g.n[1] * g.n[0] * ctx->nvp * 4};
-      const cuuint32_t boxes[3][4] = {{(cuuint32_t)kc, TX, TY, 1}, {(cuuint32_t)kc, 2, TY, 1}, {(cuuint32_t)kc, TX, 2, 1}};
-      cuuint32_t estr[4] = {1, 1, 1, 1};
-      for (int m = 0; m < 3; ++m) {
-        CUresult r = enc(&maps[3 * (2 * i + p) + m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->f[cur], dims, strides,
-                         boxes[m], estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-      }
+      args[2 * i + p] = oct_args(ctx, cur, flags + i);
+      if (encode_maps(enc, &maps[3 * (2 * i + p)], ctx->f[cur], g, ctx->nvp, ctx->oct_kc) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     }
     const int nz = g.n[2];
     const int nzb = (zrows <= 0 || zrows >= nz) ? 1 : (nz + zrows - 1) / zrows;
     const int per = (nz + nzb - 1) / nzb;
     for (int y0 = 0; y0 < g.n[1]; y0 += TY)
       for (int x0 = 0; x0 < g.n[0]; x0 += TX)
-        for (int k0 = 0; k0 < ctx->nvp; k0 += kc)
-          for (int z0 = 0; z0 < nz; z0 += per) {
+        for (int c = 0; c < ctx->nvp / ctx->oct_kc; ++c)
+          for (int za = 0; za < nz; za += per) {
             WorkItem3 it{};
             it.cas = i;
             it.x0 = x0;
             it.y0 = y0;
-            it.k0 = k0;
-            it.z0 = z0;
-            it.z1 = std::min(nz, z0 + per);
+            it.chunk = c;
+            it.za = za;
+            it.zb = std::min(nz, za + per);
             items.push_back(it);
           }
   }
   std::stable_sort(items.begin(), items.end(),
-                   [](const WorkItem3 &a, const WorkItem3 &b) { return a.z1 - a.z0 > b.z1 - b.z0; });
+                   [](const WorkItem3 &a, const WorkItem3 &b) { return a.zb - a.za > b.zb - b.za; });
   cudaError_t e;
   auto up = [&](const void *h, size_t bytes, void *&d) -> cudaError_t {
     cudaError_t r = cudaMalloc(&d, std::max<size_t>(bytes, 16));
     if (r != cudaSuccess || bytes == 0) return r;
     return cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s);
   };
-  if ((e = up(args.data(), args.size() * sizeof(Tma3Args), t.args)) != cudaSuccess) return e;
+  if ((e = up(args.data(), args.size() * sizeof(Oct3Args), t.args)) != cudaSuccess) return e;
   if ((e = up(maps.data(), maps.size() * sizeof(CUtensorMap), t.tmaps)) != cudaSuccess) return e;
   if ((e = up(items.data(), items.size() * sizeof(WorkItem3), t.items)) != cudaSuccess) return e;
   void *nx = nullptr;
@@ -878,16 +790,15 @@ cudaError_t tma3_batch_build(const std::vector<ibdvm_ctx *> &cases, int zrows, i
   t.next = static_cast<int *>(nx);
   t.nitems = static_cast<int>(items.size());
   t.dim = 3;
-  const int smem = (int)Cfg<kKpt3>::SMEM;
-  if ((e = cudaFuncSetAttribute(sweep3d_tma_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
-      cudaSuccess)
-    return e;
+  t.ksel = all8 ? 8 : (all4 ? 4 : 0);
+  const void *fn = all8 ? (const void *)sweep3d_tma_batch_kernel<8>
+                   : all4 ? (const void *)sweep3d_tma_batch_kernel<4> : (const void *)sweep3d_tma_batch_kernel<0>;
+  const int smem = all4 ? (int)Cfg<4>::SMEM : (int)Cfg<8>::SMEM;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep3d_tma_batch_kernel, NTHREADS, smem)) !=
-      cudaSuccess)
-    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NTHREADS, smem)) != cudaSuccess) return e;
   t.grid = std::max(1, std::min(t.nitems, nsm * std::max(per_sm, 1)));
   return cudaStreamSynchronize(s); // the host tables go out of scope
 }
@@ -896,9 +807,15 @@ cudaError_t tma3_batch_launch(const SweepTables &t, int par, cudaStream_t s) {
   if (t.nitems == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(t.next, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  sweep3d_tma_batch_kernel<<<t.grid, NTHREADS, Cfg<kKpt3>::SMEM, s>>>(
-      static_cast<const Tma3Args *>(t.args), static_cast<const CUtensorMap *>(t.tmaps),
-      static_cast<const WorkItem3 *>(t.items), t.nitems, t.next, par);
+  const Oct3Args *a = static_cast<const Oct3Args *>(t.args);
+  const CUtensorMap *m = static_cast<const CUtensorMap *>(t.tmaps);
+  const WorkItem3 *it = static_cast<const WorkItem3 *>(t.items);
+  if (t.ksel == 8)
+    sweep3d_tma_batch_kernel<8><<<t.grid, NTHREADS, Cfg<8>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
+  else if (t.ksel == 4)
+    sweep3d_tma_batch_kernel<4><<<t.grid, NTHREADS, Cfg<4>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
+  else
+    sweep3d_tma_batch_kernel<0><<<t.grid, NTHREADS, Cfg<8>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
   return cudaGetLastError();
 }
 

@@ -128,6 +128,7 @@ SIGNATURES = {
     "ibdvm_set_f": ([_V, _D], _S),
     "ibdvm_get_f_native": ([_V, _V, ctypes.c_size_t], _S),
     "ibdvm_set_f_native": ([_V, _V, ctypes.c_size_t], _S),
+    "ibdvm_velocity_positions": ([_V, ctypes.POINTER(ctypes.c_int)], _S),
     "ibdvm_ghost_band": ([_V, _D, _D, _D, _D], _S),
     "ibdvm_wall": ([_V, _D], _S),
     "ibdvm_set_domain": ([_V, _V], _S),
@@ -503,6 +504,13 @@ class Solver:
 
     def native_shape(self):
         return (self.ncell, self.nvel_padded, self.ncomp)
+
+    def velocity_positions(self) -> np.ndarray:
+        """Index along the velocity axis of the native layout of every velocity
+        in its natural order (ibdvm_velocity_positions)."""
+        pos = np.zeros(self.nvel, dtype=np.int32)
+        self._check(self.lib.ibdvm_velocity_positions(self.h, pos.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return pos
 
     def native_dtype(self):
         return np.float64 if self.precision == "fp64" else np.float32

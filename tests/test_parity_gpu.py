@@ -209,10 +209,11 @@ def test_native_state_transfer():
     buf = torch.empty(shp, dtype=torch.float32, pin_memory=True)
     g.get_f_native(buf.data_ptr(), buf.numel() * 4)
     f = g.get_f()
-    np.testing.assert_allclose(buf.numpy()[:, : g.nvel], f, rtol=1e-7)
+    pos = g.velocity_positions()
+    np.testing.assert_allclose(buf.numpy()[:, pos], f, rtol=1e-7)
     buf.mul_(1.01)
     g.set_f_native(buf.data_ptr(), buf.numel() * 4)
-    np.testing.assert_allclose(g.get_f(), buf.numpy()[:, : g.nvel].astype(np.float64), rtol=1e-7)
+    np.testing.assert_allclose(g.get_f(), buf.numpy()[:, pos].astype(np.float64), rtol=1e-7)
     # the moments into caller-owned pinned arrays equal those into fresh ones
     W, q, t = g.moments()
     Wp = torch.empty(W.shape, dtype=torch.float64, pin_memory=True).numpy()
@@ -247,7 +248,7 @@ def test_pipelined_state_upload(kind):
     buf.mul_(scale[:, None, None])
     g.set_f_native(buf.data_ptr(), buf.numel() * esize)
     W1, q1, t = g.moments()
-    f = buf.numpy()[:, : g.nvel].astype(np.float64)
+    f = buf.numpy()[:, g.velocity_positions()].astype(np.float64)
     g.set_f(f)
     W2, q2, _ = g.moments()
     np.testing.assert_array_equal(W1, W2)
