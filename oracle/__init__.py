@@ -114,6 +114,7 @@ def _load():
                 "or_cell_types": ([V, _U8], None),
                 "or_links": ([V, _I, _I, _I, _I, _I, _D, _D], None),
                 "or_cut_table": ([V, _D], None),
+                "or_upwind_weights": ([V, ctypes.c_int, _D], None),
                 "or_surface_count": ([V], ctypes.c_int),
                 "or_surface_cells": ([V, _I, _I, _I], None),
                 "or_get_f": ([V, _D], None),
@@ -270,6 +271,14 @@ class OracleCase:
             self.h, g.ctypes.data_as(_I), off.ctypes.data_as(_I), cells.ctypes.data_as(_I)
         )
         return g, off, cells[:tot]
+
+    def upwind_weights(self, gi: int) -> np.ndarray:
+        """Weights of Eq. upwind of ghost gi over its surface cells, [j][k]."""
+        _, off, _ = self.surface_cells()
+        ns = int(off[gi + 1] - off[gi])
+        out = np.zeros((ns, self.nvel))
+        self.lib.or_upwind_weights(self.h, int(gi), _dp(out))
+        return out
 
     # state --------------------------------------------------------------
     def shape(self):

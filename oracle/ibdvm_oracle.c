@@ -57,6 +57,11 @@
  *       each node owns the box between the midpoints to its neighbours (the
  *       trapezoid rule on non-uniform nodes), and the specular interpolation
  *       (C13) brackets a velocity by bisection on each axis.
+ *   C27 optional ablation (default off): without the upwind-weighted
+ *       strategy (Sec. 3.3.4), the intermediate ghost value of a link is the
+ *       linear extrapolation 2 f_d - f_ac from its donor and auxiliary cell
+ *       along the link axis, in place of Eq. extrapolation 1; the rest of the
+ *       construction is unchanged.
  *   C26 optional (default off): a ghost value of Eq. extrapolation 2 below
  *       zero is set to zero.  The extrapolation from the shifted point
  *       through the wall value (up to threefold) can turn negative where the
@@ -882,13 +887,15 @@ static double preghost_slope(const or_case *C, const double *f, long j, int a, i
   return 0.0;
 }
 
-/* f_gc of Eq. extrapolation 1 with the weights of Eq. upwind */
-static double ghost_interp(const or_case *C, const double *f, const or_ghost *G, int k, int m)
+/* the weights of Eq. upwind for velocity k over the surface cells of ghost
+   G: max(0, xi_k . r_j / |r_j|)^2 normalised to a unit sum, or 1 / N_S when
+   they all vanish (the text after Eq. upwind); 1 / N_S for every velocity
+   without upwind weighting */
+static void upwind_weights(const or_case *C, const or_ghost *G, int k, double *wt)
 {
   int ig[3];
   cell_ijk(C, G->cell, ig);
   double wsum = 0.0;
-  double wj[27];
   for (int j = 0; j < G->ns; ++j) {
     /* r from the integer cell offset times the spacing, so that velocities
        tangent to r give an exact zero */
@@ -904,12 +911,31 @@ static double ghost_interp(const or_case *C, const double *f, const or_ghost *G,
     double dot = 0.0;
     for (int a = 0; a < C->dim; ++a) dot += C->xi[3 * k + a] * r[a] / rl;
     double mx = dot > 0.0 ? dot : 0.0;
-    wj[j] = (C->p.upwind == 0) ? 0.0 : mx * mx;
-    wsum += wj[j];
+    wt[j] = (C->p.upwind == 0) ? 0.0 : mx * mx;
+    wsum += wt[j];
   }
+  for (int j = 0; j < G->ns; ++j) wt[j] = (wsum != 0.0) ? wt[j] / wsum : 1.0 / G->ns;
+}
+
+void or_upwind_weights(const or_case *C, int gi, double *out)
+{
+  const or_ghost *G = &C->ghosts[gi];
+  double wt[27];
+  for (int k = 0; k < C->nv; ++k) {
+    upwind_weights(C, G, k, wt);
+    for (int j = 0; j < G->ns; ++j) out[(size_t)j * C->nv + k] = wt[j];
+  }
+}
+
+/* f_gc of Eq. extrapolation 1 with the weights of Eq. upwind */
+static double ghost_interp(const or_case *C, const double *f, const or_ghost *G, int k, int m)
+{
+  int ig[3];
+  cell_ijk(C, G->cell, ig);
+  double wt[27];
+  upwind_weights(C, G, k, wt);
   double fgc = 0.0;
   for (int j = 0; j < G->ns; ++j) {
-    double wt = (wsum != 0.0) ? wj[j] / wsum : 1.0 / G->ns;
     long jc = G->surf[j];
     int ij[3];
     cell_ijk(C, jc, ij);
@@ -919,7 +945,7 @@ static double ghost_interp(const or_case *C, const double *f, const or_ghost *G,
       double ra = (ij[a] - ig[a]) * C->dx[a];
       if (ra != 0.0) v -= preghost_slope(C, f, jc, a, k, m) * ra;
     }
-    fgc += wt * v;
+    fgc += wt[j] * v;
   }
   return fgc;
 }
@@ -989,10 +1015,21 @@ void or_ghost_band(const or_case *C, const double *f, double *fgc_out, double *f
   for (int gi = 0; gi < C->nghost; ++gi) {
     const or_ghost *G = &C->ghosts[gi];
     /* step 2: intermediate ghost value f_gc (shared by the ghost's links) */
-    for (int k = 0; k < nv; ++k)
-      for (int m = 0; m < nc; ++m) fgc[k * nc + m] = ghost_interp(C, f, G, k, m);
+    if (C->p.upwind != 3)
+      for (int k = 0; k < nv; ++k)
+        for (int m = 0; m < nc; ++m) fgc[k * nc + m] = ghost_interp(C, f, G, k, m);
     for (int l = G->first_link; l < G->first_link + G->nlinks; ++l) {
       const or_link *L = &C->links[l];
+      if (C->p.upwind == 3)
+        /* the construction without upwind weighting (Sec. 3.3.4): the ghost
+           value extrapolated linearly from the donor and the auxiliary cell
+           along the link axis, f_g = 2 f_d - f_ac (f_d without an auxiliary
+           cell, as C7) */
+        for (int k = 0; k < nv; ++k)
+          for (int m = 0; m < nc; ++m) {
+            double fd = F(C, (double *)f, L->d, k)[m];
+            fgc[k * nc + m] = (L->ac >= 0) ? 2.0 * fd - F(C, (double *)f, L->ac, k)[m] : fd;
+          }
       /* step 1: shifted point, Eq. fsp with the auxiliary-cell slope */
       for (int k = 0; k < nv; ++k)
         for (int m = 0; m < nc; ++m) {

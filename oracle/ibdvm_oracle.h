@@ -65,7 +65,9 @@ typedef struct {
   int cutcell; /* 1: velocity-space cut-cell correction (Sec. 3.2.3); 0: node classification only */
   int upwind;  /* 1: upwind weights with r pointing from the fluid cell to the ghost cell,
                   2: upwind weights with r pointing from the ghost cell to the fluid cell,
-                  0: plain average 1/N_S */
+                  0: plain average 1/N_S,
+                  3: no interpolation: the linear extrapolation 2 f_d - f_ac along the
+                     link axis (the construction without upwind weighting, Sec. 3.3.4) */
   /* domain faces 2a + (s > 0) (x-, x+, y-, y+, z-, z+): 0 = two freestream
      halo layers (C17), 1 = diffuse wall at wall_T with velocity wall_U (C24) */
   int wall[6];
@@ -120,6 +122,9 @@ void or_ghost_band(const or_case *C, const double *f, double *fgc, double *fsp, 
                    double *fstarw, double *fstargc, double *rhow);
 
 /* building blocks, exposed for the pins */
+/* weights of Eq. upwind of ghost gi (index in the ghost list): out[j * nvel + k]
+   for its surface cells j (the order of or_surface_cells) and velocities k */
+void or_upwind_weights(const or_case *C, int gi, double *out);
 double or_mu0(double Kn, double alpha, double omega);
 double or_vanleer(double s1, double s2);
 void or_cell_moments(const or_case *C, const double *fcell, double *out);

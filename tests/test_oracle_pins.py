@@ -332,6 +332,148 @@ def test_p6_second_order_in_space():
     assert all(l1[i + 1] < l1[i] / 2.5 for i in range(2)), errs
 
 
+@pytest.mark.slow
+def test_p6_wall_temperature_second_order():
+    """Sec. 4.1, physical-space convergence: the wall temperature at the
+    intersect points, taken from the wall distribution f*_w that the ghost band
+    builds from the manufactured field, against the wall temperature of the
+    wall distribution built from the exact incident distribution (the field
+    evaluated at x_w) with the Maxwell wall of Sec. 2.3: the wall density from
+    zero normal mass flux over the incident and reflected parts of every
+    velocity box (Eqs. dnpc, rhowc), the reflected part rho_w times the
+    unit-density wall Maxwellian (2D reduced, B_w = T_w / 2 H_w), cut boxes
+    blended by their incident-side measure (Eq. fwc).  The paper reports second
+    order for the L1 and Linf errors of this temperature."""
+    errs = []
+    for n in (32, 64, 128):
+        body = wl.circle(0.125, center=(0.5, 0.5))
+        cfg = wl._case(2, n, ([0.0, 0.0], [1.0, 1.0]), 12, 5.0, 0.1, 0.0, body)
+        oc = oracle.OracleCase(cfg)
+        xi, w = oc.velocities()
+        idx = np.arange(oc.ncell)
+        x = (idx % n + 0.5) / n
+        y = (idx // n + 0.5) / n
+        wq = oc.wall_quantities(_manufactured(xi, x, y))
+        L = oc.links()
+        wg = oc.cut_table()
+        Tw = 1.0
+        Hw = np.exp(-np.sum(xi[:, :2] ** 2, axis=1) / Tw) / (np.pi * Tw)
+        ex = []
+        for l in range(oc.nlink):
+            fi = _manufactured(xi, L["xw"][l:l + 1, 0], L["xw"][l:l + 1, 1])[0]  # [k][h, b]
+            xn = xi[:, :2] @ L["nw"][l, :2]
+            ws = w - wg[l]
+            rho_w = -np.sum(wg[l] * xn * fi[:, 0]) / np.sum(ws * xn * Hw)
+            fr = np.stack([rho_w * Hw, 0.5 * Tw * rho_w * Hw], axis=-1)
+            fs = (wg[l][:, None] * fi + ws[:, None] * fr) / w[:, None]
+            rho = np.sum(w * fs[:, 0])
+            U = np.array([np.sum(w * xi[:, a] * fs[:, 0]) for a in range(2)]) / rho
+            c2 = np.sum((xi[:, :2] - U) ** 2, axis=1)
+            ex.append(2.0 * np.sum(w * (c2 * fs[:, 0] + fs[:, 1])) / (3.0 * rho))
+        ok = L["aux"] >= 0
+        e = np.abs(wq[:, 4] - np.array(ex))[ok]
+        errs.append((e.mean(), e.max()))
+    l1 = [e[0] for e in errs]
+    linf = [e[1] for e in errs]
+    assert 0.5 * math.log2(l1[0] / l1[2]) > 1.8, errs
+    assert 0.5 * math.log2(linf[0] / linf[2]) > 1.5, errs
+
+
+# ---------------------------------------------------------------------------
+# P5b and the weight law of Eq. upwind (Sec. 3.2.2)
+# ---------------------------------------------------------------------------
+
+def _fallback_velocities(oc, gi):
+    """Velocities whose upwind weights all vanish over the surface cells of
+    ghost gi (the 1 / N_S fallback): every weight equals 1 / N_S exactly."""
+    wts = oc.upwind_weights(gi)
+    ns = wts.shape[0]
+    return np.all(wts == 1.0 / ns, axis=0) if ns > 1 else None
+
+
+@pytest.mark.parametrize("upwind,literal", [(1, False), (2, True)])
+def test_p5b_fallback_velocities_leave_the_wall(upwind, literal):
+    """The text after Eq. upwind: when the weights of Eq. upwind all vanish,
+    the particles come from the solid, and the plain average 1 / N_S is taken.
+    On a circle the fallback velocities therefore point out of the wall (xi . n
+    > 0 with n the outward normal at the ghost): on average their direction is
+    within 60 degrees of n, and none points 30 degrees or more into the wall
+    (the exact set is the cone dual to the surface-cell directions, narrower
+    than the half plane at stair corners).  Reading C10 (r-hat from the surface
+    cell to the ghost) satisfies this at every ghost; the literal direction of
+    r-hat (from the ghost to the surface cell, upwind=2) reverses it, and the
+    test checks that the reversal is caught."""
+    cfg = wl._case(2, 48, 2.0, 16, 4.5, 0.1, 0.3, wl.circle(0.77, center=(0.03, -0.02)), upwind=upwind)
+    oc = oracle.OracleCase(cfg)
+    xi, _ = oc.velocities()
+    g, off, cells = oc.surface_cells()
+    n = 48
+    h = 4.0 / n
+    c0 = np.array([0.03, -0.02])
+    bad = checked = 0
+    for gi in range(oc.nghost):
+        fb = _fallback_velocities(oc, gi)
+        if fb is None:
+            continue
+        xg = np.array([-2.0 + (g[gi] % n + 0.5) * h, -2.0 + (g[gi] // n + 0.5) * h])
+        nrm = (xg - c0) / np.linalg.norm(xg - c0)
+        speed = np.linalg.norm(xi[:, :2], axis=1)
+        xn = xi[:, :2] @ nrm
+        checked += 1
+        # no velocity at least 30 degrees into the wall takes the fallback, and
+        # the fallback velocities point out of the wall on average
+        into = xn < -0.5 * speed
+        mean_dir = (xi[fb, :2] / speed[fb, None]).mean(axis=0) if fb.any() else np.zeros(2)
+        if np.any(fb & into) or not mean_dir @ nrm > 0.5:
+            bad += 1
+    assert checked > 20
+    if literal:
+        assert bad == checked  # the reversed r-hat is caught at every ghost
+    else:
+        assert bad == 0
+
+
+def test_upwind_weight_law_closed_forms():
+    """Eq. upwind on a straight staircase: a half-plane wall x + y = const
+    makes every ghost (i, j) on the diagonal have the surface cells (i-1, j),
+    (i, j-1) and (i-1, j-1), with r-hat (1, 0), (0, 1) and (1, 1)/sqrt(2) from
+    the surface cell to the ghost.  The squared, normalised weights are then
+    known in closed form: xi = (1, 0) gives 2/3, 0, 1/3 (a linear law would give
+    0.586, 0, 0.414), xi = (1, 1) gives 1/4, 1/4, 1/2, xi = (0, 1) gives
+    0, 2/3, 1/3, the tangential xi = (1, -1) gives 1, 0, 0, and xi = (-1, -1),
+    which leaves the wall, takes 1/3 each."""
+    n = 16
+    h = 4.0 / n
+    # solid where x + y >= s0, s0 half a cell below the centre sum of the
+    # diagonal i + j = 20
+    s0 = 2 * (-2.0 + 0.5 * h) + 20 * h - 0.5 * h
+    m = np.array([-1.0, -1.0]) / math.sqrt(2.0)
+    body = {"kind": "halfspace", "center": [s0 / 2, s0 / 2, 0.0], "radii": [m[0], m[1], 0.0], "accom": 1.0,
+            "Tw": 1.0, "Uw": [0.0, 0.0, 0.0]}
+    cfg = wl._case(2, n, 2.0, 9, 4.0, 0.1, 0.0, body)
+    oc = oracle.OracleCase(cfg)
+    xi, _ = oc.velocities()
+    g, off, cells = oc.surface_cells()
+    want = {(1, 0): (2 / 3, 0, 1 / 3), (1, 1): (1 / 4, 1 / 4, 1 / 2), (0, 1): (0, 2 / 3, 1 / 3),
+            (1, -1): (1, 0, 0), (-1, -1): (1 / 3, 1 / 3, 1 / 3)}
+    checked = 0
+    for gi in range(oc.nghost):
+        i, j = g[gi] % n, g[gi] // n
+        if i + j != 20 or min(i, j) < 2 or max(i, j) > n - 3:
+            continue  # ghosts away from the domain edge
+        sc = list(cells[off[gi]:off[gi + 1]])
+        order = [(i - 1) + n * j, i + n * (j - 1), (i - 1) + n * (j - 1)]
+        assert sorted(sc) == sorted(order)
+        wts = oc.upwind_weights(gi)
+        for (a, b), exp in want.items():
+            k = int(np.argmin(np.abs(xi[:, 0] - a) + np.abs(xi[:, 1] - b)))
+            assert xi[k, 0] == a and xi[k, 1] == b
+            got = [wts[sc.index(c), k] for c in order]
+            np.testing.assert_allclose(got, exp, rtol=1e-14, atol=1e-15)
+        checked += 1
+    assert checked >= 6
+
+
 # ---------------------------------------------------------------------------
 # P7: velocity-space cut cells (Sec. 3.2.3, 3.3.3)
 # ---------------------------------------------------------------------------
