@@ -5,11 +5,15 @@ Metric: DVM cell x velocity updates per second (fluid cells x discrete
 velocities advanced per step, summed over ranks), with the achieved fraction
 of the HBM roofline of the dominant kernel (the transport/relaxation sweep).
 
-Default workload: the 2D cylinder, 512^2 cells on [-8,8]^2, 48^2 velocities on
-[-6,6]^2, Kn 0.1, Ma 0.5, mixed precision (FP32 f, FP64 wall balance, forces
-and residual).  A step is the whole hot path: ghost band (upwind-weighted
-interpolation, wall density, cut-cell blend, ghost values), surface forces,
-transport and relaxation of every fluid cell, moments and residual.
+Default workload: the 3D sphere, 96^3 cells on [-4,4]^3, 20^3 velocities on
+[-5,5]^3, Kn 0.1, Ma 0.5, mixed precision (FP32 f, FP64 wall balance, forces
+and residual): the largest configuration that fits one GPU (7.08G cell x
+velocity pairs, 58 GB of state).  The 2D cylinder (512^2 cells on [-8,8]^2,
+48^2 velocities on [-6,6]^2, Kn 0.1, Ma 0.5, mixed) is measured in the same
+run and reported under the key "cylinder_512".  A step is the whole hot path:
+ghost band (upwind-weighted interpolation, wall density, cut-cell blend, ghost
+values), surface forces, transport and relaxation of every fluid cell,
+moments and residual.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,7 +38,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "cylinder_512": lambda p: __import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).cylinder_512(0.1, p),
+    "cylinder_512": lambda p, kn=0.1: __import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).cylinder_512(
+        kn, p),
     "sphere_96": lambda p: __import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).sphere_96(p),
     "cylinder_48": lambda p: dict(__import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).cylinder_48(),
                                   precision=p),
@@ -73,13 +78,29 @@ DESCRIPTIONS = {
 }
 
 
+def _workload_case(args, workload, precision):
+    """The case of a workload at the given precision (the cylinder at --kn)."""
+    if workload == "cylinder_512":
+        return WORKLOADS[workload](precision, args.kn)
+    return WORKLOADS[workload](precision)
+
+
+def kn_description(args, workload):
+    d = DESCRIPTIONS[workload]
+    return d.replace("Kn=0.1", f"Kn={args.kn:g}") if workload == "cylinder_512" else d
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cylinder_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sphere_96", choices=sorted(WORKLOADS))
+    ap.add_argument("--kn", type=float, default=0.1,
+                    help="cylinder_512: Knudsen number (the configuration sweeps 0.01, 0.1 and 1)")
+    ap.add_argument("--no-nested", action="store_true",
+                    help="sphere_96: skip the 512^2 cylinder measured in the same run")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -197,8 +218,9 @@ def profiled_traffic(kernel: str, source: str, pairs: int):
     return None
 
 
-# GB300's FP64 rate (nominal: 1.25 TFLOP/s dense, FMA = 2 flops); no measured
-# FP64 peak is recorded, so the FP64 path is reported against this figure
+# GB300's nominal FP64 rate (1.25 TFLOP/s dense, FMA = 2 flops), for context
+# only: the FP64 path is reported against the rate measured on this GPU by
+# ibdvm_fp64_fma_rate in the same run
 FP64_NOMINAL_TFLOPS = 1.25
 
 
@@ -254,10 +276,17 @@ def cpu_sample_case(case: dict) -> dict:
     return c
 
 
-def time_oracle(case: dict, budget_s: float, max_steps: int | None = None):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle(case: dict, budget_s: float, max_steps: int | None = None, threads: int = 1):
     import oracle
 
-    oc = oracle.OracleCase(case)
+    oc = oracle.OracleCase(case, threads=threads)
     oc.step(1)  # warm
     steps, t0 = 0, time.perf_counter()
     while True:
@@ -270,6 +299,20 @@ def time_oracle(case: dict, budget_s: float, max_steps: int | None = None):
     return pairs * steps / el, steps, el, oc
 
 
+def cpu_baseline(sample: dict, budget_s: float, what: str) -> dict:
+    """The oracle as it stands on a bounded sample of the workload, timed on all
+    the host cores this process may use (OpenMP over ghosts and cells, bitwise
+    the same results) and on one thread; `cores` is the thread count of the
+    reported value."""
+    nth = host_cores()
+    v, n, el, oc = time_oracle(sample, budget_s, threads=nth)
+    v1, n1, el1, _ = time_oracle(sample, budget_s / 2, threads=1)
+    return {"value": v, "unit": "cell-velocity updates/s", "cores": nth, "kind": "oracle",
+            "value_1thread": v1,
+            "sample": f"{n} oracle steps ({el:.1f} s) on {nth} threads and {n1} ({el1:.1f} s) on one thread, "
+                      f"of {what} on {sample['n'][0]} cells per axis ({oc.nfluid} fluid cells x {oc.nvel} velocities)"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -280,11 +323,12 @@ def run_reference(args, world, rank):
 
         case = workloads.served_stream(0, nreq=1)[0][1]
     else:
-        case = WORKLOADS[args.workload](args.precision)
+        case = _workload_case(args, args.workload, args.precision)
     sample = cpu_sample_case(case)
     import oracle
 
-    oc = oracle.OracleCase(sample)
+    nth = host_cores()
+    oc = oracle.OracleCase(sample, threads=nth)
     for _ in range(max(args.warmup, 0)):
         oc.step(1)
     t0 = time.perf_counter()
@@ -293,14 +337,15 @@ def run_reference(args, world, rank):
     el = time.perf_counter() - t0
     pairs = oc.nfluid * oc.nvel
     value = pairs * args.steps / el
-    desc = f"oracle (plain FP64 C, 1 thread) on the workload's gas, body and velocity grid with {sample['n'][0]} cells per axis"
+    desc = (f"oracle (plain FP64 C, {nth} host threads over ghosts and cells) on the workload's gas, body and "
+            f"velocity grid with {sample['n'][0]} cells per axis")
     line = {
         "impl": "reference", "metric": "DVM cell x velocity updates/s", "value": value,
         "unit": "cell-velocity updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": DESCRIPTIONS[args.workload], "sample": desc},
-        "cpu_baseline": {"value": value, "unit": "cell-velocity updates/s", "cores": 1, "kind": "oracle",
+        "config": {"workload": kn_description(args, args.workload), "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "cell-velocity updates/s", "cores": nth, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -325,7 +370,7 @@ def error_report(args):
 
     out = {}
     for prec in ("fp64", "mixed"):
-        case = WORKLOADS[args.workload](prec)
+        case = _workload_case(args, args.workload, prec)
         if args.cells:
             case["n"] = [args.cells] * case["dim"]
         s = ibdvm.Solver(case, stream=torch.cuda.Stream().cuda_stream)
@@ -338,7 +383,7 @@ def error_report(args):
     werr = [float(np.abs(a["W"][:, i] - b["W"][:, i]).max() / np.abs(b["W"][:, i]).max())
             for i in range(b["W"].shape[1])]
     rel = lambda x, y: float(abs(x - y) / max(abs(y), 1e-300))
-    line = {"report": "mixed vs fp64", "workload": DESCRIPTIONS[args.workload], "steps": args.error_report,
+    line = {"report": "mixed vs fp64", "workload": kn_description(args, args.workload), "steps": args.error_report,
             "W_rel_err": werr, "CD_rel_err": rel(a["CD"], b["CD"]), "CL_abs_err": abs(a["CL"] - b["CL"]),
             "Q_rel_err": rel(a["Q"], b["Q"]), "residual_rel_err": rel(a["res"], b["res"]),
             "fp64": {"CD": b["CD"], "CL": b["CL"], "Q": b["Q"], "residual": b["res"]},
@@ -435,11 +480,7 @@ def bench_batch(args, world, rank, local, pg):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        sample = cpu_sample_case(cases[0])
-        v, n, el, oc = time_oracle(sample, args.cpu_sample_seconds)
-        cpu = {"value": v, "unit": "cell-velocity updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} oracle steps ({el:.1f} s) of case 0's gas, body and velocity grid "
-                         f"on {sample['n'][0]} cells per axis ({oc.nfluid} fluid cells x {oc.nvel} velocities)"}
+        cpu = cpu_baseline(cpu_sample_case(cases[0]), args.cpu_sample_seconds, "case 0's gas, body and velocity grid")
     if rank == 0:
         line = {
             "metric": "DVM cell x velocity updates/s", "value": value, "unit": "cell-velocity updates/s",
@@ -584,7 +625,32 @@ def main():
             pg.barrier()
             pg.destroy_process_group()
         return rc
-    case = WORKLOADS[args.workload](args.precision)
+    line = measure_case(args, args.workload, world, rank, local, pg, with_cpu=not args.no_cpu_baseline)
+    if (args.workload == "sphere_96" and not args.cells and args.precision == "mixed" and not args.no_nested):
+        # the 2D configuration in the same run: 512^2 cells x 48^2 velocities
+        # (value, roofline and end-to-end figure of its own)
+        sub = measure_case(args, "cylinder_512", world, rank, local, pg, with_cpu=False)
+        if rank == 0:
+            line["cylinder_512"] = {k: sub[k] for k in ("value", "unit", "ms_per_step", "config", "roofline",
+                                                      "kernel_ms", "gpu_launches", "e2e", "clocks", "residual",
+                                                      "CD")}
+            line["gpu_launches"] += sub["gpu_launches"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def measure_case(args, workload, world, rank, local, pg, with_cpu=True):
+    """Times K steps of one workload on this rank's GPU (replicas on every
+    rank) and returns the JSON line of rank 0 (None on the other ranks)."""
+    import torch
+
+    from paper_2512_20252_gb300 import ibdvm
+
+    case = _workload_case(args, workload, args.precision)
     if args.cells:
         case["n"] = [args.cells] * case["dim"]
     stream = torch.cuda.Stream()
@@ -665,12 +731,8 @@ def main():
     e2e_value = job_value(pairs, e2e_steps, world, e2e_s)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        sample = cpu_sample_case(case)
-        v, n, el, oc = time_oracle(sample, args.cpu_sample_seconds)
-        cpu = {"value": v, "unit": "cell-velocity updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} oracle steps ({el:.1f} s) of the workload's gas, body and velocity grid "
-                         f"on {sample['n'][0]} cells per axis ({oc.nfluid} fluid cells x {oc.nvel} velocities)"}
+    if rank == 0 and with_cpu:
+        cpu = cpu_baseline(cpu_sample_case(case), args.cpu_sample_seconds, "the workload's gas, body and velocity grid")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": profiled_traffic(kname, ksrc, pairs),
@@ -678,12 +740,20 @@ def main():
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms / max(sweep_n, 1)}
     fpp = profiled_fp64_flops_per_pair(int(info.dim)) if args.precision == "fp64" else None
     if fpp and sweep_n:
-        # the FP64 path is bound by GB300's FP64 arithmetic rate, not by HBM
+        # the FP64 path is bound by GB300's FP64 arithmetic rate, not by HBM:
+        # its roof is the FMA rate measured now on this GPU (clocks sampled)
+        sampler = ClockSampler(local)
+        sampler.start()
+        peak64, peak_ms = ibdvm.fp64_fma_rate(20000, stream.cuda_stream)
+        peak_clocks = sampler.stop()
         tf = fpp * pairs / (sweep_ms / sweep_n / 1e3) / 1e12
-        roofline = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tf / FP64_NOMINAL_TFLOPS, "traffic": profiled_traffic(kname, ksrc, pairs),
-                    "kernel": kname, "peak_kind": "nominal FP64", "fp64_flops_per_pair": fpp,
+        roofline = {"bound": "alu", "achieved": tf, "peak": peak64, "unit": "TFLOP/s",
+                    "frac": tf / peak64, "traffic": profiled_traffic(kname, ksrc, pairs),
+                    "kernel": kname, "peak_kind": "measured FP64 FMA rate (ibdvm_fp64_fma_rate)",
+                    "peak_clocks": peak_clocks, "peak_ms": peak_ms, "nominal_fp64_tflops": FP64_NOMINAL_TFLOPS,
+                    "fp64_flops_per_pair": fpp,
                     "hbm_achieved_gbs": achieved, "avg_launch_ms": sweep_ms / max(sweep_n, 1)}
+    line = None
     if rank == 0:
         line = {
             "metric": "DVM cell x velocity updates/s",
@@ -698,7 +768,7 @@ def main():
             "vs_baseline": None,
             "dtype": "f32" if esize == 4 else "f64",
             "data": "synthetic",
-            "config": {"workload": DESCRIPTIONS[args.workload] + (f" at {args.cells} cells per axis" if args.cells else ""),
+            "config": {"workload": kn_description(args, workload) + (f" at {args.cells} cells per axis" if args.cells else ""),
                        "precision": args.precision,
                        "cells": int(info.ncell), "fluid_cells": int(info.nfluid), "velocities": int(info.nvel),
                        "l2": (f"L2 flushed between timed steps (f^n is {state_bytes / 1e6:.0f} MB)" if flush_l2
@@ -714,12 +784,12 @@ def main():
             "residual": res,
             "CD": CD if math.isfinite(CD) else None,  # none without a free stream
         }
-        print(json.dumps(line), flush=True)
     solver.close()
     if pg:
         pg.barrier()
-        pg.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
+
+
 
 
 if __name__ == "__main__":

@@ -75,8 +75,11 @@ enum {
   IBDVM_NO_CUTCELL = 1,        /* incident/reflected by the node sign of xi.n only (no Sec. 3.2.3) */
   IBDVM_PLAIN_AVERAGE = 2,     /* weights 1/N_S instead of Eq. upwind (ablation) */
   IBDVM_RHAT_GHOST_TO_FLUID = 4, /* Eq. upwind with r pointing from the ghost to the fluid cell */
-  IBDVM_GHOST_NONNEG = 8         /* ghost values of Eq. extrapolation 2 below zero are set to zero
+  IBDVM_GHOST_NONNEG = 8,        /* ghost values of Eq. extrapolation 2 below zero are set to zero
                                     (off by default: keeps the supersonic cases of Sec. 4.4 positive) */
+  IBDVM_NAIVE_EXTRAPOLATION = 16 /* ablation: no upwind-weighted interpolation; the intermediate ghost
+                                    value of a link is the linear extrapolation 2 f_d - f_ac from its
+                                    donor and auxiliary cell (Sec. 3.3.4; f_d without an auxiliary cell) */
 };
 
 /* Uniform Cartesian grid: dim = 2 or 3, n[a] cells on [lo[a], hi[a]]. */
@@ -326,6 +329,17 @@ ibdvm_status ibdvm_residual_noalloc(const double *W_old, const double *W_new,
    [0, 2^18] (a poll suspends a few microseconds on GB300, so 2^18 polls are about
    one second, the bound of the sweeps); errors: IBDVM_E_INVAL, IBDVM_E_CUDA. */
 ibdvm_status ibdvm_selftest_bounded_wait(int deliver, int spin_limit, double *seconds, void *cuda_stream);
+
+/* This GPU's FP64 arithmetic rate, the roof of the FP64 path (whose sweep is
+   bound by the FP64 pipe, not by HBM): eight independent FMA chains per
+   thread, iters x 4 FMAs per chain, on eight blocks of 256 threads per SM,
+   timed with CUDA events on cuda_stream (NULL = default) after one untimed
+   launch.  *tflops receives the rate in TFLOP/s (an FMA counts as two
+   flops), *ms (nullable) the time of the timed launch.  Allocates and frees a
+   small device buffer; IBDVM_E_INVAL for iters <= 0 or tflops NULL,
+   IBDVM_E_CUDA on a CUDA failure.  A measurement of the device, not of the
+   paper's method. */
+ibdvm_status ibdvm_fp64_fma_rate(int iters, double *tflops, double *ms, void *cuda_stream);
 
 ibdvm_status ibdvm_get_info(const ibdvm_ctx *ctx, ibdvm_info *info);
 ibdvm_status ibdvm_set_stream(ibdvm_ctx *ctx, void *cuda_stream);

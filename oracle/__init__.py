@@ -45,7 +45,7 @@ def build(force: bool = False) -> str:
     ):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         )
         os.replace(tmp, _SO)
     return _SO
@@ -108,6 +108,7 @@ def _load():
             sig = {
                 "or_create": ([P], V),
                 "or_destroy": ([V], None),
+                "or_set_threads": ([V, ctypes.c_int], None),
                 "or_sizes": ([V, _LL], None),
                 "or_dt": ([V], ctypes.c_double),
                 "or_velocities": ([V, _D, _D], None),
@@ -213,11 +214,12 @@ def _params(cfg: dict) -> tuple[_Params, object]:
 class OracleCase:
     """One case of the oracle: geometry, velocity grid and state f[cell][k][comp]."""
 
-    def __init__(self, cfg: dict):
+    def __init__(self, cfg: dict, threads: int = 1):
         self.lib = _load()
         self.cfg = dict(cfg)
         self._p, self._keep = _params(cfg)
         self.h = self.lib.or_create(ctypes.byref(self._p))
+        self.set_threads(threads)
         s = np.zeros(6, dtype=np.int64)
         self.lib.or_sizes(self.h, s.ctypes.data_as(_LL))
         self.ncell, self.nvel, self.ncomp, self.nlink, self.nghost, self.nfluid = (int(x) for x in s)
@@ -228,6 +230,12 @@ class OracleCase:
         if h:
             self.lib.or_destroy(h)
             self.h = None
+
+    def set_threads(self, threads: int) -> None:
+        """Host threads of the per-ghost and per-cell loops (bitwise the same
+        results for any count)."""
+        self.threads = max(1, int(threads))
+        self.lib.or_set_threads(self.h, self.threads)
 
     # geometry and grids -------------------------------------------------
     @property

@@ -127,6 +127,7 @@ struct or_case {
   double *wg;   /* incident-side measure per link and velocity */
   double *lval; /* ghost value f*_gc per link, velocity, component */
   double *wrho; /* rho_w of the diffuse domain faces of the state last given (C24), [cell][6] */
+  int nthreads; /* host threads of the per-ghost and per-cell loops (1 by default) */
   int any_wall;
   double dt, mu0, Uinf[3];
 };
@@ -582,6 +583,7 @@ or_case *or_create(const or_params *p)
 {
   or_case *C = (or_case *)xcalloc(1, sizeof(or_case));
   C->p = *p;
+  C->nthreads = 1;
   if (p->kind == OR_BODY_POLYGON && p->nverts > 0) {
     C->verts = (double *)xcalloc(2 * p->nverts, sizeof(double));
     memcpy(C->verts, p->verts, sizeof(double) * 2 * p->nverts);
@@ -781,6 +783,8 @@ or_case *or_create(const or_params *p)
   for (int i = 0; i < 2 * C->dim; ++i) C->any_wall |= (p->wall[i] != 0);
   return C;
 }
+
+void or_set_threads(or_case *C, int nthreads) { C->nthreads = nthreads > 0 ? nthreads : 1; }
 
 void or_destroy(or_case *C)
 {
@@ -1005,13 +1009,18 @@ void or_ghost_band(const or_case *C, const double *f, double *fgc_out, double *f
                    double *fiw_out, double *fstarw_out, double *fstargc_out, double *rhow_out)
 {
   int D = C->dim, nv = C->nv, nc = C->ncomp;
+  double alpha = C->p.accom;
+  domain_walls(C, f); /* the halo values the pre-ghost slopes see */
+  /* ghosts are independent of each other: every ghost writes only its own
+     links, so the result does not depend on the number of threads */
+#pragma omp parallel num_threads(C->nthreads)
+  {
   double *fgc = (double *)xcalloc((size_t)nv * nc, sizeof(double));
   double *fsp = (double *)xcalloc((size_t)nv * nc, sizeof(double));
   double *fi = (double *)xcalloc((size_t)nv * nc, sizeof(double));
   double *fs = (double *)xcalloc((size_t)nv * nc, sizeof(double));
   double *Gw = (double *)xcalloc((size_t)nv * nc, sizeof(double));
-  double alpha = C->p.accom;
-  domain_walls(C, f); /* the halo values the pre-ghost slopes see */
+#pragma omp for schedule(dynamic)
   for (int gi = 0; gi < C->nghost; ++gi) {
     const or_ghost *G = &C->ghosts[gi];
     /* step 2: intermediate ghost value f_gc (shared by the ghost's links) */
@@ -1090,6 +1099,7 @@ void or_ghost_band(const or_case *C, const double *f, double *fgc_out, double *f
   free(fi);
   free(fs);
   free(Gw);
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1200,15 +1210,19 @@ int or_step(or_case *C, int nsteps, double *residual)
 {
   int D = C->dim, nv = C->nv, nc = C->ncomp;
   int nw = D + 2;
-  double *gS = (double *)xcalloc((size_t)nv * nc, sizeof(double));
   double *Wold = (double *)xcalloc((size_t)C->nc * nw, sizeof(double));
   double *Wnew = (double *)xcalloc((size_t)C->nc * nw, sizeof(double));
   double res = 0.0;
   for (int it = 0; it < nsteps; ++it) {
     /* ghost band on f^n: link values f*_gc */
     or_ghost_band(C, C->f, NULL, NULL, NULL, NULL, C->lval, NULL);
-    /* fluid cells: transport and relaxation */
+    /* fluid cells: transport and relaxation (every cell writes only its own
+       values, so the result does not depend on the number of threads) */
     memcpy(C->fnew, C->f, sizeof(double) * (size_t)C->nc * nv * nc);
+#pragma omp parallel num_threads(C->nthreads)
+    {
+    double *gS = (double *)xcalloc((size_t)nv * nc, sizeof(double));
+#pragma omp for schedule(dynamic, 16)
     for (long c = 0; c < C->nc; ++c) {
       if (C->type[c] != OR_FLUID) continue;
       double rho, U[3], T, q[3], tau;
@@ -1228,6 +1242,8 @@ int or_step(or_case *C, int nsteps, double *residual)
           F(C, C->fnew, c, k)[m] = fc - C->dt * div + C->dt / tau * (gS[k * nc + m] - fc);
         }
     }
+    free(gS);
+    }
     double *t = C->f;
     C->f = C->fnew;
     C->fnew = t;
@@ -1235,7 +1251,6 @@ int or_step(or_case *C, int nsteps, double *residual)
       if (C->type[c] == OR_FLUID) conservative(C, C->f, c, Wnew + c * nw);
     res = or_residual(C, Wold, Wnew);
   }
-  free(gS);
   free(Wold);
   free(Wnew);
   if (residual) *residual = res;

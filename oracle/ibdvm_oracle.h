@@ -83,6 +83,11 @@ typedef struct or_case or_case;
 
 or_case *or_create(const or_params *p);
 void or_destroy(or_case *C);
+/* host threads of the per-ghost and per-cell loops (OpenMP when the library is
+   built with it; default 1).  Ghosts and cells are computed independently and
+   the reductions (residual, forces) stay serial, so the results are bitwise
+   the same for any thread count. */
+void or_set_threads(or_case *C, int nthreads);
 
 /* sizes: ncell, nvel, ncomp, nlink, nghost, nfluid */
 void or_sizes(const or_case *C, long long *out6);

@@ -694,6 +694,7 @@ template <typename T> struct GhostArgs {
   double dx[3];
   double Tw, Uw[3], accom;
   int plain_average;
+  int naive; // the linear extrapolation 2 f_d - f_ac in place of Eq. extrapolation 1 (Sec. 3.3.4)
   HaloArgs<T> H; // the domain halo the pre-ghost slopes see
   int n[3];
   int nodes_rule; // non-uniform velocity nodes (the specular interpolation bisects)
@@ -795,7 +796,7 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
     T xiT[3];
     for (int a = 0; a < D; ++a) xiT[a] = G.xiT[a * G.nvp + k];
     T wsum = T(0);
-    for (int j = 0; j < ns; ++j) {
+    for (int j = 0; j < (G.naive ? 0 : ns); ++j) {
       const double *sd = G.s_dbl + 8 * (s0 + j);
       // xi.r without contraction: tangential velocities give an exact zero
       T xr = T(0);
@@ -808,7 +809,14 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
     T fgc[NC];
 #pragma unroll
     for (int m = 0; m < NC; ++m) fgc[m] = T(0);
-    for (int j = 0; j < ns; ++j) {
+    if (G.naive) { // the construction without upwind weighting, Sec. 3.3.4
+#pragma unroll
+      for (int m = 0; m < NC; ++m) {
+        const T fd = G.f[((size_t)donor * G.nvp + k) * NC + m];
+        fgc[m] = (aux >= 0) ? T(2) * fd - G.f[((size_t)aux * G.nvp + k) * NC + m] : fd;
+      }
+    }
+    for (int j = 0; j < (G.naive ? 0 : ns); ++j) {
       const int *si = G.s_int + 8 * (s0 + j);
       const double *sd = G.s_dbl + 8 * (s0 + j);
       T wt;
@@ -1442,6 +1450,7 @@ template <typename T> GhostArgs<T> ghost_args(const ibdvm_ctx *ctx, int cur, dou
   G.Tw = g.body.T_w;
   G.accom = g.body.accom_alpha;
   G.plain_average = (g.gas.flags & IBDVM_PLAIN_AVERAGE) ? 1 : 0;
+  G.naive = (g.gas.flags & IBDVM_NAIVE_EXTRAPOLATION) ? 1 : 0;
   G.H = halo_args<T>(ctx);
   for (int a = 0; a < 3; ++a) G.n[a] = g.n[a];
   G.nodes_rule = (g.rule == IBDVM_RULE_NODES) ? 1 : 0;

@@ -7,7 +7,8 @@ PyTorch fallback.
 Case descriptions are plain dicts (see ``workloads``): dim, n, lo, hi, nv, vlo,
 vhi, rule, Kn, Ma, Pr, gamma, omega_vhs, alpha_vhs, rho_inf, T_inf, dir, cfl,
 dt, precision ("fp64" | "mixed"), cutcell, upwind (1 upwind weights, 2 the
-reverse unit vector, 0 plain average), ghost_nonneg (1: ghost values below
+reverse unit vector, 0 plain average, 3 the linear extrapolation without
+interpolation of Sec. 3.3.4), ghost_nonneg (1: ghost values below
 zero set to zero), body = {kind, center, radii, angle,
 verts, accom, Tw, Uw, Lref} and domain_walls (six entries for the faces x-,
 x+, y-, y+, z-, z+: None for a freestream face, {Tw, Uw} for a diffuse wall).
@@ -28,7 +29,7 @@ STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_UNSTABLE", 5: 
           6: "E_NOTCONVERGED", 7: "E_TIMEOUT", 8: "E_STATE"}
 BODY = {"none": 0, "circle": 1, "ellipse": 2, "sphere": 3, "polygon": 4, "halfspace": 5}
 FLUID, GHOST, SOLID = 0, 1, 2
-NO_CUTCELL, PLAIN_AVERAGE, RHAT_GHOST_TO_FLUID, GHOST_NONNEG = 1, 2, 4, 8
+NO_CUTCELL, PLAIN_AVERAGE, RHAT_GHOST_TO_FLUID, GHOST_NONNEG, NAIVE_EXTRAPOLATION = 1, 2, 4, 8, 16
 
 
 class IbdvmError(RuntimeError):
@@ -128,6 +129,7 @@ SIGNATURES = {
     "ibdvm_set_f": ([_V, _D], _S),
     "ibdvm_get_f_native": ([_V, _V, ctypes.c_size_t], _S),
     "ibdvm_set_f_native": ([_V, _V, ctypes.c_size_t], _S),
+    "ibdvm_fp64_fma_rate": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _V], _S),
     "ibdvm_velocity_positions": ([_V, ctypes.POINTER(ctypes.c_int)], _S),
     "ibdvm_ghost_band": ([_V, _D, _D, _D, _D], _S),
     "ibdvm_wall": ([_V, _D], _S),
@@ -200,6 +202,17 @@ def load(path: str | None = None) -> ctypes.CDLL:
     return _lib
 
 
+def fp64_fma_rate(iters: int = 20000, stream: int | None = None):
+    """This GPU's FP64 FMA rate in TFLOP/s and the timed launch in ms
+    (ibdvm_fp64_fma_rate)."""
+    lib = load()
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = lib.ibdvm_fp64_fma_rate(int(iters), ctypes.byref(tf), ctypes.byref(ms), _V(stream or 0))
+    if st != OK:
+        raise IbdvmError(st, "fp64_fma_rate")
+    return tf.value, ms.value
+
+
 def _a3(v, fill=0.0):
     v = list(v) + [fill] * 3
     return v[:3]
@@ -248,6 +261,8 @@ def descriptors(case: dict):
         flags |= PLAIN_AVERAGE
     elif up == 2:
         flags |= RHAT_GHOST_TO_FLUID
+    elif up == 3:
+        flags |= NAIVE_EXTRAPOLATION
     if int(case.get("ghost_nonneg", 0)):
         flags |= GHOST_NONNEG
     s.flags = flags

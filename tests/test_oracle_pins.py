@@ -276,6 +276,48 @@ def test_p5_linear_exactness_2d(body, n, upwind):
     assert checked >= oc.nlink // 2
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_naive_extrapolation_is_linear_along_the_link(dim):
+    """The construction without upwind weighting (Sec. 3.3.4, reading C27):
+    the intermediate ghost value of a link is 2 f_d - f_ac, the value at the
+    ghost centre of the line through the donor and the auxiliary cell, so a
+    linear field is reproduced at the ghost centre (and, through Eqs. fsp and
+    fw, at the intersect point); without an auxiliary cell it is f_d.  For a
+    field that is not linear it differs from the upwind-weighted value of Eq.
+    extrapolation 1."""
+    if dim == 2:
+        cfg = wl.small_2d("ellipse", n=24, nv=6, upwind=3)
+    else:
+        cfg = case3d(n=12, nv=4, V=4.0, L=2.0, body=wl.sphere(0.7))
+        cfg["upwind"] = 3
+    oc = oracle.OracleCase(cfg)
+    rng = np.random.default_rng(9)
+    f, exact = _linear_field(oc, rng, cfg["n"], cfg["lo"], cfg["hi"], dim)
+    gb = oc.ghost_band(f)
+    L = oc.links()
+    n = np.asarray(cfg["n"])
+    dx = (np.asarray(cfg["hi"]) - np.asarray(cfg["lo"])) / n
+    strides = [1, n[0], n[0] * (n[1] if dim == 3 else 1)]
+
+    def centre(c):
+        return np.array([cfg["lo"][a] + ((c // strides[a]) % n[a] + 0.5) * dx[a] for a in range(dim)])
+
+    with_aux = 0
+    for l in range(oc.nlink):
+        if L["aux"][l] >= 0:
+            np.testing.assert_allclose(gb["fgc"][l], exact(centre(L["ghost"][l])), rtol=1e-12, atol=1e-13)
+            np.testing.assert_allclose(gb["fiw"][l], exact(L["xw"][l]), rtol=1e-12, atol=1e-13)
+            with_aux += 1
+        else:
+            np.testing.assert_array_equal(gb["fgc"][l], f[L["donor"][l]])
+    assert with_aux >= oc.nlink // 2
+    # a quadratic field tells the two constructions apart
+    fq = f * (1.0 + 0.3 * rng.uniform(size=(oc.ncell, 1, 1)))
+    up = dict(cfg, upwind=1)
+    g_up = oracle.OracleCase(up).ghost_band(fq)["fgc"]
+    assert np.abs(oc.ghost_band(fq)["fgc"] - g_up).max() > 1e-3 * np.abs(g_up).max()
+
+
 def test_p5_linear_exactness_3d():
     cfg = case3d(n=12, nv=4, V=4.0, L=2.0, body=wl.sphere(0.7))
     oc = oracle.OracleCase(cfg)

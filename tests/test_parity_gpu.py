@@ -91,8 +91,8 @@ def test_perturbed_state_parity(body):
     assert rg == pytest.approx(ro, rel=1e-9)
 
 
-@pytest.mark.parametrize("variant", ["midpoint", "nocut", "plain_average", "rhat_reverse",
-                                     "accom_0.6", "hot_moving_wall", "bgk", "odd_grid"])
+@pytest.mark.parametrize("variant", ["midpoint", "nocut", "plain_average", "rhat_reverse", "naive",
+                                     "accom_0.6", "hot_moving_wall", "bgk", "odd_grid", "naive_3d"])
 def test_method_variants_parity(variant):
     case = wl.small_2d("ellipse", n=24, nv=10, Kn=0.08, Ma=0.5)
     if variant == "midpoint":
@@ -103,6 +103,10 @@ def test_method_variants_parity(variant):
         case["upwind"] = 0
     elif variant == "rhat_reverse":
         case["upwind"] = 2
+    elif variant == "naive":
+        case["upwind"] = 3  # no interpolation: 2 f_d - f_ac (Sec. 3.3.4)
+    elif variant == "naive_3d":
+        case = wl._case(3, 10, 2.0, 8, 4.5, 0.1, 0.5, wl.sphere(0.6), upwind=3)
     elif variant == "accom_0.6":
         case["body"]["accom"] = 0.6
     elif variant == "hot_moving_wall":
@@ -179,6 +183,32 @@ def test_mixed_precision_against_fp64_oracle():
             assert rel_err(Wg[fl, i], Wo[fl, i]) < 1e-5, i
     CDg = g.forces()[2]
     CDo = o.forces()[2]
+    assert abs(CDg - CDo) < 1e-4 * abs(CDo)
+    assert rg == pytest.approx(ro, rel=1e-3)
+
+
+@pytest.mark.parametrize("Kn", [0.01, 1.0])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_knudsen_sweep_against_the_oracle(Kn, precision):
+    """The Knudsen numbers of the 512^2 cylinder sweep other than 0.1 (Sec. 4:
+    tau = mu / p with the VHS viscosity mu0 T^omega, mu0 proportional to Kn) on a
+    small cylinder with the sweep's velocity box and Ma, 20 steps.  Kn 0.01 is
+    the stiffest relaxation (dt / tau about 0.09 here); Kn 1 nearly free
+    transport.  FP64 at 1e-11 on f and W; the mixed path at 1e-5 on W and 1e-4
+    on C_D."""
+    case = wl._case(2, 40, 4.0, 16, 6.0, Kn, 0.5, wl.circle(0.5), precision=precision)
+    g, o, rg, ro = pair(case, 20)
+    if precision == "fp64":
+        compare(g, o)
+        assert rg == pytest.approx(ro, rel=1e-9)
+        return
+    fl = o.cell_types() == oracle.FLUID
+    Wg, _, _ = g.moments()
+    Wo, _ = o.moments()
+    for i in range(4):
+        if np.abs(Wo[fl, i]).max() > 1e-9:
+            assert rel_err(Wg[fl, i], Wo[fl, i]) < 1e-5, i
+    CDg, CDo = g.forces()[2], o.forces()[2]
     assert abs(CDg - CDo) < 1e-4 * abs(CDo)
     assert rg == pytest.approx(ro, rel=1e-3)
 
