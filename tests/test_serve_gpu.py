@@ -80,6 +80,28 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
     mix.close()
 
 
+def test_converged_results_are_the_same_alone_and_in_the_mix():
+    """Requests that run to the convergence criterion of Sec. 4 (residual below
+    1e-6): each converges at the same step count, with the same residual and
+    forces, alone and in a mix of 2D and 3D requests (bit-identical in 2D; in 3D
+    a batch of one and a batch of several run the same batched kernel)."""
+    a, b, _, d, e = requests()
+    b = dict(b, nv=[16, 16])  # 8 velocities per axis lose positivity over a long run
+    cases = [a, b, d, e]
+    mix = ibdvm.Server(tol=1e-6, max_steps=30000, steps_per_round=20)
+    rm = run(mix, cases, max_polls=100000)
+    mix.close()
+    for c, r in zip(cases, rm):
+        assert r["done"] == 1 and r["status"] == 0, r  # converged
+        assert r["residual"] < 1e-6
+        alone = ibdvm.Server(tol=1e-6, max_steps=30000, steps_per_round=20)
+        (ra,) = run(alone, [c], max_polls=100000)
+        alone.close()
+        assert ra["status"] == 0 and ra["steps"] == r["steps"]
+        assert ra["residual"] == r["residual"]
+        assert (ra["CD"], ra["CL"], ra["Q"]) == (r["CD"], r["CL"], r["Q"])
+
+
 def test_admission_by_hbm_budget():
     cases = requests()[:3]
     probe = ibdvm.Server(tol=0.0, max_steps=2, steps_per_round=2)
