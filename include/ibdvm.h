@@ -146,9 +146,17 @@ typedef struct {
                         2: TMA-staged 3D FP32 sweep (sweep3d_tma.cu) */
 } ibdvm_info;
 
-/* Creates a context: velocity grid, freestream Maxwellian in every cell, no
-   body.  cuda_stream is a cudaStream_t (NULL = the legacy default stream).
-   Errors: IBDVM_E_INVAL (bad descriptor), IBDVM_E_NOMEM, IBDVM_E_CUDA. */
+/* Creates a context: the uniform Cartesian grid and the discrete velocity
+   grid with its quadrature weights (Sec. 2.2, Eq. quadrature), the gas in the
+   non-dimensional form of Sec. 4 (rho_inf = T_inf = 1, |U_inf| = Ma sqrt(gamma
+   / 2), the VHS viscosity mu = mu0 T^omega with mu0 from Kn, tau = mu / p),
+   dt from the CFL number when gas->dt <= 0 (dt = CFL / sum_a max|xi_a| / dx_a,
+   a reading: the paper gives none), the freestream Maxwellian in every cell,
+   no body.  cuda_stream is a cudaStream_t (NULL = the legacy default stream);
+   the context keeps it for every launch.  The context owns all device memory
+   it allocates (ibdvm_destroy frees it); descriptors are copied, not kept.
+   Errors: IBDVM_E_INVAL (bad descriptor), IBDVM_E_NOMEM (device memory short:
+   checked against cudaMemGetInfo before allocating), IBDVM_E_CUDA. */
 ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *vgrid,
                                const ibdvm_gas_desc *gas, void *cuda_stream, ibdvm_ctx **out);
 
@@ -309,10 +317,15 @@ ibdvm_status ibdvm_reset_kernel_times(ibdvm_ctx *ctx);
    Partial sums live in a built-in device array of 8192 x 10 doubles (640 KiB,
    held by every GPU that loads the library until exit), so ncell is limited
    to 2,097,152; larger sizes return IBDVM_E_INVAL with the limit in
-   ibdvm_last_error(NULL).  The first call on a device looks up the array's
-   device address (cudaGetSymbolAddress) and caches it: make that first call
-   before any stream capture.  All calls share the array and it keeps the last
-   call's contents; calls that overlap on the GPU race on it and must be
+   ibdvm_last_error(NULL).  The first call in each CUDA context (the one
+   current at the call: the device's primary context for runtime-API callers,
+   made current if none is; or a context the caller made current with the
+   driver API) looks up the array's device address in that context
+   (cudaGetSymbolAddress) and caches it under the context's handle: make that
+   first call before any stream capture.  A context destroyed and replaced by
+   one with the same handle (cudaDeviceReset) is not detected: make the first
+   call again outside any capture.  All calls share the array and it keeps the
+   last call's contents; calls that overlap on the GPU race on it and must be
    serialised by the caller. */
 ibdvm_status ibdvm_residual_noalloc(const double *W_old, const double *W_new,
                                     const unsigned char *celltype, long long ncell, int dim,

@@ -13,13 +13,19 @@
 // The array is a file-scope __device__ symbol of kMaxBlocks * 2 * 5 doubles
 // (640 KiB); every GPU that loads the library reserves it until the process
 // exits.  Host code cannot use the symbol's name as a device address, so the
-// first call on each device looks the address up with cudaGetSymbolAddress
-// (with that device current) and caches it; make that first call before any
-// stream capture.  All calls share the array and it keeps the last call's
+// first call in each CUDA context (the context current at the call: the
+// device's primary context for runtime-API callers, or a context the caller
+// made current with the driver API) looks the address up with
+// cudaGetSymbolAddress and caches it under that context's handle; make that
+// first call before any stream capture.  A context that is destroyed and
+// replaced by a new one with the same handle is not detected: after
+// cudaDeviceReset, a caller that keeps using this entry point makes its first
+// call again outside any capture.  All calls share the array and it keeps the last call's
 // partial sums: every block overwrites its own slots before they are read, so
 // nothing needs clearing, but two calls that overlap on the GPU (different
 // streams, or different host threads) race on it and must be serialised by
 // the caller.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -37,13 +43,34 @@ constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 8192;                  // at most kMaxBlocks * kThreads cells per call
 constexpr long long kMaxCells = static_cast<long long>(kMaxBlocks) * kThreads; // 2,097,152
 constexpr int kMaxW = 5;                          // conservative variables in 3D
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
 
 // per-block sums of (dW_i)^2 and |W_i|, [block][2 * NW]
 static __device__ __align__(256) double g_residual_scratch[kMaxBlocks * 2 * kMaxW];
 
 std::mutex g_mu;
-double *g_scratch_addr[kMaxDevices] = {};
+// the array's address in each context met so far
+struct CtxAddr {
+  CUcontext ctx;
+  double *addr;
+};
+CtxAddr g_scratch_addr[kMaxContexts] = {};
+int g_nctx = 0;
+
+// the current CUDA context through the driver entry point (no link to libcuda)
+CUresult current_context(CUcontext *out) {
+  using Fn = CUresult (*)(CUcontext *);
+  static Fn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return CUDA_ERROR_NOT_SUPPORTED;
+    fn = reinterpret_cast<Fn>(p);
+  }
+  return fn(out);
+}
 
 template <int NW>
 __global__ void __launch_bounds__(kThreads)
@@ -131,18 +158,28 @@ extern "C" ibdvm_status ibdvm_residual_noalloc(const double *W_old, const double
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(std::string("residual_noalloc: cudaGetDevice: ") + cudaGetErrorString(e), IBDVM_E_CUDA);
-  if (dev < 0 || dev >= kMaxDevices) return fail("residual_noalloc: device index beyond 63", IBDVM_E_INVAL);
+  CUcontext ctx = nullptr;
+  if (current_context(&ctx) != CUDA_SUCCESS) return fail("residual_noalloc: cuCtxGetCurrent failed", IBDVM_E_CUDA);
+  if (!ctx) {
+    // no context current yet: make the device's primary context current
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess || current_context(&ctx) != CUDA_SUCCESS || !ctx)
+      return fail("residual_noalloc: no CUDA context could be made current", IBDVM_E_CUDA);
+  }
   double *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    for (int i = 0; i < g_nctx && !scratch; ++i)
+      if (g_scratch_addr[i].ctx == ctx) scratch = g_scratch_addr[i].addr;
+    if (!scratch) {
+      if (g_nctx == kMaxContexts) return fail("residual_noalloc: more than 64 CUDA contexts", IBDVM_E_INVAL);
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_residual_scratch);
       if (e != cudaSuccess)
         return fail(std::string("residual_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e), IBDVM_E_CUDA);
-      g_scratch_addr[dev] = static_cast<double *>(p);
+      scratch = static_cast<double *>(p);
+      g_scratch_addr[g_nctx++] = CtxAddr{ctx, scratch};
     }
-    scratch = g_scratch_addr[dev];
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int nblk = static_cast<int>((ncell + kThreads - 1) / kThreads);
