@@ -418,11 +418,12 @@ ibdvm_status ibdvm_batch_step(ibdvm_batch *b, int nsteps, double *residuals, int
 ibdvm_status ibdvm_batch_forces(ibdvm_batch *b, double *F, double *Q, double *CD, double *CL);
 
 /* Tiling of the sweep's work items.  rows: target rows (3D: planes) per item
-   (0 = whole columns); kpt: velocities per lane in 2D, 4 (chunks of 128
-   velocities where the member's padded velocity count is a multiple of 128,
-   else 64), 2 (chunks of 64) or 0 (= 4); 3D members always take chunks of
-   128.  get_tiling also reports the number of work items, the
-   persistent grid and whether graphs are in use. */
+   (0 = whole columns).  kpt (0, 2 or 4) is accepted and has no effect: every
+   member's sweep takes the velocity chunks of its orthant layout (2D: 192,
+   128 or 64 velocities; 3D: 256 or 128), and get_tiling reports the
+   velocities per lane of the first member's chunk (chunk / 32; 0 without
+   members), the number of work items, the persistent grid and whether graphs
+   are in use. */
 typedef struct {
   int rows, kpt, nitems, grid, graphs;
 } ibdvm_batch_tiling;
@@ -430,10 +431,10 @@ ibdvm_status ibdvm_batch_set_tiling(ibdvm_batch *b, int rows, int kpt);
 ibdvm_status ibdvm_batch_get_tiling(const ibdvm_batch *b, ibdvm_batch_tiling *out);
 
 /* Autotuner: for each candidate tiling (rows in {16, 32, 64, 128, whole
-   columns} x kpt in {4, 2}; 3D: kpt 4 only) times steps_per_trial batched
-   steps (even, >= 2) with CUDA events on the batch's stream, after one
-   untimed pair of steps, and keeps the fastest.  The trials are real steps:
-   every member advances 10 x (steps_per_trial + 2) steps (3D: 5 x).  best_ms (nullable) receives
+   columns}) times steps_per_trial batched steps (even, >= 2) with CUDA
+   events on the batch's stream, after one untimed pair of steps, and keeps
+   the fastest.  The trials are real steps: every member advances
+   5 x (steps_per_trial + 2) steps.  best_ms (nullable) receives
    the kept tiling's time per step.  Errors: as ibdvm_batch_step;
    IBDVM_E_INVAL for a bad steps_per_trial; IBDVM_E_STATE with no members. */
 ibdvm_status ibdvm_batch_tune(ibdvm_batch *b, int steps_per_trial, double *best_ms);

@@ -26,7 +26,7 @@ struct ibdvm_batch {
   std::vector<char> stepped;    // member has stepped in this batch
   bool dirty = true;
   int par = 0;                  // steps since the tables were built, mod 2
-  int rows = 0, kpt = 0;        // tiling of the sweep's work items
+  int rows = 0, kpt = 0;        // tiling of the sweep's work items (kpt: kept, no effect)
   GroupTables gt;
   SweepTables st;
   double *d_res = nullptr;      // [cap] residual of each member's last step
@@ -138,11 +138,8 @@ void ensure_capacity(ibdvm_batch *b) {
   b->cap = cap;
 }
 
-int member_kpt(const ibdvm_batch *b, const ibdvm_ctx *ctx) {
-  if (ctx->dim == 3) return 0; // the 3D sweep takes the chunks of the context's octant layout
-  const int want = (b->kpt == 2) ? 2 : 4;
-  return (want == 4 && tma_batch_kpt_max(ctx) == 4) ? 4 : 2;
-}
+// velocities per lane of a member's sweep: those of its orthant layout's chunk
+int member_kpt(const ibdvm_ctx *ctx) { return tma_batch_kpt_max(ctx); }
 
 // (re)builds the device tables when the membership, a body or the tiling changed
 void build(ibdvm_batch *b) {
@@ -156,9 +153,8 @@ void build(ibdvm_batch *b) {
   ensure_capacity(b);
   std::vector<int> kpt(n), nchunk(n);
   for (size_t i = 0; i < n; ++i) {
-    kpt[i] = member_kpt(b, b->members[i]);
-    const ibdvm_ctx *ctx = b->members[i];
-    nchunk[i] = (ctx->dim == 3) ? ctx->tma_nchunk : ctx->nvp / (32 * kpt[i]);
+    kpt[i] = member_kpt(b->members[i]);
+    nchunk[i] = b->members[i]->tma_nchunk;
   }
   bcheck(b, group_build(b->members, nchunk, b->d_res, b->d_flags, b->d_forces, b->gt, b->stream),
          "build the grouped launch tables");
@@ -447,9 +443,9 @@ ibdvm_status ibdvm_batch_set_tiling(ibdvm_batch *b, int rows, int kpt) {
     b->err = "rows must be >= 0 and kpt one of 0, 2, 4";
     return IBDVM_E_INVAL;
   }
-  if (rows != b->rows || kpt != b->kpt) {
+  b->kpt = kpt; // no effect: every member takes the chunk of its velocity layout
+  if (rows != b->rows) {
     b->rows = rows;
-    b->kpt = kpt;
     b->dirty = true;
   }
   return IBDVM_OK;
@@ -459,7 +455,7 @@ ibdvm_status ibdvm_batch_set_tiling(ibdvm_batch *b, int rows, int kpt) {
 ibdvm_status ibdvm_batch_get_tiling(const ibdvm_batch *b, ibdvm_batch_tiling *out) {
   if (!b || !out) return IBDVM_E_INVAL;
   out->rows = b->rows;
-  out->kpt = b->kpt ? b->kpt : 4;
+  out->kpt = b->members.empty() ? 0 : member_kpt(b->members[0]);
   out->nitems = b->dirty ? 0 : b->st.nitems;
   out->grid = b->dirty ? 0 : b->st.grid;
   out->graphs = (b->graphs_enabled && !b->profiling && b->stream != nullptr) ? 1 : 0;
@@ -477,38 +473,32 @@ ibdvm_status ibdvm_batch_tune(ibdvm_batch *b, int steps_per_trial, double *best_
     return IBDVM_E_STATE;
   }
   const int rows_c[5] = {16, 32, 64, 128, 0};
-  const int kpt_c[2] = {4, 2};
-  const int nkpt = (b->members[0]->dim == 3) ? 1 : 2; // 3D: 128-velocity chunks only
   cudaEvent_t e0, e1;
   bcheck(b, cudaEventCreate(&e0), "create event");
   bcheck(b, cudaEventCreate(&e1), "create event");
   double best = 1e300;
-  int best_rows = b->rows, best_kpt = b->kpt;
+  int best_rows = b->rows;
   ibdvm_status st = IBDVM_OK;
   try {
-    for (int ik = 0; ik < nkpt; ++ik)
-      for (int r : rows_c) {
-        const int kp = kpt_c[ik];
-        b->rows = r;
-        b->kpt = kp;
-        b->dirty = true;
-        build(b);
-        bcheck(b, cudaMemsetAsync(b->d_flags, 0, b->members.size() * sizeof(int), b->stream), "clear flags");
-        advance(b, 2); // warm-up pair: captures the graphs of this tiling
-        bcheck(b, cudaEventRecord(e0, b->stream), "record event");
-        advance(b, steps_per_trial);
-        bcheck(b, cudaEventRecord(e1, b->stream), "record event");
-        st = collect(b, nullptr, nullptr);
-        if (st != IBDVM_OK) throw BFail{st};
-        float ms = 0.f;
-        bcheck(b, cudaEventElapsedTime(&ms, e0, e1), "event time");
-        const double per = ms / steps_per_trial;
-        if (per < best) {
-          best = per;
-          best_rows = r;
-          best_kpt = kp;
-        }
+    for (int r : rows_c) {
+      b->rows = r;
+      b->dirty = true;
+      build(b);
+      bcheck(b, cudaMemsetAsync(b->d_flags, 0, b->members.size() * sizeof(int), b->stream), "clear flags");
+      advance(b, 2); // warm-up pair: captures the graphs of this tiling
+      bcheck(b, cudaEventRecord(e0, b->stream), "record event");
+      advance(b, steps_per_trial);
+      bcheck(b, cudaEventRecord(e1, b->stream), "record event");
+      st = collect(b, nullptr, nullptr);
+      if (st != IBDVM_OK) throw BFail{st};
+      float ms = 0.f;
+      bcheck(b, cudaEventElapsedTime(&ms, e0, e1), "event time");
+      const double per = ms / steps_per_trial;
+      if (per < best) {
+        best = per;
+        best_rows = r;
       }
+    }
   } catch (const BFail &) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -517,7 +507,6 @@ ibdvm_status ibdvm_batch_tune(ibdvm_batch *b, int steps_per_trial, double *best_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->rows = best_rows;
-  b->kpt = best_kpt;
   b->dirty = true;
   build(b);
   if (best_ms) *best_ms = best;

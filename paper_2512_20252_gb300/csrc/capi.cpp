@@ -551,21 +551,19 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     ctx->nv = G.nv;
     ctx->nvp = G.nvp;
     ctx->ncell = G.ncell;
-    // the stored order of the velocities: natural, or grouped by octant for
-    // the 3D TMA sweep (IBDVM_NO_TMA=1 keeps the plain sweep and the natural order)
+    // the stored order of the velocities: natural, or grouped by orthant for
+    // the FP32 TMA sweeps (IBDVM_NO_TMA=1 keeps the plain sweep and the natural order)
     const char *no_tma = std::getenv("IBDVM_NO_TMA");
     const bool tma_off = no_tma && no_tma[0] == '1';
     ctx->kst_h.resize(G.nv);
     for (int i = 0; i < G.nv; ++i) ctx->kst_h[i] = i;
-    if (!tma_off && G.dim == 3 && gas->precision == IBDVM_MIXED) {
+    if (!tma_off && gas->precision == IBDVM_MIXED && tma_encoder_available()) {
       std::vector<int> kst;
       int nvp = 0;
-      const int kc = tma3_octant_layout(G, kst, nvp);
-      if (kc > 0) {
-        ctx->oct_kc = kc;
-        ctx->kst_h = std::move(kst);
-        ctx->nvp = nvp;
-      }
+      const int kc = orthant_layout(G, kst, nvp);
+      ctx->oct_kc = kc;
+      ctx->kst_h = std::move(kst);
+      ctx->nvp = nvp;
     }
     ctx->esize = (ctx->precision == IBDVM_FP64) ? sizeof(double) : sizeof(float);
     // velocity chunks: one chunk per cell unless the grid is too small to fill the GPU
@@ -609,7 +607,7 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     if (ctx->oct_kc) {
       std::vector<float> vconst;
       std::vector<uint8_t> sign;
-      tma3_octant_tables(G, ctx->kst_h, ctx->nvp, ctx->oct_kc, vconst, sign);
+      orthant_tables(G, ctx->kst_h, ctx->nvp, ctx->oct_kc, vconst, sign);
       ctx->oct_const = dalloc<float>(ctx, vconst.size(), "velocity constants");
       ctx->oct_sign = dalloc<uint8_t>(ctx, sign.size(), "chunk signs");
       upload(ctx, ctx->oct_const, vconst, "upload velocity constants");
@@ -619,8 +617,7 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     if (!tma_off && (tma_sweep_applicable(ctx) || tma3_sweep_applicable(ctx))) {
       const bool two = G.dim == 2;
       ctx->tma_nchunk = two ? tma_sweep_nchunk(ctx) : tma3_sweep_nchunk(ctx);
-      // 2D: room for 64-velocity chunks, the finest tiling a batch may choose
-      const size_t nch = two ? static_cast<size_t>(ctx->nvp / 64) : static_cast<size_t>(ctx->tma_nchunk);
+      const size_t nch = static_cast<size_t>(ctx->tma_nchunk);
       ctx->partf = dalloc<float>(ctx, nch * nmoments(G.dim) * ctx->ncell, "FP32 moment sums");
       check(ctx, two ? tma_sweep_prepare(ctx) : tma3_sweep_prepare(ctx), "TMA sweep set-up");
       ctx->use_tma = true;
@@ -1189,10 +1186,10 @@ size_t estimate_ctx_bytes(const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *v
   if (!build_grid(*grid, *vgrid, *gas, G, err)) return 0;
   const size_t es = (gas->precision == IBDVM_FP64) ? 8 : 4;
   size_t nvp = static_cast<size_t>(G.nvp);
-  if (G.dim == 3 && gas->precision == IBDVM_MIXED) { // the octant layout of the 3D TMA sweep
+  if (gas->precision == IBDVM_MIXED) { // the orthant layout of the TMA sweeps
     std::vector<int> kst;
     int np = 0;
-    if (tma3_octant_layout(G, kst, np) > 0) nvp = static_cast<size_t>(np);
+    if (orthant_layout(G, kst, np) > 0) nvp = std::max(nvp, static_cast<size_t>(np));
   }
   const size_t nc = static_cast<size_t>(G.ncell);
   const int D = G.dim, NW = D + 2, NM = nmoments(D);

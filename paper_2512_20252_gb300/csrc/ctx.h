@@ -64,14 +64,15 @@ struct ibdvm_ctx {
   void *xiT = nullptr, *wT = nullptr, *finf = nullptr;
   double *xiD = nullptr, *wD = nullptr;
   // stored position of every velocity in its natural order (x index fastest):
-  // the identity, or, for the octant layout of the 3D FP32 sweep, velocities
-  // grouped by the signs of their components with each group padded to a
-  // whole number of sweep chunks (padding positions hold zero weight and zero f)
+  // the identity, or, for the orthant layout of the FP32 TMA sweeps,
+  // velocities grouped by the signs of their components with each group
+  // padded to a whole number of sweep chunks (padding positions hold zero
+  // weight and zero f)
   int *kst = nullptr;          // [nv] device
   std::vector<int> kst_h;      // [nv] host copy
-  int oct_kc = 0;              // octant layout: velocities per sweep chunk (0: natural order)
-  float *oct_const = nullptr;  // octant layout: per stored velocity |a_x|, |a_y|, |a_z|, w (FP32)
-  uint8_t *oct_sign = nullptr; // octant layout: per chunk, bit a set when component a is negative
+  int oct_kc = 0;              // orthant layout: velocities per sweep chunk (0: natural order)
+  float *oct_const = nullptr;  // orthant layout: per stored velocity |a_x|, |a_y|, |a_z| or w, w or 0 (FP32)
+  uint8_t *oct_sign = nullptr; // orthant layout: per chunk, bit a set when component a is negative
   // cell tables
   uint8_t *ctype = nullptr;
   uint8_t *cmask = nullptr;  // per cell: ghost neighbour per face (bit 2a + (s > 0)), 64 = not fluid
@@ -153,14 +154,18 @@ bool tma_sweep_applicable(const ibdvm_ctx *ctx);
 int tma_sweep_nchunk(const ibdvm_ctx *ctx);
 cudaError_t tma_sweep_prepare(ibdvm_ctx *ctx);
 cudaError_t tma_sweep_launch(ibdvm_ctx *ctx);
-// TMA sweep of 3D FP32 cases (sweep3d_tma.cu).  The sweep takes velocity
-// chunks whose components have one sign each: tma3_octant_layout gives the
-// stored position of every velocity of G (natural order), the padded count and
-// the chunk size (0 when the sweep is not available on this device);
-// tma3_octant_tables fills the per-velocity constants and per-chunk signs.
-int tma3_octant_layout(const Geom &G, std::vector<int> &kst, int &nvp);
-void tma3_octant_tables(const Geom &G, const std::vector<int> &kst, int nvp, int kc,
-                        std::vector<float> &vconst, std::vector<uint8_t> &sign);
+// The orthant layout of the velocities for the FP32 TMA sweeps (layout.cpp):
+// chunks whose components have one sign each (quadrants in 2D, octants in
+// 3D).  orthant_layout gives the stored position of every velocity of G
+// (natural order), the padded count and the chunk size; orthant_tables fills
+// the per-velocity constants (|a_x|, |a_y|, |a_z| or w, w or 0; a_a = dt xi_a /
+// dx_a) and the per-chunk signs (bit a: component a negative).
+int orthant_layout(const Geom &G, std::vector<int> &kst, int &nvp);
+void orthant_tables(const Geom &G, const std::vector<int> &kst, int nvp, int kc, std::vector<float> &vconst,
+                    std::vector<uint8_t> &sign);
+// the driver's tensor-map encoder can be reached (the TMA sweeps can run)
+bool tma_encoder_available();
+// TMA sweep of 3D FP32 cases (sweep3d_tma.cu)
 bool tma3_sweep_applicable(const ibdvm_ctx *ctx);
 int tma3_sweep_nchunk(const ibdvm_ctx *ctx);
 cudaError_t tma3_sweep_prepare(ibdvm_ctx *ctx);

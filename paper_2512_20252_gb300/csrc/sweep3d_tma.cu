@@ -64,7 +64,6 @@ constexpr int XW = TX + 3;             // an x-extended row of a stage: 2 upwind
 constexpr int NSLOT = XW * TY + 3 * TX; // cells of a stage: the extended rows and three y halo rows (40)
 constexpr float kLn2 = 0.693147180559945309f;
 constexpr float kLog2e = 1.442695040888963407f;
-constexpr double kPadSpeed = 1e8; // |xi_a| given to padding positions: their equilibrium is exactly zero
 
 template <int VPL> struct Cfg {
   static_assert(VPL == 4 || VPL == 8, "four or eight velocities per lane");
@@ -651,54 +650,7 @@ Oct3Args oct_args(const ibdvm_ctx *ctx, int cur, int *err) {
 
 } // namespace
 
-int tma3_octant_layout(const Geom &G, std::vector<int> &kst, int &nvp) {
-  if (G.dim != 3 || encoder3() == nullptr) return 0;
-  // velocities of each octant (bit a: component a negative), in natural order
-  std::vector<int> oct[8];
-  for (int i = 0; i < G.nv; ++i) {
-    int o = 0;
-    for (int a = 0; a < 3; ++a)
-      if (G.xi[3 * i + a] < 0.0) o |= 1 << a;
-    oct[o].push_back(i);
-  }
-  auto padded = [&](int kc) {
-    long long n = 0;
-    for (const auto &v : oct) n += (static_cast<long long>(v.size()) + kc - 1) / kc * kc;
-    return n;
-  };
-  // chunks of 256 velocities unless 128 wastes clearly less padding
-  const int kc = (padded(256) <= padded(128) + padded(128) / 32) ? 256 : 128;
-  kst.assign(G.nv, 0);
-  int pos = 0;
-  for (const auto &v : oct) {
-    if (v.empty()) continue;
-    for (size_t j = 0; j < v.size(); ++j) kst[v[j]] = pos + static_cast<int>(j);
-    pos += (static_cast<int>(v.size()) + kc - 1) / kc * kc;
-  }
-  nvp = pos;
-  return kc;
-}
-
-void tma3_octant_tables(const Geom &G, const std::vector<int> &kst, int nvp, int kc, std::vector<float> &vconst,
-                        std::vector<uint8_t> &sign) {
-  vconst.assign(static_cast<size_t>(nvp) * 4, 0.f);
-  // padding positions: w = 0 and a speed that makes the equilibrium vanish
-  for (int k = 0; k < nvp; ++k)
-    for (int a = 0; a < 3; ++a) vconst[4 * static_cast<size_t>(k) + a] = (float)(kPadSpeed * G.dt / G.dx[a]);
-  sign.assign(nvp / kc, 0);
-  std::vector<char> seen(nvp / kc, 0);
-  for (int i = 0; i < G.nv; ++i) {
-    const size_t k = static_cast<size_t>(kst[i]);
-    int o = 0;
-    for (int a = 0; a < 3; ++a) {
-      const double xa = G.xi[3 * i + a];
-      vconst[4 * k + a] = (float)(G.dt * std::fabs(xa) / G.dx[a]);
-      if (xa < 0.0) o |= 1 << a;
-    }
-    vconst[4 * k + 3] = (float)G.w[i];
-    sign[k / kc] = static_cast<uint8_t>(o);
-  }
-}
+bool tma_encoder_available() { return encoder3() != nullptr; }
 
 bool tma3_sweep_applicable(const ibdvm_ctx *ctx) {
   return ctx->dim == 3 && ctx->precision == IBDVM_MIXED && ctx->oct_kc > 0 && encoder3() != nullptr;

@@ -1,36 +1,45 @@
 // sweep_tma.cu -- the transport / relaxation / moments sweep of 2D cases in
-// FP32 storage (the mixed path), staged through shared memory by TMA.
+// FP32 storage (the mixed path), staged through shared memory by TMA, and the
+// work lists of the batched sweeps.
 //
 // Same arithmetic as sweep_kernel in kernels.cu (Sec. 2.2 Eqs. reconstruction
-// and limiter, Sec. 4 reduced Shakhov equilibria, forward Euler, Eqs.
-// moments1-3 by quadrature), organised for GB300:
+// and limiter, the reduced Shakhov equilibria of Sec. 4, forward Euler, Eqs.
+// moments1-3 by quadrature), organised for GB300 around the quadrant layout
+// of the velocities (layout.cpp):
 //
-//   * a block owns TX = 8 columns of cells (one warp per column), a chunk of
-//     KC = 32 * KPT velocities (lane l owns velocities l, l + 32, ..., so every
-//     shared-memory access of a warp is 256 contiguous bytes), and marches up
-//     a range of rows;
-//   * every row of the block (its TX columns plus two halo columns on each
-//     side, all KC velocities) arrives in shared memory by one TMA tensor copy
-//     (cp.async.bulk.tensor.3d) into a ring of NST stages guarded by
-//     mbarriers, issued NST - 3 rows ahead, so HBM is read once per row and
-//     the x stencil comes from shared memory;
-//   * each lane keeps its column's y stencil in registers (f at rows y..y+2
-//     and the reconstructed faces of rows y-1..y+1), rotated by moves (one copy
-//     of the row body keeps the instruction cache warm);
-//   * x faces are exchanged through shared memory: every warp publishes the
-//     face value of its own cell on the downwind side and reads its upwind
-//     neighbour's as the inflow face; the faces of the two halo columns are
-//     spread over all threads of the block (one velocity each);
-//   * the nine moment sums of the new state (about the stored bulk velocity)
-//     are reduced over the 32 lanes by a butterfly (each shuffle round halves
-//     the values a lane holds) and written as FP32 partial sums per velocity
-//     chunk; the finalize kernel adds the chunks in FP64.
+//   * velocities are stored grouped by the signs of their two components, each
+//     group padded to a whole number of chunks of KC = 32 VPL velocities, so
+//     every velocity of a chunk has the same upwind direction along x and y:
+//     the upwind halo side, the inflow faces and the march direction are the
+//     same for the whole block, and no per-velocity selection remains;
+//   * a block owns TX = 8 columns of cells (one warp each) and one chunk; lane
+//     l owns the velocity pairs 2 l + 64 g, 2 l + 64 g + 1 (g < VPL / 2), so
+//     every access of a warp is 16 bytes per lane, (h, b) of two velocities,
+//     over 512 contiguous bytes; the arithmetic runs on packed FP32 pairs,
+//     (h, b) for the transport and two velocities for the equilibrium;
+//   * the block marches along y in the direction of the chunk's y velocities,
+//     so the y inflow face of a row is the y outflow face of the previous one
+//     (kept in registers with f one row back);
+//   * every row arrives in shared memory by one TMA tensor copy
+//     (cp.async.bulk.tensor.4d over 16-byte velocity pairs) of the TX columns
+//     extended by two upwind cells and one downwind cell, on one mbarrier per
+//     stage of a 4-stage ring;
+//   * x outflow faces are exchanged through two shared buffers: while a row is
+//     updated the faces of the next row are published, so one block barrier per
+//     row suffices; the faces of the upwind halo column are spread over the
+//     first VPL / 2 warps;
+//   * the nine moment sums (about the stored bulk velocity) are accumulated per
+//     lane, reduced over the warp by a butterfly once per row and written as
+//     FP32 partial sums per chunk; the finalize kernel adds the chunks with a
+//     compensated sum and widens them to FP64.
 //
-// Conditions that are the same for a whole warp (a ghost neighbour, the
-// domain edge, a cell that is not fluid) select between a fast path and a
-// general path per warp, never per velocity.  Every mbarrier wait is bounded:
-// on timeout the block sets an error flag, drains its copies (bounded) and
-// returns.
+// Values beyond the domain edge come from the freestream or, for a diffuse
+// domain wall (Sec. 2.3 on the domain faces, reading C24), from the wall's
+// halo slot of that boundary cell; only the general paths read them.
+// Conditions that hold for a whole warp (ghost neighbours, the domain edge, a
+// cell that is not fluid) select a general path per warp.  Every mbarrier
+// wait is bounded: on timeout the block sets an error flag, drains its copies
+// (bounded) and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -47,37 +56,43 @@ namespace {
 
 using namespace dev;
 
-constexpr int TX = 8;       // interior columns per block, one warp each
-constexpr int NST = 6;      // TMA row stages
-constexpr int COLS = TX + 4;
+constexpr int TX = 8;        // columns per block, one warp each
 constexpr int NTHREADS = TX * 32;
-constexpr int NM = 9;       // moment sums (2D)
+constexpr int NST = 4;       // TMA row stages
+constexpr int NM = 9;        // moment sums (2D)
+constexpr int XW = TX + 3;   // cells of a staged row: two upwind, the TX columns, one downwind
+constexpr float kLn2 = 0.693147180559945309f;
+constexpr float kLog2e = 1.442695040888963407f;
 
-template <int KPT> struct Cfg {
-  static constexpr int KC = 32 * KPT;
-  static constexpr int KC2 = 2 * KC; // floats of one column in a staged row
-  static constexpr int STAGE_FLOATS = COLS * KC2;
-  static constexpr int STAGE_BYTES = STAGE_FLOATS * 4;
-  static constexpr int PHI_FLOATS = (TX + 2) * KC2;
-  static constexpr size_t SMEM = (size_t)(NST * STAGE_FLOATS + 2 * PHI_FLOATS + KC2 + KC + 2 * TX * kMac) * 4 + NST * 8;
+template <int VPL> struct Cfg {
+  static_assert(VPL == 2 || VPL == 4 || VPL == 6, "two, four or six velocities per lane");
+  static constexpr int G = VPL / 2;            // groups of two velocities (a float4 of (h, b) pairs) per lane
+  static constexpr int KC = 32 * VPL;          // velocities of a chunk
+  static constexpr int KC2 = 2 * KC;           // floats of one cell of a chunk
+  static constexpr int STAGE = XW * KC2;       // floats of a staged row
+  static constexpr int FX = (TX + 2) * KC2;    // x outflow faces [x + 1][k][comp], one buffer
+  static constexpr int CONST = G * 3 * 64;     // per group and quantity a float2 per lane
+  static constexpr size_t SMEM = (size_t)(NST * STAGE + 2 * FX + CONST + KC2 + 2 * TX * kMac) * 4 + NST * 8;
 };
+static_assert(Cfg<6>::SMEM <= 113 * 1024, "two blocks per SM");
 
-struct TmaArgs {
+struct Oct2Args {
   float *__restrict__ fn;
   const float *__restrict__ f;
-  const float *__restrict__ mac;  // [ncell][kMac]
-  const float *__restrict__ xi;   // [3][nvp]
-  const float *__restrict__ w;    // [nvp]
-  const float *__restrict__ finf; // [nvp][2]
+  const float *__restrict__ mac;     // [ncell][kMac]
+  const float *__restrict__ vconst;  // [nvp][4]: |a_x|, |a_y|, w, 0 with |a_a| = dt |xi_a| / dx_a
+  const uint8_t *__restrict__ csign; // [nchunk]: bit a when component a of the chunk's velocities is negative
+  const float *__restrict__ finf;    // [nvp][2]
   const uint8_t *__restrict__ cmask;
   const int *__restrict__ dslot;
   const int *__restrict__ dlinks;
-  const float *__restrict__ lval; // [nlink][nvp][2]
-  float *__restrict__ part;       // [nchunk][NM][ncell]
+  const float *__restrict__ lval;    // [nlink][nvp][2]
+  float *__restrict__ part;          // [nchunk][NM][ncell]
   int *__restrict__ err;
   long long ncell;
-  int nx, ny, nvp, nv, rows;
-  float dt, rdx, rdy;
+  int nx, ny, nvp, rows;
+  int kc;        // velocities of a chunk (192, 128 or 64)
+  float sig[2];  // dx_a / dt: |xi_a| = |a_a| sig[a]
   // diffuse domain walls: faces 2a + (s > 0) in wmask, the halo values of
   // their boundary cells [slot][nvp][2] from the first slot woff[face]
   const float *__restrict__ whalo;
@@ -85,493 +100,453 @@ struct TmaArgs {
   int wmask;
 };
 
-// ---------------------------------------------------------------------------
-// PTX helpers
-// ---------------------------------------------------------------------------
+enum : uint8_t { kNotFluid = 64 };
 
-__device__ __forceinline__ void tma_row(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, uint64_t *bar) {
+__device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
+                                        uint64_t *bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
           smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
       : "memory");
 }
 
-
-
-__device__ __forceinline__ float2 link_value(const TmaArgs &A, long long c, int dir, int k) {
-  const int slot = A.dslot[c];
-  const int l = (slot >= 0) ? A.dlinks[slot * 6 + dir] : -1;
-  const float *p = (l >= 0) ? A.lval + ((size_t)l * A.nvp + k) * 2 : A.finf + (size_t)k * 2;
-  return make_float2(p[0], p[1]);
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+// 2^x (the hardware base-2 exponential)
+__device__ __forceinline__ float ex2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
-
-enum : uint8_t { kXm = 1, kXp = 2, kYm = 4, kYp = 8, kNotFluid = 64, kGhostAny = 15 };
-
-template <int KPT> using Ring = float2[KPT];
-
-// Shared state of one block's march, passed to the per-row body.
-template <int KPT> struct March {
-  const TmaArgs &A;
-  const CUtensorMap *tm;
-  float *stage, *phix, *sfinf, *sxi;
-  uint64_t *full;
-  int warp, lane, x0, x, k0, y0, y1, ylast;
-  int st;       // stage of row y
-  unsigned pb;  // parity of that stage's current use
-  bool col_in;
-  long long nc;
-  float xix[KPT], xiy[KPT], wk[KPT];
-  float ax[KPT], ay[KPT];    // dt |xi_a| / dx_a
-  float sy[KPT];             // sign of xi_y
-  float *smac;               // [2][TX][kMac]: cell parameters of rows y and y + 1
-  float pre_mac;             // lanes 0..kMac-1: one parameter of the next row's cell
-  uint8_t mask_next2;        // flags of (x, y + 2)
-  bool abort_local;
-  bool inner_x;              // the column is inside the domain, away from its x edges
-  // the halo column face this thread owns (threads below KC): chunk velocity,
-  // column, its slot in a staged row, its face slot
-  int h_kk, h_col, h_scol, h_out;
-  bool h_in, h_fast;         // the column lies in the domain; and away from its x edges
-  float2 h_s2;               // sign of that velocity's xi_x, packed
-  // running pointers of row y, advanced by one row per step
-  const uint8_t *cm_row;     // flags of row y
-  const float *mac_next;     // this lane's parameter of the cell at row y + 1
-  float *fn_cell;            // f^{n+1} of the own cell, first chunk velocity
-  float *part_cell;          // moment partial sums of the own cell (sum index of the lane)
-};
-
-// velocity q of a lane: k = k0 + lane + 32 q, so a warp touches 32 consecutive
-// (h, b) pairs per access (256 contiguous bytes, no bank conflicts)
-template <int KPT> __device__ __forceinline__ int klo(const March<KPT> &M, int q) { return M.lane + 32 * q; }
-template <int KPT> __device__ __forceinline__ int kof(const March<KPT> &M, int q) { return M.k0 + klo(M, q); }
-
-template <int KPT> __device__ __forceinline__ float2 sm2(const float *base, int kk) {
-  return *reinterpret_cast<const float2 *>(base + 2 * kk);
+// downwind face f + vl(f - up, dn - f) of (h, b) pairs (Eqs. reconstruction and limiter)
+__device__ __forceinline__ float2 face2u(float2 f, float2 up, float2 dn) {
+  return __fadd2_rn(f, vl_half2(sub2(f, up), sub2(dn, f)));
 }
-
-// the values of the halo cells across face i = 2a + (s > 0) of the boundary
-// cell at transverse index t (the row for x faces, the column for y faces),
-// from the chunk's first velocity: the slot a diffuse wall wrote this step,
-// or the freestream (both halo layers hold the same values)
-// (W: the case has diffuse domain walls; without, the code is that of the
-// freestream halo alone)
-template <int KPT, bool W> __device__ __forceinline__ const float *halo_ptr(const March<KPT> &M, int i, int t) {
-  if constexpr (!W) {
-    return M.sfinf;
-  } else {
-    if (!((M.A.wmask >> i) & 1)) return M.sfinf;
-    return M.A.whalo + ((size_t)(M.A.woff[i] + t) * M.A.nvp + M.k0) * 2;
-  }
+__device__ __forceinline__ float4 face4(float4 f, float4 up, float4 dn) {
+  return cat4(face2u(lo2(f), lo2(up), lo2(dn)), face2u(hi2(f), hi2(up), hi2(dn)));
 }
-
-template <int KPT> __device__ __forceinline__ void issue_row(March<KPT> &M, int r, int st) {
-  using C = Cfg<KPT>;
-  mbar_expect_tx(&M.full[st], C::STAGE_BYTES);
-  tma_row(M.stage + st * C::STAGE_FLOATS, M.tm, 2 * M.k0, M.x0 - 2, r, &M.full[st]);
+__device__ __forceinline__ float4 mean4(float4 a, float4 b) {
+  return make_float4(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z), 0.5f * (a.w + b.w));
 }
-
-template <int KPT> __device__ __forceinline__ uint8_t cmask_of(const March<KPT> &M, int cx, int r) {
-  if (cx < 0 || cx >= M.A.nx || r < 0 || r >= M.A.ny) return 0;
-  return M.A.cmask[cx + (long long)M.A.nx * r];
+// ghost values of the link across face dir (bit numbering of cmask) of cell c
+// for the two velocities from stored position k
+__device__ __forceinline__ float4 link4(const Oct2Args &A, long long c, int dir, int k) {
+  const int s = A.dslot[c];
+  const int l = (s >= 0) ? A.dlinks[s * 6 + dir] : -1;
+  return *reinterpret_cast<const float4 *>((l >= 0) ? A.lval + ((size_t)l * A.nvp + k) * 2 : A.finf + (size_t)k * 2);
 }
-
-// downwind x face of column cx at row y for chunk velocity kk, with the
-// domain edge, ghost neighbours and cells that are not fluid
-template <int KPT, bool W>
-__device__ __forceinline__ float2 phi_x_one(const March<KPT> &M, const float *srow, int cx, int scol, int y,
-                                            uint8_t m, int kk, float xi) {
-  using C = Cfg<KPT>;
-  // halo column: its value, zero slope
-  if (cx < 0 || cx >= M.A.nx) return sm2<KPT>(halo_ptr<KPT, W>(M, cx < 0 ? 0 : 1, y), kk);
-  if (m & kNotFluid) return make_float2(0.f, 0.f);
-  const float *pc = srow + scol * C::KC2;
-  const float2 f = sm2<KPT>(pc, kk);
-  float2 lo = (cx - 1 < 0) ? sm2<KPT>(halo_ptr<KPT, W>(M, 0, y), kk) : sm2<KPT>(pc - C::KC2, kk);
-  float2 hi = (cx + 1 >= M.A.nx) ? sm2<KPT>(halo_ptr<KPT, W>(M, 1, y), kk) : sm2<KPT>(pc + C::KC2, kk);
-  if (m & (kXm | kXp)) {
-    const long long c = cx + (long long)M.A.nx * y;
-    if (m & kXm) lo = link_value(M.A, c, 0, M.k0 + kk);
-    if (m & kXp) hi = link_value(M.A, c, 1, M.k0 + kk);
-  }
-  return face2(f, lo, hi, dup(copysignf(1.f, xi)));
+__device__ __forceinline__ float2 link2(const Oct2Args &A, long long c, int dir, int k) {
+  const int s = A.dslot[c];
+  const int l = (s >= 0) ? A.dlinks[s * 6 + dir] : -1;
+  return *reinterpret_cast<const float2 *>((l >= 0) ? A.lval + ((size_t)l * A.nvp + k) * 2 : A.finf + (size_t)k * 2);
 }
-
-// downwind y face of row r, cell (x, r): fr = f(r), lo = f(r-1), hi = f(r+1)
-template <int KPT, bool W>
-__device__ __forceinline__ void phi_y(const March<KPT> &M, int r, uint8_t m, const Ring<KPT> &fr,
-                                      const Ring<KPT> &lo, const Ring<KPT> &hi, Ring<KPT> &out) {
-  if (r < 0 || r >= M.A.ny || !M.col_in) { // halo row: its value, zero slope
-    const float *h = M.col_in ? halo_ptr<KPT, W>(M, r < 0 ? 2 : 3, M.x) : M.sfinf;
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) out[q] = sm2<KPT>(h, klo(M, q));
-    return;
-  }
-  if (m & kNotFluid) {
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) out[q] = make_float2(0.f, 0.f);
-    return;
-  }
-  // the last row under a top wall: the ring holds the freestream past the
-  // edge; the wall's halo slot holds the value across it
-  const bool top = W && (r == M.A.ny - 1) && (M.A.wmask & 8);
-  if (!(m & (kYm | kYp)) && !top) { // fast path
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) out[q] = face2(fr[q], lo[q], hi[q], dup(M.sy[q]));
-    return;
-  }
-  const long long c = M.x + (long long)M.A.nx * r;
-  const float *th = top ? halo_ptr<KPT, W>(M, 3, M.x) : M.sfinf;
-#pragma unroll
-  for (int q = 0; q < KPT; ++q) {
-    const float2 l = (m & kYm) ? link_value(M.A, c, 2, kof(M, q)) : lo[q];
-    const float2 h = (m & kYp) ? link_value(M.A, c, 3, kof(M, q)) : (top ? sm2<KPT>(th, klo(M, q)) : hi[q]);
-    out[q] = face2(fr[q], l, h, dup(M.sy[q]));
-  }
+// downwind face from the one-sided differences a = f - f_up and b = f_dn - f
+__device__ __forceinline__ float4 face4d(float4 f, float4 a, float4 b) {
+  return cat4(__fadd2_rn(lo2(f), vl_half2(lo2(a), lo2(b))), __fadd2_rn(hi2(f), vl_half2(hi2(a), hi2(b))));
 }
+__device__ __forceinline__ float4 sub4(float4 x, float4 y) { return cat4(sub2(lo2(x), lo2(y)), sub2(hi2(x), hi2(y))); }
+__device__ __forceinline__ void sts2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+// moment accumulators: scalars
+__device__ __forceinline__ void acc_add(float &a, float2 v) { a += v.x + v.y; }
+__device__ __forceinline__ void acc_fma(float &a, float2 u, float2 v) { a = fmaf(u.y, v.y, fmaf(u.x, v.x, a)); }
 
-// One row y of the march.  Ring arguments: Ra = f(y), Rb = f(y+1), Rc <- f(y+2);
-// Pa = phi(y-1), Pb = phi(y), Pc <- phi(y+1); mc = flags of (x, y), carried to
-// the next row as the flags of (x, y+1).  Returns false when the block aborts.
-template <int KPT, bool W>
-__device__ __forceinline__ bool row(March<KPT> &M, int y, int par, uint8_t &mc, Ring<KPT> &Ra, Ring<KPT> &Rb,
-                                    Ring<KPT> &Rc, Ring<KPT> &Pa, Ring<KPT> &Pb, Ring<KPT> &Pc) {
-  using C = Cfg<KPT>;
-  const TmaArgs &A = M.A;
-  const long long cell = M.x + (long long)A.nx * y;
-  const uint8_t m0 = mc;
-  const bool fluid = !(m0 & kNotFluid);
-  // prefetch for the next row: one cell parameter per lane, the flags of (x, y + 3);
-  // this row's parameters were staged in shared memory by the previous row
-  const float pre_next = (M.lane < kMac && M.col_in && y + 1 < A.ny) ? __ldg(M.mac_next) : 0.f;
-  const uint8_t mn = M.mask_next2; // flags of (x, y + 1), loaded a row ahead
-  const uint8_t mn3 = M.col_in ? ((y + 2 < A.ny) ? M.cm_row[2 * A.nx + M.x] : 0) : kNotFluid;
-  // stages of rows y and y + 2
-  const int st = M.st;
-  int st2 = st + 2;
-  unsigned pb2 = M.pb;
-  if (st2 >= NST) {
-    st2 -= NST;
-    pb2 ^= 1u;
-  }
-  // (1) own column of row y + 2 (the y stencil)
-  if (y + 2 < A.ny && !mbar_wait(&M.full[st2], pb2)) M.abort_local = true;
-  {
-    // the own column of row y + 2, or the freestream past the domain edge
-    // (where the top face is a wall, phi_y reads its halo for the last row)
-    const float *src = (y + 2 < A.ny && M.col_in) ? M.stage + st2 * C::STAGE_FLOATS + (M.warp + 2) * C::KC2
-                                                  : M.sfinf;
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) Rc[q] = sm2<KPT>(src, klo(M, q));
-  }
-  const float *srow = M.stage + st * C::STAGE_FLOATS; // row y, [COLS][KC][2]
-  float *ph = M.phix + par * C::PHI_FLOATS;            // [TX + 2][KC][2]
-  // (2) downwind x face of the own cell
-  Ring<KPT> PX;
-  if (M.inner_x && fluid && !(m0 & (kXm | kXp))) {
-    const float *pc = srow + (M.warp + 2) * C::KC2;
-#pragma unroll
-    for (int q = 0; q < KPT; ++q)
-      PX[q] = face2(Ra[q], sm2<KPT>(pc - C::KC2, klo(M, q)), sm2<KPT>(pc + C::KC2, klo(M, q)),
-                    dup(copysignf(1.f, M.xix[q])));
-  } else {
-#pragma unroll
-    for (int q = 0; q < KPT; ++q)
-      PX[q] = phi_x_one<KPT, W>(M, srow, M.x, M.warp + 2, y, M.col_in ? m0 : 0, klo(M, q), M.xix[q]);
-  }
-#pragma unroll
-  for (int q = 0; q < KPT; ++q) *reinterpret_cast<float2 *>(ph + (M.warp + 1) * C::KC2 + 2 * klo(M, q)) = PX[q];
-  // the halo column that is upwind of the block for each velocity: x0 - 1
-  // for xi_x >= 0, x0 + TX otherwise; one velocity per thread
-  static_assert(Cfg<KPT>::KC <= NTHREADS, "one halo face per thread at most");
-  if (threadIdx.x < C::KC) {
-    const uint8_t hm = M.h_in ? M.cm_row[M.h_col] : 0;
-    float2 o;
-    if (M.h_fast && !(hm & (kNotFluid | kXm | kXp))) {
-      // interior halo column, fluid, no ghost along x: f and its neighbours
-      // from the staged row, the sign of the velocity decides the side
-      const float *pc = srow + M.h_scol * C::KC2;
-      o = face2(sm2<KPT>(pc, M.h_kk), sm2<KPT>(pc - C::KC2, M.h_kk), sm2<KPT>(pc + C::KC2, M.h_kk), M.h_s2);
-    } else {
-      o = phi_x_one<KPT, W>(M, srow, M.h_col, M.h_scol, y, hm, M.h_kk, M.sxi[M.h_kk]);
-    }
-    *reinterpret_cast<float2 *>(ph + M.h_out) = o;
-  }
-  // (3) downwind y face of row y + 1
-  phi_y<KPT, W>(M, y + 1, mn, Rb, Ra, Rc, Pc);
-  // (4) barrier: x faces published, the stage of row y - 1 released; all
-  //     threads agree on an abort
-  if (__syncthreads_or(M.abort_local ? 1 : 0)) return false;
-  if (threadIdx.x == 0 && y + NST - 1 < M.ylast) {
-    fence_proxy_async();
-    issue_row(M, y + NST - 1, st == 0 ? NST - 1 : st - 1);
-  }
-  // (5) update of the own cell and its moment sums
-  float2 a03 = make_float2(0.f, 0.f), a17 = a03, a28 = a03, a45 = a03;
-  float a6 = 0.f;
-  if (fluid) {
-    const float4 *pm = reinterpret_cast<const float4 *>(M.smac + (par * TX + M.warp) * kMac);
-    const float4 p0 = pm[0], p1 = pm[1], p2 = pm[2];
-    const float pre = p0.x, U0 = p0.y, U1 = p0.z;
-    const float invT = p1.x, halfT = p1.y, shA = p1.z, q0 = p1.w;
-    const float q1 = p2.x, dtau = p2.z;
-    const float Tc = 2.f * halfT;
-    const float2 omd = dup(1.f - dtau), dt2 = dup(dtau);
-    const bool ghosty = (m0 & kGhostAny) != 0;
-    Ring<KPT> out;
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      // inflow faces: the upwind neighbour's downwind face
-      const bool posx = M.xix[q] >= 0.f, posy = M.xiy[q] >= 0.f;
-      float2 ix = sm2<KPT>(ph + (M.warp + (posx ? 0 : 2)) * C::KC2, klo(M, q));
-      float2 iy = posy ? Pa[q] : Pc[q];
-      if (ghosty) { // a ghost upwind neighbour: mean of its link value and this cell
-        if (posx ? (m0 & kXm) : (m0 & kXp)) {
-          const float2 g = link_value(A, cell, posx ? 0 : 1, kof(M, q));
-          ix = __fmul2_rn(dup(0.5f), __fadd2_rn(g, Ra[q]));
-        }
-        if (posy ? (m0 & kYm) : (m0 & kYp)) {
-          const float2 g = link_value(A, cell, posy ? 2 : 3, kof(M, q));
-          iy = __fmul2_rn(dup(0.5f), __fadd2_rn(g, Ra[q]));
-        }
-      }
-      // Shakhov equilibrium (Sec. 4 reduced forms) from the stored state:
-      // (H, B) = (e, T/2 e) + m (2t - 4, T t - T), t = c^2 / T
-      const float cx = M.xix[q] - U0, cy = M.xiy[q] - U1;
-      const float c2 = fmaf(cx, cx, cy * cy);
-      const float t = c2 * invT;
-      const float e = pre * __expf(-t);
-      const float mm = e * shA * fmaf(cx, q0, cy * q1);
-      const float2 G = make_float2(fmaf(mm, fmaf(2.f, t, -4.f), e), fmaf(mm, fmaf(Tc, t, -Tc), halfT * e));
-      // forward Euler: relaxation and the flux divergence of both axes,
-      // |xi_a| dt / dx_a (inflow face - outflow face)
-      float2 n = __ffma2_rn(Ra[q], omd, __fmul2_rn(dt2, G));
-      n = __ffma2_rn(dup(M.ax[q]), sub2(ix, PX[q]), n);
-      n = __ffma2_rn(dup(M.ay[q]), sub2(iy, Pb[q]), n);
-      out[q] = n;
-      // moments of the new state about the stored bulk velocity
-      const float wh = M.wk[q] * n.x;
-      const float e2 = fmaf(c2, wh, M.wk[q] * n.y); // w (c^2 h + b)
-      a03.x += wh;
-      a03.y += e2;
-      a17.x = fmaf(cx, wh, a17.x);
-      a17.y = fmaf(cx, e2, a17.y);
-      a28.x = fmaf(cy, wh, a28.x);
-      a28.y = fmaf(cy, e2, a28.y);
-      const float cxwh = cx * wh;
-      a45.x = fmaf(cx, cxwh, a45.x);
-      a45.y = fmaf(cy, cxwh, a45.y);
-      a6 = fmaf(cy * cy, wh, a6);
-    }
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) *reinterpret_cast<float2 *>(M.fn_cell + 2 * klo(M, q)) = out[q];
-  }
-  // (6) butterfly reduction of the sums over the 32 lanes: three rounds halve
-  //     the eight values a lane holds, two more finish the one it keeps; the
-  //     ninth sum is a plain xor tree
-  {
-    const float acc[NM] = {a03.x, a17.x, a28.x, a03.y, a45.x, a45.y, a6, a17.y, a28.y};
-    const int lane = M.lane;
-    float v4[4];
-    const bool b16 = lane & 16;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float keep = b16 ? acc[4 + i] : acc[i];
-      const float send = b16 ? acc[i] : acc[4 + i];
-      v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-    float v2[2];
-    const bool b8 = lane & 8;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float keep = b8 ? v4[2 + i] : v4[i];
-      const float send = b8 ? v4[i] : v4[2 + i];
-      v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    const bool b4 = lane & 4;
-    float v1 = (b4 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b4 ? v2[0] : v2[1], 4);
-    v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
-    v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
-    float s8 = acc[8];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
-    if (M.col_in) {
-      if ((lane & 3) == 0) *M.part_cell = v1;
-      if (lane == 1) *M.part_cell = s8;
-    }
-  }
-  if (M.lane < kMac) M.smac[((par ^ 1) * TX + M.warp) * kMac + M.lane] = pre_next;
-  M.mask_next2 = mn3;
-  mc = mn;
-  M.cm_row += A.nx;
-  M.mac_next += (size_t)A.nx * kMac;
-  M.fn_cell += (size_t)A.nx * A.nvp * 2;
-  M.part_cell += A.nx;
-  if (++M.st == NST) {
-    M.st = 0;
-    M.pb ^= 1u;
-  }
-  return true;
-}
-
-// The march of one block over columns [x0, x0 + TX), chunk velocities
-// [k0, k0 + KC) and rows [y0, y1).  reinit: the block's mbarriers hold an
-// earlier march (all of whose copies have landed) and are invalidated first.
-// Returns false when the block aborted on a timed-out wait.
-template <int KPT, bool W>
-__device__ __forceinline__ bool march2d(const TmaArgs &A, const CUtensorMap *tmf, int x0, int k0, int y0, int y1,
+// The march of one block over columns [x0, x0 + TX), chunk `chunk` and rows
+// [ya, yb), in the direction of the chunk's y velocities.  reinit: the
+// block's mbarriers hold an earlier march (all of whose copies have landed)
+// and are invalidated first.  Returns false when the block aborted on a
+// timed-out wait.
+template <int VPL>
+__device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm, int x0, int chunk, int ya, int yb,
                                         unsigned char *smem_raw, bool reinit) {
-  using C = Cfg<KPT>;
-  March<KPT> M{A, tmf};
-  M.stage = reinterpret_cast<float *>(smem_raw);
-  M.phix = M.stage + NST * C::STAGE_FLOATS;
-  M.sfinf = M.phix + 2 * C::PHI_FLOATS;
-  M.sxi = M.sfinf + C::KC2;
-  M.smac = M.sxi + C::KC;
-  M.full = reinterpret_cast<uint64_t *>(M.smac + 2 * TX * kMac);
-  M.warp = threadIdx.x >> 5;
-  M.lane = threadIdx.x & 31;
-  M.x0 = x0;
-  M.k0 = k0;
-  M.y0 = y0;
-  M.y1 = y1;
-  M.ylast = min(A.ny, M.y1 + 2); // rows this block reads: [y0, ylast)
-  M.x = M.x0 + M.warp;
-  M.col_in = M.x < A.nx;
-  M.nc = A.ncell;
-  M.inner_x = M.col_in && M.x > 0 && M.x + 1 < A.nx;
-  M.cm_row = A.cmask + (long long)A.nx * M.y0;
-  M.mac_next = A.mac + (M.x + (long long)A.nx * (M.y0 + 1)) * kMac + (M.lane < kMac ? M.lane : 0);
-  M.fn_cell = A.fn + ((size_t)(M.x + (long long)A.nx * M.y0) * A.nvp + M.k0) * 2;
-  {
-    // lanes 4 i write sum i (i < 8); lane 1 writes the ninth sum
-    const int sidx = ((M.lane & 3) == 0) ? (M.lane >> 2) : 8;
-    M.part_cell = A.part + ((size_t)(M.k0 / C::KC) * NM + sidx) * M.nc + M.x + (long long)A.nx * M.y0;
+  using C = Cfg<VPL>;
+  constexpr int G = C::G, KC = C::KC, KC2 = C::KC2;
+  float *stage = reinterpret_cast<float *>(smem_raw);
+  float *fxb = stage + NST * C::STAGE; // two buffers of x faces
+  float *scon = fxb + 2 * C::FX;
+  float *sfinf = scon + C::CONST;
+  float *smac = sfinf + KC2;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smac + 2 * TX * kMac);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k0 = chunk * KC;
+  const unsigned sg = A.csign[chunk];
+  const int sx = (sg & 1u) ? -1 : 1, d = (sg & 2u) ? -1 : 1; // d: the march direction
+  const float2 sigx = dup(sx * A.sig[0]), sigy = dup(d * A.sig[1]);
+  const int ox = (sx > 0) ? 2 : 1; // position of column x0 in a staged row
+  const int nx = A.nx, ny = A.ny;
+  // flag bits of a ghost across the upwind / downwind face along each axis
+  const unsigned gux = 1u << (sx < 0), gdx = 1u << (sx > 0);
+  const unsigned guy = 4u << (d < 0), gdy = 4u << (d > 0);
+  const int dux = (sx < 0), ddx = (sx > 0), duy = 2 + (d < 0), ddy = 2 + (d > 0);
+  // halo faces of the domain edges (i = 2a + (s > 0)) beyond the upwind and
+  // downwind neighbours along x and along y
+  const int hxu = (sx > 0) ? 0 : 1, hxd = 1 - hxu, hyu = (d > 0) ? 2 : 3, hyd = 5 - hyu;
+
+  // the own column
+  const int x = x0 + warp;
+  const bool col_in = x < nx;
+  const bool inner = col_in && x - 1 >= 0 && x + 1 < nx;
+  const int so = warp + ox;
+  const int fx_own = (warp + 1) * KC2, fx_in = fx_own - sx * KC2;
+  // the halo duty: thread j < KC takes velocity j of the upwind halo column's
+  // face (the first VPL warps, one (h, b) pair each)
+  const bool hduty = threadIdx.x < KC;
+  const int hj = threadIdx.x;
+  const int hi = (sx > 0) ? -1 : TX;
+  const int hc = hi + ox, hup = hc - sx, hdn = hc + sx;
+  const int hx = x0 + hi;
+  const bool h_in = hduty && hx >= 0 && hx < nx;
+  const bool h_up_in = hx - sx >= 0 && hx - sx < nx;
+  const int hout = (hi + 1) * KC2;
+  const int ho = 2 * hj;
+
+  // the value of the halo cell across face i of the boundary cell at
+  // transverse index t, this lane's group at offset o: a diffuse wall's slot
+  // of this step, or the freestream (both halo layers hold the same values)
+  auto halo4 = [&](int i, int t, int o) -> float4 {
+    if ((A.wmask >> i) & 1) return *reinterpret_cast<const float4 *>(A.whalo + ((size_t)(A.woff[i] + t) * A.nvp + k0) * 2 + o);
+    return lds4(sfinf + o);
+  };
+  auto halo2 = [&](int i, int t, int o) -> float2 {
+    if ((A.wmask >> i) & 1) return *reinterpret_cast<const float2 *>(A.whalo + ((size_t)(A.woff[i] + t) * A.nvp + k0) * 2 + o);
+    return lds2(sfinf + o);
+  };
+
+  // rows: march index m = 0..M-1 is row p0 + d m; stage m holds row p0 + d m
+  // (also m = M: the y neighbour of the last row)
+  const int M = yb - ya;
+  const int p0 = (d > 0) ? ya : yb - 1;
+  auto row_in = [&](int m) { const int p = p0 + d * m; return p >= 0 && p < ny; };
+
+  // velocity constants (quantity-major per group) and the free stream of the chunk
+  for (int t = threadIdx.x; t < G * 32; t += NTHREADS) {
+    const int g = t >> 5, l = t & 31;
+    const float4 *src = reinterpret_cast<const float4 *>(A.vconst) + (k0 + 64 * g + 2 * l);
+    const float4 v0 = src[0], v1 = src[1];
+    *reinterpret_cast<float2 *>(scon + ((g * 3 + 0) * 32 + l) * 2) = make_float2(v0.x, v1.x);
+    *reinterpret_cast<float2 *>(scon + ((g * 3 + 1) * 32 + l) * 2) = make_float2(v0.y, v1.y);
+    *reinterpret_cast<float2 *>(scon + ((g * 3 + 2) * 32 + l) * 2) = make_float2(v0.z, v1.z);
   }
-  if (threadIdx.x < C::KC) {
-    M.h_kk = threadIdx.x;
-    const bool left = A.xi[M.k0 + M.h_kk] >= 0.f; // the halo column upwind of the block
-    M.h_col = left ? M.x0 - 1 : M.x0 + TX;
-    M.h_scol = left ? 1 : TX + 2;
-    M.h_out = (left ? 0 : TX + 1) * C::KC2 + 2 * M.h_kk;
-    M.h_in = M.h_col >= 0 && M.h_col < A.nx;
-    M.h_fast = M.h_col >= 1 && M.h_col + 1 < A.nx;
-    M.h_s2 = dup(left ? 1.f : -1.f);
-  }
-  M.st = 0;
-  M.pb = 0;
-  M.abort_local = false;
-#pragma unroll
-  for (int q = 0; q < KPT; ++q) {
-    const int k = kof(M, q);
-    const bool valid = k < A.nv;
-    // padding velocities: an enormous speed makes the equilibrium vanish,
-    // zero flux coefficients and zero weight keep them out of everything
-    M.xix[q] = valid ? A.xi[k] : 1e18f;
-    M.xiy[q] = valid ? A.xi[A.nvp + k] : 1e18f;
-    M.wk[q] = valid ? A.w[k] : 0.f;
-    M.ax[q] = valid ? A.dt * fabsf(M.xix[q]) * A.rdx : 0.f;
-    M.ay[q] = valid ? A.dt * fabsf(M.xiy[q]) * A.rdy : 0.f;
-    M.sy[q] = copysignf(1.f, M.xiy[q]);
-  }
-  // parameters of the first row's cells, and the flags of row y0 + 1
-  if (M.lane < kMac)
-    M.smac[M.warp * kMac + M.lane] = M.col_in ? A.mac[(M.x + (long long)A.nx * M.y0) * kMac + M.lane] : 0.f;
-  M.mask_next2 = M.col_in ? ((M.y0 + 1 < A.ny) ? cmask_of(M, M.x, M.y0 + 1) : 0) : kNotFluid;
-  for (int i = threadIdx.x; i < C::KC2; i += NTHREADS) M.sfinf[i] = A.finf[2 * M.k0 + i];
-  for (int i = threadIdx.x; i < C::KC; i += NTHREADS) M.sxi[i] = A.xi[M.k0 + i];
+  for (int i = threadIdx.x; i < KC2; i += NTHREADS) sfinf[i] = A.finf[2 * k0 + i];
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
-      if (reinit) mbar_inval(&M.full[s]);
-      mbar_init(&M.full[s], 1);
+      if (reinit) mbar_inval(&full[s]);
+      mbar_init(&full[s], 1);
     }
     fence_mbar_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int r = M.y0; r < min(M.ylast, M.y0 + NST - 1); ++r) issue_row(M, r, r - M.y0);
+  auto issue = [&](int m) {
+    mbar_expect_tx(&full[m % NST], C::STAGE * 4);
+    tma_box(stage + (m % NST) * C::STAGE, tm, 0, k0 / 2, x0 - ox, p0 + d * m, &full[m % NST]);
+  };
+  int issued = -1; // the last stage issued (thread 0)
+  if (threadIdx.x == 0 && reinit) fence_proxy_async(); // the stages were read (and written) by threads
+  if (threadIdx.x == 0 && M > 0)
+    for (int m = 0; m < NST && m <= M && row_in(m); ++m) {
+      issue(m);
+      issued = m;
+    }
 
-  // own-column ring for rows y0-2 .. y0+1, straight from global memory
-  auto own = [&](int r, Ring<KPT> &v) {
-    if (r < 0 || r >= A.ny || !M.col_in) {
-      const float *h = M.col_in ? halo_ptr<KPT, W>(M, r < 0 ? 2 : 3, M.x) : M.sfinf;
+  auto own = [&](int p, float4 *v) {
 #pragma unroll
-      for (int q = 0; q < KPT; ++q) v[q] = sm2<KPT>(h, klo(M, q));
-    } else {
-      const float *src = A.f + ((size_t)(M.x + (long long)A.nx * r) * A.nvp + M.k0) * 2;
-#pragma unroll
-      for (int q = 0; q < KPT; ++q) v[q] = *reinterpret_cast<const float2 *>(src + 2 * klo(M, q));
+    for (int g = 0; g < G; ++g) {
+      const int o = 128 * g + 4 * lane;
+      if (!col_in) v[g] = lds4(sfinf + o);
+      else if (p < 0 || p >= ny) v[g] = halo4(p < 0 ? 2 : 3, x, o);
+      else v[g] = __ldg(reinterpret_cast<const float4 *>(A.f + ((size_t)(x + (long long)nx * p) * A.nvp + k0) * 2 + o));
     }
   };
-  Ring<KPT> R0, R1, R2, P0, P1, P2;
+  auto cflag = [&](int p) -> unsigned {
+    return (col_in && p >= 0 && p < ny) ? A.cmask[x + (long long)nx * p] : kNotFluid;
+  };
+  auto hflag = [&](int p) -> unsigned {
+    return (h_in && p >= 0 && p < ny) ? A.cmask[hx + (long long)nx * p] : kNotFluid;
+  };
+  // the y stencil of the own column, per group: the difference D = f(p) -
+  // f(p - d) of the current row p and its upwind neighbour, and the y outflow
+  // face of row p - d (the inflow of row p)
+  float4 D[G], P[G];
   {
-    Ring<KPT> Rm2;
-    own(M.y0 - 2, Rm2);
-    own(M.y0 - 1, R2);
-    own(M.y0, R0);
-    own(M.y0 + 1, R1);
-    phi_y<KPT, W>(M, M.y0 - 1, M.col_in ? cmask_of(M, M.x, M.y0 - 1) : kNotFluid, R2, Rm2, R0, P0);
-    phi_y<KPT, W>(M, M.y0, M.col_in ? cmask_of(M, M.x, M.y0) : kNotFluid, R0, R2, R1, P1);
-  }
-  // rows y0 and y0+1 are read from shared memory by the x stencil
-  for (int r = M.y0; r < min(M.ylast, M.y0 + 2); ++r)
-    if (!mbar_wait(&M.full[r - M.y0], 0)) M.abort_local = true;
-  uint8_t mc = M.col_in ? cmask_of(M, M.x, M.y0) : kNotFluid;
-  int y = M.y0;
-  int par = 0;
-  bool ok = true;
-  for (; y < M.y1; ++y) {
-    ok = row<KPT, W>(M, y, par, mc, R0, R1, R2, P0, P1, P2);
-    if (!ok) break;
+    float4 Rpp[G], Rp[G], Rc[G];
+    own(p0 - 2 * d, Rpp);
+    own(p0 - d, Rp);
+    own(p0, Rc);
+    const int r = p0 - d;
+    const unsigned mr = cflag(r);
+    const long long cr = x + (long long)nx * r;
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      R0[q] = R1[q];
-      R1[q] = R2[q];
-      P0[q] = P1[q];
-      P1[q] = P2[q];
+    for (int g = 0; g < G; ++g) {
+      const int o = 128 * g + 4 * lane, k = k0 + 64 * g + 2 * lane;
+      if (!col_in) P[g] = lds4(sfinf + o);
+      else if (r < 0 || r >= ny) P[g] = Rp[g]; // a halo row: its value, zero slope
+      else if (mr & kNotFluid) P[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+      else P[g] = face4(Rp[g], (mr & guy) ? link4(A, cr, duy, k) : Rpp[g], (mr & gdy) ? link4(A, cr, ddy, k) : Rc[g]);
+      D[g] = sub4(Rc[g], Rp[g]);
     }
-    par ^= 1;
+  }
+  if (lane < kMac) smac[warp * kMac + lane] = col_in ? A.mac[(x + (long long)nx * p0) * kMac + lane] : 0.f;
+
+  // x outflow faces of row index m (own cell and the warp's halo duty) from
+  // stage m into face buffer b
+  auto publish = [&](int m, unsigned mcm, unsigned hmm, int b) {
+    const int p = p0 + d * m;
+    const float *sp = stage + (m % NST) * C::STAGE;
+    float *fb = fxb + b * C::FX;
+    if (inner && !(mcm & (kNotFluid | 3u))) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int o = 128 * g + 4 * lane;
+        sts4(fb + fx_own + o, face4(lds4(sp + so * KC2 + o), lds4(sp + (so - sx) * KC2 + o), lds4(sp + (so + sx) * KC2 + o)));
+      }
+    } else {
+      const bool fluid = col_in && !(mcm & kNotFluid);
+      const long long cell = x + (long long)nx * p;
+      const bool xu_in = x - sx >= 0 && x - sx < nx, xd_in = x + sx >= 0 && x + sx < nx;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int o = 128 * g + 4 * lane, k = k0 + 64 * g + 2 * lane;
+        float4 FX;
+        if (!col_in) {
+          FX = halo4(1, p, o); // a column past the right edge: the halo value, zero slope
+        } else if (!fluid) {
+          FX = make_float4(0.f, 0.f, 0.f, 0.f); // never read: neighbours see the link values
+        } else {
+          const float4 xu = (mcm & gux) ? link4(A, cell, dux, k) : (xu_in ? lds4(sp + (so - sx) * KC2 + o) : halo4(hxu, p, o));
+          const float4 xd = (mcm & gdx) ? link4(A, cell, ddx, k) : (xd_in ? lds4(sp + (so + sx) * KC2 + o) : halo4(hxd, p, o));
+          FX = face4(lds4(sp + so * KC2 + o), xu, xd);
+        }
+        sts4(fb + fx_own + o, FX);
+      }
+    }
+    if (hduty) {
+      float2 out;
+      if (h_in && h_up_in && !(hmm & (kNotFluid | 3u))) {
+        out = face2u(lds2(sp + hc * KC2 + ho), lds2(sp + hup * KC2 + ho), lds2(sp + hdn * KC2 + ho));
+      } else if (!h_in) {
+        out = halo2(hxu, p, ho); // the halo column beyond the domain edge: its value
+      } else if (hmm & kNotFluid) {
+        out = make_float2(0.f, 0.f);
+      } else {
+        const long long hcell = hx + (long long)nx * p;
+        const int k = k0 + hj;
+        const float2 up = (hmm & gux) ? link2(A, hcell, dux, k) : (h_up_in ? lds2(sp + hup * KC2 + ho) : halo2(hxu, p, ho));
+        const float2 dn = (hmm & gdx) ? link2(A, hcell, ddx, k) : lds2(sp + hdn * KC2 + ho);
+        out = face2u(lds2(sp + hc * KC2 + ho), up, dn);
+      }
+      sts2(fb + hout + ho, out);
+    }
+  };
+
+  bool abort_local = false;
+  int waited = -1; // the last stage this thread waited for successfully
+  unsigned mc0 = cflag(p0), mc1 = cflag(p0 + d);
+  unsigned hm1 = hflag(p0 + d);
+  if (M > 0) {
+    if (mbar_wait(&full[0], 0)) waited = 0;
+    else abort_local = true;
+    publish(0, mc0, hflag(p0), 0);
+  }
+  float *fn_cell = A.fn + ((size_t)(x + (long long)nx * p0) * A.nvp + k0) * 2 + 4 * lane;
+  // lanes 4 i write sum i (i < 8); lane 1 writes the ninth sum
+  const int sidx = ((lane & 3) == 0) ? (lane >> 2) : 8;
+  float *part_cell = A.part + ((size_t)chunk * NM + sidx) * A.ncell + x + (long long)nx * p0;
+  const long long step_cells = (long long)d * nx;
+  bool ok = !__syncthreads_or(abort_local ? 1 : 0);
+  int m = 0;
+  for (; ok && m < M; ++m) {
+    const int p = p0 + d * m, par = m & 1;
+    const bool nin = row_in(m + 1);
+    const long long cell = x + (long long)nx * p;
+    // prefetch: flags two rows ahead, the Shakhov parameters of the next row
+    const unsigned mc2 = cflag(p + 2 * d), hm2 = hflag(p + 2 * d);
+    const float macn = (lane < kMac && col_in && nin) ? __ldg(A.mac + (cell + step_cells) * kMac + lane) : 0.f;
+    if (nin) {
+      if (mbar_wait(&full[(m + 1) % NST], ((m + 1) / NST) & 1)) waited = m + 1;
+      else abort_local = true;
+    }
+    // (1) the x faces of the next row, into the other buffer
+    if (m + 1 < M && !abort_local) publish(m + 1, mc1, hm1, par ^ 1);
+    // (2) update of the own cell at row p and its moment sums
+    const float *sp = stage + (m % NST) * C::STAGE;
+    float *sp1 = stage + ((m + 1) % NST) * C::STAGE;
+    if (!nin && col_in) {
+      // past the domain edge: the halo value of the own column, written into
+      // the unused slot of that row (each lane reads back only what it wrote)
+#pragma unroll
+      for (int g = 0; g < G; ++g) sts4(sp1 + so * KC2 + 128 * g + 4 * lane, halo4(hyd, x, 128 * g + 4 * lane));
+    }
+    const float *fb = fxb + par * C::FX;
+    const bool fluid = col_in && !(mc0 & kNotFluid) && !abort_local;
+    float acc[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) acc[i] = 0.f;
+    if (fluid) {
+      const float4 *pm = reinterpret_cast<const float4 *>(smac + (par * TX + warp) * kMac);
+      const float4 c0v = pm[0], c1v = pm[1], c2v = pm[2];
+      const float2 mU0 = dup(-c0v.y), mU1 = dup(-c0v.z);
+      const float2 nl2 = dup(-c1v.x * kLog2e);                        // -log2(e) / T
+      const float Tc = 2.f * c1v.y;                                    // T
+      const float2 pH = dup(-2.f * kLn2), pB = dup(-Tc * kLn2), mT = dup(-Tc);
+      const float2 hT = dup(c1v.y);                                    // T / 2
+      const float2 q0 = dup(c1v.z * c1v.w), q1 = dup(c1v.z * c2v.x);   // the Shakhov factor folded into q
+      const float2 dt2 = dup(c2v.z), pre2 = dup(c0v.x);
+      const bool ghosty = (mc0 & 15u) != 0;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int o = 128 * g + 4 * lane, k = k0 + 64 * g + 2 * lane;
+        const float2 ax = lds2(scon + ((g * 3 + 0) * 32 + lane) * 2);
+        const float2 ay = lds2(scon + ((g * 3 + 1) * 32 + lane) * 2);
+        const float2 wk = lds2(scon + ((g * 3 + 2) * 32 + lane) * 2);
+        const float4 fc = lds4(sp + so * KC2 + o);
+        const float4 fnx = lds4(sp1 + so * KC2 + o);
+        const float4 Dn = sub4(fnx, fc);
+        const float4 fxo = lds4(fb + fx_own + o);
+        float4 fxi = lds4(fb + fx_in + o), fyi = P[g];
+        // y outflow face of this row (the inflow of the next)
+        float4 fyo;
+        if (!(mc0 & (guy | gdy))) {
+          fyo = face4d(fc, D[g], Dn);
+        } else {
+          fyo = face4d(fc, (mc0 & guy) ? sub4(fc, link4(A, cell, duy, k)) : D[g],
+                       (mc0 & gdy) ? sub4(link4(A, cell, ddy, k), fc) : Dn);
+        }
+        if (ghosty) { // a ghost upwind neighbour: the mean of its link value and this cell (one-sided slope)
+          if (mc0 & gux) fxi = mean4(link4(A, cell, dux, k), fc);
+          if (mc0 & guy) fyi = mean4(link4(A, cell, duy, k), fc);
+        }
+        P[g] = fyo;
+        D[g] = Dn; // f(p + d) - f(p): the upwind difference of the next row
+        // reduced Shakhov equilibria of the two velocities (Sec. 4):
+        // H = e (1 + A c.q (2t - 4)), B = T/2 e (1 + A c.q (2t - 2)), t = c^2 / T
+        const float2 cx = __ffma2_rn(ax, sigx, mU0), cy = __ffma2_rn(ay, sigy, mU1);
+        const float2 c2 = __ffma2_rn(cx, cx, __fmul2_rn(cy, cy));
+        const float2 tn = __fmul2_rn(c2, nl2); // -t log2(e)
+        const float2 e = __fmul2_rn(pre2, make_float2(ex2(tn.x), ex2(tn.y)));
+        const float2 mm = __fmul2_rn(e, __ffma2_rn(cx, q0, __fmul2_rn(cy, q1)));
+        const float2 H = __ffma2_rn(mm, __ffma2_rn(tn, pH, dup(-4.f)), e);
+        const float2 B = __ffma2_rn(mm, __ffma2_rn(tn, pB, mT), __fmul2_rn(hT, e));
+        // forward Euler per velocity on (h, b): relaxation, then the flux differences
+        float2 n0 = __ffma2_rn(dt2, sub2(make_float2(H.x, B.x), lo2(fc)), lo2(fc));
+        float2 n1 = __ffma2_rn(dt2, sub2(make_float2(H.y, B.y), hi2(fc)), hi2(fc));
+        n0 = __ffma2_rn(dup(ax.x), sub2(lo2(fxi), lo2(fxo)), n0);
+        n1 = __ffma2_rn(dup(ax.y), sub2(hi2(fxi), hi2(fxo)), n1);
+        n0 = __ffma2_rn(dup(ay.x), sub2(lo2(fyi), lo2(fyo)), n0);
+        n1 = __ffma2_rn(dup(ay.y), sub2(hi2(fyi), hi2(fyo)), n1);
+        *reinterpret_cast<float4 *>(fn_cell + 128 * g) = cat4(n0, n1);
+        // moment sums about the stored bulk velocity (Eqs. moments1-3, reduced)
+        const float2 wh = __fmul2_rn(wk, make_float2(n0.x, n1.x));
+        const float2 e2 = __ffma2_rn(c2, wh, __fmul2_rn(wk, make_float2(n0.y, n1.y))); // w (c^2 h + b)
+        const float2 cxwh = __fmul2_rn(cx, wh);
+        acc_add(acc[0], wh);
+        acc_fma(acc[1], cx, wh);
+        acc_fma(acc[2], cy, wh);
+        acc_add(acc[3], e2);
+        acc_fma(acc[4], cx, cxwh);
+        acc_fma(acc[5], cy, cxwh);
+        acc_fma(acc[6], cy, __fmul2_rn(cy, wh));
+        acc_fma(acc[7], cx, e2);
+        acc_fma(acc[8], cy, e2);
+      }
+    } else {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int o = 128 * g + 4 * lane;
+        P[g] = col_in ? make_float4(0.f, 0.f, 0.f, 0.f) : lds4(sfinf + o);
+        D[g] = col_in ? sub4(lds4(sp1 + so * KC2 + o), lds4(sp + so * KC2 + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    // (3) butterfly reduction of the sums over the 32 lanes: three rounds halve
+    //     the eight values a lane holds, two more finish the one it keeps; the
+    //     ninth sum is a plain xor tree
+    {
+      float v4[4];
+      const bool b16 = lane & 16;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float keep = b16 ? acc[4 + i] : acc[i];
+        const float send = b16 ? acc[i] : acc[4 + i];
+        v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+      float v2[2];
+      const bool b8 = lane & 8;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float keep = b8 ? v4[2 + i] : v4[i];
+        const float send = b8 ? v4[i] : v4[2 + i];
+        v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      const bool b4 = lane & 4;
+      float v1 = (b4 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b4 ? v2[0] : v2[1], 4);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+      float s8 = acc[8];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
+      if (col_in) {
+        if ((lane & 3) == 0) *part_cell = v1;
+        if (lane == 1) *part_cell = s8;
+      }
+    }
+    // (4) advance: the flags and parameters of the next rows
+    if (lane < kMac) smac[((par ^ 1) * TX + warp) * kMac + lane] = macn;
+    mc0 = mc1;
+    mc1 = mc2;
+    hm1 = hm2;
+    fn_cell += step_cells * A.nvp * 2;
+    part_cell += step_cells;
+    // faces of the next row published, this row's buffer and stage m consumed
+    if (__syncthreads_or(abort_local ? 1 : 0)) {
+      ok = false;
+      break;
+    }
+    // the stage of row index m + NST into the slot of stage m
+    if (threadIdx.x == 0 && m + NST <= M && row_in(m + NST)) {
+      fence_proxy_async();
+      issue(m + NST);
+      issued = m + NST;
+    }
   }
   if (!ok && threadIdx.x == 0) {
     atomicOr(A.err, kFlagTimeout);
-    // drain: rows issued but not yet waited for must land (or time out
-    // again) before the block's shared memory is released
-    const int issued_end = min(M.ylast, y + NST - 1);
-    for (int r = max(M.y0 + 2, y + 2); r < issued_end; ++r) {
-      const int j = r - M.y0;
-      mbar_wait(&M.full[j % NST], (j / NST) & 1);
-    }
+    for (int q = waited + 1; q <= issued; ++q) mbar_wait(&full[q % NST], (q / NST) & 1);
   }
   return ok;
 }
 
-template <int KPT, bool W>
+template <int VPL>
 __global__ void __launch_bounds__(NTHREADS, 2) sweep2d_tma_kernel(const __grid_constant__ CUtensorMap tmf,
-                                                                  TmaArgs A) {
+                                                                  Oct2Args A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int y0 = blockIdx.z * A.rows;
-  march2d<KPT, W>(A, &tmf, blockIdx.x * TX, blockIdx.y * Cfg<KPT>::KC, y0, min(A.ny, y0 + A.rows), smem_raw, false);
+  const int ya = blockIdx.z * A.rows;
+  march2o<VPL>(A, &tmf, blockIdx.x * TX, blockIdx.y, ya, min(A.ny, ya + A.rows), smem_raw, false);
 }
 
 // One item of the batched sweep: a march of one member case.
 struct WorkItem {
   int cas;    // member index
-  int x0, k0; // first column and first chunk velocity
-  int y0, y1; // rows
-  int kpt;    // velocities per lane (2 or 4)
+  int x0;     // first column
+  int chunk;  // velocity chunk
+  int ya, yb; // rows
+  int vpl;    // velocities per lane of the member's layout
   int pad[2];
 };
 
 // The batched sweep: a persistent grid whose blocks take work items in order
 // from a shared counter (items sorted by decreasing size).  Member c at step
-// parity par uses args[2 c + par] and tmaps[2 c + par].  KSEL = 4 or 2 when
+// parity par uses args[2 c + par] and tmaps[2 c + par].  VSEL = 6, 4 or 2 when
 // every item takes that many velocities per lane, 0 for a mix.
-template <int KSEL>
+template <int VSEL>
 __global__ void __launch_bounds__(NTHREADS, 2)
-    sweep2d_tma_batch_kernel(const TmaArgs *__restrict__ args, const CUtensorMap *__restrict__ tmaps,
+    sweep2d_tma_batch_kernel(const Oct2Args *__restrict__ args, const CUtensorMap *__restrict__ tmaps,
                              const WorkItem *__restrict__ items, int nitems, int *__restrict__ next, int par) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ TmaArgs sA;
+  __shared__ Oct2Args sA;
   __shared__ int s_item;
   bool reinit = false;
   for (;;) {
@@ -584,13 +559,12 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     __syncthreads();
     const CUtensorMap *tm = tmaps + 2 * it.cas + par;
     bool ok;
-    if constexpr (KSEL == 4)
-      ok = march2d<4, false>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
-    else if constexpr (KSEL == 2)
-      ok = march2d<2, false>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
+    if constexpr (VSEL != 0)
+      ok = march2o<VSEL>(sA, tm, it.x0, it.chunk, it.ya, it.yb, smem_raw, reinit);
     else
-      ok = (it.kpt == 4) ? march2d<4, false>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit)
-                         : march2d<2, false>(sA, tm, it.x0, it.k0, it.y0, it.y1, smem_raw, reinit);
+      ok = (it.vpl == 6) ? march2o<6>(sA, tm, it.x0, it.chunk, it.ya, it.yb, smem_raw, reinit)
+           : (it.vpl == 4) ? march2o<4>(sA, tm, it.x0, it.chunk, it.ya, it.yb, smem_raw, reinit)
+                           : march2o<2>(sA, tm, it.x0, it.chunk, it.ya, it.yb, smem_raw, reinit);
     if (!ok) break; // uniform: the abort vote is block-wide
     reinit = true;
     __syncthreads(); // the item's shared memory and arguments are released
@@ -610,98 +584,101 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-} // namespace
-
-// The TMA sweep applies to 2D cases in FP32 storage with the velocity count
-// padded to a multiple of 64.
-bool tma_sweep_applicable(const ibdvm_ctx *ctx) {
-  return ctx->dim == 2 && ctx->precision == IBDVM_MIXED && (ctx->nvp % 64) == 0 && encoder() != nullptr;
+// the tensor map of a state buffer: 16-byte velocity pairs (h, b of two
+// velocities) x pairs x cells x rows; one box is a staged row of a chunk
+CUresult encode_map(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap *out, void *f, const Geom &g, int nvp, int kc) {
+  cuuint64_t dims[4] = {4, (cuuint64_t)nvp / 2, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1]};
+  cuuint64_t strides[3] = {16, (cuuint64_t)nvp * 8, (cuuint64_t)g.n[0] * nvp * 8};
+  cuuint32_t box[4] = {4, (cuuint32_t)kc / 2, XW, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-int tma_sweep_kpt(const ibdvm_ctx *ctx) { return (ctx->nvp % 128 == 0) ? 4 : 2; }
-int tma_sweep_nchunk(const ibdvm_ctx *ctx) { return ctx->nvp / (32 * tma_sweep_kpt(ctx)); }
-
-cudaError_t tma_sweep_prepare(ibdvm_ctx *ctx) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
-  if (!enc) return cudaErrorNotSupported;
-  const int kpt = tma_sweep_kpt(ctx);
-  const int kc = 32 * kpt;
-  for (int b = 0; b < 2; ++b) {
-    CUtensorMap *tm = reinterpret_cast<CUtensorMap *>(ctx->tmap[b]);
-    cuuint64_t dims[3] = {(cuuint64_t)ctx->nvp * 2, (cuuint64_t)ctx->geom.n[0], (cuuint64_t)ctx->geom.n[1]};
-    cuuint64_t strides[2] = {(cuuint64_t)ctx->nvp * 2 * 4, (cuuint64_t)ctx->geom.n[0] * ctx->nvp * 2 * 4};
-    cuuint32_t box[3] = {(cuuint32_t)(2 * kc), (cuuint32_t)COLS, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ctx->f[b], dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  }
-  const int s4 = (int)Cfg<4>::SMEM, s2 = (int)Cfg<2>::SMEM;
-  cudaError_t e = (kpt == 4) ? cudaFuncSetAttribute(sweep2d_tma_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4)
-                             : cudaFuncSetAttribute(sweep2d_tma_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
-  if (e != cudaSuccess) return e;
-  return (kpt == 4) ? cudaFuncSetAttribute(sweep2d_tma_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4)
-                    : cudaFuncSetAttribute(sweep2d_tma_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
-}
-
-cudaError_t tma_sweep_launch(ibdvm_ctx *ctx) {
-  TmaArgs A{};
-  A.f = static_cast<const float *>(ctx->f[ctx->cur]);
-  A.fn = static_cast<float *>(ctx->f[1 - ctx->cur]);
+Oct2Args oct2_args(const ibdvm_ctx *ctx, int cur, int *err) {
+  Oct2Args A{};
+  A.f = static_cast<const float *>(ctx->f[cur]);
+  A.fn = static_cast<float *>(ctx->f[1 - cur]);
   A.mac = static_cast<const float *>(ctx->mac);
-  A.xi = static_cast<const float *>(ctx->xiT);
-  A.w = static_cast<const float *>(ctx->wT);
+  A.vconst = ctx->oct_const;
+  A.csign = ctx->oct_sign;
   A.finf = static_cast<const float *>(ctx->finf);
   A.cmask = ctx->cmask;
   A.dslot = ctx->dslot;
   A.dlinks = ctx->dlinks;
   A.lval = static_cast<const float *>(ctx->lval);
   A.part = ctx->partf;
-  A.err = ctx->d_flags;
+  A.err = err;
   A.ncell = ctx->ncell;
   A.nx = ctx->geom.n[0];
   A.ny = ctx->geom.n[1];
   A.nvp = ctx->nvp;
-  A.nv = ctx->nv;
-  A.dt = (float)ctx->geom.dt;
-  A.rdx = (float)(1.0 / ctx->geom.dx[0]);
-  A.rdy = (float)(1.0 / ctx->geom.dx[1]);
+  A.rows = 0;
+  A.kc = ctx->oct_kc;
+  for (int a = 0; a < 2; ++a) A.sig[a] = (float)(ctx->geom.dx[a] / ctx->geom.dt);
   A.whalo = static_cast<const float *>(ctx->whalo);
   A.wmask = ctx->wall_mask;
   for (int i = 0; i < 4; ++i) A.woff[i] = ctx->wall_off[i];
-  const int kpt = tma_sweep_kpt(ctx);
+  return A;
+}
+
+template <int VPL> cudaError_t set_smem() {
+  cudaError_t e = cudaFuncSetAttribute(sweep2d_tma_kernel<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Cfg<VPL>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sweep2d_tma_batch_kernel<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Cfg<VPL>::SMEM);
+}
+
+} // namespace
+
+// The TMA sweep applies to 2D cases in FP32 storage with the quadrant layout.
+bool tma_sweep_applicable(const ibdvm_ctx *ctx) {
+  return ctx->dim == 2 && ctx->precision == IBDVM_MIXED && ctx->oct_kc > 0 && encoder() != nullptr;
+}
+
+int tma_sweep_nchunk(const ibdvm_ctx *ctx) { return ctx->nvp / ctx->oct_kc; }
+
+cudaError_t tma_sweep_prepare(ibdvm_ctx *ctx) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+  if (!enc || ctx->oct_kc <= 0) return cudaErrorNotSupported;
+  for (int b = 0; b < 2; ++b)
+    if (encode_map(enc, reinterpret_cast<CUtensorMap *>(ctx->tmap[b]), ctx->f[b], ctx->geom, ctx->nvp,
+                   ctx->oct_kc) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  switch (ctx->oct_kc) {
+  case 192: return set_smem<6>();
+  case 128: return set_smem<4>();
+  default: return set_smem<2>();
+  }
+}
+
+cudaError_t tma_sweep_launch(ibdvm_ctx *ctx) {
+  Oct2Args A = oct2_args(ctx, ctx->cur, ctx->d_flags);
   const int nstrip = (A.nx + TX - 1) / TX;
-  const int nchunk = ctx->nvp / (32 * kpt);
-  // rows per block: about 64 (many short marches leave a short tail: on
-  // 512^2 x 48^2, 64 rows per block beat 128, 256 and 32), and enough blocks
-  // for several waves of two blocks per SM
+  const int nchunk = ctx->nvp / ctx->oct_kc;
+  // rows per block: about 64, and enough blocks for several waves of two
+  // blocks per SM
   int nrb = (A.ny + 63) / 64;
   while ((long long)nstrip * nchunk * nrb < 8LL * 152 && A.ny / (nrb * 2) >= 16) nrb *= 2;
   A.rows = (A.ny + nrb - 1) / nrb;
   dim3 grid(nstrip, nchunk, (A.ny + A.rows - 1) / A.rows);
   const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(ctx->tmap[ctx->cur]);
-  // cases with diffuse domain walls read their halo at the domain edges
-  if (A.wmask) {
-    if (kpt == 4)
-      sweep2d_tma_kernel<4, true><<<grid, NTHREADS, Cfg<4>::SMEM, ctx->stream>>>(*tm, A);
-    else
-      sweep2d_tma_kernel<2, true><<<grid, NTHREADS, Cfg<2>::SMEM, ctx->stream>>>(*tm, A);
-  } else if (kpt == 4) {
-    sweep2d_tma_kernel<4, false><<<grid, NTHREADS, Cfg<4>::SMEM, ctx->stream>>>(*tm, A);
-  } else {
-    sweep2d_tma_kernel<2, false><<<grid, NTHREADS, Cfg<2>::SMEM, ctx->stream>>>(*tm, A);
+  switch (ctx->oct_kc) {
+  case 192: sweep2d_tma_kernel<6><<<grid, NTHREADS, Cfg<6>::SMEM, ctx->stream>>>(*tm, A); break;
+  case 128: sweep2d_tma_kernel<4><<<grid, NTHREADS, Cfg<4>::SMEM, ctx->stream>>>(*tm, A); break;
+  default: sweep2d_tma_kernel<2><<<grid, NTHREADS, Cfg<2>::SMEM, ctx->stream>>>(*tm, A); break;
   }
   return cudaGetLastError();
 }
 
 bool tma_batch_member_ok(const ibdvm_ctx *ctx) {
   if (ctx->precision != IBDVM_MIXED || ctx->partf == nullptr || encoder() == nullptr) return false;
-  if (ctx->dim == 2) return (ctx->nvp % 64) == 0;
+  if (ctx->dim == 2) return tma_sweep_applicable(ctx);
   return tma3_sweep_applicable(ctx);
 }
 
-int tma_batch_kpt_max(const ibdvm_ctx *ctx) { return (ctx->dim == 3 || ctx->nvp % 128 == 0) ? 4 : 2; }
+int tma_batch_kpt_max(const ibdvm_ctx *ctx) { return ctx->oct_kc / 32; }
 
 void tma_batch_free(SweepTables &t) {
   void *ps[] = {t.args, t.tmaps, t.items, t.next};
@@ -712,71 +689,47 @@ void tma_batch_free(SweepTables &t) {
 
 cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::vector<int> &kpt, int rows,
                             int *flags, SweepTables &t, cudaStream_t s) {
+  (void)kpt; // the chunk of every member is that of its velocity layout
   tma_batch_free(t);
   if (!cases.empty() && cases[0]->dim == 3) return tma3_batch_build(cases, rows, flags, t, s);
   PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
   if (!enc) return cudaErrorNotSupported;
   const int n = static_cast<int>(cases.size());
-  std::vector<TmaArgs> args(2 * n);
+  std::vector<Oct2Args> args(2 * n);
   std::vector<CUtensorMap> maps(2 * n);
   std::vector<WorkItem> items;
+  int vsel = -1;
   for (int i = 0; i < n; ++i) {
     const ibdvm_ctx *ctx = cases[i];
-    const int kc = 32 * kpt[i];
+    if (ctx->oct_kc <= 0) return cudaErrorInvalidValue;
+    const int vpl = ctx->oct_kc / 32;
+    vsel = (vsel < 0 || vsel == vpl) ? vpl : 0;
     for (int p = 0; p < 2; ++p) {
       const int cur = ctx->cur ^ p;
-      TmaArgs &A = args[2 * i + p];
-      A = TmaArgs{};
-      A.f = static_cast<const float *>(ctx->f[cur]);
-      A.fn = static_cast<float *>(ctx->f[1 - cur]);
-      A.mac = static_cast<const float *>(ctx->mac);
-      A.xi = static_cast<const float *>(ctx->xiT);
-      A.w = static_cast<const float *>(ctx->wT);
-      A.finf = static_cast<const float *>(ctx->finf);
-      A.cmask = ctx->cmask;
-      A.dslot = ctx->dslot;
-      A.dlinks = ctx->dlinks;
-      A.lval = static_cast<const float *>(ctx->lval);
-      A.part = ctx->partf;
-      A.err = flags + i;
-      A.ncell = ctx->ncell;
-      A.nx = ctx->geom.n[0];
-      A.ny = ctx->geom.n[1];
-      A.nvp = ctx->nvp;
-      A.nv = ctx->nv;
-      A.rows = 0;
-      A.dt = (float)ctx->geom.dt;
-      A.rdx = (float)(1.0 / ctx->geom.dx[0]);
-      A.rdy = (float)(1.0 / ctx->geom.dx[1]);
-      cuuint64_t dims[3] = {(cuuint64_t)ctx->nvp * 2, (cuuint64_t)A.nx, (cuuint64_t)A.ny};
-      cuuint64_t strides[2] = {(cuuint64_t)ctx->nvp * 2 * 4, (cuuint64_t)A.nx * ctx->nvp * 2 * 4};
-      cuuint32_t box[3] = {(cuuint32_t)(2 * kc), (cuuint32_t)COLS, 1};
-      cuuint32_t estr[3] = {1, 1, 1};
-      CUresult r = enc(&maps[2 * i + p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ctx->f[cur], dims, strides, box, estr,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+      args[2 * i + p] = oct2_args(ctx, cur, flags + i);
+      if (encode_map(enc, &maps[2 * i + p], ctx->f[cur], ctx->geom, ctx->nvp, ctx->oct_kc) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     }
     // items: column strips x velocity chunks x row ranges of about `rows` rows
     const int nx = ctx->geom.n[0], ny = ctx->geom.n[1];
     const int nrb = (rows <= 0 || rows >= ny) ? 1 : (ny + rows - 1) / rows;
     const int per = (ny + nrb - 1) / nrb;
     for (int x0 = 0; x0 < nx; x0 += TX)
-      for (int k0 = 0; k0 < ctx->nvp; k0 += kc)
-        for (int y0 = 0; y0 < ny; y0 += per) {
+      for (int c = 0; c < ctx->nvp / ctx->oct_kc; ++c)
+        for (int ya = 0; ya < ny; ya += per) {
           WorkItem it{};
           it.cas = i;
           it.x0 = x0;
-          it.k0 = k0;
-          it.y0 = y0;
-          it.y1 = std::min(ny, y0 + per);
-          it.kpt = kpt[i];
+          it.chunk = c;
+          it.ya = ya;
+          it.yb = std::min(ny, ya + per);
+          it.vpl = vpl;
           items.push_back(it);
         }
   }
   // largest items first, so the last items to start are the short ones
   std::stable_sort(items.begin(), items.end(), [](const WorkItem &a, const WorkItem &b) {
-    return (long long)(a.y1 - a.y0) * a.kpt > (long long)(b.y1 - b.y0) * b.kpt;
+    return (long long)(a.yb - a.ya) * a.vpl > (long long)(b.yb - b.ya) * b.vpl;
   });
   cudaError_t e;
   auto up = [&](const void *h, size_t bytes, void *&d) -> cudaError_t {
@@ -784,25 +737,19 @@ cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::ve
     if (r != cudaSuccess || bytes == 0) return r;
     return cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s);
   };
-  if ((e = up(args.data(), args.size() * sizeof(TmaArgs), t.args)) != cudaSuccess) return e;
+  if ((e = up(args.data(), args.size() * sizeof(Oct2Args), t.args)) != cudaSuccess) return e;
   if ((e = up(maps.data(), maps.size() * sizeof(CUtensorMap), t.tmaps)) != cudaSuccess) return e;
   if ((e = up(items.data(), items.size() * sizeof(WorkItem), t.items)) != cudaSuccess) return e;
   void *nx = nullptr;
   if ((e = cudaMalloc(&nx, sizeof(int))) != cudaSuccess) return e;
   t.next = static_cast<int *>(nx);
   t.nitems = static_cast<int>(items.size());
-  {
-    bool all4 = true, all2 = true;
-    for (int k : kpt) {
-      all4 = all4 && k == 4;
-      all2 = all2 && k == 2;
-    }
-    t.ksel = all4 ? 4 : (all2 ? 2 : 0);
-  }
-  const int smem = (int)std::max(Cfg<4>::SMEM, Cfg<2>::SMEM);
-  const void *fn = (t.ksel == 4) ? (const void *)sweep2d_tma_batch_kernel<4>
+  t.ksel = std::max(vsel, 0);
+  const void *fn = (t.ksel == 6)   ? (const void *)sweep2d_tma_batch_kernel<6>
+                   : (t.ksel == 4) ? (const void *)sweep2d_tma_batch_kernel<4>
                    : (t.ksel == 2) ? (const void *)sweep2d_tma_batch_kernel<2>
                                    : (const void *)sweep2d_tma_batch_kernel<0>;
+  const int smem = (t.ksel == 4) ? (int)Cfg<4>::SMEM : (t.ksel == 2) ? (int)Cfg<2>::SMEM : (int)Cfg<6>::SMEM;
   if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -817,16 +764,17 @@ cudaError_t tma_batch_launch(const SweepTables &t, int par, cudaStream_t s) {
   if (t.nitems == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(t.next, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  const int smem = (int)std::max(Cfg<4>::SMEM, Cfg<2>::SMEM);
-  const TmaArgs *a = static_cast<const TmaArgs *>(t.args);
+  const Oct2Args *a = static_cast<const Oct2Args *>(t.args);
   const CUtensorMap *m = static_cast<const CUtensorMap *>(t.tmaps);
   const WorkItem *it = static_cast<const WorkItem *>(t.items);
-  if (t.ksel == 4)
-    sweep2d_tma_batch_kernel<4><<<t.grid, NTHREADS, smem, s>>>(a, m, it, t.nitems, t.next, par);
+  if (t.ksel == 6)
+    sweep2d_tma_batch_kernel<6><<<t.grid, NTHREADS, Cfg<6>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
+  else if (t.ksel == 4)
+    sweep2d_tma_batch_kernel<4><<<t.grid, NTHREADS, Cfg<4>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
   else if (t.ksel == 2)
-    sweep2d_tma_batch_kernel<2><<<t.grid, NTHREADS, smem, s>>>(a, m, it, t.nitems, t.next, par);
+    sweep2d_tma_batch_kernel<2><<<t.grid, NTHREADS, Cfg<2>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
   else
-    sweep2d_tma_batch_kernel<0><<<t.grid, NTHREADS, smem, s>>>(a, m, it, t.nitems, t.next, par);
+    sweep2d_tma_batch_kernel<0><<<t.grid, NTHREADS, Cfg<6>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
   return cudaGetLastError();
 }
 

@@ -34,8 +34,9 @@ def rel_err(a, b):
 
 
 def mixed_cases():
-    """Uneven members: 64, 144 (padded to 192) and 256 velocities, three body
-    kinds, grids that are not multiples of the 8-column strip."""
+    """Uneven members: 64, 144 and 256 velocities (quadrants padded to
+    64-velocity chunks), three body kinds, grids that are not multiples of the
+    8-column strip."""
     a = wl.small_2d("circle", n=40, nv=16, Ma=0.4, precision="mixed")            # 256 velocities
     b = wl.small_2d("ellipse", n=24, nv=8, Ma=0.6, precision="mixed")           # 64 velocities
     b["n"] = [27, 21]
@@ -137,18 +138,10 @@ def test_tilings(torch, rows, kpt):
     b.step(4)
     for s in solo:
         s.step(4)
+    # the row tiling does not change any cell's arithmetic (kpt has no effect)
     for s, m in zip(solo, mem):
-        if kpt == 2 and s.nvel_padded % 128 == 0:
-            # 64-velocity chunks: the FP32 moment partial sums group differently
-            assert rel_err(m.get_f(), s.get_f()) < 1e-5
-            Ws, _, t = s.moments()
-            Wm, _, _ = m.moments()
-            fl = t == 0
-            for i in range(4):
-                if np.abs(Ws[fl, i]).max() > 1e-9:
-                    assert rel_err(Wm[fl, i], Ws[fl, i]) < 1e-5
-        else:
-            assert_same(s, m)
+        assert_same(s, m)
+    assert b.tiling()["kpt"] in (2, 4, 6)
     b.close()
 
 
@@ -162,8 +155,8 @@ def test_autotuner_keeps_a_candidate_and_steps_stay_correct(torch):
     best = b.tune(2)
     assert best > 0
     t = b.tiling()
-    assert t["rows"] in (16, 32, 64, 128, 0) and t["kpt"] in (2, 4)
-    nsteps = 10 * (2 + 2)  # ten trials of a warm-up pair and two timed steps
+    assert t["rows"] in (16, 32, 64, 128, 0) and t["kpt"] in (2, 4, 6)
+    nsteps = 5 * (2 + 2)  # five trials of a warm-up pair and two timed steps
     for s in solo:
         s.step(nsteps)
     for s, m in zip(solo, mem):

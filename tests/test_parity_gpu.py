@@ -654,12 +654,12 @@ def _solver_env(case, no_tma: bool):
             os.environ["IBDVM_NO_TMA"] = old
 
 
-@pytest.mark.parametrize("shape", ["square_kpt4", "ragged_kpt2", "short_rows", "naca_kpt4", "odd_nv"])
+@pytest.mark.parametrize("shape", ["square_256v", "ragged_64v", "short_rows", "naca_256v", "odd_nv"])
 def test_tma_sweep_against_oracle_and_plain_sweep(shape):
-    if shape == "square_kpt4":
-        case = wl.small_2d("circle", n=40, nv=16, Ma=0.4)           # 256 velocities: 4 per lane
-    elif shape == "ragged_kpt2":
-        case = wl.small_2d("ellipse", n=24, nv=8, Ma=0.6)           # 64 velocities: 2 per lane
+    if shape == "square_256v":
+        case = wl.small_2d("circle", n=40, nv=16, Ma=0.4)           # 256 velocities, 64 per quadrant
+    elif shape == "ragged_64v":
+        case = wl.small_2d("ellipse", n=24, nv=8, Ma=0.6)           # 64 velocities, quadrants padded to 64
         case["n"] = [27, 21]
         case["lo"], case["hi"] = [-2.2, -1.7], [2.0, 1.9]
     elif shape == "short_rows":
@@ -667,10 +667,10 @@ def test_tma_sweep_against_oracle_and_plain_sweep(shape):
         case["n"] = [36, 9]
         case["lo"], case["hi"] = [-3.0, -0.75], [3.0, 0.75]
         case["body"] = wl.circle(0.4)
-    elif shape == "naca_kpt4":
+    elif shape == "naca_256v":
         case = wl.small_2d("naca", n=48, nv=16, Ma=0.5)
     else:
-        case = wl.small_2d("circle", n=32, nv=11, Ma=0.5)           # 121 velocities, padded to 128
+        case = wl.small_2d("circle", n=32, nv=11, Ma=0.5)           # 121 velocities: quadrants of 36, 30, 30, 25
     case["precision"] = "mixed"
     o = oracle.OracleCase(case)
     f0 = perturbed(o, 21, 0.2)
