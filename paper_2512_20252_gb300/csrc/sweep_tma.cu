@@ -46,6 +46,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.h"
@@ -396,7 +397,10 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
       const float2 hT = dup(c1v.y);                                    // T / 2
       const float2 q0 = dup(c1v.z * c1v.w), q1 = dup(c1v.z * c2v.x);   // the Shakhov factor folded into q
       const float2 dt2 = dup(c2v.z), pre2 = dup(c0v.x);
-      const bool ghosty = (mc0 & 15u) != 0;
+      // the row body, in two copies: GEN = a ghost neighbour (links for the
+      // faces and the inflow), else the plain stencil
+      auto body = [&](auto gen) {
+        constexpr bool GEN = decltype(gen)::value;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int o = 128 * g + 4 * lane, k = k0 + 64 * g + 2 * lane;
@@ -410,13 +414,13 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
         float4 fxi = lds4(fb + fx_in + o), fyi = P[g];
         // y outflow face of this row (the inflow of the next)
         float4 fyo;
-        if (!(mc0 & (guy | gdy))) {
+        if constexpr (!GEN) {
+          (void)k;
           fyo = face4d(fc, D[g], Dn);
         } else {
           fyo = face4d(fc, (mc0 & guy) ? sub4(fc, link4(A, cell, duy, k)) : D[g],
                        (mc0 & gdy) ? sub4(link4(A, cell, ddy, k), fc) : Dn);
-        }
-        if (ghosty) { // a ghost upwind neighbour: the mean of its link value and this cell (one-sided slope)
+          // a ghost upwind neighbour: the mean of its link value and this cell (one-sided slope)
           if (mc0 & gux) fxi = mean4(link4(A, cell, dux, k), fc);
           if (mc0 & guy) fyi = mean4(link4(A, cell, duy, k), fc);
         }
@@ -453,6 +457,11 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
         acc_fma(acc[7], cx, e2);
         acc_fma(acc[8], cy, e2);
       }
+      };
+      if (mc0 & 15u)
+        body(std::true_type{});
+      else
+        body(std::false_type{});
     } else {
 #pragma unroll
       for (int g = 0; g < G; ++g) {
