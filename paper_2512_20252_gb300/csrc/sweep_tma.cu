@@ -293,13 +293,14 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
   }
   if (lane < kMac) smac[warp * kMac + lane] = col_in ? A.mac[(x + (long long)nx * p0) * kMac + lane] : 0.f;
 
-  // x outflow faces of row index m (own cell and the warp's halo duty) from
-  // stage m into face buffer b
-  auto publish = [&](int m, unsigned mcm, unsigned hmm, int b) {
+  // x outflow faces of row index m (own cell and the halo duty) from stage m
+  // into face buffer b; PL (plain): no cell of the march is special
+  auto publish = [&](auto plain, int m, unsigned mcm, unsigned hmm, int b) {
+    constexpr bool PL = decltype(plain)::value;
     const int p = p0 + d * m;
     const float *sp = stage + (m % NST) * C::STAGE;
     float *fb = fxb + b * C::FX;
-    if (inner && !(mcm & (kNotFluid | 3u))) {
+    if (PL || (inner && !(mcm & (kNotFluid | 3u)))) {
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int o = 128 * g + 4 * lane;
@@ -327,7 +328,7 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
     }
     if (hduty) {
       float2 out;
-      if (h_in && h_up_in && !(hmm & (kNotFluid | 3u))) {
+      if (PL || (h_in && h_up_in && !(hmm & (kNotFluid | 3u)))) {
         out = face2u(lds2(sp + hc * KC2 + ho), lds2(sp + hup * KC2 + ho), lds2(sp + hdn * KC2 + ho));
       } else if (!h_in) {
         out = halo2(hxu, p, ho); // the halo column beyond the domain edge: its value
@@ -344,6 +345,23 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
     }
   };
 
+  // A march is plain when its columns and the upwind halo column lie away
+  // from the x edges of the domain and none of their cells in its rows is
+  // special (not fluid, or a ghost neighbour: along x for the halo column);
+  // its rows then run without per-row flags.
+  bool plain_local = inner;
+  if (plain_local)
+    for (int r = ya + lane; r < yb; r += 32)
+      if (A.cmask[x + (long long)nx * r] & (kNotFluid | 15u)) plain_local = false;
+  if (warp == 0) {
+    bool hp = hx >= 0 && hx < nx && h_up_in;
+    if (hp)
+      for (int r = ya + lane; r < yb; r += 32)
+        if (A.cmask[hx + (long long)nx * r] & (kNotFluid | 3u)) hp = false;
+    plain_local = plain_local && hp;
+  }
+  const bool plain = !__syncthreads_or(plain_local ? 0 : 1);
+
   bool abort_local = false;
   int waited = -1; // the last stage this thread waited for successfully
   unsigned mc0 = cflag(p0), mc1 = cflag(p0 + d);
@@ -351,7 +369,7 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
   if (M > 0) {
     if (mbar_wait(&full[0], 0)) waited = 0;
     else abort_local = true;
-    publish(0, mc0, hflag(p0), 0);
+    publish(std::false_type{}, 0, mc0, hflag(p0), 0);
   }
   float *fn_cell = A.fn + ((size_t)(x + (long long)nx * p0) * A.nvp + k0) * 2 + 4 * lane;
   // lanes 4 i write sum i (i < 8); lane 1 writes the ninth sum
@@ -359,168 +377,175 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
   float *part_cell = A.part + ((size_t)chunk * NM + sidx) * A.ncell + x + (long long)nx * p0;
   const long long step_cells = (long long)d * nx;
   bool ok = !__syncthreads_or(abort_local ? 1 : 0);
-  int m = 0;
-  for (; ok && m < M; ++m) {
-    const int p = p0 + d * m, par = m & 1;
-    const bool nin = row_in(m + 1);
-    const long long cell = x + (long long)nx * p;
-    // prefetch: flags two rows ahead, the Shakhov parameters of the next row
-    const unsigned mc2 = cflag(p + 2 * d), hm2 = hflag(p + 2 * d);
-    const float macn = (lane < kMac && col_in && nin) ? __ldg(A.mac + (cell + step_cells) * kMac + lane) : 0.f;
-    if (nin) {
-      if (mbar_wait(&full[(m + 1) % NST], ((m + 1) / NST) & 1)) waited = m + 1;
-      else abort_local = true;
-    }
-    // (1) the x faces of the next row, into the other buffer
-    if (m + 1 < M && !abort_local) publish(m + 1, mc1, hm1, par ^ 1);
-    // (2) update of the own cell at row p and its moment sums
-    const float *sp = stage + (m % NST) * C::STAGE;
-    float *sp1 = stage + ((m + 1) % NST) * C::STAGE;
-    if (!nin && col_in) {
-      // past the domain edge: the halo value of the own column, written into
-      // the unused slot of that row (each lane reads back only what it wrote)
-#pragma unroll
-      for (int g = 0; g < G; ++g) sts4(sp1 + so * KC2 + 128 * g + 4 * lane, halo4(hyd, x, 128 * g + 4 * lane));
-    }
-    const float *fb = fxb + par * C::FX;
-    const bool fluid = col_in && !(mc0 & kNotFluid) && !abort_local;
-    float acc[NM];
-#pragma unroll
-    for (int i = 0; i < NM; ++i) acc[i] = 0.f;
-    if (fluid) {
-      const float4 *pm = reinterpret_cast<const float4 *>(smac + (par * TX + warp) * kMac);
-      const float4 c0v = pm[0], c1v = pm[1], c2v = pm[2];
-      const float2 mU0 = dup(-c0v.y), mU1 = dup(-c0v.z);
-      const float2 nl2 = dup(-c1v.x * kLog2e);                        // -log2(e) / T
-      const float Tc = 2.f * c1v.y;                                    // T
-      const float2 pH = dup(-2.f * kLn2), pB = dup(-Tc * kLn2), mT = dup(-Tc);
-      const float2 hT = dup(c1v.y);                                    // T / 2
-      const float2 q0 = dup(c1v.z * c1v.w), q1 = dup(c1v.z * c2v.x);   // the Shakhov factor folded into q
-      const float2 dt2 = dup(c2v.z), pre2 = dup(c0v.x);
-      // the row body, in two copies: GEN = a ghost neighbour (links for the
-      // faces and the inflow), else the plain stencil
-      auto body = [&](auto gen) {
-        constexpr bool GEN = decltype(gen)::value;
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int o = 128 * g + 4 * lane, k = k0 + 64 * g + 2 * lane;
-        const float2 ax = lds2(scon + ((g * 3 + 0) * 32 + lane) * 2);
-        const float2 ay = lds2(scon + ((g * 3 + 1) * 32 + lane) * 2);
-        const float2 wk = lds2(scon + ((g * 3 + 2) * 32 + lane) * 2);
-        const float4 fc = lds4(sp + so * KC2 + o);
-        const float4 fnx = lds4(sp1 + so * KC2 + o);
-        const float4 Dn = sub4(fnx, fc);
-        const float4 fxo = lds4(fb + fx_own + o);
-        float4 fxi = lds4(fb + fx_in + o), fyi = P[g];
-        // y outflow face of this row (the inflow of the next)
-        float4 fyo;
-        if constexpr (!GEN) {
-          (void)k;
-          fyo = face4d(fc, D[g], Dn);
-        } else {
-          fyo = face4d(fc, (mc0 & guy) ? sub4(fc, link4(A, cell, duy, k)) : D[g],
-                       (mc0 & gdy) ? sub4(link4(A, cell, ddy, k), fc) : Dn);
-          // a ghost upwind neighbour: the mean of its link value and this cell (one-sided slope)
-          if (mc0 & gux) fxi = mean4(link4(A, cell, dux, k), fc);
-          if (mc0 & guy) fyi = mean4(link4(A, cell, duy, k), fc);
+  // the rows, in two copies: plain (no flags), and general
+  auto rows = [&](auto plain_tag) {
+    constexpr bool PL = decltype(plain_tag)::value;
+    for (int m = 0; ok && m < M; ++m) {
+      const int p = p0 + d * m, par = m & 1;
+      const bool nin = row_in(m + 1);
+      const long long cell = x + (long long)nx * p;
+      // prefetch: flags two rows ahead, the Shakhov parameters of the next row
+      const unsigned mc2 = PL ? 0u : cflag(p + 2 * d), hm2 = PL ? 0u : hflag(p + 2 * d);
+      const float macn = (lane < kMac && (PL || col_in) && nin) ? __ldg(A.mac + (cell + step_cells) * kMac + lane) : 0.f;
+      if (nin) {
+        if (mbar_wait(&full[(m + 1) % NST], ((m + 1) / NST) & 1)) waited = m + 1;
+        else abort_local = true;
+      }
+      // (1) the x faces of the next row, into the other buffer
+      if (m + 1 < M && !abort_local) publish(plain_tag, m + 1, mc1, hm1, par ^ 1);
+      // (2) update of the own cell at row p and its moment sums
+      const float *sp = stage + (m % NST) * C::STAGE;
+      float *sp1 = stage + ((m + 1) % NST) * C::STAGE;
+      if (!nin && (PL || col_in)) {
+        // past the domain edge: the halo value of the own column, written into
+        // the unused slot of that row (each lane reads back only what it wrote)
+  #pragma unroll
+        for (int g = 0; g < G; ++g) sts4(sp1 + so * KC2 + 128 * g + 4 * lane, halo4(hyd, x, 128 * g + 4 * lane));
+      }
+      const float *fb = fxb + par * C::FX;
+      const bool fluid = PL ? !abort_local : (col_in && !(mc0 & kNotFluid) && !abort_local);
+      float acc[NM];
+  #pragma unroll
+      for (int i = 0; i < NM; ++i) acc[i] = 0.f;
+      if (fluid) {
+        const float4 *pm = reinterpret_cast<const float4 *>(smac + (par * TX + warp) * kMac);
+        const float4 c0v = pm[0], c1v = pm[1], c2v = pm[2];
+        const float2 mU0 = dup(-c0v.y), mU1 = dup(-c0v.z);
+        const float2 nl2 = dup(-c1v.x * kLog2e);                        // -log2(e) / T
+        const float Tc = 2.f * c1v.y;                                    // T
+        const float2 pH = dup(-2.f * kLn2), pB = dup(-Tc * kLn2), mT = dup(-Tc);
+        const float2 hT = dup(c1v.y);                                    // T / 2
+        const float2 q0 = dup(c1v.z * c1v.w), q1 = dup(c1v.z * c2v.x);   // the Shakhov factor folded into q
+        const float2 dt2 = dup(c2v.z), pre2 = dup(c0v.x);
+        // the row body, in two copies: GEN = a ghost neighbour (links for the
+        // faces and the inflow), else the plain stencil
+        auto body = [&](auto gen) {
+          constexpr bool GEN = decltype(gen)::value;
+  #pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int o = 128 * g + 4 * lane, k = k0 + 64 * g + 2 * lane;
+          const float2 ax = lds2(scon + ((g * 3 + 0) * 32 + lane) * 2);
+          const float2 ay = lds2(scon + ((g * 3 + 1) * 32 + lane) * 2);
+          const float2 wk = lds2(scon + ((g * 3 + 2) * 32 + lane) * 2);
+          const float4 fc = lds4(sp + so * KC2 + o);
+          const float4 fnx = lds4(sp1 + so * KC2 + o);
+          const float4 Dn = sub4(fnx, fc);
+          const float4 fxo = lds4(fb + fx_own + o);
+          float4 fxi = lds4(fb + fx_in + o), fyi = P[g];
+          // y outflow face of this row (the inflow of the next)
+          float4 fyo;
+          if constexpr (!GEN) {
+            (void)k;
+            fyo = face4d(fc, D[g], Dn);
+          } else {
+            fyo = face4d(fc, (mc0 & guy) ? sub4(fc, link4(A, cell, duy, k)) : D[g],
+                         (mc0 & gdy) ? sub4(link4(A, cell, ddy, k), fc) : Dn);
+            // a ghost upwind neighbour: the mean of its link value and this cell (one-sided slope)
+            if (mc0 & gux) fxi = mean4(link4(A, cell, dux, k), fc);
+            if (mc0 & guy) fyi = mean4(link4(A, cell, duy, k), fc);
+          }
+          P[g] = fyo;
+          D[g] = Dn; // f(p + d) - f(p): the upwind difference of the next row
+          // reduced Shakhov equilibria of the two velocities (Sec. 4):
+          // H = e (1 + A c.q (2t - 4)), B = T/2 e (1 + A c.q (2t - 2)), t = c^2 / T
+          const float2 cx = __ffma2_rn(ax, sigx, mU0), cy = __ffma2_rn(ay, sigy, mU1);
+          const float2 c2 = __ffma2_rn(cx, cx, __fmul2_rn(cy, cy));
+          const float2 tn = __fmul2_rn(c2, nl2); // -t log2(e)
+          const float2 e = __fmul2_rn(pre2, make_float2(ex2(tn.x), ex2(tn.y)));
+          const float2 mm = __fmul2_rn(e, __ffma2_rn(cx, q0, __fmul2_rn(cy, q1)));
+          const float2 H = __ffma2_rn(mm, __ffma2_rn(tn, pH, dup(-4.f)), e);
+          const float2 B = __ffma2_rn(mm, __ffma2_rn(tn, pB, mT), __fmul2_rn(hT, e));
+          // forward Euler per velocity on (h, b): relaxation, then the flux differences
+          float2 n0 = __ffma2_rn(dt2, sub2(make_float2(H.x, B.x), lo2(fc)), lo2(fc));
+          float2 n1 = __ffma2_rn(dt2, sub2(make_float2(H.y, B.y), hi2(fc)), hi2(fc));
+          n0 = __ffma2_rn(dup(ax.x), sub2(lo2(fxi), lo2(fxo)), n0);
+          n1 = __ffma2_rn(dup(ax.y), sub2(hi2(fxi), hi2(fxo)), n1);
+          n0 = __ffma2_rn(dup(ay.x), sub2(lo2(fyi), lo2(fyo)), n0);
+          n1 = __ffma2_rn(dup(ay.y), sub2(hi2(fyi), hi2(fyo)), n1);
+          *reinterpret_cast<float4 *>(fn_cell + 128 * g) = cat4(n0, n1);
+          // moment sums about the stored bulk velocity (Eqs. moments1-3, reduced)
+          const float2 wh = __fmul2_rn(wk, make_float2(n0.x, n1.x));
+          const float2 e2 = __ffma2_rn(c2, wh, __fmul2_rn(wk, make_float2(n0.y, n1.y))); // w (c^2 h + b)
+          const float2 cxwh = __fmul2_rn(cx, wh);
+          acc_add(acc[0], wh);
+          acc_fma(acc[1], cx, wh);
+          acc_fma(acc[2], cy, wh);
+          acc_add(acc[3], e2);
+          acc_fma(acc[4], cx, cxwh);
+          acc_fma(acc[5], cy, cxwh);
+          acc_fma(acc[6], cy, __fmul2_rn(cy, wh));
+          acc_fma(acc[7], cx, e2);
+          acc_fma(acc[8], cy, e2);
         }
-        P[g] = fyo;
-        D[g] = Dn; // f(p + d) - f(p): the upwind difference of the next row
-        // reduced Shakhov equilibria of the two velocities (Sec. 4):
-        // H = e (1 + A c.q (2t - 4)), B = T/2 e (1 + A c.q (2t - 2)), t = c^2 / T
-        const float2 cx = __ffma2_rn(ax, sigx, mU0), cy = __ffma2_rn(ay, sigy, mU1);
-        const float2 c2 = __ffma2_rn(cx, cx, __fmul2_rn(cy, cy));
-        const float2 tn = __fmul2_rn(c2, nl2); // -t log2(e)
-        const float2 e = __fmul2_rn(pre2, make_float2(ex2(tn.x), ex2(tn.y)));
-        const float2 mm = __fmul2_rn(e, __ffma2_rn(cx, q0, __fmul2_rn(cy, q1)));
-        const float2 H = __ffma2_rn(mm, __ffma2_rn(tn, pH, dup(-4.f)), e);
-        const float2 B = __ffma2_rn(mm, __ffma2_rn(tn, pB, mT), __fmul2_rn(hT, e));
-        // forward Euler per velocity on (h, b): relaxation, then the flux differences
-        float2 n0 = __ffma2_rn(dt2, sub2(make_float2(H.x, B.x), lo2(fc)), lo2(fc));
-        float2 n1 = __ffma2_rn(dt2, sub2(make_float2(H.y, B.y), hi2(fc)), hi2(fc));
-        n0 = __ffma2_rn(dup(ax.x), sub2(lo2(fxi), lo2(fxo)), n0);
-        n1 = __ffma2_rn(dup(ax.y), sub2(hi2(fxi), hi2(fxo)), n1);
-        n0 = __ffma2_rn(dup(ay.x), sub2(lo2(fyi), lo2(fyo)), n0);
-        n1 = __ffma2_rn(dup(ay.y), sub2(hi2(fyi), hi2(fyo)), n1);
-        *reinterpret_cast<float4 *>(fn_cell + 128 * g) = cat4(n0, n1);
-        // moment sums about the stored bulk velocity (Eqs. moments1-3, reduced)
-        const float2 wh = __fmul2_rn(wk, make_float2(n0.x, n1.x));
-        const float2 e2 = __ffma2_rn(c2, wh, __fmul2_rn(wk, make_float2(n0.y, n1.y))); // w (c^2 h + b)
-        const float2 cxwh = __fmul2_rn(cx, wh);
-        acc_add(acc[0], wh);
-        acc_fma(acc[1], cx, wh);
-        acc_fma(acc[2], cy, wh);
-        acc_add(acc[3], e2);
-        acc_fma(acc[4], cx, cxwh);
-        acc_fma(acc[5], cy, cxwh);
-        acc_fma(acc[6], cy, __fmul2_rn(cy, wh));
-        acc_fma(acc[7], cx, e2);
-        acc_fma(acc[8], cy, e2);
+        };
+        if (!PL && (mc0 & 15u))
+          body(std::true_type{});
+        else
+          body(std::false_type{});
+      } else {
+  #pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int o = 128 * g + 4 * lane;
+          P[g] = col_in ? make_float4(0.f, 0.f, 0.f, 0.f) : lds4(sfinf + o);
+          D[g] = col_in ? sub4(lds4(sp1 + so * KC2 + o), lds4(sp + so * KC2 + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
-      };
-      if (mc0 & 15u)
-        body(std::true_type{});
-      else
-        body(std::false_type{});
-    } else {
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int o = 128 * g + 4 * lane;
-        P[g] = col_in ? make_float4(0.f, 0.f, 0.f, 0.f) : lds4(sfinf + o);
-        D[g] = col_in ? sub4(lds4(sp1 + so * KC2 + o), lds4(sp + so * KC2 + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      // (3) butterfly reduction of the sums over the 32 lanes: three rounds halve
+      //     the eight values a lane holds, two more finish the one it keeps; the
+      //     ninth sum is a plain xor tree
+      {
+        float v4[4];
+        const bool b16 = lane & 16;
+  #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float keep = b16 ? acc[4 + i] : acc[i];
+          const float send = b16 ? acc[i] : acc[4 + i];
+          v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+        float v2[2];
+        const bool b8 = lane & 8;
+  #pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const float keep = b8 ? v4[2 + i] : v4[i];
+          const float send = b8 ? v4[i] : v4[2 + i];
+          v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+        const bool b4 = lane & 4;
+        float v1 = (b4 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b4 ? v2[0] : v2[1], 4);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+        float s8 = acc[8];
+  #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
+        if (PL || col_in) {
+          if ((lane & 3) == 0) *part_cell = v1;
+          if (lane == 1) *part_cell = s8;
+        }
       }
-    }
-    // (3) butterfly reduction of the sums over the 32 lanes: three rounds halve
-    //     the eight values a lane holds, two more finish the one it keeps; the
-    //     ninth sum is a plain xor tree
-    {
-      float v4[4];
-      const bool b16 = lane & 16;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float keep = b16 ? acc[4 + i] : acc[i];
-        const float send = b16 ? acc[i] : acc[4 + i];
-        v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      // (4) advance: the flags and parameters of the next rows
+      if (lane < kMac) smac[((par ^ 1) * TX + warp) * kMac + lane] = macn;
+      mc0 = mc1;
+      mc1 = mc2;
+      hm1 = hm2;
+      fn_cell += step_cells * A.nvp * 2;
+      part_cell += step_cells;
+      // faces of the next row published, this row's buffer and stage m consumed
+      if (__syncthreads_or(abort_local ? 1 : 0)) {
+        ok = false;
+        break;
       }
-      float v2[2];
-      const bool b8 = lane & 8;
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const float keep = b8 ? v4[2 + i] : v4[i];
-        const float send = b8 ? v4[i] : v4[2 + i];
-        v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-      }
-      const bool b4 = lane & 4;
-      float v1 = (b4 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b4 ? v2[0] : v2[1], 4);
-      v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
-      v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
-      float s8 = acc[8];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
-      if (col_in) {
-        if ((lane & 3) == 0) *part_cell = v1;
-        if (lane == 1) *part_cell = s8;
+      // the stage of row index m + NST into the slot of stage m
+      if (threadIdx.x == 0 && m + NST <= M && row_in(m + NST)) {
+        fence_proxy_async();
+        issue(m + NST);
+        issued = m + NST;
       }
     }
-    // (4) advance: the flags and parameters of the next rows
-    if (lane < kMac) smac[((par ^ 1) * TX + warp) * kMac + lane] = macn;
-    mc0 = mc1;
-    mc1 = mc2;
-    hm1 = hm2;
-    fn_cell += step_cells * A.nvp * 2;
-    part_cell += step_cells;
-    // faces of the next row published, this row's buffer and stage m consumed
-    if (__syncthreads_or(abort_local ? 1 : 0)) {
-      ok = false;
-      break;
-    }
-    // the stage of row index m + NST into the slot of stage m
-    if (threadIdx.x == 0 && m + NST <= M && row_in(m + NST)) {
-      fence_proxy_async();
-      issue(m + NST);
-      issued = m + NST;
-    }
-  }
+  };
+  if (plain)
+    rows(std::true_type{});
+  else
+    rows(std::false_type{});
   if (!ok && threadIdx.x == 0) {
     atomicOr(A.err, kFlagTimeout);
     for (int q = waited + 1; q <= issued; ++q) mbar_wait(&full[q % NST], (q / NST) & 1);
