@@ -45,6 +45,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.h"
@@ -126,6 +127,11 @@ __device__ __forceinline__ float2 face2u(float2 f, float2 up, float2 dn) {
 __device__ __forceinline__ float4 face4(float4 f, float4 up, float4 dn) {
   return cat4(face2u(lo2(f), lo2(up), lo2(dn)), face2u(hi2(f), hi2(up), hi2(dn)));
 }
+// downwind face from the one-sided differences a = f - f_up and b = f_dn - f
+__device__ __forceinline__ float4 face4d(float4 f, float4 a, float4 b) {
+  return cat4(__fadd2_rn(lo2(f), vl_half2(lo2(a), lo2(b))), __fadd2_rn(hi2(f), vl_half2(hi2(a), hi2(b))));
+}
+__device__ __forceinline__ float4 sub4(float4 x, float4 y) { return cat4(sub2(lo2(x), lo2(y)), sub2(hi2(x), hi2(y))); }
 // moment accumulators of a lane: scalars (packed pairs of accumulators cost
 // thirteen more registers, which the block does not have)
 using ACC = float;
@@ -272,11 +278,12 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
   auto hflag = [&](int p) -> unsigned {
     return (h_in && p >= 0 && p < nz) ? A.cmask[hplane0 + (long long)p * nxy] : kNotFluid;
   };
-  // the z stencil of the own column: f at plane p - d and the z outflow face
-  // of plane p - d (the inflow of plane p), per group
-  float4 Rp[NG], P[NG];
+  // the z stencil of the own column, per group: the difference D = f(p) -
+  // f(p - d) of the current plane p and its upwind neighbour, and the z
+  // outflow face of plane p - d (the inflow of plane p)
+  float4 D[NG], P[NG];
   {
-    float4 Rpp[NG], Rc[NG];
+    float4 Rpp[NG], Rp[NG], Rc[NG];
     own(p0 - 2 * d, Rpp);
     own(p0 - d, Rp);
     own(p0, Rc);
@@ -289,6 +296,7 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
       if (!col_in || r < 0 || r >= nz) P[g] = lds4(sfinf + 128 * g + 4 * lane);
       else if (mr & kNotFluid) P[g] = make_float4(0.f, 0.f, 0.f, 0.f);
       else P[g] = face4(Rp[g], (mr & guz) ? link4(A, cr, duz, k) : Rpp[g], (mr & gdz) ? link4(A, cr, ddz, k) : Rc[g]);
+      D[g] = sub4(Rc[g], Rp[g]);
     }
   }
   if (lane < kMac)
@@ -296,13 +304,14 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
 
   // x and y outflow faces of plane index m (own cell and the warp's halo
   // cell) from stage m into face buffer b
-  auto publish = [&](int m, unsigned mcm, unsigned hmm, int b) {
+  auto publish = [&](auto plain, int m, unsigned mcm, unsigned hmm, int b) {
+    constexpr bool PL = decltype(plain)::value;
     const int p = p0 + d * m;
     const float *sp = stage + (m % NST) * C::STAGE;
     const long long cell = plane0 + (long long)p * nxy;
     float *fxo = fxb + b * C::FX + fx_own, *fyo = fyb + b * C::FY + fy_own;
-    const float *rc = col_in ? sp + so * KC + 4 * lane : sfinf + 4 * lane;
-    if (inner && !(mcm & (kNotFluid | 15u))) {
+    const float *rc = (PL || col_in) ? sp + so * KC + 4 * lane : sfinf + 4 * lane;
+    if (PL || (inner && !(mcm & (kNotFluid | 15u)))) {
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
         const int o = 128 * g + 4 * lane;
@@ -338,7 +347,7 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
     }
     if (hduty) {
       float4 out;
-      if (h_in && h_up_in && !(hmm & (kNotFluid | hgu | hgd))) {
+      if (PL || (h_in && h_up_in && !(hmm & (kNotFluid | hgu | hgd)))) {
         out = face4(lds4(sp + hc * KC + ho), lds4(sp + hup * KC + ho), lds4(sp + hdn * KC + ho));
       } else if (!h_in) {
         out = lds4(sfinf + ho);
@@ -356,6 +365,23 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
     }
   };
 
+  // A march is plain when its columns and the halo cells of the tile lie
+  // away from the x and y edges of the domain and none of their cells in its
+  // planes is special (not fluid, or a ghost neighbour: along the halo cell's
+  // axis for a halo cell); its planes then run without per-plane flags.
+  bool plain_local = inner;
+  if (plain_local)
+    for (int r = za + lane; r < zb; r += 32)
+      if (A.cmask[plane0 + (long long)r * nxy] & (kNotFluid | 63u)) plain_local = false;
+  if (hduty) {
+    bool hp = h_in && h_up_in;
+    if (hp)
+      for (int r = za + lane; r < zb; r += 32)
+        if (A.cmask[hplane0 + (long long)r * nxy] & (kNotFluid | hgu | hgd)) hp = false;
+    plain_local = plain_local && hp;
+  }
+  const bool plain = !__syncthreads_or(plain_local ? 0 : 1);
+
   bool abort_local = false;
   int waited = -1; // the last stage this thread waited for successfully
   unsigned mc0 = cflag(p0), mc1 = cflag(p0 + d);
@@ -363,35 +389,43 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
   if (M > 0) {
     if (mbar_wait(&full[0], 0)) waited = 0;
     else abort_local = true;
-    publish(0, mc0, hflag(p0), 0);
+    publish(std::false_type{}, 0, mc0, hflag(p0), 0);
   }
   float *fn_cell = A.fn + (size_t)(plane0 + (long long)p0 * nxy) * A.nvp + k0 + 4 * lane;
   float *part_cell =
       A.part + ((size_t)chunk * NM + ((lane >> 1) < NM ? (lane >> 1) : 0)) * A.ncell + plane0 + (long long)p0 * nxy;
   const long long step_cells = d * nxy;
   bool ok = !__syncthreads_or(abort_local ? 1 : 0);
-  int m = 0;
-  for (; ok && m < M; ++m) {
+  // the planes, in two copies: plain (no flags), and general
+  auto planes = [&](auto plain_tag) {
+    constexpr bool PL = decltype(plain_tag)::value;
+  for (int m = 0; ok && m < M; ++m) {
     const int p = p0 + d * m, par = m & 1;
     const bool nin = plane_in(m + 1);
     const long long cell = plane0 + (long long)p * nxy;
     // prefetch: flags two planes ahead, the Shakhov parameters of the next plane
-    const unsigned mc2 = cflag(p + 2 * d), hm2 = hflag(p + 2 * d);
-    const float macn = (lane < kMac && col_in && nin) ? __ldg(A.mac + (cell + d * nxy) * kMac + lane) : 0.f;
+    const unsigned mc2 = PL ? 0u : cflag(p + 2 * d), hm2 = PL ? 0u : hflag(p + 2 * d);
+    const float macn = (lane < kMac && (PL || col_in) && nin) ? __ldg(A.mac + (cell + d * nxy) * kMac + lane) : 0.f;
     if (nin) {
       if (mbar_wait(&full[(m + 1) % NST], ((m + 1) / NST) & 1)) waited = m + 1;
       else abort_local = true;
     }
     // (1) the faces of the next plane, into the other buffer
-    if (m + 1 < M && !abort_local) publish(m + 1, mc1, hm1, par ^ 1);
+    if (m + 1 < M && !abort_local) publish(plain_tag, m + 1, mc1, hm1, par ^ 1);
     // (2) update of the own cell at plane p and its moment sums (13 independent
     // sums: the sum of w c^2 f is the trace of the second moments)
     const float *sp = stage + (m % NST) * C::STAGE;
-    const float *sp1 = stage + ((m + 1) % NST) * C::STAGE;
-    const float *rc = col_in ? sp + so * KC + 4 * lane : sfinf + 4 * lane;
-    const float *rn = (nin && col_in) ? sp1 + so * KC + 4 * lane : sfinf + 4 * lane;
+    float *sp1 = stage + ((m + 1) % NST) * C::STAGE;
+    const float *rc = (PL || col_in) ? sp + so * KC + 4 * lane : sfinf + 4 * lane;
+    const float *rn = (PL || col_in) ? sp1 + so * KC + 4 * lane : sfinf + 4 * lane;
+    if (!nin && (PL || col_in)) {
+      // past the domain edge: the free stream, written into the unused slot
+      // of that plane (each lane reads back only what it wrote)
+#pragma unroll
+      for (int g = 0; g < NG; ++g) sts4(sp1 + so * KC + 128 * g + 4 * lane, lds4(sfinf + 128 * g + 4 * lane));
+    }
     const float *fxo_b = fxb + par * C::FX, *fyo_b = fyb + par * C::FY;
-    const bool fluid = col_in && !(mc0 & kNotFluid) && !abort_local;
+    const bool fluid = PL ? !abort_local : (col_in && !(mc0 & kNotFluid) && !abort_local);
     ACC acc[13];
 #pragma unroll
     for (int i = 0; i < 13; ++i) acc[i] = ACC{};
@@ -404,7 +438,10 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
       const float2 q0 = dup(c1v.z * c1v.w), q1 = dup(c1v.z * c2v.x), q2 = dup(c1v.z * c2v.y);
       const float2 dt2 = dup(c2v.z);
       const float2 pre2 = dup(c0v.x);
-      const bool ghosty = (mc0 & 63u) != 0;
+      // the plane body, in two copies: GEN = a ghost neighbour (links for
+      // the faces and the inflow), else the plain stencil
+      auto body = [&](auto gen) {
+        constexpr bool GEN = decltype(gen)::value;
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
         const int o = 128 * g + 4 * lane;
@@ -413,23 +450,23 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
         const float4 az4 = lds4(scon + ((g * 4 + 2) * 32 + lane) * 4);
         const float4 w4 = lds4(scon + ((g * 4 + 3) * 32 + lane) * 4);
         const float4 fc = lds4(rc + 128 * g), fnx = lds4(rn + 128 * g);
+        const float4 Dn = sub4(fnx, fc);
         const float4 fxo = lds4(fxo_b + fx_own + o), fyo = lds4(fyo_b + fy_own + o);
         float4 fxi = lds4(fxo_b + fx_in + o), fyi = lds4(fyo_b + fy_in + o), fzi = P[g];
         // z outflow face of this plane (the inflow of the next)
         float4 fzo;
-        if (!(mc0 & (guz | gdz))) {
-          fzo = face4(fc, Rp[g], fnx);
+        if constexpr (!GEN) {
+          fzo = face4d(fc, D[g], Dn);
         } else {
-          fzo = face4(fc, (mc0 & guz) ? link4(A, cell, duz, k0 + o) : Rp[g],
-                      (mc0 & gdz) ? link4(A, cell, ddz, k0 + o) : fnx);
-        }
-        if (ghosty) { // a ghost upwind neighbour: the mean of its link value and this cell (one-sided slope)
+          fzo = face4d(fc, (mc0 & guz) ? sub4(fc, link4(A, cell, duz, k0 + o)) : D[g],
+                       (mc0 & gdz) ? sub4(link4(A, cell, ddz, k0 + o), fc) : Dn);
+          // a ghost upwind neighbour: the mean of its link value and this cell (one-sided slope)
           if (mc0 & gux) fxi = mean4(link4(A, cell, dux, k0 + o), fc);
           if (mc0 & guy) fyi = mean4(link4(A, cell, duy, k0 + o), fc);
           if (mc0 & guz) fzi = mean4(link4(A, cell, duz, k0 + o), fc);
         }
         P[g] = fzo;
-        Rp[g] = fc; // f at plane p: the z upwind value of the next plane
+        D[g] = Dn; // f(p + d) - f(p): the upwind difference of the next plane
         float2 out[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -469,11 +506,16 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
         }
         *reinterpret_cast<float4 *>(fn_cell + 128 * g) = cat4(out[0], out[1]);
       }
+      };
+      if (!PL && (mc0 & 63u))
+        body(std::true_type{});
+      else
+        body(std::false_type{});
     } else {
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
         P[g] = col_in ? make_float4(0.f, 0.f, 0.f, 0.f) : lds4(sfinf + 128 * g + 4 * lane);
-        Rp[g] = lds4(rc + 128 * g);
+        D[g] = col_in ? sub4(lds4(rn + 128 * g), lds4(rc + 128 * g)) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     // (3) butterfly of the 16 (14 used) sums over the 32 lanes, in the order of
@@ -514,7 +556,7 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
       float v1 = (b2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? v2[0] : v2[1], 2);
       v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
       // lane l holds sum index 8 b4(l) + 4 b3(l) + 2 b2(l) + b1(l) = l >> 1
-      if (col_in && (lane & 1) == 0 && (lane >> 1) < NM) *part_cell = v1;
+      if ((PL || col_in) && (lane & 1) == 0 && (lane >> 1) < NM) *part_cell = v1;
     }
     // (4) advance: the flags and parameters of the next planes
     if (lane < kMac) smac[((par ^ 1) * NW + warp) * kMac + lane] = macn;
@@ -535,6 +577,11 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
       issued = m + NST;
     }
   }
+  };
+  if (plain)
+    planes(std::true_type{});
+  else
+    planes(std::false_type{});
   if (!ok && threadIdx.x == 0) {
     atomicOr(A.err, kFlagTimeout);
     for (int q = waited + 1; q <= issued; ++q) mbar_wait(&full[q % NST], (q / NST) & 1);
