@@ -184,7 +184,9 @@ void one_step(ibdvm_batch *b, int p) {
   {
     BTimed t(b, kKSweep);
     bcheck(b, tma_batch_launch(b->st, p, b->stream), "batched sweep kernel");
-    b->kernel_launches[kKSweep] += b->st.nitems ? 1 : 0;
+    int nl = 0; // 2D: one launch per chunk width present; 3D: one
+    for (int c = 0; c < 3; ++c) nl += (b->st.cls_off[c + 1] > b->st.cls_off[c]) ? 1 : 0;
+    b->kernel_launches[kKSweep] += (b->st.dim == 3) ? (b->st.nitems ? 1 : 0) : nl;
   }
   {
     BTimed t(b, kKMoments);

@@ -189,15 +189,19 @@ cudaError_t group_ghost(const GroupTables &t, int par, cudaStream_t s);
 cudaError_t group_forces(const GroupTables &t, int par, cudaStream_t s);
 cudaError_t group_finalize(const GroupTables &t, int par, cudaStream_t s);
 
-// The batched TMA sweep of 2D FP32 members (sweep_tma.cu): one persistent
-// launch over a packed work list of (member, column strip, velocity chunk,
-// row range) items.  kpt[m] = 2 or 4 velocities per lane for member m; rows =
-// target rows per item (0: whole columns).
+// The batched TMA sweep of 2D FP32 members (sweep_tma.cu): persistent
+// launches over a packed work list of (member, column strip, velocity chunk,
+// row range) items, one per chunk width of the members' layouts.  kpt is not
+// used (the chunk is that of each member's layout); rows = target rows per
+// item (0: whole columns).
 struct SweepTables {
   void *args = nullptr, *tmaps = nullptr, *items = nullptr; // [ncase][2], [ncase][2], [nitems]
-  int *next = nullptr; // work counter
+  int *next = nullptr; // work counters (2D: one per class)
   int nitems = 0, grid = 0, dim = 2;
-  int ksel = 0;        // 2D: velocities per lane of every item (4 or 2), 0 for a mix
+  int ksel = 0;        // 3D: velocities per lane of every item (8 or 4), 0 for a mix
+  // 2D: the items grouped by velocities per lane (6, 4, 2), one persistent
+  // launch per class: items [cls_off[c], cls_off[c + 1]) on cls_grid[c] blocks
+  int cls_off[4] = {0, 0, 0, 0}, cls_grid[3] = {0, 0, 0};
 };
 bool tma_batch_member_ok(const ibdvm_ctx *ctx);
 int tma_batch_kpt_max(const ibdvm_ctx *ctx);

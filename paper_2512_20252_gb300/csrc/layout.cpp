@@ -34,15 +34,23 @@ int orthant_layout(const Geom &G, std::vector<int> &kst, int &nvp) {
     for (const auto &v : grp) n += (static_cast<long long>(v.size()) + kc - 1) / kc * kc;
     return n;
   };
-  int kc;
-  if (D == 3) {
-    // 256-velocity chunks unless 128 wastes clearly less padding
-    kc = (padded(256) <= padded(128) + padded(128) / 32) ? 256 : 128;
-  } else {
-    // the chunk of least padding among 192, 128 and 64 (the larger on a tie)
-    kc = 192;
-    for (int c : {128, 64})
-      if (padded(c) < padded(kc)) kc = c;
+  // The chunk of least sweep time: padded velocities x the sweep's time per
+  // padded velocity at that chunk width, relative to the widest (measured on
+  // GB300: a lane's per-row work is shared by fewer velocities in narrower
+  // chunks).  2D: 192, 128, 64 velocities at 1.00, 1.12, 1.53; 3D: 256, 128
+  // at 1.00, 1.32.  The wider chunk on a tie.
+  static const int kc2[3] = {192, 128, 64}, w2[3] = {100, 112, 153};
+  static const int kc3[2] = {256, 128}, w3[2] = {100, 132};
+  const int nc = (D == 3) ? 2 : 3;
+  const int *kcs = (D == 3) ? kc3 : kc2, *ws = (D == 3) ? w3 : w2;
+  int kc = kcs[0];
+  long long best = padded(kcs[0]) * ws[0];
+  for (int i = 1; i < nc; ++i) {
+    const long long c = padded(kcs[i]) * ws[i];
+    if (c < best) {
+      best = c;
+      kc = kcs[i];
+    }
   }
   kst.assign(G.nv, 0);
   int pos = 0;

@@ -43,6 +43,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <type_traits>
@@ -236,12 +237,15 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
     sts4(scon + ((g * 4 + 3) * 32 + l) * 4, make_float4(v0.w, v1.w, v2.w, v3.w));
   }
   for (int i = threadIdx.x; i < KC; i += NTHREADS) sfinf[i] = A.finf[k0 + i];
+  __shared__ int s_seg[2]; // first and last special row (march indices)
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       if (reinit) mbar_inval(&full[s]);
       mbar_init(&full[s], 1);
     }
     fence_mbar_init();
+    s_seg[0] = INT_MAX;
+    s_seg[1] = -1;
   }
   __syncthreads();
   const int ys_pair = (sy > 0) ? y0 - 2 : y0 + TY, ys_single = (sy > 0) ? y0 + TY : y0 - 1;
@@ -365,22 +369,37 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
     }
   };
 
-  // A march is plain when its columns and the halo cells of the tile lie
-  // away from the x and y edges of the domain and none of their cells in its
-  // planes is special (not fluid, or a ghost neighbour: along the halo cell's
-  // axis for a halo cell); its planes then run without per-plane flags.
-  bool plain_local = inner;
-  if (plain_local)
-    for (int r = za + lane; r < zb; r += 32)
-      if (A.cmask[plane0 + (long long)r * nxy] & (kNotFluid | 63u)) plain_local = false;
-  if (hduty) {
-    bool hp = h_in && h_up_in;
-    if (hp)
-      for (int r = za + lane; r < zb; r += 32)
-        if (A.cmask[hplane0 + (long long)r * nxy] & (kNotFluid | hgu | hgd)) hp = false;
-    plain_local = plain_local && hp;
+  // Special planes: a cell of the tile's columns that is not fluid or has a
+  // ghost neighbour (along its axis for a halo cell); every plane when a
+  // column or halo cell lies at an x or y edge of the domain.  Planes from
+  // the one before the first special plane to the last run the general copy
+  // of the plane body, the others the plain one (no per-plane flags).
+  {
+    int lo = INT_MAX, hi = -1;
+    const bool edge = !inner || (hduty && !(h_in && h_up_in));
+    if (edge) {
+      lo = 0;
+      hi = M - 1;
+    } else {
+      for (int r = za + lane; r < zb; r += 32) {
+        unsigned fl = A.cmask[plane0 + (long long)r * nxy] & (kNotFluid | 63u);
+        if (hduty) fl |= A.cmask[hplane0 + (long long)r * nxy] & (kNotFluid | hgu | hgd);
+        if (fl) {
+          const int mr = (r - p0) * d;
+          lo = min(lo, mr);
+          hi = max(hi, mr);
+        }
+      }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0 && hi >= 0) {
+      atomicMin(&s_seg[0], lo);
+      atomicMax(&s_seg[1], hi);
+    }
   }
-  const bool plain = !__syncthreads_or(plain_local ? 0 : 1);
+  __syncthreads();
+  const int gs = (s_seg[1] >= 0) ? max(0, s_seg[0] - 1) : M, ge = (s_seg[1] >= 0) ? s_seg[1] + 1 : M;
 
   bool abort_local = false;
   int waited = -1; // the last stage this thread waited for successfully
@@ -396,10 +415,15 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
       A.part + ((size_t)chunk * NM + ((lane >> 1) < NM ? (lane >> 1) : 0)) * A.ncell + plane0 + (long long)p0 * nxy;
   const long long step_cells = d * nxy;
   bool ok = !__syncthreads_or(abort_local ? 1 : 0);
-  // the planes, in two copies: plain (no flags), and general
-  auto planes = [&](auto plain_tag) {
+  // planes [mb, me), in two copies: plain (no flags), and general
+  auto planes = [&](auto plain_tag, int mb, int me) {
     constexpr bool PL = decltype(plain_tag)::value;
-  for (int m = 0; ok && m < M; ++m) {
+    if (!PL && mb < me) { // the flags of the segment's first planes
+      mc0 = cflag(p0 + d * mb);
+      mc1 = cflag(p0 + d * (mb + 1));
+      hm1 = hflag(p0 + d * (mb + 1));
+    }
+  for (int m = mb; ok && m < me; ++m) {
     const int p = p0 + d * m, par = m & 1;
     const bool nin = plane_in(m + 1);
     const long long cell = plane0 + (long long)p * nxy;
@@ -578,10 +602,9 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
     }
   }
   };
-  if (plain)
-    planes(std::true_type{});
-  else
-    planes(std::false_type{});
+  planes(std::true_type{}, 0, gs);
+  planes(std::false_type{}, gs, ge);
+  planes(std::true_type{}, ge, M);
   if (!ok && threadIdx.x == 0) {
     atomicOr(A.err, kFlagTimeout);
     for (int q = waited + 1; q <= issued; ++q) mbar_wait(&full[q % NST], (q / NST) & 1);

@@ -45,6 +45,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <type_traits>
 #include <vector>
@@ -234,12 +235,15 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
     *reinterpret_cast<float2 *>(scon + ((g * 3 + 2) * 32 + l) * 2) = make_float2(v0.z, v1.z);
   }
   for (int i = threadIdx.x; i < KC2; i += NTHREADS) sfinf[i] = A.finf[2 * k0 + i];
+  __shared__ int s_seg[2]; // first and last special row (march indices)
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       if (reinit) mbar_inval(&full[s]);
       mbar_init(&full[s], 1);
     }
     fence_mbar_init();
+    s_seg[0] = INT_MAX;
+    s_seg[1] = -1;
   }
   __syncthreads();
   auto issue = [&](int m) {
@@ -345,22 +349,38 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
     }
   };
 
-  // A march is plain when its columns and the upwind halo column lie away
-  // from the x edges of the domain and none of their cells in its rows is
-  // special (not fluid, or a ghost neighbour: along x for the halo column);
-  // its rows then run without per-row flags.
-  bool plain_local = inner;
-  if (plain_local)
-    for (int r = ya + lane; r < yb; r += 32)
-      if (A.cmask[x + (long long)nx * r] & (kNotFluid | 15u)) plain_local = false;
-  if (warp == 0) {
-    bool hp = hx >= 0 && hx < nx && h_up_in;
-    if (hp)
-      for (int r = ya + lane; r < yb; r += 32)
-        if (A.cmask[hx + (long long)nx * r] & (kNotFluid | 3u)) hp = false;
-    plain_local = plain_local && hp;
+  // Special rows: a cell of the block's columns that is not fluid or has a
+  // ghost neighbour (along x for the upwind halo column); every row when a
+  // column lies at an x edge of the domain.  Rows from the one before the
+  // first special row to the last run the general copy of the row body, the
+  // others the plain one (no per-row flags).
+  {
+    int lo = INT_MAX, hi = -1;
+    bool edge = !inner;
+    if (warp == 0) edge = edge || !(hx >= 0 && hx < nx && h_up_in);
+    if (edge) {
+      lo = 0;
+      hi = M - 1;
+    } else {
+      for (int r = ya + lane; r < yb; r += 32) {
+        unsigned fl = A.cmask[x + (long long)nx * r] & (kNotFluid | 15u);
+        if (warp == 0) fl |= A.cmask[hx + (long long)nx * r] & (kNotFluid | 3u);
+        if (fl) {
+          const int mr = (r - p0) * d;
+          lo = min(lo, mr);
+          hi = max(hi, mr);
+        }
+      }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0 && hi >= 0) {
+      atomicMin(&s_seg[0], lo);
+      atomicMax(&s_seg[1], hi);
+    }
   }
-  const bool plain = !__syncthreads_or(plain_local ? 0 : 1);
+  __syncthreads();
+  const int gs = (s_seg[1] >= 0) ? max(0, s_seg[0] - 1) : M, ge = (s_seg[1] >= 0) ? s_seg[1] + 1 : M;
 
   bool abort_local = false;
   int waited = -1; // the last stage this thread waited for successfully
@@ -377,10 +397,15 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
   float *part_cell = A.part + ((size_t)chunk * NM + sidx) * A.ncell + x + (long long)nx * p0;
   const long long step_cells = (long long)d * nx;
   bool ok = !__syncthreads_or(abort_local ? 1 : 0);
-  // the rows, in two copies: plain (no flags), and general
-  auto rows = [&](auto plain_tag) {
+  // rows [mb, me), in two copies: plain (no flags), and general
+  auto rows = [&](auto plain_tag, int mb, int me) {
     constexpr bool PL = decltype(plain_tag)::value;
-    for (int m = 0; ok && m < M; ++m) {
+    if (!PL && mb < me) { // the flags of the segment's first rows
+      mc0 = cflag(p0 + d * mb);
+      mc1 = cflag(p0 + d * (mb + 1));
+      hm1 = hflag(p0 + d * (mb + 1));
+    }
+    for (int m = mb; ok && m < me; ++m) {
       const int p = p0 + d * m, par = m & 1;
       const bool nin = row_in(m + 1);
       const long long cell = x + (long long)nx * p;
@@ -542,10 +567,9 @@ __device__ __forceinline__ bool march2o(const Oct2Args &A, const CUtensorMap *tm
       }
     }
   };
-  if (plain)
-    rows(std::true_type{});
-  else
-    rows(std::false_type{});
+  rows(std::true_type{}, 0, gs);
+  rows(std::false_type{}, gs, ge);
+  rows(std::true_type{}, ge, M);
   if (!ok && threadIdx.x == 0) {
     atomicOr(A.err, kFlagTimeout);
     for (int q = waited + 1; q <= issued; ++q) mbar_wait(&full[q % NST], (q / NST) & 1);
@@ -572,10 +596,10 @@ struct WorkItem {
 };
 
 // The batched sweep: a persistent grid whose blocks take work items in order
-// from a shared counter (items sorted by decreasing size).  Member c at step
-// parity par uses args[2 c + par] and tmaps[2 c + par].  VSEL = 6, 4 or 2 when
-// every item takes that many velocities per lane, 0 for a mix.
-template <int VSEL>
+// from a shared counter (items sorted by decreasing size), all of VPL
+// velocities per lane.  Member c at step parity par uses args[2 c + par] and
+// tmaps[2 c + par].
+template <int VPL>
 __global__ void __launch_bounds__(NTHREADS, 2)
     sweep2d_tma_batch_kernel(const Oct2Args *__restrict__ args, const CUtensorMap *__restrict__ tmaps,
                              const WorkItem *__restrict__ items, int nitems, int *__restrict__ next, int par) {
@@ -592,13 +616,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     if (threadIdx.x == 0) sA = args[2 * it.cas + par];
     __syncthreads();
     const CUtensorMap *tm = tmaps + 2 * it.cas + par;
-    bool ok;
-    if constexpr (VSEL != 0)
-      ok = march2o<VSEL>(sA, tm, it.x0, it.chunk, it.ya, it.yb, smem_raw, reinit);
-    else
-      ok = (it.vpl == 6) ? march2o<6>(sA, tm, it.x0, it.chunk, it.ya, it.yb, smem_raw, reinit)
-           : (it.vpl == 4) ? march2o<4>(sA, tm, it.x0, it.chunk, it.ya, it.yb, smem_raw, reinit)
-                           : march2o<2>(sA, tm, it.x0, it.chunk, it.ya, it.yb, smem_raw, reinit);
+    const bool ok = march2o<VPL>(sA, tm, it.x0, it.chunk, it.ya, it.yb, smem_raw, reinit);
     if (!ok) break; // uniform: the abort vote is block-wide
     reinit = true;
     __syncthreads(); // the item's shared memory and arguments are released
@@ -657,10 +675,7 @@ Oct2Args oct2_args(const ibdvm_ctx *ctx, int cur, int *err) {
 }
 
 template <int VPL> cudaError_t set_smem() {
-  cudaError_t e = cudaFuncSetAttribute(sweep2d_tma_kernel<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Cfg<VPL>::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sweep2d_tma_batch_kernel<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(sweep2d_tma_kernel<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Cfg<VPL>::SMEM);
 }
 
@@ -732,12 +747,10 @@ cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::ve
   std::vector<Oct2Args> args(2 * n);
   std::vector<CUtensorMap> maps(2 * n);
   std::vector<WorkItem> items;
-  int vsel = -1;
   for (int i = 0; i < n; ++i) {
     const ibdvm_ctx *ctx = cases[i];
     if (ctx->oct_kc <= 0) return cudaErrorInvalidValue;
     const int vpl = ctx->oct_kc / 32;
-    vsel = (vsel < 0 || vsel == vpl) ? vpl : 0;
     for (int p = 0; p < 2; ++p) {
       const int cur = ctx->cur ^ p;
       args[2 * i + p] = oct2_args(ctx, cur, flags + i);
@@ -761,10 +774,18 @@ cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::ve
           items.push_back(it);
         }
   }
-  // largest items first, so the last items to start are the short ones
+  // grouped by velocities per lane (6, 4, 2), the largest items of a group
+  // first, so the last items to start are the short ones
   std::stable_sort(items.begin(), items.end(), [](const WorkItem &a, const WorkItem &b) {
-    return (long long)(a.yb - a.ya) * a.vpl > (long long)(b.yb - b.ya) * b.vpl;
+    if (a.vpl != b.vpl) return a.vpl > b.vpl;
+    return (a.yb - a.ya) > (b.yb - b.ya);
   });
+  static const int kVpl[3] = {6, 4, 2};
+  for (int c = 0, i = 0; c < 3; ++c) {
+    t.cls_off[c] = i;
+    while (i < static_cast<int>(items.size()) && items[i].vpl == kVpl[c]) ++i;
+    t.cls_off[c + 1] = i;
+  }
   cudaError_t e;
   auto up = [&](const void *h, size_t bytes, void *&d) -> cudaError_t {
     cudaError_t r = cudaMalloc(&d, std::max<size_t>(bytes, 16));
@@ -775,41 +796,50 @@ cudaError_t tma_batch_build(const std::vector<ibdvm_ctx *> &cases, const std::ve
   if ((e = up(maps.data(), maps.size() * sizeof(CUtensorMap), t.tmaps)) != cudaSuccess) return e;
   if ((e = up(items.data(), items.size() * sizeof(WorkItem), t.items)) != cudaSuccess) return e;
   void *nx = nullptr;
-  if ((e = cudaMalloc(&nx, sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&nx, 3 * sizeof(int))) != cudaSuccess) return e;
   t.next = static_cast<int *>(nx);
   t.nitems = static_cast<int>(items.size());
-  t.ksel = std::max(vsel, 0);
-  const void *fn = (t.ksel == 6)   ? (const void *)sweep2d_tma_batch_kernel<6>
-                   : (t.ksel == 4) ? (const void *)sweep2d_tma_batch_kernel<4>
-                   : (t.ksel == 2) ? (const void *)sweep2d_tma_batch_kernel<2>
-                                   : (const void *)sweep2d_tma_batch_kernel<0>;
-  const int smem = (t.ksel == 4) ? (int)Cfg<4>::SMEM : (t.ksel == 2) ? (int)Cfg<2>::SMEM : (int)Cfg<6>::SMEM;
-  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-  int dev = 0, nsm = 0, per_sm = 0;
+  int dev = 0, nsm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NTHREADS, smem)) != cudaSuccess) return e;
-  t.grid = std::max(1, std::min(t.nitems, nsm * std::max(per_sm, 1)));
+  t.grid = 0;
+  for (int c = 0; c < 3; ++c) {
+    const int n = t.cls_off[c + 1] - t.cls_off[c];
+    t.cls_grid[c] = 0;
+    if (n == 0) continue;
+    const void *fn = (c == 0)   ? (const void *)sweep2d_tma_batch_kernel<6>
+                     : (c == 1) ? (const void *)sweep2d_tma_batch_kernel<4>
+                                : (const void *)sweep2d_tma_batch_kernel<2>;
+    const int smem = (c == 0) ? (int)Cfg<6>::SMEM : (c == 1) ? (int)Cfg<4>::SMEM : (int)Cfg<2>::SMEM;
+    int per_sm = 0;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NTHREADS, smem)) != cudaSuccess) return e;
+    t.cls_grid[c] = std::max(1, std::min(n, nsm * std::max(per_sm, 1)));
+    t.grid = std::max(t.grid, t.cls_grid[c]);
+  }
   return cudaStreamSynchronize(s); // the host tables go out of scope
 }
 
 cudaError_t tma_batch_launch(const SweepTables &t, int par, cudaStream_t s) {
   if (t.dim == 3) return tma3_batch_launch(t, par, s);
   if (t.nitems == 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(t.next, 0, sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(t.next, 0, 3 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   const Oct2Args *a = static_cast<const Oct2Args *>(t.args);
   const CUtensorMap *m = static_cast<const CUtensorMap *>(t.tmaps);
   const WorkItem *it = static_cast<const WorkItem *>(t.items);
-  if (t.ksel == 6)
-    sweep2d_tma_batch_kernel<6><<<t.grid, NTHREADS, Cfg<6>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
-  else if (t.ksel == 4)
-    sweep2d_tma_batch_kernel<4><<<t.grid, NTHREADS, Cfg<4>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
-  else if (t.ksel == 2)
-    sweep2d_tma_batch_kernel<2><<<t.grid, NTHREADS, Cfg<2>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
-  else
-    sweep2d_tma_batch_kernel<0><<<t.grid, NTHREADS, Cfg<6>::SMEM, s>>>(a, m, it, t.nitems, t.next, par);
-  return cudaGetLastError();
+  for (int c = 0; c < 3; ++c) {
+    const int off = t.cls_off[c], n = t.cls_off[c + 1] - off;
+    if (n == 0) continue;
+    if (c == 0)
+      sweep2d_tma_batch_kernel<6><<<t.cls_grid[c], NTHREADS, Cfg<6>::SMEM, s>>>(a, m, it + off, n, t.next + c, par);
+    else if (c == 1)
+      sweep2d_tma_batch_kernel<4><<<t.cls_grid[c], NTHREADS, Cfg<4>::SMEM, s>>>(a, m, it + off, n, t.next + c, par);
+    else
+      sweep2d_tma_batch_kernel<2><<<t.cls_grid[c], NTHREADS, Cfg<2>::SMEM, s>>>(a, m, it + off, n, t.next + c, par);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 } // namespace ibdvm
