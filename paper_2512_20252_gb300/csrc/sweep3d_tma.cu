@@ -250,9 +250,9 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
   __syncthreads();
   const int ys_pair = (sy > 0) ? y0 - 2 : y0 + TY, ys_single = (sy > 0) ? y0 + TY : y0 - 1;
   const int yr_pair = (sy > 0) ? 0 : 1, yr_single = (sy > 0) ? 2 : 0;
-  auto issue = [&](int m) {
-    float *dst = stage + (m % NST) * C::STAGE;
-    uint64_t *bar = &full[m % NST];
+  auto issue = [&](int m, int st) { // stage m into slot st = m mod NST
+    float *dst = stage + st * C::STAGE;
+    uint64_t *bar = &full[st];
     const int z = p0 + d * m;
     mbar_expect_tx(bar, C::STAGE * 4);
     tma_box(dst, tmx, k0, x0 - ox, y0, z, bar);
@@ -262,7 +262,7 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
   int issued = -1; // the last stage issued (thread 0)
   if (threadIdx.x == 0 && M > 0)
     for (int m = 0; m < NST && m <= M && plane_in(m); ++m) {
-      issue(m);
+      issue(m, m);
       issued = m;
     }
 
@@ -308,10 +308,10 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
 
   // x and y outflow faces of plane index m (own cell and the warp's halo
   // cell) from stage m into face buffer b
-  auto publish = [&](auto plain, int m, unsigned mcm, unsigned hmm, int b) {
+  auto publish = [&](auto plain, int m, int st, unsigned mcm, unsigned hmm, int b) { // st: slot of stage m
     constexpr bool PL = decltype(plain)::value;
     const int p = p0 + d * m;
-    const float *sp = stage + (m % NST) * C::STAGE;
+    const float *sp = stage + st * C::STAGE;
     const long long cell = plane0 + (long long)p * nxy;
     float *fxo = fxb + b * C::FX + fx_own, *fyo = fyb + b * C::FY + fy_own;
     const float *rc = (PL || col_in) ? sp + so * KC + 4 * lane : sfinf + 4 * lane;
@@ -408,7 +408,7 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
   if (M > 0) {
     if (mbar_wait(&full[0], 0)) waited = 0;
     else abort_local = true;
-    publish(std::false_type{}, 0, mc0, hflag(p0), 0);
+    publish(std::false_type{}, 0, 0, mc0, hflag(p0), 0);
   }
   float *fn_cell = A.fn + (size_t)(plane0 + (long long)p0 * nxy) * A.nvp + k0 + 4 * lane;
   float *part_cell =
@@ -423,6 +423,9 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
       mc1 = cflag(p0 + d * (mb + 1));
       hm1 = hflag(p0 + d * (mb + 1));
     }
+  // stage slots of planes m and m + 1, and the parity of the latter
+  int st0 = mb % NST, st1 = (mb + 1) % NST;
+  unsigned ph1 = ((mb + 1) / NST) & 1;
   for (int m = mb; ok && m < me; ++m) {
     const int p = p0 + d * m, par = m & 1;
     const bool nin = plane_in(m + 1);
@@ -431,15 +434,15 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
     const unsigned mc2 = PL ? 0u : cflag(p + 2 * d), hm2 = PL ? 0u : hflag(p + 2 * d);
     const float macn = (lane < kMac && (PL || col_in) && nin) ? __ldg(A.mac + (cell + d * nxy) * kMac + lane) : 0.f;
     if (nin) {
-      if (mbar_wait(&full[(m + 1) % NST], ((m + 1) / NST) & 1)) waited = m + 1;
+      if (mbar_wait(&full[st1], ph1)) waited = m + 1;
       else abort_local = true;
     }
     // (1) the faces of the next plane, into the other buffer
-    if (m + 1 < M && !abort_local) publish(plain_tag, m + 1, mc1, hm1, par ^ 1);
+    if (m + 1 < M && !abort_local) publish(plain_tag, m + 1, st1, mc1, hm1, par ^ 1);
     // (2) update of the own cell at plane p and its moment sums (13 independent
     // sums: the sum of w c^2 f is the trace of the second moments)
-    const float *sp = stage + (m % NST) * C::STAGE;
-    float *sp1 = stage + ((m + 1) % NST) * C::STAGE;
+    const float *sp = stage + st0 * C::STAGE;
+    float *sp1 = stage + st1 * C::STAGE;
     const float *rc = (PL || col_in) ? sp + so * KC + 4 * lane : sfinf + 4 * lane;
     const float *rn = (PL || col_in) ? sp1 + so * KC + 4 * lane : sfinf + 4 * lane;
     if (!nin && (PL || col_in)) {
@@ -597,8 +600,13 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
     // the stage of plane index m + NST into the slot of stage m
     if (threadIdx.x == 0 && m + NST <= M && plane_in(m + NST)) {
       fence_proxy_async();
-      issue(m + NST);
+      issue(m + NST, st0);
       issued = m + NST;
+    }
+    st0 = st1;
+    if (++st1 == NST) {
+      st1 = 0;
+      ph1 ^= 1u;
     }
   }
   };
