@@ -110,6 +110,7 @@ __device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *tm, int c0
 }
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 __device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
@@ -142,12 +143,18 @@ __device__ __forceinline__ float acc_value(float a) { return a; }
 __device__ __forceinline__ float4 mean4(float4 a, float4 b) {
   return make_float4(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z), 0.5f * (a.w + b.w));
 }
+__device__ __forceinline__ float2 mean2(float2 a, float2 b) { return make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y)); }
 // ghost values of the link across face dir (bit numbering of cmask) of cell c
 // for the four velocities from stored position k
 __device__ __forceinline__ float4 link4(const Oct3Args &A, long long c, int dir, int k) {
   const int s = A.dslot[c];
   const int l = (s >= 0) ? A.dlinks[s * 6 + dir] : -1;
   return *reinterpret_cast<const float4 *>((l >= 0) ? A.lval + (size_t)l * A.nvp + k : A.finf + k);
+}
+__device__ __forceinline__ float2 link2(const Oct3Args &A, long long c, int dir, int k) {
+  const int s = A.dslot[c];
+  const int l = (s >= 0) ? A.dlinks[s * 6 + dir] : -1;
+  return *reinterpret_cast<const float2 *>((l >= 0) ? A.lval + (size_t)l * A.nvp + k : A.finf + k);
 }
 
 // The march of one block over the tile of columns at (x0, y0), chunk `chunk`
@@ -285,7 +292,8 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
   // the z stencil of the own column, per group: the difference D = f(p) -
   // f(p - d) of the current plane p and its upwind neighbour, and the z
   // outflow face of plane p - d (the inflow of plane p)
-  float4 D[NG], P[NG];
+  // (as pairs of velocities: unit u = 2 g + q holds velocities 2 q, 2 q + 1 of group g)
+  float2 D[2 * NG], P[2 * NG];
   {
     float4 Rpp[NG], Rp[NG], Rc[NG];
     own(p0 - 2 * d, Rpp);
@@ -297,10 +305,15 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
       const int k = k0 + 128 * g + 4 * lane;
-      if (!col_in || r < 0 || r >= nz) P[g] = lds4(sfinf + 128 * g + 4 * lane);
-      else if (mr & kNotFluid) P[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-      else P[g] = face4(Rp[g], (mr & guz) ? link4(A, cr, duz, k) : Rpp[g], (mr & gdz) ? link4(A, cr, ddz, k) : Rc[g]);
-      D[g] = sub4(Rc[g], Rp[g]);
+      float4 P4;
+      if (!col_in || r < 0 || r >= nz) P4 = lds4(sfinf + 128 * g + 4 * lane);
+      else if (mr & kNotFluid) P4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      else P4 = face4(Rp[g], (mr & guz) ? link4(A, cr, duz, k) : Rpp[g], (mr & gdz) ? link4(A, cr, ddz, k) : Rc[g]);
+      const float4 D4 = sub4(Rc[g], Rp[g]);
+      P[2 * g] = lo2(P4);
+      P[2 * g + 1] = hi2(P4);
+      D[2 * g] = lo2(D4);
+      D[2 * g + 1] = hi2(D4);
     }
   }
   if (lane < kMac)
@@ -471,34 +484,35 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
         constexpr bool GEN = decltype(gen)::value;
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
-        const int o = 128 * g + 4 * lane;
-        const float4 ax4 = lds4(scon + ((g * 4 + 0) * 32 + lane) * 4);
-        const float4 ay4 = lds4(scon + ((g * 4 + 1) * 32 + lane) * 4);
-        const float4 az4 = lds4(scon + ((g * 4 + 2) * 32 + lane) * 4);
-        const float4 w4 = lds4(scon + ((g * 4 + 3) * 32 + lane) * 4);
-        const float4 fc = lds4(rc + 128 * g), fnx = lds4(rn + 128 * g);
-        const float4 Dn = sub4(fnx, fc);
-        const float4 fxo = lds4(fxo_b + fx_own + o), fyo = lds4(fyo_b + fy_own + o);
-        float4 fxi = lds4(fxo_b + fx_in + o), fyi = lds4(fyo_b + fy_in + o), fzi = P[g];
-        // z outflow face of this plane (the inflow of the next)
-        float4 fzo;
-        if constexpr (!GEN) {
-          fzo = face4d(fc, D[g], Dn);
-        } else {
-          fzo = face4d(fc, (mc0 & guz) ? sub4(fc, link4(A, cell, duz, k0 + o)) : D[g],
-                       (mc0 & gdz) ? sub4(link4(A, cell, ddz, k0 + o), fc) : Dn);
-          // a ghost upwind neighbour: the mean of its link value and this cell (one-sided slope)
-          if (mc0 & gux) fxi = mean4(link4(A, cell, dux, k0 + o), fc);
-          if (mc0 & guy) fyi = mean4(link4(A, cell, duy, k0 + o), fc);
-          if (mc0 & guz) fzi = mean4(link4(A, cell, duz, k0 + o), fc);
-        }
-        P[g] = fzo;
-        D[g] = Dn; // f(p + d) - f(p): the upwind difference of the next plane
         float2 out[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const float2 ax = q ? hi2(ax4) : lo2(ax4), ay = q ? hi2(ay4) : lo2(ay4), az = q ? hi2(az4) : lo2(az4);
-          const float2 wk = q ? hi2(w4) : lo2(w4), f = q ? hi2(fc) : lo2(fc);
+          // velocities 2 q, 2 q + 1 of group g: one 8-byte access each
+          const int u = 2 * g + q;
+          const int o = 128 * g + 4 * lane + 2 * q;
+          const float2 ax = lds2(scon + ((g * 4 + 0) * 32 + lane) * 4 + 2 * q);
+          const float2 ay = lds2(scon + ((g * 4 + 1) * 32 + lane) * 4 + 2 * q);
+          const float2 az = lds2(scon + ((g * 4 + 2) * 32 + lane) * 4 + 2 * q);
+          const float2 wk = lds2(scon + ((g * 4 + 3) * 32 + lane) * 4 + 2 * q);
+          const float2 f = lds2(rc + 128 * g + 2 * q), fnx = lds2(rn + 128 * g + 2 * q);
+          const float2 Dn = sub2(fnx, f);
+          const float2 fxo = lds2(fxo_b + fx_own + o), fyo = lds2(fyo_b + fy_own + o);
+          float2 fxi = lds2(fxo_b + fx_in + o), fyi = lds2(fyo_b + fy_in + o), fzi = P[u];
+          // z outflow face of this plane (the inflow of the next)
+          float2 fzo;
+          if constexpr (!GEN) {
+            fzo = __fadd2_rn(f, vl_half2(D[u], Dn));
+          } else {
+            const float2 a = (mc0 & guz) ? sub2(f, link2(A, cell, duz, k0 + o)) : D[u];
+            const float2 b = (mc0 & gdz) ? sub2(link2(A, cell, ddz, k0 + o), f) : Dn;
+            fzo = __fadd2_rn(f, vl_half2(a, b));
+            // a ghost upwind neighbour: the mean of its link value and this cell (one-sided slope)
+            if (mc0 & gux) fxi = mean2(link2(A, cell, dux, k0 + o), f);
+            if (mc0 & guy) fyi = mean2(link2(A, cell, duy, k0 + o), f);
+            if (mc0 & guz) fzi = mean2(link2(A, cell, duz, k0 + o), f);
+          }
+          P[u] = fzo;
+          D[u] = Dn; // f(p + d) - f(p): the upwind difference of the next plane
           // Shakhov equilibrium g (1 + A c.q (2 c^2 / T - 5)) from the stored state
           const float2 cx = __ffma2_rn(ax, sigx, mUx), cy = __ffma2_rn(ay, sigy, mUy), cz = __ffma2_rn(az, sigz, mUz);
           const float2 c2 = __ffma2_rn(cx, cx, __ffma2_rn(cy, cy, __fmul2_rn(cz, cz)));
@@ -509,9 +523,9 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
           const float2 geq = __ffma2_rn(__fmul2_rn(e, cq), poly, e);
           // forward Euler: relaxation, then the flux differences along x, y, z
           float2 n = __ffma2_rn(dt2, sub2(geq, f), f);
-          n = __ffma2_rn(ax, sub2(q ? hi2(fxi) : lo2(fxi), q ? hi2(fxo) : lo2(fxo)), n);
-          n = __ffma2_rn(ay, sub2(q ? hi2(fyi) : lo2(fyi), q ? hi2(fyo) : lo2(fyo)), n);
-          n = __ffma2_rn(az, sub2(q ? hi2(fzi) : lo2(fzi), q ? hi2(fzo) : lo2(fzo)), n);
+          n = __ffma2_rn(ax, sub2(fxi, fxo), n);
+          n = __ffma2_rn(ay, sub2(fyi, fyo), n);
+          n = __ffma2_rn(az, sub2(fzi, fzo), n);
           out[q] = n;
           // moment sums about the stored bulk velocity (Eqs. moments1-3)
           const float2 wf = __fmul2_rn(wk, n);
@@ -530,6 +544,9 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
           acc_fma(acc[10], cx, e2);
           acc_fma(acc[11], cy, e2);
           acc_fma(acc[12], cz, e2);
+          // the next unit's loads after this unit: the units run one after the
+          // other instead of interleaved (fewer live registers, no spills)
+          asm volatile("" ::: "memory");
         }
         *reinterpret_cast<float4 *>(fn_cell + 128 * g) = cat4(out[0], out[1]);
       }
@@ -540,9 +557,10 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
         body(std::false_type{});
     } else {
 #pragma unroll
-      for (int g = 0; g < NG; ++g) {
-        P[g] = col_in ? make_float4(0.f, 0.f, 0.f, 0.f) : lds4(sfinf + 128 * g + 4 * lane);
-        D[g] = col_in ? sub4(lds4(rn + 128 * g), lds4(rc + 128 * g)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < 2 * NG; ++u) {
+        const int ou = 128 * (u >> 1) + 2 * (u & 1);
+        P[u] = col_in ? make_float2(0.f, 0.f) : lds2(sfinf + ou + 4 * lane);
+        D[u] = col_in ? sub2(lds2(rn + ou), lds2(rc + ou)) : make_float2(0.f, 0.f);
       }
     }
     // (3) butterfly of the 16 (14 used) sums over the 32 lanes, in the order of
