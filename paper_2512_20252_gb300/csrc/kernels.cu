@@ -38,6 +38,15 @@ constexpr int kThreadsPerCell = 64; // threads over velocities for one cell
 constexpr int kCellsPerBlock = 4;   // cells of one sweep block
 constexpr int kBlock = kThreadsPerCell * kCellsPerBlock;
 constexpr int kGhostThreads = 512; // threads over the velocities of one link
+// The ghost band's tiling: U velocities a thread takes at a time, and blocks
+// of 512 threads per SM.  FP32 storage: two velocities at a time, two blocks
+// per SM (64 registers); FP64 storage and the grouped launches of a batch
+// (their arguments come from shared memory) need more registers: one block.
+template <typename T, bool GROUPED> struct GhostTiling {
+  static constexpr bool two = std::is_same<T, float>::value && !GROUPED;
+  static constexpr int U = 2;
+  static constexpr int blocks = two ? 2 : 1;
+};
 
 template <int D> struct Dims {
   static constexpr int NC = (D == 2) ? 2 : 1;   // components: (h, b) or f
@@ -777,7 +786,11 @@ __device__ __forceinline__ bool mirror_bracket(const GhostArgs<T> &G, int a, dou
   return !(x < xl || x > xh);
 }
 
-template <typename T, int D>
+// The ghost band of link l, one block: every thread takes U velocities at a
+// time (strided by the block), so that U independent chains of loads are in
+// flight per thread and the link's surface-cell entries are read once per U
+// velocities.
+template <typename T, int D, int U>
 __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int l) {
   constexpr int NC = Dims<D>::NC;
   __shared__ double sh[kGhostThreads / 32 + 1];
@@ -789,80 +802,121 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
   const double nw[3] = {ld[3], ld[4], ld[5]};
   const double alpha = G.accom;
   const double *wgl = G.l_wg + (size_t)l * G.nvp;
+  // per-link constants in the storage type, converted once (FP64 divisions
+  // and conversions run on GB300's narrow FP64 pipe)
+  T rdx[3];
+  for (int a = 0; a < 3; ++a) rdx[a] = (a < D) ? (T)(1.0 / G.dx[a]) : T(0);
+  const T csp = (T)c_sp, ciw = (T)c_iw, wfall = T(1) / T(ns > 0 ? ns : 1);
   double Nsum = 0.0, Dsum = 0.0;
-  for (int iv = threadIdx.x; iv < G.nv; iv += blockDim.x) {
-    const int k = G.kst[iv];
+  for (int iv0 = threadIdx.x; iv0 < G.nv; iv0 += U * blockDim.x) {
+    int k[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int iv = iv0 + u * blockDim.x;
+      ok[u] = iv < G.nv;
+      k[u] = G.kst[ok[u] ? iv : iv0];
+    }
     // upwind weights, Eq. upwind (FP64 for the exact-zero decision in the FP64 path)
-    T xiT[3];
-    for (int a = 0; a < D; ++a) xiT[a] = G.xiT[a * G.nvp + k];
-    T wsum = T(0);
+    T xiT[U][3];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      for (int a = 0; a < 3; ++a) xiT[u][a] = (a < D) ? G.xiT[a * G.nvp + k[u]] : T(0);
+    T wsum[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) wsum[u] = T(0);
     for (int j = 0; j < (G.naive ? 0 : ns); ++j) {
       const double *sd = G.s_dbl + 8 * (s0 + j);
-      // xi.r without contraction: tangential velocities give an exact zero
-      T xr = T(0);
-      for (int a = 0; a < D; ++a) xr = add_rn(xr, mul_rn(xiT[a], (T)sd[a]));
-      const T dot = mul_rn(xr, (T)sd[7]);
-      T mx = dot > T(0) ? dot : T(0);
-      wsum = add_rn(wsum, mul_rn(mx, mx));
-    }
-    const bool fallback = G.plain_average || !(wsum != T(0));
-    T fgc[NC];
+      T r[3];
+      for (int a = 0; a < 3; ++a) r[a] = (a < D) ? (T)sd[a] : T(0);
+      const T rinv = (T)sd[7];
 #pragma unroll
-    for (int m = 0; m < NC; ++m) fgc[m] = T(0);
+      for (int u = 0; u < U; ++u) {
+        // xi.r without contraction: tangential velocities give an exact zero
+        T xr = T(0);
+        for (int a = 0; a < D; ++a) xr = add_rn(xr, mul_rn(xiT[u][a], r[a]));
+        const T dot = mul_rn(xr, rinv);
+        const T mx = dot > T(0) ? dot : T(0);
+        wsum[u] = add_rn(wsum[u], mul_rn(mx, mx));
+      }
+    }
+    T fgc[U][NC];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int m = 0; m < NC; ++m) fgc[u][m] = T(0);
     if (G.naive) { // the construction without upwind weighting, Sec. 3.3.4
 #pragma unroll
-      for (int m = 0; m < NC; ++m) {
-        const T fd = G.f[((size_t)donor * G.nvp + k) * NC + m];
-        fgc[m] = (aux >= 0) ? T(2) * fd - G.f[((size_t)aux * G.nvp + k) * NC + m] : fd;
-      }
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+          const T fd = G.f[((size_t)donor * G.nvp + k[u]) * NC + m];
+          fgc[u][m] = (aux >= 0) ? T(2) * fd - G.f[((size_t)aux * G.nvp + k[u]) * NC + m] : fd;
+        }
     }
     for (int j = 0; j < (G.naive ? 0 : ns); ++j) {
       const int *si = G.s_int + 8 * (s0 + j);
       const double *sd = G.s_dbl + 8 * (s0 + j);
-      T wt;
-      if (fallback) {
-        wt = T(1) / T(ns);
-      } else {
-        T xr = T(0);
-        for (int a = 0; a < D; ++a) xr = add_rn(xr, mul_rn(xiT[a], (T)sd[a]));
-        const T dot = mul_rn(xr, (T)sd[7]);
-        T mx = dot > T(0) ? dot : T(0);
-        wt = mul_rn(mx, mx) / wsum;
-      }
       const int jc = si[0];
+      T r[3], dxg[3];
+      bool has[3];
+      for (int a = 0; a < 3; ++a) {
+        r[a] = (a < D) ? (T)sd[a] : T(0);
+        has[a] = (a < D) && sd[4 + a] != 0.0;
+        dxg[a] = (a < D) ? (T)sd[4 + a] : T(0);
+      }
+      const T rinv = (T)sd[7];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool fallback = G.plain_average || !(wsum[u] != T(0));
+        T wt;
+        if (fallback) {
+          wt = wfall;
+        } else {
+          T xr = T(0);
+          for (int a = 0; a < D; ++a) xr = add_rn(xr, mul_rn(xiT[u][a], r[a]));
+          const T dot = mul_rn(xr, rinv);
+          const T mx = dot > T(0) ? dot : T(0);
+          wt = mul_rn(mx, mx) / wsum[u];
+        }
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+          const T fj = G.f[((size_t)jc * G.nvp + k[u]) * NC + m];
+          T v = fj; // f_j - sigma_j . (x_j - x_g)
+          for (int a = 0; a < D; ++a) {
+            if (has[a]) {
+              T sig = preghost_slope<T, NC>(G, si[1 + 2 * a], si[2 + 2 * a], fj, k[u], m, rdx[a], jc, a);
+              v -= sig * dxg[a];
+            }
+          }
+          fgc[u][m] += wt * v;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+      const int ku = k[u];
+      // shifted point (Eq. fsp) and incident distribution at the wall (Eq. fw)
+      T fiv0 = T(0);
 #pragma unroll
       for (int m = 0; m < NC; ++m) {
-        const T fj = G.f[((size_t)jc * G.nvp + k) * NC + m];
-        T v = fj; // f_j - sigma_j . (x_j - x_g)
-        for (int a = 0; a < D; ++a) {
-          const double r = sd[4 + a];
-          if (r != 0.0) {
-            T sig = preghost_slope<T, NC>(G, si[1 + 2 * a], si[2 + 2 * a], fj, k, m, (T)(1.0 / G.dx[a]), jc, a);
-            v -= sig * (T)r;
-          }
-        }
-        fgc[m] += wt * v;
+        const T fd = G.f[((size_t)donor * G.nvp + ku) * NC + m];
+        T sp = fd;
+        if (aux >= 0) sp = fd + csp * (G.f[((size_t)aux * G.nvp + ku) * NC + m] - fd);
+        const T fiv = sp + ciw * (fgc[u][m] - sp);
+        if (m == 0) fiv0 = fiv;
+        G.fsp[((size_t)l * G.nvp + ku) * NC + m] = sp;
+        G.fi[((size_t)l * G.nvp + ku) * NC + m] = fiv;
       }
+      // zero-net-mass-flux balance with the cut-cell split (Eq. rhowc), FP64
+      double xn = 0.0;
+      for (int a = 0; a < D; ++a) xn += G.xiD[a * G.nvp + ku] * nw[a];
+      const double Gw = G.gwu[ku];
+      const double wg = wgl[ku], ws = G.wD[ku] - wg;
+      Nsum += wg * xn * (double)fiv0;
+      Dsum += ws * xn * Gw;
     }
-    // shifted point (Eq. fsp) and incident distribution at the wall (Eq. fw)
-    T fs[NC], fiv[NC];
-#pragma unroll
-    for (int m = 0; m < NC; ++m) {
-      const T fd = G.f[((size_t)donor * G.nvp + k) * NC + m];
-      T sp = fd;
-      if (aux >= 0) sp = fd + (T)c_sp * (G.f[((size_t)aux * G.nvp + k) * NC + m] - fd);
-      fs[m] = sp;
-      fiv[m] = sp + (T)c_iw * (fgc[m] - sp);
-      G.fsp[((size_t)l * G.nvp + k) * NC + m] = sp;
-      G.fi[((size_t)l * G.nvp + k) * NC + m] = fiv[m];
-    }
-    // zero-net-mass-flux balance with the cut-cell split (Eq. rhowc), FP64
-    double xn = 0.0;
-    for (int a = 0; a < D; ++a) xn += G.xiD[a * G.nvp + k] * nw[a];
-    const double Gw = G.gwu[k];
-    const double wg = wgl[k], ws = G.wD[k] - wg;
-    Nsum += wg * xn * (double)fiv[0];
-    Dsum += ws * xn * Gw;
   }
   __syncthreads(); // scratch writes of this block are visible to the block
   const double N = block_sum<kGhostThreads>(Nsum, sh);
@@ -901,6 +955,7 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
   const double rho_w = (alpha > 0.0) ? -(N + (1.0 - alpha) * S) / (alpha * Dd) : 0.0;
   if (threadIdx.x == 0) G.rhow[l] = rho_w;
   // wall distribution (Eqs. general bc, Maxwell BC, fwc) and ghost value (Eq. extrapolation 2)
+#pragma unroll U
   for (int iv = threadIdx.x; iv < G.nv; iv += blockDim.x) {
     const int k = G.kst[iv];
     double xn = 0.0;
@@ -949,8 +1004,8 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kGhostThreads) ghost_band_kernel(GhostArgs<T> G) {
-  ghost_band_body<T, D>(G, blockIdx.x);
+__global__ void __launch_bounds__(kGhostThreads, (GhostTiling<T, false>::blocks)) ghost_band_kernel(GhostArgs<T> G) {
+  ghost_band_body<T, D, GhostTiling<T, false>::U>(G, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1242,13 +1297,13 @@ __device__ __forceinline__ int group_case(const int *__restrict__ start, int nca
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kGhostThreads) ghost_band_grouped(const GhostArgs<T> *__restrict__ tab,
+__global__ void __launch_bounds__(kGhostThreads, (GhostTiling<T, true>::blocks)) ghost_band_grouped(const GhostArgs<T> *__restrict__ tab,
                                                           const int *__restrict__ start, int ncase, int par) {
   __shared__ GhostArgs<T> sG;
   const int c = group_case(start, ncase, blockIdx.x);
   if (threadIdx.x == 0) sG = tab[2 * c + par];
   __syncthreads();
-  ghost_band_body<T, D>(sG, blockIdx.x - __ldg(start + c));
+  ghost_band_body<T, D, GhostTiling<T, true>::U>(sG, blockIdx.x - __ldg(start + c));
 }
 
 template <typename T, int D>
