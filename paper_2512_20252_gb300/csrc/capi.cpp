@@ -639,9 +639,17 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
           finf[static_cast<size_t>(ctx->kst_h[i]) * G.ncomp + m] = nat[static_cast<size_t>(i) * G.ncomp + m];
     }
     ctx->xiD = dalloc<double>(ctx, xi3.size(), "velocities");
-    ctx->wD = dalloc<double>(ctx, w.size(), "weights");
     upload(ctx, ctx->xiD, xi3, "upload velocities");
-    upload(ctx, ctx->wD, w, "upload weights");
+    {
+      // the weights, followed by their reciprocals (zero at padding positions)
+      std::vector<double> w2(2 * w.size(), 0.0);
+      for (size_t k = 0; k < w.size(); ++k) {
+        w2[k] = w[k];
+        w2[w.size() + k] = (w[k] > 0.0) ? 1.0 / w[k] : 0.0;
+      }
+      ctx->wD = dalloc<double>(ctx, w2.size(), "weights");
+      upload(ctx, ctx->wD, w2, "upload weights");
+    }
     if (ctx->precision == IBDVM_FP64) {
       double *a = dalloc<double>(ctx, xi3.size(), "velocities");
       double *b = dalloc<double>(ctx, w.size(), "weights");

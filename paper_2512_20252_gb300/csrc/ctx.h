@@ -62,7 +62,7 @@ struct ibdvm_ctx {
   int *d_flags = nullptr;
   // velocity tables, indexed by the stored position of a velocity
   void *xiT = nullptr, *wT = nullptr, *finf = nullptr;
-  double *xiD = nullptr, *wD = nullptr;
+  double *xiD = nullptr, *wD = nullptr; // wD: [2][nvp], the weights then their reciprocals (0 at padding)
   // stored position of every velocity in its natural order (x index fastest):
   // the identity, or, for the orthant layout of the FP32 TMA sweeps,
   // velocities grouped by the signs of their components with each group

@@ -684,6 +684,7 @@ template <typename T> struct GhostArgs {
   const T *__restrict__ finf;
   const double *__restrict__ xiD; // [3][nvp]
   const double *__restrict__ wD;  // [nvp]
+  const double *__restrict__ rwD; // [nvp]: 1 / w (0 at padding positions)
   const T *__restrict__ xiT;
   const int *__restrict__ l_int;  // [nlink][8]: gidx, donor, aux, axis, side, ghost, s0, s1
   const double *__restrict__ l_dbl; // [nlink][8]: c_sp, c_iw, c_gc, n0, n1, n2, S, -
@@ -987,13 +988,34 @@ __device__ __forceinline__ void ghost_band_body(const GhostArgs<T> &G, const int
         }
     }
     const double wk = G.wD[k], wg = wgl[k], ws = wk - wg;
+    if (std::is_same<T, float>::value && !G.dbg_fstar) {
+      // FP32 storage: the wall distribution and the ghost value of the step
+      // in FP32 (the wall density above stays FP64; a launch that reports
+      // f*_w for the wall quantities takes the FP64 branch below, so that
+      // the normal mass flux of f*_w vanishes to FP64 rounding)
+      const float wkf = (float)wk, wgf = (float)wg, wsf = wkf - wgf, rw = (float)G.rwD[k];
+      const float arw = (float)(alpha * rho_w), oma = (float)(1.0 - alpha), cgc = (float)c_gc, Gwf = (float)Gw;
+#pragma unroll
+      for (int m = 0; m < NC; ++m) {
+        const size_t o = ((size_t)l * G.nvp + k) * NC + m;
+        const float gw = (m == 0) ? Gwf : (float)(0.5 * G.Tw) * Gwf;
+        const float fr = arw * gw + oma * (float)fsv[m];
+        const float fiv = (float)G.fi[o];
+        const float fstar = (wkf > 0.f) ? (wgf * fiv + wsf * fr) * rw : fiv;
+        const float spv = (float)G.fsp[o];
+        float gv = spv + cgc * (fstar - spv);
+        if (G.ghost_nonneg && gv < 0.f) gv = 0.f;
+        G.lval[o] = (T)gv;
+      }
+      continue;
+    }
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
       const size_t o = ((size_t)l * G.nvp + k) * NC + m;
       const double gw = (m == 0) ? Gw : 0.5 * G.Tw * Gw; // B_w = T_w / 2 H_w
       const double fr = alpha * rho_w * gw + (1.0 - alpha) * fsv[m];
       const double fiv = (double)G.fi[o];
-      const double fstar = (wk > 0.0) ? (wg * fiv + ws * fr) / wk : fiv;
+      const double fstar = (wk > 0.0) ? (wg * fiv + ws * fr) * G.rwD[k] : fiv;
       const double spv = (double)G.fsp[o];
       double gv = spv + c_gc * (fstar - spv);
       if (G.ghost_nonneg && gv < 0.0) gv = 0.0; // optional nonnegative ghost values
@@ -1476,6 +1498,7 @@ template <typename T> GhostArgs<T> ghost_args(const ibdvm_ctx *ctx, int cur, dou
   G.finf = static_cast<const T *>(ctx->finf);
   G.xiD = ctx->xiD;
   G.wD = ctx->wD;
+  G.rwD = ctx->wD + ctx->nvp;
   G.xiT = static_cast<const T *>(ctx->xiT);
   G.l_int = ctx->l_int;
   G.l_dbl = ctx->l_dbl;
