@@ -585,6 +585,30 @@ def test_cylinder_512_full_size_properties(precision, tol):
     g.close()
 
 
+@pytest.mark.parametrize("workload,steps", [("cylinder_512", 5), ("sphere_96", 3)])
+def test_full_size_mixed_against_fp64(workload, steps):
+    """The mixed path at the benchmark's full size and launch shape (the TMA
+    sweep, the FP32 ghost values, the chunked moment sums) against the FP64
+    path (which matches the oracle to 1e-11 on the smaller cases) after a few
+    steps: W within 1e-5 of its largest magnitude per component, C_D within
+    1e-4."""
+    out = {}
+    for prec in ("fp64", "mixed"):
+        case = getattr(wl, workload)(precision=prec)
+        g = ibdvm.Solver(case)
+        g.step(steps)
+        W, q, t = g.moments()
+        _, _, CD, _ = g.forces()
+        out[prec] = (W, t, CD)
+        g.close()
+    (Wd, t, CDd), (Wm, _, CDm) = out["fp64"], out["mixed"]
+    fl = t == ibdvm.FLUID
+    for i in range(Wd.shape[1]):
+        scale = np.abs(Wd[fl, i]).max()
+        assert np.abs(Wm[fl, i] - Wd[fl, i]).max() < 1e-5 * scale, i
+    assert abs(CDm - CDd) < 1e-4 * abs(CDd)
+
+
 def test_cylinder_512_axis_exchange():
     """The TMA sweep treats x (faces exchanged through shared memory) and y
     (the march, faces in registers) by different code: a stream along y must
