@@ -678,7 +678,7 @@ def _solver_env(case, no_tma: bool):
             os.environ["IBDVM_NO_TMA"] = old
 
 
-@pytest.mark.parametrize("shape", ["square_256v", "ragged_64v", "short_rows", "naca_256v", "odd_nv"])
+@pytest.mark.parametrize("shape", ["square_256v", "ragged_64v", "short_rows", "naca_256v", "odd_nv", "asym_padded"])
 def test_tma_sweep_against_oracle_and_plain_sweep(shape):
     if shape == "square_256v":
         case = wl.small_2d("circle", n=40, nv=16, Ma=0.4)           # 256 velocities, 64 per quadrant
@@ -693,14 +693,21 @@ def test_tma_sweep_against_oracle_and_plain_sweep(shape):
         case["body"] = wl.circle(0.4)
     elif shape == "naca_256v":
         case = wl.small_2d("naca", n=48, nv=16, Ma=0.5)
-    else:
+    elif shape == "odd_nv":
         case = wl.small_2d("circle", n=32, nv=11, Ma=0.5)           # 121 velocities: quadrants of 36, 30, 30, 25
+    else:
+        # 24^2 velocities on [-4,8] x [-6,6]: quadrants of 192, 96, 192, 96 in
+        # 192-velocity chunks, two of them half padding (the cost model's choice)
+        case = wl.small_2d("circle", n=36, nv=24, Ma=0.5)
+        case["vlo"], case["vhi"] = [-4.0, -6.0], [8.0, 6.0]
     case["precision"] = "mixed"
     o = oracle.OracleCase(case)
     f0 = perturbed(o, 21, 0.2)
     o.set_f(f0)
     g = _solver_env(case, False)
     p = _solver_env(case, True)
+    if shape == "asym_padded":
+        assert g.nvel_padded == 4 * 192
     g.set_f(f0)
     p.set_f(f0)
     rg = g.step(4)
