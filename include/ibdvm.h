@@ -185,9 +185,8 @@ typedef struct {
   double U_w[6][3];  /* wall velocity; its normal component does not move the split plane */
 } ibdvm_domain_desc;
 
-/* Sets the domain faces.  2D FP32 cases keep the TMA sweep, which reads the
-   wall halo at the domain edges; other cases with a diffuse domain wall run
-   the generic sweep kernel (the 3D TMA sweep handles freestream faces only).
+/* Sets the domain faces.  FP32 cases keep their TMA sweep, which reads the
+   wall halo at the domain faces; FP64 cases run the generic sweep kernel.
    Cases with a wall cannot be batch members.  The state is kept.  With any wall the library allocates
    (2 ncell / n[a] summed over the D axes) * nvel_padded * ncomp elements of
    the storage type for the halo values, and frees them with the context or

@@ -778,8 +778,8 @@ ibdvm_status ibdvm_set_domain(ibdvm_ctx *ctx, const ibdvm_domain_desc *d) {
     ctx->wall_T[i] = (mask >> i & 1) ? d->T_w[i] : 1.0;
     for (int a = 0; a < 3; ++a) ctx->wall_U[i][a] = (mask >> i & 1) ? d->U_w[i][a] : 0.0;
   }
-  // the 2D TMA sweep reads the wall halo; the 3D one serves freestream faces only
-  ctx->use_tma = ctx->tma_ok && (!mask || D == 2);
+  // the TMA sweeps read the wall halo at the domain faces
+  ctx->use_tma = ctx->tma_ok;
   drop_graphs(ctx);
   return IBDVM_OK;
   IBDVM_END

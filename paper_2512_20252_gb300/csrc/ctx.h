@@ -123,7 +123,7 @@ struct ibdvm_ctx {
   double wall_U[6][3] = {};
   long long wall_off[7] = {};
   void *whalo = nullptr;
-  bool tma_ok = false; // the TMA sweep was set up (it serves cases without domain walls)
+  bool tma_ok = false; // the TMA sweep was set up (it serves cases with and without domain walls)
   // host uploads of the state in cell ranges (a copy stream, one event per range)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_ev[ibdvm::kUploadParts + 1] = {};

@@ -96,6 +96,12 @@ struct Oct3Args {
   int nx, ny, nz, nvp, zrows;
   int kc;       // velocities of a chunk (256 or 128)
   float sig[3]; // dx_a / dt: |xi_a| = |a_a| sig[a]
+  // diffuse domain walls: faces 2a + (s > 0) in wmask, the halo values of
+  // their boundary cells [slot][nvp] from the first slot woff[face]; the slot
+  // of a boundary cell is its transverse index (y + ny z, x + nx z, x + nx y)
+  const float *__restrict__ whalo;
+  long long woff[6];
+  int wmask;
 };
 
 enum : uint8_t { kNotFluid = 64 };
@@ -150,6 +156,14 @@ __device__ __forceinline__ float4 link4(const Oct3Args &A, long long c, int dir,
   const int s = A.dslot[c];
   const int l = (s >= 0) ? A.dlinks[s * 6 + dir] : -1;
   return *reinterpret_cast<const float4 *>((l >= 0) ? A.lval + (size_t)l * A.nvp + k : A.finf + k);
+}
+// the value of the halo cell across domain face i = 2a + (s > 0) of the
+// boundary cell with transverse slot t, for the four velocities at offset o of
+// the chunk from k0: a diffuse wall's slot of this step, or the freestream
+// (both halo layers hold the same values)
+__device__ __forceinline__ float4 halo3(const Oct3Args &A, int i, long long t, int k0, int o, const float *sfinf) {
+  if ((A.wmask >> i) & 1) return *reinterpret_cast<const float4 *>(A.whalo + (size_t)(A.woff[i] + t) * A.nvp + k0 + o);
+  return *reinterpret_cast<const float4 *>(sfinf + o);
 }
 __device__ __forceinline__ float2 link2(const Oct3Args &A, long long c, int dir, int k) {
   const int s = A.dslot[c];
@@ -273,10 +287,21 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
       issued = m;
     }
 
+  // halo values beyond the domain faces for this lane's groups: x faces at
+  // (y, plane p), y faces at (x, plane p), z faces at (x, y)
+  auto hx_face = [&](int xo, int yy, int p, int o) { // xo: the x index beyond the edge
+    return halo3(A, xo < 0 ? 0 : 1, yy + (long long)ny * p, k0, o, sfinf);
+  };
+  auto hy_face = [&](int xx, int yo, int p, int o) {
+    return halo3(A, yo < 0 ? 2 : 3, xx + (long long)nx * p, k0, o, sfinf);
+  };
   auto own = [&](int p, float4 *v) {
-    if (!col_in || p < 0 || p >= nz) {
+    if (!col_in) {
 #pragma unroll
       for (int g = 0; g < NG; ++g) v[g] = lds4(sfinf + 128 * g + 4 * lane);
+    } else if (p < 0 || p >= nz) {
+#pragma unroll
+      for (int g = 0; g < NG; ++g) v[g] = halo3(A, p < 0 ? 4 : 5, plane0, k0, 128 * g + 4 * lane, sfinf);
     } else {
       const float *src = A.f + (size_t)(plane0 + (long long)p * nxy) * A.nvp + k0 + 4 * lane;
 #pragma unroll
@@ -306,7 +331,8 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
     for (int g = 0; g < NG; ++g) {
       const int k = k0 + 128 * g + 4 * lane;
       float4 P4;
-      if (!col_in || r < 0 || r >= nz) P4 = lds4(sfinf + 128 * g + 4 * lane);
+      if (!col_in) P4 = lds4(sfinf + 128 * g + 4 * lane);
+      else if (r < 0 || r >= nz) P4 = Rp[g]; // a halo plane: its value, zero slope
       else if (mr & kNotFluid) P4 = make_float4(0.f, 0.f, 0.f, 0.f);
       else P4 = face4(Rp[g], (mr & guz) ? link4(A, cr, duz, k) : Rpp[g], (mr & gdz) ? link4(A, cr, ddz, k) : Rc[g]);
       const float4 D4 = sub4(Rc[g], Rp[g]);
@@ -345,15 +371,17 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
         const int o = 128 * g + 4 * lane, k = k0 + o;
         float4 FX, FY;
         if (!col_in) {
-          FX = FY = lds4(sfinf + o); // outside the domain: the free stream, zero slope
+          // a column past the x or y edge: the halo value (zero slope) across
+          // that edge; the face along the other axis is never read
+          FX = (x >= nx && y < ny) ? hx_face(x, y, p, o) : lds4(sfinf + o);
+          FY = (y >= ny && x < nx) ? hy_face(x, y, p, o) : lds4(sfinf + o);
         } else if (!fluid) {
           FX = FY = make_float4(0.f, 0.f, 0.f, 0.f); // never read: neighbours see the link values
         } else {
-          const float4 fin = lds4(sfinf + o);
-          const float4 xu = (mcm & gux) ? link4(A, cell, dux, k) : (xu_in ? lds4(sp + (so - sx) * KC + o) : fin);
-          const float4 xd = (mcm & gdx) ? link4(A, cell, ddx, k) : (xd_in ? lds4(sp + (so + sx) * KC + o) : fin);
-          const float4 yu = (mcm & guy) ? link4(A, cell, duy, k) : (yu_in ? lds4(sp + syu * KC + o) : fin);
-          const float4 yd = (mcm & gdy) ? link4(A, cell, ddy, k) : (yd_in ? lds4(sp + syd * KC + o) : fin);
+          const float4 xu = (mcm & gux) ? link4(A, cell, dux, k) : (xu_in ? lds4(sp + (so - sx) * KC + o) : hx_face(x - sx, y, p, o));
+          const float4 xd = (mcm & gdx) ? link4(A, cell, ddx, k) : (xd_in ? lds4(sp + (so + sx) * KC + o) : hx_face(x + sx, y, p, o));
+          const float4 yu = (mcm & guy) ? link4(A, cell, duy, k) : (yu_in ? lds4(sp + syu * KC + o) : hy_face(x, y - sy, p, o));
+          const float4 yd = (mcm & gdy) ? link4(A, cell, ddy, k) : (yd_in ? lds4(sp + syd * KC + o) : hy_face(x, y + sy, p, o));
           const float4 fc = lds4(rc + 128 * g);
           FX = face4(fc, xu, xd);
           FY = face4(fc, yu, yd);
@@ -367,13 +395,18 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
       if (PL || (h_in && h_up_in && !(hmm & (kNotFluid | hgu | hgd)))) {
         out = face4(lds4(sp + hc * KC + ho), lds4(sp + hup * KC + ho), lds4(sp + hdn * KC + ho));
       } else if (!h_in) {
-        out = lds4(sfinf + ho);
+        // a halo cell beyond the domain edge of its axis: the halo value; one
+        // beyond the other axis's edge as well is never read
+        if (hxa) out = (hy >= 0 && hy < ny) ? hx_face(hx, hy, p, ho) : lds4(sfinf + ho);
+        else out = (hx >= 0 && hx < nx) ? hy_face(hx, hy, p, ho) : lds4(sfinf + ho);
       } else if (hmm & kNotFluid) {
         out = make_float4(0.f, 0.f, 0.f, 0.f);
       } else {
         const long long hcell = hplane0 + (long long)p * nxy;
-        const float4 up =
-            (hmm & hgu) ? link4(A, hcell, hdu, k0 + ho) : (h_up_in ? lds4(sp + hup * KC + ho) : lds4(sfinf + ho));
+        const float4 up = (hmm & hgu) ? link4(A, hcell, hdu, k0 + ho)
+                          : h_up_in ? lds4(sp + hup * KC + ho)
+                          : hxa     ? hx_face(hx - hs, hy, p, ho)
+                                    : hy_face(hx, hy - hs, p, ho);
         const float4 dn = (hmm & hgd) ? link4(A, hcell, hdd, k0 + ho) : lds4(sp + hdn * KC + ho);
         out = face4(lds4(sp + hc * KC + ho), up, dn);
       }
@@ -459,10 +492,11 @@ __device__ __forceinline__ bool march3o(const Oct3Args &A, const CUtensorMap *tm
     const float *rc = (PL || col_in) ? sp + so * KC + 4 * lane : sfinf + 4 * lane;
     const float *rn = (PL || col_in) ? sp1 + so * KC + 4 * lane : sfinf + 4 * lane;
     if (!nin && (PL || col_in)) {
-      // past the domain edge: the free stream, written into the unused slot
-      // of that plane (each lane reads back only what it wrote)
+      // past the domain edge: the halo value of the own column, written into
+      // the unused slot of that plane (each lane reads back only what it wrote)
 #pragma unroll
-      for (int g = 0; g < NG; ++g) sts4(sp1 + so * KC + 128 * g + 4 * lane, lds4(sfinf + 128 * g + 4 * lane));
+      for (int g = 0; g < NG; ++g)
+        sts4(sp1 + so * KC + 128 * g + 4 * lane, halo3(A, d > 0 ? 5 : 4, plane0, k0, 128 * g + 4 * lane, sfinf));
     }
     const float *fxo_b = fxb + par * C::FX, *fyo_b = fyb + par * C::FY;
     const bool fluid = PL ? !abort_local : (col_in && !(mc0 & kNotFluid) && !abort_local);
@@ -741,6 +775,9 @@ Oct3Args oct_args(const ibdvm_ctx *ctx, int cur, int *err) {
   A.zrows = 0;
   A.kc = ctx->oct_kc;
   for (int a = 0; a < 3; ++a) A.sig[a] = (float)(ctx->geom.dx[a] / ctx->geom.dt);
+  A.whalo = static_cast<const float *>(ctx->whalo);
+  A.wmask = ctx->wall_mask;
+  for (int i = 0; i < 6; ++i) A.woff[i] = ctx->wall_off[i];
   return A;
 }
 
