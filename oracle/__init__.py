@@ -134,6 +134,16 @@ def _load():
                 "or_cut_fraction_2d": ([_D, _D, _D], ctypes.c_double),
                 "or_cut_fraction_3d": ([_D, _D, _D], ctypes.c_double),
                 "or_residual": ([V, _D, _D], ctypes.c_double),
+                "or_tree_create": ([P, ctypes.c_long, ctypes.c_int, _I, _I, _I], V),
+                "or_tree_destroy": ([V], None),
+                "or_tree_set_threads": ([V, ctypes.c_int], None),
+                "or_tree_sizes": ([V, _LL], None),
+                "or_tree_dt": ([V], ctypes.c_double),
+                "or_tree_neighbours": ([V, _LL], None),
+                "or_tree_get_f": ([V, _D], None),
+                "or_tree_set_f": ([V, _D], None),
+                "or_tree_step": ([V, ctypes.c_int, _D], ctypes.c_int),
+                "or_tree_moments": ([V, _D, _D], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -451,3 +461,77 @@ def cut_fraction_2d(blo, bhi, n) -> float:
 def cut_fraction_3d(blo, bhi, n) -> float:
     a = [np.asarray(_arr3(list(v)), dtype=np.float64) for v in (blo, bhi, n)]
     return float(_load().or_cut_fraction_3d(*[_dp(x) for x in a]))
+
+
+class OracleTree:
+    """A case on a tree-refined 2D grid (reading C28): the leaves of
+    ``cfg["tree"]`` (level, ix, iy over the root grid ``cfg["n"]``) and the
+    state f[leaf][k][comp]; no body, freestream domain faces."""
+
+    def __init__(self, cfg: dict, threads: int = 1):
+        self.lib = _load()
+        self.cfg = dict(cfg)
+        self._p, self._keep = _params(cfg)
+        tree = cfg["tree"]
+        self._lev = np.ascontiguousarray(np.asarray(tree["level"], dtype=np.int32))
+        self._ix = np.ascontiguousarray(np.asarray(tree["ix"], dtype=np.int32))
+        self._iy = np.ascontiguousarray(np.asarray(tree["iy"], dtype=np.int32))
+        self.h = self.lib.or_tree_create(ctypes.byref(self._p), self._lev.size, int(tree["maxlevel"]),
+                                         self._lev.ctypes.data_as(_I), self._ix.ctypes.data_as(_I),
+                                         self._iy.ctypes.data_as(_I))
+        if not self.h:
+            raise ValueError("invalid tree: the leaves must tile the domain with face neighbours at most one level apart")
+        self.lib.or_tree_set_threads(self.h, max(1, int(threads)))
+        s = np.zeros(3, dtype=np.int64)
+        self.lib.or_tree_sizes(self.h, s.ctypes.data_as(_LL))
+        self.nleaf, self.nvel, self.ncomp = (int(x) for x in s)
+        self.dim = 2
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.or_tree_destroy(h)
+            self.h = None
+
+    @property
+    def dt(self) -> float:
+        return float(self.lib.or_tree_dt(self.h))
+
+    def shape(self):
+        return (self.nleaf, self.nvel, self.ncomp)
+
+    def neighbours(self) -> np.ndarray:
+        nb = np.zeros((self.nleaf, 4, 2), dtype=np.int64)
+        self.lib.or_tree_neighbours(self.h, nb.ctypes.data_as(_LL))
+        return nb
+
+    def get_f(self) -> np.ndarray:
+        f = np.zeros(self.shape())
+        self.lib.or_tree_get_f(self.h, _dp(f))
+        return f
+
+    def set_f(self, f) -> None:
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(self.shape()))
+        self.lib.or_tree_set_f(self.h, _dp(f))
+
+    def step(self, n: int = 1) -> float:
+        r = ctypes.c_double()
+        self.lib.or_tree_step(self.h, int(n), ctypes.byref(r))
+        return r.value
+
+    def moments(self):
+        W = np.zeros((self.nleaf, 4))
+        q = np.zeros((self.nleaf, 2))
+        self.lib.or_tree_moments(self.h, _dp(W), _dp(q))
+        return W, q
+
+    def sizes(self) -> np.ndarray:
+        """Edge length of every leaf along x and y."""
+        lev = self._lev.astype(np.float64)
+        H = [(self.cfg["hi"][a] - self.cfg["lo"][a]) / self.cfg["n"][a] for a in range(2)]
+        return np.stack([H[0] * 0.5 ** lev, H[1] * 0.5 ** lev], axis=1)
+
+    def centres(self) -> np.ndarray:
+        hs = self.sizes()
+        return np.stack([self.cfg["lo"][0] + (self._ix + 0.5) * hs[:, 0],
+                         self.cfg["lo"][1] + (self._iy + 0.5) * hs[:, 1]], axis=1)

@@ -77,6 +77,21 @@
  *       value: the limiter sees a zero difference); rho_w makes the mass flux
  *       through the face zero with those face values.
  *
+ *   C28 tree-refined physical grids (Sec. 4.2-4.4 use a tree-based AMR mesh
+ *       and give no scheme for it): 2D, a root grid of equal cells, each
+ *       leaf a square of level l (edge h / 2^l), face neighbours at most one
+ *       level apart (2:1).  Finite volumes on the leaves with the uniform
+ *       grid's arithmetic: the van Leer slope of a cell along an axis from
+ *       the value on each side (the neighbour's, the mean of the two finer
+ *       neighbours', or the freestream halo) over the distance between
+ *       centres along the axis ((h_c + h_n) / 2; h_c across the domain
+ *       edge); the face value of the upwind cell f + s sigma h / 2; the
+ *       inflow of a side with two finer neighbours the mean of their face
+ *       values (each covers half the side), so the flux through every
+ *       interface is the same for both cells; one time step for all cells,
+ *       C16 with the finest cell size; no body on the tree.  On a tree of
+ *       one level it is the uniform grid's step.
+ *
  * Parity unpinned: C4-C7, C9, C10, C14, C16-C19 and the first-order
  * outgoing face of C24 are choices the paper does not fix; they are pinned
  * only by agreement with an independent implementation, not by the paper.
@@ -1407,6 +1422,264 @@ void or_moments(const or_case *C, double *W, double *q)
   double out[16];
   for (long c = 0; c < C->nc; ++c) {
     or_cell_moments(C, C->f + (size_t)c * C->nv * C->ncomp, out);
+    for (int i = 0; i < D + 2; ++i) W[c * (D + 2) + i] = out[i];
+    for (int a = 0; a < D; ++a) q[c * D + a] = out[D + 4 + a];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tree-refined 2D grids (reading C28)                                       */
+/* ------------------------------------------------------------------------ */
+
+struct or_tree {
+  or_case *V;   /* velocity grid, gas and time step: a body-free case on the finest uniform grid */
+  long n;       /* leaves */
+  int L;        /* finest level */
+  int *lev;
+  double *h;    /* [n][2] edge lengths */
+  long *nb;     /* [n][4][2] face neighbours, sides 2a + (s > 0) */
+  double *f, *fnew, *sl; /* [n][nv][nc]; slopes [n][2][nv][nc] */
+  int nthreads;
+};
+
+or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int *level, const int *ix,
+                        const int *iy)
+{
+  if (p->dim != 2 || p->kind != OR_BODY_NONE || maxlevel < 0 || maxlevel > 12 || nleaf <= 0) return NULL;
+  for (int i = 0; i < 6; ++i)
+    if (p->wall[i]) return NULL;
+  const long nfx = (long)p->n[0] << maxlevel, nfy = (long)p->n[1] << maxlevel;
+  /* owner of every cell of the finest grid */
+  long *own = (long *)xcalloc((size_t)(nfx * nfy), sizeof(long));
+  for (long q = 0; q < nfx * nfy; ++q) own[q] = -1;
+  int ok = 1;
+  for (long c = 0; c < nleaf && ok; ++c) {
+    const int l = level[c];
+    if (l < 0 || l > maxlevel || ix[c] < 0 || iy[c] < 0 || ix[c] >= (p->n[0] << l) || iy[c] >= (p->n[1] << l)) {
+      ok = 0;
+      break;
+    }
+    const long s = 1L << (maxlevel - l);
+    for (long i = ix[c] * s; i < (ix[c] + 1) * s; ++i)
+      for (long j = iy[c] * s; j < (iy[c] + 1) * s; ++j) {
+        if (own[i + nfx * j] >= 0) ok = 0; /* overlapping leaves */
+        own[i + nfx * j] = c;
+      }
+  }
+  for (long q = 0; ok && q < nfx * nfy; ++q)
+    if (own[q] < 0) ok = 0; /* a hole */
+  or_tree *T = NULL;
+  if (ok) {
+    T = (or_tree *)xcalloc(1, sizeof(or_tree));
+    or_params pf = *p;
+    pf.n[0] = (int)nfx;
+    pf.n[1] = (int)nfy;
+    T->V = or_create(&pf);
+    T->n = nleaf;
+    T->L = maxlevel;
+    T->lev = (int *)xcalloc((size_t)nleaf, sizeof(int));
+    T->h = (double *)xcalloc((size_t)nleaf * 2, sizeof(double));
+    T->nb = (long *)xcalloc((size_t)nleaf * 8, sizeof(long));
+    T->nthreads = 1;
+    const double H[2] = {(p->hi[0] - p->lo[0]) / p->n[0], (p->hi[1] - p->lo[1]) / p->n[1]};
+    for (long c = 0; c < nleaf && ok; ++c) {
+      const int l = level[c];
+      T->lev[c] = l;
+      for (int a = 0; a < 2; ++a) T->h[2 * c + a] = H[a] / (double)(1L << l);
+      const long s = 1L << (maxlevel - l);
+      const long i0 = ix[c] * s, j0 = iy[c] * s;
+      for (int a = 0; a < 2 && ok; ++a)
+        for (int side = 0; side < 2 && ok; ++side) {
+          long *out = T->nb + (size_t)c * 8 + (2 * a + side) * 2;
+          out[0] = out[1] = -1;
+          /* the finest cells just beyond the face, in increasing transverse order */
+          const long fa = (a == 0) ? (side ? i0 + s : i0 - 1) : (side ? j0 + s : j0 - 1);
+          if (fa < 0 || fa >= (a == 0 ? nfx : nfy)) continue; /* the domain edge */
+          int cnt = 0;
+          for (long t = 0; t < s; ++t) {
+            const long q = (a == 0) ? fa + nfx * (j0 + t) : (i0 + t) + nfx * fa;
+            const long o = own[q];
+            if (cnt > 0 && out[cnt - 1] == o) continue;
+            if (cnt == 2) {
+              ok = 0;
+              break;
+            }
+            out[cnt++] = o;
+          }
+          /* 2:1: one neighbour of the same or the coarser level, or two of the finer one */
+          if (cnt == 1 && !(level[out[0]] == l || level[out[0]] == l - 1)) ok = 0;
+          if (cnt == 2 && !(level[out[0]] == l + 1 && level[out[1]] == l + 1)) ok = 0;
+        }
+    }
+    if (ok) {
+      const size_t sz = (size_t)nleaf * T->V->nv * T->V->ncomp;
+      T->f = (double *)xcalloc(sz, sizeof(double));
+      T->fnew = (double *)xcalloc(sz, sizeof(double));
+      T->sl = (double *)xcalloc(sz * 2, sizeof(double));
+      for (long c = 0; c < nleaf; ++c)
+        memcpy(T->f + (size_t)c * T->V->nv * T->V->ncomp, T->V->finf, sizeof(double) * T->V->nv * T->V->ncomp);
+    }
+  }
+  free(own);
+  if (T && !ok) {
+    or_tree_destroy(T);
+    T = NULL;
+  }
+  return T;
+}
+
+void or_tree_destroy(or_tree *T)
+{
+  if (!T) return;
+  if (T->V) or_destroy(T->V);
+  free(T->lev);
+  free(T->h);
+  free(T->nb);
+  free(T->f);
+  free(T->fnew);
+  free(T->sl);
+  free(T);
+}
+
+void or_tree_set_threads(or_tree *T, int nthreads) { T->nthreads = nthreads > 0 ? nthreads : 1; }
+
+void or_tree_sizes(const or_tree *T, long long *o)
+{
+  o[0] = T->n;
+  o[1] = T->V->nv;
+  o[2] = T->V->ncomp;
+}
+
+double or_tree_dt(const or_tree *T) { return T->V->dt; }
+
+void or_tree_neighbours(const or_tree *T, long long *nb)
+{
+  for (long i = 0; i < T->n * 8; ++i) nb[i] = T->nb[i];
+}
+
+void or_tree_get_f(const or_tree *T, double *f)
+{
+  memcpy(f, T->f, sizeof(double) * (size_t)T->n * T->V->nv * T->V->ncomp);
+}
+
+void or_tree_set_f(or_tree *T, const double *f)
+{
+  memcpy(T->f, f, sizeof(double) * (size_t)T->n * T->V->nv * T->V->ncomp);
+}
+
+/* the value on side (a, s) of leaf c as its slope sees it, and the distance
+   to it along a (C28) */
+static double tree_side(const or_tree *T, const double *f, long c, int a, int s, int k, int m, double *dist)
+{
+  const long *nb = T->nb + (size_t)c * 8 + (2 * a + (s > 0)) * 2;
+  const int nv = T->V->nv, nc = T->V->ncomp;
+  const double hc = T->h[2 * c + a];
+  if (nb[0] < 0) {
+    *dist = hc;
+    return T->V->finf[k * nc + m]; /* the freestream halo */
+  }
+  *dist = 0.5 * (hc + T->h[2 * nb[0] + a]);
+  const double v0 = f[((size_t)nb[0] * nv + k) * nc + m];
+  if (nb[1] < 0) return v0;
+  return 0.5 * (v0 + f[((size_t)nb[1] * nv + k) * nc + m]);
+}
+
+/* face value on side (a, s) of leaf c (Eq. reconstruction with the slope of C28) */
+static double tree_face(const or_tree *T, const double *f, long c, int a, int s, int k, int m)
+{
+  const int nv = T->V->nv, nc = T->V->ncomp;
+  const double fc = f[((size_t)c * nv + k) * nc + m];
+  const double sig = T->sl[(((size_t)c * 2 + a) * nv + k) * nc + m];
+  return fc + sig * (s * 0.5 * T->h[2 * c + a]);
+}
+
+int or_tree_step(or_tree *T, int nsteps, double *residual)
+{
+  or_case *V = T->V;
+  const int nv = V->nv, nc = V->ncomp, D = 2, nw = D + 2;
+  const long n = T->n;
+  double *Wold = (double *)xcalloc((size_t)n * nw, sizeof(double));
+  double *Wnew = (double *)xcalloc((size_t)n * nw, sizeof(double));
+  double res = 0.0;
+  for (int it = 0; it < nsteps; ++it) {
+    /* slopes of every leaf along both axes (Eq. limiter over the centre distances) */
+#pragma omp parallel for num_threads(T->nthreads) schedule(dynamic, 16)
+    for (long c = 0; c < n; ++c)
+      for (int a = 0; a < D; ++a)
+        for (int k = 0; k < nv; ++k)
+          for (int m = 0; m < nc; ++m) {
+            const double fc = T->f[((size_t)c * nv + k) * nc + m];
+            double dm, dp;
+            const double fm = tree_side(T, T->f, c, a, -1, k, m, &dm);
+            const double fp = tree_side(T, T->f, c, a, +1, k, m, &dp);
+            T->sl[(((size_t)c * 2 + a) * nv + k) * nc + m] = or_vanleer((fc - fm) / dm, (fp - fc) / dp);
+          }
+    /* transport and relaxation of every leaf */
+#pragma omp parallel num_threads(T->nthreads)
+    {
+      double *gS = (double *)xcalloc((size_t)nv * nc, sizeof(double));
+#pragma omp for schedule(dynamic, 16)
+      for (long c = 0; c < n; ++c) {
+        double rho, U[3], Tm, q[3], tau;
+        cell_macros(V, T->f, c, &rho, U, &Tm, q, &tau);
+        conservative(V, T->f, c, Wold + c * nw);
+        or_shakhov(V, rho, U, Tm, q, gS);
+        for (int k = 0; k < nv; ++k)
+          for (int m = 0; m < nc; ++m) {
+            const double fc = T->f[((size_t)c * nv + k) * nc + m];
+            double div = 0.0;
+            for (int a = 0; a < D; ++a) {
+              const double xia = V->xi[3 * k + a];
+              if (xia == 0.0) continue;
+              const int s = (xia > 0.0) ? 1 : -1; /* the downwind side */
+              const double fout = tree_face(T, T->f, c, a, s, k, m);
+              /* inflow through the upwind side: the upwind cells' face values,
+                 each over the share of the side it covers */
+              const long *nb = T->nb + (size_t)c * 8 + (2 * a + (-s > 0)) * 2;
+              double fin;
+              if (nb[0] < 0)
+                fin = V->finf[k * nc + m]; /* halo: its value, zero slope */
+              else if (nb[1] < 0)
+                fin = tree_face(T, T->f, nb[0], a, s, k, m);
+              else
+                fin = 0.5 * (tree_face(T, T->f, nb[0], a, s, k, m) + tree_face(T, T->f, nb[1], a, s, k, m));
+              div += fabs(xia) * (fout - fin) / T->h[2 * c + a];
+            }
+            T->fnew[((size_t)c * nv + k) * nc + m] = fc - V->dt * div + V->dt / tau * (gS[k * nc + m] - fc);
+          }
+      }
+      free(gS);
+    }
+    double *t = T->f;
+    T->f = T->fnew;
+    T->fnew = t;
+    for (long c = 0; c < n; ++c) conservative(V, T->f, c, Wnew + c * nw);
+    /* residual over the leaves (the formula of the uniform grid, C18) */
+    res = 0.0;
+    for (int i = 0; i < nw; ++i) {
+      double num = 0.0, den = 0.0;
+      for (long c = 0; c < n; ++c) {
+        const double d = Wnew[c * nw + i] - Wold[c * nw + i];
+        num += d * d;
+        den += fabs(Wnew[c * nw + i]);
+      }
+      if (den == 0.0) continue;
+      const double r = sqrt(num) / den;
+      if (r > res) res = r;
+    }
+  }
+  free(Wold);
+  free(Wnew);
+  if (residual) *residual = res;
+  return 0;
+}
+
+void or_tree_moments(const or_tree *T, double *W, double *q)
+{
+  const int D = 2, nv = T->V->nv, nc = T->V->ncomp;
+  double out[16];
+  for (long c = 0; c < T->n; ++c) {
+    or_cell_moments(T->V, T->f + (size_t)c * nv * nc, out);
     for (int i = 0; i < D + 2; ++i) W[c * (D + 2) + i] = out[i];
     for (int a = 0; a < D; ++a) q[c * D + a] = out[D + 4 + a];
   }

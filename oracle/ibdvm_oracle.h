@@ -140,6 +140,27 @@ double or_cut_fraction_2d(const double *blo, const double *bhi, const double *n)
 double or_cut_fraction_3d(const double *blo, const double *bhi, const double *n);
 double or_residual(const or_case *C, const double *Wold, const double *Wnew);
 
+/* Tree-refined 2D grids (reading C28): leaves (level, ix, iy) over the root
+   grid p->n[0] x p->n[1] on [lo, hi], integer coordinates of the leaf's level
+   (0 <= ix < n[0] 2^level); the leaves must tile the domain and face
+   neighbours differ by at most one level.  p->kind must be OR_BODY_NONE and
+   the domain faces freestream.  NULL for an invalid tree. */
+typedef struct or_tree or_tree;
+or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int *level, const int *ix,
+                        const int *iy);
+void or_tree_destroy(or_tree *T);
+void or_tree_set_threads(or_tree *T, int nthreads);
+/* sizes: nleaf, nvel, ncomp */
+void or_tree_sizes(const or_tree *T, long long *out3);
+double or_tree_dt(const or_tree *T);
+/* face neighbours nb[leaf][side 2a + (s > 0)][2] (-1: none; the first is -1
+   at the domain edge, the second unless two finer neighbours share the side) */
+void or_tree_neighbours(const or_tree *T, long long *nb);
+void or_tree_get_f(const or_tree *T, double *f);
+void or_tree_set_f(or_tree *T, const double *f);
+int or_tree_step(or_tree *T, int nsteps, double *residual);
+void or_tree_moments(const or_tree *T, double *W, double *q);
+
 #ifdef __cplusplus
 }
 #endif

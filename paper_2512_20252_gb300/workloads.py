@@ -270,3 +270,88 @@ def small_2d(body="circle", n=16, nv=8, precision="fp64", **kw):
          "none": {"kind": "none"}}[body]
     return _case(2, n, 2.0, nv, 4.5, kw.pop("Kn", 0.1), kw.pop("Ma", 0.3), b, precision=precision,
                  steps=kw.pop("steps", 5), **kw)
+
+
+# ---------------------------------------------------------------------------
+# quadtree meshes (the tree-refined physical grids of Sec. 4.2-4.4)
+# ---------------------------------------------------------------------------
+
+def tree_leaves(root, maxlevel, lo, hi, center, radii, metric="point"):
+    """Leaves (level, ix, iy) of a 2:1-balanced quadtree over a root grid of
+    root[0] x root[1] cells on [lo, hi]: a cell of level l < maxlevel is split
+    while its centre lies within radii[l] of `center` (radii decreasing with
+    the level; metric "point": the distance to the point, "x" or "y": the
+    distance along that axis only, which refines stripes), then any leaf with
+    a face neighbour two or more levels finer is split until the tree is
+    balanced.  Integer coordinates are those of
+    the leaf's level (0 <= ix < root[0] 2^level).  Geometry only."""
+    nx0, ny0 = root
+    hx0, hy0 = (hi[0] - lo[0]) / nx0, (hi[1] - lo[1]) / ny0
+    L = maxlevel
+    # leaf level of every finest cell: the tree as a level map
+    nf = (nx0 << L, ny0 << L)
+    lev = np.zeros(nf, dtype=np.int64)
+
+    def split_wanted(l, i, j):
+        h = 2.0 ** -l
+        xc = lo[0] + (i + 0.5) * hx0 * h
+        yc = lo[1] + (j + 0.5) * hy0 * h
+        if metric == "x":
+            return abs(xc - center[0]) <= radii[l]
+        if metric == "y":
+            return abs(yc - center[1]) <= radii[l]
+        return math.hypot(xc - center[0], yc - center[1]) <= radii[l]
+
+    for l in range(L):
+        s = 1 << (L - l)  # finest cells per leaf side at level l
+        for i in range(nx0 << l):
+            for j in range(ny0 << l):
+                blk = lev[i * s:(i + 1) * s, j * s:(j + 1) * s]
+                if (blk == l).all() and split_wanted(l, i, j):
+                    blk[...] = l + 1
+    # 2:1 balance across faces: raise a leaf whose face neighbour is two or more
+    # levels finer (one level at a time, until nothing changes)
+    changed = True
+    while changed:
+        changed = False
+        for l in range(L):
+            s = 1 << (L - l)
+            for i in range(nx0 << l):
+                for j in range(ny0 << l):
+                    blk = lev[i * s:(i + 1) * s, j * s:(j + 1) * s]
+                    if not (blk == l).all():
+                        continue
+                    finer = False
+                    if i > 0 and lev[i * s - 1, j * s:(j + 1) * s].max() >= l + 2:
+                        finer = True
+                    if (i + 1) * s < nf[0] and lev[(i + 1) * s, j * s:(j + 1) * s].max() >= l + 2:
+                        finer = True
+                    if j > 0 and lev[i * s:(i + 1) * s, j * s - 1].max() >= l + 2:
+                        finer = True
+                    if (j + 1) * s < nf[1] and lev[i * s:(i + 1) * s, (j + 1) * s].max() >= l + 2:
+                        finer = True
+                    if finer:
+                        blk[...] = l + 1
+                        changed = True
+    level, ix, iy = [], [], []
+    for l in range(L + 1):
+        s = 1 << (L - l)
+        for j in range(ny0 << l):
+            for i in range(nx0 << l):
+                if (lev[i * s:(i + 1) * s, j * s:(j + 1) * s] == l).all():
+                    level.append(l)
+                    ix.append(i)
+                    iy.append(j)
+    return {"maxlevel": L, "level": level, "ix": ix, "iy": iy}
+
+
+def tree_case(root=16, maxlevel=2, L=2.0, nv=12, V=4.5, Kn=0.1, Ma=0.3, radii=None, center=(0.0, 0.0),
+              precision="fp64", steps=20, metric="point"):
+    """A 2D case on a quadtree: root^2 cells on [-L, L]^2 refined around
+    `center` (by default to level 1 within 0.6 L and to level 2 within 0.3 L),
+    freestream domain faces, no body."""
+    if radii is None:
+        radii = [0.6 * L, 0.3 * L] + [0.3 * L * 0.5 ** i for i in range(1, maxlevel)]
+    d = _case(2, root, L, nv, V, Kn, Ma, {"kind": "none"}, precision=precision, steps=steps)
+    d["tree"] = tree_leaves((root, root), maxlevel, d["lo"], d["hi"], center, radii, metric)
+    return d
