@@ -132,6 +132,8 @@ void free_all(ibdvm_ctx *ctx) {
   cfree_t(ctx->oct_sign);
   cfree_t(ctx->ctype);
   cfree_t(ctx->cmask);
+  cfree_t(ctx->tree_nb);
+  cfree_t(ctx->tree_lev);
   cfree_t(ctx->partf);
   cfree_t(ctx->d_forces);
   cfree_t(ctx->d_step_forces);
@@ -529,8 +531,11 @@ const char *ibdvm_status_string(ibdvm_status s) {
   return "unknown status";
 }
 
-ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *vgrid,
-                               const ibdvm_gas_desc *gas, void *cuda_stream, ibdvm_ctx **out) {
+// a context on a uniform grid, or (tree != NULL) on the leaves of a
+// tree-refined 2D grid over the root grid `grid`
+static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_desc *tree,
+                               const ibdvm_vgrid_desc *vgrid, const ibdvm_gas_desc *gas, void *cuda_stream,
+                               ibdvm_ctx **out) {
   if (!out) return IBDVM_E_INVAL;
   *out = nullptr;
   if (!grid || !vgrid || !gas) return IBDVM_E_INVAL;
@@ -540,9 +545,30 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
   ibdvm_status st = IBDVM_OK;
   try {
     std::string err;
-    if (!build_grid(*grid, *vgrid, *gas, ctx->geom, err)) {
+    ibdvm_grid_desc gd = *grid;
+    std::vector<int> tlev, tnb;
+    if (tree) {
+      // the velocity grid, the gas and the time step of the finest level (dt by
+      // the CFL of the smallest leaf); the cells are the leaves
+      if (!build_tree_mesh(*grid, *tree, tlev, tnb, err)) {
+        ctx->err = err;
+        throw Fail{IBDVM_E_INVAL};
+      }
+      for (int a = 0; a < 2; ++a) gd.n[a] = grid->n[a] << tree->maxlevel;
+    }
+    if (!build_grid(gd, *vgrid, *gas, ctx->geom, err)) {
       ctx->err = err;
       throw Fail{IBDVM_E_INVAL};
+    }
+    if (tree) {
+      Geom &Gt = ctx->geom;
+      Gt.ncell = tree->nleaf;
+      Gt.n[0] = tree->nleaf;
+      Gt.n[1] = Gt.n[2] = 1;
+      Gt.type.assign(static_cast<size_t>(tree->nleaf), IBDVM_CELL_FLUID);
+      Gt.nfluid = tree->nleaf;
+      ctx->tree = true;
+      for (int a = 0; a < 2; ++a) ctx->tree_h0[a] = (grid->hi[a] - grid->lo[a]) / grid->n[a];
     }
     const Geom &G = ctx->geom;
     ctx->precision = gas->precision;
@@ -554,7 +580,7 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     // the stored order of the velocities: natural, or grouped by orthant for
     // the FP32 TMA sweeps (IBDVM_NO_TMA=1 keeps the plain sweep and the natural order)
     const char *no_tma = std::getenv("IBDVM_NO_TMA");
-    const bool tma_off = no_tma && no_tma[0] == '1';
+    const bool tma_off = (no_tma && no_tma[0] == '1') || tree != nullptr; // trees: the generic tree sweep
     ctx->kst_h.resize(G.nv);
     for (int i = 0; i < G.nv; ++i) ctx->kst_h[i] = i;
     if (!tma_off && gas->precision == IBDVM_MIXED && tma_encoder_available()) {
@@ -602,6 +628,13 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
     check(ctx, cudaMemsetAsync(ctx->d_step_forces, 0, 4 * sizeof(double), ctx->stream), "clear");
     ctx->ctype = dalloc<uint8_t>(ctx, ctx->ncell, "cell classes");
     ctx->cmask = dalloc<uint8_t>(ctx, ctx->ncell, "cell flags");
+    if (tree) {
+      ctx->tree_nb = dalloc<int>(ctx, tnb.size(), "tree neighbours");
+      ctx->tree_lev = dalloc<int>(ctx, tlev.size(), "tree levels");
+      upload(ctx, ctx->tree_nb, tnb, "upload tree neighbours");
+      upload(ctx, ctx->tree_lev, tlev, "upload tree levels");
+      ctx->tree_nb_h = std::move(tnb);
+    }
     ctx->kst = dalloc<int>(ctx, G.nv, "velocity positions");
     upload(ctx, ctx->kst, ctx->kst_h, "upload velocity positions");
     if (ctx->oct_kc) {
@@ -694,8 +727,34 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
   return IBDVM_OK;
 }
 
+ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *vgrid,
+                               const ibdvm_gas_desc *gas, void *cuda_stream, ibdvm_ctx **out) {
+  return create_ctx(grid, nullptr, vgrid, gas, cuda_stream, out);
+}
+
+ibdvm_status ibdvm_create_tree(const ibdvm_grid_desc *root, const ibdvm_tree_desc *tree,
+                               const ibdvm_vgrid_desc *vgrid, const ibdvm_gas_desc *gas, void *cuda_stream,
+                               ibdvm_ctx **out) {
+  if (!tree) {
+    if (out) *out = nullptr;
+    return IBDVM_E_INVAL;
+  }
+  return create_ctx(root, tree, vgrid, gas, cuda_stream, out);
+}
+
+ibdvm_status ibdvm_tree_neighbours(const ibdvm_ctx *ctx, long long *nb) {
+  if (!ctx || !nb) return IBDVM_E_INVAL;
+  if (!ctx->tree) return IBDVM_E_STATE;
+  for (size_t i = 0; i < ctx->tree_nb_h.size(); ++i) nb[i] = ctx->tree_nb_h[i];
+  return IBDVM_OK;
+}
+
 ibdvm_status ibdvm_set_body(ibdvm_ctx *ctx, const ibdvm_body_desc *body) {
   IBDVM_GUARD(ctx)
+  if (ctx->tree) {
+    ctx->err = "set_body: a tree-refined grid carries no body";
+    return IBDVM_E_STATE;
+  }
   if (!body) {
     ctx->err = "body is NULL";
     return IBDVM_E_INVAL;
@@ -725,6 +784,10 @@ ibdvm_status ibdvm_set_body(ibdvm_ctx *ctx, const ibdvm_body_desc *body) {
 
 ibdvm_status ibdvm_set_domain(ibdvm_ctx *ctx, const ibdvm_domain_desc *d) {
   IBDVM_GUARD(ctx)
+  if (ctx->tree) {
+    ctx->err = "set_domain: a tree-refined grid keeps freestream domain faces";
+    return IBDVM_E_STATE;
+  }
   if (!d) {
     ctx->err = "domain description is NULL";
     return IBDVM_E_INVAL;

@@ -124,6 +124,12 @@ struct ibdvm_ctx {
   long long wall_off[7] = {};
   void *whalo = nullptr;
   bool tma_ok = false; // the TMA sweep was set up (it serves cases with and without domain walls)
+  // a tree-refined 2D grid: the cells are the leaves of a quadtree
+  bool tree = false;
+  int *tree_nb = nullptr;  // [leaf][4][2] face neighbours (sides 2a + (s > 0)), -1 none
+  int *tree_lev = nullptr; // [leaf] level
+  double tree_h0[2] = {0, 0};
+  std::vector<int> tree_nb_h;
   // host uploads of the state in cell ranges (a copy stream, one event per range)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_ev[ibdvm::kUploadParts + 1] = {};
@@ -165,6 +171,10 @@ void orthant_tables(const Geom &G, const std::vector<int> &kst, int nvp, int kc,
                     std::vector<uint8_t> &sign);
 // the driver's tensor-map encoder can be reached (the TMA sweeps can run)
 bool tma_encoder_available();
+// tree.cpp: the face neighbour tables of a tree-refined 2D grid; false with a
+// message when the leaves do not tile the domain or break the 2:1 rule
+bool build_tree_mesh(const ibdvm_grid_desc &root, const ibdvm_tree_desc &t, std::vector<int> &lev,
+                     std::vector<int> &nb, std::string &err);
 // TMA sweep of 3D FP32 cases (sweep3d_tma.cu)
 bool tma3_sweep_applicable(const ibdvm_ctx *ctx);
 int tma3_sweep_nchunk(const ibdvm_ctx *ctx);

@@ -353,6 +353,167 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
 }
 
 // ---------------------------------------------------------------------------
+// tree-refined 2D grids (the tree-based AMR meshes of Sec. 4.2-4.4; the paper
+// gives no scheme for them): finite volumes on the leaves of a 2:1-balanced
+// quadtree.  The slope of a cell along an axis is the van Leer limited slope
+// of the values on each side (the neighbour's, the mean of the two finer
+// neighbours', or the freestream halo) over the distances between centres
+// along the axis; the upwind cell supplies the face value f + s sigma h / 2;
+// a side with two finer neighbours takes the mean of their face values as
+// its inflow, so both cells of an interface see the same flux.  One time
+// step for all leaves (the CFL of the finest cell).
+// ---------------------------------------------------------------------------
+
+template <typename T> struct TreeArgs {
+  SweepArgs<T> S;
+  const int *__restrict__ nb;  // [leaf][4][2]: face neighbours, sides 2a + (s > 0); -1 none
+  const int *__restrict__ lev; // [leaf]
+  double h0[2];                // edge of a root cell along x and y
+};
+
+// the value on side (a, s) of leaf c as its slope sees it, component m, and
+// the distance to it along a
+template <typename T, int NC>
+__device__ __forceinline__ T tree_side(const TreeArgs<T> &A, long long c, T hc, int a, int s, int k, int m, T &dist) {
+  const int *nb = A.nb + c * 8 + (2 * a + (s > 0)) * 2;
+  const int n0 = nb[0], n1 = nb[1];
+  if (n0 < 0) {
+    dist = hc;
+    return A.S.finf[(size_t)k * NC + m];
+  }
+  dist = T(0.5) * (hc + (T)(A.h0[a] / (double)(1 << A.lev[n0])));
+  const T v0 = A.S.f[((size_t)n0 * A.S.nvp + k) * NC + m];
+  if (n1 < 0) return v0;
+  return T(0.5) * (v0 + A.S.f[((size_t)n1 * A.S.nvp + k) * NC + m]);
+}
+
+// the face value on side (a, s) of leaf c, component m (Eq. reconstruction
+// with the limited slope over the centre distances)
+template <typename T, int NC>
+__device__ __forceinline__ T tree_face(const TreeArgs<T> &A, long long c, int a, int s, int k, int m) {
+  const T hc = (T)(A.h0[a] / (double)(1 << A.lev[c]));
+  const T fc = A.S.f[((size_t)c * A.S.nvp + k) * NC + m];
+  T dm, dp;
+  const T fm = tree_side<T, NC>(A, c, hc, a, -1, k, m, dm);
+  const T fp = tree_side<T, NC>(A, c, hc, a, +1, k, m, dp);
+  const T sig = vanleer((fc - fm) / dm, (fp - fc) / dp);
+  return fc + sig * (T(s) * T(0.5) * hc);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) tree_sweep_kernel(TreeArgs<T> TA) {
+  static_assert(D == 2, "tree-refined grids are 2D");
+  constexpr int NC = Dims<D>::NC;
+  constexpr int NM = Dims<D>::NM;
+  const SweepArgs<T> &A = TA.S;
+  __shared__ double red[kCellsPerBlock][2][NM];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long long c = (long long)blockIdx.x * kCellsPerBlock + ty;
+  const int chunk = blockIdx.y;
+  const bool active = c < A.ncell;
+  Acc<T> acc[NM];
+  if (active) {
+    const T *M = A.mac;
+    T U[3], q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      U[a] = M[c * kMac + kU0 + a];
+      q[a] = M[c * kMac + kQ0 + a];
+    }
+    const T pre = M[c * kMac + kPre], invT = M[c * kMac + kInvT], halfT = M[c * kMac + kHalfT];
+    const T shA = M[c * kMac + kShA], dtau = M[c * kMac + kDtTau];
+    const T hc[2] = {(T)(TA.h0[0] / (double)(1 << TA.lev[c])), (T)(TA.h0[1] / (double)(1 << TA.lev[c]))};
+    for (int j = 0; j < A.kloop; ++j) {
+      const int iv = (chunk * A.kloop + j) * kThreadsPerCell + tx;
+      if (iv >= A.nv) break;
+      const int k = A.kst[iv];
+      T fc[NC];
+      load_nc<T, NC>(A.f + ((size_t)c * A.nvp + k) * NC, fc);
+      T cv[3] = {T(0), T(0), T(0)};
+      T c2 = T(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        cv[a] = A.xi[a * A.nvp + k] - U[a];
+        c2 += cv[a] * cv[a];
+      }
+      T div[NC];
+#pragma unroll
+      for (int m = 0; m < NC; ++m) div[m] = T(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const T xa = A.xi[a * A.nvp + k];
+        if (xa == T(0)) continue;
+        const int s = (xa > T(0)) ? 1 : -1; // the downwind side
+        const int *nb = TA.nb + c * 8 + (2 * a + (-s > 0)) * 2;
+        const int u0 = nb[0], u1 = nb[1];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+          const T fout = tree_face<T, NC>(TA, c, a, s, k, m);
+          T fin;
+          if (u0 < 0)
+            fin = A.finf[(size_t)k * NC + m]; // the halo: its value, zero slope
+          else if (u1 < 0)
+            fin = tree_face<T, NC>(TA, u0, a, s, k, m);
+          else
+            fin = T(0.5) * (tree_face<T, NC>(TA, u0, a, s, k, m) + tree_face<T, NC>(TA, u1, a, s, k, m));
+          div[m] += fabs(xa) * (fout - fin) / hc[a];
+        }
+      }
+      // Shakhov equilibrium (Sec. 4 reduced forms)
+      T cq = T(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) cq += cv[a] * q[a];
+      const T e = pre * exp_t(-c2 * invT);
+      const T corr = shA * cq;
+      const T tc = T(2) * c2 * invT;
+      const T H = e * (T(1) + corr * (tc - T(4)));
+      const T B = halfT * e * (T(1) + corr * (tc - T(2)));
+      T fo[NC];
+      fo[0] = fc[0] - A.dt * div[0] + dtau * (H - fc[0]);
+      fo[NC - 1] = fc[NC - 1] - A.dt * div[NC - 1] + dtau * (B - fc[NC - 1]);
+      T *dst = A.fn + ((size_t)c * A.nvp + k) * NC;
+#pragma unroll
+      for (int m = 0; m < NC; ++m) dst[m] = fo[m];
+      // moments about the current bulk velocity: c' = xi - U^n
+      const T wk = A.w[k];
+      const T wh = wk * fo[0];
+      const T wb = wk * fo[NC - 1];
+      const T e2 = c2 * wh + wb;
+      acc[0].add(wh);
+      acc[1].add(cv[0] * wh);
+      acc[2].add(cv[1] * wh);
+      acc[3].add(e2);
+      acc[4].add(cv[0] * cv[0] * wh);
+      acc[5].add(cv[0] * cv[1] * wh);
+      acc[6].add(cv[1] * cv[1] * wh);
+      acc[7].add(cv[0] * e2);
+      acc[8].add(cv[1] * e2);
+    }
+  }
+  // reduce the moment sums of each leaf over its 64 threads (two warps)
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    T h = acc[m].hi(), l = acc[m].lo();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T oh = shfl_down(h, o), ol = shfl_down(l, o);
+      Acc<T> t;
+      t.s = h;
+      if constexpr (sizeof(T) == 4) t.c = l;
+      t.merge(oh, ol);
+      h = t.hi();
+      l = t.lo();
+    }
+    if ((tx & 31) == 0) red[ty][tx >> 5][m] = (double)h + (double)l;
+  }
+  __syncthreads();
+  if (c < A.ncell && tx < NM) {
+    double v = active ? red[ty][0][tx] + red[ty][1][tx] : 0.0;
+    A.part[((size_t)chunk * NM + tx) * A.ncell + c] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // moments of a stored state, without transport (after a state is loaded or a
 // body is set): one warp per cell reads the cell's row of velocities with
 // 16-byte loads, several in flight per lane; plain sums over the velocities of
@@ -1446,6 +1607,23 @@ template <typename T, int D> cudaError_t sweep_t(ibdvm_ctx *ctx, int update, int
   return cudaGetLastError();
 }
 
+template <typename T, int D> cudaError_t tree_sweep_t(ibdvm_ctx *ctx) {
+  if constexpr (D != 2) {
+    return cudaErrorNotSupported;
+  } else {
+    TreeArgs<T> A{};
+    A.S = sweep_args<T>(ctx, 1, 1);
+    A.nb = ctx->tree_nb;
+    A.lev = ctx->tree_lev;
+    A.h0[0] = ctx->tree_h0[0];
+    A.h0[1] = ctx->tree_h0[1];
+    dim3 block(kThreadsPerCell, kCellsPerBlock);
+    dim3 grid((unsigned)((ctx->ncell + kCellsPerBlock - 1) / kCellsPerBlock), (unsigned)ctx->nchunk);
+    tree_sweep_kernel<T, D><<<grid, block, 0, ctx->stream>>>(A);
+    return cudaGetLastError();
+  }
+}
+
 // arguments of the finalize kernel for moment buffer parity wcur
 template <typename T, typename P>
 FinalArgs<T, P> final_args(const ibdvm_ctx *ctx, int wcur, bool shift, bool residual, const P *part, int nchunk) {
@@ -1751,7 +1929,9 @@ cudaError_t launch_sweep(ibdvm_ctx *ctx) {
     {
       Timed tm(ctx, kKSweep);
       ctx->kernel_launches[kKSweep] += 1;
-      e = tma ? (D == 2 ? tma_sweep_launch(ctx) : tma3_sweep_launch(ctx)) : sweep_t<T, D>(ctx, 1, 1);
+      e = ctx->tree ? tree_sweep_t<T, D>(ctx)
+          : tma     ? (D == 2 ? tma_sweep_launch(ctx) : tma3_sweep_launch(ctx))
+                    : sweep_t<T, D>(ctx, 1, 1);
     }
     if (e != cudaSuccess) return e;
     ctx->cur = 1 - ctx->cur;

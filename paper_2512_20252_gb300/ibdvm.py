@@ -43,6 +43,11 @@ class GridDesc(ctypes.Structure):
                 ("hi", ctypes.c_double * 3)]
 
 
+class TreeDesc(ctypes.Structure):
+    _fields_ = [("nleaf", ctypes.c_int), ("maxlevel", ctypes.c_int), ("level", ctypes.POINTER(ctypes.c_int)),
+                ("ix", ctypes.POINTER(ctypes.c_int)), ("iy", ctypes.POINTER(ctypes.c_int))]
+
+
 class VGridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("rule", ctypes.c_int), ("nodes", ctypes.POINTER(ctypes.c_double) * 3)]
@@ -117,6 +122,9 @@ _S = ctypes.c_int
 SIGNATURES = {
     "ibdvm_create_grid": ([ctypes.POINTER(GridDesc), ctypes.POINTER(VGridDesc),
                            ctypes.POINTER(GasDesc), _V, ctypes.POINTER(_V)], _S),
+    "ibdvm_create_tree": ([ctypes.POINTER(GridDesc), ctypes.POINTER(TreeDesc), ctypes.POINTER(VGridDesc),
+                           ctypes.POINTER(GasDesc), _V, ctypes.POINTER(_V)], _S),
+    "ibdvm_tree_neighbours": ([_V, _LL], _S),
     "ibdvm_set_body": ([_V, ctypes.POINTER(BodyDesc)], _S),
     "ibdvm_step": ([_V, ctypes.c_int, _D], _S),
     "ibdvm_moments": ([_V, _D, _D, _U8], _S),
@@ -393,8 +401,20 @@ class Solver:
         self.case = dict(case)
         g, v, s, b, keep = descriptors(case)
         h = _V()
-        st = self.lib.ibdvm_create_grid(ctypes.byref(g), ctypes.byref(v), ctypes.byref(s),
-                                        _V(stream or 0), ctypes.byref(h))
+        tree = case.get("tree")
+        if tree:
+            # a tree-refined 2D grid over the root grid case["n"] (ibdvm_create_tree)
+            arrs = [np.ascontiguousarray(np.asarray(tree[k], dtype=np.int32)) for k in ("level", "ix", "iy")]
+            keep = list(keep) + arrs
+            t = TreeDesc()
+            t.nleaf = arrs[0].size
+            t.maxlevel = int(tree["maxlevel"])
+            t.level, t.ix, t.iy = (a.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) for a in arrs)
+            st = self.lib.ibdvm_create_tree(ctypes.byref(g), ctypes.byref(t), ctypes.byref(v), ctypes.byref(s),
+                                            _V(stream or 0), ctypes.byref(h))
+        else:
+            st = self.lib.ibdvm_create_grid(ctypes.byref(g), ctypes.byref(v), ctypes.byref(s),
+                                            _V(stream or 0), ctypes.byref(h))
         if st != OK:
             raise IbdvmError(st, self.lib.ibdvm_last_error(None).decode())
         self.h = h
@@ -405,6 +425,12 @@ class Solver:
             self.set_domain(case["domain_walls"])
         self._keep = keep
         self.refresh_info()
+
+    def tree_neighbours(self) -> np.ndarray:
+        """Face neighbours [leaf][side 2a + (s > 0)][2] of a tree context (-1: none)."""
+        nb = np.zeros((self.ncell, 4, 2), dtype=np.int64)
+        self._check(self.lib.ibdvm_tree_neighbours(self.h, nb.ctypes.data_as(_LL)))
+        return nb
 
     def set_domain(self, walls):
         """Domain faces x-, x+, y-, y+, z-, z+: None = freestream halo,

@@ -1,0 +1,111 @@
+"""The tree-refined 2D grid (reading C28) through the C-ABI against the
+oracle's tree: the neighbour tables, the FP64 path within 1e-11 on f and W
+after several steps from a perturbed state, the mixed path within 1e-5 on W,
+a one-level tree against the uniform grid's GPU path, and the refusals."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_20252_gb300 import ibdvm
+from paper_2512_20252_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def rel_err(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _perturbed(o, seed, amp=0.2):
+    rng = np.random.default_rng(seed)
+    return o.get_f() * (1.0 + amp * rng.uniform(-1.0, 1.0, size=o.shape()))
+
+
+@pytest.mark.parametrize("metric,levels", [("point", 2), ("point", 3), ("x", 2)])
+def test_tree_fp64_against_the_oracle(metric, levels):
+    case = wl.tree_case(16, levels, nv=10, Ma=0.5, metric=metric,
+                        radii=[0.9, 0.5, 0.3][:levels] if metric == "x" else None)
+    o = oracle.OracleTree(case)
+    g = ibdvm.Solver(case)
+    assert g.ncell == o.nleaf and g.dt == pytest.approx(o.dt, rel=1e-14)
+    np.testing.assert_array_equal(g.tree_neighbours(), o.neighbours())
+    f0 = _perturbed(o, 7)
+    o.set_f(f0)
+    g.set_f(f0)
+    ro = o.step(6)
+    rg = g.step(6)
+    assert rel_err(g.get_f(), o.get_f()) < 1e-11
+    Wg, qg, t = g.moments()
+    Wo, qo = o.moments()
+    assert np.all(t == ibdvm.FLUID)
+    for i in range(4):
+        if np.abs(Wo[:, i]).max() > 1e-9:
+            assert rel_err(Wg[:, i], Wo[:, i]) < 1e-11, i
+    assert float(np.abs(qg - qo).max() / max(np.abs(qo).max(), 1e-3)) < 1e-8
+    assert rg == pytest.approx(ro, rel=1e-9)
+    g.close()
+
+
+def test_tree_mixed_against_the_oracle():
+    case = wl.tree_case(16, 2, nv=12, Ma=0.5, precision="mixed")
+    o = oracle.OracleTree(case)
+    g = ibdvm.Solver(case)
+    f0 = _perturbed(o, 11)
+    o.set_f(f0)
+    g.set_f(f0)
+    o.step(8)
+    g.step(8)
+    Wg, _, _ = g.moments()
+    Wo, _ = o.moments()
+    for i in range(4):
+        if np.abs(Wo[:, i]).max() > 1e-9:
+            assert rel_err(Wg[:, i], Wo[:, i]) < 1e-5, i
+    g.close()
+
+
+def test_one_level_tree_matches_the_uniform_gpu_path():
+    n = 24
+    case = wl._case(2, n, 2.0, 10, 4.5, 0.1, 0.4, {"kind": "none"})
+    u = ibdvm.Solver(case)
+    tree = {"maxlevel": 1, "level": [1] * (n * n), "ix": [i for _ in range(n) for i in range(n)],
+            "iy": [j for j in range(n) for _ in range(n)]}
+    t = ibdvm.Solver(dict(case, n=[n // 2, n // 2], tree=tree))
+    rng = np.random.default_rng(2)
+    f0 = u.get_f() * (1.0 + 0.2 * rng.uniform(-1.0, 1.0, size=u.get_f().shape))
+    u.set_f(f0)
+    t.set_f(f0)
+    u.step(5)
+    t.step(5)
+    assert rel_err(t.get_f(), u.get_f()) < 1e-12
+    u.close()
+    t.close()
+
+
+def test_tree_refusals():
+    case = wl.tree_case(8, 2, nv=6)
+    g = ibdvm.Solver(case)
+    with pytest.raises(ibdvm.IbdvmError):
+        g.set_domain(wl.box_walls(2, 1.0))
+    F, Q, CD, CL = g.forces()
+    assert np.all(F == 0.0) and Q == 0.0
+    g.close()
+    bad = dict(case["tree"])
+    bad["level"] = list(bad["level"])[1:]
+    bad["ix"] = list(bad["ix"])[1:]
+    bad["iy"] = list(bad["iy"])[1:]
+    with pytest.raises(ibdvm.IbdvmError, match="hole"):
+        ibdvm.Solver(dict(case, tree=bad))
+    body = dict(case, body=wl.circle(0.3))
+    with pytest.raises(ibdvm.IbdvmError):
+        ibdvm.Solver(body)
