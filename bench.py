@@ -53,6 +53,7 @@ WORKLOADS = {
                                             fromlist=["x"]).naca_supersonic(precision=p),
     "cylinder_hypersonic": lambda p: __import__("paper_2512_20252_gb300.workloads",
                                                 fromlist=["x"]).cylinder_hypersonic(precision=p),
+    "tree_2d": lambda p: __import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).tree_2d(precision=p),
     "batched_2d": None,  # a list of cases: see bench_batch
     "served": None,      # a request stream: see bench_serve
 }
@@ -70,6 +71,9 @@ DESCRIPTIONS = {
                            "(central spacing 0.25), Kn=0.1, Ma=0.5",
     "cavity_64": "2D lid-driven cavity [0,1]^2 with a cylinder of diameter 0.25 at its centre, 64x64 cells, "
                  "100x100 trapezoid velocities on [-5,5]^2, diffuse walls at T_w=1, lid 0.15, Kn=0.075",
+    "tree_2d": "2D tree-refined grid: a 128x128 root on [-8,8]^2 refined around the origin to level 1 within 4, "
+               "2 within 2 and 3 within 1 (finest edge 1/64), 2:1 balanced, 45,436 leaves, 48x48 trapezoid "
+               "velocities on [-6,6]^2, Kn=0.1, Ma=0.5, no body",
     "batched_2d": "64 seeded 2D cases (seed 0): n ~ U{64..384} cells per axis on [-4,4]^2, m ~ U{16..40} "
                   "velocities per axis on [-6,6]^2, circle / ellipse (aspect U[1,3]) / NACA0012 (AoA U[0,10] deg), "
                   "Kn 10^U[-2,0], Ma U[0.1,0.8], mixed precision, one batch",
@@ -188,7 +192,8 @@ L2_BYTES = 129 * 1000 * 1000  # GB300 L2 cache
 
 SWEEP_KERNELS = {0: ("sweep_kernel", "paper_2512_20252_gb300/csrc/kernels.cu"),
                  1: ("sweep2d_tma_kernel", "paper_2512_20252_gb300/csrc/sweep_tma.cu"),
-                 2: ("sweep3d_tma_kernel", "paper_2512_20252_gb300/csrc/sweep3d_tma.cu")}
+                 2: ("sweep3d_tma_kernel", "paper_2512_20252_gb300/csrc/sweep3d_tma.cu"),
+                 3: ("tree_sweep_kernel", "paper_2512_20252_gb300/csrc/kernels.cu")}
 
 
 def pinned_moments(torch, s):
@@ -271,11 +276,24 @@ def dist_setup(nprocs: int):
 def cpu_sample_case(case: dict) -> dict:
     """A bounded sample of the workload for the CPU oracle: the same gas,
     body, velocity grid and domain on a coarser cell grid (48 cells per axis in
-    2D, 12 in 3D) so that one oracle step takes about a second."""
+    2D, 12 in 3D; a tree: a 16^2 root refined the same way) so that one oracle
+    step takes about a second."""
     c = dict(case)
-    c["n"] = [48] * 2 if case["dim"] == 2 else [12] * 3
     c["precision"] = "fp64"
+    if case.get("tree"):
+        from paper_2512_20252_gb300 import workloads
+
+        c["n"] = [16, 16]
+        c["tree"] = workloads.tree_leaves((16, 16), 3, case["lo"], case["hi"], (0.0, 0.0), [4.0, 2.0, 1.0])
+        return c
+    c["n"] = [48] * 2 if case["dim"] == 2 else [12] * 3
     return c
+
+
+def oracle_case(case: dict, threads: int):
+    import oracle
+
+    return oracle.OracleTree(case, threads=threads) if case.get("tree") else oracle.OracleCase(case, threads=threads)
 
 
 def host_cores() -> int:
@@ -288,7 +306,7 @@ def host_cores() -> int:
 def time_oracle(case: dict, budget_s: float, max_steps: int | None = None, threads: int = 1):
     import oracle
 
-    oc = oracle.OracleCase(case, threads=threads)
+    oc = oracle_case(case, threads)
     oc.step(1)  # warm
     steps, t0 = 0, time.perf_counter()
     while True:
@@ -330,7 +348,7 @@ def run_reference(args, world, rank):
     import oracle
 
     nth = host_cores()
-    oc = oracle.OracleCase(sample, threads=nth)
+    oc = oracle_case(sample, nth)
     for _ in range(max(args.warmup, 0)):
         oc.step(1)
     t0 = time.perf_counter()
@@ -373,7 +391,7 @@ def error_report(args):
     out = {}
     for prec in ("fp64", "mixed"):
         case = _workload_case(args, args.workload, prec)
-        if args.cells:
+        if args.cells and not case.get("tree"):
             case["n"] = [args.cells] * case["dim"]
         s = ibdvm.Solver(case, stream=torch.cuda.Stream().cuda_stream)
         res = s.step(args.error_report)
@@ -668,7 +686,7 @@ def measure_case(args, workload, world, rank, local, pg, with_cpu=True):
     from paper_2512_20252_gb300 import ibdvm
 
     case = _workload_case(args, workload, args.precision)
-    if args.cells:
+    if args.cells and not case.get("tree"):
         case["n"] = [args.cells] * case["dim"]
     stream = torch.cuda.Stream()
     solver = ibdvm.Solver(case, stream=stream.cuda_stream)
@@ -755,7 +773,8 @@ def measure_case(args, workload, world, rank, local, pg, with_cpu=True):
                 "traffic": profiled_traffic(kname, ksrc, pairs),
                 "kernel": kname, "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms / max(sweep_n, 1)}
-    fpp = profiled_fp64_flops_per_pair(int(info.dim)) if args.precision == "fp64" else None
+    fpp = (profiled_fp64_flops_per_pair(int(info.dim))
+           if args.precision == "fp64" and not case.get("tree") else None)
     if fpp and sweep_n:
         # the FP64 path is bound by GB300's FP64 arithmetic rate, not by HBM:
         # its roof is the FMA rate measured now on this GPU (clocks sampled)

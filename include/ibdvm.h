@@ -156,7 +156,8 @@ typedef struct {
   long long steps_done;
   size_t device_bytes;
   int sweep_variant; /* 0: plain sweep (kernels.cu), 1: TMA-staged 2D FP32 sweep (sweep_tma.cu),
-                        2: TMA-staged 3D FP32 sweep (sweep3d_tma.cu) */
+                        2: TMA-staged 3D FP32 sweep (sweep3d_tma.cu), 3: the sweep of a
+                        tree-refined grid (kernels.cu) */
 } ibdvm_info;
 
 /* Creates a context: the uniform Cartesian grid and the discrete velocity

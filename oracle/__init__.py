@@ -485,6 +485,7 @@ class OracleTree:
         s = np.zeros(3, dtype=np.int64)
         self.lib.or_tree_sizes(self.h, s.ctypes.data_as(_LL))
         self.nleaf, self.nvel, self.ncomp = (int(x) for x in s)
+        self.ncell = self.nfluid = self.nleaf
         self.dim = 2
 
     def __del__(self):

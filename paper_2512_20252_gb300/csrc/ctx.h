@@ -127,7 +127,7 @@ struct ibdvm_ctx {
   // a tree-refined 2D grid: the cells are the leaves of a quadtree
   bool tree = false;
   int *tree_nb = nullptr;  // [leaf][4][2] face neighbours (sides 2a + (s > 0)), -1 none
-  int *tree_lev = nullptr; // [leaf] level
+  double *tree_geo = nullptr; // [leaf][axis]{1/d-, 1/d+, h/2, 1/h}
   double tree_h0[2] = {0, 0};
   std::vector<int> tree_nb_h;
   // host uploads of the state in cell ranges (a copy stream, one event per range)

@@ -29,6 +29,7 @@
 #include <type_traits>
 
 #include "ctx.h"
+#include "tma_sync.cuh"
 
 namespace ibdvm {
 namespace {
@@ -158,10 +159,32 @@ template <typename T> struct SweepArgs {
   HaloArgs<T> H;
 };
 
+// the NC components of one (cell, velocity): a vector access for (h, b) pairs
 template <typename T, int NC>
 __device__ __forceinline__ void load_nc(const T *p, T *o) {
+  if constexpr (NC == 2 && sizeof(T) == 8) {
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+  } else if constexpr (NC == 2 && sizeof(T) == 4) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+  } else {
 #pragma unroll
-  for (int m = 0; m < NC; ++m) o[m] = p[m];
+    for (int m = 0; m < NC; ++m) o[m] = p[m];
+  }
+}
+template <typename T, int NC>
+__device__ __forceinline__ void store_nc(T *p, const T *o) {
+  if constexpr (NC == 2 && sizeof(T) == 8) {
+    *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+  } else if constexpr (NC == 2 && sizeof(T) == 4) {
+    *reinterpret_cast<float2 *>(p) = make_float2(o[0], o[1]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < NC; ++m) p[m] = o[m];
+  }
 }
 
 // value of the cell across face (a, s) of fluid cell c, as c sees it: the
@@ -362,43 +385,79 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
 // a side with two finer neighbours takes the mean of their face values as
 // its inflow, so both cells of an interface see the same flux.  One time
 // step for all leaves (the CFL of the finest cell).
+//
+// The geometry is static: the host lists for every leaf and axis the
+// reciprocal centre distances to both sides, half the edge and its
+// reciprocal.  A block takes four leaves; before its velocity loop it builds
+// in shared memory, per leaf and axis, the stencil of the leaf itself and of
+// each upwind neighbour on either side, so that the loop holds no division
+// of the geometry and no lookup of levels.  The velocities of tree cases are
+// stored grouped by quadrant, so the threads of a warp share their upwind
+// sides and take the same branches.
 // ---------------------------------------------------------------------------
 
 template <typename T> struct TreeArgs {
   SweepArgs<T> S;
-  const int *__restrict__ nb;  // [leaf][4][2]: face neighbours, sides 2a + (s > 0); -1 none
-  const int *__restrict__ lev; // [leaf]
-  double h0[2];                // edge of a root cell along x and y
+  const int *__restrict__ nb;     // [leaf][4][2]: face neighbours, sides 2a + (s > 0); -1 none
+  const double *__restrict__ geo; // [leaf][axis]{1/d-, 1/d+, h/2, 1/h}: centre distances, edge
 };
 
-// the value on side (a, s) of leaf c as its slope sees it, component m, and
-// the distance to it along a
+// the stencil of one cell along one axis: the rows [nvp][NC] of the cell and
+// of its neighbours on the - and + sides (the second null for a single
+// neighbour; the freestream's row, second null, at the domain edge), the
+// reciprocal centre distances to both sides and the edge.  `mut` marks an
+// upwind neighbour u of leaf c that is c's only neighbour on that side and
+// has c as its only neighbour on the other: u's value and the value on its
+// side towards c are then c's side value and c's own value.
+template <typename T> struct __align__(16) TreeStencil {
+  const T *c, *m0, *m1, *p0, *p1;
+  T rdm, rdp, h;
+  int mut;
+};
+
+// the value on one side of a cell as its slope sees it: the neighbour's, or
+// the mean of the two finer neighbours'
 template <typename T, int NC>
-__device__ __forceinline__ T tree_side(const TreeArgs<T> &A, long long c, T hc, int a, int s, int k, int m, T &dist) {
-  const int *nb = A.nb + c * 8 + (2 * a + (s > 0)) * 2;
-  const int n0 = nb[0], n1 = nb[1];
-  if (n0 < 0) {
-    dist = hc;
-    return A.S.finf[(size_t)k * NC + m];
+__device__ __forceinline__ void tree_side_value(const T *r0, const T *r1, int k, T *v) {
+  load_nc<T, NC>(r0 + (size_t)k * NC, v);
+  if (r1) {
+    T w[NC];
+    load_nc<T, NC>(r1 + (size_t)k * NC, w);
+#pragma unroll
+    for (int m = 0; m < NC; ++m) v[m] = T(0.5) * (v[m] + w[m]);
   }
-  dist = T(0.5) * (hc + (T)(A.h0[a] / (double)(1 << A.lev[n0])));
-  const T v0 = A.S.f[((size_t)n0 * A.S.nvp + k) * NC + m];
-  if (n1 < 0) return v0;
-  return T(0.5) * (v0 + A.S.f[((size_t)n1 * A.S.nvp + k) * NC + m]);
 }
 
-// the face value on side (a, s) of leaf c, component m (Eq. reconstruction
-// with the limited slope over the centre distances)
+// the face value on side s of a cell of value fc with side values fm, fp:
+// the limited slope over the centre distances times s h / 2
 template <typename T, int NC>
-__device__ __forceinline__ T tree_face(const TreeArgs<T> &A, long long c, int a, int s, int k, int m) {
-  const T hc = (T)(A.h0[a] / (double)(1 << A.lev[c]));
-  const T fc = A.S.f[((size_t)c * A.S.nvp + k) * NC + m];
-  T dm, dp;
-  const T fm = tree_side<T, NC>(A, c, hc, a, -1, k, m, dm);
-  const T fp = tree_side<T, NC>(A, c, hc, a, +1, k, m, dp);
-  const T sig = vanleer((fc - fm) / dm, (fp - fc) / dp);
-  return fc + sig * (T(s) * T(0.5) * hc);
+__device__ __forceinline__ void tree_face_value(const TreeStencil<T> &S, const T *fc, const T *fm, const T *fp, T s,
+                                                T *out) {
+  const T sh = s * (T(0.5) * S.h);
+#pragma unroll
+  for (int m = 0; m < NC; ++m) out[m] = fc[m] + vanleer((fc[m] - fm[m]) * S.rdm, (fp[m] - fc[m]) * S.rdp) * sh;
 }
+
+// FP32 (h, b) pairs: packed arithmetic, the limiter through the hardware
+// reciprocal (half the van Leer slope times the edge: h ab / (a + b))
+__device__ __forceinline__ float2 tree_side2(const float *r0, const float *r1, int k) {
+  const float2 v = reinterpret_cast<const float2 *>(r0)[k];
+  if (!r1) return v;
+  const float2 w = reinterpret_cast<const float2 *>(r1)[k];
+  return __fmul2_rn(__fadd2_rn(v, w), dev::dup(0.5f));
+}
+__device__ __forceinline__ float2 tree_face2(const TreeStencil<float> &S, float2 fc, float2 fm, float2 fp, float s) {
+  const float2 a = __fmul2_rn(dev::sub2(fc, fm), dev::dup(S.rdm));
+  const float2 b = __fmul2_rn(dev::sub2(fp, fc), dev::dup(S.rdp));
+  return __ffma2_rn(dev::dup(s * S.h), dev::vl_half2(a, b), fc);
+}
+// 2^x (the hardware base-2 exponential)
+__device__ __forceinline__ float tree_ex2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+constexpr float kTreeLog2e = 1.442695040888963407f;
 
 template <typename T, int D>
 __global__ void __launch_bounds__(kBlock) tree_sweep_kernel(TreeArgs<T> TA) {
@@ -407,11 +466,56 @@ __global__ void __launch_bounds__(kBlock) tree_sweep_kernel(TreeArgs<T> TA) {
   constexpr int NM = Dims<D>::NM;
   const SweepArgs<T> &A = TA.S;
   __shared__ double red[kCellsPerBlock][2][NM];
+  // per leaf: its own stencil along x and y, then the upwind neighbours'
+  // along axis a, side sd (0: -, 1: +), neighbour j at 2 + 4a + 2sd + j
+  __shared__ TreeStencil<T> st[kCellsPerBlock][10];
+  __shared__ int nup[kCellsPerBlock][4]; // neighbours on side 2a + sd: 0 (domain edge), 1 or 2
+  __shared__ T rh[kCellsPerBlock][2];    // 1 / h
   const int tx = threadIdx.x, ty = threadIdx.y;
   const long long c = (long long)blockIdx.x * kCellsPerBlock + ty;
   const int chunk = blockIdx.y;
   const bool active = c < A.ncell;
-  Acc<T> acc[NM];
+  if (active && tx < 10) {
+    int u, a, sd = 0;
+    if (tx < 2) {
+      a = tx;
+      u = (int)c;
+    } else {
+      const int t = tx - 2;
+      a = t >> 2;
+      sd = (t >> 1) & 1;
+      u = TA.nb[c * 8 + (2 * a + sd) * 2 + (t & 1)];
+    }
+    TreeStencil<T> S{};
+    if (u >= 0) {
+      auto row = [&](int i) { return (i < 0) ? A.finf : A.f + (size_t)i * A.nvp * NC; };
+      const int *nu = TA.nb + (size_t)u * 8 + 4 * a;
+      S.c = row(u);
+      S.m0 = row(nu[0]);
+      S.m1 = (nu[0] >= 0 && nu[1] >= 0) ? row(nu[1]) : nullptr;
+      S.p0 = row(nu[2]);
+      S.p1 = (nu[2] >= 0 && nu[3] >= 0) ? row(nu[3]) : nullptr;
+      const double *g = TA.geo + ((size_t)u * 2 + a) * 4;
+      S.rdm = (T)g[0];
+      S.rdp = (T)g[1];
+      S.h = (T)(2.0 * g[2]);
+      if (tx >= 2) {
+        const int *ncs = TA.nb + c * 8 + (2 * a + sd) * 2;     // c's side towards u
+        const int *nus = TA.nb + (size_t)u * 8 + (2 * a + 1 - sd) * 2; // u's side towards c
+        S.mut = (ncs[1] < 0 && nus[0] == (int)c && nus[1] < 0) ? 1 : 0;
+      }
+    }
+    st[ty][tx] = S;
+  } else if (active && tx < 14) {
+    const int *n = TA.nb + c * 8 + (tx - 10) * 2;
+    nup[ty][tx - 10] = (n[0] < 0) ? 0 : (n[1] < 0 ? 1 : 2);
+  } else if (active && tx < 16) {
+    rh[ty][tx - 14] = (T)TA.geo[((size_t)c * 2 + (tx - 14)) * 4 + 3];
+  }
+  __syncthreads();
+  T acc[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) acc[m] = T(0);
   if (active) {
     const T *M = A.mac;
     T U[3], q[3];
@@ -422,89 +526,159 @@ __global__ void __launch_bounds__(kBlock) tree_sweep_kernel(TreeArgs<T> TA) {
     }
     const T pre = M[c * kMac + kPre], invT = M[c * kMac + kInvT], halfT = M[c * kMac + kHalfT];
     const T shA = M[c * kMac + kShA], dtau = M[c * kMac + kDtTau];
-    const T hc[2] = {(T)(TA.h0[0] / (double)(1 << TA.lev[c])), (T)(TA.h0[1] / (double)(1 << TA.lev[c]))};
-    for (int j = 0; j < A.kloop; ++j) {
-      const int iv = (chunk * A.kloop + j) * kThreadsPerCell + tx;
-      if (iv >= A.nv) break;
-      const int k = A.kst[iv];
-      T fc[NC];
-      load_nc<T, NC>(A.f + ((size_t)c * A.nvp + k) * NC, fc);
-      T cv[3] = {T(0), T(0), T(0)};
-      T c2 = T(0);
+    const T *own = st[ty][0].c;
+    // the stored velocities of a tree case come first, padding after
+    const int kbeg = chunk * A.kloop * kThreadsPerCell;
+    const int kend = min(A.nv, kbeg + A.kloop * kThreadsPerCell);
+    if constexpr (std::is_same<T, float>::value) {
+      const float nl2 = -invT * kTreeLog2e;
+      const float2 *finf2 = reinterpret_cast<const float2 *>(A.finf);
+#pragma unroll 2
+      for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
+        const float2 f2 = reinterpret_cast<const float2 *>(own)[k];
+        float2 dv = make_float2(0.f, 0.f);
+        float cv[2], c2 = 0.f;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        cv[a] = A.xi[a * A.nvp + k] - U[a];
-        c2 += cv[a] * cv[a];
-      }
-      T div[NC];
-#pragma unroll
-      for (int m = 0; m < NC; ++m) div[m] = T(0);
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const T xa = A.xi[a * A.nvp + k];
-        if (xa == T(0)) continue;
-        const int s = (xa > T(0)) ? 1 : -1; // the downwind side
-        const int *nb = TA.nb + c * 8 + (2 * a + (-s > 0)) * 2;
-        const int u0 = nb[0], u1 = nb[1];
-#pragma unroll
-        for (int m = 0; m < NC; ++m) {
-          const T fout = tree_face<T, NC>(TA, c, a, s, k, m);
-          T fin;
-          if (u0 < 0)
-            fin = A.finf[(size_t)k * NC + m]; // the halo: its value, zero slope
-          else if (u1 < 0)
-            fin = tree_face<T, NC>(TA, u0, a, s, k, m);
-          else
-            fin = T(0.5) * (tree_face<T, NC>(TA, u0, a, s, k, m) + tree_face<T, NC>(TA, u1, a, s, k, m));
-          div[m] += fabs(xa) * (fout - fin) / hc[a];
+        for (int a = 0; a < 2; ++a) {
+          const float xa = A.xi[a * A.nvp + k];
+          cv[a] = xa - U[a];
+          c2 = fmaf(cv[a], cv[a], c2);
+          if (xa == 0.f) continue;
+          const float s = (xa > 0.f) ? 1.f : -1.f; // the downwind side
+          const int sd = (xa > 0.f) ? 0 : 1;       // the upwind side
+          const TreeStencil<float> &So = st[ty][a];
+          const float2 fm = tree_side2(So.m0, So.m1, k), fp = tree_side2(So.p0, So.p1, k);
+          const float2 fout = tree_face2(So, f2, fm, fp, s);
+          const int n = nup[ty][2 * a + sd];
+          float2 fin;
+          if (n == 0) {
+            fin = finf2[k]; // the halo: its value, zero slope
+          } else {
+            const TreeStencil<float> &S0 = st[ty][2 + 4 * a + 2 * sd];
+            if (S0.mut) {
+              const float2 fu = sd ? fp : fm;
+              const float2 far = sd ? tree_side2(S0.p0, S0.p1, k) : tree_side2(S0.m0, S0.m1, k);
+              fin = tree_face2(S0, fu, sd ? f2 : far, sd ? far : f2, s);
+            } else {
+              fin = tree_face2(S0, reinterpret_cast<const float2 *>(S0.c)[k], tree_side2(S0.m0, S0.m1, k),
+                               tree_side2(S0.p0, S0.p1, k), s);
+              if (n == 2) {
+                const TreeStencil<float> &S1 = st[ty][3 + 4 * a + 2 * sd];
+                const float2 g1 = tree_face2(S1, reinterpret_cast<const float2 *>(S1.c)[k],
+                                             tree_side2(S1.m0, S1.m1, k), tree_side2(S1.p0, S1.p1, k), s);
+                fin = __fmul2_rn(__fadd2_rn(fin, g1), dev::dup(0.5f));
+              }
+            }
+          }
+          dv = __ffma2_rn(dev::dup(fabsf(xa) * rh[ty][a]), dev::sub2(fout, fin), dv);
         }
+        // Shakhov equilibrium (Sec. 4 reduced forms)
+        const float cq = fmaf(cv[1], q[1], cv[0] * q[0]);
+        const float e = pre * tree_ex2(c2 * nl2);
+        const float corr = shA * cq;
+        const float tc = 2.f * c2 * invT;
+        const float H = e * fmaf(corr, tc - 4.f, 1.f);
+        const float B = halfT * e * fmaf(corr, tc - 2.f, 1.f);
+        float fo[2];
+        fo[0] = f2.x - A.dt * dv.x + dtau * (H - f2.x);
+        fo[1] = f2.y - A.dt * dv.y + dtau * (B - f2.y);
+        reinterpret_cast<float2 *>(A.fn)[(size_t)c * A.nvp + k] = make_float2(fo[0], fo[1]);
+        // moments about the current bulk velocity: c' = xi - U^n
+        const float wk = A.w[k];
+        const float wh = wk * fo[0];
+        const float e2 = fmaf(c2, wh, wk * fo[1]);
+        acc[0] += wh;
+        acc[1] = fmaf(cv[0], wh, acc[1]);
+        acc[2] = fmaf(cv[1], wh, acc[2]);
+        acc[3] += e2;
+        acc[4] = fmaf(cv[0] * cv[0], wh, acc[4]);
+        acc[5] = fmaf(cv[0] * cv[1], wh, acc[5]);
+        acc[6] = fmaf(cv[1] * cv[1], wh, acc[6]);
+        acc[7] = fmaf(cv[0], e2, acc[7]);
+        acc[8] = fmaf(cv[1], e2, acc[8]);
       }
-      // Shakhov equilibrium (Sec. 4 reduced forms)
-      T cq = T(0);
+    } else {
+      for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
+        T fc[NC], div[NC];
+        T cv[3] = {T(0), T(0), T(0)};
+        T c2 = T(0);
+        load_nc<T, NC>(own + (size_t)k * NC, fc);
 #pragma unroll
-      for (int a = 0; a < D; ++a) cq += cv[a] * q[a];
-      const T e = pre * exp_t(-c2 * invT);
-      const T corr = shA * cq;
-      const T tc = T(2) * c2 * invT;
-      const T H = e * (T(1) + corr * (tc - T(4)));
-      const T B = halfT * e * (T(1) + corr * (tc - T(2)));
-      T fo[NC];
-      fo[0] = fc[0] - A.dt * div[0] + dtau * (H - fc[0]);
-      fo[NC - 1] = fc[NC - 1] - A.dt * div[NC - 1] + dtau * (B - fc[NC - 1]);
-      T *dst = A.fn + ((size_t)c * A.nvp + k) * NC;
+        for (int m = 0; m < NC; ++m) div[m] = T(0);
 #pragma unroll
-      for (int m = 0; m < NC; ++m) dst[m] = fo[m];
-      // moments about the current bulk velocity: c' = xi - U^n
-      const T wk = A.w[k];
-      const T wh = wk * fo[0];
-      const T wb = wk * fo[NC - 1];
-      const T e2 = c2 * wh + wb;
-      acc[0].add(wh);
-      acc[1].add(cv[0] * wh);
-      acc[2].add(cv[1] * wh);
-      acc[3].add(e2);
-      acc[4].add(cv[0] * cv[0] * wh);
-      acc[5].add(cv[0] * cv[1] * wh);
-      acc[6].add(cv[1] * cv[1] * wh);
-      acc[7].add(cv[0] * e2);
-      acc[8].add(cv[1] * e2);
+        for (int a = 0; a < D; ++a) {
+          const T xa = A.xi[a * A.nvp + k];
+          cv[a] = xa - U[a];
+          c2 += cv[a] * cv[a];
+          if (xa == T(0)) continue;
+          const T s = (xa > T(0)) ? T(1) : T(-1);
+          const int sd = (xa > T(0)) ? 0 : 1;
+          const TreeStencil<T> &So = st[ty][a];
+          T fm[NC], fp[NC], fout[NC], fin[NC];
+          tree_side_value<T, NC>(So.m0, So.m1, k, fm);
+          tree_side_value<T, NC>(So.p0, So.p1, k, fp);
+          tree_face_value<T, NC>(So, fc, fm, fp, s, fout);
+          const int n = nup[ty][2 * a + sd];
+          if (n == 0) {
+            load_nc<T, NC>(A.finf + (size_t)k * NC, fin);
+          } else {
+            const TreeStencil<T> &S0 = st[ty][2 + 4 * a + 2 * sd];
+            T fu[NC], um[NC], up[NC];
+            load_nc<T, NC>(S0.c + (size_t)k * NC, fu);
+            tree_side_value<T, NC>(S0.m0, S0.m1, k, um);
+            tree_side_value<T, NC>(S0.p0, S0.p1, k, up);
+            tree_face_value<T, NC>(S0, fu, um, up, s, fin);
+            if (n == 2) {
+              const TreeStencil<T> &S1 = st[ty][3 + 4 * a + 2 * sd];
+              T g1[NC];
+              load_nc<T, NC>(S1.c + (size_t)k * NC, fu);
+              tree_side_value<T, NC>(S1.m0, S1.m1, k, um);
+              tree_side_value<T, NC>(S1.p0, S1.p1, k, up);
+              tree_face_value<T, NC>(S1, fu, um, up, s, g1);
+#pragma unroll
+              for (int m = 0; m < NC; ++m) fin[m] = T(0.5) * (fin[m] + g1[m]);
+            }
+          }
+          const T wa = fabs(xa) * rh[ty][a];
+#pragma unroll
+          for (int m = 0; m < NC; ++m) div[m] += wa * (fout[m] - fin[m]);
+        }
+        // Shakhov equilibrium (Sec. 4 reduced forms)
+        T cq = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) cq += cv[a] * q[a];
+        const T e = pre * exp_t(-c2 * invT);
+        const T corr = shA * cq;
+        const T tc = T(2) * c2 * invT;
+        const T H = e * (T(1) + corr * (tc - T(4)));
+        const T B = halfT * e * (T(1) + corr * (tc - T(2)));
+        T fo[NC];
+        fo[0] = fc[0] - A.dt * div[0] + dtau * (H - fc[0]);
+        fo[NC - 1] = fc[NC - 1] - A.dt * div[NC - 1] + dtau * (B - fc[NC - 1]);
+        store_nc<T, NC>(A.fn + ((size_t)c * A.nvp + k) * NC, fo);
+        // moments about the current bulk velocity: c' = xi - U^n
+        const T wk = A.w[k];
+        const T wh = wk * fo[0];
+        const T e2 = c2 * wh + wk * fo[NC - 1];
+        acc[0] += wh;
+        acc[1] += cv[0] * wh;
+        acc[2] += cv[1] * wh;
+        acc[3] += e2;
+        acc[4] += cv[0] * cv[0] * wh;
+        acc[5] += cv[0] * cv[1] * wh;
+        acc[6] += cv[1] * cv[1] * wh;
+        acc[7] += cv[0] * e2;
+        acc[8] += cv[1] * e2;
+      }
     }
   }
   // reduce the moment sums of each leaf over its 64 threads (two warps)
 #pragma unroll
   for (int m = 0; m < NM; ++m) {
-    T h = acc[m].hi(), l = acc[m].lo();
+    T v = acc[m];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      T oh = shfl_down(h, o), ol = shfl_down(l, o);
-      Acc<T> t;
-      t.s = h;
-      if constexpr (sizeof(T) == 4) t.c = l;
-      t.merge(oh, ol);
-      h = t.hi();
-      l = t.lo();
-    }
-    if ((tx & 31) == 0) red[ty][tx >> 5][m] = (double)h + (double)l;
+    for (int o = 16; o > 0; o >>= 1) v += shfl_down(v, o);
+    if ((tx & 31) == 0) red[ty][tx >> 5][m] = (double)v;
   }
   __syncthreads();
   if (c < A.ncell && tx < NM) {
@@ -1614,9 +1788,7 @@ template <typename T, int D> cudaError_t tree_sweep_t(ibdvm_ctx *ctx) {
     TreeArgs<T> A{};
     A.S = sweep_args<T>(ctx, 1, 1);
     A.nb = ctx->tree_nb;
-    A.lev = ctx->tree_lev;
-    A.h0[0] = ctx->tree_h0[0];
-    A.h0[1] = ctx->tree_h0[1];
+    A.geo = ctx->tree_geo;
     dim3 block(kThreadsPerCell, kCellsPerBlock);
     dim3 grid((unsigned)((ctx->ncell + kCellsPerBlock - 1) / kCellsPerBlock), (unsigned)ctx->nchunk);
     tree_sweep_kernel<T, D><<<grid, block, 0, ctx->stream>>>(A);

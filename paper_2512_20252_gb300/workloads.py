@@ -292,23 +292,33 @@ def tree_leaves(root, maxlevel, lo, hi, center, radii, metric="point"):
     nf = (nx0 << L, ny0 << L)
     lev = np.zeros(nf, dtype=np.int64)
 
-    def split_wanted(l, i, j):
-        h = 2.0 ** -l
-        xc = lo[0] + (i + 0.5) * hx0 * h
-        yc = lo[1] + (j + 0.5) * hy0 * h
-        if metric == "x":
-            return abs(xc - center[0]) <= radii[l]
-        if metric == "y":
-            return abs(yc - center[1]) <= radii[l]
-        return math.hypot(xc - center[0], yc - center[1]) <= radii[l]
+    def blocks(l):
+        """level map in blocks of level-l cells: (nx_l, s, ny_l, s)"""
+        s = 1 << (L - l)
+        return lev.reshape(nx0 << l, s, ny0 << l, s)
+
+    def uniform_at(l):
+        """level-l cells that are one leaf of level l"""
+        bl = blocks(l)
+        return (bl.min(axis=(1, 3)) == l) & (bl.max(axis=(1, 3)) == l)
+
+    def split(l, mask):
+        s = 1 << (L - l)
+        up = np.repeat(np.repeat(mask, s, axis=0), s, axis=1)
+        lev[up] = l + 1
 
     for l in range(L):
-        s = 1 << (L - l)  # finest cells per leaf side at level l
-        for i in range(nx0 << l):
-            for j in range(ny0 << l):
-                blk = lev[i * s:(i + 1) * s, j * s:(j + 1) * s]
-                if (blk == l).all() and split_wanted(l, i, j):
-                    blk[...] = l + 1
+        h = 2.0 ** -l
+        xc = lo[0] + (np.arange(nx0 << l) + 0.5) * hx0 * h
+        yc = lo[1] + (np.arange(ny0 << l) + 0.5) * hy0 * h
+        X, Y = np.meshgrid(xc, yc, indexing="ij")
+        if metric == "x":
+            near = np.abs(X - center[0]) <= radii[l]
+        elif metric == "y":
+            near = np.abs(Y - center[1]) <= radii[l]
+        else:
+            near = np.hypot(X - center[0], Y - center[1]) <= radii[l]
+        split(l, uniform_at(l) & near)
     # 2:1 balance across faces: raise a leaf whose face neighbour is two or more
     # levels finer (one level at a time, until nothing changes)
     changed = True
@@ -316,23 +326,22 @@ def tree_leaves(root, maxlevel, lo, hi, center, radii, metric="point"):
         changed = False
         for l in range(L):
             s = 1 << (L - l)
-            for i in range(nx0 << l):
-                for j in range(ny0 << l):
-                    blk = lev[i * s:(i + 1) * s, j * s:(j + 1) * s]
-                    if not (blk == l).all():
-                        continue
-                    finer = False
-                    if i > 0 and lev[i * s - 1, j * s:(j + 1) * s].max() >= l + 2:
-                        finer = True
-                    if (i + 1) * s < nf[0] and lev[(i + 1) * s, j * s:(j + 1) * s].max() >= l + 2:
-                        finer = True
-                    if j > 0 and lev[i * s:(i + 1) * s, j * s - 1].max() >= l + 2:
-                        finer = True
-                    if (j + 1) * s < nf[1] and lev[i * s:(i + 1) * s, (j + 1) * s].max() >= l + 2:
-                        finer = True
-                    if finer:
-                        blk[...] = l + 1
-                        changed = True
+            nxl, nyl = nx0 << l, ny0 << l
+            leaf = uniform_at(l)
+            # the largest level in the strip of finest cells beyond each face
+            big = np.zeros((nxl, nyl), dtype=bool)
+            first = lev[0::s, :].reshape(nxl, nyl, s).max(axis=2)   # x-first finest column of each block
+            last = lev[s - 1::s, :].reshape(nxl, nyl, s).max(axis=2)
+            big[1:, :] |= last[:-1, :] >= l + 2
+            big[:-1, :] |= first[1:, :] >= l + 2
+            firsty = lev[:, 0::s].reshape(nxl, s, nyl).max(axis=1)
+            lasty = lev[:, s - 1::s].reshape(nxl, s, nyl).max(axis=1)
+            big[:, 1:] |= lasty[:, :-1] >= l + 2
+            big[:, :-1] |= firsty[:, 1:] >= l + 2
+            m = leaf & big
+            if m.any():
+                split(l, m)
+                changed = True
     level, ix, iy = [], [], []
     for l in range(L + 1):
         s = 1 << (L - l)
@@ -354,4 +363,15 @@ def tree_case(root=16, maxlevel=2, L=2.0, nv=12, V=4.5, Kn=0.1, Ma=0.3, radii=No
         radii = [0.6 * L, 0.3 * L] + [0.3 * L * 0.5 ** i for i in range(1, maxlevel)]
     d = _case(2, root, L, nv, V, Kn, Ma, {"kind": "none"}, precision=precision, steps=steps)
     d["tree"] = tree_leaves((root, root), maxlevel, d["lo"], d["hi"], center, radii, metric)
+    return d
+
+
+def tree_2d(precision="mixed", steps=200):
+    """A tree-refined 2D grid at GB300 size: a root grid of 128^2 cells on
+    [-8,8]^2 refined around the origin to level 1 within 4, level 2 within 2
+    and level 3 within 1 (finest edge 1/64: the 1024^2 uniform grid's), 2:1
+    balanced (45,436 leaves), 48^2 velocities on [-6,6]^2, Kn 0.1, Ma 0.5, no
+    body (the tree's transport, relaxation and moments alone)."""
+    d = _case(2, 128, 8.0, 48, 6.0, 0.1, 0.5, {"kind": "none"}, precision=precision, steps=steps)
+    d["tree"] = tree_leaves((128, 128), 3, d["lo"], d["hi"], (0.0, 0.0), [4.0, 2.0, 1.0])
     return d
