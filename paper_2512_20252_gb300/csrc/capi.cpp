@@ -132,8 +132,9 @@ void free_all(ibdvm_ctx *ctx) {
   cfree_t(ctx->oct_sign);
   cfree_t(ctx->ctype);
   cfree_t(ctx->cmask);
-  cfree_t(ctx->tree_nb);
-  cfree_t(ctx->tree_geo);
+  cfree_t(ctx->tree_sti);
+  cfree_t(ctx->tree_stg);
+  cfree_t(ctx->tree_lrec);
   cfree_t(ctx->partf);
   cfree_t(ctx->d_forces);
   cfree_t(ctx->d_step_forces);
@@ -587,9 +588,11 @@ static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_des
       // trees: grouped by quadrant (x < 0 in bit 0, y < 0 in bit 1), packed,
       // so that the threads of a warp of the tree sweep share upwind sides
       int pos = 0;
-      for (int o = 0; o < 4; ++o)
+      for (int o = 0; o < 4; ++o) {
+        if (o > 0) ctx->tree_qb[o - 1] = pos;
         for (int i = 0; i < G.nv; ++i)
           if (((G.xi[3 * i] < 0.0) ? 1 : 0) + ((G.xi[3 * i + 1] < 0.0) ? 2 : 0) == o) ctx->kst_h[i] = pos++;
+      }
     }
     if (!tma_off && gas->precision == IBDVM_MIXED && tma_encoder_available()) {
       std::vector<int> kst;
@@ -637,26 +640,15 @@ static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_des
     ctx->ctype = dalloc<uint8_t>(ctx, ctx->ncell, "cell classes");
     ctx->cmask = dalloc<uint8_t>(ctx, ctx->ncell, "cell flags");
     if (tree) {
-      // per leaf and axis: the reciprocal centre distances to the - and +
-      // sides (the neighbour's centre, or h to the domain edge's halo), h / 2, 1 / h
-      const size_t nl = tlev.size();
-      std::vector<double> geo(nl * 8);
-      auto edge = [&](int leaf, int a) { return ctx->tree_h0[a] / static_cast<double>(1 << tlev[leaf]); };
-      for (size_t c = 0; c < nl; ++c)
-        for (int a = 0; a < 2; ++a) {
-          const double h = edge(static_cast<int>(c), a);
-          double *g = &geo[(c * 2 + a) * 4];
-          for (int sd = 0; sd < 2; ++sd) {
-            const int n0 = tnb[c * 8 + (2 * a + sd) * 2];
-            g[sd] = 1.0 / ((n0 < 0) ? h : 0.5 * (h + edge(n0, a)));
-          }
-          g[2] = 0.5 * h;
-          g[3] = 1.0 / h;
-        }
-      ctx->tree_nb = dalloc<int>(ctx, tnb.size(), "tree neighbours");
-      ctx->tree_geo = dalloc<double>(ctx, geo.size(), "tree geometry");
-      upload(ctx, ctx->tree_nb, tnb, "upload tree neighbours");
-      upload(ctx, ctx->tree_geo, geo, "upload tree geometry");
+      std::vector<int> sti, lrec;
+      std::vector<double> stg;
+      build_tree_stencils(tlev, tnb, ctx->tree_h0, sti, stg, lrec);
+      ctx->tree_sti = dalloc<int>(ctx, sti.size(), "tree stencils");
+      ctx->tree_stg = dalloc<double>(ctx, stg.size(), "tree stencil geometry");
+      ctx->tree_lrec = dalloc<int>(ctx, lrec.size(), "tree leaf records");
+      upload(ctx, ctx->tree_sti, sti, "upload tree stencils");
+      upload(ctx, ctx->tree_stg, stg, "upload tree stencil geometry");
+      upload(ctx, ctx->tree_lrec, lrec, "upload tree leaf records");
       ctx->tree_nb_h = std::move(tnb);
     }
     ctx->kst = dalloc<int>(ctx, G.nv, "velocity positions");

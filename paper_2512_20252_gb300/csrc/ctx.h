@@ -126,9 +126,11 @@ struct ibdvm_ctx {
   bool tma_ok = false; // the TMA sweep was set up (it serves cases with and without domain walls)
   // a tree-refined 2D grid: the cells are the leaves of a quadtree
   bool tree = false;
-  int *tree_nb = nullptr;  // [leaf][4][2] face neighbours (sides 2a + (s > 0)), -1 none
-  double *tree_geo = nullptr; // [leaf][axis]{1/d-, 1/d+, h/2, 1/h}
+  int *tree_sti = nullptr;    // [leaf][10][8] stencil rows and flags (build_tree_stencils)
+  double *tree_stg = nullptr; // [leaf][10][4] stencil geometry
+  int *tree_lrec = nullptr;   // [leaf][8] side counts, regular flag
   double tree_h0[2] = {0, 0};
+  int tree_qb[3] = {0, 0, 0}; // first stored velocity of the quadrants 1, 2, 3 (bit 0: x < 0, bit 1: y < 0)
   std::vector<int> tree_nb_h;
   // host uploads of the state in cell ranges (a copy stream, one event per range)
   cudaStream_t copy_stream = nullptr;
@@ -175,6 +177,8 @@ bool tma_encoder_available();
 // message when the leaves do not tile the domain or break the 2:1 rule
 bool build_tree_mesh(const ibdvm_grid_desc &root, const ibdvm_tree_desc &t, std::vector<int> &lev,
                      std::vector<int> &nb, std::string &err);
+void build_tree_stencils(const std::vector<int> &lev, const std::vector<int> &nb, const double h0[2],
+                         std::vector<int> &sti, std::vector<double> &stg, std::vector<int> &lrec);
 // TMA sweep of 3D FP32 cases (sweep3d_tma.cu)
 bool tma3_sweep_applicable(const ibdvm_ctx *ctx);
 int tma3_sweep_nchunk(const ibdvm_ctx *ctx);

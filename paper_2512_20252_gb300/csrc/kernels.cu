@@ -398,8 +398,10 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
 
 template <typename T> struct TreeArgs {
   SweepArgs<T> S;
-  const int *__restrict__ nb;     // [leaf][4][2]: face neighbours, sides 2a + (s > 0); -1 none
-  const double *__restrict__ geo; // [leaf][axis]{1/d-, 1/d+, h/2, 1/h}: centre distances, edge
+  const int4 *__restrict__ sti;     // [leaf][10][2]: stencil rows (-1 none, -2 the halo) and the mutual flag
+  const double2 *__restrict__ stg;  // [leaf][10][2]: 1/d-, 1/d+, h, 1/h (own entries)
+  const int4 *__restrict__ lrec;    // [leaf][2]: leaves on sides 0..3, regular flag
+  int qb[3];                      // first stored position of the quadrants 1, 2, 3 (bit 0: x < 0, bit 1: y < 0)
 };
 
 // the stencil of one cell along one axis: the rows [nvp][NC] of the cell and
@@ -459,8 +461,10 @@ __device__ __forceinline__ float tree_ex2(float x) {
 }
 constexpr float kTreeLog2e = 1.442695040888963407f;
 
+// FP32: four blocks of 256 threads per SM (the loop waits on gathers from L2
+// and HBM: resident warps hide it); FP64, bound by its arithmetic: two
 template <typename T, int D>
-__global__ void __launch_bounds__(kBlock) tree_sweep_kernel(TreeArgs<T> TA) {
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_kernel(TreeArgs<T> TA) {
   static_assert(D == 2, "tree-refined grids are 2D");
   constexpr int NC = Dims<D>::NC;
   constexpr int NM = Dims<D>::NM;
@@ -471,46 +475,38 @@ __global__ void __launch_bounds__(kBlock) tree_sweep_kernel(TreeArgs<T> TA) {
   __shared__ TreeStencil<T> st[kCellsPerBlock][10];
   __shared__ int nup[kCellsPerBlock][4]; // neighbours on side 2a + sd: 0 (domain edge), 1 or 2
   __shared__ T rh[kCellsPerBlock][2];    // 1 / h
+  __shared__ int fast[kCellsPerBlock];   // one neighbour of the leaf's own level on every side
   const int tx = threadIdx.x, ty = threadIdx.y;
   const long long c = (long long)blockIdx.x * kCellsPerBlock + ty;
   const int chunk = blockIdx.y;
   const bool active = c < A.ncell;
   if (active && tx < 10) {
-    int u, a, sd = 0;
-    if (tx < 2) {
-      a = tx;
-      u = (int)c;
-    } else {
-      const int t = tx - 2;
-      a = t >> 2;
-      sd = (t >> 1) & 1;
-      u = TA.nb[c * 8 + (2 * a + sd) * 2 + (t & 1)];
-    }
-    TreeStencil<T> S{};
-    if (u >= 0) {
-      auto row = [&](int i) { return (i < 0) ? A.finf : A.f + (size_t)i * A.nvp * NC; };
-      const int *nu = TA.nb + (size_t)u * 8 + 4 * a;
-      S.c = row(u);
-      S.m0 = row(nu[0]);
-      S.m1 = (nu[0] >= 0 && nu[1] >= 0) ? row(nu[1]) : nullptr;
-      S.p0 = row(nu[2]);
-      S.p1 = (nu[2] >= 0 && nu[3] >= 0) ? row(nu[3]) : nullptr;
-      const double *g = TA.geo + ((size_t)u * 2 + a) * 4;
-      S.rdm = (T)g[0];
-      S.rdp = (T)g[1];
-      S.h = (T)(2.0 * g[2]);
-      if (tx >= 2) {
-        const int *ncs = TA.nb + c * 8 + (2 * a + sd) * 2;     // c's side towards u
-        const int *nus = TA.nb + (size_t)u * 8 + (2 * a + 1 - sd) * 2; // u's side towards c
-        S.mut = (ncs[1] < 0 && nus[0] == (int)c && nus[1] < 0) ? 1 : 0;
-      }
-    }
+    // the stencil tables built on the host (one pass, no chain of lookups)
+    const size_t e = ((size_t)c * 10 + tx) * 2;
+    const int4 i0 = TA.sti[e], i1 = TA.sti[e + 1];
+    const double2 g0 = TA.stg[e], g1 = TA.stg[e + 1];
+    auto row = [&](int i) -> const T * {
+      return (i >= 0) ? A.f + (size_t)i * A.nvp * NC : (i == -2 ? A.finf : nullptr);
+    };
+    TreeStencil<T> S;
+    S.c = row(i0.x);
+    S.m0 = row(i0.y);
+    S.m1 = row(i0.z);
+    S.p0 = row(i0.w);
+    S.p1 = row(i1.x);
+    S.mut = i1.y;
+    S.rdm = (T)g0.x;
+    S.rdp = (T)g0.y;
+    S.h = (T)g1.x;
     st[ty][tx] = S;
-  } else if (active && tx < 14) {
-    const int *n = TA.nb + c * 8 + (tx - 10) * 2;
-    nup[ty][tx - 10] = (n[0] < 0) ? 0 : (n[1] < 0 ? 1 : 2);
-  } else if (active && tx < 16) {
-    rh[ty][tx - 14] = (T)TA.geo[((size_t)c * 2 + (tx - 14)) * 4 + 3];
+    if (tx < 2) rh[ty][tx] = (T)g1.y;
+  } else if (active && tx == 10) {
+    const int4 r0 = TA.lrec[(size_t)c * 2], r1 = TA.lrec[(size_t)c * 2 + 1];
+    nup[ty][0] = r0.x;
+    nup[ty][1] = r0.y;
+    nup[ty][2] = r0.z;
+    nup[ty][3] = r0.w;
+    fast[ty] = r1.x;
   }
   __syncthreads();
   T acc[NM];
@@ -533,7 +529,64 @@ __global__ void __launch_bounds__(kBlock) tree_sweep_kernel(TreeArgs<T> TA) {
     if constexpr (std::is_same<T, float>::value) {
       const float nl2 = -invT * kTreeLog2e;
       const float2 *finf2 = reinterpret_cast<const float2 *>(A.finf);
-#pragma unroll 2
+      // relaxation, the store of f^{n+1} and the moment sums of one velocity
+      auto finish = [&](int k, float2 f2, float2 dv, const float *cv, float c2, float wk) {
+        // Shakhov equilibrium (Sec. 4 reduced forms)
+        const float cq = fmaf(cv[1], q[1], cv[0] * q[0]);
+        const float e = pre * tree_ex2(c2 * nl2);
+        const float corr = shA * cq;
+        const float tc = 2.f * c2 * invT;
+        const float H = e * fmaf(corr, tc - 4.f, 1.f);
+        const float B = halfT * e * fmaf(corr, tc - 2.f, 1.f);
+        float fo[2];
+        fo[0] = f2.x - A.dt * dv.x + dtau * (H - f2.x);
+        fo[1] = f2.y - A.dt * dv.y + dtau * (B - f2.y);
+        reinterpret_cast<float2 *>(A.fn)[(size_t)c * A.nvp + k] = make_float2(fo[0], fo[1]);
+        // moments about the current bulk velocity: c' = xi - U^n
+        const float wh = wk * fo[0];
+        const float e2 = fmaf(c2, wh, wk * fo[1]);
+        acc[0] += wh;
+        acc[1] = fmaf(cv[0], wh, acc[1]);
+        acc[2] = fmaf(cv[1], wh, acc[2]);
+        acc[3] += e2;
+        acc[4] = fmaf(cv[0] * cv[0], wh, acc[4]);
+        acc[5] = fmaf(cv[0] * cv[1], wh, acc[5]);
+        acc[6] = fmaf(cv[1] * cv[1], wh, acc[6]);
+        acc[7] = fmaf(cv[0], e2, acc[7]);
+        acc[8] = fmaf(cv[1], e2, acc[8]);
+      };
+      if (fast[ty]) {
+        // a leaf with one neighbour of its own level on every side: the
+        // upwind neighbour's value and its side towards the leaf are the
+        // leaf's side value and own value, so one velocity reads the leaf,
+        // its four neighbours and the two far neighbours upwind; every load
+        // is issued before any arithmetic, the upwind sides taken from the
+        // quadrant of the stored position (a zero component moves nothing)
+        const TreeStencil<float> &Sx = st[ty][0], &Sy = st[ty][1];
+        const float2 *xm = reinterpret_cast<const float2 *>(Sx.m0), *xp = reinterpret_cast<const float2 *>(Sx.p0);
+        const float2 *ym = reinterpret_cast<const float2 *>(Sy.m0), *yp = reinterpret_cast<const float2 *>(Sy.p0);
+        const float2 *xf0 = reinterpret_cast<const float2 *>(st[ty][2].m0);
+        const float2 *xf1 = reinterpret_cast<const float2 *>(st[ty][4].p0);
+        const float2 *yf0 = reinterpret_cast<const float2 *>(st[ty][6].m0);
+        const float2 *yf1 = reinterpret_cast<const float2 *>(st[ty][8].p0);
+        const float2 *own2 = reinterpret_cast<const float2 *>(own);
+        for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
+          const int o = (k >= TA.qb[0]) + (k >= TA.qb[1]) + (k >= TA.qb[2]); // bit 0: x < 0, bit 1: y < 0
+          const int bx = o & 1, by = o >> 1;
+          const float2 f2 = own2[k], vxm = xm[k], vxp = xp[k], vym = ym[k], vyp = yp[k];
+          const float2 vxf = (bx ? xf1 : xf0)[k], vyf = (by ? yf1 : yf0)[k];
+          const float xix = A.xi[k], xiy = A.xi[A.nvp + k], wk = A.w[k];
+          const float sx = bx ? -1.f : 1.f, sy = by ? -1.f : 1.f;
+          const float2 foutx = tree_face2(Sx, f2, vxm, vxp, sx);
+          const float2 fouty = tree_face2(Sy, f2, vym, vyp, sy);
+          const float2 finx = tree_face2(st[ty][bx ? 4 : 2], bx ? vxp : vxm, bx ? f2 : vxf, bx ? vxf : f2, sx);
+          const float2 finy = tree_face2(st[ty][by ? 8 : 6], by ? vyp : vym, by ? f2 : vyf, by ? vyf : f2, sy);
+          float2 dv = __fmul2_rn(dev::dup(fabsf(xix) * rh[ty][0]), dev::sub2(foutx, finx));
+          dv = __ffma2_rn(dev::dup(fabsf(xiy) * rh[ty][1]), dev::sub2(fouty, finy), dv);
+          const float cv[2] = {xix - U[0], xiy - U[1]};
+          finish(k, f2, dv, cv, fmaf(cv[1], cv[1], cv[0] * cv[0]), wk);
+        }
+      } else {
       for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
         const float2 f2 = reinterpret_cast<const float2 *>(own)[k];
         float2 dv = make_float2(0.f, 0.f);
@@ -572,30 +625,8 @@ __global__ void __launch_bounds__(kBlock) tree_sweep_kernel(TreeArgs<T> TA) {
           }
           dv = __ffma2_rn(dev::dup(fabsf(xa) * rh[ty][a]), dev::sub2(fout, fin), dv);
         }
-        // Shakhov equilibrium (Sec. 4 reduced forms)
-        const float cq = fmaf(cv[1], q[1], cv[0] * q[0]);
-        const float e = pre * tree_ex2(c2 * nl2);
-        const float corr = shA * cq;
-        const float tc = 2.f * c2 * invT;
-        const float H = e * fmaf(corr, tc - 4.f, 1.f);
-        const float B = halfT * e * fmaf(corr, tc - 2.f, 1.f);
-        float fo[2];
-        fo[0] = f2.x - A.dt * dv.x + dtau * (H - f2.x);
-        fo[1] = f2.y - A.dt * dv.y + dtau * (B - f2.y);
-        reinterpret_cast<float2 *>(A.fn)[(size_t)c * A.nvp + k] = make_float2(fo[0], fo[1]);
-        // moments about the current bulk velocity: c' = xi - U^n
-        const float wk = A.w[k];
-        const float wh = wk * fo[0];
-        const float e2 = fmaf(c2, wh, wk * fo[1]);
-        acc[0] += wh;
-        acc[1] = fmaf(cv[0], wh, acc[1]);
-        acc[2] = fmaf(cv[1], wh, acc[2]);
-        acc[3] += e2;
-        acc[4] = fmaf(cv[0] * cv[0], wh, acc[4]);
-        acc[5] = fmaf(cv[0] * cv[1], wh, acc[5]);
-        acc[6] = fmaf(cv[1] * cv[1], wh, acc[6]);
-        acc[7] = fmaf(cv[0], e2, acc[7]);
-        acc[8] = fmaf(cv[1], e2, acc[8]);
+        finish(k, f2, dv, cv, c2, A.w[k]);
+      }
       }
     } else {
       for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
@@ -1787,8 +1818,10 @@ template <typename T, int D> cudaError_t tree_sweep_t(ibdvm_ctx *ctx) {
   } else {
     TreeArgs<T> A{};
     A.S = sweep_args<T>(ctx, 1, 1);
-    A.nb = ctx->tree_nb;
-    A.geo = ctx->tree_geo;
+    A.sti = reinterpret_cast<const int4 *>(ctx->tree_sti);
+    A.stg = reinterpret_cast<const double2 *>(ctx->tree_stg);
+    A.lrec = reinterpret_cast<const int4 *>(ctx->tree_lrec);
+    for (int i = 0; i < 3; ++i) A.qb[i] = ctx->tree_qb[i];
     dim3 block(kThreadsPerCell, kCellsPerBlock);
     dim3 grid((unsigned)((ctx->ncell + kCellsPerBlock - 1) / kCellsPerBlock), (unsigned)ctx->nchunk);
     tree_sweep_kernel<T, D><<<grid, block, 0, ctx->stream>>>(A);

@@ -93,4 +93,68 @@ bool build_tree_mesh(const ibdvm_grid_desc &root, const ibdvm_tree_desc &t, std:
   return true;
 }
 
+// The stencil tables of the tree sweep, one record per leaf so that a block
+// reads its leaves' stencils in one pass.  Entry t of leaf c: t < 2 the leaf
+// itself along axis t; t >= 2 the upwind neighbour j = (t - 2) & 1 on side
+// sd = ((t - 2) >> 1) & 1 of axis a = (t - 2) >> 2.  Ints per entry: the cell,
+// its - side (one or two leaves), its + side, the mutual flag (the entry is
+// c's only neighbour on that side and has c as its only neighbour on the
+// other), then padding; rows -1 none, -2 the freestream halo.  Doubles per
+// entry: the reciprocal centre distances to the - and + sides (the
+// neighbour's centre, or h to the halo), h, and 1 / h for t < 2.  Ints per
+// leaf: the number of leaves on side 2a + sd (0 at the domain edge, 1, 2),
+// then the regular flag: one leaf of c's level on every side, each with one
+// leaf or the domain edge beyond it.
+void build_tree_stencils(const std::vector<int> &lev, const std::vector<int> &nb, const double h0[2],
+                         std::vector<int> &sti, std::vector<double> &stg, std::vector<int> &lrec) {
+  const size_t n = lev.size();
+  sti.assign(n * 10 * 8, -1);
+  stg.assign(n * 10 * 4, 0.0);
+  lrec.assign(n * 8, 0);
+  auto edge = [&](int leaf, int a) { return h0[a] / static_cast<double>(1 << lev[leaf]); };
+  auto side = [&](size_t c, int s, int j) { return nb[c * 8 + s * 2 + j]; };
+  for (size_t c = 0; c < n; ++c) {
+    for (int t = 0; t < 10; ++t) {
+      int a, u, sd = 0;
+      if (t < 2) {
+        a = t;
+        u = static_cast<int>(c);
+      } else {
+        a = (t - 2) >> 2;
+        sd = ((t - 2) >> 1) & 1;
+        u = side(c, 2 * a + sd, (t - 2) & 1);
+      }
+      if (u < 0) continue;
+      int *I = &sti[(c * 10 + t) * 8];
+      double *D = &stg[(c * 10 + t) * 4];
+      I[0] = u;
+      for (int q = 0; q < 2; ++q) {
+        const int n0 = side(u, 2 * a + q, 0), n1 = side(u, 2 * a + q, 1);
+        I[1 + 2 * q] = (n0 < 0) ? -2 : n0;
+        I[2 + 2 * q] = (n0 >= 0 && n1 >= 0) ? n1 : -1;
+      }
+      if (t >= 2)
+        I[5] = (side(c, 2 * a + sd, 1) < 0 && side(u, 2 * a + 1 - sd, 0) == static_cast<int>(c) &&
+                side(u, 2 * a + 1 - sd, 1) < 0)
+                   ? 1
+                   : 0;
+      const double h = edge(u, a);
+      for (int q = 0; q < 2; ++q) {
+        const int n0 = side(u, 2 * a + q, 0);
+        D[q] = 1.0 / ((n0 < 0) ? h : 0.5 * (h + edge(n0, a)));
+      }
+      D[2] = h;
+      D[3] = (t < 2) ? 1.0 / h : 0.0;
+    }
+    bool regular = true;
+    for (int s = 0; s < 4; ++s) {
+      const int n0 = side(c, s, 0), n1 = side(c, s, 1);
+      lrec[c * 8 + s] = (n0 < 0) ? 0 : (n1 < 0 ? 1 : 2);
+      regular = regular && n0 >= 0 && n1 < 0 && side(n0, s ^ 1, 0) == static_cast<int>(c) && side(n0, s ^ 1, 1) < 0 &&
+                side(n0, s, 1) < 0;
+    }
+    lrec[c * 8 + 4] = regular ? 1 : 0;
+  }
+}
+
 } // namespace ibdvm

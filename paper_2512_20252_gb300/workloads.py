@@ -342,15 +342,25 @@ def tree_leaves(root, maxlevel, lo, hi, center, radii, metric="point"):
             if m.any():
                 split(l, m)
                 changed = True
+    # the leaves in the tree's depth-first (Z) order: root cells row by row,
+    # the four children of a cell as (0,0), (1,0), (0,1), (1,1), so that
+    # consecutive leaves are close in space
     level, ix, iy = [], [], []
-    for l in range(L + 1):
+
+    def visit(l, i, j):
         s = 1 << (L - l)
-        for j in range(ny0 << l):
-            for i in range(nx0 << l):
-                if (lev[i * s:(i + 1) * s, j * s:(j + 1) * s] == l).all():
-                    level.append(l)
-                    ix.append(i)
-                    iy.append(j)
+        if lev[i * s, j * s] == l:
+            level.append(l)
+            ix.append(i)
+            iy.append(j)
+            return
+        for dj in (0, 1):
+            for di in (0, 1):
+                visit(l + 1, 2 * i + di, 2 * j + dj)
+
+    for j in range(ny0):
+        for i in range(nx0):
+            visit(0, i, j)
     return {"maxlevel": L, "level": level, "ix": ix, "iy": iy}
 
 

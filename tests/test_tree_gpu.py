@@ -57,8 +57,14 @@ def test_tree_fp64_against_the_oracle(metric, levels):
     g.close()
 
 
-def test_tree_mixed_against_the_oracle():
-    case = wl.tree_case(16, 2, nv=12, Ma=0.5, precision="mixed")
+@pytest.mark.parametrize("metric,levels,nv", [("point", 2, 12), ("point", 3, 16), ("y", 2, 15)])
+def test_tree_mixed_against_the_oracle(metric, levels, nv):
+    """FP32 storage: f within 1e-5 of the oracle's FP64 after eight steps from
+    a perturbed state, W within 1e-5; leaves of one level on every side and
+    leaves at coarse-fine interfaces and domain edges, velocity counts whose
+    quadrants end inside a warp."""
+    case = wl.tree_case(16, levels, nv=nv, Ma=0.5, precision="mixed", metric=metric,
+                        radii=[0.9, 0.5, 0.3][:levels] if metric == "y" else None)
     o = oracle.OracleTree(case)
     g = ibdvm.Solver(case)
     f0 = _perturbed(o, 11)
@@ -66,6 +72,7 @@ def test_tree_mixed_against_the_oracle():
     g.set_f(f0)
     o.step(8)
     g.step(8)
+    assert rel_err(g.get_f(), o.get_f()) < 1e-5
     Wg, _, _ = g.moments()
     Wo, _ = o.moments()
     for i in range(4):
