@@ -364,6 +364,16 @@ def tree_leaves(root, maxlevel, lo, hi, center, radii, metric="point"):
     return {"maxlevel": L, "level": level, "ix": ix, "iy": iy}
 
 
+def tree_centres(case):
+    """Centres (nleaf, 2) of the leaves of a tree case (geometry only)."""
+    tr = case["tree"]
+    lev = np.asarray(tr["level"], dtype=np.float64)
+    h = np.array([(case["hi"][a] - case["lo"][a]) / case["n"][a] for a in range(2)])
+    size = h[None, :] * (0.5 ** lev)[:, None]
+    ij = np.stack([np.asarray(tr["ix"], dtype=np.float64), np.asarray(tr["iy"], dtype=np.float64)], axis=1)
+    return np.asarray(case["lo"][:2])[None, :] + (ij + 0.5) * size
+
+
 def tree_case(root=16, maxlevel=2, L=2.0, nv=12, V=4.5, Kn=0.1, Ma=0.3, radii=None, center=(0.0, 0.0),
               precision="fp64", steps=20, metric="point"):
     """A 2D case on a quadtree: root^2 cells on [-L, L]^2 refined around
