@@ -134,7 +134,7 @@ def _load():
                 "or_cut_fraction_2d": ([_D, _D, _D], ctypes.c_double),
                 "or_cut_fraction_3d": ([_D, _D, _D], ctypes.c_double),
                 "or_residual": ([V, _D, _D], ctypes.c_double),
-                "or_tree_create": ([P, ctypes.c_long, ctypes.c_int, _I, _I, _I], V),
+                "or_tree_create": ([P, ctypes.c_long, ctypes.c_int, _I, _I, _I, ctypes.POINTER(ctypes.c_int)], V),
                 "or_tree_destroy": ([V], None),
                 "or_tree_set_threads": ([V, ctypes.c_int], None),
                 "or_tree_sizes": ([V, _LL], None),
@@ -144,6 +144,8 @@ def _load():
                 "or_tree_set_f": ([V, _D], None),
                 "or_tree_step": ([V, ctypes.c_int, _D], ctypes.c_int),
                 "or_tree_moments": ([V, _D, _D], None),
+                "or_tree_cell_types": ([V, ctypes.POINTER(ctypes.c_ubyte)], None),
+                "or_tree_forces": ([V, _D, _D, _D, _D], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -466,7 +468,8 @@ def cut_fraction_3d(blo, bhi, n) -> float:
 class OracleTree:
     """A case on a tree-refined 2D grid (reading C28): the leaves of
     ``cfg["tree"]`` (level, ix, iy over the root grid ``cfg["n"]``) and the
-    state f[leaf][k][comp]; no body, freestream domain faces."""
+    state f[leaf][k][comp]; freestream domain faces; a body in the finest
+    level (reading C29)."""
 
     def __init__(self, cfg: dict, threads: int = 1):
         self.lib = _load()
@@ -476,17 +479,21 @@ class OracleTree:
         self._lev = np.ascontiguousarray(np.asarray(tree["level"], dtype=np.int32))
         self._ix = np.ascontiguousarray(np.asarray(tree["ix"], dtype=np.int32))
         self._iy = np.ascontiguousarray(np.asarray(tree["iy"], dtype=np.int32))
+        why = ctypes.c_int(0)
         self.h = self.lib.or_tree_create(ctypes.byref(self._p), self._lev.size, int(tree["maxlevel"]),
                                          self._lev.ctypes.data_as(_I), self._ix.ctypes.data_as(_I),
-                                         self._iy.ctypes.data_as(_I))
+                                         self._iy.ctypes.data_as(_I), ctypes.byref(why))
         if not self.h:
+            if why.value == 2:
+                raise ValueError("the body must lie in the finest level of the tree")
             raise ValueError("invalid tree: the leaves must tile the domain with face neighbours at most one level apart")
         self.lib.or_tree_set_threads(self.h, max(1, int(threads)))
         s = np.zeros(3, dtype=np.int64)
         self.lib.or_tree_sizes(self.h, s.ctypes.data_as(_LL))
         self.nleaf, self.nvel, self.ncomp = (int(x) for x in s)
-        self.ncell = self.nfluid = self.nleaf
         self.dim = 2
+        self.ncell = self.nleaf
+        self.nfluid = int(np.count_nonzero(self.cell_types() == 0))
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -525,6 +532,19 @@ class OracleTree:
         q = np.zeros((self.nleaf, 2))
         self.lib.or_tree_moments(self.h, _dp(W), _dp(q))
         return W, q
+
+    def cell_types(self) -> np.ndarray:
+        t = np.zeros(self.nleaf, dtype=np.uint8)
+        self.lib.or_tree_cell_types(self.h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        return t
+
+    def forces(self):
+        F = np.zeros(3)
+        Q = ctypes.c_double()
+        CD = ctypes.c_double()
+        CL = ctypes.c_double()
+        self.lib.or_tree_forces(self.h, _dp(F), ctypes.byref(Q), ctypes.byref(CD), ctypes.byref(CL))
+        return F, Q.value, CD.value, CL.value
 
     def sizes(self) -> np.ndarray:
         """Edge length of every leaf along x and y."""

@@ -89,8 +89,17 @@
  *       inflow of a side with two finer neighbours the mean of their face
  *       values (each covers half the side), so the flux through every
  *       interface is the same for both cells; one time step for all cells,
- *       C16 with the finest cell size; no body on the tree.  On a tree of
- *       one level it is the uniform grid's step.
+ *       C16 with the finest cell size.  On a tree of one level it is the
+ *       uniform grid's step.
+ *   C29 a body on a tree (Sec. 4.2-4.4 refine the mesh towards the wall):
+ *       the body lies in the finest level, so its ghost band (ghost cells,
+ *       donors, auxiliary cells and the cells beyond the donors, surface
+ *       cells and their fluid neighbours) is the uniform grid's on the
+ *       finest grid, and a fluid leaf next to a ghost sees the link's ghost
+ *       value as that side's value (slope) and, when the ghost is upwind,
+ *       the mean of the link value and its own value as the inflow (C14);
+ *       a coarser leaf is all fluid or all solid; solid leaves keep their
+ *       values and the residual runs over the fluid leaves.
  *
  * Parity unpinned: C4-C7, C9, C10, C14, C16-C19 and the first-order
  * outgoing face of C24 are choices the paper does not fix; they are pinned
@@ -1432,20 +1441,55 @@ void or_moments(const or_case *C, double *W, double *q)
 /* ------------------------------------------------------------------------ */
 
 struct or_tree {
-  or_case *V;   /* velocity grid, gas and time step: a body-free case on the finest uniform grid */
+  or_case *V;   /* velocity grid, gas, time step and body: a case on the finest uniform grid */
   long n;       /* leaves */
   int L;        /* finest level */
   int *lev;
   double *h;    /* [n][2] edge lengths */
   long *nb;     /* [n][4][2] face neighbours, sides 2a + (s > 0) */
   double *f, *fnew, *sl; /* [n][nv][nc]; slopes [n][2][nv][nc] */
+  unsigned char *type;   /* [n] OR_FLUID, OR_GHOST, OR_SOLID (C29) */
+  long *leafv;  /* [n] the finest-grid cell of a finest leaf, -1 for coarser leaves */
+  int body;
   int nthreads;
 };
 
-or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int *level, const int *ix,
-                        const int *iy)
+/* the leaf owning finest-grid cell q is of the finest level */
+static int finest_owned(const long *own, const int *level, int L, long q) { return q >= 0 && level[own[q]] == L; }
+
+/* C29: every cell the immersed boundary reads or writes lies in the finest
+   level: the ghost cells, the donors, the auxiliary cells and the cells
+   beyond the donors along the link axes (their slopes and face values), the
+   surface cells and their fluid face neighbours (the pre-ghost slopes).  A
+   coarser leaf is all fluid or all solid. */
+static int tree_body_fits(const or_case *V, const long *own, const int *level, int L)
 {
-  if (p->dim != 2 || p->kind != OR_BODY_NONE || maxlevel < 0 || maxlevel > 12 || nleaf <= 0) return NULL;
+  for (int l = 0; l < V->nlink; ++l) {
+    const or_link *K = &V->links[l];
+    if (!finest_owned(own, level, L, K->g) || !finest_owned(own, level, L, K->d)) return 0;
+    if (K->ac >= 0 && !finest_owned(own, level, L, K->ac)) return 0;
+    const long far = neighbour(V, K->d, K->axis, K->side);
+    if (far >= 0 && V->type[far] == OR_FLUID && !finest_owned(own, level, L, far)) return 0;
+  }
+  for (int gi = 0; gi < V->nghost; ++gi) {
+    const or_ghost *G = &V->ghosts[gi];
+    for (int j = 0; j < G->ns; ++j) {
+      if (!finest_owned(own, level, L, G->surf[j])) return 0;
+      for (int a = 0; a < V->dim; ++a)
+        for (int s = -1; s <= 1; s += 2) {
+          const long q = neighbour(V, G->surf[j], a, s);
+          if (q >= 0 && V->type[q] == OR_FLUID && !finest_owned(own, level, L, q)) return 0;
+        }
+    }
+  }
+  return 1;
+}
+
+or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int *level, const int *ix,
+                        const int *iy, int *why)
+{
+  if (why) *why = 1;
+  if (p->dim != 2 || maxlevel < 0 || maxlevel > 12 || nleaf <= 0) return NULL;
   for (int i = 0; i < 6; ++i)
     if (p->wall[i]) return NULL;
   const long nfx = (long)p->n[0] << maxlevel, nfy = (long)p->n[1] << maxlevel;
@@ -1512,6 +1556,29 @@ or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int 
         }
     }
     if (ok) {
+      /* leaf classes from the finest grid (C29) */
+      or_case *V = T->V;
+      T->body = p->kind != OR_BODY_NONE;
+      T->type = (unsigned char *)xcalloc((size_t)nleaf, 1);
+      T->leafv = (long *)xcalloc((size_t)nleaf, sizeof(long));
+      int fits = tree_body_fits(V, own, level, maxlevel);
+      for (long c = 0; c < nleaf && fits; ++c) {
+        const int l = level[c];
+        const long s = 1L << (maxlevel - l);
+        const long i0 = ix[c] * s, j0 = iy[c] * s;
+        T->leafv[c] = (l == maxlevel) ? i0 + nfx * j0 : -1;
+        const unsigned char t0 = V->type[i0 + nfx * j0];
+        for (long i = i0; i < i0 + s && fits; ++i)
+          for (long j = j0; j < j0 + s; ++j)
+            if (V->type[i + nfx * j] != t0 || (l < maxlevel && t0 == OR_GHOST)) fits = 0;
+        T->type[c] = t0;
+      }
+      if (!fits) {
+        ok = 0;
+        if (why) *why = 2;
+      }
+    }
+    if (ok) {
       const size_t sz = (size_t)nleaf * T->V->nv * T->V->ncomp;
       T->f = (double *)xcalloc(sz, sizeof(double));
       T->fnew = (double *)xcalloc(sz, sizeof(double));
@@ -1525,6 +1592,7 @@ or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int 
     or_tree_destroy(T);
     T = NULL;
   }
+  if (T && why) *why = 0;
   return T;
 }
 
@@ -1538,6 +1606,8 @@ void or_tree_destroy(or_tree *T)
   free(T->f);
   free(T->fnew);
   free(T->sl);
+  free(T->type);
+  free(T->leafv);
   free(T);
 }
 
@@ -1567,8 +1637,25 @@ void or_tree_set_f(or_tree *T, const double *f)
   memcpy(T->f, f, sizeof(double) * (size_t)T->n * T->V->nv * T->V->ncomp);
 }
 
-/* the value on side (a, s) of leaf c as its slope sees it, and the distance
-   to it along a (C28) */
+/* the ghost value of the link from ghost leaf g to its fluid face neighbour
+   c (both of the finest level, C29): the value c sees across that face */
+static double tree_link_value(const or_tree *T, long g, long c, int k, int m)
+{
+  const int l = find_link(T->V, T->leafv[g], T->leafv[c]);
+  return T->V->lval[((size_t)l * T->V->nv + k) * T->V->ncomp + m];
+}
+
+/* the finest leaves' values into the finest grid of the helper case (the
+   cells the immersed boundary reads, C29) */
+static void tree_scatter(or_tree *T)
+{
+  const size_t row = (size_t)T->V->nv * T->V->ncomp;
+  for (long c = 0; c < T->n; ++c)
+    if (T->leafv[c] >= 0) memcpy(T->V->f + (size_t)T->leafv[c] * row, T->f + (size_t)c * row, sizeof(double) * row);
+}
+
+/* the value on side (a, s) of fluid leaf c as its slope sees it, and the
+   distance to it along a (C28; a ghost neighbour's link value, C29) */
 static double tree_side(const or_tree *T, const double *f, long c, int a, int s, int k, int m, double *dist)
 {
   const long *nb = T->nb + (size_t)c * 8 + (2 * a + (s > 0)) * 2;
@@ -1579,6 +1666,7 @@ static double tree_side(const or_tree *T, const double *f, long c, int a, int s,
     return T->V->finf[k * nc + m]; /* the freestream halo */
   }
   *dist = 0.5 * (hc + T->h[2 * nb[0] + a]);
+  if (T->type[nb[0]] != OR_FLUID) return tree_link_value(T, nb[0], c, k, m);
   const double v0 = f[((size_t)nb[0] * nv + k) * nc + m];
   if (nb[1] < 0) return v0;
   return 0.5 * (v0 + f[((size_t)nb[1] * nv + k) * nc + m]);
@@ -1602,9 +1690,15 @@ int or_tree_step(or_tree *T, int nsteps, double *residual)
   double *Wnew = (double *)xcalloc((size_t)n * nw, sizeof(double));
   double res = 0.0;
   for (int it = 0; it < nsteps; ++it) {
-    /* slopes of every leaf along both axes (Eq. limiter over the centre distances) */
+    /* the ghost band on the finest grid around the body: link values f*_gc */
+    if (T->body) {
+      tree_scatter(T);
+      or_ghost_band(V, V->f, NULL, NULL, NULL, NULL, V->lval, NULL);
+    }
+    /* slopes of every fluid leaf along both axes (Eq. limiter over the centre distances) */
 #pragma omp parallel for num_threads(T->nthreads) schedule(dynamic, 16)
-    for (long c = 0; c < n; ++c)
+    for (long c = 0; c < n; ++c) {
+      if (T->type[c] != OR_FLUID) continue;
       for (int a = 0; a < D; ++a)
         for (int k = 0; k < nv; ++k)
           for (int m = 0; m < nc; ++m) {
@@ -1614,12 +1708,19 @@ int or_tree_step(or_tree *T, int nsteps, double *residual)
             const double fp = tree_side(T, T->f, c, a, +1, k, m, &dp);
             T->sl[(((size_t)c * 2 + a) * nv + k) * nc + m] = or_vanleer((fc - fm) / dm, (fp - fc) / dp);
           }
+    }
     /* transport and relaxation of every leaf */
 #pragma omp parallel num_threads(T->nthreads)
     {
       double *gS = (double *)xcalloc((size_t)nv * nc, sizeof(double));
 #pragma omp for schedule(dynamic, 16)
       for (long c = 0; c < n; ++c) {
+        const size_t row = (size_t)nv * nc;
+        if (T->type[c] != OR_FLUID) { /* solid leaves keep their values */
+          memcpy(T->fnew + c * row, T->f + c * row, sizeof(double) * row);
+          conservative(V, T->f, c, Wold + c * nw);
+          continue;
+        }
         double rho, U[3], Tm, q[3], tau;
         cell_macros(V, T->f, c, &rho, U, &Tm, q, &tau);
         conservative(V, T->f, c, Wold + c * nw);
@@ -1639,6 +1740,8 @@ int or_tree_step(or_tree *T, int nsteps, double *residual)
               double fin;
               if (nb[0] < 0)
                 fin = V->finf[k * nc + m]; /* halo: its value, zero slope */
+              else if (T->type[nb[0]] != OR_FLUID) /* a ghost: its link value with the one-sided slope (C14) */
+                fin = 0.5 * (tree_link_value(T, nb[0], c, k, m) + fc);
               else if (nb[1] < 0)
                 fin = tree_face(T, T->f, nb[0], a, s, k, m);
               else
@@ -1659,6 +1762,7 @@ int or_tree_step(or_tree *T, int nsteps, double *residual)
     for (int i = 0; i < nw; ++i) {
       double num = 0.0, den = 0.0;
       for (long c = 0; c < n; ++c) {
+        if (T->type[c] != OR_FLUID) continue;
         const double d = Wnew[c * nw + i] - Wold[c * nw + i];
         num += d * d;
         den += fabs(Wnew[c * nw + i]);
@@ -1672,6 +1776,16 @@ int or_tree_step(or_tree *T, int nsteps, double *residual)
   free(Wnew);
   if (residual) *residual = res;
   return 0;
+}
+
+void or_tree_cell_types(const or_tree *T, unsigned char *types) { memcpy(types, T->type, (size_t)T->n); }
+
+/* surface force and heat flux of the current state through the donor-ghost
+   faces (C19), on the finest grid around the body (C29) */
+void or_tree_forces(or_tree *T, double *F3, double *Q, double *CD, double *CL)
+{
+  tree_scatter(T);
+  or_forces(T->V, F3, Q, CD, CL);
 }
 
 void or_tree_moments(const or_tree *T, double *W, double *q)

@@ -143,11 +143,14 @@ double or_residual(const or_case *C, const double *Wold, const double *Wnew);
 /* Tree-refined 2D grids (reading C28): leaves (level, ix, iy) over the root
    grid p->n[0] x p->n[1] on [lo, hi], integer coordinates of the leaf's level
    (0 <= ix < n[0] 2^level); the leaves must tile the domain and face
-   neighbours differ by at most one level.  p->kind must be OR_BODY_NONE and
-   the domain faces freestream.  NULL for an invalid tree. */
+   neighbours differ by at most one level.  The domain faces are freestream.
+   A body (reading C29) must lie in the finest level: every cell its ghost
+   band reads or writes is a leaf of the finest level, a coarser leaf is all
+   fluid or all solid.  NULL when refused; *why (if given) = 1 for an invalid
+   tree, 2 for a body outside the finest level, 0 on success. */
 typedef struct or_tree or_tree;
 or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int *level, const int *ix,
-                        const int *iy);
+                        const int *iy, int *why);
 void or_tree_destroy(or_tree *T);
 void or_tree_set_threads(or_tree *T, int nthreads);
 /* sizes: nleaf, nvel, ncomp */
@@ -160,6 +163,8 @@ void or_tree_get_f(const or_tree *T, double *f);
 void or_tree_set_f(or_tree *T, const double *f);
 int or_tree_step(or_tree *T, int nsteps, double *residual);
 void or_tree_moments(const or_tree *T, double *W, double *q);
+void or_tree_cell_types(const or_tree *T, unsigned char *types);
+void or_tree_forces(or_tree *T, double *F3, double *Q, double *CD, double *CL);
 
 #ifdef __cplusplus
 }

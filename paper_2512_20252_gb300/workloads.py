@@ -375,13 +375,14 @@ def tree_centres(case):
 
 
 def tree_case(root=16, maxlevel=2, L=2.0, nv=12, V=4.5, Kn=0.1, Ma=0.3, radii=None, center=(0.0, 0.0),
-              precision="fp64", steps=20, metric="point"):
+              precision="fp64", steps=20, metric="point", body=None):
     """A 2D case on a quadtree: root^2 cells on [-L, L]^2 refined around
     `center` (by default to level 1 within 0.6 L and to level 2 within 0.3 L),
-    freestream domain faces, no body."""
+    freestream domain faces, no body unless given (it must lie in the finest
+    level)."""
     if radii is None:
         radii = [0.6 * L, 0.3 * L] + [0.3 * L * 0.5 ** i for i in range(1, maxlevel)]
-    d = _case(2, root, L, nv, V, Kn, Ma, {"kind": "none"}, precision=precision, steps=steps)
+    d = _case(2, root, L, nv, V, Kn, Ma, body or {"kind": "none"}, precision=precision, steps=steps)
     d["tree"] = tree_leaves((root, root), maxlevel, d["lo"], d["hi"], center, radii, metric)
     return d
 

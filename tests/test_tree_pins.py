@@ -151,3 +151,84 @@ def test_invalid_trees_are_refused():
     t = oracle.OracleTree(case)
     hs = t.sizes()
     assert np.sum(hs[:, 0] * hs[:, 1]) == pytest.approx((case["hi"][0] - case["lo"][0]) ** 2)
+
+
+def _bump(x):
+    return 1.0 + 0.2 * np.exp(-((x[:, 0] - 0.1) ** 2 + (x[:, 1] + 0.05) ** 2) / 0.3)
+
+
+def _uniform_centres(case):
+    n = case["n"]
+    h = [(case["hi"][a] - case["lo"][a]) / n[a] for a in range(2)]
+    i, j = np.meshgrid(np.arange(n[0]), np.arange(n[1]), indexing="xy")
+    return np.stack([case["lo"][0] + (i.ravel() + 0.5) * h[0], case["lo"][1] + (j.ravel() + 0.5) * h[1]], axis=1)
+
+
+def test_one_level_tree_with_a_body_is_the_uniform_case():
+    """C29 on a tree of one level: the ghost band, the fluid cells next to the
+    ghosts, the solid cells, the residual and the surface force are the
+    uniform grid's with the same body."""
+    n = 32
+    case = wl._case(2, n, 2.0, 8, 4.5, 0.1, 0.4, wl.circle(0.5))
+    u = oracle.OracleCase(case)
+    root, tree = _uniform_tree(n, 1)
+    t = oracle.OracleTree(dict(case, n=[root, root], tree=tree))
+    np.testing.assert_array_equal(t.cell_types(), u.cell_types())
+    assert t.nfluid == u.nfluid
+    f0 = u.get_f() * _bump(_uniform_centres(case))[:, None, None]
+    u.set_f(f0)
+    t.set_f(f0)
+    ru = u.step(3)
+    rt = t.step(3)
+    fu, ft = u.get_f(), t.get_f()
+    assert np.abs(ft - fu).max() < 1e-13 * np.abs(fu).max()
+    assert rt == pytest.approx(ru, rel=1e-10)
+    Fu, Qu, CDu, _ = u.forces()
+    Ft, Qt, CDt, _ = t.forces()
+    assert np.abs(Ft - Fu).max() < 1e-12 * np.abs(Fu).max()
+    assert Qt == pytest.approx(Qu, rel=1e-10, abs=1e-14)
+    assert CDt == pytest.approx(CDu, rel=1e-12)
+
+
+def test_body_on_a_refined_tree_is_the_finest_grid_near_it():
+    """A body in the finest level of a three-level tree: one step from the
+    same smooth state gives, at every finest leaf whose neighbourhood of
+    three finest cells holds no coarser leaf (the body's ghost band and its
+    donors among them), the values of the uniform finest grid with the same
+    body, and the same surface force."""
+    case = wl.tree_case(16, 2, nv=8, radii=[1.4, 1.0], body=wl.circle(0.3))
+    t = oracle.OracleTree(case)
+    ucase = dict(case, n=[64, 64])
+    ucase.pop("tree")
+    u = oracle.OracleCase(ucase)
+    tr = case["tree"]
+    lev = np.asarray(tr["level"])
+    # the level of every finest-grid cell, and the finest leaves' cells
+    levmap = np.zeros((64, 64), dtype=int)
+    for l, i, j in zip(tr["level"], tr["ix"], tr["iy"]):
+        s = 1 << (2 - l)
+        levmap[i * s:(i + 1) * s, j * s:(j + 1) * s] = l
+    fine = np.where(lev == 2)[0]
+    vcell = np.asarray(tr["ix"])[fine] + 64 * np.asarray(tr["iy"])[fine]
+    ok = np.array([levmap[max(i - 3, 0):i + 4, max(j - 3, 0):j + 4].min() == 2
+                   for i, j in zip(np.asarray(tr["ix"])[fine], np.asarray(tr["iy"])[fine])])
+    np.testing.assert_array_equal(t.cell_types()[fine], u.cell_types()[vcell])
+    assert ok.sum() > 300 and np.any(t.cell_types()[fine][ok] == 1)
+    t.set_f(t.get_f() * _bump(t.centres())[:, None, None])
+    u.set_f(u.get_f() * _bump(_uniform_centres(ucase))[:, None, None])
+    t.step(1)
+    u.step(1)
+    ft, fu = t.get_f()[fine][ok], u.get_f()[vcell][ok]
+    assert np.abs(ft - fu).max() < 1e-14 * np.abs(fu).max()
+    Ft, Qt, CDt, _ = t.forces()
+    Fu, Qu, CDu, _ = u.forces()
+    assert np.abs(Ft - Fu).max() < 1e-13 * np.abs(Fu).max()
+    assert CDt == pytest.approx(CDu, rel=1e-13)
+
+
+def test_a_body_outside_the_finest_level_is_refused():
+    with pytest.raises(ValueError, match="finest level"):
+        oracle.OracleTree(wl.tree_case(16, 2, nv=6, body=wl.circle(0.55)))
+    with pytest.raises(ValueError, match="finest level"):
+        oracle.OracleTree(wl.tree_case(16, 2, nv=6, body=wl.circle(0.2, center=(1.0, 0.0))))
+    oracle.OracleTree(wl.tree_case(16, 2, nv=6, body=wl.circle(0.3)))
