@@ -135,6 +135,7 @@ void free_all(ibdvm_ctx *ctx) {
   cfree_t(ctx->tree_sti);
   cfree_t(ctx->tree_stg);
   cfree_t(ctx->tree_lrec);
+  cfree_t(ctx->tree_far);
   cfree_t(ctx->partf);
   cfree_t(ctx->d_forces);
   cfree_t(ctx->d_step_forces);
@@ -167,8 +168,13 @@ void harvest(ibdvm_ctx *ctx) {
 }
 
 // Uploads the cell classes, links, surface cells and cut table of ctx->geom.
-void upload_body(ibdvm_ctx *ctx) {
+// A tree (C29) passes the finest grid GV the body was placed on and the leaf
+// of each of its cells (vmap): ctx->geom then holds the ghost band in leaf
+// indices, and the surface vectors and neighbour codes come from GV.
+void upload_body(ibdvm_ctx *ctx, const Geom *GV = nullptr, const std::vector<int> *vmap = nullptr) {
   const Geom &G = ctx->geom;
+  const Geom &GS = GV ? *GV : G; // the grid of the surface cells
+  auto cell_of = [&](long long v) { return vmap ? (*vmap)[static_cast<size_t>(v)] : static_cast<int>(v); };
   const int D = G.dim;
   const size_t nl = G.links.size();
   const int nvp = ctx->nvp;
@@ -214,31 +220,31 @@ void upload_body(ibdvm_ctx *ctx) {
   std::vector<int> s_int(8 * ns, -2);
   std::vector<double> s_dbl(8 * ns, 0.0);
   auto ijk_of = [&](long long c, int *o) {
-    o[0] = static_cast<int>(c % G.n[0]);
-    o[1] = static_cast<int>((c / G.n[0]) % G.n[1]);
-    o[2] = static_cast<int>(c / (static_cast<long long>(G.n[0]) * G.n[1]));
+    o[0] = static_cast<int>(c % GS.n[0]);
+    o[1] = static_cast<int>((c / GS.n[0]) % GS.n[1]);
+    o[2] = static_cast<int>(c / (static_cast<long long>(GS.n[0]) * GS.n[1]));
   };
-  for (size_t gi = 0; gi < G.ghosts.size(); ++gi) {
+  for (size_t gi = 0; gi < GS.ghosts.size(); ++gi) {
     int ig[3];
-    ijk_of(G.ghosts[gi], ig);
-    for (int e = G.surf_off[gi]; e < G.surf_off[gi + 1]; ++e) {
-      const int j = G.surf_cell[e];
+    ijk_of(GS.ghosts[gi], ig);
+    for (int e = GS.surf_off[gi]; e < GS.surf_off[gi + 1]; ++e) {
+      const int j = GS.surf_cell[e];
       int ij[3];
       ijk_of(j, ij);
       int *si = &s_int[8 * e];
       double *sd = &s_dbl[8 * e];
-      si[0] = j;
+      si[0] = cell_of(j);
       for (int a = 0; a < 3; ++a)
         for (int s = 0; s < 2; ++s) {
           int code = -2;
           if (a < D) {
             int q[3] = {ij[0], ij[1], ij[2]};
             q[a] += s ? 1 : -1;
-            if (q[a] < 0 || q[a] >= G.n[a]) {
+            if (q[a] < 0 || q[a] >= GS.n[a]) {
               code = -1; // domain halo: freestream or a diffuse domain wall
             } else {
-              long long nb = q[0] + G.n[0] * (q[1] + static_cast<long long>(G.n[1]) * q[2]);
-              if (G.type[nb] == IBDVM_CELL_FLUID) code = static_cast<int>(nb);
+              long long nb = q[0] + GS.n[0] * (q[1] + static_cast<long long>(GS.n[1]) * q[2]);
+              if (GS.type[nb] == IBDVM_CELL_FLUID) code = cell_of(nb);
             }
           }
           si[1 + 2 * a + s] = code;
@@ -262,6 +268,7 @@ void upload_body(ibdvm_ctx *ctx) {
       cmask[c] = 64;
       continue;
     }
+    if (GV) continue; // a tree: the tree sweep reads ghost faces from its stencil tables
     int ijk[3];
     ijk_of(c, ijk);
     for (int a = 0; a < D; ++a)
@@ -515,6 +522,58 @@ struct ibdvm_geom {
   Geom g;
 };
 
+namespace {
+
+// the stencil tables of the tree sweep for the leaf classes and ghost links of
+// ctx->geom, and the row beyond each donor for the surface force
+void upload_tree_tables(ibdvm_ctx *ctx, const std::vector<int> &glink, const std::vector<int> &far) {
+  std::vector<int> sti, lrec;
+  std::vector<double> stg;
+  build_tree_stencils(ctx->tree_lev_h, ctx->tree_nb_h, ctx->tree_h0, ctx->geom.type, glink, sti, stg, lrec);
+  upload(ctx, ctx->tree_sti, sti, "upload tree stencils");
+  upload(ctx, ctx->tree_stg, stg, "upload tree stencil geometry");
+  upload(ctx, ctx->tree_lrec, lrec, "upload tree leaf records");
+  cfree_t(ctx->tree_far);
+  if (!far.empty()) {
+    ctx->tree_far = dalloc<int>(ctx, far.size(), "tree donor rows");
+    upload(ctx, ctx->tree_far, far, "upload tree donor rows");
+  }
+}
+
+// a body on a tree-refined grid (C29): placed on the finest grid, moved onto
+// the leaves when its ghost band lies in the finest level
+ibdvm_status tree_set_body(ibdvm_ctx *ctx, const ibdvm_body_desc *body) {
+  Geom Gv = ctx->tree_vgeom;
+  std::string err;
+  if (!place_body(*body, Gv, err)) {
+    ctx->err = err;
+    return IBDVM_E_INVAL;
+  }
+  Geom Gt = ctx->geom;
+  std::vector<int> glink, far;
+  if (!map_tree_body(Gv, ctx->tree_own, ctx->tree_lev_h, ctx->tree_L, Gt, glink, far, err)) {
+    ctx->err = err;
+    return IBDVM_E_INVAL;
+  }
+  drop_graphs(ctx);
+  ++ctx->body_gen;
+  Geom old = std::move(ctx->geom);
+  ctx->geom = std::move(Gt);
+  try {
+    upload_body(ctx, &Gv, &ctx->tree_own);
+    upload_tree_tables(ctx, glink, far);
+  } catch (const Fail &f) {
+    std::string e = ctx->err;
+    ctx->geom = std::move(old);
+    ctx->err = e;
+    return f.st;
+  }
+  refresh_moments(ctx);
+  return status_of_flags(ctx, read_flags(ctx));
+}
+
+} // namespace
+
 extern "C" {
 
 const char *ibdvm_status_string(ibdvm_status s) {
@@ -547,11 +606,11 @@ static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_des
   try {
     std::string err;
     ibdvm_grid_desc gd = *grid;
-    std::vector<int> tlev, tnb;
+    std::vector<int> tlev, tnb, town;
     if (tree) {
       // the velocity grid, the gas and the time step of the finest level (dt by
       // the CFL of the smallest leaf); the cells are the leaves
-      if (!build_tree_mesh(*grid, *tree, tlev, tnb, err)) {
+      if (!build_tree_mesh(*grid, *tree, tlev, tnb, town, err)) {
         ctx->err = err;
         throw Fail{IBDVM_E_INVAL};
       }
@@ -562,6 +621,10 @@ static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_des
       throw Fail{IBDVM_E_INVAL};
     }
     if (tree) {
+      ctx->tree_vgeom = ctx->geom; // the finest grid: a body is placed there (C29)
+      ctx->tree_own = std::move(town);
+      ctx->tree_lev_h = tlev;
+      ctx->tree_L = tree->maxlevel;
       Geom &Gt = ctx->geom;
       Gt.ncell = tree->nleaf;
       Gt.n[0] = tree->nleaf;
@@ -642,7 +705,7 @@ static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_des
     if (tree) {
       std::vector<int> sti, lrec;
       std::vector<double> stg;
-      build_tree_stencils(tlev, tnb, ctx->tree_h0, sti, stg, lrec);
+      build_tree_stencils(tlev, tnb, ctx->tree_h0, {}, {}, sti, stg, lrec);
       ctx->tree_sti = dalloc<int>(ctx, sti.size(), "tree stencils");
       ctx->tree_stg = dalloc<double>(ctx, stg.size(), "tree stencil geometry");
       ctx->tree_lrec = dalloc<int>(ctx, lrec.size(), "tree leaf records");
@@ -767,14 +830,11 @@ ibdvm_status ibdvm_tree_neighbours(const ibdvm_ctx *ctx, long long *nb) {
 
 ibdvm_status ibdvm_set_body(ibdvm_ctx *ctx, const ibdvm_body_desc *body) {
   IBDVM_GUARD(ctx)
-  if (ctx->tree) {
-    ctx->err = "set_body: a tree-refined grid carries no body";
-    return IBDVM_E_STATE;
-  }
   if (!body) {
     ctx->err = "body is NULL";
     return IBDVM_E_INVAL;
   }
+  if (ctx->tree) return tree_set_body(ctx, body);
   Geom G2 = ctx->geom;
   std::string err;
   if (!place_body(*body, G2, err)) {

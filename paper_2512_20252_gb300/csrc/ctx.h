@@ -130,6 +130,10 @@ struct ibdvm_ctx {
   double *tree_stg = nullptr; // [leaf][10][4] stencil geometry
   int *tree_lrec = nullptr;   // [leaf][8] side counts, regular flag
   double tree_h0[2] = {0, 0};
+  int tree_L = 0;
+  std::vector<int> tree_lev_h, tree_own; // leaf levels; the leaf of every finest-grid cell
+  ibdvm::Geom tree_vgeom;                // the finest grid (a body is placed there)
+  int *tree_far = nullptr;               // [link] row beyond the donor (map_tree_body)
   int tree_qb[3] = {0, 0, 0}; // first stored velocity of the quadrants 1, 2, 3 (bit 0: x < 0, bit 1: y < 0)
   std::vector<int> tree_nb_h;
   // host uploads of the state in cell ranges (a copy stream, one event per range)
@@ -175,10 +179,24 @@ void orthant_tables(const Geom &G, const std::vector<int> &kst, int nvp, int kc,
 bool tma_encoder_available();
 // tree.cpp: the face neighbour tables of a tree-refined 2D grid; false with a
 // message when the leaves do not tile the domain or break the 2:1 rule
+// (own: the leaf of every cell of the finest grid, x fastest)
 bool build_tree_mesh(const ibdvm_grid_desc &root, const ibdvm_tree_desc &t, std::vector<int> &lev,
-                     std::vector<int> &nb, std::string &err);
+                     std::vector<int> &nb, std::vector<int> &own, std::string &err);
+// the sweep's stencil tables; type (leaf classes) and glink (the link from
+// the ghost across side 2a + sd of a fluid leaf, [leaf][4]) may be empty
+// without a body
 void build_tree_stencils(const std::vector<int> &lev, const std::vector<int> &nb, const double h0[2],
+                         const std::vector<uint8_t> &type, const std::vector<int> &glink,
                          std::vector<int> &sti, std::vector<double> &stg, std::vector<int> &lrec);
+// a body placed on the finest grid Gv of a tree, moved onto its leaves: false
+// with a message unless every cell the ghost band reads or writes is a leaf
+// of the finest level and every coarser leaf is all fluid or all solid.
+// Gt receives the leaf classes and the ghost band in leaf indices; glink
+// [leaf][4] the link of a ghost face neighbour; far [link] the row the
+// donor's slope sees beyond it along the link axis (a leaf, -2 the halo,
+// -3 - l the ghost value of link l)
+bool map_tree_body(const Geom &Gv, const std::vector<int> &own, const std::vector<int> &lev, int L, Geom &Gt,
+                   std::vector<int> &glink, std::vector<int> &far, std::string &err);
 // TMA sweep of 3D FP32 cases (sweep3d_tma.cu)
 bool tma3_sweep_applicable(const ibdvm_ctx *ctx);
 int tma3_sweep_nchunk(const ibdvm_ctx *ctx);

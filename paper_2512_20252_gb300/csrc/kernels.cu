@@ -473,9 +473,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
   // per leaf: its own stencil along x and y, then the upwind neighbours'
   // along axis a, side sd (0: -, 1: +), neighbour j at 2 + 4a + 2sd + j
   __shared__ TreeStencil<T> st[kCellsPerBlock][10];
-  __shared__ int nup[kCellsPerBlock][4]; // neighbours on side 2a + sd: 0 (domain edge), 1 or 2
+  __shared__ int nup[kCellsPerBlock][4]; // neighbours on side 2a + sd: 0 (domain edge), 1, 2, 3 (a ghost)
   __shared__ T rh[kCellsPerBlock][2];    // 1 / h
   __shared__ int fast[kCellsPerBlock];   // one neighbour of the leaf's own level on every side
+  __shared__ int fluid[kCellsPerBlock];  // the leaf is updated (not a solid leaf of a body, C29)
   const int tx = threadIdx.x, ty = threadIdx.y;
   const long long c = (long long)blockIdx.x * kCellsPerBlock + ty;
   const int chunk = blockIdx.y;
@@ -486,7 +487,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
     const int4 i0 = TA.sti[e], i1 = TA.sti[e + 1];
     const double2 g0 = TA.stg[e], g1 = TA.stg[e + 1];
     auto row = [&](int i) -> const T * {
-      return (i >= 0) ? A.f + (size_t)i * A.nvp * NC : (i == -2 ? A.finf : nullptr);
+      return (i >= 0) ? A.f + (size_t)i * A.nvp * NC
+             : (i == -2) ? A.finf
+             : (i <= -3) ? A.lval + (size_t)(-3 - i) * A.nvp * NC // a ghost's value for this leaf (C29)
+                         : nullptr;
     };
     TreeStencil<T> S;
     S.c = row(i0.x);
@@ -507,6 +511,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
     nup[ty][2] = r0.z;
     nup[ty][3] = r0.w;
     fast[ty] = r1.x;
+    fluid[ty] = r1.y;
   }
   __syncthreads();
   T acc[NM];
@@ -526,7 +531,27 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
     // the stored velocities of a tree case come first, padding after
     const int kbeg = chunk * A.kloop * kThreadsPerCell;
     const int kend = min(A.nv, kbeg + A.kloop * kThreadsPerCell);
-    if constexpr (std::is_same<T, float>::value) {
+    if (!fluid[ty]) {
+      // a solid leaf (C29): not updated; the moments of its stored values
+      for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
+        T fc[NC];
+        load_nc<T, NC>(A.f + ((size_t)c * A.nvp + k) * NC, fc);
+        const T cx = A.xi[k] - U[0], cy = A.xi[A.nvp + k] - U[1];
+        const T c2 = cx * cx + cy * cy;
+        const T wk = A.w[k];
+        const T wh = wk * fc[0];
+        const T e2 = c2 * wh + wk * fc[NC - 1];
+        acc[0] += wh;
+        acc[1] += cx * wh;
+        acc[2] += cy * wh;
+        acc[3] += e2;
+        acc[4] += cx * cx * wh;
+        acc[5] += cx * cy * wh;
+        acc[6] += cy * cy * wh;
+        acc[7] += cx * e2;
+        acc[8] += cy * e2;
+      }
+    } else if constexpr (std::is_same<T, float>::value) {
       const float nl2 = -invT * kTreeLog2e;
       const float2 *finf2 = reinterpret_cast<const float2 *>(A.finf);
       // relaxation, the store of f^{n+1} and the moment sums of one velocity
@@ -606,6 +631,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
           float2 fin;
           if (n == 0) {
             fin = finf2[k]; // the halo: its value, zero slope
+          } else if (n == 3) {
+            // a ghost upwind (C29): its link value with the one-sided slope
+            const float2 g = reinterpret_cast<const float2 *>(st[ty][2 + 4 * a + 2 * sd].c)[k];
+            fin = __fmul2_rn(__fadd2_rn(g, f2), dev::dup(0.5f));
           } else {
             const TreeStencil<float> &S0 = st[ty][2 + 4 * a + 2 * sd];
             if (S0.mut) {
@@ -652,6 +681,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
           const int n = nup[ty][2 * a + sd];
           if (n == 0) {
             load_nc<T, NC>(A.finf + (size_t)k * NC, fin);
+          } else if (n == 3) {
+            load_nc<T, NC>(st[ty][2 + 4 * a + 2 * sd].c + (size_t)k * NC, fin);
+#pragma unroll
+            for (int m = 0; m < NC; ++m) fin[m] = T(0.5) * (fin[m] + fc[m]);
           } else {
             const TreeStencil<T> &S0 = st[ty][2 + 4 * a + 2 * sd];
             T fu[NC], um[NC], up[NC];
@@ -1592,6 +1625,9 @@ template <typename T> struct ForceArgs {
   double *__restrict__ fpart; // [nlink][4]
   int nlink;
   double *__restrict__ dst;   // [4]: F_x, F_y, F_z, Q
+  // a tree (C29): per link the row beyond the donor along the link axis (a
+  // leaf, -2 the halo, -3 - l the ghost value of link l); null on uniform grids
+  const int *__restrict__ tree_far;
 };
 
 template <typename T, int D>
@@ -1614,10 +1650,17 @@ __device__ __forceinline__ void forces_body(const ForceArgs<T> &A, const int l) 
     if (xin == 0.0) continue;
     T fd[NC], fg[NC], face[NC];
     load_nc<T, NC>(S.f + ((size_t)d * S.nvp + k) * NC, fd);
-    seen<T, NC>(S, d, ijk, a, sf, k, fg); // the link's ghost value
+    if (A.tree_far) load_nc<T, NC>(S.lval + ((size_t)l * S.nvp + k) * NC, fg);
+    else seen<T, NC>(S, d, ijk, a, sf, k, fg); // the link's ghost value
     if (xin > 0.0) {
       T fb[NC];
-      seen<T, NC>(S, d, ijk, a, -sf, k, fb);
+      if (A.tree_far) {
+        const int r = A.tree_far[l];
+        load_nc<T, NC>((r >= 0) ? S.f + ((size_t)r * S.nvp + k) * NC
+                       : (r == -2) ? S.finf + (size_t)k * NC : S.lval + ((size_t)(-3 - r) * S.nvp + k) * NC, fb);
+      } else {
+        seen<T, NC>(S, d, ijk, a, -sf, k, fb);
+      }
 #pragma unroll
       for (int m = 0; m < NC; ++m) face[m] = fd[m] + T(0.5) * vanleer(fd[m] - fb[m], fg[m] - fd[m]);
     } else {
@@ -1958,6 +2001,7 @@ template <typename T> ForceArgs<T> force_args(const ibdvm_ctx *ctx, int cur, dou
   A.fpart = ctx->fpart;
   A.nlink = ctx->nlink;
   A.dst = dst;
+  A.tree_far = ctx->tree ? ctx->tree_far : nullptr;
   return A;
 }
 

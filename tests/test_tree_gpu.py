@@ -1,7 +1,8 @@
-"""The tree-refined 2D grid (reading C28) through the C-ABI against the
-oracle's tree: the neighbour tables, the FP64 path within 1e-11 on f and W
-after several steps from a perturbed state, the mixed path within 1e-5 on W,
-a one-level tree against the uniform grid's GPU path, and the refusals."""
+"""The tree-refined 2D grid (reading C28) and a body on it (C29) through the
+C-ABI against the oracle's tree: the neighbour tables, the FP64 path within
+1e-11 on f and W after several steps from a perturbed state, the mixed path
+within 1e-5, the surface force, one-level trees against the uniform grid's
+GPU path, and the refusals."""
 import numpy as np
 import pytest
 
@@ -113,6 +114,87 @@ def test_tree_refusals():
     bad["iy"] = list(bad["iy"])[1:]
     with pytest.raises(ibdvm.IbdvmError, match="hole"):
         ibdvm.Solver(dict(case, tree=bad))
-    body = dict(case, body=wl.circle(0.3))
-    with pytest.raises(ibdvm.IbdvmError):
-        ibdvm.Solver(body)
+    # a body whose ghost band reaches a coarser leaf (C29)
+    with pytest.raises(ibdvm.IbdvmError, match="finest level"):
+        ibdvm.Solver(dict(case, body=wl.circle(0.55)))
+    with pytest.raises(ValueError, match="finest level"):
+        oracle.OracleTree(dict(case, body=wl.circle(0.55)))
+
+
+def _body_tree(precision, nv=10):
+    return wl.tree_case(16, 2, nv=nv, Ma=0.5, radii=[1.4, 1.0], body=wl.circle(0.3), precision=precision)
+
+
+def test_tree_with_a_body_fp64_against_the_oracle():
+    """C29: a cylinder in the finest level of a three-level tree; FP64 within
+    1e-11 of the oracle on f, W, the surface force and the residual after six
+    steps from a perturbed state."""
+    case = _body_tree("fp64")
+    o = oracle.OracleTree(case)
+    g = ibdvm.Solver(case)
+    assert g.info.nfluid == o.nfluid
+    f0 = _perturbed(o, 5, amp=0.1)
+    o.set_f(f0)
+    g.set_f(f0)
+    ro = o.step(6)
+    rg = g.step(6)
+    assert rel_err(g.get_f(), o.get_f()) < 1e-11
+    Wg, _, t = g.moments()
+    Wo, _ = o.moments()
+    np.testing.assert_array_equal(t, o.cell_types())
+    fl = t == ibdvm.FLUID
+    for i in range(4):
+        if np.abs(Wo[fl, i]).max() > 1e-9:
+            assert rel_err(Wg[fl, i], Wo[fl, i]) < 1e-11, i
+    Fg, Qg, CDg, _ = g.forces()
+    Fo, Qo, CDo, _ = o.forces()
+    assert np.abs(Fg - Fo).max() < 1e-10 * np.abs(Fo).max()
+    assert CDg == pytest.approx(CDo, rel=1e-10)
+    assert Qg == pytest.approx(Qo, rel=1e-8, abs=1e-12)
+    assert rg == pytest.approx(ro, rel=1e-9)
+    g.close()
+
+
+def test_tree_with_a_body_mixed_against_the_oracle():
+    case = _body_tree("mixed", nv=12)
+    o = oracle.OracleTree(case)
+    g = ibdvm.Solver(case)
+    f0 = _perturbed(o, 9, amp=0.1)
+    o.set_f(f0)
+    g.set_f(f0)
+    o.step(8)
+    g.step(8)
+    assert rel_err(g.get_f(), o.get_f()) < 1e-5
+    Wg, _, t = g.moments()
+    Wo, _ = o.moments()
+    fl = t == ibdvm.FLUID
+    for i in range(4):
+        if np.abs(Wo[fl, i]).max() > 1e-9:
+            assert rel_err(Wg[fl, i], Wo[fl, i]) < 1e-5, i
+    _, _, CDg, _ = g.forces()
+    _, _, CDo, _ = o.forces()
+    assert CDg == pytest.approx(CDo, rel=1e-4)
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_one_level_tree_with_a_body_matches_the_uniform_gpu_path(precision):
+    n = 32
+    case = wl._case(2, n, 2.0, 10, 4.5, 0.1, 0.4, wl.circle(0.5), precision=precision)
+    u = ibdvm.Solver(case)
+    tree = {"maxlevel": 1, "level": [1] * (n * n), "ix": [i for _ in range(n) for i in range(n)],
+            "iy": [j for j in range(n) for _ in range(n)]}
+    t = ibdvm.Solver(dict(case, n=[n // 2, n // 2], tree=tree))
+    rng = np.random.default_rng(4)
+    f0 = u.get_f() * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, size=u.get_f().shape))
+    u.set_f(f0)
+    t.set_f(f0)
+    u.step(5)
+    t.step(5)
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert rel_err(t.get_f(), u.get_f()) < tol
+    _, _, CDu, _ = u.forces()
+    _, _, CDt, _ = t.forces()
+    assert CDt == pytest.approx(CDu, rel=1e-10 if precision == "fp64" else 1e-5)
+    u.close()
+    t.close()
