@@ -54,6 +54,8 @@ WORKLOADS = {
     "cylinder_hypersonic": lambda p: __import__("paper_2512_20252_gb300.workloads",
                                                 fromlist=["x"]).cylinder_hypersonic(precision=p),
     "tree_2d": lambda p: __import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).tree_2d(precision=p),
+    "cylinder_hypersonic_tree": lambda p: __import__("paper_2512_20252_gb300.workloads",
+                                                     fromlist=["x"]).cylinder_hypersonic_tree(precision=p),
     "batched_2d": None,  # a list of cases: see bench_batch
     "served": None,      # a request stream: see bench_serve
 }
@@ -75,6 +77,10 @@ DESCRIPTIONS = {
                "2 within 2 and 3 within 1 (finest edge 1/64), 2:1 balanced, 45,436 leaves in Z order, 48x48 "
                "trapezoid velocities on [-6,6]^2, Kn=0.1, Ma=0.5, no body, a 20% density bump over the refined "
                "region at the start",
+    "cylinder_hypersonic_tree": "2D cylinder r=1 at Ma 5, Kn 0.1 on a tree: a 128x128 root on [-16,16]^2 refined "
+                                "about the centre to level 1 within 8, 2 within 4, 3 within 2.2, 4 within 1.5 "
+                                "(finest edge 1/64 at the wall), 2:1 balanced, 69,148 leaves in Z order, 60x60 "
+                                "trapezoid velocities on [-10,10]^2, T_w=1, nonnegative ghost values",
     "batched_2d": "64 seeded 2D cases (seed 0): n ~ U{64..384} cells per axis on [-4,4]^2, m ~ U{16..40} "
                   "velocities per axis on [-6,6]^2, circle / ellipse (aspect U[1,3]) / NACA0012 (AoA U[0,10] deg), "
                   "Kn 10^U[-2,0], Ma U[0.1,0.8], mixed precision, one batch",
@@ -277,15 +283,16 @@ def dist_setup(nprocs: int):
 def cpu_sample_case(case: dict) -> dict:
     """A bounded sample of the workload for the CPU oracle: the same gas,
     body, velocity grid and domain on a coarser cell grid (48 cells per axis in
-    2D, 12 in 3D; a tree: a 16^2 root refined the same way) so that one oracle
-    step takes about a second."""
+    2D, 12 in 3D; a tree: a 16^2 root refined about the same centre within
+    the same radii to level 3) so that one oracle step takes about a second."""
     c = dict(case)
     c["precision"] = "fp64"
     if case.get("tree"):
         from paper_2512_20252_gb300 import workloads
 
+        spec = case.get("tree_spec", {"center": [0.0, 0.0], "radii": [4.0, 2.0, 1.0]})
         c["n"] = [16, 16]
-        c["tree"] = workloads.tree_leaves((16, 16), 3, case["lo"], case["hi"], (0.0, 0.0), [4.0, 2.0, 1.0])
+        c["tree"] = workloads.tree_leaves((16, 16), 3, case["lo"], case["hi"], spec["center"], spec["radii"][:3])
         return c
     c["n"] = [48] * 2 if case["dim"] == 2 else [12] * 3
     return c
@@ -691,7 +698,7 @@ def measure_case(args, workload, world, rank, local, pg, with_cpu=True):
         case["n"] = [args.cells] * case["dim"]
     stream = torch.cuda.Stream()
     solver = ibdvm.Solver(case, stream=stream.cuda_stream)
-    if case.get("tree"):
+    if case.get("tree") and case["body"]["kind"] == "none":
         # no body on a tree: start from the freestream with a density bump of
         # 20% over the refined region, so that the steps do transport work
         import numpy as np

@@ -193,6 +193,20 @@ def cylinder_hypersonic(n=1536, nv=60, precision="mixed", steps=200):
                  ghost_nonneg=1)
 
 
+def cylinder_hypersonic_tree(nv=60, precision="mixed", steps=200, root=128, maxlevel=4,
+                             radii=(8.0, 4.0, 2.2, 1.5)):
+    """The hypersonic cylinder of Sec. 4.2 on a tree-refined grid (C28, C29):
+    Ma 5, Kn 0.1, radius 1, T_w = 1, the domain [-16,16]^2 on a root grid of
+    root^2 cells refined about the cylinder's centre to level l within
+    radii[l] (the finest edge 32 / (root 2^maxlevel) = 1/64 at the wall, the
+    paper's wall spacing is 0.01), 2:1 balanced, nv^2 velocities on
+    [-10,10]^2, nonnegative ghost values."""
+    d = _case(2, root, 16.0, nv, 10.0, 0.1, 5.0, circle(1.0), precision=precision, steps=steps, ghost_nonneg=1)
+    d["tree"] = tree_leaves((root, root), maxlevel, d["lo"], d["hi"], (0.0, 0.0), list(radii))
+    d["tree_spec"] = {"center": [0.0, 0.0], "radii": list(radii)}
+    return d
+
+
 def naca_supersonic(cells_per_unit=100, nv=60, precision="mixed", steps=200):
     """The NACA0012 airfoil of Sec. 4.3: Ma 2, Kn 0.026, T_w = 1, angle of
     attack 0, chord 1 with the leading edge at the origin, the domain
@@ -395,4 +409,5 @@ def tree_2d(precision="mixed", steps=200):
     body (the tree's transport, relaxation and moments alone)."""
     d = _case(2, 128, 8.0, 48, 6.0, 0.1, 0.5, {"kind": "none"}, precision=precision, steps=steps)
     d["tree"] = tree_leaves((128, 128), 3, d["lo"], d["hi"], (0.0, 0.0), [4.0, 2.0, 1.0])
+    d["tree_spec"] = {"center": [0.0, 0.0], "radii": [4.0, 2.0, 1.0]}
     return d
