@@ -183,9 +183,11 @@ ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_de
    between centres; the upwind leaf's face value; a side shared with two finer
    leaves takes the mean of their face values, so every interface conserves;
    dt from the CFL number with the finest edge.  FP64 or mixed precision (the
-   mixed path keeps FP32 f and runs the same kernel in FP32).  No body and no
-   domain walls: ibdvm_set_body and ibdvm_set_domain return IBDVM_E_STATE on
-   such a context, which cannot join a batch.  Errors as ibdvm_create_grid;
+   mixed path keeps FP32 f and runs the same kernel in FP32).  A body may be
+   placed with ibdvm_set_body (below); no domain walls: ibdvm_set_domain
+   returns IBDVM_E_STATE on such a context, which cannot join a batch.  The
+   context keeps the geometry of the finest uniform grid (root.n 2^maxlevel
+   cells per axis) on the host for the body.  Errors as ibdvm_create_grid;
    IBDVM_E_INVAL (with a message) for leaves that do not tile the domain or
    face neighbours more than one level apart. */
 ibdvm_status ibdvm_create_tree(const ibdvm_grid_desc *root, const ibdvm_tree_desc *tree,
@@ -202,7 +204,14 @@ ibdvm_status ibdvm_tree_neighbours(const ibdvm_ctx *ctx, long long *nb);
    (ghost cell, fluid face neighbour) with its intersect point, normal, donor,
    auxiliary cell and shifted point, the surface-cell lists, and the
    incident-side velocity measures of the cut cells (Sec. 3.2.3).  Resets
-   nothing else: f is kept.  Errors: IBDVM_E_INVAL, IBDVM_E_NOMEM, IBDVM_E_CUDA. */
+   nothing else: f is kept.  On a tree context (reading C29 of the tree
+   meshes of Sec. 4.2-4.4) the body is placed on the finest uniform grid and
+   its ghost band moved onto the leaves; every cell the band reads or writes
+   (ghosts, donors, auxiliary cells and the cells beyond the donors, surface
+   cells and their fluid neighbours) must be a leaf of the finest level and
+   every coarser leaf all fluid or all solid, else IBDVM_E_INVAL with a
+   message and the context unchanged.  Errors: IBDVM_E_INVAL, IBDVM_E_NOMEM,
+   IBDVM_E_CUDA. */
 ibdvm_status ibdvm_set_body(ibdvm_ctx *ctx, const ibdvm_body_desc *body);
 
 /* Domain faces, index 2a + (s > 0): x-, x+, y-, y+, z-, z+.  A freestream face

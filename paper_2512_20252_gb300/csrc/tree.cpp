@@ -6,7 +6,9 @@
 // The builder checks that the leaves tile the domain and keep the 2:1 rule,
 // and lists for every leaf and side 2a + (s > 0) its one neighbour (same or
 // coarser level), its two finer neighbours in increasing transverse order, or
-// none at the domain edge.
+// none at the domain edge.  The stencil tables of the tree sweep come from
+// these lists; a body placed on the finest grid is moved onto the leaves
+// when its ghost band lies in the finest level.
 #include <string>
 #include <vector>
 
