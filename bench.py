@@ -56,6 +56,8 @@ WORKLOADS = {
     "tree_2d": lambda p: __import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).tree_2d(precision=p),
     "cylinder_hypersonic_tree": lambda p: __import__("paper_2512_20252_gb300.workloads",
                                                      fromlist=["x"]).cylinder_hypersonic_tree(precision=p),
+    "naca_supersonic_tree": lambda p: __import__("paper_2512_20252_gb300.workloads",
+                                                 fromlist=["x"]).naca_supersonic_tree(precision=p),
     "batched_2d": None,  # a list of cases: see bench_batch
     "served": None,      # a request stream: see bench_serve
 }
@@ -81,6 +83,10 @@ DESCRIPTIONS = {
                                 "about the centre to level 1 within 8, 2 within 4, 3 within 2.2, 4 within 1.5 "
                                 "(finest edge 1/64 at the wall), 2:1 balanced, 69,148 leaves in Z order, 60x60 "
                                 "trapezoid velocities on [-10,10]^2, T_w=1, nonnegative ghost values",
+    "naca_supersonic_tree": "NACA0012 (chord 1, 400-vertex polygon) at Ma 2, Kn 0.026, AoA 0 on a tree: an 80x112 "
+                            "root on [-3,7]x[-7,7] refined about the chord to level 1 within 1.5, 2 within 0.6, 3 "
+                            "within 0.25, 4 within 0.1 (finest edge 1/128), 2:1 balanced, 17,528 leaves in Z "
+                            "order, 60x60 trapezoid velocities on [-4,8]x[-6,6], T_w=1",
     "batched_2d": "64 seeded 2D cases (seed 0): n ~ U{64..384} cells per axis on [-4,4]^2, m ~ U{16..40} "
                   "velocities per axis on [-6,6]^2, circle / ellipse (aspect U[1,3]) / NACA0012 (AoA U[0,10] deg), "
                   "Kn 10^U[-2,0], Ma U[0.1,0.8], mixed precision, one batch",
@@ -283,16 +289,19 @@ def dist_setup(nprocs: int):
 def cpu_sample_case(case: dict) -> dict:
     """A bounded sample of the workload for the CPU oracle: the same gas,
     body, velocity grid and domain on a coarser cell grid (48 cells per axis in
-    2D, 12 in 3D; a tree: a 16^2 root refined about the same centre within
-    the same radii to level 3) so that one oracle step takes about a second."""
+    2D, 12 in 3D; a tree: the coarser tree the workload names, refined about
+    the same centre or segment) so that one oracle step takes about a second."""
     c = dict(case)
     c["precision"] = "fp64"
     if case.get("tree"):
         from paper_2512_20252_gb300 import workloads
 
-        spec = case.get("tree_spec", {"center": [0.0, 0.0], "radii": [4.0, 2.0, 1.0]})
-        c["n"] = [16, 16]
-        c["tree"] = workloads.tree_leaves((16, 16), 3, case["lo"], case["hi"], spec["center"], spec["radii"][:3])
+        spec = case["tree_spec"]
+        smp = spec["sample"]
+        c["n"] = list(smp["root"])
+        c["tree"] = workloads.tree_leaves(tuple(smp["root"]), smp["maxlevel"], case["lo"], case["hi"], spec["center"],
+                                          smp["radii"], metric=spec.get("metric", "point"),
+                                          segment=spec.get("segment"))
         return c
     c["n"] = [48] * 2 if case["dim"] == 2 else [12] * 3
     return c

@@ -1519,6 +1519,10 @@ or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int 
     pf.n[0] = (int)nfx;
     pf.n[1] = (int)nfy;
     T->V = or_create(&pf);
+    /* the helper case never steps: only its state buffer is used (the
+       scatter target of the body's ghost band) */
+    free(T->V->fnew);
+    T->V->fnew = NULL;
     T->n = nleaf;
     T->L = maxlevel;
     T->lev = (int *)xcalloc((size_t)nleaf, sizeof(int));

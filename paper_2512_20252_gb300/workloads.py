@@ -203,7 +203,27 @@ def cylinder_hypersonic_tree(nv=60, precision="mixed", steps=200, root=128, maxl
     [-10,10]^2, nonnegative ghost values."""
     d = _case(2, root, 16.0, nv, 10.0, 0.1, 5.0, circle(1.0), precision=precision, steps=steps, ghost_nonneg=1)
     d["tree"] = tree_leaves((root, root), maxlevel, d["lo"], d["hi"], (0.0, 0.0), list(radii))
-    d["tree_spec"] = {"center": [0.0, 0.0], "radii": list(radii)}
+    d["tree_spec"] = {"center": [0.0, 0.0], "radii": list(radii),
+                      "sample": {"root": [16, 16], "maxlevel": 3, "radii": [8.0, 4.0, 2.2]}}
+    return d
+
+
+def naca_supersonic_tree(nv=60, precision="mixed", steps=200, root=(80, 112), maxlevel=4,
+                         radii=(1.5, 0.6, 0.25, 0.1)):
+    """The NACA0012 airfoil of Sec. 4.3 (Ma 2, Kn 0.026, T_w = 1, angle of
+    attack 0, chord 1 from the origin) on a tree-refined grid (C28, C29):
+    the domain [-3,7] x [-7,7] on a root grid of 80 x 112 cells (edge 1/8)
+    refined about the chord to level l within radii[l] of it (the finest
+    edge 1/128 within 0.1 of the chord), 2:1 balanced, nv^2 velocities on
+    [-4,8] x [-6,6]."""
+    body = naca0012(1.0, 0.0, 400, center=(0.25, 0.0))
+    d = _case(2, list(root), ([-3.0, -7.0], [7.0, 7.0]), nv, ([-4.0, -6.0], [8.0, 6.0]), 0.026, 2.0, body,
+              precision=precision, steps=steps)
+    d["tree"] = tree_leaves(tuple(root), maxlevel, d["lo"], d["hi"], (0.5, 0.0), list(radii), metric="segment",
+                            segment=((0.0, 0.0), (1.0, 0.0)))
+    d["tree_spec"] = {"center": [0.5, 0.0], "radii": list(radii), "metric": "segment",
+                      "segment": [[0.0, 0.0], [1.0, 0.0]],
+                      "sample": {"root": [20, 28], "maxlevel": 3, "radii": [1.5, 0.6, 0.25]}}
     return d
 
 
@@ -290,15 +310,17 @@ def small_2d(body="circle", n=16, nv=8, precision="fp64", **kw):
 # quadtree meshes (the tree-refined physical grids of Sec. 4.2-4.4)
 # ---------------------------------------------------------------------------
 
-def tree_leaves(root, maxlevel, lo, hi, center, radii, metric="point"):
+def tree_leaves(root, maxlevel, lo, hi, center, radii, metric="point", segment=None):
     """Leaves (level, ix, iy) of a 2:1-balanced quadtree over a root grid of
     root[0] x root[1] cells on [lo, hi]: a cell of level l < maxlevel is split
     while its centre lies within radii[l] of `center` (radii decreasing with
     the level; metric "point": the distance to the point, "x" or "y": the
-    distance along that axis only, which refines stripes), then any leaf with
-    a face neighbour two or more levels finer is split until the tree is
-    balanced.  Integer coordinates are those of
-    the leaf's level (0 <= ix < root[0] 2^level).  Geometry only."""
+    distance along that axis only, which refines stripes, "segment": the
+    distance to the segment ((x0, y0), (x1, y1)) given as `segment`, which
+    refines about a thin body), then any leaf with a face neighbour two or
+    more levels finer is split until the tree is balanced.  Integer
+    coordinates are those of the leaf's level (0 <= ix < root[0] 2^level).
+    Geometry only."""
     nx0, ny0 = root
     hx0, hy0 = (hi[0] - lo[0]) / nx0, (hi[1] - lo[1]) / ny0
     L = maxlevel
@@ -326,7 +348,12 @@ def tree_leaves(root, maxlevel, lo, hi, center, radii, metric="point"):
         xc = lo[0] + (np.arange(nx0 << l) + 0.5) * hx0 * h
         yc = lo[1] + (np.arange(ny0 << l) + 0.5) * hy0 * h
         X, Y = np.meshgrid(xc, yc, indexing="ij")
-        if metric == "x":
+        if metric == "segment":
+            (x0, y0), (x1, y1) = segment
+            ex, ey = x1 - x0, y1 - y0
+            t = np.clip(((X - x0) * ex + (Y - y0) * ey) / (ex * ex + ey * ey), 0.0, 1.0)
+            near = np.hypot(X - x0 - t * ex, Y - y0 - t * ey) <= radii[l]
+        elif metric == "x":
             near = np.abs(X - center[0]) <= radii[l]
         elif metric == "y":
             near = np.abs(Y - center[1]) <= radii[l]
@@ -409,5 +436,6 @@ def tree_2d(precision="mixed", steps=200):
     body (the tree's transport, relaxation and moments alone)."""
     d = _case(2, 128, 8.0, 48, 6.0, 0.1, 0.5, {"kind": "none"}, precision=precision, steps=steps)
     d["tree"] = tree_leaves((128, 128), 3, d["lo"], d["hi"], (0.0, 0.0), [4.0, 2.0, 1.0])
-    d["tree_spec"] = {"center": [0.0, 0.0], "radii": [4.0, 2.0, 1.0]}
+    d["tree_spec"] = {"center": [0.0, 0.0], "radii": [4.0, 2.0, 1.0],
+                      "sample": {"root": [16, 16], "maxlevel": 3, "radii": [4.0, 2.0, 1.0]}}
     return d
