@@ -146,6 +146,7 @@ def _load():
                 "or_tree_moments": ([V, _D, _D], None),
                 "or_tree_cell_types": ([V, ctypes.POINTER(ctypes.c_ubyte)], None),
                 "or_tree_forces": ([V, _D, _D, _D, _D], None),
+                "or_tree_finest": ([V], V),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -239,9 +240,20 @@ class OracleCase:
 
     def __del__(self):
         h = getattr(self, "h", None)
-        if h:
+        if h and not getattr(self, "_owner", None):
             self.lib.or_destroy(h)
-            self.h = None
+        self.h = None
+
+    @classmethod
+    def _view(cls, lib, h, cfg: dict, owner):
+        """A case whose handle another object owns (the finest grid of a tree)."""
+        c = cls.__new__(cls)
+        c.lib, c.h, c.cfg, c._owner = lib, h, dict(cfg), owner
+        s = np.zeros(6, dtype=np.int64)
+        lib.or_sizes(h, s.ctypes.data_as(_LL))
+        c.ncell, c.nvel, c.ncomp, c.nlink, c.nghost, c.nfluid = (int(x) for x in s)
+        c.dim = int(cfg["dim"])
+        return c
 
     def set_threads(self, threads: int) -> None:
         """Host threads of the per-ghost and per-cell loops (bitwise the same
@@ -545,6 +557,14 @@ class OracleTree:
         CL = ctypes.c_double()
         self.lib.or_tree_forces(self.h, _dp(F), ctypes.byref(Q), ctypes.byref(CD), ctypes.byref(CL))
         return F, Q.value, CD.value, CL.value
+
+    def finest_case(self) -> "OracleCase":
+        """The finest uniform grid under the tree with the finest leaves'
+        current values (C29): its links are the tree's, so its ghost band and
+        wall quantities are the tree's.  Valid while this tree lives."""
+        fine = dict(self.cfg, n=[int(x) << int(self.cfg["tree"]["maxlevel"]) for x in self.cfg["n"][:2]])
+        fine.pop("tree", None)
+        return OracleCase._view(self.lib, self.lib.or_tree_finest(self.h), fine, self)
 
     def sizes(self) -> np.ndarray:
         """Edge length of every leaf along x and y."""

@@ -1784,6 +1784,14 @@ int or_tree_step(or_tree *T, int nsteps, double *residual)
 
 void or_tree_cell_types(const or_tree *T, unsigned char *types) { memcpy(types, T->type, (size_t)T->n); }
 
+/* the helper case on the finest grid, holding the finest leaves' current
+   values (the cells the body's ghost band reads, C29); owned by the tree */
+or_case *or_tree_finest(or_tree *T)
+{
+  tree_scatter(T);
+  return T->V;
+}
+
 /* surface force and heat flux of the current state through the donor-ghost
    faces (C19), on the finest grid around the body (C29) */
 void or_tree_forces(or_tree *T, double *F3, double *Q, double *CD, double *CL)

@@ -165,6 +165,10 @@ int or_tree_step(or_tree *T, int nsteps, double *residual);
 void or_tree_moments(const or_tree *T, double *W, double *q);
 void or_tree_cell_types(const or_tree *T, unsigned char *types);
 void or_tree_forces(or_tree *T, double *F3, double *Q, double *CD, double *CL);
+/* the helper case on the finest grid with the finest leaves' current values
+   (the body's links and ghost band in the order of the tree's links); owned
+   by the tree, valid until it is destroyed */
+or_case *or_tree_finest(or_tree *T);
 
 #ifdef __cplusplus
 }

@@ -198,3 +198,22 @@ def test_one_level_tree_with_a_body_matches_the_uniform_gpu_path(precision):
     assert CDt == pytest.approx(CDu, rel=1e-10 if precision == "fp64" else 1e-5)
     u.close()
     t.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tree_wall_quantities_against_the_oracle(precision):
+    """Wall-point quantities of a body on a tree (C29) through the C-ABI
+    against the oracle's finest grid under the tree, after a few steps."""
+    case = _body_tree(precision)
+    g = ibdvm.Solver(case)
+    o = oracle.OracleTree(case)
+    g.step(4)
+    o.step(4)
+    wg = g.wall()
+    wo = o.finest_case().wall_quantities()
+    assert wg.shape == wo.shape and wo.shape[0] > 8
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    for i, c in enumerate(oracle.OracleCase.WALL_COLUMNS):
+        err = np.abs(wg[:, i] - wo[:, i]).max() / max(np.abs(wo[:, i]).max(), 1e-3)
+        assert err < tol, (c, err)
+    g.close()
