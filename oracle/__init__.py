@@ -134,7 +134,7 @@ def _load():
                 "or_cut_fraction_2d": ([_D, _D, _D], ctypes.c_double),
                 "or_cut_fraction_3d": ([_D, _D, _D], ctypes.c_double),
                 "or_residual": ([V, _D, _D], ctypes.c_double),
-                "or_tree_create": ([P, ctypes.c_long, ctypes.c_int, _I, _I, _I, ctypes.POINTER(ctypes.c_int)], V),
+                "or_tree_create": ([P, ctypes.c_long, ctypes.c_int, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_int)], V),
                 "or_tree_destroy": ([V], None),
                 "or_tree_set_threads": ([V, ctypes.c_int], None),
                 "or_tree_sizes": ([V, _LL], None),
@@ -478,23 +478,27 @@ def cut_fraction_3d(blo, bhi, n) -> float:
 
 
 class OracleTree:
-    """A case on a tree-refined 2D grid (reading C28): the leaves of
-    ``cfg["tree"]`` (level, ix, iy over the root grid ``cfg["n"]``) and the
-    state f[leaf][k][comp]; freestream domain faces; a body in the finest
-    level (reading C29)."""
+    """A case on a tree-refined grid (reading C28; a quadtree in 2D, an octree
+    in 3D): the leaves of ``cfg["tree"]`` (level, ix, iy, and iz in 3D, over
+    the root grid ``cfg["n"]``) and the state f[leaf][k][comp]; freestream
+    domain faces; a body in the finest level (reading C29)."""
 
     def __init__(self, cfg: dict, threads: int = 1):
         self.lib = _load()
         self.cfg = dict(cfg)
         self._p, self._keep = _params(cfg)
         tree = cfg["tree"]
+        self.dim = int(cfg["dim"])
         self._lev = np.ascontiguousarray(np.asarray(tree["level"], dtype=np.int32))
         self._ix = np.ascontiguousarray(np.asarray(tree["ix"], dtype=np.int32))
         self._iy = np.ascontiguousarray(np.asarray(tree["iy"], dtype=np.int32))
+        self._iz = np.ascontiguousarray(np.asarray(tree["iz"], dtype=np.int32)) if self.dim == 3 else None
         why = ctypes.c_int(0)
         self.h = self.lib.or_tree_create(ctypes.byref(self._p), self._lev.size, int(tree["maxlevel"]),
                                          self._lev.ctypes.data_as(_I), self._ix.ctypes.data_as(_I),
-                                         self._iy.ctypes.data_as(_I), ctypes.byref(why))
+                                         self._iy.ctypes.data_as(_I),
+                                         self._iz.ctypes.data_as(_I) if self._iz is not None else None,
+                                         ctypes.byref(why))
         if not self.h:
             if why.value == 2:
                 raise ValueError("the body must lie in the finest level of the tree")
@@ -503,7 +507,6 @@ class OracleTree:
         s = np.zeros(3, dtype=np.int64)
         self.lib.or_tree_sizes(self.h, s.ctypes.data_as(_LL))
         self.nleaf, self.nvel, self.ncomp = (int(x) for x in s)
-        self.dim = 2
         self.ncell = self.nleaf
         self.nfluid = int(np.count_nonzero(self.cell_types() == 0))
 
@@ -521,7 +524,7 @@ class OracleTree:
         return (self.nleaf, self.nvel, self.ncomp)
 
     def neighbours(self) -> np.ndarray:
-        nb = np.zeros((self.nleaf, 4, 2), dtype=np.int64)
+        nb = np.zeros((self.nleaf, 2 * self.dim, 1 << (self.dim - 1)), dtype=np.int64)
         self.lib.or_tree_neighbours(self.h, nb.ctypes.data_as(_LL))
         return nb
 
@@ -540,8 +543,8 @@ class OracleTree:
         return r.value
 
     def moments(self):
-        W = np.zeros((self.nleaf, 4))
-        q = np.zeros((self.nleaf, 2))
+        W = np.zeros((self.nleaf, self.dim + 2))
+        q = np.zeros((self.nleaf, self.dim))
         self.lib.or_tree_moments(self.h, _dp(W), _dp(q))
         return W, q
 
@@ -562,17 +565,17 @@ class OracleTree:
         """The finest uniform grid under the tree with the finest leaves'
         current values (C29): its links are the tree's, so its ghost band and
         wall quantities are the tree's.  Valid while this tree lives."""
-        fine = dict(self.cfg, n=[int(x) << int(self.cfg["tree"]["maxlevel"]) for x in self.cfg["n"][:2]])
+        fine = dict(self.cfg, n=[int(x) << int(self.cfg["tree"]["maxlevel"]) for x in self.cfg["n"][:self.dim]])
         fine.pop("tree", None)
         return OracleCase._view(self.lib, self.lib.or_tree_finest(self.h), fine, self)
 
     def sizes(self) -> np.ndarray:
-        """Edge length of every leaf along x and y."""
+        """Edge length of every leaf along each axis."""
         lev = self._lev.astype(np.float64)
-        H = [(self.cfg["hi"][a] - self.cfg["lo"][a]) / self.cfg["n"][a] for a in range(2)]
-        return np.stack([H[0] * 0.5 ** lev, H[1] * 0.5 ** lev], axis=1)
+        H = [(self.cfg["hi"][a] - self.cfg["lo"][a]) / self.cfg["n"][a] for a in range(self.dim)]
+        return np.stack([H[a] * 0.5 ** lev for a in range(self.dim)], axis=1)
 
     def centres(self) -> np.ndarray:
         hs = self.sizes()
-        return np.stack([self.cfg["lo"][0] + (self._ix + 0.5) * hs[:, 0],
-                         self.cfg["lo"][1] + (self._iy + 0.5) * hs[:, 1]], axis=1)
+        idx = [self._ix, self._iy] + ([self._iz] if self.dim == 3 else [])
+        return np.stack([self.cfg["lo"][a] + (idx[a] + 0.5) * hs[:, a] for a in range(self.dim)], axis=1)

@@ -78,17 +78,18 @@
  *       through the face zero with those face values.
  *
  *   C28 tree-refined physical grids (Sec. 4.2-4.4 use a tree-based AMR mesh
- *       and give no scheme for it): 2D, a root grid of equal cells, each
- *       leaf a square of level l (edge h / 2^l), face neighbours at most one
- *       level apart (2:1).  Finite volumes on the leaves with the uniform
- *       grid's arithmetic: the van Leer slope of a cell along an axis from
- *       the value on each side (the neighbour's, the mean of the two finer
- *       neighbours', or the freestream halo) over the distance between
- *       centres along the axis ((h_c + h_n) / 2; h_c across the domain
- *       edge); the face value of the upwind cell f + s sigma h / 2; the
- *       inflow of a side with two finer neighbours the mean of their face
- *       values (each covers half the side), so the flux through every
- *       interface is the same for both cells; one time step for all cells,
+ *       and give no scheme for it): a root grid of equal cells, each leaf a
+ *       square (2D, a quadtree) or cube (3D, an octree) of level l (edge
+ *       h / 2^l), face neighbours at most one level apart (2:1).  Finite
+ *       volumes on the leaves with the uniform grid's arithmetic: the van
+ *       Leer slope of a cell along an axis from the value on each side (the
+ *       neighbour's, the mean of the 2^(dim-1) finer neighbours', or the
+ *       freestream halo) over the distance between centres along the axis
+ *       ((h_c + h_n) / 2; h_c across the domain edge); the face value of the
+ *       upwind cell f + s sigma h / 2; the inflow of a side with finer
+ *       neighbours the mean of their face values (each covers an equal share
+ *       of the side), so the flux through every interface is the same for
+ *       both cells; one time step for all cells,
  *       C16 with the finest cell size.  On a tree of one level it is the
  *       uniform grid's step.
  *   C29 a body on a tree (Sec. 4.2-4.4 refine the mesh towards the wall):
@@ -1444,10 +1445,11 @@ struct or_tree {
   or_case *V;   /* velocity grid, gas, time step and body: a case on the finest uniform grid */
   long n;       /* leaves */
   int L;        /* finest level */
+  int D, NF;    /* dimension; leaves beyond a face at most (2^(D-1) finer ones) */
   int *lev;
-  double *h;    /* [n][2] edge lengths */
-  long *nb;     /* [n][4][2] face neighbours, sides 2a + (s > 0) */
-  double *f, *fnew, *sl; /* [n][nv][nc]; slopes [n][2][nv][nc] */
+  double *h;    /* [n][D] edge lengths */
+  long *nb;     /* [n][2D][NF] face neighbours, sides 2a + (s > 0) */
+  double *f, *fnew, *sl; /* [n][nv][nc]; slopes [n][D][nv][nc] */
   unsigned char *type;   /* [n] OR_FLUID, OR_GHOST, OR_SOLID (C29) */
   long *leafv;  /* [n] the finest-grid cell of a finest leaf, -1 for coarser leaves */
   int body;
@@ -1485,39 +1487,56 @@ static int tree_body_fits(const or_case *V, const long *own, const int *level, i
   return 1;
 }
 
+/* the finest-grid cells of a leaf: origin q0 and edge s (in finest cells) */
+static void leaf_block(const int *ix, const int *iy, const int *iz, int D, int L, int l, long c, long q0[3],
+                       long *s)
+{
+  *s = 1L << (L - l);
+  q0[0] = ix[c] * *s;
+  q0[1] = iy[c] * *s;
+  q0[2] = (D == 3) ? iz[c] * *s : 0;
+}
+
 or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int *level, const int *ix,
-                        const int *iy, int *why)
+                        const int *iy, const int *iz, int *why)
 {
   if (why) *why = 1;
-  if (p->dim != 2 || maxlevel < 0 || maxlevel > 12 || nleaf <= 0) return NULL;
+  const int D = p->dim;
+  if ((D != 2 && D != 3) || maxlevel < 0 || maxlevel > 12 || nleaf <= 0 || (D == 3 && !iz)) return NULL;
   for (int i = 0; i < 6; ++i)
     if (p->wall[i]) return NULL;
-  const long nfx = (long)p->n[0] << maxlevel, nfy = (long)p->n[1] << maxlevel;
+  long nf[3] = {1, 1, 1};
+  for (int a = 0; a < D; ++a) nf[a] = (long)p->n[a] << maxlevel;
+  const long nfc = nf[0] * nf[1] * nf[2];
   /* owner of every cell of the finest grid */
-  long *own = (long *)xcalloc((size_t)(nfx * nfy), sizeof(long));
-  for (long q = 0; q < nfx * nfy; ++q) own[q] = -1;
+  long *own = (long *)xcalloc((size_t)nfc, sizeof(long));
+  for (long q = 0; q < nfc; ++q) own[q] = -1;
   int ok = 1;
   for (long c = 0; c < nleaf && ok; ++c) {
     const int l = level[c];
-    if (l < 0 || l > maxlevel || ix[c] < 0 || iy[c] < 0 || ix[c] >= (p->n[0] << l) || iy[c] >= (p->n[1] << l)) {
-      ok = 0;
-      break;
-    }
-    const long s = 1L << (maxlevel - l);
-    for (long i = ix[c] * s; i < (ix[c] + 1) * s; ++i)
-      for (long j = iy[c] * s; j < (iy[c] + 1) * s; ++j) {
-        if (own[i + nfx * j] >= 0) ok = 0; /* overlapping leaves */
-        own[i + nfx * j] = c;
-      }
+    const int co[3] = {ix[c], iy[c], (D == 3) ? iz[c] : 0};
+    if (l < 0 || l > maxlevel) ok = 0;
+    for (int a = 0; a < D && ok; ++a)
+      if (co[a] < 0 || co[a] >= (p->n[a] << l)) ok = 0;
+    if (!ok) break;
+    long q0[3], s;
+    leaf_block(ix, iy, iz, D, maxlevel, l, c, q0, &s);
+    const long sz = (D == 3) ? s : 1;
+    for (long k = q0[2]; k < q0[2] + sz; ++k)
+      for (long j = q0[1]; j < q0[1] + s; ++j)
+        for (long i = q0[0]; i < q0[0] + s; ++i) {
+          const long q = i + nf[0] * (j + nf[1] * k);
+          if (own[q] >= 0) ok = 0; /* overlapping leaves */
+          own[q] = c;
+        }
   }
-  for (long q = 0; ok && q < nfx * nfy; ++q)
+  for (long q = 0; ok && q < nfc; ++q)
     if (own[q] < 0) ok = 0; /* a hole */
   or_tree *T = NULL;
   if (ok) {
     T = (or_tree *)xcalloc(1, sizeof(or_tree));
     or_params pf = *p;
-    pf.n[0] = (int)nfx;
-    pf.n[1] = (int)nfy;
+    for (int a = 0; a < D; ++a) pf.n[a] = (int)nf[a];
     T->V = or_create(&pf);
     /* the helper case never steps: only its state buffer is used (the
        scatter target of the body's ghost band) */
@@ -1525,38 +1544,55 @@ or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int 
     T->V->fnew = NULL;
     T->n = nleaf;
     T->L = maxlevel;
+    T->D = D;
+    T->NF = 1 << (D - 1);
+    const int NF = T->NF;
     T->lev = (int *)xcalloc((size_t)nleaf, sizeof(int));
-    T->h = (double *)xcalloc((size_t)nleaf * 2, sizeof(double));
-    T->nb = (long *)xcalloc((size_t)nleaf * 8, sizeof(long));
+    T->h = (double *)xcalloc((size_t)nleaf * D, sizeof(double));
+    T->nb = (long *)xcalloc((size_t)nleaf * 2 * D * NF, sizeof(long));
     T->nthreads = 1;
-    const double H[2] = {(p->hi[0] - p->lo[0]) / p->n[0], (p->hi[1] - p->lo[1]) / p->n[1]};
+    double H[3];
+    for (int a = 0; a < D; ++a) H[a] = (p->hi[a] - p->lo[a]) / p->n[a];
     for (long c = 0; c < nleaf && ok; ++c) {
       const int l = level[c];
       T->lev[c] = l;
-      for (int a = 0; a < 2; ++a) T->h[2 * c + a] = H[a] / (double)(1L << l);
-      const long s = 1L << (maxlevel - l);
-      const long i0 = ix[c] * s, j0 = iy[c] * s;
-      for (int a = 0; a < 2 && ok; ++a)
+      for (int a = 0; a < D; ++a) T->h[(size_t)D * c + a] = H[a] / (double)(1L << l);
+      long q0[3], s;
+      leaf_block(ix, iy, iz, D, maxlevel, l, c, q0, &s);
+      for (int a = 0; a < D && ok; ++a)
         for (int side = 0; side < 2 && ok; ++side) {
-          long *out = T->nb + (size_t)c * 8 + (2 * a + side) * 2;
-          out[0] = out[1] = -1;
-          /* the finest cells just beyond the face, in increasing transverse order */
-          const long fa = (a == 0) ? (side ? i0 + s : i0 - 1) : (side ? j0 + s : j0 - 1);
-          if (fa < 0 || fa >= (a == 0 ? nfx : nfy)) continue; /* the domain edge */
+          long *out = T->nb + ((size_t)c * 2 * D + 2 * a + side) * NF;
+          for (int j = 0; j < NF; ++j) out[j] = -1;
+          /* the finest cells just beyond the face, the first transverse axis
+             fastest: their distinct owners in the order met */
+          const long fa = side ? q0[a] + s : q0[a] - 1;
+          if (fa < 0 || fa >= nf[a]) continue; /* the domain edge */
+          const int u = (a == 0) ? 1 : 0, v = (a == 2) ? 1 : 2; /* the transverse axes */
+          const long sv = (D == 3) ? s : 1;
           int cnt = 0;
-          for (long t = 0; t < s; ++t) {
-            const long q = (a == 0) ? fa + nfx * (j0 + t) : (i0 + t) + nfx * fa;
-            const long o = own[q];
-            if (cnt > 0 && out[cnt - 1] == o) continue;
-            if (cnt == 2) {
-              ok = 0;
-              break;
+          for (long tv = 0; tv < sv && ok; ++tv)
+            for (long tu = 0; tu < s && ok; ++tu) {
+              long q[3];
+              q[a] = fa;
+              q[u] = q0[u] + tu;
+              q[v] = (D == 3) ? q0[v] + tv : 0;
+              const long o = own[q[0] + nf[0] * (q[1] + nf[1] * q[2])];
+              int seen = 0;
+              for (int j = 0; j < cnt; ++j) seen |= out[j] == o;
+              if (seen) continue;
+              if (cnt == NF) {
+                ok = 0;
+                break;
+              }
+              out[cnt++] = o;
             }
-            out[cnt++] = o;
-          }
-          /* 2:1: one neighbour of the same or the coarser level, or two of the finer one */
+          /* 2:1: one neighbour of the same or the coarser level, or NF of the finer one */
           if (cnt == 1 && !(level[out[0]] == l || level[out[0]] == l - 1)) ok = 0;
-          if (cnt == 2 && !(level[out[0]] == l + 1 && level[out[1]] == l + 1)) ok = 0;
+          if (cnt > 1) {
+            if (cnt != NF) ok = 0;
+            for (int j = 0; j < cnt; ++j)
+              if (level[out[j]] != l + 1) ok = 0;
+          }
         }
     }
     if (ok) {
@@ -1568,13 +1604,16 @@ or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int 
       int fits = tree_body_fits(V, own, level, maxlevel);
       for (long c = 0; c < nleaf && fits; ++c) {
         const int l = level[c];
-        const long s = 1L << (maxlevel - l);
-        const long i0 = ix[c] * s, j0 = iy[c] * s;
-        T->leafv[c] = (l == maxlevel) ? i0 + nfx * j0 : -1;
-        const unsigned char t0 = V->type[i0 + nfx * j0];
-        for (long i = i0; i < i0 + s && fits; ++i)
-          for (long j = j0; j < j0 + s; ++j)
-            if (V->type[i + nfx * j] != t0 || (l < maxlevel && t0 == OR_GHOST)) fits = 0;
+        long q0[3], s;
+        leaf_block(ix, iy, iz, D, maxlevel, l, c, q0, &s);
+        const long q00 = q0[0] + nf[0] * (q0[1] + nf[1] * q0[2]);
+        T->leafv[c] = (l == maxlevel) ? q00 : -1;
+        const unsigned char t0 = V->type[q00];
+        const long sz = (D == 3) ? s : 1;
+        for (long k = q0[2]; k < q0[2] + sz && fits; ++k)
+          for (long j = q0[1]; j < q0[1] + s && fits; ++j)
+            for (long i = q0[0]; i < q0[0] + s; ++i)
+              if (V->type[i + nf[0] * (j + nf[1] * k)] != t0 || (l < maxlevel && t0 == OR_GHOST)) fits = 0;
         T->type[c] = t0;
       }
       if (!fits) {
@@ -1586,7 +1625,7 @@ or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int 
       const size_t sz = (size_t)nleaf * T->V->nv * T->V->ncomp;
       T->f = (double *)xcalloc(sz, sizeof(double));
       T->fnew = (double *)xcalloc(sz, sizeof(double));
-      T->sl = (double *)xcalloc(sz * 2, sizeof(double));
+      T->sl = (double *)xcalloc(sz * D, sizeof(double));
       for (long c = 0; c < nleaf; ++c)
         memcpy(T->f + (size_t)c * T->V->nv * T->V->ncomp, T->V->finf, sizeof(double) * T->V->nv * T->V->ncomp);
     }
@@ -1628,7 +1667,7 @@ double or_tree_dt(const or_tree *T) { return T->V->dt; }
 
 void or_tree_neighbours(const or_tree *T, long long *nb)
 {
-  for (long i = 0; i < T->n * 8; ++i) nb[i] = T->nb[i];
+  for (long i = 0; i < T->n * 2 * T->D * T->NF; ++i) nb[i] = T->nb[i];
 }
 
 void or_tree_get_f(const or_tree *T, double *f)
@@ -1658,37 +1697,45 @@ static void tree_scatter(or_tree *T)
     if (T->leafv[c] >= 0) memcpy(T->V->f + (size_t)T->leafv[c] * row, T->f + (size_t)c * row, sizeof(double) * row);
 }
 
-/* the value on side (a, s) of fluid leaf c as its slope sees it, and the
-   distance to it along a (C28; a ghost neighbour's link value, C29) */
+/* the leaves beyond side (a, s) of leaf c */
+static const long *tree_nbrs(const or_tree *T, long c, int a, int s)
+{
+  return T->nb + ((size_t)c * 2 * T->D + 2 * a + (s > 0)) * T->NF;
+}
+
+/* the value on side (a, s) of fluid leaf c as its slope sees it (the
+   neighbour's, the mean of the finer neighbours', the freestream halo; a
+   ghost neighbour's link value, C29), and the distance to it along a (C28) */
 static double tree_side(const or_tree *T, const double *f, long c, int a, int s, int k, int m, double *dist)
 {
-  const long *nb = T->nb + (size_t)c * 8 + (2 * a + (s > 0)) * 2;
-  const int nv = T->V->nv, nc = T->V->ncomp;
-  const double hc = T->h[2 * c + a];
+  const long *nb = tree_nbrs(T, c, a, s);
+  const int nv = T->V->nv, nc = T->V->ncomp, D = T->D;
+  const double hc = T->h[(size_t)D * c + a];
   if (nb[0] < 0) {
     *dist = hc;
     return T->V->finf[k * nc + m]; /* the freestream halo */
   }
-  *dist = 0.5 * (hc + T->h[2 * nb[0] + a]);
+  *dist = 0.5 * (hc + T->h[(size_t)D * nb[0] + a]);
   if (T->type[nb[0]] != OR_FLUID) return tree_link_value(T, nb[0], c, k, m);
-  const double v0 = f[((size_t)nb[0] * nv + k) * nc + m];
-  if (nb[1] < 0) return v0;
-  return 0.5 * (v0 + f[((size_t)nb[1] * nv + k) * nc + m]);
+  double v = f[((size_t)nb[0] * nv + k) * nc + m];
+  int cnt = 1;
+  while (cnt < T->NF && nb[cnt] >= 0) v += f[((size_t)nb[cnt++] * nv + k) * nc + m];
+  return (cnt == 1) ? v : v * (1.0 / cnt);
 }
 
 /* face value on side (a, s) of leaf c (Eq. reconstruction with the slope of C28) */
 static double tree_face(const or_tree *T, const double *f, long c, int a, int s, int k, int m)
 {
-  const int nv = T->V->nv, nc = T->V->ncomp;
+  const int nv = T->V->nv, nc = T->V->ncomp, D = T->D;
   const double fc = f[((size_t)c * nv + k) * nc + m];
-  const double sig = T->sl[(((size_t)c * 2 + a) * nv + k) * nc + m];
-  return fc + sig * (s * 0.5 * T->h[2 * c + a]);
+  const double sig = T->sl[(((size_t)c * D + a) * nv + k) * nc + m];
+  return fc + sig * (s * 0.5 * T->h[(size_t)D * c + a]);
 }
 
 int or_tree_step(or_tree *T, int nsteps, double *residual)
 {
   or_case *V = T->V;
-  const int nv = V->nv, nc = V->ncomp, D = 2, nw = D + 2;
+  const int nv = V->nv, nc = V->ncomp, D = T->D, nw = D + 2;
   const long n = T->n;
   double *Wold = (double *)xcalloc((size_t)n * nw, sizeof(double));
   double *Wnew = (double *)xcalloc((size_t)n * nw, sizeof(double));
@@ -1699,7 +1746,7 @@ int or_tree_step(or_tree *T, int nsteps, double *residual)
       tree_scatter(T);
       or_ghost_band(V, V->f, NULL, NULL, NULL, NULL, V->lval, NULL);
     }
-    /* slopes of every fluid leaf along both axes (Eq. limiter over the centre distances) */
+    /* slopes of every fluid leaf along each axis (Eq. limiter over the centre distances) */
 #pragma omp parallel for num_threads(T->nthreads) schedule(dynamic, 16)
     for (long c = 0; c < n; ++c) {
       if (T->type[c] != OR_FLUID) continue;
@@ -1710,7 +1757,7 @@ int or_tree_step(or_tree *T, int nsteps, double *residual)
             double dm, dp;
             const double fm = tree_side(T, T->f, c, a, -1, k, m, &dm);
             const double fp = tree_side(T, T->f, c, a, +1, k, m, &dp);
-            T->sl[(((size_t)c * 2 + a) * nv + k) * nc + m] = or_vanleer((fc - fm) / dm, (fp - fc) / dp);
+            T->sl[(((size_t)c * D + a) * nv + k) * nc + m] = or_vanleer((fc - fm) / dm, (fp - fc) / dp);
           }
     }
     /* transport and relaxation of every leaf */
@@ -1740,17 +1787,20 @@ int or_tree_step(or_tree *T, int nsteps, double *residual)
               const double fout = tree_face(T, T->f, c, a, s, k, m);
               /* inflow through the upwind side: the upwind cells' face values,
                  each over the share of the side it covers */
-              const long *nb = T->nb + (size_t)c * 8 + (2 * a + (-s > 0)) * 2;
+              const long *nb = tree_nbrs(T, c, a, -s);
               double fin;
-              if (nb[0] < 0)
+              if (nb[0] < 0) {
                 fin = V->finf[k * nc + m]; /* halo: its value, zero slope */
-              else if (T->type[nb[0]] != OR_FLUID) /* a ghost: its link value with the one-sided slope (C14) */
+              } else if (T->type[nb[0]] != OR_FLUID) {
+                /* a ghost: its link value with the one-sided slope (C14) */
                 fin = 0.5 * (tree_link_value(T, nb[0], c, k, m) + fc);
-              else if (nb[1] < 0)
+              } else {
                 fin = tree_face(T, T->f, nb[0], a, s, k, m);
-              else
-                fin = 0.5 * (tree_face(T, T->f, nb[0], a, s, k, m) + tree_face(T, T->f, nb[1], a, s, k, m));
-              div += fabs(xia) * (fout - fin) / T->h[2 * c + a];
+                int cnt = 1;
+                while (cnt < T->NF && nb[cnt] >= 0) fin += tree_face(T, T->f, nb[cnt++], a, s, k, m);
+                if (cnt > 1) fin *= 1.0 / cnt;
+              }
+              div += fabs(xia) * (fout - fin) / T->h[(size_t)D * c + a];
             }
             T->fnew[((size_t)c * nv + k) * nc + m] = fc - V->dt * div + V->dt / tau * (gS[k * nc + m] - fc);
           }
@@ -1761,7 +1811,7 @@ int or_tree_step(or_tree *T, int nsteps, double *residual)
     T->f = T->fnew;
     T->fnew = t;
     for (long c = 0; c < n; ++c) conservative(V, T->f, c, Wnew + c * nw);
-    /* residual over the leaves (the formula of the uniform grid, C18) */
+    /* residual over the fluid leaves (the formula of the uniform grid, C18) */
     res = 0.0;
     for (int i = 0; i < nw; ++i) {
       double num = 0.0, den = 0.0;
@@ -1802,7 +1852,7 @@ void or_tree_forces(or_tree *T, double *F3, double *Q, double *CD, double *CL)
 
 void or_tree_moments(const or_tree *T, double *W, double *q)
 {
-  const int D = 2, nv = T->V->nv, nc = T->V->ncomp;
+  const int D = T->D, nv = T->V->nv, nc = T->V->ncomp;
   double out[16];
   for (long c = 0; c < T->n; ++c) {
     or_cell_moments(T->V, T->f + (size_t)c * nv * nc, out);

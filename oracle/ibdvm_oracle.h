@@ -140,24 +140,27 @@ double or_cut_fraction_2d(const double *blo, const double *bhi, const double *n)
 double or_cut_fraction_3d(const double *blo, const double *bhi, const double *n);
 double or_residual(const or_case *C, const double *Wold, const double *Wnew);
 
-/* Tree-refined 2D grids (reading C28): leaves (level, ix, iy) over the root
-   grid p->n[0] x p->n[1] on [lo, hi], integer coordinates of the leaf's level
-   (0 <= ix < n[0] 2^level); the leaves must tile the domain and face
-   neighbours differ by at most one level.  The domain faces are freestream.
+/* Tree-refined grids (reading C28), quadtrees in 2D and octrees in 3D:
+   leaves (level, ix, iy, iz) over the root grid p->n on [lo, hi], integer
+   coordinates of the leaf's level (0 <= ix < n[0] 2^level; iz NULL in 2D);
+   the leaves must tile the domain and face neighbours differ by at most one
+   level (a face borders one leaf or 2^(dim-1) finer ones).  The domain
+   faces are freestream.
    A body (reading C29) must lie in the finest level: every cell its ghost
    band reads or writes is a leaf of the finest level, a coarser leaf is all
    fluid or all solid.  NULL when refused; *why (if given) = 1 for an invalid
    tree, 2 for a body outside the finest level, 0 on success. */
 typedef struct or_tree or_tree;
 or_tree *or_tree_create(const or_params *p, long nleaf, int maxlevel, const int *level, const int *ix,
-                        const int *iy, int *why);
+                        const int *iy, const int *iz, int *why);
 void or_tree_destroy(or_tree *T);
 void or_tree_set_threads(or_tree *T, int nthreads);
 /* sizes: nleaf, nvel, ncomp */
 void or_tree_sizes(const or_tree *T, long long *out3);
 double or_tree_dt(const or_tree *T);
-/* face neighbours nb[leaf][side 2a + (s > 0)][2] (-1: none; the first is -1
-   at the domain edge, the second unless two finer neighbours share the side) */
+/* face neighbours nb[leaf][side 2a + (s > 0)][2^(dim-1)] (-1: none; the first
+   is -1 at the domain edge, the others unless finer neighbours share the
+   side, in the order met with the first transverse axis fastest) */
 void or_tree_neighbours(const or_tree *T, long long *nb);
 void or_tree_get_f(const or_tree *T, double *f);
 void or_tree_set_f(or_tree *T, const double *f);

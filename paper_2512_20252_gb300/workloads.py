@@ -407,14 +407,105 @@ def tree_leaves(root, maxlevel, lo, hi, center, radii, metric="point", segment=N
     return {"maxlevel": L, "level": level, "ix": ix, "iy": iy}
 
 
+def tree_leaves_3d(root, maxlevel, lo, hi, center, radii):
+    """Leaves (level, ix, iy, iz) of a 2:1-balanced octree over a root grid of
+    root[0] x root[1] x root[2] cells on [lo, hi]: a cell of level l <
+    maxlevel is split while its centre lies within radii[l] of `center`, then
+    any leaf with a face neighbour two or more levels finer is split until
+    the tree is balanced; listed depth first (Z order: root cells with x
+    fastest, the eight children with x, then y, then z fastest).  Geometry
+    only."""
+    n0 = tuple(int(r) for r in root)
+    L = maxlevel
+    nf = tuple(r << L for r in n0)
+    lev = np.zeros(nf, dtype=np.int64)
+
+    def blocks(l):
+        s = 1 << (L - l)
+        return lev.reshape(n0[0] << l, s, n0[1] << l, s, n0[2] << l, s)
+
+    def uniform_at(l):
+        bl = blocks(l)
+        return (bl.min(axis=(1, 3, 5)) == l) & (bl.max(axis=(1, 3, 5)) == l)
+
+    def split(l, mask):
+        s = 1 << (L - l)
+        up = mask.repeat(s, axis=0).repeat(s, axis=1).repeat(s, axis=2)
+        lev[up] = l + 1
+
+    h0 = [(hi[a] - lo[a]) / n0[a] for a in range(3)]
+    for l in range(L):
+        c = [lo[a] + (np.arange(n0[a] << l) + 0.5) * h0[a] * 2.0 ** -l for a in range(3)]
+        X, Y, Z = np.meshgrid(*c, indexing="ij")
+        near = np.sqrt((X - center[0]) ** 2 + (Y - center[1]) ** 2 + (Z - center[2]) ** 2) <= radii[l]
+        split(l, uniform_at(l) & near)
+    changed = True
+    while changed:
+        changed = False
+        for l in range(L):
+            s = 1 << (L - l)
+            nl = tuple(r << l for r in n0)
+            big = np.zeros(nl, dtype=bool)
+            for a in range(3):
+                # the largest level in the slab of finest cells on each side of every block
+                first = np.take(lev, np.arange(0, nf[a], s), axis=a)
+                last = np.take(lev, np.arange(s - 1, nf[a], s), axis=a)
+                shp = [nl[0], s, nl[1], s, nl[2], s]
+                shp[2 * a + 1] = 1
+                fmax = first.reshape(shp).max(axis=(1, 3, 5))
+                lmax = last.reshape(shp).max(axis=(1, 3, 5))
+                lo_sl = [slice(None)] * 3
+                hi_sl = [slice(None)] * 3
+                lo_sl[a], hi_sl[a] = slice(1, None), slice(None, -1)
+                big[tuple(lo_sl)] |= lmax[tuple(hi_sl)] >= l + 2
+                big[tuple(hi_sl)] |= fmax[tuple(lo_sl)] >= l + 2
+            m = uniform_at(l) & big
+            if m.any():
+                split(l, m)
+                changed = True
+    level, ix, iy, iz = [], [], [], []
+
+    def visit(l, i, j, k):
+        s = 1 << (L - l)
+        if lev[i * s, j * s, k * s] == l:
+            level.append(l)
+            ix.append(i)
+            iy.append(j)
+            iz.append(k)
+            return
+        for dk in (0, 1):
+            for dj in (0, 1):
+                for di in (0, 1):
+                    visit(l + 1, 2 * i + di, 2 * j + dj, 2 * k + dk)
+
+    for k in range(n0[2]):
+        for j in range(n0[1]):
+            for i in range(n0[0]):
+                visit(0, i, j, k)
+    return {"maxlevel": L, "level": level, "ix": ix, "iy": iy, "iz": iz}
+
+
+def tree_case_3d(root=8, maxlevel=2, L=2.0, nv=6, V=4.5, Kn=0.1, Ma=0.3, radii=None, center=(0.0, 0.0, 0.0),
+                 precision="fp64", steps=20, body=None):
+    """A 3D case on an octree: root^3 cells on [-L, L]^3 refined about
+    `center` (by default to level 1 within 0.6 L and to level 2 within 0.3 L),
+    freestream domain faces, no body unless given (in the finest level)."""
+    if radii is None:
+        radii = [0.6 * L, 0.3 * L] + [0.3 * L * 0.5 ** i for i in range(1, maxlevel)]
+    d = _case(3, root, L, nv, V, Kn, Ma, body or {"kind": "none"}, precision=precision, steps=steps)
+    d["tree"] = tree_leaves_3d((root, root, root), maxlevel, d["lo"], d["hi"], center, radii)
+    return d
+
+
 def tree_centres(case):
-    """Centres (nleaf, 2) of the leaves of a tree case (geometry only)."""
+    """Centres (nleaf, dim) of the leaves of a tree case (geometry only)."""
     tr = case["tree"]
+    D = int(case["dim"])
     lev = np.asarray(tr["level"], dtype=np.float64)
-    h = np.array([(case["hi"][a] - case["lo"][a]) / case["n"][a] for a in range(2)])
+    h = np.array([(case["hi"][a] - case["lo"][a]) / case["n"][a] for a in range(D)])
     size = h[None, :] * (0.5 ** lev)[:, None]
-    ij = np.stack([np.asarray(tr["ix"], dtype=np.float64), np.asarray(tr["iy"], dtype=np.float64)], axis=1)
-    return np.asarray(case["lo"][:2])[None, :] + (ij + 0.5) * size
+    ij = np.stack([np.asarray(tr[k], dtype=np.float64) for k in ("ix", "iy", "iz")[:D]], axis=1)
+    return np.asarray(case["lo"][:D])[None, :] + (ij + 0.5) * size
 
 
 def tree_case(root=16, maxlevel=2, L=2.0, nv=12, V=4.5, Kn=0.1, Ma=0.3, radii=None, center=(0.0, 0.0),

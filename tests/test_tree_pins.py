@@ -232,3 +232,129 @@ def test_a_body_outside_the_finest_level_is_refused():
     with pytest.raises(ValueError, match="finest level"):
         oracle.OracleTree(wl.tree_case(16, 2, nv=6, body=wl.circle(0.2, center=(1.0, 0.0))))
     oracle.OracleTree(wl.tree_case(16, 2, nv=6, body=wl.circle(0.3)))
+
+
+# ---------------------------------------------------------------------------
+# octrees (3D): the same pins, with four finer leaves across a face
+# ---------------------------------------------------------------------------
+
+def _uniform_tree_3d(n, level):
+    root = n >> level
+    ix, iy, iz = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    return root, {"maxlevel": level, "level": [level] * n ** 3, "ix": ix.T.ravel().tolist(),
+                  "iy": iy.T.ravel().tolist(), "iz": iz.T.ravel().tolist()}
+
+
+@pytest.mark.parametrize("body", [False, True])
+def test_one_level_octree_is_the_uniform_step(body):
+    n = 12
+    case = wl._case(3, n, 2.0, 6, 4.5, 0.1, 0.4, wl.sphere(0.7) if body else {"kind": "none"})
+    u = oracle.OracleCase(case)
+    root, tree = _uniform_tree_3d(n, 1)
+    t = oracle.OracleTree(dict(case, n=[root] * 3, tree=tree))
+    np.testing.assert_array_equal(t.cell_types(), u.cell_types())
+    assert t.dt == pytest.approx(u.dt, rel=1e-15)
+    rng = np.random.default_rng(6)
+    f0 = u.get_f() * (1.0 + 0.2 * rng.uniform(-1.0, 1.0, size=u.shape()))
+    u.set_f(f0)
+    t.set_f(f0)
+    ru = u.step(3)
+    rt = t.step(3)
+    fu, ft = u.get_f(), t.get_f()
+    assert np.abs(ft - fu).max() < 1e-13 * np.abs(fu).max()
+    assert rt == pytest.approx(ru, rel=1e-10)
+    if body:
+        Fu, _, CDu, _ = u.forces()
+        Ft, _, CDt, _ = t.forces()
+        assert np.abs(Ft - Fu).max() < 1e-12 * np.abs(Fu).max()
+
+
+def test_octree_uniform_state_and_conservation():
+    """On a three-level octree: a uniform state stays uniform away from the
+    domain edges, and with relaxation made negligible the volume-weighted
+    total of every velocity changes only by the (cancelling) freestream
+    boundary fluxes, across faces with four finer neighbours."""
+    case = wl.tree_case_3d(16, 2, nv=6)
+    t = oracle.OracleTree(case)
+    nb = t.neighbours()
+    assert (nb[:, :, 3] >= 0).any()  # faces with four finer neighbours
+    t.step(2)
+    f = t.get_f()
+    xc = t.centres()
+    inner = np.where(np.abs(xc).max(axis=1) < 2.0 - 4 * 0.25)[0]
+    lev = np.asarray(case["tree"]["level"])
+    assert set(lev[inner]) == {0, 1, 2}
+    assert np.abs(f[inner] - f[inner][:1]).max() < 1e-14 * np.abs(f[inner]).max()
+    case = wl.tree_case_3d(8, 2, nv=6, Kn=1e12)
+    t = oracle.OracleTree(case)
+    xc, hs = t.centres(), t.sizes()
+    vol = hs.prod(axis=1)
+    f0 = t.get_f() * (1.0 + 0.2 * np.exp(-((xc - [0.2, -0.1, 0.05]) ** 2).sum(axis=1) / 0.1))[:, None, None]
+    t.set_f(f0)
+    t.step(1)
+    d = np.einsum("c,ckm->km", vol, t.get_f() - f0)
+    ref = np.einsum("c,ckm->km", vol, np.abs(f0 - f0[:1]))
+    assert np.abs(d).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_invalid_octrees_are_refused():
+    case = wl.tree_case_3d(4, 2, nv=4)
+    tr = case["tree"]
+    bad = {k: (v[1:] if isinstance(v, list) else v) for k, v in tr.items()}
+    with pytest.raises(ValueError):
+        oracle.OracleTree(dict(case, tree=bad))
+    # a level-2 block next to level-0 cells
+    lev, ix, iy, iz = [], [], [], []
+    for k in range(4):
+        for j in range(4):
+            for i in range(4):
+                if (i, j, k) == (1, 1, 1):
+                    for kk in range(4):
+                        for jj in range(4):
+                            for ii in range(4):
+                                lev.append(2)
+                                ix.append(4 + ii)
+                                iy.append(4 + jj)
+                                iz.append(4 + kk)
+                else:
+                    lev.append(0)
+                    ix.append(i)
+                    iy.append(j)
+                    iz.append(k)
+    with pytest.raises(ValueError):
+        oracle.OracleTree(dict(case, tree={"maxlevel": 2, "level": lev, "ix": ix, "iy": iy, "iz": iz}))
+    t = oracle.OracleTree(case)
+    assert np.sum(t.sizes().prod(axis=1)) == pytest.approx(4.0 ** 3)
+
+
+def test_body_on_a_refined_octree_is_the_finest_grid_near_it():
+    case = wl.tree_case_3d(8, 2, nv=6, radii=[1.6, 1.2], body=wl.sphere(0.4))
+    t = oracle.OracleTree(case)
+    ucase = dict(case, n=[32, 32, 32])
+    ucase.pop("tree")
+    u = oracle.OracleCase(ucase)
+    tr = case["tree"]
+    lev = np.asarray(tr["level"])
+    levmap = np.zeros((32, 32, 32), dtype=int)
+    for l, i, j, k in zip(tr["level"], tr["ix"], tr["iy"], tr["iz"]):
+        s = 1 << (2 - l)
+        levmap[i * s:(i + 1) * s, j * s:(j + 1) * s, k * s:(k + 1) * s] = l
+    fine = np.where(lev == 2)[0]
+    I, J, K = (np.asarray(tr[q])[fine] for q in ("ix", "iy", "iz"))
+    vcell = I + 32 * (J + 32 * K)
+    ok = np.array([levmap[max(i - 3, 0):i + 4, max(j - 3, 0):j + 4, max(k - 3, 0):k + 4].min() == 2
+                   for i, j, k in zip(I, J, K)])
+    np.testing.assert_array_equal(t.cell_types()[fine], u.cell_types()[vcell])
+    assert ok.sum() > 100 and np.any(t.cell_types()[fine][ok] == 1)
+    bump = lambda x: 1.0 + 0.2 * np.exp(-((x - [0.1, -0.05, 0.02]) ** 2).sum(axis=1) / 0.3)
+    uc = np.stack(np.meshgrid(*[ucase["lo"][a] + (np.arange(32) + 0.5) * 4.0 / 32 for a in range(3)],
+                              indexing="ij"), axis=-1).transpose(2, 1, 0, 3).reshape(-1, 3)
+    t.set_f(t.get_f() * bump(t.centres())[:, None, None])
+    u.set_f(u.get_f() * bump(uc)[:, None, None])
+    t.step(1)
+    u.step(1)
+    ft, fu = t.get_f()[fine][ok], u.get_f()[vcell][ok]
+    assert np.abs(ft - fu).max() < 1e-14 * np.abs(fu).max()
+    Ft, _, CDt, _ = t.forces()
+    Fu, _, CDu, _ = u.forces()
+    assert np.abs(Ft - Fu).max() < 1e-13 * np.abs(Fu).max()
