@@ -121,17 +121,19 @@ typedef struct {
   int flags;
 } ibdvm_gas_desc;
 
-/* Tree-refined 2D grid (the tree-based AMR meshes of Sec. 4.2-4.4, which the
-   paper states but does not specify): nleaf leaves of a quadtree over the
-   root grid of ibdvm_create_tree, leaf c of level level[c] (0 = a root cell,
-   edge halved per level, at most maxlevel <= 12) at integer coordinates
-   (ix[c], iy[c]) of its level (0 <= ix < n[0] 2^level).  The leaves must tile
-   the domain and face neighbours differ by at most one level (2:1).  The
-   arrays are read during the call only. */
+/* Tree-refined grid (the tree-based AMR meshes of Sec. 4.2-4.4, which the
+   paper states but does not specify): nleaf leaves of a quadtree (2D) or an
+   octree (3D) over the root grid of ibdvm_create_tree, leaf c of level
+   level[c] (0 = a root cell, edge halved per level, at most maxlevel <= 12)
+   at integer coordinates (ix[c], iy[c], iz[c]) of its level (0 <= ix < n[0]
+   2^level; iz NULL in 2D).  The leaves must tile the domain and face
+   neighbours differ by at most one level (2:1: a face borders one leaf or
+   2^(dim-1) finer ones).  The arrays are read during the call only. */
 typedef struct {
   int nleaf;
   int maxlevel;
   const int *level, *ix, *iy;
+  const int *iz;
 } ibdvm_tree_desc;
 
 /* Immersed body and its wall (Sec. 2.3): Maxwell accommodation coefficient
@@ -174,13 +176,13 @@ typedef struct {
 ibdvm_status ibdvm_create_grid(const ibdvm_grid_desc *grid, const ibdvm_vgrid_desc *vgrid,
                                const ibdvm_gas_desc *gas, void *cuda_stream, ibdvm_ctx **out);
 
-/* Creates a context on a tree-refined 2D grid: root is the grid of level-0
-   cells (dim 2), tree its leaves (ibdvm_tree_desc), which are the cells of
+/* Creates a context on a tree-refined grid: root is the grid of level-0
+   cells (dim 2 or 3), tree its leaves (ibdvm_tree_desc), which are the cells of
    the context in the order given (ncell = nleaf; ibdvm_moments, ibdvm_get_f
    and ibdvm_set_f index them so).  Finite volumes on the leaves: the van Leer
    slope of a leaf along an axis from the value on each side (the neighbour,
-   the mean of two finer neighbours, or the freestream halo) over the distance
-   between centres; the upwind leaf's face value; a side shared with two finer
+   the mean of the finer neighbours, or the freestream halo) over the distance
+   between centres; the upwind leaf's face value; a side shared with finer
    leaves takes the mean of their face values, so every interface conserves;
    dt from the CFL number with the finest edge.  FP64 or mixed precision (the
    mixed path keeps FP32 f and runs the same kernel in FP32).  A body may be
@@ -194,9 +196,10 @@ ibdvm_status ibdvm_create_tree(const ibdvm_grid_desc *root, const ibdvm_tree_des
                                const ibdvm_vgrid_desc *vgrid, const ibdvm_gas_desc *gas, void *cuda_stream,
                                ibdvm_ctx **out);
 
-/* The face neighbours of every leaf of a tree context: nb[leaf][side][2]
-   with side = 2a + (s > 0) (-1: none; the first is -1 at the domain edge, the
-   second unless two finer leaves share the side).  IBDVM_E_STATE on a
+/* The face neighbours of every leaf of a tree context: nb[leaf][side][m]
+   with side = 2a + (s > 0) and m < 2^(dim-1) (-1: none; the first is -1 at
+   the domain edge, the others unless finer leaves share the side, in the
+   order met with the first transverse axis fastest).  IBDVM_E_STATE on a
    context that is not a tree. */
 ibdvm_status ibdvm_tree_neighbours(const ibdvm_ctx *ctx, long long *nb);
 

@@ -529,7 +529,8 @@ namespace {
 void upload_tree_tables(ibdvm_ctx *ctx, const std::vector<int> &glink, const std::vector<int> &far) {
   std::vector<int> sti, lrec;
   std::vector<double> stg;
-  build_tree_stencils(ctx->tree_lev_h, ctx->tree_nb_h, ctx->tree_h0, ctx->geom.type, glink, sti, stg, lrec);
+  build_tree_stencils(ctx->dim, ctx->tree_lev_h, ctx->tree_nb_h, ctx->tree_h0, ctx->geom.type, glink, sti, stg,
+                      lrec);
   upload(ctx, ctx->tree_sti, sti, "upload tree stencils");
   upload(ctx, ctx->tree_stg, stg, "upload tree stencil geometry");
   upload(ctx, ctx->tree_lrec, lrec, "upload tree leaf records");
@@ -614,7 +615,7 @@ static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_des
         ctx->err = err;
         throw Fail{IBDVM_E_INVAL};
       }
-      for (int a = 0; a < 2; ++a) gd.n[a] = grid->n[a] << tree->maxlevel;
+      for (int a = 0; a < grid->dim; ++a) gd.n[a] = grid->n[a] << tree->maxlevel;
     }
     if (!build_grid(gd, *vgrid, *gas, ctx->geom, err)) {
       ctx->err = err;
@@ -632,7 +633,7 @@ static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_des
       Gt.type.assign(static_cast<size_t>(tree->nleaf), IBDVM_CELL_FLUID);
       Gt.nfluid = tree->nleaf;
       ctx->tree = true;
-      for (int a = 0; a < 2; ++a) ctx->tree_h0[a] = (grid->hi[a] - grid->lo[a]) / grid->n[a];
+      for (int a = 0; a < grid->dim; ++a) ctx->tree_h0[a] = (grid->hi[a] - grid->lo[a]) / grid->n[a];
     }
     const Geom &G = ctx->geom;
     ctx->precision = gas->precision;
@@ -648,13 +649,16 @@ static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_des
     ctx->kst_h.resize(G.nv);
     for (int i = 0; i < G.nv; ++i) ctx->kst_h[i] = i;
     if (tree) {
-      // trees: grouped by quadrant (x < 0 in bit 0, y < 0 in bit 1), packed,
-      // so that the threads of a warp of the tree sweep share upwind sides
+      // trees: grouped by orthant (bit a: component a < 0), packed, so that
+      // the threads of a warp of the tree sweep share upwind sides
       int pos = 0;
-      for (int o = 0; o < 4; ++o) {
-        if (o > 0) ctx->tree_qb[o - 1] = pos;
-        for (int i = 0; i < G.nv; ++i)
-          if (((G.xi[3 * i] < 0.0) ? 1 : 0) + ((G.xi[3 * i + 1] < 0.0) ? 2 : 0) == o) ctx->kst_h[i] = pos++;
+      for (int o = 0; o < (1 << G.dim); ++o) {
+        if (o > 0 && o < 4) ctx->tree_qb[o - 1] = pos;
+        for (int i = 0; i < G.nv; ++i) {
+          int oi = 0;
+          for (int a = 0; a < G.dim; ++a) oi |= (G.xi[3 * i + a] < 0.0) ? (1 << a) : 0;
+          if (oi == o) ctx->kst_h[i] = pos++;
+        }
       }
     }
     if (!tma_off && gas->precision == IBDVM_MIXED && tma_encoder_available()) {
@@ -705,7 +709,7 @@ static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_des
     if (tree) {
       std::vector<int> sti, lrec;
       std::vector<double> stg;
-      build_tree_stencils(tlev, tnb, ctx->tree_h0, {}, {}, sti, stg, lrec);
+      build_tree_stencils(G.dim, tlev, tnb, ctx->tree_h0, {}, {}, sti, stg, lrec);
       ctx->tree_sti = dalloc<int>(ctx, sti.size(), "tree stencils");
       ctx->tree_stg = dalloc<double>(ctx, stg.size(), "tree stencil geometry");
       ctx->tree_lrec = dalloc<int>(ctx, lrec.size(), "tree leaf records");

@@ -129,7 +129,7 @@ struct ibdvm_ctx {
   int *tree_sti = nullptr;    // [leaf][10][8] stencil rows and flags (build_tree_stencils)
   double *tree_stg = nullptr; // [leaf][10][4] stencil geometry
   int *tree_lrec = nullptr;   // [leaf][8] side counts, regular flag
-  double tree_h0[2] = {0, 0};
+  double tree_h0[3] = {0, 0, 0};
   int tree_L = 0;
   std::vector<int> tree_lev_h, tree_own; // leaf levels; the leaf of every finest-grid cell
   ibdvm::Geom tree_vgeom;                // the finest grid (a body is placed there)
@@ -183,16 +183,19 @@ bool tma_encoder_available();
 bool build_tree_mesh(const ibdvm_grid_desc &root, const ibdvm_tree_desc &t, std::vector<int> &lev,
                      std::vector<int> &nb, std::vector<int> &own, std::string &err);
 // the sweep's stencil tables; type (leaf classes) and glink (the link from
-// the ghost across side 2a + sd of a fluid leaf, [leaf][4]) may be empty
+// the ghost across side 2a + sd of a fluid leaf, [leaf][2 dim]) may be empty
 // without a body
-void build_tree_stencils(const std::vector<int> &lev, const std::vector<int> &nb, const double h0[2],
+void build_tree_stencils(int D, const std::vector<int> &lev, const std::vector<int> &nb, const double h0[3],
                          const std::vector<uint8_t> &type, const std::vector<int> &glink,
                          std::vector<int> &sti, std::vector<double> &stg, std::vector<int> &lrec);
+// the stencil entries of a leaf (D own + 2 D 2^(D-1) upwind) and the ints of an entry
+__host__ __device__ constexpr int tree_entries(int D) { return D + 2 * D * (1 << (D - 1)); }
+__host__ __device__ constexpr int tree_entry_ints(int D) { return D == 2 ? 8 : 12; }
 // a body placed on the finest grid Gv of a tree, moved onto its leaves: false
 // with a message unless every cell the ghost band reads or writes is a leaf
 // of the finest level and every coarser leaf is all fluid or all solid.
 // Gt receives the leaf classes and the ghost band in leaf indices; glink
-// [leaf][4] the link of a ghost face neighbour; far [link] the row the
+// [leaf][2 dim] the link of a ghost face neighbour; far [link] the row the
 // donor's slope sees beyond it along the link axis (a leaf, -2 the halo,
 // -3 - l the ghost value of link l)
 bool map_tree_body(const Geom &Gv, const std::vector<int> &own, const std::vector<int> &lev, int L, Geom &Gt,

@@ -376,15 +376,15 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
 }
 
 // ---------------------------------------------------------------------------
-// tree-refined 2D grids (the tree-based AMR meshes of Sec. 4.2-4.4; the paper
+// tree-refined grids (the tree-based AMR meshes of Sec. 4.2-4.4; the paper
 // gives no scheme for them): finite volumes on the leaves of a 2:1-balanced
-// quadtree.  The slope of a cell along an axis is the van Leer limited slope
-// of the values on each side (the neighbour's, the mean of the two finer
-// neighbours', or the freestream halo) over the distances between centres
-// along the axis; the upwind cell supplies the face value f + s sigma h / 2;
-// a side with two finer neighbours takes the mean of their face values as
-// its inflow, so both cells of an interface see the same flux.  One time
-// step for all leaves (the CFL of the finest cell).
+// quadtree (2D) or octree (3D).  The slope of a cell along an axis is the van
+// Leer limited slope of the values on each side (the neighbour's, the mean of
+// the 2^(D-1) finer neighbours', or the freestream halo) over the distances
+// between centres along the axis; the upwind cell supplies the face value
+// f + s sigma h / 2; a side with finer neighbours takes the mean of their
+// face values as its inflow, so both cells of an interface see the same
+// flux.  One time step for all leaves (the CFL of the finest cell).
 //
 // The geometry is static: the host lists for every leaf and axis the
 // reciprocal centre distances to both sides, half the edge and its
@@ -392,63 +392,83 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(SweepArgs<T> A) {
 // in shared memory, per leaf and axis, the stencil of the leaf itself and of
 // each upwind neighbour on either side, so that the loop holds no division
 // of the geometry and no lookup of levels.  The velocities of tree cases are
-// stored grouped by quadrant, so the threads of a warp share their upwind
+// stored grouped by orthant, so the threads of a warp share their upwind
 // sides and take the same branches.
 // ---------------------------------------------------------------------------
 
 template <typename T> struct TreeArgs {
   SweepArgs<T> S;
-  const int4 *__restrict__ sti;     // [leaf][10][2]: stencil rows (-1 none, -2 the halo) and the mutual flag
-  const double2 *__restrict__ stg;  // [leaf][10][2]: 1/d-, 1/d+, h, 1/h (own entries)
-  const int4 *__restrict__ lrec;    // [leaf][2]: leaves on sides 0..3, regular flag
-  int qb[3];                      // first stored position of the quadrants 1, 2, 3 (bit 0: x < 0, bit 1: y < 0)
+  const int4 *__restrict__ sti;     // [leaf][entries][ints / 4]: stencil rows (-1 none, -2 the halo, -3 - l a ghost value) and the mutual flag
+  const double2 *__restrict__ stg;  // [leaf][entries][2]: 1/d-, 1/d+, h, 1/h (own entries)
+  const int4 *__restrict__ lrec;    // [leaf][2]: leaves on the sides, regular flag, fluid flag
+  int qb[3];                        // 2D: first stored position of the quadrants 1, 2, 3 (bit 0: x < 0, bit 1: y < 0)
 };
 
 // the stencil of one cell along one axis: the rows [nvp][NC] of the cell and
-// of its neighbours on the - and + sides (the second null for a single
-// neighbour; the freestream's row, second null, at the domain edge), the
-// reciprocal centre distances to both sides and the edge.  `mut` marks an
-// upwind neighbour u of leaf c that is c's only neighbour on that side and
-// has c as its only neighbour on the other: u's value and the value on its
-// side towards c are then c's side value and c's own value.
-template <typename T> struct __align__(16) TreeStencil {
-  const T *c, *m0, *m1, *p0, *p1;
+// of the NF leaves at most on its - and + sides (null beyond the first for a
+// single neighbour; the freestream's row alone at the domain edge; a ghost's
+// link row alone, C29), the reciprocal centre distances to both sides and
+// the edge.  `mut` marks an upwind neighbour u of leaf c that is c's only
+// neighbour on that side and has c as its only neighbour on the other: u's
+// value and the value on its side towards c are then c's side value and
+// c's own value.
+template <typename T, int NF> struct __align__(16) TreeStencil {
+  const T *c, *m[NF], *p[NF];
   T rdm, rdp, h;
   int mut;
 };
 
 // the value on one side of a cell as its slope sees it: the neighbour's, or
-// the mean of the two finer neighbours'
-template <typename T, int NC>
-__device__ __forceinline__ void tree_side_value(const T *r0, const T *r1, int k, T *v) {
-  load_nc<T, NC>(r0 + (size_t)k * NC, v);
-  if (r1) {
-    T w[NC];
-    load_nc<T, NC>(r1 + (size_t)k * NC, w);
+// the mean of the finer neighbours'
+template <typename T, int NC, int NF>
+__device__ __forceinline__ void tree_side_value(const T *const *r, int k, T *v) {
+  load_nc<T, NC>(r[0] + (size_t)k * NC, v);
+  int cnt = 1;
 #pragma unroll
-    for (int m = 0; m < NC; ++m) v[m] = T(0.5) * (v[m] + w[m]);
+  for (int j = 1; j < NF; ++j)
+    if (r[j]) {
+      T w[NC];
+      load_nc<T, NC>(r[j] + (size_t)k * NC, w);
+#pragma unroll
+      for (int m = 0; m < NC; ++m) v[m] += w[m];
+      ++cnt;
+    }
+  if (cnt > 1) {
+    const T rc = T(1) / T(cnt);
+#pragma unroll
+    for (int m = 0; m < NC; ++m) v[m] *= rc;
   }
 }
 
 // the face value on side s of a cell of value fc with side values fm, fp:
 // the limited slope over the centre distances times s h / 2
-template <typename T, int NC>
-__device__ __forceinline__ void tree_face_value(const TreeStencil<T> &S, const T *fc, const T *fm, const T *fp, T s,
+template <typename T, int NC, int NF>
+__device__ __forceinline__ void tree_face_value(const TreeStencil<T, NF> &S, const T *fc, const T *fm, const T *fp, T s,
                                                 T *out) {
   const T sh = s * (T(0.5) * S.h);
 #pragma unroll
   for (int m = 0; m < NC; ++m) out[m] = fc[m] + vanleer((fc[m] - fm[m]) * S.rdm, (fp[m] - fc[m]) * S.rdp) * sh;
 }
 
-// FP32 (h, b) pairs: packed arithmetic, the limiter through the hardware
-// reciprocal (half the van Leer slope times the edge: h ab / (a + b))
+// the face value of the upwind stencil S on side s (its own value and sides loaded)
+template <typename T, int NC, int NF>
+__device__ __forceinline__ void tree_upwind_face(const TreeStencil<T, NF> &S, T s, int k, T *out) {
+  T fu[NC], um[NC], up[NC];
+  load_nc<T, NC>(S.c + (size_t)k * NC, fu);
+  tree_side_value<T, NC, NF>(S.m, k, um);
+  tree_side_value<T, NC, NF>(S.p, k, up);
+  tree_face_value<T, NC, NF>(S, fu, um, up, s, out);
+}
+
+// FP32 (h, b) pairs of quadtrees: packed arithmetic, the limiter through the
+// hardware reciprocal (half the van Leer slope times the edge: h ab / (a + b))
 __device__ __forceinline__ float2 tree_side2(const float *r0, const float *r1, int k) {
   const float2 v = reinterpret_cast<const float2 *>(r0)[k];
   if (!r1) return v;
   const float2 w = reinterpret_cast<const float2 *>(r1)[k];
   return __fmul2_rn(__fadd2_rn(v, w), dev::dup(0.5f));
 }
-__device__ __forceinline__ float2 tree_face2(const TreeStencil<float> &S, float2 fc, float2 fm, float2 fp, float s) {
+__device__ __forceinline__ float2 tree_face2(const TreeStencil<float, 2> &S, float2 fc, float2 fm, float2 fp, float s) {
   const float2 a = __fmul2_rn(dev::sub2(fc, fm), dev::dup(S.rdm));
   const float2 b = __fmul2_rn(dev::sub2(fp, fc), dev::dup(S.rdp));
   return __ffma2_rn(dev::dup(s * S.h), dev::vl_half2(a, b), fc);
@@ -461,62 +481,106 @@ __device__ __forceinline__ float tree_ex2(float x) {
 }
 constexpr float kTreeLog2e = 1.442695040888963407f;
 
-// FP32: four blocks of 256 threads per SM (the loop waits on gathers from L2
-// and HBM: resident warps hide it); FP64, bound by its arithmetic: two
+// FP32 quadtrees: four blocks of 256 threads per SM (the loop waits on
+// gathers from L2 and HBM: resident warps hide it); FP64, bound by its
+// arithmetic, and octrees: two
 template <typename T, int D>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_kernel(TreeArgs<T> TA) {
-  static_assert(D == 2, "tree-refined grids are 2D");
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && D == 2) ? 4 : 2) tree_sweep_kernel(TreeArgs<T> TA) {
   constexpr int NC = Dims<D>::NC;
   constexpr int NM = Dims<D>::NM;
+  constexpr int NF = 1 << (D - 1); // leaves at most beyond a face
+  constexpr int NS = 2 * D;        // sides
+  constexpr int E = tree_entries(D), EI = tree_entry_ints(D);
+  constexpr bool kF32 = std::is_same<T, float>::value && D == 2; // the packed quadtree paths
+  static_assert(E <= kThreadsPerCell, "one thread per stencil entry");
   const SweepArgs<T> &A = TA.S;
   __shared__ double red[kCellsPerBlock][2][NM];
-  // per leaf: its own stencil along x and y, then the upwind neighbours'
-  // along axis a, side sd (0: -, 1: +), neighbour j at 2 + 4a + 2sd + j
-  __shared__ TreeStencil<T> st[kCellsPerBlock][10];
-  __shared__ int nup[kCellsPerBlock][4]; // neighbours on side 2a + sd: 0 (domain edge), 1, 2, 3 (a ghost)
-  __shared__ T rh[kCellsPerBlock][2];    // 1 / h
-  __shared__ int fast[kCellsPerBlock];   // one neighbour of the leaf's own level on every side
-  __shared__ int fluid[kCellsPerBlock];  // the leaf is updated (not a solid leaf of a body, C29)
+  // per leaf: its own stencil along each axis, then the upwind neighbours'
+  // along axis a, side sd (0: -, 1: +), neighbour j at D + (2a + sd) NF + j
+  __shared__ TreeStencil<T, NF> st[kCellsPerBlock][E];
+  __shared__ int nup[kCellsPerBlock][NS]; // leaves on side 2a + sd: 0 (domain edge), 1, NF, 3 (a ghost)
+  __shared__ T rh[kCellsPerBlock][D];     // 1 / h
+  __shared__ int fast[kCellsPerBlock];    // one neighbour of the leaf's own level on every side (2D)
+  __shared__ int fluid[kCellsPerBlock];   // the leaf is updated (not a solid leaf of a body, C29)
   const int tx = threadIdx.x, ty = threadIdx.y;
   const long long c = (long long)blockIdx.x * kCellsPerBlock + ty;
   const int chunk = blockIdx.y;
   const bool active = c < A.ncell;
-  if (active && tx < 10) {
+  if (active && tx < E) {
     // the stencil tables built on the host (one pass, no chain of lookups)
-    const size_t e = ((size_t)c * 10 + tx) * 2;
-    const int4 i0 = TA.sti[e], i1 = TA.sti[e + 1];
-    const double2 g0 = TA.stg[e], g1 = TA.stg[e + 1];
+    const size_t e = (size_t)c * E + tx;
+    int I[EI];
+#pragma unroll
+    for (int q = 0; q < EI / 4; ++q) {
+      const int4 v = TA.sti[e * (EI / 4) + q];
+      I[4 * q] = v.x;
+      I[4 * q + 1] = v.y;
+      I[4 * q + 2] = v.z;
+      I[4 * q + 3] = v.w;
+    }
+    const double2 g0 = TA.stg[2 * e], g1 = TA.stg[2 * e + 1];
     auto row = [&](int i) -> const T * {
       return (i >= 0) ? A.f + (size_t)i * A.nvp * NC
              : (i == -2) ? A.finf
              : (i <= -3) ? A.lval + (size_t)(-3 - i) * A.nvp * NC // a ghost's value for this leaf (C29)
                          : nullptr;
     };
-    TreeStencil<T> S;
-    S.c = row(i0.x);
-    S.m0 = row(i0.y);
-    S.m1 = row(i0.z);
-    S.p0 = row(i0.w);
-    S.p1 = row(i1.x);
-    S.mut = i1.y;
+    TreeStencil<T, NF> S;
+    S.c = row(I[0]);
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+      S.m[j] = row(I[1 + j]);
+      S.p[j] = row(I[1 + NF + j]);
+    }
+    S.mut = I[1 + 2 * NF];
     S.rdm = (T)g0.x;
     S.rdp = (T)g0.y;
     S.h = (T)g1.x;
     st[ty][tx] = S;
-    if (tx < 2) rh[ty][tx] = (T)g1.y;
-  } else if (active && tx == 10) {
+    if (tx < D) rh[ty][tx] = (T)g1.y;
+  } else if (active && tx == E) {
     const int4 r0 = TA.lrec[(size_t)c * 2], r1 = TA.lrec[(size_t)c * 2 + 1];
-    nup[ty][0] = r0.x;
-    nup[ty][1] = r0.y;
-    nup[ty][2] = r0.z;
-    nup[ty][3] = r0.w;
-    fast[ty] = r1.x;
-    fluid[ty] = r1.y;
+    const int r[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+    for (int s = 0; s < NS; ++s) nup[ty][s] = r[s];
+    fast[ty] = r[NS];
+    fluid[ty] = r[NS + 1];
   }
   __syncthreads();
   T acc[NM];
 #pragma unroll
   for (int m = 0; m < NM; ++m) acc[m] = T(0);
+  // the moment sums of one velocity of value fo about the current bulk
+  // velocity (c' = xi - U^n), in the order of the finalize kernel
+  auto moments = [&](const T *cv, T c2, T wk, const T *fo) {
+    const T wh = wk * fo[0];
+    const T e2 = c2 * wh + ((D == 2) ? wk * fo[NC - 1] : T(0));
+    acc[0] += wh;
+    if constexpr (D == 2) {
+      acc[1] += cv[0] * wh;
+      acc[2] += cv[1] * wh;
+      acc[3] += e2;
+      acc[4] += cv[0] * cv[0] * wh;
+      acc[5] += cv[0] * cv[1] * wh;
+      acc[6] += cv[1] * cv[1] * wh;
+      acc[7] += cv[0] * e2;
+      acc[8] += cv[1] * e2;
+    } else {
+      acc[1] += cv[0] * wh;
+      acc[2] += cv[1] * wh;
+      acc[3] += cv[2] * wh;
+      acc[4] += e2;
+      acc[5] += cv[0] * cv[0] * wh;
+      acc[6] += cv[0] * cv[1] * wh;
+      acc[7] += cv[0] * cv[2] * wh;
+      acc[8] += cv[1] * cv[1] * wh;
+      acc[9] += cv[1] * cv[2] * wh;
+      acc[10] += cv[2] * cv[2] * wh;
+      acc[11] += cv[0] * e2;
+      acc[12] += cv[1] * e2;
+      acc[13] += cv[2] * e2;
+    }
+  };
   if (active) {
     const T *M = A.mac;
     T U[3], q[3];
@@ -534,24 +598,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
     if (!fluid[ty]) {
       // a solid leaf (C29): not updated; the moments of its stored values
       for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
-        T fc[NC];
+        T fc[NC], cv[3] = {T(0), T(0), T(0)}, c2 = T(0);
         load_nc<T, NC>(A.f + ((size_t)c * A.nvp + k) * NC, fc);
-        const T cx = A.xi[k] - U[0], cy = A.xi[A.nvp + k] - U[1];
-        const T c2 = cx * cx + cy * cy;
-        const T wk = A.w[k];
-        const T wh = wk * fc[0];
-        const T e2 = c2 * wh + wk * fc[NC - 1];
-        acc[0] += wh;
-        acc[1] += cx * wh;
-        acc[2] += cy * wh;
-        acc[3] += e2;
-        acc[4] += cx * cx * wh;
-        acc[5] += cx * cy * wh;
-        acc[6] += cy * cy * wh;
-        acc[7] += cx * e2;
-        acc[8] += cy * e2;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          cv[a] = A.xi[a * A.nvp + k] - U[a];
+          c2 += cv[a] * cv[a];
+        }
+        moments(cv, c2, A.w[k], fc);
       }
-    } else if constexpr (std::is_same<T, float>::value) {
+    } else if constexpr (kF32) {
       const float nl2 = -invT * kTreeLog2e;
       const float2 *finf2 = reinterpret_cast<const float2 *>(A.finf);
       // relaxation, the store of f^{n+1} and the moment sums of one velocity
@@ -587,13 +643,13 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
         // its four neighbours and the two far neighbours upwind; every load
         // is issued before any arithmetic, the upwind sides taken from the
         // quadrant of the stored position (a zero component moves nothing)
-        const TreeStencil<float> &Sx = st[ty][0], &Sy = st[ty][1];
-        const float2 *xm = reinterpret_cast<const float2 *>(Sx.m0), *xp = reinterpret_cast<const float2 *>(Sx.p0);
-        const float2 *ym = reinterpret_cast<const float2 *>(Sy.m0), *yp = reinterpret_cast<const float2 *>(Sy.p0);
-        const float2 *xf0 = reinterpret_cast<const float2 *>(st[ty][2].m0);
-        const float2 *xf1 = reinterpret_cast<const float2 *>(st[ty][4].p0);
-        const float2 *yf0 = reinterpret_cast<const float2 *>(st[ty][6].m0);
-        const float2 *yf1 = reinterpret_cast<const float2 *>(st[ty][8].p0);
+        const TreeStencil<float, 2> &Sx = st[ty][0], &Sy = st[ty][1];
+        const float2 *xm = reinterpret_cast<const float2 *>(Sx.m[0]), *xp = reinterpret_cast<const float2 *>(Sx.p[0]);
+        const float2 *ym = reinterpret_cast<const float2 *>(Sy.m[0]), *yp = reinterpret_cast<const float2 *>(Sy.p[0]);
+        const float2 *xf0 = reinterpret_cast<const float2 *>(st[ty][2].m[0]);
+        const float2 *xf1 = reinterpret_cast<const float2 *>(st[ty][4].p[0]);
+        const float2 *yf0 = reinterpret_cast<const float2 *>(st[ty][6].m[0]);
+        const float2 *yf1 = reinterpret_cast<const float2 *>(st[ty][8].p[0]);
         const float2 *own2 = reinterpret_cast<const float2 *>(own);
         for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
           const int o = (k >= TA.qb[0]) + (k >= TA.qb[1]) + (k >= TA.qb[2]); // bit 0: x < 0, bit 1: y < 0
@@ -624,8 +680,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
           if (xa == 0.f) continue;
           const float s = (xa > 0.f) ? 1.f : -1.f; // the downwind side
           const int sd = (xa > 0.f) ? 0 : 1;       // the upwind side
-          const TreeStencil<float> &So = st[ty][a];
-          const float2 fm = tree_side2(So.m0, So.m1, k), fp = tree_side2(So.p0, So.p1, k);
+          const TreeStencil<float, 2> &So = st[ty][a];
+          const float2 fm = tree_side2(So.m[0], So.m[1], k), fp = tree_side2(So.p[0], So.p[1], k);
           const float2 fout = tree_face2(So, f2, fm, fp, s);
           const int n = nup[ty][2 * a + sd];
           float2 fin;
@@ -636,18 +692,18 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
             const float2 g = reinterpret_cast<const float2 *>(st[ty][2 + 4 * a + 2 * sd].c)[k];
             fin = __fmul2_rn(__fadd2_rn(g, f2), dev::dup(0.5f));
           } else {
-            const TreeStencil<float> &S0 = st[ty][2 + 4 * a + 2 * sd];
+            const TreeStencil<float, 2> &S0 = st[ty][2 + 4 * a + 2 * sd];
             if (S0.mut) {
               const float2 fu = sd ? fp : fm;
-              const float2 far = sd ? tree_side2(S0.p0, S0.p1, k) : tree_side2(S0.m0, S0.m1, k);
+              const float2 far = sd ? tree_side2(S0.p[0], S0.p[1], k) : tree_side2(S0.m[0], S0.m[1], k);
               fin = tree_face2(S0, fu, sd ? f2 : far, sd ? far : f2, s);
             } else {
-              fin = tree_face2(S0, reinterpret_cast<const float2 *>(S0.c)[k], tree_side2(S0.m0, S0.m1, k),
-                               tree_side2(S0.p0, S0.p1, k), s);
+              fin = tree_face2(S0, reinterpret_cast<const float2 *>(S0.c)[k], tree_side2(S0.m[0], S0.m[1], k),
+                               tree_side2(S0.p[0], S0.p[1], k), s);
               if (n == 2) {
-                const TreeStencil<float> &S1 = st[ty][3 + 4 * a + 2 * sd];
+                const TreeStencil<float, 2> &S1 = st[ty][3 + 4 * a + 2 * sd];
                 const float2 g1 = tree_face2(S1, reinterpret_cast<const float2 *>(S1.c)[k],
-                                             tree_side2(S1.m0, S1.m1, k), tree_side2(S1.p0, S1.p1, k), s);
+                                             tree_side2(S1.m[0], S1.m[1], k), tree_side2(S1.p[0], S1.p[1], k), s);
                 fin = __fmul2_rn(__fadd2_rn(fin, g1), dev::dup(0.5f));
               }
             }
@@ -673,66 +729,58 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) tree_sweep_ker
           if (xa == T(0)) continue;
           const T s = (xa > T(0)) ? T(1) : T(-1);
           const int sd = (xa > T(0)) ? 0 : 1;
-          const TreeStencil<T> &So = st[ty][a];
+          const TreeStencil<T, NF> &So = st[ty][a];
           T fm[NC], fp[NC], fout[NC], fin[NC];
-          tree_side_value<T, NC>(So.m0, So.m1, k, fm);
-          tree_side_value<T, NC>(So.p0, So.p1, k, fp);
-          tree_face_value<T, NC>(So, fc, fm, fp, s, fout);
+          tree_side_value<T, NC, NF>(So.m, k, fm);
+          tree_side_value<T, NC, NF>(So.p, k, fp);
+          tree_face_value<T, NC, NF>(So, fc, fm, fp, s, fout);
           const int n = nup[ty][2 * a + sd];
+          const TreeStencil<T, NF> *Su = &st[ty][D + (2 * a + sd) * NF];
           if (n == 0) {
-            load_nc<T, NC>(A.finf + (size_t)k * NC, fin);
+            load_nc<T, NC>(A.finf + (size_t)k * NC, fin); // the halo: its value, zero slope
           } else if (n == 3) {
-            load_nc<T, NC>(st[ty][2 + 4 * a + 2 * sd].c + (size_t)k * NC, fin);
+            // a ghost upwind (C29): its link value with the one-sided slope
+            load_nc<T, NC>(Su[0].c + (size_t)k * NC, fin);
 #pragma unroll
             for (int m = 0; m < NC; ++m) fin[m] = T(0.5) * (fin[m] + fc[m]);
           } else {
-            const TreeStencil<T> &S0 = st[ty][2 + 4 * a + 2 * sd];
-            T fu[NC], um[NC], up[NC];
-            load_nc<T, NC>(S0.c + (size_t)k * NC, fu);
-            tree_side_value<T, NC>(S0.m0, S0.m1, k, um);
-            tree_side_value<T, NC>(S0.p0, S0.p1, k, up);
-            tree_face_value<T, NC>(S0, fu, um, up, s, fin);
-            if (n == 2) {
-              const TreeStencil<T> &S1 = st[ty][3 + 4 * a + 2 * sd];
-              T g1[NC];
-              load_nc<T, NC>(S1.c + (size_t)k * NC, fu);
-              tree_side_value<T, NC>(S1.m0, S1.m1, k, um);
-              tree_side_value<T, NC>(S1.p0, S1.p1, k, up);
-              tree_face_value<T, NC>(S1, fu, um, up, s, g1);
+            // the upwind leaves' face values, each over its share of the side
+            tree_upwind_face<T, NC, NF>(Su[0], s, k, fin);
+            if (n > 1) {
+              for (int j = 1; j < n; ++j) {
+                T g[NC];
+                tree_upwind_face<T, NC, NF>(Su[j], s, k, g);
 #pragma unroll
-              for (int m = 0; m < NC; ++m) fin[m] = T(0.5) * (fin[m] + g1[m]);
+                for (int m = 0; m < NC; ++m) fin[m] += g[m];
+              }
+              const T rn = T(1) / T(n);
+#pragma unroll
+              for (int m = 0; m < NC; ++m) fin[m] *= rn;
             }
           }
           const T wa = fabs(xa) * rh[ty][a];
 #pragma unroll
           for (int m = 0; m < NC; ++m) div[m] += wa * (fout[m] - fin[m]);
         }
-        // Shakhov equilibrium (Sec. 4 reduced forms)
+        // Shakhov equilibrium (Sec. 4 reduced forms in 2D, g^S in 3D)
         T cq = T(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) cq += cv[a] * q[a];
         const T e = pre * exp_t(-c2 * invT);
         const T corr = shA * cq;
         const T tc = T(2) * c2 * invT;
-        const T H = e * (T(1) + corr * (tc - T(4)));
-        const T B = halfT * e * (T(1) + corr * (tc - T(2)));
         T fo[NC];
-        fo[0] = fc[0] - A.dt * div[0] + dtau * (H - fc[0]);
-        fo[NC - 1] = fc[NC - 1] - A.dt * div[NC - 1] + dtau * (B - fc[NC - 1]);
+        if constexpr (D == 2) {
+          const T H = e * (T(1) + corr * (tc - T(4)));
+          const T B = halfT * e * (T(1) + corr * (tc - T(2)));
+          fo[0] = fc[0] - A.dt * div[0] + dtau * (H - fc[0]);
+          fo[NC - 1] = fc[NC - 1] - A.dt * div[NC - 1] + dtau * (B - fc[NC - 1]);
+        } else {
+          const T g = e * (T(1) + corr * (tc - T(5)));
+          fo[0] = fc[0] - A.dt * div[0] + dtau * (g - fc[0]);
+        }
         store_nc<T, NC>(A.fn + ((size_t)c * A.nvp + k) * NC, fo);
-        // moments about the current bulk velocity: c' = xi - U^n
-        const T wk = A.w[k];
-        const T wh = wk * fo[0];
-        const T e2 = c2 * wh + wk * fo[NC - 1];
-        acc[0] += wh;
-        acc[1] += cv[0] * wh;
-        acc[2] += cv[1] * wh;
-        acc[3] += e2;
-        acc[4] += cv[0] * cv[0] * wh;
-        acc[5] += cv[0] * cv[1] * wh;
-        acc[6] += cv[1] * cv[1] * wh;
-        acc[7] += cv[0] * e2;
-        acc[8] += cv[1] * e2;
+        moments(cv, c2, A.w[k], fo);
       }
     }
   }
@@ -1856,9 +1904,7 @@ template <typename T, int D> cudaError_t sweep_t(ibdvm_ctx *ctx, int update, int
 }
 
 template <typename T, int D> cudaError_t tree_sweep_t(ibdvm_ctx *ctx) {
-  if constexpr (D != 2) {
-    return cudaErrorNotSupported;
-  } else {
+  {
     TreeArgs<T> A{};
     A.S = sweep_args<T>(ctx, 1, 1);
     A.sti = reinterpret_cast<const int4 *>(ctx->tree_sti);

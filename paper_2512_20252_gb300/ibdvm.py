@@ -45,7 +45,8 @@ class GridDesc(ctypes.Structure):
 
 class TreeDesc(ctypes.Structure):
     _fields_ = [("nleaf", ctypes.c_int), ("maxlevel", ctypes.c_int), ("level", ctypes.POINTER(ctypes.c_int)),
-                ("ix", ctypes.POINTER(ctypes.c_int)), ("iy", ctypes.POINTER(ctypes.c_int))]
+                ("ix", ctypes.POINTER(ctypes.c_int)), ("iy", ctypes.POINTER(ctypes.c_int)),
+                ("iz", ctypes.POINTER(ctypes.c_int))]
 
 
 class VGridDesc(ctypes.Structure):
@@ -404,12 +405,15 @@ class Solver:
         tree = case.get("tree")
         if tree:
             # a tree-refined 2D grid over the root grid case["n"] (ibdvm_create_tree)
-            arrs = [np.ascontiguousarray(np.asarray(tree[k], dtype=np.int32)) for k in ("level", "ix", "iy")]
+            keys = ("level", "ix", "iy", "iz") if int(case["dim"]) == 3 else ("level", "ix", "iy")
+            arrs = [np.ascontiguousarray(np.asarray(tree[k], dtype=np.int32)) for k in keys]
             keep = list(keep) + arrs
             t = TreeDesc()
             t.nleaf = arrs[0].size
             t.maxlevel = int(tree["maxlevel"])
-            t.level, t.ix, t.iy = (a.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) for a in arrs)
+            ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) for a in arrs]
+            t.level, t.ix, t.iy = ptrs[:3]
+            t.iz = ptrs[3] if len(ptrs) > 3 else None
             st = self.lib.ibdvm_create_tree(ctypes.byref(g), ctypes.byref(t), ctypes.byref(v), ctypes.byref(s),
                                             _V(stream or 0), ctypes.byref(h))
         else:
@@ -427,8 +431,9 @@ class Solver:
         self.refresh_info()
 
     def tree_neighbours(self) -> np.ndarray:
-        """Face neighbours [leaf][side 2a + (s > 0)][2] of a tree context (-1: none)."""
-        nb = np.zeros((self.ncell, 4, 2), dtype=np.int64)
+        """Face neighbours [leaf][side 2a + (s > 0)][2^(dim-1)] of a tree context (-1: none)."""
+        D = int(self.case["dim"])
+        nb = np.zeros((self.ncell, 2 * D, 1 << (D - 1)), dtype=np.int64)
         self._check(self.lib.ibdvm_tree_neighbours(self.h, nb.ctypes.data_as(_LL)))
         return nb
 

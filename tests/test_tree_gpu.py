@@ -217,3 +217,116 @@ def test_tree_wall_quantities_against_the_oracle(precision):
         err = np.abs(wg[:, i] - wo[:, i]).max() / max(np.abs(wo[:, i]).max(), 1e-3)
         assert err < tol, (c, err)
     g.close()
+
+
+@pytest.mark.parametrize("workload,steps", [("tree_2d", 5), ("cylinder_hypersonic_tree", 5)])
+def test_tree_full_size_mixed_against_fp64(workload, steps):
+    """The tree workloads at their full size and launch shape: the mixed path
+    (gather-first leaves, FP32 ghost values) against the FP64 path (which
+    matches the oracle to 1e-11 on the smaller trees) after a few steps from
+    the bench's start: W within 1e-5 of its largest magnitude per component
+    (at least 1% of the largest density: a momentum component near zero by
+    symmetry carries FP32 rounding of order 1e-8), C_D within 1e-4."""
+    out = {}
+    for prec in ("fp64", "mixed"):
+        case = getattr(wl, workload)(precision=prec)
+        g = ibdvm.Solver(case)
+        if case["body"]["kind"] == "none":
+            xc = wl.tree_centres(case)
+            f = g.get_f()
+            f *= (1.0 + 0.2 * np.exp(-(xc[:, 0] ** 2 + xc[:, 1] ** 2) / 2.0))[:, None, None]
+            g.set_f(f)
+            del f
+        g.step(steps)
+        W, q, t = g.moments()
+        _, _, CD, _ = g.forces()
+        out[prec] = (W, t, CD)
+        g.close()
+    (Wd, t, CDd), (Wm, _, CDm) = out["fp64"], out["mixed"]
+    fl = t == ibdvm.FLUID
+    for i in range(Wd.shape[1]):
+        scale = max(np.abs(Wd[fl, i]).max(), 1e-2 * np.abs(Wd[fl, 0]).max())
+        assert np.abs(Wm[fl, i] - Wd[fl, i]).max() < 1e-5 * scale, i
+    assert abs(CDm - CDd) <= 1e-4 * abs(CDd)
+
+
+# ---------------------------------------------------------------------------
+# octrees (3D)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("body", [False, True])
+def test_octree_fp64_against_the_oracle(body):
+    """An octree with four finer leaves across some faces, with and without a
+    sphere in its finest level (C29): FP64 within 1e-11 of the oracle on f,
+    W, the surface force and the residual after four steps from a perturbed
+    state; the neighbour tables equal."""
+    case = wl.tree_case_3d(8, 2, nv=6, Ma=0.5, radii=[1.6, 1.2] if body else None,
+                           body=wl.sphere(0.4) if body else None)
+    o = oracle.OracleTree(case)
+    g = ibdvm.Solver(case)
+    assert g.ncell == o.nleaf and g.info.nfluid == o.nfluid
+    np.testing.assert_array_equal(g.tree_neighbours(), o.neighbours())
+    f0 = _perturbed(o, 13, amp=0.1)
+    o.set_f(f0)
+    g.set_f(f0)
+    ro = o.step(4)
+    rg = g.step(4)
+    assert rel_err(g.get_f(), o.get_f()) < 1e-11
+    Wg, _, t = g.moments()
+    Wo, _ = o.moments()
+    np.testing.assert_array_equal(t, o.cell_types())
+    fl = t == ibdvm.FLUID
+    for i in range(5):
+        if np.abs(Wo[fl, i]).max() > 1e-9:
+            assert rel_err(Wg[fl, i], Wo[fl, i]) < 1e-11, i
+    assert rg == pytest.approx(ro, rel=1e-9)
+    if body:
+        Fg, Qg, CDg, _ = g.forces()
+        Fo, Qo, CDo, _ = o.forces()
+        assert np.abs(Fg - Fo).max() < 1e-10 * np.abs(Fo).max()
+        assert CDg == pytest.approx(CDo, rel=1e-10)
+    g.close()
+
+
+def test_octree_mixed_against_the_oracle():
+    case = wl.tree_case_3d(8, 2, nv=8, Ma=0.5, radii=[1.6, 1.2], body=wl.sphere(0.4), precision="mixed")
+    o = oracle.OracleTree(case)
+    g = ibdvm.Solver(case)
+    f0 = _perturbed(o, 17, amp=0.1)
+    o.set_f(f0)
+    g.set_f(f0)
+    o.step(6)
+    g.step(6)
+    assert rel_err(g.get_f(), o.get_f()) < 1e-5
+    Wg, _, t = g.moments()
+    Wo, _ = o.moments()
+    fl = t == ibdvm.FLUID
+    for i in range(5):
+        if np.abs(Wo[fl, i]).max() > 1e-9:
+            assert rel_err(Wg[fl, i], Wo[fl, i]) < 1e-5, i
+    _, _, CDg, _ = g.forces()
+    _, _, CDo, _ = o.forces()
+    assert CDg == pytest.approx(CDo, rel=1e-4)
+    g.close()
+
+
+def test_one_level_octree_matches_the_uniform_gpu_path():
+    n = 12
+    case = wl._case(3, n, 2.0, 6, 4.5, 0.1, 0.4, wl.sphere(0.7))
+    u = ibdvm.Solver(case)
+    ix, iy, iz = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    tree = {"maxlevel": 1, "level": [1] * n ** 3, "ix": ix.T.ravel().tolist(), "iy": iy.T.ravel().tolist(),
+            "iz": iz.T.ravel().tolist()}
+    t = ibdvm.Solver(dict(case, n=[n // 2] * 3, tree=tree))
+    rng = np.random.default_rng(8)
+    f0 = u.get_f() * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, size=u.get_f().shape))
+    u.set_f(f0)
+    t.set_f(f0)
+    u.step(4)
+    t.step(4)
+    assert rel_err(t.get_f(), u.get_f()) < 1e-12
+    _, _, CDu, _ = u.forces()
+    _, _, CDt, _ = t.forces()
+    assert CDt == pytest.approx(CDu, rel=1e-10)
+    u.close()
+    t.close()
