@@ -58,6 +58,7 @@ WORKLOADS = {
                                                      fromlist=["x"]).cylinder_hypersonic_tree(precision=p),
     "naca_supersonic_tree": lambda p: __import__("paper_2512_20252_gb300.workloads",
                                                  fromlist=["x"]).naca_supersonic_tree(precision=p),
+    "sphere_96_tree": lambda p: __import__("paper_2512_20252_gb300.workloads", fromlist=["x"]).sphere_96_tree(precision=p),
     "batched_2d": None,  # a list of cases: see bench_batch
     "served": None,      # a request stream: see bench_serve
 }
@@ -87,6 +88,9 @@ DESCRIPTIONS = {
                             "root on [-3,7]x[-7,7] refined about the chord to level 1 within 1.5, 2 within 0.6, 3 "
                             "within 0.25, 4 within 0.1 (finest edge 1/128), 2:1 balanced, 17,528 leaves in Z "
                             "order, 60x60 trapezoid velocities on [-4,8]x[-6,6], T_w=1",
+    "sphere_96_tree": "3D sphere r=0.5 at Ma 0.5, Kn 0.1 on an octree: a 32^3 root on [-4,4]^3 refined about the "
+                      "centre to level 1 within 2.4 and 2 within 1.5 (finest edge 1/16), 2:1 balanced, 108,760 leaves "
+                      "in Z order, 20^3 trapezoid velocities on [-5,5]^3",
     "batched_2d": "64 seeded 2D cases (seed 0): n ~ U{64..384} cells per axis on [-4,4]^2, m ~ U{16..40} "
                   "velocities per axis on [-6,6]^2, circle / ellipse (aspect U[1,3]) / NACA0012 (AoA U[0,10] deg), "
                   "Kn 10^U[-2,0], Ma U[0.1,0.8], mixed precision, one batch",
@@ -299,9 +303,13 @@ def cpu_sample_case(case: dict) -> dict:
         spec = case["tree_spec"]
         smp = spec["sample"]
         c["n"] = list(smp["root"])
-        c["tree"] = workloads.tree_leaves(tuple(smp["root"]), smp["maxlevel"], case["lo"], case["hi"], spec["center"],
-                                          smp["radii"], metric=spec.get("metric", "point"),
-                                          segment=spec.get("segment"))
+        if case["dim"] == 3:
+            c["tree"] = workloads.tree_leaves_3d(tuple(smp["root"]), smp["maxlevel"], case["lo"], case["hi"],
+                                                 spec["center"], smp["radii"])
+        else:
+            c["tree"] = workloads.tree_leaves(tuple(smp["root"]), smp["maxlevel"], case["lo"], case["hi"],
+                                              spec["center"], smp["radii"], metric=spec.get("metric", "point"),
+                                              segment=spec.get("segment"))
         return c
     c["n"] = [48] * 2 if case["dim"] == 2 else [12] * 3
     return c

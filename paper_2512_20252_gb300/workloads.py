@@ -170,6 +170,18 @@ def sphere_96(precision="mixed", steps=200):
     return _case(3, 96, 4.0, 20, 5.0, 0.1, 0.5, sphere(0.5), precision=precision, steps=steps)
 
 
+def sphere_96_tree(precision="mixed", steps=200, root=32, maxlevel=2, radii=(2.4, 1.5)):
+    """The flow of sphere_96 (r = 0.5, Ma 0.5, Kn 0.1, 20^3 velocities on
+    [-5,5]^3, [-4,4]^3) on an octree: a root of root^3 cells refined about the
+    centre to level l within radii[l] (the finest edge 1/16 at the wall, the
+    96^3 grid's is 1/12), 2:1 balanced, leaves in Z order."""
+    d = _case(3, root, 4.0, 20, 5.0, 0.1, 0.5, sphere(0.5), precision=precision, steps=steps)
+    d["tree"] = tree_leaves_3d((root,) * 3, maxlevel, d["lo"], d["hi"], (0.0, 0.0, 0.0), list(radii))
+    d["tree_spec"] = {"center": [0.0, 0.0, 0.0], "radii": list(radii),
+                      "sample": {"root": [8, 8, 8], "maxlevel": 2, "radii": list(radii)}}
+    return d
+
+
 def sphere_supersonic(n=64, nv=24, precision="mixed", steps=200):
     """The supersonic sphere of Sec. 4.4 on a uniform grid: Ma 3.834, Kn 0.03,
     T_w = 1 + (gamma - 1) Ma^2 / 2, n^3 cells on [-4,4]^3, r = 0.5, nv^3
