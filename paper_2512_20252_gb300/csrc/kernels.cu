@@ -440,6 +440,14 @@ __device__ __forceinline__ void tree_side_value(const T *const *r, int k, T *v) 
   }
 }
 
+// the van Leer limiter of the tree sweep: FP64 divides; FP32 takes the
+// hardware reciprocal (as the packed quadtree path does)
+__device__ __forceinline__ double tree_vanleer(double a, double b) { return vanleer(a, b); }
+__device__ __forceinline__ float tree_vanleer(float a, float b) {
+  const float p = a * b;
+  return (p > 0.f) ? 2.f * p * dev::rcp_approx(a + b) : 0.f;
+}
+
 // the face value on side s of a cell of value fc with side values fm, fp:
 // the limited slope over the centre distances times s h / 2
 template <typename T, int NC, int NF>
@@ -447,7 +455,7 @@ __device__ __forceinline__ void tree_face_value(const TreeStencil<T, NF> &S, con
                                                 T *out) {
   const T sh = s * (T(0.5) * S.h);
 #pragma unroll
-  for (int m = 0; m < NC; ++m) out[m] = fc[m] + vanleer((fc[m] - fm[m]) * S.rdm, (fp[m] - fc[m]) * S.rdp) * sh;
+  for (int m = 0; m < NC; ++m) out[m] = fc[m] + tree_vanleer((fc[m] - fm[m]) * S.rdm, (fp[m] - fc[m]) * S.rdp) * sh;
 }
 
 // the face value of the upwind stencil S on side s (its own value and sides loaded)
@@ -595,6 +603,83 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && D == 2) ? 4 : 2) tr
     // the stored velocities of a tree case come first, padding after
     const int kbeg = chunk * A.kloop * kThreadsPerCell;
     const int kend = min(A.nv, kbeg + A.kloop * kThreadsPerCell);
+    // the general path: any leaf (levels apart, finer or ghost neighbours, the domain edge)
+    auto general = [&]() {
+        for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
+          T fc[NC], div[NC];
+          T cv[3] = {T(0), T(0), T(0)};
+          T c2 = T(0);
+          load_nc<T, NC>(own + (size_t)k * NC, fc);
+#pragma unroll
+          for (int m = 0; m < NC; ++m) div[m] = T(0);
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            const T xa = A.xi[a * A.nvp + k];
+            cv[a] = xa - U[a];
+            c2 += cv[a] * cv[a];
+            if (xa == T(0)) continue;
+            const T s = (xa > T(0)) ? T(1) : T(-1);
+            const int sd = (xa > T(0)) ? 0 : 1;
+            const TreeStencil<T, NF> &So = st[ty][a];
+            T fm[NC], fp[NC], fout[NC], fin[NC];
+            tree_side_value<T, NC, NF>(So.m, k, fm);
+            tree_side_value<T, NC, NF>(So.p, k, fp);
+            tree_face_value<T, NC, NF>(So, fc, fm, fp, s, fout);
+            const int n = nup[ty][2 * a + sd];
+            const TreeStencil<T, NF> *Su = &st[ty][D + (2 * a + sd) * NF];
+            if (n == 0) {
+              load_nc<T, NC>(A.finf + (size_t)k * NC, fin); // the halo: its value, zero slope
+            } else if (n == 3) {
+              // a ghost upwind (C29): its link value with the one-sided slope
+              load_nc<T, NC>(Su[0].c + (size_t)k * NC, fin);
+#pragma unroll
+              for (int m = 0; m < NC; ++m) fin[m] = T(0.5) * (fin[m] + fc[m]);
+            } else if (n == 1 && Su[0].mut) {
+              // one upwind leaf of c's level: its value and its side towards c
+              // are c's side value and c's own value
+              T far[NC];
+              tree_side_value<T, NC, NF>(sd ? Su[0].p : Su[0].m, k, far);
+              tree_face_value<T, NC, NF>(Su[0], sd ? fp : fm, sd ? fc : far, sd ? far : fc, s, fin);
+            } else {
+              // the upwind leaves' face values, each over its share of the side
+              tree_upwind_face<T, NC, NF>(Su[0], s, k, fin);
+              if (n > 1) {
+                for (int j = 1; j < n; ++j) {
+                  T g[NC];
+                  tree_upwind_face<T, NC, NF>(Su[j], s, k, g);
+#pragma unroll
+                  for (int m = 0; m < NC; ++m) fin[m] += g[m];
+                }
+                const T rn = T(1) / T(n);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) fin[m] *= rn;
+              }
+            }
+            const T wa = fabs(xa) * rh[ty][a];
+#pragma unroll
+            for (int m = 0; m < NC; ++m) div[m] += wa * (fout[m] - fin[m]);
+          }
+          // Shakhov equilibrium (Sec. 4 reduced forms in 2D, g^S in 3D)
+          T cq = T(0);
+#pragma unroll
+          for (int a = 0; a < D; ++a) cq += cv[a] * q[a];
+          const T e = pre * exp_t(-c2 * invT);
+          const T corr = shA * cq;
+          const T tc = T(2) * c2 * invT;
+          T fo[NC];
+          if constexpr (D == 2) {
+            const T H = e * (T(1) + corr * (tc - T(4)));
+            const T B = halfT * e * (T(1) + corr * (tc - T(2)));
+            fo[0] = fc[0] - A.dt * div[0] + dtau * (H - fc[0]);
+            fo[NC - 1] = fc[NC - 1] - A.dt * div[NC - 1] + dtau * (B - fc[NC - 1]);
+          } else {
+            const T g = e * (T(1) + corr * (tc - T(5)));
+            fo[0] = fc[0] - A.dt * div[0] + dtau * (g - fc[0]);
+          }
+          store_nc<T, NC>(A.fn + ((size_t)c * A.nvp + k) * NC, fo);
+          moments(cv, c2, A.w[k], fo);
+        }
+    };
     if (!fluid[ty]) {
       // a solid leaf (C29): not updated; the moments of its stored values
       for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
@@ -713,75 +798,61 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && D == 2) ? 4 : 2) tr
         finish(k, f2, dv, cv, c2, A.w[k]);
       }
       }
-    } else {
-      for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
-        T fc[NC], div[NC];
-        T cv[3] = {T(0), T(0), T(0)};
-        T c2 = T(0);
-        load_nc<T, NC>(own + (size_t)k * NC, fc);
+    } else if constexpr (D == 3 && std::is_same<T, float>::value) {
+      if (fast[ty]) {
+        // an octree leaf with one fluid neighbour of its own level on every
+        // side: one velocity reads the leaf, its six neighbours and the three
+        // far neighbours upwind (the mutual shortcut), every load before any
+        // arithmetic
+        const T *nm[3], *np[3], *fm0[3], *fp1[3];
 #pragma unroll
-        for (int m = 0; m < NC; ++m) div[m] = T(0);
+        for (int a = 0; a < 3; ++a) {
+          nm[a] = st[ty][a].m[0];
+          np[a] = st[ty][a].p[0];
+          fm0[a] = st[ty][D + (2 * a) * NF].m[0];     // beyond the - neighbour
+          fp1[a] = st[ty][D + (2 * a + 1) * NF].p[0]; // beyond the + neighbour
+        }
+        for (int k = kbeg + tx; k < kend; k += kThreadsPerCell) {
+          T xa[3], vm[3], vp[3], vf[3];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          const T xa = A.xi[a * A.nvp + k];
-          cv[a] = xa - U[a];
-          c2 += cv[a] * cv[a];
-          if (xa == T(0)) continue;
-          const T s = (xa > T(0)) ? T(1) : T(-1);
-          const int sd = (xa > T(0)) ? 0 : 1;
-          const TreeStencil<T, NF> &So = st[ty][a];
-          T fm[NC], fp[NC], fout[NC], fin[NC];
-          tree_side_value<T, NC, NF>(So.m, k, fm);
-          tree_side_value<T, NC, NF>(So.p, k, fp);
-          tree_face_value<T, NC, NF>(So, fc, fm, fp, s, fout);
-          const int n = nup[ty][2 * a + sd];
-          const TreeStencil<T, NF> *Su = &st[ty][D + (2 * a + sd) * NF];
-          if (n == 0) {
-            load_nc<T, NC>(A.finf + (size_t)k * NC, fin); // the halo: its value, zero slope
-          } else if (n == 3) {
-            // a ghost upwind (C29): its link value with the one-sided slope
-            load_nc<T, NC>(Su[0].c + (size_t)k * NC, fin);
+          for (int a = 0; a < 3; ++a) xa[a] = A.xi[a * A.nvp + k];
+          const T fc = own[k];
 #pragma unroll
-            for (int m = 0; m < NC; ++m) fin[m] = T(0.5) * (fin[m] + fc[m]);
-          } else {
-            // the upwind leaves' face values, each over its share of the side
-            tree_upwind_face<T, NC, NF>(Su[0], s, k, fin);
-            if (n > 1) {
-              for (int j = 1; j < n; ++j) {
-                T g[NC];
-                tree_upwind_face<T, NC, NF>(Su[j], s, k, g);
-#pragma unroll
-                for (int m = 0; m < NC; ++m) fin[m] += g[m];
-              }
-              const T rn = T(1) / T(n);
-#pragma unroll
-              for (int m = 0; m < NC; ++m) fin[m] *= rn;
-            }
+          for (int a = 0; a < 3; ++a) {
+            vm[a] = nm[a][k];
+            vp[a] = np[a][k];
+            vf[a] = (xa[a] > T(0)) ? fm0[a][k] : fp1[a][k];
           }
-          const T wa = fabs(xa) * rh[ty][a];
+          T cv[3], c2 = T(0), div = T(0);
 #pragma unroll
-          for (int m = 0; m < NC; ++m) div[m] += wa * (fout[m] - fin[m]);
-        }
-        // Shakhov equilibrium (Sec. 4 reduced forms in 2D, g^S in 3D)
-        T cq = T(0);
+          for (int a = 0; a < 3; ++a) {
+            cv[a] = xa[a] - U[a];
+            c2 += cv[a] * cv[a];
+            const bool pos = xa[a] > T(0);
+            const T s = pos ? T(1) : T(-1);
+            const TreeStencil<T, NF> &So = st[ty][a];
+            const TreeStencil<T, NF> &Su = st[ty][D + (2 * a + (pos ? 0 : 1)) * NF];
+            const T fout = fc + tree_vanleer((fc - vm[a]) * So.rdm, (vp[a] - fc) * So.rdp) * (s * (T(0.5) * So.h));
+            const T fu = pos ? vm[a] : vp[a];
+            const T um = pos ? vf[a] : fc, up = pos ? fc : vf[a];
+            const T fin = fu + tree_vanleer((fu - um) * Su.rdm, (up - fu) * Su.rdp) * (s * (T(0.5) * Su.h));
+            div += fabs(xa[a]) * rh[ty][a] * (fout - fin); // zero for a zero component
+          }
+          T cq = T(0);
 #pragma unroll
-        for (int a = 0; a < D; ++a) cq += cv[a] * q[a];
-        const T e = pre * exp_t(-c2 * invT);
-        const T corr = shA * cq;
-        const T tc = T(2) * c2 * invT;
-        T fo[NC];
-        if constexpr (D == 2) {
-          const T H = e * (T(1) + corr * (tc - T(4)));
-          const T B = halfT * e * (T(1) + corr * (tc - T(2)));
-          fo[0] = fc[0] - A.dt * div[0] + dtau * (H - fc[0]);
-          fo[NC - 1] = fc[NC - 1] - A.dt * div[NC - 1] + dtau * (B - fc[NC - 1]);
-        } else {
-          const T g = e * (T(1) + corr * (tc - T(5)));
-          fo[0] = fc[0] - A.dt * div[0] + dtau * (g - fc[0]);
+          for (int a = 0; a < 3; ++a) cq += cv[a] * q[a];
+          const T e = pre * exp_t(-c2 * invT);
+          const T g = e * (T(1) + shA * cq * (T(2) * c2 * invT - T(5)));
+          T fo[NC];
+          fo[0] = fc - A.dt * div + dtau * (g - fc);
+          A.fn[(size_t)c * A.nvp + k] = fo[0];
+          moments(cv, c2, A.w[k], fo);
         }
-        store_nc<T, NC>(A.fn + ((size_t)c * A.nvp + k) * NC, fo);
-        moments(cv, c2, A.w[k], fo);
+      } else {
+        general();
       }
+    } else {
+      general();
     }
   }
   // reduce the moment sums of each leaf over its 64 threads (two warps)

@@ -137,8 +137,8 @@ bool build_tree_mesh(const ibdvm_grid_desc &root, const ibdvm_tree_desc &t, std:
 // the - and + sides (the neighbour's centre, or h to the halo), h, and 1 / h
 // for t < D.  Eight ints per leaf: the number of leaves on each side 2a + sd
 // (0 at the domain edge, 1, NF, or 3 for a ghost), then the regular flag
-// (2D: one fluid leaf of c's level on every side, each with one leaf or the
-// domain edge beyond it; 0 in 3D) and the fluid flag.
+// (one fluid leaf of c's level on every side, each with one leaf or the
+// domain edge beyond it) and the fluid flag.
 void build_tree_stencils(int D, const std::vector<int> &lev, const std::vector<int> &nb, const double h0[3],
                          const std::vector<uint8_t> &type, const std::vector<int> &glink,
                          std::vector<int> &sti, std::vector<double> &stg, std::vector<int> &lrec) {
@@ -197,7 +197,7 @@ void build_tree_stencils(int D, const std::vector<int> &lev, const std::vector<i
       Dd[2] = h;
       Dd[3] = (t < D) ? 1.0 / h : 0.0;
     }
-    bool regular = D == 2;
+    bool regular = true;
     for (int s = 0; s < NS; ++s) {
       const int n0 = side(c, s, 0), n1 = side(c, s, 1);
       lrec[c * 8 + s] = (n0 < 0) ? 0 : (!fluid(n0) ? 3 : (n1 < 0 ? 1 : NF));
