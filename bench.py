@@ -127,7 +127,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--cells", type=int, default=0,
-                    help="override the cells per axis (smaller cases for profiling captures)")
+                    help="override the cells per axis, for tree workloads the root cells per axis (smaller cases for profiling captures)")
     ap.add_argument("--ncases", type=int, default=64, help="batched_2d: number of cases")
     ap.add_argument("--tune-steps", type=int, default=4,
                     help="batched_2d: steps per autotuner trial (0 = no tuning)")
@@ -713,6 +713,11 @@ def measure_case(args, workload, world, rank, local, pg, with_cpu=True):
     case = _workload_case(args, workload, args.precision)
     if args.cells and not case.get("tree"):
         case["n"] = [args.cells] * case["dim"]
+    elif args.cells:
+        # a tree workload with a smaller root grid (profiling captures)
+        from paper_2512_20252_gb300 import workloads
+
+        case = getattr(workloads, workload)(precision=args.precision, root=args.cells)
     stream = torch.cuda.Stream()
     solver = ibdvm.Solver(case, stream=stream.cuda_stream)
     if case.get("tree") and case["body"]["kind"] == "none":

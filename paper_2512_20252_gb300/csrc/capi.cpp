@@ -136,6 +136,7 @@ void free_all(ibdvm_ctx *ctx) {
   cfree_t(ctx->tree_stg);
   cfree_t(ctx->tree_lrec);
   cfree_t(ctx->tree_far);
+  cfree_t(ctx->tree_sched);
   cfree_t(ctx->partf);
   cfree_t(ctx->d_forces);
   cfree_t(ctx->d_step_forces);
@@ -534,6 +535,7 @@ void upload_tree_tables(ibdvm_ctx *ctx, const std::vector<int> &glink, const std
   upload(ctx, ctx->tree_sti, sti, "upload tree stencils");
   upload(ctx, ctx->tree_stg, stg, "upload tree stencil geometry");
   upload(ctx, ctx->tree_lrec, lrec, "upload tree leaf records");
+  upload(ctx, ctx->tree_sched, tree_schedule(ctx->dim, lrec), "upload tree leaf schedule");
   cfree_t(ctx->tree_far);
   if (!far.empty()) {
     ctx->tree_far = dalloc<int>(ctx, far.size(), "tree donor rows");
@@ -713,9 +715,11 @@ static ibdvm_status create_ctx(const ibdvm_grid_desc *grid, const ibdvm_tree_des
       ctx->tree_sti = dalloc<int>(ctx, sti.size(), "tree stencils");
       ctx->tree_stg = dalloc<double>(ctx, stg.size(), "tree stencil geometry");
       ctx->tree_lrec = dalloc<int>(ctx, lrec.size(), "tree leaf records");
+      ctx->tree_sched = dalloc<int>(ctx, lrec.size() / 8, "tree leaf schedule");
       upload(ctx, ctx->tree_sti, sti, "upload tree stencils");
       upload(ctx, ctx->tree_stg, stg, "upload tree stencil geometry");
       upload(ctx, ctx->tree_lrec, lrec, "upload tree leaf records");
+      upload(ctx, ctx->tree_sched, tree_schedule(G.dim, lrec), "upload tree leaf schedule");
       ctx->tree_nb_h = std::move(tnb);
     }
     ctx->kst = dalloc<int>(ctx, G.nv, "velocity positions");

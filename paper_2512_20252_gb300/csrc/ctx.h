@@ -129,6 +129,7 @@ struct ibdvm_ctx {
   int *tree_sti = nullptr;    // [leaf][10][8] stencil rows and flags (build_tree_stencils)
   double *tree_stg = nullptr; // [leaf][10][4] stencil geometry
   int *tree_lrec = nullptr;   // [leaf][8] side counts, regular flag
+  int *tree_sched = nullptr;  // [leaf] the order of the leaves in the sweep's blocks
   double tree_h0[3] = {0, 0, 0};
   int tree_L = 0;
   std::vector<int> tree_lev_h, tree_own; // leaf levels; the leaf of every finest-grid cell
@@ -188,6 +189,8 @@ bool build_tree_mesh(const ibdvm_grid_desc &root, const ibdvm_tree_desc &t, std:
 void build_tree_stencils(int D, const std::vector<int> &lev, const std::vector<int> &nb, const double h0[3],
                          const std::vector<uint8_t> &type, const std::vector<int> &glink,
                          std::vector<int> &sti, std::vector<double> &stg, std::vector<int> &lrec);
+// the leaves in the order the sweep's blocks take them (regular, other fluid, solid)
+std::vector<int> tree_schedule(int D, const std::vector<int> &lrec);
 // the stencil entries of a leaf (D own + 2 D 2^(D-1) upwind) and the ints of an entry
 __host__ __device__ constexpr int tree_entries(int D) { return D + 2 * D * (1 << (D - 1)); }
 __host__ __device__ constexpr int tree_entry_ints(int D) { return D == 2 ? 8 : 12; }

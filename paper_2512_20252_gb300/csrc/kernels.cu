@@ -401,6 +401,7 @@ template <typename T> struct TreeArgs {
   const int4 *__restrict__ sti;     // [leaf][entries][ints / 4]: stencil rows (-1 none, -2 the halo, -3 - l a ghost value) and the mutual flag
   const double2 *__restrict__ stg;  // [leaf][entries][2]: 1/d-, 1/d+, h, 1/h (own entries)
   const int4 *__restrict__ lrec;    // [leaf][2]: leaves on the sides, regular flag, fluid flag
+  const int *__restrict__ sched;    // [leaf]: the leaf of each block slot (regular, other fluid, solid)
   int qb[3];                        // 2D: first stored position of the quadrants 1, 2, 3 (bit 0: x < 0, bit 1: y < 0)
 };
 
@@ -511,9 +512,10 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && D == 2) ? 4 : 2) tr
   __shared__ int fast[kCellsPerBlock];    // one neighbour of the leaf's own level on every side (2D)
   __shared__ int fluid[kCellsPerBlock];   // the leaf is updated (not a solid leaf of a body, C29)
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const long long c = (long long)blockIdx.x * kCellsPerBlock + ty;
+  const long long slot = (long long)blockIdx.x * kCellsPerBlock + ty;
+  const bool active = slot < A.ncell;
+  const long long c = active ? TA.sched[slot] : slot;
   const int chunk = blockIdx.y;
-  const bool active = c < A.ncell;
   if (active && tx < E) {
     // the stencil tables built on the host (one pass, no chain of lookups)
     const size_t e = (size_t)c * E + tx;
@@ -864,8 +866,8 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && D == 2) ? 4 : 2) tr
     if ((tx & 31) == 0) red[ty][tx >> 5][m] = (double)v;
   }
   __syncthreads();
-  if (c < A.ncell && tx < NM) {
-    double v = active ? red[ty][0][tx] + red[ty][1][tx] : 0.0;
+  if (active && tx < NM) {
+    double v = red[ty][0][tx] + red[ty][1][tx];
     A.part[((size_t)chunk * NM + tx) * A.ncell + c] = v;
   }
 }
@@ -1981,6 +1983,7 @@ template <typename T, int D> cudaError_t tree_sweep_t(ibdvm_ctx *ctx) {
     A.sti = reinterpret_cast<const int4 *>(ctx->tree_sti);
     A.stg = reinterpret_cast<const double2 *>(ctx->tree_stg);
     A.lrec = reinterpret_cast<const int4 *>(ctx->tree_lrec);
+    A.sched = ctx->tree_sched;
     for (int i = 0; i < 3; ++i) A.qb[i] = ctx->tree_qb[i];
     dim3 block(kThreadsPerCell, kCellsPerBlock);
     dim3 grid((unsigned)((ctx->ncell + kCellsPerBlock - 1) / kCellsPerBlock), (unsigned)ctx->nchunk);

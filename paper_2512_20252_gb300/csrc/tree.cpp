@@ -209,6 +209,22 @@ void build_tree_stencils(int D, const std::vector<int> &lev, const std::vector<i
   }
 }
 
+// The order in which the sweep's blocks take the leaves: the regular leaves
+// (the gather-first path), then the other fluid leaves (the general path),
+// then the solid ones, each in the caller's order, so that the four leaves of
+// a block take paths of about the same length.
+std::vector<int> tree_schedule(int D, const std::vector<int> &lrec) {
+  const size_t n = lrec.size() / 8;
+  std::vector<int> sched;
+  sched.reserve(n);
+  for (int cls = 0; cls < 3; ++cls)
+    for (size_t c = 0; c < n; ++c) {
+      const bool fluid = lrec[c * 8 + 2 * D + 1] != 0, regular = lrec[c * 8 + 2 * D] != 0;
+      if ((fluid && regular ? 0 : fluid ? 1 : 2) == cls) sched.push_back(static_cast<int>(c));
+    }
+  return sched;
+}
+
 // A body on a tree (C29): placed on the finest grid Gv by the uniform grid's
 // geometry, then moved onto the leaves.  The ghost band must lie in the
 // finest level, where the tree's arithmetic is the uniform grid's.

@@ -230,6 +230,7 @@ def naca_supersonic_tree(nv=60, precision="mixed", steps=200, root=(80, 112), ma
     [-4,8] x [-6,6].  Like the uniform grid, it loses positivity after about
     550 steps from the impulsive start; throughput runs are short."""
     body = naca0012(1.0, 0.0, 400, center=(0.25, 0.0))
+    root = (root, root * 7 // 5) if np.isscalar(root) else root
     d = _case(2, list(root), ([-3.0, -7.0], [7.0, 7.0]), nv, ([-4.0, -6.0], [8.0, 6.0]), 0.026, 2.0, body,
               precision=precision, steps=steps)
     d["tree"] = tree_leaves(tuple(root), maxlevel, d["lo"], d["hi"], (0.5, 0.0), list(radii), metric="segment",
@@ -533,14 +534,14 @@ def tree_case(root=16, maxlevel=2, L=2.0, nv=12, V=4.5, Kn=0.1, Ma=0.3, radii=No
     return d
 
 
-def tree_2d(precision="mixed", steps=200):
+def tree_2d(precision="mixed", steps=200, root=128):
     """A tree-refined 2D grid at GB300 size: a root grid of 128^2 cells on
     [-8,8]^2 refined around the origin to level 1 within 4, level 2 within 2
     and level 3 within 1 (finest edge 1/64: the 1024^2 uniform grid's), 2:1
     balanced (45,436 leaves), 48^2 velocities on [-6,6]^2, Kn 0.1, Ma 0.5, no
     body (the tree's transport, relaxation and moments alone)."""
-    d = _case(2, 128, 8.0, 48, 6.0, 0.1, 0.5, {"kind": "none"}, precision=precision, steps=steps)
-    d["tree"] = tree_leaves((128, 128), 3, d["lo"], d["hi"], (0.0, 0.0), [4.0, 2.0, 1.0])
+    d = _case(2, root, 8.0, 48, 6.0, 0.1, 0.5, {"kind": "none"}, precision=precision, steps=steps)
+    d["tree"] = tree_leaves((root, root), 3, d["lo"], d["hi"], (0.0, 0.0), [4.0, 2.0, 1.0])
     d["tree_spec"] = {"center": [0.0, 0.0], "radii": [4.0, 2.0, 1.0],
                       "sample": {"root": [16, 16], "maxlevel": 3, "radii": [4.0, 2.0, 1.0]}}
     return d
