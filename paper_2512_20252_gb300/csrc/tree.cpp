@@ -9,6 +9,7 @@
 // none at the domain edge.  The stencil tables of the tree sweep come from
 // these lists; a body placed on the finest grid is moved onto the leaves
 // when its ghost band lies in the finest level.
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -209,19 +210,23 @@ void build_tree_stencils(int D, const std::vector<int> &lev, const std::vector<i
   }
 }
 
-// The order in which the sweep's blocks take the leaves: the regular leaves
-// (the gather-first path), then the other fluid leaves (the general path),
-// then the solid ones, each in the caller's order, so that the four leaves of
-// a block take paths of about the same length.
+// The order in which the sweep's blocks take the leaves: within each window
+// of 256 consecutive leaves (the caller's order, near in space for leaves in
+// Z order), the regular leaves (the gather-first path), then the other fluid
+// leaves (the general path), then the solid ones, so that the four leaves of
+// a block take paths of about the same length while the blocks of a window
+// share the rows they read.
 std::vector<int> tree_schedule(int D, const std::vector<int> &lrec) {
+  constexpr size_t kWindow = 256;
   const size_t n = lrec.size() / 8;
   std::vector<int> sched;
   sched.reserve(n);
-  for (int cls = 0; cls < 3; ++cls)
-    for (size_t c = 0; c < n; ++c) {
-      const bool fluid = lrec[c * 8 + 2 * D + 1] != 0, regular = lrec[c * 8 + 2 * D] != 0;
-      if ((fluid && regular ? 0 : fluid ? 1 : 2) == cls) sched.push_back(static_cast<int>(c));
-    }
+  for (size_t w0 = 0; w0 < n; w0 += kWindow)
+    for (int cls = 0; cls < 3; ++cls)
+      for (size_t c = w0; c < std::min(n, w0 + kWindow); ++c) {
+        const bool fluid = lrec[c * 8 + 2 * D + 1] != 0, regular = lrec[c * 8 + 2 * D] != 0;
+        if ((fluid && regular ? 0 : fluid ? 1 : 2) == cls) sched.push_back(static_cast<int>(c));
+      }
   return sched;
 }
 
