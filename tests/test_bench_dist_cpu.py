@@ -81,3 +81,25 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+
+
+@pytest.mark.parametrize("workload", ["tree_2d", "cylinder_hypersonic_tree", "naca_supersonic_tree", "sphere_96_tree"])
+def test_tree_workloads_have_bounded_oracle_samples(workload):
+    """Every tree workload names a coarser tree the CPU oracle runs in about
+    a second per step (the cpu_baseline and reference legs); the sample keeps
+    the workload's body inside its finest level."""
+    import time
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+
+    case = bench._workload_case(None, workload, "mixed")
+    sample = bench.cpu_sample_case(case)
+    assert sample["precision"] == "fp64" and len(sample["tree"]["level"]) < len(case["tree"]["level"])
+    o = oracle.OracleTree(sample, threads=4)
+    if case["body"]["kind"] != "none":
+        assert o.nfluid < o.nleaf
+    t0 = time.perf_counter()
+    o.step(1)
+    assert time.perf_counter() - t0 < 20.0
