@@ -490,11 +490,11 @@ __device__ __forceinline__ float tree_ex2(float x) {
 }
 constexpr float kTreeLog2e = 1.442695040888963407f;
 
-// FP32 quadtrees: four blocks of 256 threads per SM (the loop waits on
-// gathers from L2 and HBM: resident warps hide it); FP64, bound by its
-// arithmetic, and octrees: two
+// FP32: four blocks of 256 threads per SM (the loop waits on gathers from L2
+// and HBM: resident warps hide it, a few spilled registers cost less); FP64,
+// bound by its arithmetic: two
 template <typename T, int D>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && D == 2) ? 4 : 2) tree_sweep_kernel(TreeArgs<T> TA) {
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4) ? 4 : 2) tree_sweep_kernel(TreeArgs<T> TA) {
   constexpr int NC = Dims<D>::NC;
   constexpr int NM = Dims<D>::NM;
   constexpr int NF = 1 << (D - 1); // leaves at most beyond a face
